@@ -304,7 +304,7 @@ def random_program(seed: int, max_extent: int = 12, max_tasks: int = 10, allow_3
         kdims = B.dims
         chunks = int(rng.integers(1, 7))
         accs = []
-        bad = allow_bad and rng.random() < 0.06 and chunks > 1
+        bad = allow_bad and rng.random() < 0.06 and chunks > 1 and kr[0] > 1
         rw = (not trans) and written[wb] and rng.random() < 0.4
         if bad:
             accs.append(Accessor(wb, WRITE, all_mapper()))

@@ -1,0 +1,207 @@
+"""Pins of the oracle to what the paper states about concrete programs."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2503_10516_gb300 import workloads as W
+from tests.harness import OracleImpl, feed, oracle_graphs
+from tests.replay import (ALLOC, AWAIT_RECEIVE, COPY, FREE, HORIZON, K_FRONT, KERNEL, RECEIVE, SEND,
+                          SPLIT_RECEIVE, _ancestors, task_seqs)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = (x.strip() for x in line.split("="))
+            out[k] = v
+    return out
+
+
+def _mem_of_alloc(g):
+    mem = {}
+    for r in g["instrs"]:
+        if r[1] == ALLOC:
+            mem[int(r[3])] = int(r[4])
+    return mem
+
+
+def _iteration_counts(g, seqs):
+    mem = _mem_of_alloc(g)
+    c = {"kernel": 0, "send": 0, "receive": 0, "split_receive": 0, "horizon": 0, "alloc": 0,
+         "copy.d2h": 0, "copy.h2d": 0, "copy.d2d": 0}
+    for r in g["instrs"]:
+        if int(r[2]) not in seqs:
+            continue
+        t = r[1]
+        if t == KERNEL:
+            c["kernel"] += 1
+        elif t == SEND:
+            c["send"] += 1
+        elif t == RECEIVE:
+            c["receive"] += 1
+        elif t == SPLIT_RECEIVE:
+            c["split_receive"] += 1
+        elif t == HORIZON:
+            c["horizon"] += 1
+        elif t == ALLOC:
+            c["alloc"] += 1
+        elif t == COPY:
+            src, dst = mem.get(int(r[3]), 0), mem[int(r[4])]
+            if src >= 2 and dst == 1:
+                c["copy.d2h"] += 1
+            elif src == 1 and dst >= 2:
+                c["copy.h2d"] += 1
+            elif src >= 2 and dst >= 2:
+                c["copy.d2d"] += 1
+    return c
+
+
+def test_nbody_worked_example_node0():
+    """Sec. 3.6: the instruction graph of node N0 for Listing 1 on 2 nodes x 2 devices."""
+    gold = _golden("nbody_2x2_node0.txt")
+    n = 64
+    p = W.nbody_example_program(n=n, iterations=5)
+    gs, rej = oracle_graphs(p)
+    g = gs[0]
+    assert not rej
+    # first iteration allocations: P whole on M2 and M3, V quarters
+    allocs = [(int(r[5]), int(r[4]), tuple(int(v) for v in g["boxes"][r[7]])) for r in g["instrs"] if r[1] == ALLOC]
+    whole = (0, 0, 0, n, 1, 1)
+    assert (0, 2, whole) in allocs and (0, 3, whole) in allocs
+    assert gold["first.alloc.P.M2"] == "whole" and gold["first.alloc.P.M3"] == "whole"
+    assert (1, 2, (0, 0, 0, n // 4, 1, 1)) in allocs
+    assert (1, 3, (n // 4, 0, 0, n // 2, 1, 1)) in allocs
+    # every later iteration has the steady topology
+    seqs = task_seqs(p)
+    hseq = lambda k: seqs[2 * k + 1] + 1  # horizon after each iteration (horizon step 2)
+    for k in range(2, 5):
+        it = {seqs[2 * k], seqs[2 * k + 1], hseq(k)}
+        c = _iteration_counts(g, it)
+        for key, v in gold.items():
+            if key.startswith("steady."):
+                assert c[key[len("steady."):]] == int(v), (k, key, c)
+        assert c["alloc"] == 0
+    # sends and the receive of one iteration are mutually concurrent (Fig. 5 caption)
+    anc, _ = _ancestors(g["instrs"], g["edges"])
+    for k in range(1, 5):
+        ids = [i for i, r in enumerate(g["instrs"]) if int(r[2]) == seqs[2 * k] and r[1] in (SEND, RECEIVE)]
+        assert len(ids) == 3
+        for a in ids:
+            for b in ids:
+                if a < b:
+                    assert not (anc[b] >> a) & 1, "send/receive ordered"
+    # a horizon depends exactly on the execution front (instructions without successors)
+    succ = set(int(e[0]) for e in g["edges"])
+    for i, r in enumerate(g["instrs"]):
+        if r[1] == HORIZON:
+            preds = [int(e[0]) for e in g["edges"] if int(e[1]) == i]
+            assert all(int(e[2]) == K_FRONT for e in g["edges"] if int(e[1]) == i)
+            for q in preds:
+                later = [int(e[1]) for e in g["edges"] if int(e[0]) == q and int(e[1]) < i]
+                assert not later, "horizon predecessor already had a successor"
+
+
+@pytest.mark.parametrize("lookahead,resizes", [(0, 1), (1, 0), (4, 0)])
+def test_listing2_resize(lookahead, resizes):
+    """Listing 2: one_to_one write, then neighborhood read -> one resize per
+    device without lookahead (Sec. 4.3), none with lookahead."""
+    p = W.listing2_program(16, lookahead, nodes=1, devices=2, chunks=2)
+    g = oracle_graphs(p)[0][0]
+    frees = [r for r in g["instrs"] if r[1] == FREE]
+    resize_copies = [r for r in g["instrs"] if r[1] == COPY and r[6] == 1]
+    assert len(frees) == 2 * resizes
+    assert len(resize_copies) == 2 * resizes
+
+
+def test_rsim_growing_resizes_every_step_without_lookahead():
+    """Sec. 5 (RSim): a buffer growing by rows resizes on every time step."""
+    p = W.growing_program(rows_max=96, cols=4, grow=(1, 6), devices=2, chunks=2, lookahead=0)
+    g = oracle_graphs(p)[0][0]
+    seqs = task_seqs(p)
+    free_seqs = {int(r[2]) for r in g["instrs"] if r[1] == FREE}
+    assert all(s in free_seqs for s in seqs[1:]), "a step without a resize"
+
+
+def test_rsim_growing_no_resize_with_unbounded_lookahead():
+    """Sec. 4.3: with the queue never flushed before the end, the first
+    instructions already hold allocations covering the whole program."""
+    p = W.growing_program(rows_max=96, cols=4, grow=(1, 6), devices=2, chunks=2, lookahead=0xFFFFFFFF)
+    g = oracle_graphs(p)[0][0]
+    assert not any(r[1] == FREE for r in g["instrs"])
+    assert not any(r[1] == COPY and r[6] == 1 for r in g["instrs"])
+
+
+def test_overlapping_write_rejected():
+    """Sec. 4.4: an all-mapper write split over two devices is an error."""
+    rng = np.random.default_rng(3)
+    buf = W.Buffer(1, (16, 1, 1), 4, rng.integers(0, 2**32, 16, dtype=np.uint64).astype(np.uint32), "u32")
+    ops = [("buffer", buf),
+           ("task", W.Task(1, (16, 1, 1), 2, W.K_GENERIC, [W.Accessor(0, W.WRITE, W.all_mapper())])),
+           ("task", W.Task(1, (16, 1, 1), 2, W.K_GENERIC, [W.Accessor(0, W.READ_WRITE, W.one_to_one())])),
+           ("flush",)]
+    p = W.Program("overlap", 1, 2, 4, 0, ops)
+    impl = OracleImpl(p)
+    res = feed(impl, p)
+    assert res == [-2, 0]
+    bad = task_seqs(p)[0]
+    assert impl.rejected() == [bad]
+    g = impl.graph(0)
+    assert not any(int(r[2]) == bad for r in g["instrs"])
+    # the accepted task still reads the host data: copies from the user allocation on M0
+    alloced = {int(r[3]) for r in g["instrs"] if r[1] == ALLOC}
+    srcs = {int(r[3]) for r in g["instrs"] if r[1] == COPY}
+    assert srcs and all(s not in alloced for s in srcs)
+
+
+def test_uninitialized_read_warning():
+    """Sec. 4.4: reading a never-written region of a buffer is reported."""
+    ops = [("buffer", W.Buffer(2, (8, 8, 1), 4, None, "u32")),
+           ("buffer", W.Buffer(2, (8, 8, 1), 4, None, "u32")),
+           ("task", W.Task(2, (8, 8, 1), 2, W.K_GENERIC,
+                           [W.Accessor(1, W.WRITE, W.one_to_one()), W.Accessor(0, W.READ, W.one_to_one())])),
+           ("flush",)]
+    p = W.Program("uninit", 1, 2, 4, 0, ops)
+    g = oracle_graphs(p)[0][0]
+    seq = task_seqs(p)[0]
+    assert sorted(map(tuple, g["diags"].tolist())) == [(seq, 0, 1), (seq, 1, 1)]
+    assert not any(r[1] == COPY for r in g["instrs"])
+
+
+def test_single_device_one_to_one_needs_no_copies_after_first_use():
+    """With one node and one device, one_to_one-only programs copy host data once."""
+    rng = np.random.default_rng(5)
+    ops = [("buffer", W.Buffer(2, (8, 8, 1), 4, rng.integers(0, 2**32, 64, dtype=np.uint64).astype(np.uint32), "u32"))]
+    for _ in range(6):
+        ops.append(("task", W.Task(2, (8, 8, 1), 3, W.K_GENERIC, [W.Accessor(0, W.READ_WRITE, W.one_to_one())])))
+    ops.append(("flush",))
+    p = W.Program("o2o", 1, 1, 2, 0, ops)
+    g = oracle_graphs(p)[0][0]
+    seqs = task_seqs(p)
+    copy_seqs = [int(r[2]) for r in g["instrs"] if r[1] == COPY]
+    assert copy_seqs and set(copy_seqs) == {seqs[0]}
+
+
+def test_split_receive_when_consumers_differ():
+    """Sec. 3.4: consumers reading different parts of an awaited region get a
+    split receive and one await receive each."""
+    n = 16
+    rng = np.random.default_rng(9)
+    init = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+    ops = [("buffer", W.Buffer(1, (n, 1, 1), 4, init, "u32")), ("buffer", W.Buffer(1, (n, 1, 1), 4, None, "u32")),
+           # node 1 (chunks 2,3) overwrites the upper half
+           ("task", W.Task(1, (n, 1, 1), 4, W.K_GENERIC, [W.Accessor(0, W.READ_WRITE, W.one_to_one())])),
+           # node 0's two devices read the upper half shifted differently
+           ("task", W.Task(1, (n, 1, 1), 4, W.K_GENERIC,
+                           [W.Accessor(1, W.WRITE, W.one_to_one()),
+                            W.Accessor(0, W.READ, [W.affine(0, n // 2, 0), W.all_dim(), W.all_dim()])])),
+           ("flush",)]
+    p = W.Program("split", 2, 2, 8, 0, ops)
+    g = oracle_graphs(p)[0][0]
+    kinds = [int(r[1]) for r in g["instrs"]]
+    assert kinds.count(SPLIT_RECEIVE) == 1
+    assert kinds.count(AWAIT_RECEIVE) == 2

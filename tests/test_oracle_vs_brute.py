@@ -1,0 +1,39 @@
+"""The oracle emits exactly the graph of the per-element brute-force generator."""
+import pytest
+
+from paper_2503_10516_gb300 import workloads as W
+from tests.harness import BruteImpl, OracleImpl, assert_same_graph, feed
+
+
+def _check(p):
+    o, b = OracleImpl(p), BruteImpl(p)
+    r1, r2 = feed(o, p), feed(b, p)
+    assert r1 == r2
+    assert o.rejected() == b.rejected()
+    for n in range(p.nodes):
+        assert_same_graph(o.graph(n), b.graph(n), f"{p.name} node {n}")
+
+
+@pytest.mark.parametrize("seed", range(400))
+def test_random_programs(seed):
+    _check(W.random_program(seed, max_extent=10, max_tasks=12))
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_programs_uninitialized_reads(seed):
+    _check(W.random_program(50_000 + seed, max_extent=8, max_tasks=8, uninit_reads=True))
+
+
+@pytest.mark.parametrize("prog", [
+    W.jacobi_program(n=16, steps=6),
+    W.listing2_program(8, 0, devices=2, chunks=2),
+    W.listing2_program(8, 1, devices=2, chunks=2),
+    W.nbody_example_program(n=16, iterations=3),
+    W.growing_program(rows_max=24, cols=4, grow=(1, 4)),
+    W.growing_program(rows_max=24, cols=4, grow=(1, 4), lookahead=0xFFFFFFFF),
+    W.growing_program(rows_max=30, cols=1, grow=(1, 5), devices=3, chunks=3, lookahead=2),
+    W.wave_program(n=16, steps=6, nodes=2, devices=2, chunks=8, lookahead=2),
+    W.wave_program(n=12, steps=5, nodes=3, devices=1, chunks=5, lookahead=0),
+], ids=lambda p: f"{p.name}-L{p.lookahead}")
+def test_paper_shaped_programs(prog):
+    _check(prog)

@@ -1,0 +1,248 @@
+/* igs.h — GB300-native instruction-graph lowering and box copies (C ABI).
+ *
+ * Implements the data-parallel hot path of the instruction-graph scheduler of
+ * "Concurrent Scheduling of High-Level Parallel Programs on Multi-GPU
+ * Systems" (Knorr, Salzmann, Thoman, Fahringer): a stream of Celerity-style
+ * tasks (a kernel over an index range split into chunks, with range-mapped
+ * buffer accesses; Sec. 2.1, Listing 1) is lowered into per-node instruction
+ * graphs — alloc, free, copy, send, receive, split receive, await receive,
+ * device kernel, horizon, epoch instructions and dependency edges (Sec. 3,
+ * Table 1) — with scheduler lookahead merging allocations (Sec. 4.3). The
+ * emitted graph can then be executed on one GPU, virtual nodes and devices
+ * being disjoint HBM partitions, box copies running as CUDA kernels.
+ *
+ * All lowering runs in CUDA kernels on the device (region maps stay in HBM
+ * between calls); this header holds plain C types only.
+ *
+ * Conventions
+ *   Return codes: IGS_OK (0) or a negative IGS_ERR_* code. No C++ exception
+ *   crosses this boundary. igs_last_error() gives a message for the last
+ *   failing call on a context.
+ *   Ownership: the library owns every igs_ctx and all device state; the
+ *   caller owns every pointer it passes (host_init is read during the call
+ *   only; fetch/read destinations are written before the call returns).
+ *   Threading: one context must not be used from two threads at once;
+ *   different contexts are independent.
+ *   Ids: buffer ids are dense per context in creation order. Instruction,
+ *   allocation and message ids are dense per virtual node (each node builds
+ *   its own instruction graph, Sec. 2.4); instruction 0 of every node is the
+ *   initial epoch.
+ *   Memory ids (Sec. 3.2): 0 = user host memory (host_init data, shared by
+ *   all nodes), 1 = the node's pinned staging memory, 2 + d = device d of the
+ *   node.
+ *   Boxes: half-open [lo, hi) in three dimensions, dim 0 slowest; a
+ *   1- or 2-dimensional buffer has extent 1 in its unused trailing dims.
+ */
+#ifndef IGS_H
+#define IGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes -------------------------------------------------------- */
+#define IGS_OK 0
+#define IGS_ERR_INVALID_ARG -1      /* malformed descriptor, unknown buffer, bad config */
+#define IGS_ERR_OVERLAPPING_WRITE -2 /* chunks of one task write overlapping regions (Sec. 4.4) */
+#define IGS_ERR_CAPACITY -3         /* a device-side table or output array is full */
+#define IGS_ERR_TRUNCATED -4        /* caller's fetch arrays too small; counts hold the sizes needed */
+#define IGS_ERR_TIMEOUT -5          /* a bounded device-side wait gave up */
+#define IGS_ERR_CUDA -6             /* a CUDA runtime call failed */
+#define IGS_ERR_BUDGET -7           /* HBM admission budget exceeded (serving) */
+#define IGS_ERR_STATE -8            /* call not valid in the context's current state */
+
+/* ---- instruction types (Table 1) and dependency kinds (Fig. 5 legend) ---- */
+enum igs_instruction_type {
+  IGS_EPOCH = 0, IGS_HORIZON = 1, IGS_ALLOC = 2, IGS_FREE = 3, IGS_COPY = 4, IGS_SEND = 5,
+  IGS_RECEIVE = 6, IGS_SPLIT_RECEIVE = 7, IGS_AWAIT_RECEIVE = 8, IGS_KERNEL = 9
+};
+enum igs_dependency_kind {
+  IGS_DEP_DATAFLOW = 1,  /* read after write */
+  IGS_DEP_ANTI = 2,      /* write after read or write (anti- and output dependencies) */
+  IGS_DEP_ALLOC = 4,     /* allocation lifetime: alloc -> first use, uses -> free */
+  IGS_DEP_EPOCH = 8,     /* no other predecessor: depends on the last epoch / applied horizon */
+  IGS_DEP_FRONT = 16     /* horizon or epoch on the execution front */
+};
+
+/* access modes (Sec. 2.1; WRITE is write_only with no_init) */
+#define IGS_READ 1u
+#define IGS_WRITE 2u
+#define IGS_READ_WRITE 3u
+
+/* range-mapper dimension kinds (Sec. 2.1 one_to_one / all / neighborhood; Listing 2) */
+#define IGS_MAP_AFFINE 0u /* [klo[a] + (int32)b - c, khi[a] + (int32)b + c): kernel dim a, offset b, radius c */
+#define IGS_MAP_ALL 1u    /* [0, extent) */
+#define IGS_MAP_FIXED 2u  /* [a, b) */
+
+#define IGS_MAX_ACCESSORS 8
+#define IGS_LOOKAHEAD_INFINITE 0xFFFFFFFFu
+#define IGS_NONE 0xFFFFFFFFu
+
+/* lowering modes */
+#define IGS_MODE_PLAIN 0u   /* every submit lowers that task in its own launch */
+#define IGS_MODE_BATCHED 1u /* submits accumulate; igs_flush / igs_lower_batch lower them in one launch */
+
+typedef struct igs_config {
+  uint32_t num_nodes;        /* virtual nodes, 1..32 */
+  uint32_t devices_per_node; /* virtual devices per node, 1..29 */
+  uint32_t horizon_step;     /* a horizon after every k submitted tasks; 0 = none (Sec. 3.5) */
+  uint32_t lookahead;        /* scheduler lookahead window in tasks (Sec. 4.3); IGS_LOOKAHEAD_INFINITE */
+  uint32_t mode;             /* IGS_MODE_PLAIN or IGS_MODE_BATCHED */
+  uint32_t max_instructions; /* per node output capacity; 0 = default (1 << 20) */
+  uint32_t max_edges;        /* per node; 0 = default (4 x max_instructions) */
+  uint32_t max_boxes;        /* per node; 0 = default (4 x max_instructions) */
+  uint32_t map_capacity;     /* entries per device-side region map; 0 = default (16384) */
+  uint32_t scratch_capacity; /* boxes per device-side scratch table; 0 = default (8192) */
+  int device;                /* CUDA device ordinal */
+  void* stream;              /* cudaStream_t to launch on; NULL = the library's own stream */
+} igs_config;
+
+typedef struct igs_map_dim { uint32_t kind, a, b, c; } igs_map_dim;
+
+typedef struct igs_accessor {
+  uint32_t buffer;        /* buffer id */
+  uint32_t mode;          /* IGS_READ / IGS_WRITE / IGS_READ_WRITE */
+  igs_map_dim dim[3];     /* range mapper, one descriptor per buffer dimension */
+} igs_accessor;
+
+/* A task: a kernel over `range` (dims 1..3, trailing extents 1), split along
+ * dim 0 into num_chunks chunks (Sec. 3.1). Same layout as 11 + 14 * 8 uint32
+ * words. */
+typedef struct igs_task {
+  uint32_t dims;
+  uint32_t range[3];
+  uint32_t num_chunks;    /* >= 1 */
+  uint32_t kernel_id;     /* workload kernel run by execute (0 = none) */
+  uint32_t num_accessors; /* 0..8 */
+  uint32_t params[4];     /* workload kernel parameters */
+  igs_accessor acc[IGS_MAX_ACCESSORS];
+} igs_task;
+
+/* Output records (all uint32). Field meaning by type:
+ *   ALLOC  a=allocation id, b=memory, c=buffer; boxes = [allocation box]
+ *   FREE   a=allocation id, b=memory, c=buffer
+ *   COPY   a=source allocation, b=destination allocation, c=buffer,
+ *          d=0 coherence copy / 1 resize copy; boxes = canonical region
+ *   SEND   a=staging allocation, b=target node, c=buffer, d=message id; boxes = [box]
+ *   RECEIVE / SPLIT_RECEIVE  a=staging allocation, c=buffer; boxes = awaited region
+ *   AWAIT_RECEIVE  a=staging allocation, b=split receive id, c=buffer; boxes = region
+ *   KERNEL a=chunk index, b=memory, c=kernel id; boxes = [chunk box];
+ *          bindings = one per accessor (allocation or IGS_NONE, accessed box)
+ *   EPOCH / HORIZON  no fields
+ * Unused fields are IGS_NONE. seq is the submission sequence number of the
+ * buffer / task / horizon / epoch / destroy that emitted the instruction. */
+typedef struct igs_instruction {
+  uint32_t id, type, seq, a, b, c, d, box_off, box_cnt, bind_off, bind_cnt;
+} igs_instruction;
+typedef struct igs_edge { uint32_t from, to, kind; } igs_edge;       /* from = predecessor */
+typedef struct igs_box { uint32_t lo[3], hi[3]; } igs_box;
+typedef struct igs_binding { uint32_t alloc; uint32_t lo[3], hi[3]; } igs_binding;
+typedef struct igs_diag { uint32_t seq, chunk, accessor; } igs_diag; /* uninitialized read (Sec. 4.4) */
+
+/* Caller-owned destination arrays for igs_fetch_instructions. On entry the
+ * *_cap fields give capacities; on return the num_* fields give the counts of
+ * the whole graph of `node` so far. */
+typedef struct igs_graph_view {
+  uint32_t node;
+  igs_instruction* instrs; uint32_t instr_cap, num_instrs;
+  igs_edge* edges;         uint32_t edge_cap, num_edges;
+  igs_box* boxes;          uint32_t box_cap, num_boxes;
+  igs_binding* binds;      uint32_t bind_cap, num_binds;
+  igs_diag* diags;         uint32_t diag_cap, num_diags;
+} igs_graph_view;
+
+typedef struct igs_ctx igs_ctx;
+
+/* Creates a lowering context on cfg->device (Sec. 3: one instruction graph per
+ * virtual node; initial epoch I0 emitted on every node). Allocates the
+ * device-resident region maps and output arrays. *out is NULL on error. */
+int igs_create(const igs_config* cfg, igs_ctx** out);
+void igs_destroy(igs_ctx* ctx);
+
+/* Creates a virtual buffer (Sec. 2.2, Sec. 3.2). host_init (nullable): extent
+ * product x elem_size bytes, row-major, copied during the call into user
+ * memory M0; NULL leaves the buffer uninitialized (reads warn, Sec. 4.4). */
+int igs_create_buffer(igs_ctx* ctx, uint32_t dims, const uint32_t extent[3], uint32_t elem_size,
+                      const void* host_init, uint32_t* out_buffer);
+
+/* Drops the user's buffer: emits the frees of its backing allocations once
+ * every queued task has been lowered (Sec. 3.2, last paragraph). */
+int igs_destroy_buffer(igs_ctx* ctx, uint32_t buffer);
+
+/* Submits one task (Sec. 2.1). Validates the descriptor on the host; the
+ * lowering itself (chunking, mappers, push / await push, allocations,
+ * coherence, transfers, dependencies) runs on the device — immediately in
+ * IGS_MODE_PLAIN, at the next flush in IGS_MODE_BATCHED. A task whose chunks
+ * write overlapping regions is rejected by the device (no instructions, no
+ * state change) and reported by the next igs_flush / igs_sync as
+ * IGS_ERR_OVERLAPPING_WRITE. *out_seq receives the task's sequence number. */
+int igs_submit_task(igs_ctx* ctx, const igs_task* task, uint64_t* out_seq);
+
+/* Sets the scheduler lookahead window (Sec. 4.3): tasks queue while an
+ * allocating task is queued and are compiled once more than `window_tasks`
+ * tasks are queued, or at an epoch / buffer destruction. */
+int igs_set_lookahead(igs_ctx* ctx, uint32_t window_tasks);
+
+/* Submits an epoch (Sec. 2.4): compiles every queued task, then emits an epoch
+ * instruction on every node that depends on the execution front. Lowers all
+ * pending submissions and waits for the device. Returns the first rejected
+ * task's error, if any. */
+int igs_flush(igs_ctx* ctx);
+
+/* Lowers pending submissions (no epoch) and waits for the device. */
+int igs_sync(igs_ctx* ctx);
+
+/* Copies node view->node's graph (everything emitted so far) into the
+ * caller's arrays. IGS_ERR_TRUNCATED if a capacity is too small (counts are
+ * still filled in). */
+int igs_fetch_instructions(igs_ctx* ctx, igs_graph_view* view);
+
+/* Sequence numbers of rejected tasks: writes up to cap of them; *count = total. */
+int igs_rejected_tasks(igs_ctx* ctx, uint64_t* seqs, uint32_t cap, uint32_t* count);
+
+/* Executes every instruction emitted and not yet executed, on the device, in
+ * an order that respects the graph: allocations from a stream-ordered pool,
+ * copies and send/receive pairs (matched by task, buffer and receiver) as
+ * box-copy kernels, device kernels as the workload kernels. Asynchronous on
+ * the context's stream unless IGS_EXEC_SYNC. */
+#define IGS_EXEC_SYNC 1u
+int igs_execute(igs_ctx* ctx, uint32_t flags);
+
+/* Reads box [lo, hi) of a buffer, after execute, from the memory holding the
+ * newest version of each element, into host_dst (row-major, elem_size each). */
+int igs_read_buffer(igs_ctx* ctx, uint32_t buffer, const uint32_t lo[3], const uint32_t hi[3], void* host_dst);
+
+/* Lowers the pending submissions of n contexts in ONE persistent launch (all
+ * contexts must share a device). Waits for completion. */
+int igs_lower_batch(igs_ctx* const* ctxs, uint32_t n);
+
+/* Counters: [0] instructions, [1] edges, [2] boxes, [3] map entries read,
+ * [4] map entries written, [5] launches of the lowering kernel, summed over
+ * nodes. */
+int igs_counters(igs_ctx* ctx, uint64_t out[8]);
+
+const char* igs_last_error(const igs_ctx* ctx);
+
+/* ---- box copies (Table 1 "copy"; a11) ------------------------------------ */
+/* One strided box copy job: copy box [lo, hi) (buffer coordinates) from an
+ * allocation holding box src_box at src to one holding dst_box at dst,
+ * elem_size bytes per element. Both allocations are row-major over their box.
+ * Pointers are device pointers. */
+typedef struct igs_copy_job {
+  const void* src; void* dst;
+  igs_box src_box, dst_box, box;
+  uint32_t elem_size;
+} igs_copy_job;
+
+/* Runs n box-copy jobs in one launch on `stream` (cudaStream_t, NULL =
+ * default stream). jobs is a HOST array; the library stages it on the
+ * device. Jobs must not overlap in their destinations. */
+int igs_box_copy(const igs_copy_job* jobs, uint32_t n, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGS_H */

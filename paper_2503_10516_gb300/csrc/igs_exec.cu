@@ -1,0 +1,289 @@
+// Execution kernels: strided box copies (copy / send-receive instructions,
+// paper Table 1) and the workload kernels launched by device-kernel
+// instructions. Compiled with -fmad=false so the float workload kernels round
+// after every operation, in the order written.
+#include <cuda_runtime.h>
+
+#include "igs_exec.h"
+
+namespace igs {
+
+// Set when a workload kernel meets an index outside its allocation (the
+// access is skipped); read and cleared by the executor after every call.
+__device__ uint32_t g_exec_error = 0;
+
+namespace {
+
+// ---- box copy ---------------------------------------------------------------
+//
+// A job is a 3-level strided copy: rows0 x rows1 rows of `run` contiguous
+// bytes. Work units are (job, row0, row1, segment of seg_bytes); a CTA copies
+// one unit at a time with 16-byte vectors when every address and the length
+// allow it. The grid is persistent (a multiple of the SM count).
+
+__device__ __forceinline__ uint32_t find_job(const CopyJob* jobs, uint32_t n, uint64_t u) {
+  uint32_t lo = 0, hi = n;  // last job with unit_begin <= u
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (jobs[mid].unit_begin <= u) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) box_copy_kernel(const CopyJob* __restrict__ jobs, uint32_t n_jobs,
+                                                       uint64_t n_units) {
+  for (uint64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+    const uint32_t j = find_job(jobs, n_jobs, u);
+    const CopyJob& J = jobs[j];
+    const uint64_t local = u - J.unit_begin;
+    const uint32_t segs = (J.extent[2] + J.seg_bytes - 1) / J.seg_bytes;
+    const uint64_t row = local / segs;
+    const uint32_t seg = (uint32_t)(local % segs);
+    const uint32_t r0 = (uint32_t)(row / J.extent[1]), r1 = (uint32_t)(row % J.extent[1]);
+    const uint32_t off = seg * J.seg_bytes;
+    const uint32_t len = min(J.seg_bytes, J.extent[2] - off);
+    const uint8_t* s = J.src + r0 * J.src_stride[0] + r1 * J.src_stride[1] + off;
+    uint8_t* d = J.dst + r0 * J.dst_stride[0] + r1 * J.dst_stride[1] + off;
+    if ((((uintptr_t)s | (uintptr_t)d | len) & 15u) == 0) {
+      const uint4* s4 = reinterpret_cast<const uint4*>(s);
+      uint4* d4 = reinterpret_cast<uint4*>(d);
+      const uint32_t n4 = len >> 4;
+      for (uint32_t i = threadIdx.x; i < n4; i += blockDim.x) d4[i] = __ldcs(s4 + i);
+    } else if ((((uintptr_t)s | (uintptr_t)d | len) & 3u) == 0) {
+      const uint32_t* s1 = reinterpret_cast<const uint32_t*>(s);
+      uint32_t* d1 = reinterpret_cast<uint32_t*>(d);
+      const uint32_t n1 = len >> 2;
+      for (uint32_t i = threadIdx.x; i < n1; i += blockDim.x) d1[i] = s1[i];
+    } else {
+      for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) d[i] = s[i];
+    }
+  }
+}
+
+// ---- workload kernels ---------------------------------------------------------
+
+// Address of element p in an allocation; nullptr (and the error flag) if p
+// lies outside the allocation's box or the accessor has no allocation.
+__device__ __forceinline__ uint8_t* elem_ptr(const KAcc& a, uint32_t p0, uint32_t p1, uint32_t p2) {
+  if (!a.valid || p0 < a.lo[0] || p0 >= a.hi[0] || p1 < a.lo[1] || p1 >= a.hi[1] || p2 < a.lo[2] || p2 >= a.hi[2]) {
+    atomicOr(&g_exec_error, 1u);
+    return nullptr;
+  }
+  const uint64_t w1 = a.hi[1] - a.lo[1], w2 = a.hi[2] - a.lo[2];
+  return a.ptr + ((((uint64_t)(p0 - a.lo[0]) * w1) + (p1 - a.lo[1])) * w2 + (p2 - a.lo[2])) * a.elem;
+}
+
+// Low corner of the mapped box of one kernel item, false if clamped empty.
+__device__ bool item_lo(const KAcc& a, const uint32_t item[3], uint32_t p[3]) {
+  for (int d = 0; d < 3; ++d) {
+    int64_t l, h;
+    const uint32_t ext = a.ext[d];
+    if (d >= (int)a.dims) {
+      l = 0;
+      h = 1;
+    } else if (a.map[d].kind == IGS_MAP_ALL) {
+      l = 0;
+      h = ext;
+    } else if (a.map[d].kind == IGS_MAP_FIXED) {
+      l = a.map[d].a;
+      h = a.map[d].b;
+    } else {
+      const int64_t off = (int32_t)a.map[d].b;
+      l = (int64_t)item[a.map[d].a] + off - a.map[d].c;
+      h = (int64_t)item[a.map[d].a] + off + a.map[d].c + 1;
+    }
+    l = l < 0 ? 0 : l;
+    h = h > (int64_t)ext ? (int64_t)ext : h;
+    if (l >= h) return false;
+    p[d] = (uint32_t)l;
+  }
+  return true;
+}
+
+__device__ __forceinline__ uint32_t mix(uint32_t seq, uint32_t w, uint32_t lin) {
+  uint32_t h = seq * 0x9E3779B1u + (w + 1u) * 0x85EBCA77u + lin * 0xC2B2AE3Du;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  return h;
+}
+
+__device__ __forceinline__ float ldf(const KAcc& a, uint32_t y, uint32_t x) {
+  const uint8_t* p = elem_ptr(a, y, x, 0);
+  return p ? *reinterpret_cast<const float*>(p) : 0.0f;
+}
+__device__ __forceinline__ void stf(const KAcc& a, uint32_t y, uint32_t x, float v) {
+  uint8_t* p = elem_ptr(a, y, x, 0);
+  if (p) *reinterpret_cast<float*>(p) = v;
+}
+__device__ __forceinline__ float4 ld4(const KAcc& a, uint32_t i) {
+  const uint8_t* p = elem_ptr(a, i, 0, 0);
+  return p ? *reinterpret_cast<const float4*>(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ void st4(const KAcc& a, uint32_t i, float4 v) {
+  uint8_t* p = elem_ptr(a, i, 0, 0);
+  if (p) *reinterpret_cast<float4*>(p) = v;
+}
+
+__device__ void run_item(const KernelJob& J, uint32_t y, uint32_t x, uint32_t z) {
+  switch (J.kernel) {
+    case K_JACOBI:
+    case K_WAVE: {
+      const bool wave = J.kernel == K_WAVE;
+      const KAcc& U = J.acc[wave ? 1 : 0];
+      const KAcc& O = J.acc[wave ? 2 : 1];
+      const uint32_t H = U.ext[0], W = U.ext[1];
+      const float c = ldf(U, y, x);
+      float v = c;
+      if (y > 0 && y + 1 < H && x > 0 && x + 1 < W) {
+        const float n = ldf(U, y - 1, x), s = ldf(U, y + 1, x), w = ldf(U, y, x - 1), e = ldf(U, y, x + 1);
+        if (!wave) {
+          v = ((n + s) + (w + e)) * 0.25f;
+        } else {
+          const float pv = ldf(J.acc[0], y, x);
+          const float t2 = (2.0f * c) - pv;
+          const float t5 = (n + s) + (w + e);
+          const float t8 = 0.25f * (t5 - 4.0f * c);
+          v = t2 + t8;
+        }
+      }
+      stf(O, y, x, v);
+      break;
+    }
+    case K_NBODY_STEP: {
+      const KAcc& P = J.acc[0];
+      const KAcc& V = J.acc[1];
+      const uint32_t n = P.ext[0];
+      const float4 pi = ld4(P, y);
+      float ax = 0.f, ay = 0.f, az = 0.f;
+      for (uint32_t j = 0; j < n; ++j) {
+        const float4 pj = ld4(P, j);
+        const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+        const float r2 = ((dx * dx + dy * dy) + dz * dz) + 1e-6f;
+        const float s = sqrtf(r2);
+        const float inv = 1.0f / (r2 * s);
+        const float wgt = pj.w * inv;
+        ax = ax + dx * wgt;
+        ay = ay + dy * wgt;
+        az = az + dz * wgt;
+      }
+      float4 v = ld4(V, y);
+      v.x = v.x + ax * 0.01f;
+      v.y = v.y + ay * 0.01f;
+      v.z = v.z + az * 0.01f;
+      st4(V, y, v);
+      break;
+    }
+    case K_NBODY_UPDATE: {
+      const float4 v = ld4(J.acc[0], y);
+      float4 p = ld4(J.acc[1], y);
+      p.x = p.x + v.x * 0.01f;
+      p.y = p.y + v.y * 0.01f;
+      p.z = p.z + v.z * 0.01f;
+      st4(J.acc[1], y, p);
+      break;
+    }
+    case K_GROW: {
+      if (J.nacc == 1) {
+        const float v = (float)((y * 131u + x * 7u) & 1023u) * 0.5f;
+        stf(J.acc[0], y, x, v);
+      } else {
+        const uint32_t r = J.params[0];
+        const uint32_t yy = y + r;
+        const float last = ldf(J.acc[0], r - 1, x);
+        const float v = last * 0.5f + (float)(yy & 255u);
+        stf(J.acc[1], yy, x, v);
+      }
+      break;
+    }
+    case K_GENERIC: {
+      const uint32_t item[3] = {y, x, z};
+      uint32_t s = 0;
+      for (uint32_t a = 0; a < J.nacc; ++a) {
+        const KAcc& A = J.acc[a];
+        if (!A.valid || !(A.mode & IGS_READ)) continue;
+        uint32_t p[3];
+        if (!item_lo(A, item, p)) continue;
+        const uint8_t* q = elem_ptr(A, p[0], p[1], p[2]);
+        if (q) s += *reinterpret_cast<const uint32_t*>(q);
+      }
+      for (uint32_t a = 0; a < J.nacc; ++a) {
+        const KAcc& A = J.acc[a];
+        if (!A.valid || !(A.mode & IGS_WRITE)) continue;
+        uint32_t p[3];
+        if (!item_lo(A, item, p)) continue;
+        const uint32_t lin = (p[0] * A.ext[1] + p[1]) * A.ext[2] + p[2];
+        uint8_t* q = elem_ptr(A, p[0], p[1], p[2]);
+        if (q) *reinterpret_cast<uint32_t*>(q) = mix(J.seq, a, lin) + s;
+      }
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+__device__ __forceinline__ uint32_t find_kjob(const KernelJob* jobs, uint32_t n, uint64_t u) {
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (jobs[mid].item_begin <= u) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// One thread per kernel item over all jobs of a wave (independent chunks).
+// GENERIC reads its inputs before any write of the same item; items of one
+// chunk never write a location another item of the chunk reads.
+__global__ void __launch_bounds__(256) workload_kernel(const KernelJob* __restrict__ jobs, uint32_t n_jobs,
+                                                       uint64_t n_items) {
+  for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n_items; u += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = find_kjob(jobs, n_jobs, u);
+    const KernelJob& J = jobs[j];
+    uint64_t local = u - J.item_begin;
+    const uint32_t e1 = J.hi[1] - J.lo[1], e2 = J.hi[2] - J.lo[2];
+    const uint32_t z = J.lo[2] + (uint32_t)(local % e2);
+    local /= e2;
+    const uint32_t x = J.lo[1] + (uint32_t)(local % e1);
+    const uint32_t y = J.lo[0] + (uint32_t)(local / e1);
+    run_item(J, y, x, z);
+  }
+}
+
+}  // namespace
+}  // namespace igs
+
+int igs_launch_copies(const igs::CopyJob* jobs_dev, uint32_t n_jobs, uint64_t n_units, void* stream) {
+  if (n_units == 0) return 0;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t want = (uint64_t)sms * 8;
+  const uint32_t grid = (uint32_t)(n_units < want ? n_units : want);
+  igs::box_copy_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(jobs_dev, n_jobs, n_units);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int igs_exec_error(bool clear) {
+  uint32_t v = 0;
+  if (cudaMemcpyFromSymbol(&v, igs::g_exec_error, sizeof v) != cudaSuccess) return -1;
+  if (clear && v) {
+    const uint32_t z = 0;
+    cudaMemcpyToSymbol(igs::g_exec_error, &z, sizeof z);
+  }
+  return (int)v;
+}
+
+int igs_launch_workload(const igs::KernelJob* jobs_dev, uint32_t n_jobs, uint64_t n_items, void* stream) {
+  if (n_items == 0) return 0;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t blocks = (n_items + 255) / 256;
+  const uint64_t cap = (uint64_t)sms * 16;
+  const uint32_t grid = (uint32_t)(blocks < cap ? blocks : cap);
+  igs::workload_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(jobs_dev, n_jobs, n_items);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}

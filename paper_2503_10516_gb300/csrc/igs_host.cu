@@ -1,0 +1,993 @@
+// Host front-end of libigs: the C ABI of include/igs.h.
+//
+// The host side only validates descriptors, appends submissions to the
+// device-visible item stream, launches the lowering kernel, and drives the
+// executor; chunking, range mappers, region maps, allocation planning,
+// coherence, transfers and dependencies all run in the CUDA lowering engine.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "igs_exec.h"
+#include "igs_internal.h"
+
+using namespace igs;
+
+namespace {
+
+struct ExecAlloc {
+  uint8_t* ptr = nullptr;
+  uint32_t buffer = 0, mem = 0;
+  uint32_t lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+  bool live = false, user = false;
+};
+
+struct NodeHost {
+  // fetched graph (everything so far) for execution
+  std::vector<igs_instruction> instrs;
+  std::vector<igs_edge> edges;
+  std::vector<igs_box> boxes;
+  std::vector<igs_binding> binds;
+  std::vector<uint32_t> first_edge;  // per instruction: index of its first edge
+  uint32_t executed = 1;             // instruction 0 is the initial epoch
+  std::map<uint32_t, ExecAlloc> allocs;
+  std::vector<uint32_t> wave;        // wave id per instruction
+};
+
+}  // namespace
+
+struct igs_ctx {
+  igs_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  uint32_t N = 0, D = 0;
+  std::vector<BufDesc> bufs;
+  std::vector<uint8_t*> init_dev;  // per buffer: device copy of host_init (user memory M0), or null
+  std::vector<bool> buf_live;
+  std::vector<Item> items;
+  std::vector<igs_task> tasks;
+  std::vector<uint32_t> seq_task;  // submission sequence number -> task index (NONE if not a task)
+  uint32_t items_up = 0, tasks_up = 0, bufs_up = 0;
+  uint32_t seq = 0, ntasks = 0;
+  // device
+  Item* d_items = nullptr;
+  uint32_t cap_items = 0;
+  igs_task* d_tasks = nullptr;
+  uint32_t cap_tasks = 0;
+  BufDesc* d_bufs = nullptr;
+  uint32_t cap_bufs = 0;
+  uint32_t* d_nitems = nullptr;
+  ProgDev* d_prog = nullptr;
+  NodeDev* d_nodes = nullptr;
+  Unit* d_units = nullptr;
+  void* d_arena = nullptr;
+  std::vector<NodeDev> nodes_host;  // layout templates (pointers), refreshed by downloads
+  // executor
+  std::vector<NodeHost> nh;
+  uint32_t wave_id = 1;
+  CopyJob* d_cjobs = nullptr;
+  uint32_t cap_cjobs = 0;
+  KernelJob* d_kjobs = nullptr;
+  uint32_t cap_kjobs = 0;
+  uint64_t launches = 0;
+};
+
+namespace {
+
+int fail_ctx(igs_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(x)                                                                               \
+  do {                                                                                      \
+    cudaError_t e_ = (x);                                                                   \
+    if (e_ != cudaSuccess) return fail_ctx(c, IGS_ERR_CUDA, std::string(#x ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+int grow_device(igs_ctx* c, T*& ptr, uint32_t& cap, uint32_t need, uint32_t used) {
+  if (need <= cap) return IGS_OK;
+  uint32_t ncap = std::max<uint32_t>(need, std::max<uint32_t>(64, cap * 2));
+  T* np = nullptr;
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMalloc(&np, sizeof(T) * (size_t)ncap));
+  if (ptr && used) CK(cudaMemcpy(np, ptr, sizeof(T) * (size_t)used, cudaMemcpyDeviceToDevice));
+  if (ptr) CK(cudaFree(ptr));
+  ptr = np;
+  cap = ncap;
+  return IGS_OK;
+}
+
+int upload_prog(igs_ctx* c) {
+  int r;
+  if ((r = grow_device(c, c->d_items, c->cap_items, (uint32_t)c->items.size(), c->items_up))) return r;
+  if ((r = grow_device(c, c->d_tasks, c->cap_tasks, (uint32_t)c->tasks.size(), c->tasks_up))) return r;
+  if ((r = grow_device(c, c->d_bufs, c->cap_bufs, (uint32_t)c->bufs.size(), c->bufs_up))) return r;
+  if (c->tasks.size() > c->tasks_up)
+    CK(cudaMemcpyAsync(c->d_tasks + c->tasks_up, c->tasks.data() + c->tasks_up,
+                       sizeof(igs_task) * (c->tasks.size() - c->tasks_up), cudaMemcpyHostToDevice, c->stream));
+  if (c->bufs.size() > c->bufs_up)
+    CK(cudaMemcpyAsync(c->d_bufs + c->bufs_up, c->bufs.data() + c->bufs_up,
+                       sizeof(BufDesc) * (c->bufs.size() - c->bufs_up), cudaMemcpyHostToDevice, c->stream));
+  if (c->items.size() > c->items_up)
+    CK(cudaMemcpyAsync(c->d_items + c->items_up, c->items.data() + c->items_up,
+                       sizeof(Item) * (c->items.size() - c->items_up), cudaMemcpyHostToDevice, c->stream));
+  c->tasks_up = (uint32_t)c->tasks.size();
+  c->bufs_up = (uint32_t)c->bufs.size();
+  c->items_up = (uint32_t)c->items.size();
+  ProgDev p;
+  p.items = c->d_items;
+  p.tasks = c->d_tasks;
+  p.bufs = c->d_bufs;
+  p.n_items = c->d_nitems;
+  CK(cudaMemcpyAsync(c->d_prog, &p, sizeof p, cudaMemcpyHostToDevice, c->stream));
+  const uint32_t n = (uint32_t)c->items.size();
+  CK(cudaMemcpyAsync(c->d_nitems, &n, sizeof n, cudaMemcpyHostToDevice, c->stream));
+  return IGS_OK;
+}
+
+int launch_lower(igs_ctx* c) {
+  int r = upload_prog(c);
+  if (r) return r;
+  if (igs_launch_lower(c->d_units, c->N, IGS_NONE, c->stream)) return fail_ctx(c, IGS_ERR_CUDA, "lowering launch failed");
+  c->launches++;
+  return IGS_OK;
+}
+
+int download_nodes(igs_ctx* c) {
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(c->nodes_host.data(), c->d_nodes, sizeof(NodeDev) * c->N, cudaMemcpyDeviceToHost));
+  return IGS_OK;
+}
+
+int check_status(igs_ctx* c) {
+  int r = download_nodes(c);
+  if (r) return r;
+  for (uint32_t n = 0; n < c->N; ++n) {
+    const NodeDev& nd = c->nodes_host[n];
+    if (nd.status == ST_CAPACITY) return fail_ctx(c, IGS_ERR_CAPACITY, "device table or output capacity exceeded on node " + std::to_string(n));
+    if (nd.status == ST_TIMEOUT) return fail_ctx(c, IGS_ERR_TIMEOUT, "device wait timed out");
+    if (nd.status != ST_OK) return fail_ctx(c, IGS_ERR_CUDA, "lowering engine internal error on node " + std::to_string(n));
+  }
+  if (c->nodes_host[0].n_rej) return fail_ctx(c, IGS_ERR_OVERLAPPING_WRITE, "a task with overlapping writes was rejected");
+  return IGS_OK;
+}
+
+void push_item(igs_ctx* c, uint32_t kind, uint32_t arg, uint32_t task) {
+  Item it;
+  it.kind = kind;
+  if (kind != IT_LOOKAHEAD) c->seq_task.push_back(kind == IT_TASK ? task : NONE);
+  it.seq = kind == IT_LOOKAHEAD ? c->seq : c->seq++;
+  it.arg = arg;
+  it.task = task;
+  c->items.push_back(it);
+}
+
+size_t table_bytes(uint32_t cap) { return (size_t)F_COUNT * cap * sizeof(uint32_t); }
+
+}  // namespace
+
+extern "C" {
+
+int igs_create(const igs_config* cfg, igs_ctx** out) {
+  if (!out) return IGS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!cfg || cfg->num_nodes < 1 || cfg->num_nodes > 32 || cfg->devices_per_node < 1 || cfg->devices_per_node > 29)
+    return IGS_ERR_INVALID_ARG;
+  if (cfg->mode > IGS_MODE_BATCHED) return IGS_ERR_INVALID_ARG;
+  igs_ctx* c = new igs_ctx();
+  c->cfg = *cfg;
+  c->N = cfg->num_nodes;
+  c->D = cfg->devices_per_node;
+  const uint32_t cap_instr = cfg->max_instructions ? cfg->max_instructions : (1u << 18);
+  const uint32_t cap_edge = cfg->max_edges ? cfg->max_edges : 4 * cap_instr;
+  const uint32_t cap_box = cfg->max_boxes ? cfg->max_boxes : 4 * cap_instr;
+  const uint32_t cap_bind = 2 * cap_instr;
+  const uint32_t cap_map = cfg->map_capacity ? cfg->map_capacity : 16384;
+  const uint32_t cap_scr = cfg->scratch_capacity ? cfg->scratch_capacity : 8192;
+  const uint32_t cap_alloc = 8192, cap_queue = 1u << 16, cap_diag = 1u << 16, cap_rej = 1024;
+  cudaError_t e = cudaSetDevice(cfg->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return IGS_ERR_CUDA;
+  }
+  if (cfg->stream) {
+    c->stream = (cudaStream_t)cfg->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return IGS_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  // per-node arena
+  size_t per = 0;
+  auto take = [&](size_t bytes) {
+    size_t off = per;
+    per += (bytes + 255) & ~(size_t)255;
+    return off;
+  };
+  const size_t o_tab = take(table_bytes(cap_map) * 5);
+  const size_t o_alloc = take(sizeof(AllocRec) * cap_alloc);
+  const size_t o_queue = take(sizeof(uint32_t) * cap_queue);
+  const size_t o_succ = take(cap_instr);
+  const size_t o_instr = take(sizeof(igs_instruction) * cap_instr);
+  const size_t o_edge = take(sizeof(igs_edge) * cap_edge);
+  const size_t o_box = take(sizeof(igs_box) * cap_box);
+  const size_t o_bind = take(sizeof(igs_binding) * cap_bind);
+  const size_t o_diag = take(sizeof(igs_diag) * cap_diag);
+  const size_t o_rej = take(sizeof(uint32_t) * cap_rej);
+  const size_t o_scr = take(table_bytes(cap_scr) * 14);
+  if (cudaMalloc(&c->d_arena, per * c->N) != cudaSuccess || cudaMalloc(&c->d_nodes, sizeof(NodeDev) * c->N) != cudaSuccess ||
+      cudaMalloc(&c->d_units, sizeof(Unit) * c->N) != cudaSuccess || cudaMalloc(&c->d_prog, sizeof(ProgDev)) != cudaSuccess ||
+      cudaMalloc(&c->d_nitems, sizeof(uint32_t)) != cudaSuccess) {
+    igs_destroy(c);
+    return IGS_ERR_CUDA;
+  }
+  c->nodes_host.resize(c->N);
+  std::vector<Unit> units(c->N);
+  for (uint32_t n = 0; n < c->N; ++n) {
+    uint8_t* base = static_cast<uint8_t*>(c->d_arena) + per * n;
+    NodeDev nd;
+    std::memset(&nd, 0, sizeof nd);
+    nd.node = n;
+    nd.N = c->N;
+    nd.D = c->D;
+    nd.status = ST_OK;
+    nd.cursor = 0;
+    nd.lookahead = cfg->lookahead;
+    nd.epoch = 0;
+    nd.last_horizon = NONE;
+    nd.last_sync = 0;
+    nd.n_instr = 1;
+    nd.cap_instr = cap_instr;
+    nd.cap_edge = cap_edge;
+    nd.cap_box = cap_box;
+    nd.cap_bind = cap_bind;
+    nd.cap_diag = cap_diag;
+    nd.cap_rej = cap_rej;
+    nd.cap_alloc = cap_alloc;
+    nd.cap_queue = cap_queue;
+    nd.cap_map = cap_map;
+    nd.cap_scratch = cap_scr;
+    Table* tabs[5] = {&nd.own, &nd.bst, &nd.wr, &nd.rd, &nd.qr};
+    for (int k = 0; k < 5; ++k) {
+      tabs[k]->base = reinterpret_cast<uint32_t*>(base + o_tab + table_bytes(cap_map) * k);
+      tabs[k]->n = 0;
+      tabs[k]->cap = cap_map;
+    }
+    nd.allocs = reinterpret_cast<AllocRec*>(base + o_alloc);
+    nd.queue = reinterpret_cast<uint32_t*>(base + o_queue);
+    nd.has_succ = base + o_succ;
+    nd.instrs = reinterpret_cast<igs_instruction*>(base + o_instr);
+    nd.edges = reinterpret_cast<igs_edge*>(base + o_edge);
+    nd.boxes = reinterpret_cast<igs_box*>(base + o_box);
+    nd.binds = reinterpret_cast<igs_binding*>(base + o_bind);
+    nd.diags = reinterpret_cast<igs_diag*>(base + o_diag);
+    nd.rejected = reinterpret_cast<uint32_t*>(base + o_rej);
+    for (int k = 0; k < 14; ++k) {
+      nd.s[k].base = reinterpret_cast<uint32_t*>(base + o_scr + table_bytes(cap_scr) * k);
+      nd.s[k].n = 0;
+      nd.s[k].cap = cap_scr;
+    }
+    c->nodes_host[n] = nd;
+    units[n].node = c->d_nodes + n;
+    units[n].prog = c->d_prog;
+    // initial epoch I0
+    igs_instruction i0{0, IGS_EPOCH, NONE, NONE, NONE, NONE, NONE, 0, 0, 0, 0};
+    if (cudaMemcpy(nd.instrs, &i0, sizeof i0, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(nd.has_succ, 0, 1) != cudaSuccess) {
+      igs_destroy(c);
+      return IGS_ERR_CUDA;
+    }
+  }
+  uint32_t zero = 0;
+  if (cudaMemcpy(c->d_nodes, c->nodes_host.data(), sizeof(NodeDev) * c->N, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_units, units.data(), sizeof(Unit) * c->N, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_nitems, &zero, sizeof zero, cudaMemcpyHostToDevice) != cudaSuccess) {
+    igs_destroy(c);
+    return IGS_ERR_CUDA;
+  }
+  c->nh.resize(c->N);
+  *out = c;
+  return IGS_OK;
+}
+
+void igs_destroy(igs_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& n : c->nh)
+    for (auto& a : n.allocs)
+      if (a.second.live && !a.second.user && a.second.ptr) cudaFree(a.second.ptr);
+  for (uint8_t* p : c->init_dev)
+    if (p) cudaFree(p);
+  cudaFree(c->d_items);
+  cudaFree(c->d_tasks);
+  cudaFree(c->d_bufs);
+  cudaFree(c->d_nitems);
+  cudaFree(c->d_prog);
+  cudaFree(c->d_nodes);
+  cudaFree(c->d_units);
+  cudaFree(c->d_arena);
+  cudaFree(c->d_cjobs);
+  cudaFree(c->d_kjobs);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* igs_last_error(const igs_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int igs_create_buffer(igs_ctx* c, uint32_t dims, const uint32_t extent[3], uint32_t elem_size, const void* host_init,
+                      uint32_t* out_buffer) {
+  if (!c || !extent || !out_buffer) return fail_ctx(c, IGS_ERR_INVALID_ARG, "null argument");
+  if (dims < 1 || dims > 3 || elem_size == 0) return fail_ctx(c, IGS_ERR_INVALID_ARG, "bad buffer shape");
+  BufDesc b{};
+  b.dims = dims;
+  uint64_t count = 1;
+  for (int d = 0; d < 3; ++d) {
+    b.extent[d] = d < (int)dims ? extent[d] : 1;
+    if (b.extent[d] == 0) return fail_ctx(c, IGS_ERR_INVALID_ARG, "zero extent");
+    count *= b.extent[d];
+  }
+  b.elem = elem_size;
+  b.init = host_init ? 1 : 0;
+  uint8_t* dev = nullptr;
+  if (host_init) {
+    CK(cudaMalloc(&dev, count * elem_size));
+    CK(cudaMemcpy(dev, host_init, count * elem_size, cudaMemcpyHostToDevice));
+  }
+  const uint32_t id = (uint32_t)c->bufs.size();
+  c->bufs.push_back(b);
+  c->init_dev.push_back(dev);
+  c->buf_live.push_back(true);
+  push_item(c, IT_CREATE, id, 0);
+  *out_buffer = id;
+  if (c->cfg.mode == IGS_MODE_PLAIN) return launch_lower(c);
+  return IGS_OK;
+}
+
+int igs_destroy_buffer(igs_ctx* c, uint32_t b) {
+  if (!c || b >= c->bufs.size() || !c->buf_live[b]) return fail_ctx(c, IGS_ERR_INVALID_ARG, "unknown buffer");
+  c->buf_live[b] = false;
+  push_item(c, IT_DESTROY, b, 0);
+  if (c->cfg.mode == IGS_MODE_PLAIN) return launch_lower(c);
+  return IGS_OK;
+}
+
+int igs_submit_task(igs_ctx* c, const igs_task* t, uint64_t* out_seq) {
+  if (!c || !t) return fail_ctx(c, IGS_ERR_INVALID_ARG, "null argument");
+  if (t->dims < 1 || t->dims > 3 || t->num_chunks == 0 || t->num_accessors > IGS_MAX_ACCESSORS)
+    return fail_ctx(c, IGS_ERR_INVALID_ARG, "bad task header");
+  for (int d = 0; d < 3; ++d)
+    if (d >= (int)t->dims && t->range[d] != 1) return fail_ctx(c, IGS_ERR_INVALID_ARG, "unused range dims must be 1");
+  for (uint32_t a = 0; a < t->num_accessors; ++a) {
+    const igs_accessor& ac = t->acc[a];
+    if (ac.buffer >= c->bufs.size() || !c->buf_live[ac.buffer]) return fail_ctx(c, IGS_ERR_INVALID_ARG, "unknown buffer");
+    if (ac.mode < 1 || ac.mode > 3) return fail_ctx(c, IGS_ERR_INVALID_ARG, "bad access mode");
+    for (int d = 0; d < 3; ++d)
+      if (ac.dim[d].kind > IGS_MAP_FIXED || (ac.dim[d].kind == IGS_MAP_AFFINE && ac.dim[d].a > 2))
+        return fail_ctx(c, IGS_ERR_INVALID_ARG, "bad range mapper");
+  }
+  const uint32_t ti = (uint32_t)c->tasks.size();
+  c->tasks.push_back(*t);
+  const uint32_t s = c->seq;
+  push_item(c, IT_TASK, 0, ti);
+  c->ntasks++;
+  if (c->cfg.horizon_step && c->ntasks % c->cfg.horizon_step == 0) push_item(c, IT_HORIZON, 0, 0);
+  if (out_seq) *out_seq = s;
+  if (c->cfg.mode == IGS_MODE_PLAIN) return launch_lower(c);
+  return IGS_OK;
+}
+
+int igs_set_lookahead(igs_ctx* c, uint32_t L) {
+  if (!c) return IGS_ERR_INVALID_ARG;
+  push_item(c, IT_LOOKAHEAD, L, 0);
+  if (c->cfg.mode == IGS_MODE_PLAIN) return launch_lower(c);
+  return IGS_OK;
+}
+
+int igs_sync(igs_ctx* c) {
+  if (!c) return IGS_ERR_INVALID_ARG;
+  if (c->items_up < c->items.size() || c->cfg.mode == IGS_MODE_BATCHED) {
+    int r = launch_lower(c);
+    if (r) return r;
+  }
+  return check_status(c);
+}
+
+int igs_flush(igs_ctx* c) {
+  if (!c) return IGS_ERR_INVALID_ARG;
+  push_item(c, IT_EPOCH, 0, 0);
+  int r = launch_lower(c);
+  if (r) return r;
+  return check_status(c);
+}
+
+int igs_lower_batch(igs_ctx* const* ctxs, uint32_t n) {
+  if (!ctxs || n == 0) return IGS_ERR_INVALID_ARG;
+  igs_ctx* c = ctxs[0];
+  std::vector<Unit> units;
+  for (uint32_t i = 0; i < n; ++i) {
+    int r = upload_prog(ctxs[i]);
+    if (r) return r;
+    if (cudaStreamSynchronize(ctxs[i]->stream) != cudaSuccess) return IGS_ERR_CUDA;
+    for (uint32_t k = 0; k < ctxs[i]->N; ++k) units.push_back(Unit{ctxs[i]->d_nodes + k, ctxs[i]->d_prog});
+  }
+  static thread_local Unit* d_units = nullptr;
+  static thread_local size_t cap_units = 0;
+  if (units.size() > cap_units) {
+    if (d_units) cudaFree(d_units);
+    cap_units = units.size() * 2;
+    if (cudaMalloc(&d_units, sizeof(Unit) * cap_units) != cudaSuccess) return fail_ctx(c, IGS_ERR_CUDA, "alloc units");
+  }
+  CK(cudaMemcpyAsync(d_units, units.data(), sizeof(Unit) * units.size(), cudaMemcpyHostToDevice, c->stream));
+  if (igs_launch_lower(d_units, (uint32_t)units.size(), IGS_NONE, c->stream)) return fail_ctx(c, IGS_ERR_CUDA, "batch launch");
+  CK(cudaStreamSynchronize(c->stream));
+  for (uint32_t i = 0; i < n; ++i) {
+    ctxs[i]->launches++;
+    int r = check_status(ctxs[i]);
+    if (r && r != IGS_ERR_OVERLAPPING_WRITE) return r;
+  }
+  return IGS_OK;
+}
+
+int igs_rejected_tasks(igs_ctx* c, uint64_t* seqs, uint32_t cap, uint32_t* count) {
+  if (!c || !count) return IGS_ERR_INVALID_ARG;
+  int r = download_nodes(c);
+  if (r) return r;
+  const NodeDev& nd = c->nodes_host[0];
+  *count = nd.n_rej;
+  std::vector<uint32_t> tmp(nd.n_rej);
+  if (nd.n_rej) CK(cudaMemcpy(tmp.data(), nd.rejected, sizeof(uint32_t) * nd.n_rej, cudaMemcpyDeviceToHost));
+  for (uint32_t i = 0; i < nd.n_rej && i < cap; ++i) seqs[i] = tmp[i];
+  return IGS_OK;
+}
+
+int igs_fetch_instructions(igs_ctx* c, igs_graph_view* v) {
+  if (!c || !v || v->node >= c->N) return fail_ctx(c, IGS_ERR_INVALID_ARG, "bad view");
+  int r = download_nodes(c);
+  if (r) return r;
+  const NodeDev& nd = c->nodes_host[v->node];
+  v->num_instrs = nd.n_instr;
+  v->num_edges = nd.n_edge;
+  v->num_boxes = nd.n_box;
+  v->num_binds = nd.n_bind;
+  v->num_diags = nd.n_diag;
+  if (v->instr_cap < nd.n_instr || v->edge_cap < nd.n_edge || v->box_cap < nd.n_box || v->bind_cap < nd.n_bind ||
+      v->diag_cap < nd.n_diag)
+    return IGS_ERR_TRUNCATED;
+  if (nd.n_instr) CK(cudaMemcpyAsync(v->instrs, nd.instrs, sizeof(igs_instruction) * nd.n_instr, cudaMemcpyDeviceToHost, c->stream));
+  if (nd.n_edge) CK(cudaMemcpyAsync(v->edges, nd.edges, sizeof(igs_edge) * nd.n_edge, cudaMemcpyDeviceToHost, c->stream));
+  if (nd.n_box) CK(cudaMemcpyAsync(v->boxes, nd.boxes, sizeof(igs_box) * nd.n_box, cudaMemcpyDeviceToHost, c->stream));
+  if (nd.n_bind) CK(cudaMemcpyAsync(v->binds, nd.binds, sizeof(igs_binding) * nd.n_bind, cudaMemcpyDeviceToHost, c->stream));
+  if (nd.n_diag) CK(cudaMemcpyAsync(v->diags, nd.diags, sizeof(igs_diag) * nd.n_diag, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return IGS_OK;
+}
+
+int igs_counters(igs_ctx* c, uint64_t out[8]) {
+  if (!c || !out) return IGS_ERR_INVALID_ARG;
+  int r = download_nodes(c);
+  if (r) return r;
+  std::memset(out, 0, sizeof(uint64_t) * 8);
+  for (const NodeDev& nd : c->nodes_host) {
+    out[0] += nd.n_instr;
+    out[1] += nd.n_edge;
+    out[2] += nd.n_box;
+    out[3] += nd.map_reads;
+    out[4] += nd.map_writes;
+  }
+  out[5] = c->launches;
+  return IGS_OK;
+}
+
+}  // extern "C"
+
+// ---- executor ----------------------------------------------------------------
+
+namespace {
+
+// Work collected by one execute call: waves of independent box copies or
+// workload kernels, and frees, replayed in order after one upload.
+struct Action {
+  int kind;  // 0 copy wave, 1 kernel wave, 2 free
+  uint32_t first, count;
+  uint64_t units;
+  void* ptr;
+};
+
+struct Pending {
+  std::vector<CopyJob> copies;
+  std::vector<KernelJob> kernels;
+  std::vector<Action> actions;
+  uint32_t wave_first = 0;
+  uint64_t copy_units = 0, kernel_items = 0;
+  bool open_copy = false, open_kernel = false;
+};
+
+// Collapses a box copy between two row-major allocations into rows of
+// contiguous bytes.
+bool make_copy_job(const uint8_t* src, const uint32_t slo[3], const uint32_t shi[3], uint8_t* dst, const uint32_t dlo[3],
+                   const uint32_t dhi[3], const igs_box& b, uint32_t elem, CopyJob& J) {
+  uint64_t e[3], ss[3], ds[3];
+  for (int d = 0; d < 3; ++d) {
+    if (b.lo[d] >= b.hi[d]) return false;
+    // the box must lie inside both allocations
+    if (b.lo[d] < slo[d] || b.hi[d] > shi[d] || b.lo[d] < dlo[d] || b.hi[d] > dhi[d]) return false;
+    e[d] = b.hi[d] - b.lo[d];
+  }
+  ss[2] = elem;
+  ds[2] = elem;
+  ss[1] = ss[2] * (shi[2] - slo[2]);
+  ds[1] = ds[2] * (dhi[2] - dlo[2]);
+  ss[0] = ss[1] * (shi[1] - slo[1]);
+  ds[0] = ds[1] * (dhi[1] - dlo[1]);
+  const uint64_t soff = (b.lo[0] - slo[0]) * ss[0] + (b.lo[1] - slo[1]) * ss[1] + (b.lo[2] - slo[2]) * ss[2];
+  const uint64_t doff = (b.lo[0] - dlo[0]) * ds[0] + (b.lo[1] - dlo[1]) * ds[1] + (b.lo[2] - dlo[2]) * ds[2];
+  // contiguous run: innermost dims while the box spans both allocations fully
+  uint64_t run = e[2] * elem;
+  int outer = 1;  // dims [0, outer] remain as rows
+  if (e[2] == shi[2] - slo[2] && e[2] == dhi[2] - dlo[2]) {
+    run *= e[1];
+    outer = 0;
+    if (e[1] == shi[1] - slo[1] && e[1] == dhi[1] - dlo[1]) {
+      run *= e[0];
+      outer = -1;
+    }
+  }
+  J.src = src + soff;
+  J.dst = dst + doff;
+  if (outer == 1) {
+    J.extent[0] = (uint32_t)e[0];
+    J.extent[1] = (uint32_t)e[1];
+    J.src_stride[0] = ss[0];
+    J.src_stride[1] = ss[1];
+    J.dst_stride[0] = ds[0];
+    J.dst_stride[1] = ds[1];
+  } else if (outer == 0) {
+    J.extent[0] = (uint32_t)e[0];
+    J.extent[1] = 1;
+    J.src_stride[0] = ss[0];
+    J.dst_stride[0] = ds[0];
+    J.src_stride[1] = J.dst_stride[1] = 0;
+  } else {
+    J.extent[0] = J.extent[1] = 1;
+    J.src_stride[0] = J.dst_stride[0] = J.src_stride[1] = J.dst_stride[1] = 0;
+  }
+  // very long runs are split into rows of at most 1 GiB to keep 32-bit lengths
+  J.extent[2] = (uint32_t)std::min<uint64_t>(run, 1ull << 30);
+  if (run > (1ull << 30)) return false;
+  J.seg_bytes = 64 * 1024;
+  return true;
+}
+
+// Closes the open wave (if any): later instructions that depend on it go to a new one.
+void close_wave(igs_ctx* c, Pending& p) {
+  if (p.open_copy) p.actions.push_back(Action{0, p.wave_first, (uint32_t)p.copies.size() - p.wave_first, p.copy_units, nullptr});
+  if (p.open_kernel)
+    p.actions.push_back(Action{1, p.wave_first, (uint32_t)p.kernels.size() - p.wave_first, p.kernel_items, nullptr});
+  p.open_copy = p.open_kernel = false;
+  p.copy_units = p.kernel_items = 0;
+  c->wave_id++;
+}
+
+void add_copy(igs_ctx* c, Pending& p, const CopyJob& J) {
+  if (p.open_kernel) close_wave(c, p);
+  if (!p.open_copy) {
+    p.open_copy = true;
+    p.wave_first = (uint32_t)p.copies.size();
+  }
+  CopyJob j = J;
+  j.unit_begin = p.copy_units;
+  const uint64_t segs = (j.extent[2] + j.seg_bytes - 1) / j.seg_bytes;
+  p.copy_units += (uint64_t)j.extent[0] * j.extent[1] * segs;
+  p.copies.push_back(j);
+}
+
+void add_kernel(igs_ctx* c, Pending& p, KernelJob J, uint64_t items) {
+  if (p.open_copy) close_wave(c, p);
+  if (!p.open_kernel) {
+    p.open_kernel = true;
+    p.wave_first = (uint32_t)p.kernels.size();
+  }
+  J.item_begin = p.kernel_items;
+  p.kernel_items += items;
+  p.kernels.push_back(J);
+}
+
+// Uploads every job once and replays the actions on the stream.
+int run_pending(igs_ctx* c, Pending& p) {
+  close_wave(c, p);
+  int r;
+  if (!p.copies.empty()) {
+    if ((r = grow_device(c, c->d_cjobs, c->cap_cjobs, (uint32_t)p.copies.size(), 0))) return r;
+    CK(cudaMemcpyAsync(c->d_cjobs, p.copies.data(), sizeof(CopyJob) * p.copies.size(), cudaMemcpyHostToDevice, c->stream));
+  }
+  if (!p.kernels.empty()) {
+    if ((r = grow_device(c, c->d_kjobs, c->cap_kjobs, (uint32_t)p.kernels.size(), 0))) return r;
+    CK(cudaMemcpyAsync(c->d_kjobs, p.kernels.data(), sizeof(KernelJob) * p.kernels.size(), cudaMemcpyHostToDevice, c->stream));
+  }
+  for (const Action& a : p.actions) {
+    if (a.kind == 0) {
+      if (igs_launch_copies(c->d_cjobs + a.first, a.count, a.units, c->stream)) return fail_ctx(c, IGS_ERR_CUDA, "box copy launch");
+    } else if (a.kind == 1) {
+      if (igs_launch_workload(c->d_kjobs + a.first, a.count, a.units, c->stream)) return fail_ctx(c, IGS_ERR_CUDA, "workload launch");
+    } else {
+      CK(cudaFreeAsync(a.ptr, c->stream));
+    }
+  }
+  // the job arrays are reused by the next call
+  CK(cudaStreamSynchronize(c->stream));
+  if (igs_exec_error(true)) return fail_ctx(c, IGS_ERR_STATE, "a workload kernel accessed outside its allocation");
+  p.copies.clear();
+  p.kernels.clear();
+  p.actions.clear();
+  return IGS_OK;
+}
+
+ExecAlloc* get_alloc(igs_ctx* c, uint32_t node, uint32_t aid, uint32_t buffer_hint) {
+  auto& m = c->nh[node].allocs;
+  auto it = m.find(aid);
+  if (it != m.end()) return &it->second;
+  // a user allocation (M0): host data of the buffer
+  if (buffer_hint >= c->bufs.size() || !c->init_dev[buffer_hint]) return nullptr;
+  ExecAlloc a;
+  a.ptr = c->init_dev[buffer_hint];
+  a.buffer = buffer_hint;
+  a.mem = 0;
+  for (int d = 0; d < 3; ++d) {
+    a.lo[d] = 0;
+    a.hi[d] = c->bufs[buffer_hint].extent[d];
+  }
+  a.live = true;
+  a.user = true;
+  return &(m[aid] = a);
+}
+
+int fetch_for_exec(igs_ctx* c) {
+  int r = download_nodes(c);
+  if (r) return r;
+  for (uint32_t n = 0; n < c->N; ++n) {
+    const NodeDev& nd = c->nodes_host[n];
+    NodeHost& h = c->nh[n];
+    const size_t oi = h.instrs.size(), oe = h.edges.size(), ob = h.boxes.size(), ok = h.binds.size();
+    h.instrs.resize(nd.n_instr);
+    h.edges.resize(nd.n_edge);
+    h.boxes.resize(nd.n_box);
+    h.binds.resize(nd.n_bind);
+    if (nd.n_instr > oi)
+      CK(cudaMemcpy(h.instrs.data() + oi, nd.instrs + oi, sizeof(igs_instruction) * (nd.n_instr - oi), cudaMemcpyDeviceToHost));
+    if (nd.n_edge > oe)
+      CK(cudaMemcpy(h.edges.data() + oe, nd.edges + oe, sizeof(igs_edge) * (nd.n_edge - oe), cudaMemcpyDeviceToHost));
+    if (nd.n_box > ob)
+      CK(cudaMemcpy(h.boxes.data() + ob, nd.boxes + ob, sizeof(igs_box) * (nd.n_box - ob), cudaMemcpyDeviceToHost));
+    if (nd.n_bind > ok)
+      CK(cudaMemcpy(h.binds.data() + ok, nd.binds + ok, sizeof(igs_binding) * (nd.n_bind - ok), cudaMemcpyDeviceToHost));
+    h.first_edge.resize(nd.n_instr + 1, 0);
+    h.wave.resize(nd.n_instr, 0);
+    // edges are grouped by successor in emission order
+    size_t e = oe;
+    for (uint32_t i = (uint32_t)oi; i < nd.n_instr; ++i) {
+      while (e < h.edges.size() && h.edges[e].to < i) ++e;
+      h.first_edge[i] = (uint32_t)e;
+    }
+    h.first_edge[nd.n_instr] = (uint32_t)h.edges.size();
+  }
+  return IGS_OK;
+}
+
+bool depends_on_wave(const igs_ctx* c, const NodeHost& h, uint32_t id) {
+  const uint32_t e0 = h.first_edge[id], e1 = h.first_edge[id + 1];
+  for (uint32_t e = e0; e < e1; ++e)
+    if (h.wave[h.edges[e].from] == c->wave_id) return true;
+  return false;
+}
+
+struct SendRec {
+  uint32_t node, alloc, wave;
+  igs_box box;
+};
+
+}  // namespace
+
+extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
+  if (!c) return IGS_ERR_INVALID_ARG;
+  int r = fetch_for_exec(c);
+  if (r) return r;
+  // global order: by submission sequence; within it, every node's part up to
+  // its first receive, then the rest (sends precede the matching receives)
+  std::map<uint32_t, std::vector<std::pair<uint32_t, std::pair<uint32_t, uint32_t>>>> order;  // seq -> (node, [i0, i1))
+  for (uint32_t n = 0; n < c->N; ++n) {
+    NodeHost& h = c->nh[n];
+    uint32_t i = h.executed;
+    while (i < h.instrs.size()) {
+      const uint32_t s = h.instrs[i].seq;
+      uint32_t j = i;
+      while (j < h.instrs.size() && h.instrs[j].seq == s) ++j;
+      order[s].push_back({n, {i, j}});
+      i = j;
+    }
+    h.executed = (uint32_t)h.instrs.size();
+  }
+  Pending p;
+  std::multimap<uint64_t, SendRec> sends;  // key: (seq << 32) | (buffer << 8) | receiver
+  auto key_of = [](uint32_t seq, uint32_t buf, uint32_t recv) { return ((uint64_t)seq << 32) | ((uint64_t)buf << 8) | recv; };
+  for (auto& so : order) {
+    for (int half = 0; half < 2; ++half) {
+      for (auto& part : so.second) {
+        const uint32_t n = part.first;
+        NodeHost& h = c->nh[n];
+        uint32_t i0 = part.second.first, i1 = part.second.second, cut = i1;
+        for (uint32_t i = i0; i < i1; ++i)
+          if (h.instrs[i].type == IGS_RECEIVE || h.instrs[i].type == IGS_SPLIT_RECEIVE) {
+            cut = i;
+            break;
+          }
+        const uint32_t a0 = half == 0 ? i0 : cut, a1 = half == 0 ? cut : i1;
+        for (uint32_t i = a0; i < a1; ++i) {
+          const igs_instruction& in = h.instrs[i];
+          const bool dep = depends_on_wave(c, h, i);
+          switch (in.type) {
+            case IGS_ALLOC: {
+              const igs_box& b = h.boxes[in.box_off];
+              ExecAlloc a;
+              a.buffer = in.c;
+              a.mem = in.b;
+              uint64_t cnt = c->bufs[in.c].elem;
+              for (int d = 0; d < 3; ++d) {
+                a.lo[d] = b.lo[d];
+                a.hi[d] = b.hi[d];
+                cnt *= (b.hi[d] - b.lo[d]);
+              }
+              CK(cudaMallocAsync((void**)&a.ptr, cnt ? cnt : 1, c->stream));
+              a.live = true;
+              h.allocs[in.a] = a;
+              break;
+            }
+            case IGS_FREE: {
+              if (dep) close_wave(c, p);
+              auto it = h.allocs.find(in.a);
+              if (it != h.allocs.end()) {
+                if (!it->second.user) p.actions.push_back(Action{2, 0, 0, 0, it->second.ptr});
+                h.allocs.erase(it);
+              }
+              break;
+            }
+            case IGS_COPY: {
+              if (dep) close_wave(c, p);
+              ExecAlloc* s = get_alloc(c, n, in.a, in.c);
+              ExecAlloc* d = get_alloc(c, n, in.b, in.c);
+              if (!s || !d) return fail_ctx(c, IGS_ERR_STATE, "copy between unknown allocations");
+              for (uint32_t k = 0; k < in.box_cnt; ++k) {
+                CopyJob J{};
+                if (!make_copy_job(s->ptr, s->lo, s->hi, d->ptr, d->lo, d->hi, h.boxes[in.box_off + k], c->bufs[in.c].elem, J))
+                  return fail_ctx(c, IGS_ERR_STATE, "bad copy box");
+                add_copy(c, p, J);
+              }
+              h.wave[i] = c->wave_id;
+              break;
+            }
+            case IGS_SEND: {
+              SendRec sr;
+              sr.node = n;
+              sr.alloc = in.a;
+              sr.box = h.boxes[in.box_off];
+              sr.wave = dep ? c->wave_id : 0;
+              sends.insert({key_of(in.seq, in.c, in.b), sr});
+              h.wave[i] = sr.wave;
+              break;
+            }
+            case IGS_RECEIVE:
+            case IGS_SPLIT_RECEIVE: {
+              auto range = sends.equal_range(key_of(in.seq, in.c, n));
+              bool need_flush = dep;
+              for (auto it = range.first; it != range.second; ++it)
+                if (it->second.wave == c->wave_id) need_flush = true;
+              if (need_flush) close_wave(c, p);
+              ExecAlloc* d = get_alloc(c, n, in.a, in.c);
+              if (!d) return fail_ctx(c, IGS_ERR_STATE, "receive into unknown allocation");
+              for (auto it = range.first; it != range.second; ++it) {
+                ExecAlloc* s = get_alloc(c, it->second.node, it->second.alloc, in.c);
+                if (!s) return fail_ctx(c, IGS_ERR_STATE, "send from unknown allocation");
+                CopyJob J{};
+                if (!make_copy_job(s->ptr, s->lo, s->hi, d->ptr, d->lo, d->hi, it->second.box, c->bufs[in.c].elem, J))
+                  return fail_ctx(c, IGS_ERR_STATE, "bad send box");
+                add_copy(c, p, J);
+              }
+              sends.erase(range.first, range.second);
+              h.wave[i] = c->wave_id;
+              break;
+            }
+            case IGS_AWAIT_RECEIVE:
+              h.wave[i] = h.wave[in.b];
+              break;
+            case IGS_KERNEL: {
+              if (dep) close_wave(c, p);
+              if (in.seq >= c->seq_task.size() || c->seq_task[in.seq] == NONE)
+                return fail_ctx(c, IGS_ERR_STATE, "kernel of unknown task");
+              const igs_task& t = c->tasks[c->seq_task[in.seq]];
+              KernelJob J{};
+              J.kernel = t.kernel_id;
+              J.seq = in.seq;
+              J.nacc = t.num_accessors;
+              const igs_box& cb = h.boxes[in.box_off];
+              uint64_t items = 1;
+              for (int d = 0; d < 3; ++d) {
+                J.lo[d] = cb.lo[d];
+                J.hi[d] = cb.hi[d];
+                items *= (cb.hi[d] - cb.lo[d]);
+              }
+              for (int k = 0; k < 4; ++k) J.params[k] = t.params[k];
+              for (uint32_t a = 0; a < t.num_accessors; ++a) {
+                const igs_binding& bd = h.binds[in.bind_off + a];
+                KAcc& A = J.acc[a];
+                const BufDesc& bf = c->bufs[t.acc[a].buffer];
+                A.dims = bf.dims;
+                A.elem = bf.elem;
+                A.mode = t.acc[a].mode;
+                for (int d = 0; d < 3; ++d) {
+                  A.ext[d] = bf.extent[d];
+                  A.map[d] = t.acc[a].dim[d];
+                }
+                A.valid = 0;
+                if (bd.alloc != IGS_NONE) {
+                  ExecAlloc* al = get_alloc(c, n, bd.alloc, t.acc[a].buffer);
+                  if (!al) return fail_ctx(c, IGS_ERR_STATE, "kernel on unknown allocation");
+                  A.ptr = al->ptr;
+                  for (int d = 0; d < 3; ++d) {
+                    A.lo[d] = al->lo[d];
+                    A.hi[d] = al->hi[d];
+                  }
+                  A.valid = 1;
+                }
+              }
+              if (J.kernel != K_NOP && items) add_kernel(c, p, J, items);
+              h.wave[i] = c->wave_id;
+              break;
+            }
+            default:
+              break;
+          }
+        }
+      }
+    }
+  }
+  r = run_pending(c, p);
+  if (r) return r;
+  (void)flags;
+  return IGS_OK;
+}
+
+namespace {
+
+// Host-side view of one node table (read back for igs_read_buffer).
+struct HEntry {
+  uint32_t key, lo[3], hi[3], v[3];
+};
+
+int read_table(igs_ctx* c, const Table& t, uint32_t n, std::vector<HEntry>& out) {
+  std::vector<uint32_t> raw((size_t)F_COUNT * t.cap);
+  out.clear();
+  if (n == 0) return IGS_OK;
+  for (int f = 0; f < F_COUNT; ++f)
+    CK(cudaMemcpy(raw.data() + (size_t)f * t.cap, t.base + (size_t)f * t.cap, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+  for (uint32_t i = 0; i < n; ++i) {
+    HEntry e;
+    e.key = raw[i];
+    for (int d = 0; d < 3; ++d) {
+      e.lo[d] = raw[(size_t)(F_LO + d) * t.cap + i];
+      e.hi[d] = raw[(size_t)(F_HI + d) * t.cap + i];
+    }
+    for (int k = 0; k < 3; ++k) e.v[k] = raw[(size_t)(F_V + k) * t.cap + i];
+    if (e.key != DEAD) out.push_back(e);
+  }
+  return IGS_OK;
+}
+
+bool isect(const uint32_t alo[3], const uint32_t ahi[3], const uint32_t blo[3], const uint32_t bhi[3], igs_box& o) {
+  for (int d = 0; d < 3; ++d) {
+    o.lo[d] = std::max(alo[d], blo[d]);
+    o.hi[d] = std::min(ahi[d], bhi[d]);
+    if (o.lo[d] >= o.hi[d]) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" int igs_read_buffer(igs_ctx* c, uint32_t b, const uint32_t lo[3], const uint32_t hi[3], void* host_dst) {
+  if (!c || b >= c->bufs.size() || !lo || !hi || !host_dst) return fail_ctx(c, IGS_ERR_INVALID_ARG, "bad read");
+  const BufDesc& bf = c->bufs[b];
+  uint64_t cnt = bf.elem;
+  uint32_t rl[3], rh[3];
+  for (int d = 0; d < 3; ++d) {
+    rl[d] = lo[d];
+    rh[d] = hi[d];
+    if (rl[d] >= rh[d] || rh[d] > bf.extent[d]) return fail_ctx(c, IGS_ERR_INVALID_ARG, "read box outside buffer");
+    cnt *= rh[d] - rl[d];
+  }
+  int r = download_nodes(c);
+  if (r) return r;
+  uint8_t* stage = nullptr;
+  CK(cudaMalloc(&stage, cnt));
+  CK(cudaMemsetAsync(stage, 0, cnt, c->stream));
+  std::vector<HEntry> own, bst;
+  r = read_table(c, c->nodes_host[0].own, c->nodes_host[0].tab_n[0], own);
+  if (r) return r;
+  Pending p;
+  for (const HEntry& e : own) {
+    if (e.key != b) continue;
+    igs_box piece;
+    if (!isect(e.lo, e.hi, rl, rh, piece)) continue;
+    if (e.v[0] == HOST) {
+      CopyJob J{};
+      uint32_t blo[3] = {0, 0, 0}, bhi[3] = {bf.extent[0], bf.extent[1], bf.extent[2]};
+      if (make_copy_job(c->init_dev[b], blo, bhi, stage, rl, rh, piece, bf.elem, J)) add_copy(c, p, J);
+      continue;
+    }
+    if (e.v[0] >= c->N) continue;  // never written
+    const uint32_t o = e.v[0];
+    r = read_table(c, c->nodes_host[o].bst, c->nodes_host[o].tab_n[1], bst);
+    if (r) return r;
+    for (const HEntry& f : bst) {
+      if (f.key != b) continue;
+      igs_box q;
+      if (!isect(f.lo, f.hi, piece.lo, piece.hi, q)) continue;
+      const uint32_t pmem = f.v[1];
+      for (auto& al : c->nh[o].allocs) {
+        const ExecAlloc& A = al.second;
+        if (!A.live || A.buffer != b || A.mem != pmem) continue;
+        igs_box z;
+        if (!isect(A.lo, A.hi, q.lo, q.hi, z)) continue;
+        CopyJob J{};
+        if (make_copy_job(A.ptr, A.lo, A.hi, stage, rl, rh, z, bf.elem, J)) add_copy(c, p, J);
+      }
+    }
+  }
+  r = run_pending(c, p);
+  if (r) return r;
+  CK(cudaMemcpyAsync(host_dst, stage, cnt, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaFree(stage));
+  return IGS_OK;
+}
+
+extern "C" int igs_box_copy(const igs_copy_job* jobs, uint32_t n, void* stream) {
+  igs_ctx* c = nullptr;
+  if (!jobs && n) return IGS_ERR_INVALID_ARG;
+  std::vector<CopyJob> v;
+  uint64_t units = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    const igs_copy_job& j = jobs[i];
+    CopyJob J{};
+    for (int d = 0; d < 3; ++d)
+      if (j.box.lo[d] < j.src_box.lo[d] || j.box.hi[d] > j.src_box.hi[d] || j.box.lo[d] < j.dst_box.lo[d] ||
+          j.box.hi[d] > j.dst_box.hi[d])
+        return IGS_ERR_INVALID_ARG;
+    if (!make_copy_job(static_cast<const uint8_t*>(j.src), j.src_box.lo, j.src_box.hi, static_cast<uint8_t*>(j.dst),
+                       j.dst_box.lo, j.dst_box.hi, j.box, j.elem_size, J))
+      continue;
+    J.unit_begin = units;
+    units += (uint64_t)J.extent[0] * J.extent[1] * ((J.extent[2] + J.seg_bytes - 1) / J.seg_bytes);
+    v.push_back(J);
+  }
+  if (v.empty()) return IGS_OK;
+  static thread_local CopyJob* d_jobs = nullptr;
+  static thread_local size_t cap = 0;
+  if (v.size() > cap) {
+    if (d_jobs) cudaFree(d_jobs);
+    cap = v.size() * 2;
+    CK(cudaMalloc(&d_jobs, sizeof(CopyJob) * cap));
+  }
+  CK(cudaMemcpyAsync(d_jobs, v.data(), sizeof(CopyJob) * v.size(), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+  if (igs_launch_copies(d_jobs, (uint32_t)v.size(), units, stream)) return IGS_ERR_CUDA;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return IGS_OK;
+}

@@ -1,0 +1,102 @@
+// Internal structures shared by the lowering engine, the executor and the
+// host front-end of libigs. Not part of the public C ABI (include/igs.h).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include "igs.h"
+
+namespace igs {
+
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr uint32_t REMOTE = 0xFFFFFFFEu;  // producer: written by another node
+constexpr uint32_t HOST = 0xFFFFFFFEu;    // owner: user host memory, present on every node
+constexpr uint32_t DEAD = 0xFFFFFFFFu;    // table key of a removed entry
+
+enum ItemKind : uint32_t { IT_CREATE = 0, IT_TASK = 1, IT_HORIZON = 2, IT_EPOCH = 3, IT_DESTROY = 4, IT_LOOKAHEAD = 5 };
+
+// One submission as seen by every node's lowering warp.
+struct Item {
+  uint32_t kind, seq, arg, task;  // arg: buffer id / lookahead; task: index into the task array
+};
+
+struct BufDesc {
+  uint32_t dims, extent[3], elem, init;
+};
+
+enum Status : uint32_t { ST_OK = 0, ST_CAPACITY = 1, ST_INTERNAL = 2, ST_TIMEOUT = 3 };
+
+// Field layout of a box table (structure of arrays, `cap` entries per field).
+enum TableField : int { F_KEY = 0, F_LO = 1, F_HI = 4, F_V = 7, F_COUNT = 10 };
+
+struct Table {
+  uint32_t* base;  // F_COUNT * cap words
+  uint32_t n, cap;
+};
+
+struct AllocRec {
+  uint32_t buffer, mem, live, user;
+  uint32_t lo[3], hi[3];
+  uint32_t mark;  // scratch: cluster index during allocation planning
+  uint32_t pad;
+};
+
+// Persistent device state of one virtual node's lowering (one warp owns it).
+struct NodeDev {
+  // configuration
+  uint32_t node, N, D, prog;
+  // scalars (owned by the warp; written back after every item)
+  uint32_t status, cursor, lookahead, epoch, last_horizon, last_sync, next_msg, n_alloc;
+  uint32_t n_instr, n_edge, n_box, n_bind, n_diag, n_rej;
+  uint32_t q_head, q_count;
+  uint32_t tab_n[6];  // counts of the persistent tables (own, bst, wr, rd, qr, spare)
+  uint64_t map_reads, map_writes, launches;
+  // capacities
+  uint32_t cap_instr, cap_edge, cap_box, cap_bind, cap_diag, cap_rej, cap_alloc, cap_queue;
+  uint32_t cap_map, cap_scratch;
+  // persistent tables: node-level ownership, buffer state, per-allocation
+  // writers / readers, per-task push and await regions
+  Table own, bst, wr, rd, qr;
+  AllocRec* allocs;
+  uint32_t* queue;     // item indices (ring of cap_queue)
+  uint8_t* has_succ;   // per instruction: has a successor
+  // outputs (same record layouts as the public structs)
+  igs_instruction* instrs;
+  igs_edge* edges;
+  igs_box* boxes;
+  igs_binding* binds;
+  igs_diag* diags;
+  uint32_t* rejected;
+  // scratch tables for the warp
+  Table s[14];
+};
+
+// Program-level inputs shared by all node warps of one context.
+struct ProgDev {
+  const Item* items;
+  const igs_task* tasks;
+  const BufDesc* bufs;
+  volatile uint32_t* n_items;  // number of valid items (host-mapped in serving)
+};
+
+// A unit of lowering work: one node of one program.
+struct Unit {
+  NodeDev* node;
+  ProgDev* prog;
+};
+
+// Box-copy work descriptor (device side).
+struct CopyJob {
+  const uint8_t* src;
+  uint8_t* dst;
+  uint64_t src_stride[2], dst_stride[2];  // bytes per step of dim 0 / dim 1 (after collapsing)
+  uint32_t extent[3];                     // rows0, rows1, contiguous bytes per row
+  uint32_t seg_bytes;                     // bytes per work unit along the row
+  uint64_t unit_begin;                    // prefix of work units
+};
+
+}  // namespace igs
+
+// Device entry points implemented in the .cu translation units.
+int igs_launch_lower(const igs::Unit* units_dev, uint32_t n_units, uint32_t max_items, void* stream);
+int igs_launch_copies(const igs::CopyJob* jobs_dev, uint32_t n_jobs, uint64_t n_units, void* stream);

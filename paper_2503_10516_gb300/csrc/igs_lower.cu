@@ -1,0 +1,2121 @@
+// Device lowering engine: Celerity-style tasks -> per-node instruction graphs.
+//
+// One warp owns one virtual node of one program (each node generates only its
+// own instruction graph, paper Sec. 2.4). The node's region maps live in HBM
+// as structure-of-arrays box tables, scanned coalesced 32 entries at a time;
+// variable numbers of boxes, instructions and edges are emitted with warp
+// ballot / prefix-sum compaction. The warp's control flow is uniform: every
+// lane follows the same path and holds the same scalars.
+//
+// Steps (paper passages):
+//   a1 chunk split + device assignment ... Sec. 3.1
+//   a2 range mappers ..................... Sec. 2.1, Listing 1, Listing 2
+//   a3 push / await push ................. Sec. 2.4, Sec. 3.4
+//   a4 allocation + lookahead merge ...... Sec. 3.2, Sec. 4.3
+//   a5 coherence copies .................. Sec. 3.3 (producer x consumer split)
+//   a6 sends, a7 receives ................ Sec. 3.4
+//   a8 dependencies ...................... Fig. 5 legend, Sec. 3.5, Sec. 4.2
+//   a9 horizon / epoch compaction ........ Sec. 3.5
+//   a10 emission ......................... Sec. 4.1 (topological emission order)
+//   debug checks ......................... Sec. 4.4
+#include <cuda_runtime.h>
+
+#include "igs_internal.h"
+
+namespace igs {
+namespace {
+
+constexpr uint32_t FULL = 0xffffffffu;
+
+// scratch table slots
+enum : int {
+  S_CH = 0, S_MP = 1, S_CH2 = 2, S_MP2 = 3, S_T0 = 4, S_T1 = 5, S_T2 = 6, S_T3 = 7, S_T4 = 8, S_T5 = 9,
+  S_CL = 10, S_DEP = 11, S_CAN = 12, S_RG = 13
+};
+
+struct Bx {
+  uint32_t lo[3], hi[3];
+};
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ bool bx_empty(const Bx& b) {
+  return b.lo[0] >= b.hi[0] || b.lo[1] >= b.hi[1] || b.lo[2] >= b.hi[2];
+}
+__device__ __forceinline__ Bx bx_isect(const Bx& a, const Bx& b) {
+  Bx r;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    r.lo[d] = max(a.lo[d], b.lo[d]);
+    r.hi[d] = min(a.hi[d], b.hi[d]);
+  }
+  return r;
+}
+__device__ __forceinline__ bool bx_overlap(const Bx& a, const Bx& b) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    if (max(a.lo[d], b.lo[d]) >= min(a.hi[d], b.hi[d])) return false;
+  return true;
+}
+__device__ __forceinline__ bool bx_contains(const Bx& o, const Bx& i) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    if (i.lo[d] < o.lo[d] || i.hi[d] > o.hi[d]) return false;
+  return true;
+}
+__device__ __forceinline__ Bx bx_union(const Bx& a, const Bx& b) {
+  Bx r;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    r.lo[d] = min(a.lo[d], b.lo[d]);
+    r.hi[d] = max(a.hi[d], b.hi[d]);
+  }
+  return r;
+}
+__device__ __forceinline__ bool bx_less(const Bx& a, const Bx& b) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    if (a.lo[d] != b.lo[d]) return a.lo[d] < b.lo[d];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    if (a.hi[d] != b.hi[d]) return a.hi[d] < b.hi[d];
+  return false;
+}
+__device__ __forceinline__ bool bx_eq(const Bx& a, const Bx& b) {
+  return a.lo[0] == b.lo[0] && a.lo[1] == b.lo[1] && a.lo[2] == b.lo[2] && a.hi[0] == b.hi[0] &&
+         a.hi[1] == b.hi[1] && a.hi[2] == b.hi[2];
+}
+__device__ __forceinline__ uint64_t bx_volume(const Bx& b) {
+  if (bx_empty(b)) return 0;
+  return (uint64_t)(b.hi[0] - b.lo[0]) * (b.hi[1] - b.lo[1]) * (b.hi[2] - b.lo[2]);
+}
+// a \ b: up to six disjoint pieces; a itself when they do not overlap.
+__device__ __forceinline__ int bx_minus(const Bx& a, const Bx& b, Bx* out) {
+  if (!bx_overlap(a, b)) {
+    out[0] = a;
+    return 1;
+  }
+  int k = 0;
+  Bx rem = a;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (rem.lo[d] < b.lo[d]) {
+      out[k] = rem;
+      out[k].hi[d] = b.lo[d];
+      ++k;
+      rem.lo[d] = b.lo[d];
+    }
+    if (rem.hi[d] > b.hi[d]) {
+      out[k] = rem;
+      out[k].lo[d] = b.hi[d];
+      ++k;
+      rem.hi[d] = b.hi[d];
+    }
+  }
+  return k;
+}
+// Two boxes whose union is a box (adjacent along one dimension, equal in the others).
+__device__ __forceinline__ bool bx_mergeable(const Bx& a, const Bx& b) {
+  int adj = -1;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (a.lo[d] == b.lo[d] && a.hi[d] == b.hi[d]) continue;
+    if (adj >= 0) return false;
+    if (a.hi[d] == b.lo[d] || b.hi[d] == a.lo[d]) adj = d;
+    else return false;
+  }
+  return adj >= 0;
+}
+
+// ---- tables ----------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t* TP(const Table& t, int f) { return t.base + (size_t)f * t.cap; }
+__device__ __forceinline__ uint32_t t_key(const Table& t, uint32_t i) { return TP(t, F_KEY)[i]; }
+__device__ __forceinline__ uint32_t t_v(const Table& t, int k, uint32_t i) { return TP(t, F_V + k)[i]; }
+__device__ __forceinline__ Bx t_box(const Table& t, uint32_t i) {
+  Bx b;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    b.lo[d] = TP(t, F_LO + d)[i];
+    b.hi[d] = TP(t, F_HI + d)[i];
+  }
+  return b;
+}
+__device__ __forceinline__ void t_put(const Table& t, uint32_t i, uint32_t key, const Bx& b, uint32_t v0, uint32_t v1,
+                                      uint32_t v2) {
+  TP(t, F_KEY)[i] = key;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    TP(t, F_LO + d)[i] = b.lo[d];
+    TP(t, F_HI + d)[i] = b.hi[d];
+  }
+  TP(t, F_V)[i] = v0;
+  TP(t, F_V + 1)[i] = v1;
+  TP(t, F_V + 2)[i] = v2;
+}
+__device__ __forceinline__ void t_kill(const Table& t, uint32_t i) { TP(t, F_KEY)[i] = DEAD; }
+
+struct Acc {
+  const Table* t;
+  uint32_t from, to, alloc, mode;
+};
+
+struct Ctx {
+  NodeDev* nd;
+  const ProgDev* pg;
+  uint32_t lane, err;
+  uint32_t node, N, D;
+  uint32_t epoch, last_horizon, last_sync, next_msg, n_alloc;
+  uint32_t n_instr, n_edge, n_box, n_bind, n_diag, n_rej;
+  uint32_t lookahead, q_head, q_count;
+  Table own, bst, wr, rd, qr;
+  Table s[14];
+  uint64_t map_reads, map_writes;
+};
+
+__device__ __forceinline__ void fail(Ctx& c, uint32_t code) {
+  if (c.err == ST_OK) c.err = code;
+}
+
+// Claims one slot per predicated lane (all lanes call). NONE on overflow.
+__device__ __forceinline__ uint32_t t_claim(Ctx& c, Table& t, bool pred) {
+  const uint32_t m = __ballot_sync(FULL, pred);
+  const uint32_t slot = t.n + __popc(m & lanemask_lt());
+  const uint32_t nn = t.n + __popc(m);
+  if (nn > t.cap) {
+    fail(c, ST_CAPACITY);
+    return NONE;
+  }
+  t.n = nn;
+  c.map_writes += __popc(m);
+  return pred ? slot : NONE;
+}
+// Claims k consecutive slots per lane; returns this lane's first slot.
+__device__ __forceinline__ uint32_t t_claim_n(Ctx& c, Table& t, uint32_t k) {
+  uint32_t x = k;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, x, o);
+    if ((int)c.lane >= o) x += y;
+  }
+  const uint32_t total = __shfl_sync(FULL, x, 31);
+  const uint32_t first = t.n + x - k;
+  if (t.n + total > t.cap) {
+    fail(c, ST_CAPACITY);
+    return NONE;
+  }
+  t.n += total;
+  c.map_writes += total;
+  return first;
+}
+
+template <class P>
+__device__ __forceinline__ uint32_t warp_find_first(const Ctx& c, uint32_t n, P pred) {
+  for (uint32_t base = 0; base < n; base += 32) {
+    const uint32_t i = base + c.lane;
+    const bool h = i < n && pred(i);
+    const uint32_t m = __ballot_sync(FULL, h);
+    if (m) return base + __ffs(m) - 1;
+  }
+  return NONE;
+}
+
+__device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t y = __shfl_xor_sync(FULL, v, o);
+    v = y < v ? y : v;
+  }
+  return v;
+}
+__device__ __forceinline__ uint32_t warp_or(uint32_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+__device__ __forceinline__ Bx warp_bbox(Bx b, bool valid) {
+  Bx r;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    uint32_t lo = valid ? b.lo[d] : 0xFFFFFFFFu, hi = valid ? b.hi[d] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(FULL, lo, o));
+      hi = max(hi, __shfl_xor_sync(FULL, hi, o));
+    }
+    r.lo[d] = lo;
+    r.hi[d] = hi;
+  }
+  return r;
+}
+
+// Stable in-place removal of dead entries.
+__device__ void t_compact(Ctx& c, Table& t) {
+  uint32_t w = 0;
+  for (uint32_t base = 0; base < t.n; base += 32) {
+    const uint32_t i = base + c.lane;
+    const bool in = i < t.n;
+    uint32_t key = DEAD, v0 = 0, v1 = 0, v2 = 0;
+    Bx b{};
+    if (in) {
+      key = t_key(t, i);
+      b = t_box(t, i);
+      v0 = t_v(t, 0, i);
+      v1 = t_v(t, 1, i);
+      v2 = t_v(t, 2, i);
+    }
+    __syncwarp();
+    const bool live = in && key != DEAD;
+    const uint32_t m = __ballot_sync(FULL, live);
+    if (live) t_put(t, w + __popc(m & lanemask_lt()), key, b, v0, v1, v2);
+    w += __popc(m);
+    __syncwarp();
+  }
+  t.n = w;
+}
+
+__device__ Bx t_bbox(const Ctx& c, const Table& t, uint32_t from, uint32_t to) {
+  Bx acc;
+  acc.lo[0] = acc.lo[1] = acc.lo[2] = 0xFFFFFFFFu;
+  acc.hi[0] = acc.hi[1] = acc.hi[2] = 0;
+  for (uint32_t base = from; base < to; base += 32) {
+    const uint32_t i = base + c.lane;
+    const bool in = i < to && t_key(t, i) != DEAD;
+    Bx b{};
+    if (in) b = t_box(t, i);
+    Bx r = warp_bbox(b, in);
+    acc = bx_union(acc, r);
+  }
+  return acc;
+}
+
+// Appends (entry n q) with the entry's values for every entry of `key`
+// (NONE = any) that overlaps q and satisfies pred(values).
+template <class P>
+__device__ void t_query(Ctx& c, const Table& src, uint32_t key, const Bx& q, Table& out, P pred) {
+  const uint32_t n = src.n;
+  for (uint32_t base = 0; base < n; base += 32) {
+    const uint32_t i = base + c.lane;
+    bool hit = false;
+    Bx is{};
+    uint32_t v0 = 0, v1 = 0, v2 = 0;
+    if (i < n) {
+      const uint32_t k = t_key(src, i);
+      if (k != DEAD && (key == NONE || k == key)) {
+        is = bx_isect(t_box(src, i), q);
+        if (!bx_empty(is)) {
+          v0 = t_v(src, 0, i);
+          v1 = t_v(src, 1, i);
+          v2 = t_v(src, 2, i);
+          hit = pred(v0, v1, v2);
+        }
+      }
+    }
+    c.map_reads += warp_sum(hit ? 1u : 0u);
+    const uint32_t s = t_claim(c, out, hit);
+    if (c.err) return;
+    if (hit) t_put(out, s, 0, is, v0, v1, v2);
+  }
+  __syncwarp();
+}
+
+// Removes box r from every entry of `key` (NONE = any) that matches the
+// optional value filter; the remainders keep their values.
+__device__ void t_subtract(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t vfilter = NONE) {
+  const uint32_t n0 = t.n;
+  for (uint32_t base = 0; base < n0; base += 32) {
+    const uint32_t i = base + c.lane;
+    bool hit = false;
+    uint32_t k = DEAD, v0 = 0, v1 = 0, v2 = 0;
+    Bx e{};
+    if (i < n0) {
+      k = t_key(t, i);
+      if (k != DEAD && (key == NONE || k == key)) {
+        e = t_box(t, i);
+        v0 = t_v(t, 0, i);
+        hit = bx_overlap(e, r) && (vfilter == NONE || v0 == vfilter);
+        if (hit) {
+          v1 = t_v(t, 1, i);
+          v2 = t_v(t, 2, i);
+        }
+      }
+    }
+    Bx pc[6];
+    int np = 0;
+    if (hit) np = bx_minus(e, r, pc);
+    const uint32_t first = t_claim_n(c, t, hit ? (uint32_t)np : 0u);
+    if (c.err) return;
+    if (hit) {
+      t_kill(t, i);
+      for (int j = 0; j < np; ++j) t_put(t, first + j, k, pc[j], v0, v1, v2);
+    }
+  }
+  __syncwarp();
+}
+
+// value[vidx] |= bits on box r for entries of `key`.
+__device__ void t_or(Ctx& c, Table& t, uint32_t key, const Bx& r, int vidx, uint32_t bits) {
+  const uint32_t n0 = t.n;
+  for (uint32_t base = 0; base < n0; base += 32) {
+    const uint32_t i = base + c.lane;
+    bool hit = false;
+    uint32_t v[3] = {0, 0, 0};
+    Bx e{};
+    if (i < n0 && t_key(t, i) == key) {
+      e = t_box(t, i);
+      v[0] = t_v(t, 0, i);
+      v[1] = t_v(t, 1, i);
+      v[2] = t_v(t, 2, i);
+      hit = bx_overlap(e, r) && (v[vidx] & bits) != bits;
+    }
+    Bx pc[6];
+    int np = 0;
+    if (hit) np = bx_minus(e, r, pc);
+    const uint32_t first = t_claim_n(c, t, hit ? (uint32_t)np + 1 : 0u);
+    if (c.err) return;
+    if (hit) {
+      t_kill(t, i);
+      for (int j = 0; j < np; ++j) t_put(t, first + j, key, pc[j], v[0], v[1], v[2]);
+      v[vidx] |= bits;
+      t_put(t, first + np, key, bx_isect(e, r), v[0], v[1], v[2]);
+    }
+  }
+  __syncwarp();
+}
+
+// Sets the values of box r for `key`.
+__device__ void t_set(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t v0, uint32_t v1, uint32_t v2) {
+  t_subtract(c, t, key, r);
+  const uint32_t s = t_claim(c, t, c.lane == 0);
+  if (c.err) return;
+  if (c.lane == 0) t_put(t, s, key, r, v0, v1, v2);
+  __syncwarp();
+}
+
+// Merges entries from index `from` on with equal key and values into
+// adjacent entries whose union is a box (keeps the tables small).
+__device__ void t_merge_from(Ctx& c, Table& t, uint32_t from) {
+  for (uint32_t i = from; i < t.n; ++i) {
+    uint32_t cand = i;
+    for (int guard = 0; guard < 4096; ++guard) {
+      const uint32_t k = t_key(t, cand);
+      if (k == DEAD) break;
+      const Bx e = t_box(t, cand);
+      const uint32_t v0 = t_v(t, 0, cand), v1 = t_v(t, 1, cand), v2 = t_v(t, 2, cand);
+      const uint32_t j = warp_find_first(c, t.n, [&](uint32_t x) {
+        return x != cand && t_key(t, x) == k && t_v(t, 0, x) == v0 && t_v(t, 1, x) == v1 && t_v(t, 2, x) == v2 &&
+               bx_mergeable(e, t_box(t, x));
+      });
+      if (j == NONE) break;
+      const Bx u = bx_union(e, t_box(t, j));
+      __syncwarp();
+      if (c.lane == 0) {
+        t_put(t, j, k, u, v0, v1, v2);
+        t_kill(t, cand);
+      }
+      __syncwarp();
+      cand = j;
+    }
+  }
+}
+
+// Makes the live entries with value v0 == val (NONE = all) of each key
+// pairwise disjoint by subtracting earlier entries from later ones.
+__device__ void t_make_disjoint(Ctx& c, Table& t, uint32_t val = NONE) {
+  for (uint32_t i = 0; i < t.n; ++i) {
+    const uint32_t k = t_key(t, i);
+    if (k == DEAD) continue;
+    if (val != NONE && t_v(t, 0, i) != val) continue;
+    const Bx e = t_box(t, i);
+    const uint32_t n0 = t.n;
+    for (uint32_t base = i + 1; base < n0; base += 32) {
+      const uint32_t j = base + c.lane;
+      bool hit = false;
+      Bx f{};
+      uint32_t w0 = 0, w1 = 0, w2 = 0;
+      if (j < n0 && t_key(t, j) == k && (val == NONE || t_v(t, 0, j) == val)) {
+        f = t_box(t, j);
+        hit = bx_overlap(e, f);
+        if (hit) {
+          w0 = t_v(t, 0, j);
+          w1 = t_v(t, 1, j);
+          w2 = t_v(t, 2, j);
+        }
+      }
+      Bx pc[6];
+      int np = 0;
+      if (hit) np = bx_minus(f, e, pc);
+      const uint32_t first = t_claim_n(c, t, hit ? (uint32_t)np : 0u);
+      if (c.err) return;
+      if (hit) {
+        t_kill(t, j);
+        for (int q = 0; q < np; ++q) t_put(t, first + q, k, pc[q], w0, w1, w2);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Canonical form (row-major maximal decomposition) of the live boxes of
+// in[from, to), which must be pairwise disjoint; appended to `out` sorted by
+// (lo, hi). Three rewrite phases on a work table: make intervals along the
+// fastest dimension maximal (splitting partially overlapping neighbours),
+// then merge identical intervals over the middle dimension, then identical
+// rectangles over the slowest dimension.
+__device__ uint32_t canonical(Ctx& c, const Table& in, uint32_t from, uint32_t to, Table& out) {
+  Table& W = c.s[S_CAN];
+  W.n = 0;
+  for (uint32_t base = from; base < to; base += 32) {
+    const uint32_t i = base + c.lane;
+    bool live = false;
+    Bx b{};
+    if (i < to && t_key(in, i) != DEAD) {
+      b = t_box(in, i);
+      live = !bx_empty(b);
+    }
+    const uint32_t s = t_claim(c, W, live);
+    if (c.err) return 0;
+    if (live) t_put(W, s, 0, b, 0, 0, 0);
+  }
+  __syncwarp();
+  if (W.n > 512) {  // the pairwise rewrite is quadratic per step: bound its input
+    fail(c, ST_CAPACITY);
+    return 0;
+  }
+  if (W.n > 1) {
+    for (int phase = 0; phase < 3; ++phase) {
+      const int md = 2 - phase;  // dimension merged in this phase
+      for (int guard = 0;; ++guard) {
+        if (guard > 20000) {
+          fail(c, ST_INTERNAL);
+          return 0;
+        }
+        const uint32_t n = W.n;
+        uint32_t found = NONE;
+        const uint64_t pairs = (uint64_t)n * n;
+        for (uint64_t base = 0; base < pairs; base += 32) {
+          const uint64_t p = base + c.lane;
+          bool act = false;
+          if (p < pairs) {
+            const uint32_t i = (uint32_t)(p / n), j = (uint32_t)(p % n);
+            if (i != j && t_key(W, i) != DEAD && t_key(W, j) != DEAD) {
+              const Bx a = t_box(W, i), b = t_box(W, j);
+              act = a.hi[md] == b.lo[md];
+              for (int d = 0; d < 3 && act; ++d) {
+                if (d == md) continue;
+                if (d > md) act = a.lo[d] == b.lo[d] && a.hi[d] == b.hi[d];  // equal in faster dims
+                else act = max(a.lo[d], b.lo[d]) < min(a.hi[d], b.hi[d]);  // overlap in slower dims
+              }
+            }
+          }
+          const uint32_t m = __ballot_sync(FULL, act);
+          if (m) {
+            found = (uint32_t)(base + __ffs(m) - 1);
+            break;
+          }
+        }
+        if (found == NONE) break;
+        const uint32_t i = found / n, j = found % n;
+        const Bx a = t_box(W, i), b = t_box(W, j);
+        bool same = true;
+        for (int d = 0; d < md; ++d) same = same && a.lo[d] == b.lo[d] && a.hi[d] == b.hi[d];
+        __syncwarp();
+        if (same) {
+          if (c.lane == 0) {
+            Bx u = a;
+            u.hi[md] = b.hi[md];
+            t_put(W, i, 0, u, 0, 0, 0);
+            t_kill(W, j);
+          }
+          __syncwarp();
+        } else {
+          // split a and b so that their slower-dimension extents coincide
+          Bx ia = a, ib = b;
+          for (int d = 0; d < md; ++d) {
+            ia.lo[d] = ib.lo[d] = max(a.lo[d], b.lo[d]);
+            ia.hi[d] = ib.hi[d] = min(a.hi[d], b.hi[d]);
+          }
+          Bx pa[6], pb[6];
+          const int na = bx_minus(a, ia, pa), nb = bx_minus(b, ib, pb);
+          const uint32_t first = t_claim_n(c, W, c.lane == 0 ? (uint32_t)(na + nb + 2) : 0u);
+          if (c.err) return 0;
+          if (c.lane == 0) {
+            t_kill(W, i);
+            t_kill(W, j);
+            uint32_t q = first;
+            t_put(W, q++, 0, ia, 0, 0, 0);
+            t_put(W, q++, 0, ib, 0, 0, 0);
+            for (int x = 0; x < na; ++x) t_put(W, q++, 0, pa[x], 0, 0, 0);
+            for (int x = 0; x < nb; ++x) t_put(W, q++, 0, pb[x], 0, 0, 0);
+          }
+          __syncwarp();
+          t_compact(c, W);
+        }
+      }
+      t_compact(c, W);
+    }
+  }
+  // rank sort into out
+  const uint32_t n = W.n;
+  if (out.n + n > out.cap) {
+    fail(c, ST_CAPACITY);
+    return 0;
+  }
+  for (uint32_t base = 0; base < n; base += 32) {
+    const uint32_t i = base + c.lane;
+    if (i < n) {
+      const Bx b = t_box(W, i);
+      uint32_t rank = 0;
+      for (uint32_t j = 0; j < n; ++j)
+        if (j != i && bx_less(t_box(W, j), b)) ++rank;
+      t_put(out, out.n + rank, 0, b, 0, 0, 0);
+    }
+  }
+  out.n += n;
+  __syncwarp();
+  return n;
+}
+
+// ---- node state helpers ----------------------------------------------------
+
+__device__ __forceinline__ Bx alloc_box(const AllocRec& a) {
+  Bx b;
+  for (int d = 0; d < 3; ++d) {
+    b.lo[d] = a.lo[d];
+    b.hi[d] = a.hi[d];
+  }
+  return b;
+}
+
+// The live allocation of (buffer, memory) containing box, or NONE.
+__device__ uint32_t find_alloc(const Ctx& c, uint32_t buf, uint32_t mem, const Bx& b) {
+  const AllocRec* A = c.nd->allocs;
+  return warp_find_first(c, c.n_alloc, [&](uint32_t i) {
+    const AllocRec& a = A[i];
+    return a.live && a.buffer == buf && a.mem == mem && bx_contains(alloc_box(a), b);
+  });
+}
+
+// Per-lane variant (no warp collectives).
+__device__ bool covered_by_alloc(const Ctx& c, uint32_t buf, uint32_t mem, const Bx& b) {
+  const AllocRec* A = c.nd->allocs;
+  for (uint32_t i = 0; i < c.n_alloc; ++i) {
+    const AllocRec& a = A[i];
+    if (a.live && a.buffer == buf && a.mem == mem && bx_contains(alloc_box(a), b)) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ const igs_task& task_of(const Ctx& c, uint32_t item) {
+  return c.pg->tasks[c.pg->items[item].task];
+}
+__device__ __forceinline__ const BufDesc& buf_of(const Ctx& c, uint32_t b) { return c.pg->bufs[b]; }
+
+__device__ Bx buffer_box(const BufDesc& b) {
+  Bx x;
+  for (int d = 0; d < 3; ++d) {
+    x.lo[d] = 0;
+    x.hi[d] = d < (int)b.dims ? b.extent[d] : 1;
+  }
+  return x;
+}
+
+// a1: chunks of a task: key = chunk index, v0 = node, v1 = memory (Sec. 3.1).
+__device__ void task_chunks(Ctx& c, const igs_task& t, Table& CH) {
+  CH.n = 0;
+  const uint64_t E0 = t.range[0], C = t.num_chunks, M = (uint64_t)c.N * c.D;
+  for (uint32_t base = 0; base < t.num_chunks; base += 32) {
+    const uint32_t i = base + c.lane;
+    bool ok = false;
+    Bx b{};
+    uint32_t node = 0, mem = 0;
+    if (i < t.num_chunks) {
+      const uint32_t r0 = (uint32_t)((uint64_t)i * E0 / C), r1 = (uint32_t)((uint64_t)(i + 1) * E0 / C);
+      ok = r0 < r1;
+      const uint32_t g = (uint32_t)((uint64_t)i * M / C);
+      node = g / c.D;
+      mem = 2 + g % c.D;
+      b.lo[0] = r0;
+      b.hi[0] = r1;
+      for (int d = 1; d < 3; ++d) {
+        b.lo[d] = 0;
+        b.hi[d] = t.range[d];
+      }
+    }
+    const uint32_t s = t_claim(c, CH, ok);
+    if (c.err) return;
+    if (ok) t_put(CH, s, i, b, node, mem, 0);
+  }
+  __syncwarp();
+}
+
+// a2: mapped box of accessor a for a chunk box, clamped to the buffer.
+__device__ Bx map_box(const igs_accessor& a, const Bx& ch, const BufDesc& buf) {
+  Bx r;
+  for (int d = 0; d < 3; ++d) {
+    const uint32_t ext = d < (int)buf.dims ? buf.extent[d] : 1;
+    int64_t lo, hi;
+    const igs_map_dim& m = a.dim[d];
+    if (d >= (int)buf.dims) {
+      lo = 0;
+      hi = 1;
+    } else if (m.kind == IGS_MAP_ALL) {
+      lo = 0;
+      hi = ext;
+    } else if (m.kind == IGS_MAP_FIXED) {
+      lo = m.a;
+      hi = m.b;
+    } else {
+      const uint32_t k = m.a;
+      lo = (int64_t)ch.lo[k] + (int32_t)m.b - (int64_t)m.c;
+      hi = (int64_t)ch.hi[k] + (int32_t)m.b + (int64_t)m.c;
+    }
+    lo = lo < 0 ? 0 : lo;
+    hi = hi > (int64_t)ext ? (int64_t)ext : hi;
+    if (lo >= hi) {
+      lo = 0;
+      hi = 0;
+    }
+    r.lo[d] = (uint32_t)lo;
+    r.hi[d] = (uint32_t)hi;
+  }
+  return r;
+}
+
+// Mapped boxes for every (chunk slot, accessor): MP[slot * nacc + a].
+__device__ void task_mapped(Ctx& c, const igs_task& t, const Table& CH, Table& MP) {
+  const uint32_t na = t.num_accessors, total = CH.n * na;
+  if (total > MP.cap) {
+    fail(c, ST_CAPACITY);
+    return;
+  }
+  for (uint32_t base = 0; base < total; base += 32) {
+    const uint32_t i = base + c.lane;
+    if (i < total) {
+      const uint32_t slot = i / na, a = i % na;
+      const Bx b = map_box(t.acc[a], t_box(CH, slot), buf_of(c, t.acc[a].buffer));
+      t_put(MP, i, 0, b, 0, 0, 0);
+    }
+  }
+  MP.n = total;
+  __syncwarp();
+}
+
+// Sec. 4.4: chunks of one task writing overlapping regions.
+__device__ bool overlapping_writes(Ctx& c, const igs_task& t, const Table& CH, const Table& MP) {
+  const uint32_t na = t.num_accessors, nw = CH.n * na;
+  const uint64_t pairs = (uint64_t)nw * nw;
+  for (uint64_t base = 0; base < pairs; base += 32) {
+    const uint64_t p = base + c.lane;
+    bool bad = false;
+    if (p < pairs) {
+      const uint32_t x = (uint32_t)(p / nw), y = (uint32_t)(p % nw);
+      const uint32_t sx = x / na, ax = x % na, sy = y / na, ay = y % na;
+      if (sx < sy && (t.acc[ax].mode & IGS_WRITE) && (t.acc[ay].mode & IGS_WRITE) &&
+          t.acc[ax].buffer == t.acc[ay].buffer)
+        bad = bx_overlap(t_box(MP, x), t_box(MP, y));
+    }
+    if (__ballot_sync(FULL, bad)) return true;
+  }
+  return false;
+}
+
+// ---- emission with dependency tracking (a8, a10) --------------------------
+
+__device__ uint32_t instr_type(const Ctx& c, uint32_t id) { return c.nd->instrs[id].type; }
+
+// Emits one instruction. Dependencies: extra edges already in S_DEP (when
+// keep_dep) plus, per access, the last writers (RAW dataflow; WAW anti; a
+// fresh allocation's own alloc instruction: allocation lifetime) and, for
+// writes, the readers since the last write (WAR anti); no predecessor at all
+// means an edge to the last epoch. Then reads, then writes are applied to
+// the per-allocation tracking tables.
+__device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint32_t fb, uint32_t fc, uint32_t fd,
+                         const Table* bt, uint32_t bfrom, uint32_t bto, const Acc* acc, int nacc, bool keep_dep,
+                         const Table* bindt = nullptr, uint32_t bind_from = 0, uint32_t bind_n = 0) {
+  if (c.err) return NONE;
+  NodeDev* nd = c.nd;
+  Table& D = c.s[S_DEP];
+  if (!keep_dep) D.n = 0;
+  const uint32_t id = c.n_instr;
+  for (int k = 0; k < nacc; ++k) {
+    const Acc& A = acc[k];
+    for (uint32_t r = A.from; r < A.to; ++r) {
+      if (t_key(*A.t, r) == DEAD) continue;
+      const Bx q = t_box(*A.t, r);
+      // writers
+      {
+        const Table& T = c.wr;
+        for (uint32_t base = 0; base < T.n; base += 32) {
+          const uint32_t i = base + c.lane;
+          bool hit = false;
+          uint32_t w = 0, kind = 0;
+          if (i < T.n && t_key(T, i) == A.alloc && bx_overlap(t_box(T, i), q)) {
+            hit = true;
+            w = t_v(T, 0, i);
+            if (instr_type(c, w) == IGS_ALLOC) kind = IGS_DEP_ALLOC;
+            else kind = ((A.mode & IGS_READ) ? IGS_DEP_DATAFLOW : 0u) | ((A.mode & IGS_WRITE) ? IGS_DEP_ANTI : 0u);
+          }
+          c.map_reads += warp_sum(hit ? 1u : 0u);
+          const uint32_t s = t_claim(c, D, hit);
+          if (c.err) return NONE;
+          if (hit) {
+            TP(D, F_V)[s] = w;
+            TP(D, F_V + 1)[s] = kind;
+          }
+        }
+      }
+      if (A.mode & IGS_WRITE) {
+        const Table& T = c.rd;
+        for (uint32_t base = 0; base < T.n; base += 32) {
+          const uint32_t i = base + c.lane;
+          bool hit = i < T.n && t_key(T, i) == A.alloc && bx_overlap(t_box(T, i), q);
+          c.map_reads += warp_sum(hit ? 1u : 0u);
+          const uint32_t s = t_claim(c, D, hit);
+          if (c.err) return NONE;
+          if (hit) {
+            TP(D, F_V)[s] = t_v(T, 0, i);
+            TP(D, F_V + 1)[s] = IGS_DEP_ANTI;
+          }
+        }
+      }
+    }
+  }
+  __syncwarp();
+  if (D.n == 0) {
+    if (c.lane == 0) {
+      TP(D, F_V)[0] = c.epoch;
+      TP(D, F_V + 1)[0] = IGS_DEP_EPOCH;
+    }
+    D.n = 1;
+    __syncwarp();
+  }
+  // unique predecessors in ascending order, kinds OR-ed
+  const uint32_t nd0 = D.n;
+  uint32_t n_unique = 0;
+  {
+    // count firsts
+    for (uint32_t base = 0; base < nd0; base += 32) {
+      const uint32_t i = base + c.lane;
+      bool first = false;
+      if (i < nd0) {
+        const uint32_t p = TP(D, F_V)[i];
+        first = true;
+        for (uint32_t j = 0; j < i; ++j)
+          if (TP(D, F_V)[j] == p) {
+            first = false;
+            break;
+          }
+      }
+      n_unique += __popc(__ballot_sync(FULL, first));
+    }
+  }
+  if (c.n_edge + n_unique > nd->cap_edge || c.n_instr + 1 > nd->cap_instr) {
+    fail(c, ST_CAPACITY);
+    return NONE;
+  }
+  for (uint32_t base = 0; base < nd0; base += 32) {
+    const uint32_t i = base + c.lane;
+    if (i < nd0) {
+      const uint32_t p = TP(D, F_V)[i];
+      bool first = true;
+      uint32_t kind = 0, rank = 0;
+      for (uint32_t j = 0; j < nd0; ++j) {
+        const uint32_t q = TP(D, F_V)[j];
+        if (q == p) {
+          kind |= TP(D, F_V + 1)[j];
+          if (j < i) first = false;
+        } else if (q < p) {
+          bool qfirst = true;
+          for (uint32_t x = 0; x < j; ++x)
+            if (TP(D, F_V)[x] == q) {
+              qfirst = false;
+              break;
+            }
+          if (qfirst) ++rank;
+        }
+      }
+      if (first) {
+        igs_edge e;
+        e.from = p;
+        e.to = id;
+        e.kind = kind;
+        nd->edges[c.n_edge + rank] = e;
+        nd->has_succ[p] = 1;
+      }
+    }
+  }
+  c.n_edge += n_unique;
+  // instruction record, its boxes and bindings
+  uint32_t nb = 0;
+  if (bt) {
+    for (uint32_t base = bfrom; base < bto; base += 32) {
+      const uint32_t i = base + c.lane;
+      const bool live = i < bto && t_key(*bt, i) != DEAD;
+      const uint32_t m = __ballot_sync(FULL, live);
+      if (c.n_box + nb + __popc(m) > nd->cap_box) {
+        fail(c, ST_CAPACITY);
+        return NONE;
+      }
+      if (live) {
+        const Bx b = t_box(*bt, i);
+        igs_box o;
+        for (int d = 0; d < 3; ++d) {
+          o.lo[d] = b.lo[d];
+          o.hi[d] = b.hi[d];
+        }
+        nd->boxes[c.n_box + nb + __popc(m & lanemask_lt())] = o;
+      }
+      nb += __popc(m);
+    }
+  }
+  if (c.n_bind + bind_n > nd->cap_bind) {
+    fail(c, ST_CAPACITY);
+    return NONE;
+  }
+  if (bindt && c.lane < bind_n) {
+    const uint32_t i = bind_from + c.lane;
+    const Bx b = t_box(*bindt, i);
+    igs_binding o;
+    o.alloc = t_v(*bindt, 0, i);
+    for (int d = 0; d < 3; ++d) {
+      o.lo[d] = b.lo[d];
+      o.hi[d] = b.hi[d];
+    }
+    nd->binds[c.n_bind + c.lane] = o;
+  }
+  if (c.lane == 0) {
+    igs_instruction r;
+    r.id = id;
+    r.type = type;
+    r.seq = seq;
+    r.a = fa;
+    r.b = fb;
+    r.c = fc;
+    r.d = fd;
+    r.box_off = c.n_box;
+    r.box_cnt = nb;
+    r.bind_off = c.n_bind;
+    r.bind_cnt = bind_n;
+    nd->instrs[id] = r;
+    nd->has_succ[id] = 0;
+  }
+  c.n_box += nb;
+  c.n_bind += bind_n;
+  c.n_instr += 1;
+  __syncwarp();
+  // apply reads, then writes
+  for (int k = 0; k < nacc; ++k) {
+    const Acc& A = acc[k];
+    if (!(A.mode & IGS_READ)) continue;
+    bool again = false;
+    for (int j = 0; j < k; ++j)
+      if (acc[j].alloc == A.alloc && (acc[j].mode & IGS_READ)) again = true;
+    const uint32_t from = c.rd.n;
+    for (uint32_t r = A.from; r < A.to; ++r) {
+      if (t_key(*A.t, r) == DEAD) continue;
+      const Bx q = t_box(*A.t, r);
+      if (again) t_subtract(c, c.rd, A.alloc, q, id);
+      const uint32_t s = t_claim(c, c.rd, c.lane == 0);
+      if (c.err) return NONE;
+      if (c.lane == 0) t_put(c.rd, s, A.alloc, q, id, 0, 0);
+      __syncwarp();
+    }
+    t_merge_from(c, c.rd, from);
+  }
+  for (int k = 0; k < nacc; ++k) {
+    const Acc& A = acc[k];
+    if (!(A.mode & IGS_WRITE)) continue;
+    const uint32_t from = c.wr.n;
+    for (uint32_t r = A.from; r < A.to; ++r) {
+      if (t_key(*A.t, r) == DEAD) continue;
+      const Bx q = t_box(*A.t, r);
+      t_subtract(c, c.rd, A.alloc, q);
+      t_set(c, c.wr, A.alloc, q, id, 0, 0);
+      if (c.err) return NONE;
+    }
+    t_merge_from(c, c.wr, from);
+  }
+  return id;
+}
+
+// Replace every tracked instruction id older than h by h and re-merge (a9).
+__device__ void apply_epoch(Ctx& c, uint32_t h) {
+  Table* ts[3] = {&c.wr, &c.rd, &c.bst};
+  for (int k = 0; k < 3; ++k) {
+    Table& T = *ts[k];
+    for (uint32_t base = 0; base < T.n; base += 32) {
+      const uint32_t i = base + c.lane;
+      if (i < T.n && t_key(T, i) != DEAD) {
+        const uint32_t v = t_v(T, 0, i);
+        if (v < h) TP(T, F_V)[i] = h;
+      }
+    }
+    __syncwarp();
+  }
+  t_make_disjoint(c, c.rd, h);
+  for (int k = 0; k < 3; ++k) {
+    t_compact(c, *ts[k]);
+    t_merge_from(c, *ts[k], 0);
+    t_compact(c, *ts[k]);
+  }
+  c.epoch = h;
+}
+
+// Free of an allocation: depends on every writer and reader (allocation lifetime).
+__device__ void emit_free(Ctx& c, uint32_t seq, uint32_t aid) {
+  Table& D = c.s[S_DEP];
+  D.n = 0;
+  Table* ts[2] = {&c.wr, &c.rd};
+  for (int k = 0; k < 2; ++k) {
+    Table& T = *ts[k];
+    for (uint32_t base = 0; base < T.n; base += 32) {
+      const uint32_t i = base + c.lane;
+      const bool hit = i < T.n && t_key(T, i) == aid;
+      const uint32_t s = t_claim(c, D, hit);
+      if (c.err) return;
+      if (hit) {
+        TP(D, F_V)[s] = t_v(T, 0, i);
+        TP(D, F_V + 1)[s] = IGS_DEP_ALLOC;
+        t_kill(T, i);
+      }
+    }
+  }
+  __syncwarp();
+  const AllocRec a = c.nd->allocs[aid];
+  emit(c, IGS_FREE, seq, aid, a.mem, a.buffer, NONE, nullptr, 0, 0, nullptr, 0, true);
+  if (c.lane == 0) c.nd->allocs[aid].live = 0;
+  __syncwarp();
+}
+
+// a5: coherence copies making need = T[from, to) (disjoint boxes) up to date
+// in memory m, allocation dst: stale parts split by original producer, then
+// by source allocation, one copy per (producer, source allocation).
+__device__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_t m, uint32_t dst, const Table& T, uint32_t from,
+                          uint32_t to) {
+  Table& Q = c.s[S_T0];
+  Table& G = c.s[S_T1];
+  Table& P = c.s[S_T2];
+  Table& CP = c.s[S_T3];
+  Table& CN = c.s[S_T5];
+  Q.n = 0;
+  CP.n = 0;
+  for (uint32_t r = from; r < to; ++r) {
+    if (t_key(T, r) == DEAD) continue;
+    const Bx q = t_box(T, r);
+    t_query(c, c.bst, b, q, Q, [m](uint32_t prod, uint32_t, uint32_t mask) {
+      return !((mask >> m) & 1u) && prod != NONE;
+    });
+    if (c.err) return;
+  }
+  uint64_t last = 0;
+  bool first_round = true;
+  for (;;) {
+    uint64_t best = ~0ull;
+    for (uint32_t base = 0; base < Q.n; base += 32) {
+      const uint32_t i = base + c.lane;
+      uint64_t k = ~0ull;
+      if (i < Q.n) {
+        k = ((uint64_t)t_v(Q, 0, i) << 32) | t_v(Q, 1, i);
+        if (!first_round && k <= last) k = ~0ull;
+      }
+      k = warp_min64(k);
+      best = k < best ? k : best;
+    }
+    if (best == ~0ull) break;
+    first_round = false;
+    last = best;
+    const uint32_t prod = (uint32_t)(best >> 32), pmem = (uint32_t)best;
+    if (prod == REMOTE) {
+      fail(c, ST_INTERNAL);
+      return;
+    }
+    G.n = 0;
+    for (uint32_t base = 0; base < Q.n; base += 32) {
+      const uint32_t i = base + c.lane;
+      const bool hit = i < Q.n && t_v(Q, 0, i) == prod && t_v(Q, 1, i) == pmem;
+      const uint32_t s = t_claim(c, G, hit);
+      if (c.err) return;
+      if (hit) t_put(G, s, 0, t_box(Q, i), 0, 0, 0);
+    }
+    __syncwarp();
+    for (uint32_t src = 0; src < c.n_alloc; ++src) {
+      const AllocRec a = c.nd->allocs[src];
+      if (!a.live || a.buffer != b || a.mem != pmem) continue;
+      P.n = 0;
+      const Bx ab = alloc_box(a);
+      for (uint32_t base = 0; base < G.n; base += 32) {
+        const uint32_t i = base + c.lane;
+        Bx is{};
+        bool hit = false;
+        if (i < G.n) {
+          is = bx_isect(t_box(G, i), ab);
+          hit = !bx_empty(is);
+        }
+        const uint32_t s = t_claim(c, P, hit);
+        if (c.err) return;
+        if (hit) t_put(P, s, 0, is, 0, 0, 0);
+      }
+      __syncwarp();
+      if (P.n == 0) continue;
+      CN.n = 0;
+      canonical(c, P, 0, P.n, CN);
+      if (c.err) return;
+      Acc acc[2] = {{&CN, 0, CN.n, src, IGS_READ}, {&CN, 0, CN.n, dst, IGS_WRITE}};
+      emit(c, IGS_COPY, seq, src, dst, b, 0, &CN, 0, CN.n, acc, 2, false);
+      if (c.err) return;
+      // remember the copied region
+      for (uint32_t base = 0; base < CN.n; base += 32) {
+        const uint32_t i = base + c.lane;
+        const bool in = i < CN.n;
+        const uint32_t s = t_claim(c, CP, in);
+        if (c.err) return;
+        if (in) t_put(CP, s, 0, t_box(CN, i), 0, 0, 0);
+      }
+      __syncwarp();
+    }
+  }
+  const uint32_t from_bst = c.bst.n;
+  for (uint32_t i = 0; i < CP.n; ++i) {
+    t_or(c, c.bst, b, t_box(CP, i), 2, 1u << m);
+    if (c.err) return;
+  }
+  t_merge_from(c, c.bst, from_bst);
+}
+
+// ---- a3: push / await push (node level) ------------------------------------
+
+// Per buffer: missing_m = reads of node m's chunks not replicated on m; this
+// node awaits missing_node and pushes missing_m n owned(node) to every m.
+// Results go to the QR table under key seq: v0 = 0 push boxes, 1 await boxes,
+// 2 push bbox, 3 await bbox; v1 = buffer; v2 = target node.
+__device__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP) {
+  const uint32_t na = t.num_accessors;
+  Table& TMP = c.s[S_T0];
+  Table& MISS = c.s[S_T1];
+  Table& PT = c.s[S_T2];
+  Table& CN = c.s[S_T3];
+  uint32_t done = 0;  // bitmask over accessor indices whose buffer was handled
+  for (;;) {
+    // next buffer in ascending order
+    uint32_t b = NONE;
+    for (uint32_t a = 0; a < na; ++a)
+      if (!(done >> a & 1u) && (b == NONE || t.acc[a].buffer < b)) b = t.acc[a].buffer;
+    if (b == NONE) break;
+    for (uint32_t a = 0; a < na; ++a)
+      if (t.acc[a].buffer == b) done |= 1u << a;
+    MISS.n = 0;
+    for (uint32_t m = 0; m < c.N; ++m) {
+      TMP.n = 0;
+      for (uint32_t slot = 0; slot < CH.n; ++slot) {
+        if (t_v(CH, 0, slot) != m) continue;
+        for (uint32_t a = 0; a < na; ++a) {
+          if (t.acc[a].buffer != b || !(t.acc[a].mode & IGS_READ)) continue;
+          const Bx x = t_box(MP, slot * na + a);
+          if (bx_empty(x)) continue;
+          t_query(c, c.own, b, x, TMP, [m](uint32_t, uint32_t repl, uint32_t) { return !((repl >> m) & 1u); });
+          if (c.err) return;
+        }
+      }
+      t_make_disjoint(c, TMP);
+      if (c.err) return;
+      for (uint32_t base = 0; base < TMP.n; base += 32) {
+        const uint32_t i = base + c.lane;
+        const bool live = i < TMP.n && t_key(TMP, i) != DEAD;
+        const uint32_t s = t_claim(c, MISS, live);
+        if (c.err) return;
+        if (live) t_put(MISS, s, 0, t_box(TMP, i), m, 0, 0);
+      }
+      __syncwarp();
+    }
+    // this node's await (canonical) and bbox
+    {
+      Table& sel = TMP;
+      sel.n = 0;
+      for (uint32_t base = 0; base < MISS.n; base += 32) {
+        const uint32_t i = base + c.lane;
+        const bool hit = i < MISS.n && t_v(MISS, 0, i) == c.node;
+        const uint32_t s = t_claim(c, sel, hit);
+        if (c.err) return;
+        if (hit) t_put(sel, s, 0, t_box(MISS, i), 0, 0, 0);
+      }
+      __syncwarp();
+      if (sel.n) {
+        CN.n = 0;
+        canonical(c, sel, 0, sel.n, CN);
+        if (c.err) return;
+        const Bx bb = t_bbox(c, CN, 0, CN.n);
+        for (uint32_t base = 0; base < CN.n + 1; base += 32) {
+          const uint32_t i = base + c.lane;
+          const bool in = i < CN.n + 1;
+          const uint32_t s = t_claim(c, c.qr, in);
+          if (c.err) return;
+          if (in) {
+            if (i < CN.n) t_put(c.qr, s, seq, t_box(CN, i), 1, b, NONE);
+            else t_put(c.qr, s, seq, bb, 3, b, NONE);
+          }
+        }
+        __syncwarp();
+      }
+    }
+    // this node's pushes to every other node
+    for (uint32_t m = 0; m < c.N; ++m) {
+      if (m == c.node) continue;
+      PT.n = 0;
+      for (uint32_t i = 0; i < MISS.n; ++i) {
+        if (t_v(MISS, 0, i) != m) continue;
+        const uint32_t me = c.node;
+        t_query(c, c.own, b, t_box(MISS, i), PT, [me](uint32_t owner, uint32_t, uint32_t) { return owner == me; });
+        if (c.err) return;
+      }
+      if (PT.n == 0) continue;
+      CN.n = 0;
+      canonical(c, PT, 0, PT.n, CN);
+      if (c.err) return;
+      const Bx bb = t_bbox(c, CN, 0, CN.n);
+      for (uint32_t base = 0; base < CN.n + 1; base += 32) {
+        const uint32_t i = base + c.lane;
+        const bool in = i < CN.n + 1;
+        const uint32_t s = t_claim(c, c.qr, in);
+        if (c.err) return;
+        if (in) {
+          if (i < CN.n) t_put(c.qr, s, seq, t_box(CN, i), 0, b, m);
+          else t_put(c.qr, s, seq, bb, 2, b, m);
+        }
+      }
+      __syncwarp();
+    }
+    // replication: every node now holds what it awaited
+    const uint32_t from = c.own.n;
+    for (uint32_t i = 0; i < MISS.n; ++i) {
+      t_or(c, c.own, b, t_box(MISS, i), 1, 1u << t_v(MISS, 0, i));
+      if (c.err) return;
+    }
+    // writes: owner = writing node, replicated there only
+    for (uint32_t slot = 0; slot < CH.n; ++slot) {
+      const uint32_t wn = t_v(CH, 0, slot);
+      for (uint32_t a = 0; a < na; ++a) {
+        if (t.acc[a].buffer != b || !(t.acc[a].mode & IGS_WRITE)) continue;
+        const Bx x = t_box(MP, slot * na + a);
+        if (bx_empty(x)) continue;
+        t_set(c, c.own, b, x, wn, 1u << wn, 0);
+        if (c.err) return;
+      }
+    }
+    t_merge_from(c, c.own, from);
+  }
+}
+
+// ---- requirements, allocation planning (a4) --------------------------------
+
+// QR block [qs, qe) of a task (entries of key seq are contiguous).
+__device__ void qr_block(const Ctx& c, uint32_t seq, uint32_t& qs, uint32_t& qe) {
+  qs = warp_find_first(c, c.qr.n, [&](uint32_t i) { return t_key(c.qr, i) == seq; });
+  if (qs == NONE) {
+    qs = qe = 0;
+    return;
+  }
+  qe = qs;
+  while (qe < c.qr.n && t_key(c.qr, qe) == seq) ++qe;
+}
+
+// Appends the requirements (key = buffer * 32 + memory, box) of a task on this
+// node: every non-empty mapped box of a local chunk, plus the staging bboxes.
+__device__ void requirements(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP, Table& RQ,
+                             uint32_t only_key, uint32_t own_flag) {
+  const uint32_t na = t.num_accessors, total = CH.n * na;
+  for (uint32_t base = 0; base < total; base += 32) {
+    const uint32_t i = base + c.lane;
+    bool hit = false;
+    Bx x{};
+    uint32_t key = 0;
+    if (i < total) {
+      const uint32_t slot = i / na, a = i % na;
+      if (t_v(CH, 0, slot) == c.node) {
+        x = t_box(MP, i);
+        key = t.acc[a].buffer * 32 + t_v(CH, 1, slot);
+        hit = !bx_empty(x) && (only_key == NONE || key == only_key);
+      }
+    }
+    const uint32_t s = t_claim(c, RQ, hit);
+    if (c.err) return;
+    if (hit) t_put(RQ, s, key, x, own_flag, 0, 0);
+  }
+  uint32_t qs, qe;
+  qr_block(c, seq, qs, qe);
+  for (uint32_t base = qs; base < qe; base += 32) {
+    const uint32_t i = base + c.lane;
+    bool hit = false;
+    uint32_t key = 0;
+    if (i < qe) {
+      const uint32_t kind = t_v(c.qr, 0, i);
+      key = t_v(c.qr, 1, i) * 32 + 1;
+      hit = (kind == 2 || kind == 3) && (only_key == NONE || key == only_key);
+    }
+    const uint32_t s = t_claim(c, RQ, hit);
+    if (c.err) return;
+    if (hit) t_put(RQ, s, key, t_box(c.qr, i), own_flag, 0, 0);
+  }
+  __syncwarp();
+}
+
+__device__ bool allocating(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP) {
+  Table& RQ = c.s[S_CL];
+  RQ.n = 0;
+  requirements(c, t, seq, CH, MP, RQ, NONE, 1);
+  if (c.err) return false;
+  for (uint32_t base = 0; base < RQ.n; base += 32) {
+    const uint32_t i = base + c.lane;
+    bool need = false;
+    if (i < RQ.n) {
+      const uint32_t key = t_key(RQ, i);
+      need = !covered_by_alloc(c, key >> 5, key & 31u, t_box(RQ, i));
+    }
+    if (__ballot_sync(FULL, need)) return true;
+  }
+  return false;
+}
+
+__device__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP) {
+  Table& RQ = c.s[S_T4];
+  Table& CL = c.s[S_CL];
+  Table& CH2 = c.s[S_CH2];
+  Table& MP2 = c.s[S_MP2];
+  Table& Q = c.s[S_T0];
+  Table& CN = c.s[S_T5];
+  RQ.n = 0;
+  requirements(c, t, seq, CH, MP, RQ, NONE, 1);
+  if (c.err) return;
+  uint32_t last_key = NONE;
+  bool first_key = true;
+  for (;;) {
+    uint64_t best = ~0ull;
+    for (uint32_t base = 0; base < RQ.n; base += 32) {
+      const uint32_t i = base + c.lane;
+      uint64_t k = ~0ull;
+      if (i < RQ.n) {
+        const uint32_t key = t_key(RQ, i);
+        if (first_key || key > last_key) k = key;
+      }
+      k = warp_min64(k);
+      best = k < best ? k : best;
+    }
+    if (best == ~0ull) break;
+    first_key = false;
+    const uint32_t key = (uint32_t)best;
+    last_key = key;
+    const uint32_t b = key >> 5, m = key & 31u;
+    CL.n = 0;
+    for (uint32_t base = 0; base < RQ.n; base += 32) {
+      const uint32_t i = base + c.lane;
+      bool hit = false;
+      Bx x{};
+      if (i < RQ.n && t_key(RQ, i) == key) {
+        x = t_box(RQ, i);
+        hit = !covered_by_alloc(c, b, m, x);
+      }
+      const uint32_t s = t_claim(c, CL, hit);
+      if (c.err) return;
+      if (hit) t_put(CL, s, 0, x, 1, 0, 0);
+    }
+    __syncwarp();
+    if (CL.n == 0) continue;
+    // lookahead: requirements of every task still queued (Sec. 4.3)
+    for (uint32_t q = 0; q < c.q_count; ++q) {
+      const uint32_t item = c.nd->queue[(c.q_head + q) % c.nd->cap_queue];
+      const Item it = c.pg->items[item];
+      if (it.kind != IT_TASK) continue;
+      const igs_task& qt = c.pg->tasks[it.task];
+      task_chunks(c, qt, CH2);
+      task_mapped(c, qt, CH2, MP2);
+      const uint32_t from = CL.n;
+      requirements(c, qt, it.seq, CH2, MP2, CL, key, 0);
+      if (c.err) return;
+      // drop the ones already inside an allocation
+      for (uint32_t base = from; base < CL.n; base += 32) {
+        const uint32_t i = base + c.lane;
+        if (i < CL.n && covered_by_alloc(c, b, m, t_box(CL, i))) t_kill(CL, i);
+      }
+      __syncwarp();
+      for (uint32_t base = from; base < CL.n; base += 32) {
+        const uint32_t i = base + c.lane;
+        if (i < CL.n && t_key(CL, i) != DEAD) TP(CL, F_KEY)[i] = 0;
+      }
+      __syncwarp();
+    }
+    // clusters: fixed point of merging positively overlapping bounding boxes
+    // and absorbing every overlapping live allocation of (b, m) [positive
+    // volume, merely touching boxes stay apart]
+    AllocRec* A = c.nd->allocs;
+    for (uint32_t base = 0; base < c.n_alloc; base += 32) {
+      const uint32_t i = base + c.lane;
+      if (i < c.n_alloc) A[i].mark = NONE;
+    }
+    __syncwarp();
+    for (int guard = 0;; ++guard) {
+      if (guard > 1 << 20) {
+        fail(c, ST_INTERNAL);
+        return;
+      }
+      const uint32_t n = CL.n;
+      const uint64_t pairs = (uint64_t)n * n;
+      uint32_t found = NONE;
+      for (uint64_t base = 0; base < pairs; base += 32) {
+        const uint64_t p = base + c.lane;
+        bool h = false;
+        if (p < pairs) {
+          const uint32_t i = (uint32_t)(p / n), j = (uint32_t)(p % n);
+          h = i < j && t_key(CL, i) != DEAD && t_key(CL, j) != DEAD && bx_overlap(t_box(CL, i), t_box(CL, j));
+        }
+        const uint32_t mm = __ballot_sync(FULL, h);
+        if (mm) {
+          found = (uint32_t)(base + __ffs(mm) - 1);
+          break;
+        }
+      }
+      if (found != NONE) {
+        const uint32_t i = found / n, j = found % n;
+        const Bx u = bx_union(t_box(CL, i), t_box(CL, j));
+        const uint32_t own = t_v(CL, 0, i) | t_v(CL, 0, j);
+        __syncwarp();
+        if (c.lane == 0) {
+          t_put(CL, i, 0, u, own, 0, 0);
+          t_kill(CL, j);
+        }
+        for (uint32_t base = 0; base < c.n_alloc; base += 32) {
+          const uint32_t x = base + c.lane;
+          if (x < c.n_alloc && A[x].mark == j) A[x].mark = i;
+        }
+        __syncwarp();
+        continue;
+      }
+      // a cluster overlapping an unabsorbed allocation
+      const uint64_t cp = (uint64_t)n * c.n_alloc;
+      found = NONE;
+      for (uint64_t base = 0; base < cp; base += 32) {
+        const uint64_t p = base + c.lane;
+        bool h = false;
+        if (p < cp) {
+          const uint32_t i = (uint32_t)(p / c.n_alloc), x = (uint32_t)(p % c.n_alloc);
+          const AllocRec& a = A[x];
+          h = t_key(CL, i) != DEAD && a.live && a.buffer == b && a.mem == m && a.mark == NONE &&
+              bx_overlap(t_box(CL, i), alloc_box(a));
+        }
+        const uint32_t mm = __ballot_sync(FULL, h);
+        if (mm) {
+          found = (uint32_t)(base + __ffs(mm) - 1);
+          break;
+        }
+      }
+      if (found == NONE) break;
+      {
+        const uint32_t i = found / c.n_alloc, x = found % c.n_alloc;
+        const Bx u = bx_union(t_box(CL, i), alloc_box(A[x]));
+        const uint32_t own = t_v(CL, 0, i);
+        __syncwarp();
+        if (c.lane == 0) {
+          t_put(CL, i, 0, u, own, 0, 0);
+          A[x].mark = i;
+        }
+        __syncwarp();
+      }
+    }
+    // emit one allocation per cluster holding a requirement of this task, in
+    // box order; resize: copy the live part of every absorbed allocation, free it
+    const uint32_t n = CL.n;
+    for (uint32_t base = 0; base < n; base += 32) {
+      const uint32_t i = base + c.lane;
+      if (i < n && t_key(CL, i) != DEAD && t_v(CL, 0, i) == 1) {
+        const Bx bi = t_box(CL, i);
+        uint32_t rank = 0;
+        for (uint32_t j = 0; j < n; ++j)
+          if (j != i && t_key(CL, j) != DEAD && t_v(CL, 0, j) == 1 && bx_less(t_box(CL, j), bi)) ++rank;
+        TP(CL, F_V + 1)[i] = rank;
+      }
+    }
+    __syncwarp();
+    for (uint32_t r = 0;; ++r) {
+      const uint32_t ci = warp_find_first(c, n, [&](uint32_t i) {
+        return t_key(CL, i) != DEAD && t_v(CL, 0, i) == 1 && t_v(CL, 1, i) == r;
+      });
+      if (ci == NONE) break;
+      const Bx bb = t_box(CL, ci);
+      if (c.n_alloc >= c.nd->cap_alloc) {
+        fail(c, ST_CAPACITY);
+        return;
+      }
+      const uint32_t aid = c.n_alloc;
+      const uint32_t iid = emit(c, IGS_ALLOC, seq, aid, m, b, NONE, &CL, ci, ci + 1, nullptr, 0, false);
+      if (c.err) return;
+      if (c.lane == 0) {
+        AllocRec rec;
+        rec.buffer = b;
+        rec.mem = m;
+        rec.live = 1;
+        rec.user = 0;
+        for (int d = 0; d < 3; ++d) {
+          rec.lo[d] = bb.lo[d];
+          rec.hi[d] = bb.hi[d];
+        }
+        rec.mark = NONE;
+        rec.pad = 0;
+        A[aid] = rec;
+      }
+      c.n_alloc += 1;
+      __syncwarp();
+      {
+        const uint32_t s = t_claim(c, c.wr, c.lane == 0);
+        if (c.err) return;
+        if (c.lane == 0) t_put(c.wr, s, aid, bb, iid, 0, 0);
+        __syncwarp();
+      }
+      for (uint32_t old = 0; old < aid; ++old) {
+        if (A[old].mark != ci || !A[old].live) continue;
+        Q.n = 0;
+        t_query(c, c.bst, b, alloc_box(A[old]), Q, [m](uint32_t, uint32_t, uint32_t mask) { return ((mask >> m) & 1u) != 0; });
+        if (c.err) return;
+        CN.n = 0;
+        canonical(c, Q, 0, Q.n, CN);
+        if (c.err) return;
+        if (CN.n) {
+          Acc acc[2] = {{&CN, 0, CN.n, old, IGS_READ}, {&CN, 0, CN.n, aid, IGS_WRITE}};
+          emit(c, IGS_COPY, seq, old, aid, b, 1, &CN, 0, CN.n, acc, 2, false);
+          if (c.err) return;
+        }
+        emit_free(c, seq, old);
+        if (c.err) return;
+      }
+    }
+  }
+}
+
+// ---- compile one task (P1..P5) ----------------------------------------------
+
+__device__ void compile_task(Ctx& c, uint32_t item) {
+  const Item it = c.pg->items[item];
+  const igs_task& t = c.pg->tasks[it.task];
+  const uint32_t seq = it.seq, na = t.num_accessors;
+  Table& CH = c.s[S_CH];
+  Table& MP = c.s[S_MP];
+  task_chunks(c, t, CH);
+  task_mapped(c, t, CH, MP);
+  if (c.err) return;
+  // P1
+  alloc_phase(c, t, seq, CH, MP);
+  if (c.err) return;
+  uint32_t qs, qe;
+  qr_block(c, seq, qs, qe);
+  // P2: pushes, (buffer, target) ascending
+  Table& Q = c.s[S_T0];
+  Table& G = c.s[S_T1];
+  Table& CN = c.s[S_T5];
+  Table& RG = c.s[S_RG];
+  for (uint32_t g0 = qs; g0 < qe;) {
+    uint32_t g1 = g0;
+    while (g1 < qe && t_v(c.qr, 0, g1) == t_v(c.qr, 0, g0)) ++g1;  // boxes, then one bbox entry
+    const uint32_t kind = t_v(c.qr, 0, g0);
+    if (kind != 0) {
+      g0 = g1 + (kind == 1 ? 1 : 0);
+      continue;
+    }
+    const uint32_t b = t_v(c.qr, 1, g0), target = t_v(c.qr, 2, g0);
+    const Bx bb = t_box(c.qr, g1);  // the bbox entry follows the boxes
+    const uint32_t dst = find_alloc(c, b, 1, bb);
+    if (dst == NONE) {
+      fail(c, ST_INTERNAL);
+      return;
+    }
+    // copy the push region into RG (coherence uses the scratch tables)
+    RG.n = 0;
+    for (uint32_t base = g0; base < g1; base += 32) {
+      const uint32_t i = base + c.lane;
+      const bool in = i < g1;
+      const uint32_t s = t_claim(c, RG, in);
+      if (c.err) return;
+      if (in) t_put(RG, s, 0, t_box(c.qr, i), 0, 0, 0);
+    }
+    __syncwarp();
+    coherence(c, seq, b, 1, dst, RG, 0, RG.n);
+    if (c.err) return;
+    // sends: one per (original producer, canonical box)
+    Q.n = 0;
+    for (uint32_t r = 0; r < RG.n; ++r) {
+      t_query(c, c.bst, b, t_box(RG, r), Q, [](uint32_t, uint32_t, uint32_t) { return true; });
+      if (c.err) return;
+    }
+    uint64_t last = 0;
+    bool first_round = true;
+    for (;;) {
+      uint64_t best = ~0ull;
+      for (uint32_t base = 0; base < Q.n; base += 32) {
+        const uint32_t i = base + c.lane;
+        uint64_t k = ~0ull;
+        if (i < Q.n) {
+          k = ((uint64_t)t_v(Q, 0, i) << 32) | t_v(Q, 1, i);
+          if (!first_round && k <= last) k = ~0ull;
+        }
+        k = warp_min64(k);
+        best = k < best ? k : best;
+      }
+      if (best == ~0ull) break;
+      first_round = false;
+      last = best;
+      G.n = 0;
+      for (uint32_t base = 0; base < Q.n; base += 32) {
+        const uint32_t i = base + c.lane;
+        const bool hit = i < Q.n && (((uint64_t)t_v(Q, 0, i) << 32) | t_v(Q, 1, i)) == best;
+        const uint32_t s = t_claim(c, G, hit);
+        if (c.err) return;
+        if (hit) t_put(G, s, 0, t_box(Q, i), 0, 0, 0);
+      }
+      __syncwarp();
+      CN.n = 0;
+      canonical(c, G, 0, G.n, CN);
+      if (c.err) return;
+      for (uint32_t i = 0; i < CN.n; ++i) {
+        Acc acc[1] = {{&CN, i, i + 1, dst, IGS_READ}};
+        emit(c, IGS_SEND, seq, dst, target, b, c.next_msg, &CN, i, i + 1, acc, 1, false);
+        if (c.err) return;
+        c.next_msg += 1;
+      }
+    }
+    g0 = g1 + 1;
+  }
+  // P3: await push per buffer: one receive, or split receive + await receives
+  Table& CONS = c.s[S_T4];
+  Table& COV = c.s[S_CL];
+  for (uint32_t g0 = qs; g0 < qe;) {
+    uint32_t g1 = g0;
+    while (g1 < qe && t_v(c.qr, 0, g1) == t_v(c.qr, 0, g0)) ++g1;
+    const uint32_t kind = t_v(c.qr, 0, g0);
+    if (kind != 1) {
+      g0 = g1 + (kind == 0 ? 1 : 0);
+      continue;
+    }
+    const uint32_t b = t_v(c.qr, 1, g0);
+    const Bx bb = t_box(c.qr, g1);
+    const uint32_t dst = find_alloc(c, b, 1, bb);
+    if (dst == NONE) {
+      fail(c, ST_INTERNAL);
+      return;
+    }
+    RG.n = 0;
+    uint64_t wvol = 0;
+    for (uint32_t base = g0; base < g1; base += 32) {
+      const uint32_t i = base + c.lane;
+      const bool in = i < g1;
+      const uint32_t s = t_claim(c, RG, in);
+      if (c.err) return;
+      if (in) t_put(RG, s, 0, t_box(c.qr, i), 0, 0, 0);
+    }
+    __syncwarp();
+    for (uint32_t i = 0; i < RG.n; ++i) wvol += bx_volume(t_box(RG, i));
+    // consumers in (chunk, accessor) order: v0 = consumer index
+    CONS.n = 0;
+    uint32_t ncons = 0;
+    bool whole = true;
+    for (uint32_t slot = 0; slot < CH.n; ++slot) {
+      if (t_v(CH, 0, slot) != c.node) continue;
+      for (uint32_t a = 0; a < na; ++a) {
+        if (t.acc[a].buffer != b || !(t.acc[a].mode & IGS_READ)) continue;
+        const Bx x = t_box(MP, slot * na + a);
+        if (bx_empty(x)) continue;
+        uint64_t vol = 0;
+        const uint32_t from = CONS.n;
+        for (uint32_t base = 0; base < RG.n; base += 32) {
+          const uint32_t i = base + c.lane;
+          Bx is{};
+          bool hit = false;
+          if (i < RG.n) {
+            is = bx_isect(t_box(RG, i), x);
+            hit = !bx_empty(is);
+          }
+          vol += warp_sum(hit ? (uint32_t)0 : 0u);
+          const uint32_t s = t_claim(c, CONS, hit);
+          if (c.err) return;
+          if (hit) t_put(CONS, s, 0, is, ncons, 0, 0);
+        }
+        __syncwarp();
+        if (CONS.n == from) continue;
+        for (uint32_t i = from; i < CONS.n; ++i) vol += bx_volume(t_box(CONS, i));
+        if (vol != wvol) whole = false;
+        ++ncons;
+      }
+    }
+    if (ncons <= 1) whole = true;
+    if (whole) {
+      Acc acc[1] = {{&RG, 0, RG.n, dst, IGS_WRITE}};
+      const uint32_t id = emit(c, IGS_RECEIVE, seq, dst, NONE, b, NONE, &RG, 0, RG.n, acc, 1, false);
+      if (c.err) return;
+      const uint32_t from = c.bst.n;
+      for (uint32_t i = 0; i < RG.n; ++i) {
+        t_set(c, c.bst, b, t_box(RG, i), id, 1, 1u << 1);
+        if (c.err) return;
+      }
+      t_merge_from(c, c.bst, from);
+    } else {
+      Acc acc[1] = {{&RG, 0, RG.n, dst, IGS_WRITE}};
+      const uint32_t sid = emit(c, IGS_SPLIT_RECEIVE, seq, dst, NONE, b, NONE, &RG, 0, RG.n, acc, 1, false);
+      if (c.err) return;
+      COV.n = 0;
+      for (uint32_t k = 0; k < ncons; ++k) {
+        // part = consumer k's region minus what earlier await receives cover
+        G.n = 0;
+        for (uint32_t base = 0; base < CONS.n; base += 32) {
+          const uint32_t i = base + c.lane;
+          const bool hit = i < CONS.n && t_v(CONS, 0, i) == k;
+          const uint32_t s = t_claim(c, G, hit);
+          if (c.err) return;
+          if (hit) t_put(G, s, 0, t_box(CONS, i), 0, 0, 0);
+        }
+        __syncwarp();
+        for (uint32_t i = 0; i < COV.n; ++i) {
+          t_subtract(c, G, NONE, t_box(COV, i));
+          if (c.err) return;
+        }
+        CN.n = 0;
+        canonical(c, G, 0, G.n, CN);
+        if (c.err) return;
+        if (CN.n == 0) continue;
+        Table& D = c.s[S_DEP];
+        D.n = 0;
+        if (c.lane == 0) {
+          TP(D, F_V)[0] = sid;
+          TP(D, F_V + 1)[0] = IGS_DEP_DATAFLOW;
+        }
+        D.n = 1;
+        __syncwarp();
+        const uint32_t aid = emit(c, IGS_AWAIT_RECEIVE, seq, dst, sid, b, NONE, &CN, 0, CN.n, nullptr, 0, true);
+        if (c.err) return;
+        const uint32_t fw = c.wr.n, fb = c.bst.n;
+        for (uint32_t i = 0; i < CN.n; ++i) {
+          const Bx x = t_box(CN, i);
+          t_set(c, c.wr, dst, x, aid, 0, 0);
+          t_set(c, c.bst, b, x, aid, 1, 1u << 1);
+          if (c.err) return;
+        }
+        t_merge_from(c, c.wr, fw);
+        t_merge_from(c, c.bst, fb);
+        for (uint32_t base = 0; base < CN.n; base += 32) {
+          const uint32_t i = base + c.lane;
+          const bool in = i < CN.n;
+          const uint32_t s = t_claim(c, COV, in);
+          if (c.err) return;
+          if (in) t_put(COV, s, 0, t_box(CN, i), 0, 0, 0);
+        }
+        __syncwarp();
+      }
+    }
+    g0 = g1 + 1;
+  }
+  // P4: coherence for every reading accessor, (chunk, accessor) order
+  for (uint32_t slot = 0; slot < CH.n; ++slot) {
+    if (t_v(CH, 0, slot) != c.node) continue;
+    const uint32_t mem = t_v(CH, 1, slot);
+    for (uint32_t a = 0; a < na; ++a) {
+      const igs_accessor& ac = t.acc[a];
+      if (!(ac.mode & IGS_READ)) continue;
+      const Bx x = t_box(MP, slot * na + a);
+      if (bx_empty(x)) continue;
+      // uninitialized read warning (Sec. 4.4)
+      const uint32_t b = ac.buffer;
+      const uint32_t un = warp_find_first(c, c.bst.n, [&](uint32_t i) {
+        return t_key(c.bst, i) == b && t_v(c.bst, 0, i) == NONE && bx_overlap(t_box(c.bst, i), x);
+      });
+      if (un != NONE) {
+        if (c.n_diag >= c.nd->cap_diag) {
+          fail(c, ST_CAPACITY);
+          return;
+        }
+        if (c.lane == 0) {
+          igs_diag dg;
+          dg.seq = seq;
+          dg.chunk = t_key(CH, slot);
+          dg.accessor = a;
+          c.nd->diags[c.n_diag] = dg;
+        }
+        c.n_diag += 1;
+        __syncwarp();
+      }
+      const uint32_t dst = find_alloc(c, b, mem, x);
+      if (dst == NONE) {
+        fail(c, ST_INTERNAL);
+        return;
+      }
+      RG.n = 0;
+      {
+        const uint32_t s = t_claim(c, RG, c.lane == 0);
+        if (c.err) return;
+        if (c.lane == 0) t_put(RG, s, 0, x, 0, 0, 0);
+        __syncwarp();
+      }
+      coherence(c, seq, b, mem, dst, RG, 0, 1);
+      if (c.err) return;
+    }
+  }
+  // P5: one device kernel per local chunk
+  Table& BT = c.s[S_T4];
+  for (uint32_t slot = 0; slot < CH.n; ++slot) {
+    if (t_v(CH, 0, slot) != c.node) continue;
+    const uint32_t mem = t_v(CH, 1, slot);
+    BT.n = 0;
+    Acc acc[IGS_MAX_ACCESSORS];
+    int nacc = 0;
+    for (uint32_t a = 0; a < na; ++a) {
+      const Bx x = t_box(MP, slot * na + a);
+      uint32_t al = NONE;
+      if (!bx_empty(x)) {
+        al = find_alloc(c, t.acc[a].buffer, mem, x);
+        if (al == NONE) {
+          fail(c, ST_INTERNAL);
+          return;
+        }
+      }
+      if (c.lane == 0) {
+        Bx z{};
+        t_put(BT, a, 0, bx_empty(x) ? z : x, al, 0, 0);
+      }
+      if (al != NONE) acc[nacc++] = Acc{&BT, a, a + 1, al, t.acc[a].mode};
+    }
+    BT.n = na;
+    __syncwarp();
+    const uint32_t kid = emit(c, IGS_KERNEL, seq, t_key(CH, slot), mem, t.kernel_id, NONE, &CH, slot, slot + 1, acc,
+                              nacc, false, &BT, 0, na);
+    if (c.err) return;
+    const uint32_t from = c.bst.n;
+    for (uint32_t a = 0; a < na; ++a) {
+      const Bx x = t_box(MP, slot * na + a);
+      if (!(t.acc[a].mode & IGS_WRITE) || bx_empty(x)) continue;
+      t_set(c, c.bst, t.acc[a].buffer, x, kid, mem, 1u << mem);
+      if (c.err) return;
+    }
+    t_merge_from(c, c.bst, from);
+  }
+  // writes of other nodes make the local copies stale
+  {
+    const uint32_t from = c.bst.n;
+    for (uint32_t slot = 0; slot < CH.n; ++slot) {
+      if (t_v(CH, 0, slot) == c.node) continue;
+      for (uint32_t a = 0; a < na; ++a) {
+        const Bx x = t_box(MP, slot * na + a);
+        if (!(t.acc[a].mode & IGS_WRITE) || bx_empty(x)) continue;
+        t_set(c, c.bst, t.acc[a].buffer, x, REMOTE, 0, 0);
+        if (c.err) return;
+      }
+    }
+    t_merge_from(c, c.bst, from);
+  }
+  // the task's push / await regions are consumed
+  for (uint32_t base = qs; base < qe; base += 32) {
+    const uint32_t i = base + c.lane;
+    if (i < qe) t_kill(c.qr, i);
+  }
+  __syncwarp();
+}
+
+// ---- items ---------------------------------------------------------------------
+
+__device__ void process(Ctx& c, uint32_t item) {
+  const Item it = c.pg->items[item];
+  switch (it.kind) {
+    case IT_CREATE: {
+      const BufDesc& bd = buf_of(c, it.arg);
+      const Bx dom = buffer_box(bd);
+      if (bd.init) {
+        if (c.n_alloc >= c.nd->cap_alloc) {
+          fail(c, ST_CAPACITY);
+          return;
+        }
+        const uint32_t aid = c.n_alloc;
+        if (c.lane == 0) {
+          AllocRec rec;
+          rec.buffer = it.arg;
+          rec.mem = 0;
+          rec.live = 1;
+          rec.user = 1;
+          for (int d = 0; d < 3; ++d) {
+            rec.lo[d] = dom.lo[d];
+            rec.hi[d] = dom.hi[d];
+          }
+          rec.mark = NONE;
+          rec.pad = 0;
+          c.nd->allocs[aid] = rec;
+        }
+        c.n_alloc += 1;
+        __syncwarp();
+        const uint32_t s = t_claim(c, c.wr, c.lane == 0);
+        if (c.err) return;
+        if (c.lane == 0) t_put(c.wr, s, aid, dom, c.epoch, 0, 0);
+        const uint32_t s2 = t_claim(c, c.bst, c.lane == 0);
+        if (c.err) return;
+        if (c.lane == 0) t_put(c.bst, s2, it.arg, dom, c.epoch, 0, 1u);
+      } else {
+        const uint32_t s2 = t_claim(c, c.bst, c.lane == 0);
+        if (c.err) return;
+        if (c.lane == 0) t_put(c.bst, s2, it.arg, dom, NONE, 0, 0);
+      }
+      __syncwarp();
+      break;
+    }
+    case IT_TASK:
+      compile_task(c, item);
+      break;
+    case IT_HORIZON:
+    case IT_EPOCH: {
+      Table& D = c.s[S_DEP];
+      D.n = 0;
+      for (uint32_t base = c.last_sync; base < c.n_instr; base += 32) {
+        const uint32_t i = base + c.lane;
+        const bool f = i < c.n_instr && !c.nd->has_succ[i];
+        const uint32_t s = t_claim(c, D, f);
+        if (c.err) return;
+        if (f) {
+          TP(D, F_V)[s] = i;
+          TP(D, F_V + 1)[s] = IGS_DEP_FRONT;
+        }
+      }
+      __syncwarp();
+      const uint32_t id = emit(c, it.kind == IT_EPOCH ? IGS_EPOCH : IGS_HORIZON, it.seq, NONE, NONE, NONE, NONE,
+                               nullptr, 0, 0, nullptr, 0, true);
+      if (c.err) return;
+      c.last_sync = id;
+      if (it.kind == IT_EPOCH) {
+        apply_epoch(c, id);
+        c.last_horizon = NONE;
+      } else {
+        if (c.last_horizon != NONE) apply_epoch(c, c.last_horizon);
+        c.last_horizon = id;
+      }
+      break;
+    }
+    case IT_DESTROY: {
+      const uint32_t b = it.arg;
+      for (uint32_t m = 0; m < 2 + c.D; ++m)
+        for (uint32_t aid = 0; aid < c.n_alloc; ++aid) {
+          const AllocRec a = c.nd->allocs[aid];
+          if (!a.live || a.buffer != b || a.mem != m) continue;
+          if (!a.user) {
+            emit_free(c, it.seq, aid);
+            if (c.err) return;
+          } else {
+            for (uint32_t base = 0; base < c.wr.n; base += 32) {
+              const uint32_t i = base + c.lane;
+              if (i < c.wr.n && t_key(c.wr, i) == aid) t_kill(c.wr, i);
+            }
+            for (uint32_t base = 0; base < c.rd.n; base += 32) {
+              const uint32_t i = base + c.lane;
+              if (i < c.rd.n && t_key(c.rd, i) == aid) t_kill(c.rd, i);
+            }
+            if (c.lane == 0) c.nd->allocs[aid].live = 0;
+            __syncwarp();
+          }
+        }
+      for (uint32_t base = 0; base < c.bst.n; base += 32) {
+        const uint32_t i = base + c.lane;
+        if (i < c.bst.n && t_key(c.bst, i) == b) t_kill(c.bst, i);
+      }
+      __syncwarp();
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+__device__ uint32_t queued_tasks(const Ctx& c) {
+  uint32_t k = 0;
+  for (uint32_t q = 0; q < c.q_count; ++q)
+    if (c.pg->items[c.nd->queue[(c.q_head + q) % c.nd->cap_queue]].kind == IT_TASK) ++k;
+  return k;
+}
+
+__device__ void flush_queue(Ctx& c) {
+  while (c.q_count > 0 && !c.err) {
+    const uint32_t item = c.nd->queue[c.q_head];
+    c.q_head = (c.q_head + 1) % c.nd->cap_queue;
+    c.q_count -= 1;
+    process(c, item);
+  }
+}
+
+__device__ void enqueue(Ctx& c, uint32_t item) {
+  if (c.q_count >= c.nd->cap_queue) {
+    fail(c, ST_CAPACITY);
+    return;
+  }
+  if (c.lane == 0) c.nd->queue[(c.q_head + c.q_count) % c.nd->cap_queue] = item;
+  c.q_count += 1;
+  __syncwarp();
+}
+
+__device__ void maintain(Ctx& c) {
+  Table* ts[5] = {&c.own, &c.bst, &c.wr, &c.rd, &c.qr};
+  for (int k = 0; k < 5; ++k)
+    if (ts[k]->n > ts[k]->cap / 4) t_compact(c, *ts[k]);
+}
+
+// Scheduler lookahead (Sec. 4.3): a task is queued while an allocating task
+// is queued; the queue is compiled when it holds more than `lookahead` tasks,
+// at an epoch, or when a buffer is destroyed.
+__device__ void deliver(Ctx& c, uint32_t item) {
+  const Item it = c.pg->items[item];
+  maintain(c);
+  if (c.err) return;
+  if (it.kind == IT_LOOKAHEAD) {
+    c.lookahead = it.arg;
+    if (c.q_count > 0 && queued_tasks(c) > c.lookahead) flush_queue(c);
+    return;
+  }
+  if (it.kind == IT_CREATE) {
+    const BufDesc& bd = buf_of(c, it.arg);
+    const uint32_t s = t_claim(c, c.own, c.lane == 0);
+    if (c.err) return;
+    if (c.lane == 0) t_put(c.own, s, it.arg, buffer_box(bd), bd.init ? HOST : NONE, 0xFFFFFFFFu, 0);
+    __syncwarp();
+  }
+  bool alloc_now = false;
+  if (it.kind == IT_TASK) {
+    const igs_task& t = c.pg->tasks[it.task];
+    Table& CH = c.s[S_CH];
+    Table& MP = c.s[S_MP];
+    task_chunks(c, t, CH);
+    task_mapped(c, t, CH, MP);
+    if (c.err) return;
+    if (overlapping_writes(c, t, CH, MP)) {
+      if (c.n_rej < c.nd->cap_rej) {
+        if (c.lane == 0) c.nd->rejected[c.n_rej] = it.seq;
+        c.n_rej += 1;
+        __syncwarp();
+      }
+      return;
+    }
+    a3_task(c, t, it.seq, CH, MP);
+    if (c.err) return;
+    if (c.q_count == 0) alloc_now = allocating(c, t, it.seq, CH, MP);
+    if (c.err) return;
+  }
+  if (c.q_count == 0) {
+    if (alloc_now) {
+      enqueue(c, item);
+      if (queued_tasks(c) > c.lookahead) flush_queue(c);
+    } else {
+      process(c, item);
+    }
+  } else {
+    enqueue(c, item);
+    if (it.kind == IT_EPOCH || it.kind == IT_DESTROY || queued_tasks(c) > c.lookahead) flush_queue(c);
+  }
+  if (c.err) return;
+  if (it.kind == IT_DESTROY) {
+    for (uint32_t base = 0; base < c.own.n; base += 32) {
+      const uint32_t i = base + c.lane;
+      if (i < c.own.n && t_key(c.own, i) == it.arg) t_kill(c.own, i);
+    }
+    __syncwarp();
+  }
+}
+
+__device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg) {
+  c.nd = nd;
+  c.pg = pg;
+  c.lane = threadIdx.x & 31u;
+  c.err = nd->status;
+  c.node = nd->node;
+  c.N = nd->N;
+  c.D = nd->D;
+  c.epoch = nd->epoch;
+  c.last_horizon = nd->last_horizon;
+  c.last_sync = nd->last_sync;
+  c.next_msg = nd->next_msg;
+  c.n_alloc = nd->n_alloc;
+  c.n_instr = nd->n_instr;
+  c.n_edge = nd->n_edge;
+  c.n_box = nd->n_box;
+  c.n_bind = nd->n_bind;
+  c.n_diag = nd->n_diag;
+  c.n_rej = nd->n_rej;
+  c.lookahead = nd->lookahead;
+  c.q_head = nd->q_head;
+  c.q_count = nd->q_count;
+  c.own = nd->own;
+  c.bst = nd->bst;
+  c.wr = nd->wr;
+  c.rd = nd->rd;
+  c.qr = nd->qr;
+  c.own.n = nd->tab_n[0];
+  c.bst.n = nd->tab_n[1];
+  c.wr.n = nd->tab_n[2];
+  c.rd.n = nd->tab_n[3];
+  c.qr.n = nd->tab_n[4];
+  for (int k = 0; k < 14; ++k) c.s[k] = nd->s[k];
+  c.map_reads = 0;
+  c.map_writes = 0;
+}
+
+__device__ void store_ctx(Ctx& c, uint32_t cursor) {
+  __syncwarp();
+  if (c.lane != 0) return;
+  NodeDev* nd = c.nd;
+  nd->status = c.err;
+  nd->cursor = cursor;
+  nd->epoch = c.epoch;
+  nd->last_horizon = c.last_horizon;
+  nd->last_sync = c.last_sync;
+  nd->next_msg = c.next_msg;
+  nd->n_alloc = c.n_alloc;
+  nd->n_instr = c.n_instr;
+  nd->n_edge = c.n_edge;
+  nd->n_box = c.n_box;
+  nd->n_bind = c.n_bind;
+  nd->n_diag = c.n_diag;
+  nd->n_rej = c.n_rej;
+  nd->lookahead = c.lookahead;
+  nd->q_head = c.q_head;
+  nd->q_count = c.q_count;
+  nd->tab_n[0] = c.own.n;
+  nd->tab_n[1] = c.bst.n;
+  nd->tab_n[2] = c.wr.n;
+  nd->tab_n[3] = c.rd.n;
+  nd->tab_n[4] = c.qr.n;
+  nd->map_reads += c.map_reads;
+  nd->map_writes += c.map_writes;
+  nd->launches += 1;
+}
+
+// One warp per unit; each lowers the unit's pending items (at most max_items).
+__global__ void __launch_bounds__(128) lower_kernel(const Unit* units, uint32_t n_units, uint32_t max_items) {
+  const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= n_units) return;
+  const Unit u = units[w];
+  Ctx c;
+  load_ctx(c, u.node, u.prog);
+  uint32_t cursor = u.node->cursor;
+  const uint32_t avail = *u.prog->n_items;
+  uint32_t end = avail;
+  if (max_items != NONE && cursor + max_items < end) end = cursor + max_items;
+  while (cursor < end && c.err == ST_OK) {
+    deliver(c, cursor);
+    ++cursor;
+  }
+  store_ctx(c, cursor);
+}
+
+}  // namespace
+}  // namespace igs
+
+int igs_launch_lower(const igs::Unit* units_dev, uint32_t n_units, uint32_t max_items, void* stream) {
+  if (n_units == 0) return 0;
+  const uint32_t threads = 128, warps = threads / 32;
+  const uint32_t blocks = (n_units + warps - 1) / warps;
+  igs::lower_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(units_dev, n_units, max_items);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}

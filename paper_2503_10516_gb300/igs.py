@@ -1,0 +1,266 @@
+"""Python binding of libigs (include/igs.h): argument marshalling only.
+
+Every lowering step and every box copy runs in the library's CUDA kernels;
+this module converts Python / numpy arguments to the C structs and back. It
+raises if the compiled library is missing — there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libigs.so")
+
+IGS_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "OVERLAPPING_WRITE", -3: "CAPACITY", -4: "TRUNCATED", -5: "TIMEOUT",
+          -6: "CUDA", -7: "BUDGET", -8: "STATE"}
+MODE_PLAIN, MODE_BATCHED = 0, 1
+LOOKAHEAD_INFINITE = 0xFFFFFFFF
+
+EXPORTS = ("igs_create", "igs_destroy", "igs_create_buffer", "igs_destroy_buffer", "igs_submit_task",
+           "igs_set_lookahead", "igs_flush", "igs_sync", "igs_fetch_instructions", "igs_rejected_tasks",
+           "igs_execute", "igs_read_buffer", "igs_lower_batch", "igs_counters", "igs_last_error", "igs_box_copy")
+
+
+class IgsError(RuntimeError):
+    def __init__(self, code: int, msg: str = ""):
+        super().__init__(f"igs error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("num_nodes", ctypes.c_uint32), ("devices_per_node", ctypes.c_uint32),
+                ("horizon_step", ctypes.c_uint32), ("lookahead", ctypes.c_uint32), ("mode", ctypes.c_uint32),
+                ("max_instructions", ctypes.c_uint32), ("max_edges", ctypes.c_uint32),
+                ("max_boxes", ctypes.c_uint32), ("map_capacity", ctypes.c_uint32),
+                ("scratch_capacity", ctypes.c_uint32), ("device", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class GraphView(ctypes.Structure):
+    _fields_ = [("node", ctypes.c_uint32),
+                ("instrs", ctypes.c_void_p), ("instr_cap", ctypes.c_uint32), ("num_instrs", ctypes.c_uint32),
+                ("edges", ctypes.c_void_p), ("edge_cap", ctypes.c_uint32), ("num_edges", ctypes.c_uint32),
+                ("boxes", ctypes.c_void_p), ("box_cap", ctypes.c_uint32), ("num_boxes", ctypes.c_uint32),
+                ("binds", ctypes.c_void_p), ("bind_cap", ctypes.c_uint32), ("num_binds", ctypes.c_uint32),
+                ("diags", ctypes.c_void_p), ("diag_cap", ctypes.c_uint32), ("num_diags", ctypes.c_uint32)]
+
+
+class Box(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_uint32 * 3), ("hi", ctypes.c_uint32 * 3)]
+
+
+class CopyJob(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("src_box", Box), ("dst_box", Box),
+                ("box", Box), ("elem_size", ctypes.c_uint32)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libigs.so; raises if it has not been built (no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libigs.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, u32, P32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)
+        L.igs_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(vp)]
+        L.igs_destroy.argtypes = [vp]
+        L.igs_destroy.restype = None
+        L.igs_create_buffer.argtypes = [vp, u32, P32, u32, vp, P32]
+        L.igs_destroy_buffer.argtypes = [vp, u32]
+        L.igs_submit_task.argtypes = [vp, P32, ctypes.POINTER(ctypes.c_uint64)]
+        L.igs_set_lookahead.argtypes = [vp, u32]
+        L.igs_flush.argtypes = [vp]
+        L.igs_sync.argtypes = [vp]
+        L.igs_fetch_instructions.argtypes = [vp, ctypes.POINTER(GraphView)]
+        L.igs_rejected_tasks.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), u32, P32]
+        L.igs_execute.argtypes = [vp, u32]
+        L.igs_read_buffer.argtypes = [vp, u32, P32, P32, vp]
+        L.igs_lower_batch.argtypes = [ctypes.POINTER(vp), u32]
+        L.igs_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.igs_last_error.argtypes = [vp]
+        L.igs_last_error.restype = ctypes.c_char_p
+        L.igs_box_copy.argtypes = [ctypes.POINTER(CopyJob), u32, vp]
+        _lib = L
+    return _lib
+
+
+def _p32(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+
+
+class Context:
+    """One lowering context (virtual nodes x devices) on one GPU."""
+
+    def __init__(self, nodes: int, devices: int, horizon_step: int = 4, lookahead: int = 0,
+                 mode: int = MODE_PLAIN, device: int = 0, stream: Optional[int] = None,
+                 max_instructions: int = 0, map_capacity: int = 0, scratch_capacity: int = 0):
+        self.nodes = nodes
+        cfg = Config(nodes, devices, horizon_step, lookahead, mode, max_instructions, 0, 0, map_capacity,
+                     scratch_capacity, device, stream)
+        h = ctypes.c_void_p()
+        r = lib().igs_create(ctypes.byref(cfg), ctypes.byref(h))
+        if r != IGS_OK:
+            raise IgsError(r, "igs_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _check(self, r: int, what: str):
+        if r != IGS_OK:
+            raise IgsError(r, f"{what}: {lib().igs_last_error(self._h).decode()}")
+        return r
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().igs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def create_buffer(self, dims: int, extent: Sequence[int], elem_size: int, init: Optional[np.ndarray]) -> int:
+        ext = np.ones(3, dtype=np.uint32)
+        ext[:len(extent)] = extent
+        out = np.zeros(1, dtype=np.uint32)
+        ptr = None
+        if init is not None:
+            init = np.ascontiguousarray(init)
+            ptr = init.ctypes.data_as(ctypes.c_void_p)
+        self._check(lib().igs_create_buffer(self._h, dims, _p32(ext), elem_size, ptr, _p32(out)), "create_buffer")
+        return int(out[0])
+
+    def destroy_buffer(self, b: int):
+        self._check(lib().igs_destroy_buffer(self._h, b), "destroy_buffer")
+
+    def submit(self, task: W.Task) -> int:
+        w = np.ascontiguousarray(task.flat(), dtype=np.uint32)
+        seq = ctypes.c_uint64()
+        self._check(lib().igs_submit_task(self._h, _p32(w), ctypes.byref(seq)), "submit_task")
+        return 0
+
+    def set_lookahead(self, L: int):
+        self._check(lib().igs_set_lookahead(self._h, L), "set_lookahead")
+
+    def flush(self, allow_rejected: bool = True) -> int:
+        r = lib().igs_flush(self._h)
+        if r == -2 and allow_rejected:
+            return r
+        return self._check(r, "flush")
+
+    def sync(self, allow_rejected: bool = True) -> int:
+        r = lib().igs_sync(self._h)
+        if r == -2 and allow_rejected:
+            return r
+        return self._check(r, "sync")
+
+    def graph(self, node: int) -> dict:
+        v = GraphView()
+        v.node = node
+        r = lib().igs_fetch_instructions(self._h, ctypes.byref(v))
+        if r not in (IGS_OK, -4):
+            self._check(r, "fetch_instructions")
+        out = {"instrs": np.zeros((v.num_instrs, 11), np.uint32), "edges": np.zeros((v.num_edges, 3), np.uint32),
+               "boxes": np.zeros((v.num_boxes, 6), np.uint32), "binds": np.zeros((v.num_binds, 7), np.uint32),
+               "diags": np.zeros((v.num_diags, 3), np.uint32)}
+        v.instrs, v.instr_cap = out["instrs"].ctypes.data, v.num_instrs
+        v.edges, v.edge_cap = out["edges"].ctypes.data, v.num_edges
+        v.boxes, v.box_cap = out["boxes"].ctypes.data, v.num_boxes
+        v.binds, v.bind_cap = out["binds"].ctypes.data, v.num_binds
+        v.diags, v.diag_cap = out["diags"].ctypes.data, v.num_diags
+        self._check(lib().igs_fetch_instructions(self._h, ctypes.byref(v)), "fetch_instructions")
+        return out
+
+    def rejected(self) -> list:
+        cnt = np.zeros(1, np.uint32)
+        buf = (ctypes.c_uint64 * 1024)()
+        self._check(lib().igs_rejected_tasks(self._h, buf, 1024, _p32(cnt)), "rejected_tasks")
+        return [int(buf[i]) for i in range(min(int(cnt[0]), 1024))]
+
+    def execute(self, sync: bool = True):
+        self._check(lib().igs_execute(self._h, 1 if sync else 0), "execute")
+
+    def read_buffer(self, b: int, lo, hi, elem_size: int) -> np.ndarray:
+        lo3 = np.zeros(3, np.uint32)
+        hi3 = np.ones(3, np.uint32)
+        lo3[:len(lo)] = lo
+        hi3[:len(hi)] = hi
+        shape = tuple(int(hi3[d] - lo3[d]) for d in range(3)) + (elem_size,)
+        out = np.zeros(shape, np.uint8)
+        self._check(lib().igs_read_buffer(self._h, b, _p32(lo3), _p32(hi3), out.ctypes.data_as(ctypes.c_void_p)),
+                    "read_buffer")
+        return out
+
+    def counters(self) -> dict:
+        c = (ctypes.c_uint64 * 8)()
+        self._check(lib().igs_counters(self._h, c), "counters")
+        return {"instructions": c[0], "edges": c[1], "boxes": c[2], "map_reads": c[3], "map_writes": c[4],
+                "launches": c[5]}
+
+
+def lower_batch(ctxs: Sequence[Context]):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.handle.value for c in ctxs])
+    r = lib().igs_lower_batch(arr, len(ctxs))
+    if r not in (IGS_OK, -2):
+        raise IgsError(r, "lower_batch")
+
+
+def box_copy(jobs: Sequence[tuple], stream: Optional[int] = None):
+    """jobs: (src_ptr, src_box, dst_ptr, dst_box, box, elem_size); boxes as 6-tuples (lo3 + hi3)."""
+    arr = (CopyJob * len(jobs))()
+    for i, (sp, sb, dp, db, bx, es) in enumerate(jobs):
+        arr[i].src, arr[i].dst, arr[i].elem_size = sp, dp, es
+        for name, b in (("src_box", sb), ("dst_box", db), ("box", bx)):
+            B = getattr(arr[i], name)
+            for d in range(3):
+                B.lo[d], B.hi[d] = b[d], b[3 + d]
+    r = lib().igs_box_copy(arr, len(jobs), stream)
+    if r != IGS_OK:
+        raise IgsError(r, "box_copy")
+
+
+class GpuImpl:
+    """Adapter with the same methods as the test harness implementations."""
+
+    def __init__(self, prog: W.Program, mode: int = MODE_PLAIN, **kw):
+        self.ctx = Context(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead, mode=mode, **kw)
+        self.nodes = prog.nodes
+        self.prog = prog
+        self._buffers = []
+
+    def create_buffer(self, dims, extent, elem, init):
+        b = self.prog.buffers[len(self._buffers)]
+        self._buffers.append(b)
+        return self.ctx.create_buffer(dims, extent, elem, b.init if init else None)
+
+    def submit(self, task):
+        self.ctx.submit(task)
+        return 0
+
+    def flush(self):
+        self.ctx.flush()
+
+    def destroy_buffer(self, b):
+        self.ctx.destroy_buffer(b)
+
+    def set_lookahead(self, L):
+        self.ctx.set_lookahead(L)
+
+    def graph(self, n):
+        return self.ctx.graph(n)
+
+    def rejected(self):
+        return self.ctx.rejected()

@@ -1,0 +1,347 @@
+"""Benchmark: instruction-graph lowering + execution of the 2D wave-stencil program.
+
+Workload (one step): the WaveSim-shaped program over three rotating
+8192 x 8192 fp32 buffers, 4 virtual nodes x 4 devices, 64 row chunks, 1000
+time steps, lookahead 8, horizon every 4 tasks. A step lowers the whole
+program on the GPU (batched: every node's warp lowers all 1000 tasks in one
+launch) and executes every emitted instruction (allocations, coherence and
+send/receive box copies, the stencil kernels).
+
+Prints one JSON line. --impl reference times the CPU oracle (test
+infrastructure) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2503_10516_gb300 import workloads as W  # noqa: E402
+
+METRIC = "instructions lowered/s"
+UNIT = "instructions/s"
+N, STEPS, NODES, DEVICES, CHUNKS, LOOKAHEAD, HSTEP = 8192, 1000, 4, 4, 64, 8, 4
+WORKLOAD = (f"wave2d: 3 x {N}x{N} fp32 buffers rotating, {NODES} nodes x {DEVICES} devices, {CHUNKS} row chunks, "
+            f"{STEPS} time steps, lookahead {LOOKAHEAD}, horizon every {HSTEP} tasks")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def __enter__(self):
+        def run():
+            q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap")
+            while not self._stop.is_set():
+                try:
+                    out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                         timeout=5).stdout.strip()
+                    if out:
+                        self.samples.append([x.strip() for x in out.split(",")])
+                except Exception:
+                    pass
+                self._stop.wait(0.2)
+        self._t = threading.Thread(target=run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if len(s) > 3 + k and "Active" in s[3 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def _program(with_data: bool = True):
+    return W.wave_program(n=N, steps=STEPS, nodes=NODES, devices=DEVICES, chunks=CHUNKS, lookahead=LOOKAHEAD,
+                          horizon_step=HSTEP) if with_data else None
+
+
+def _program_shape():
+    """The same program with tiny data arrays: lowering depends on shapes only."""
+    p = W.wave_program(n=8, steps=STEPS, nodes=NODES, devices=DEVICES, chunks=CHUNKS, lookahead=LOOKAHEAD,
+                       horizon_step=HSTEP)
+    for op in p.ops:
+        if op[0] == "buffer":
+            op[1].extent = (N, N, 1)
+        elif op[0] == "task":
+            op[1].range = (N, N, 1)
+    return p
+
+
+def _oracle_lower(prog) -> int:
+    """Lowers a program with the CPU oracle; returns the instruction count."""
+    import oracle
+    o = oracle.Oracle(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead)
+    for op in prog.ops:
+        if op[0] == "buffer":
+            b = op[1]
+            o.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init is not None)
+        elif op[0] == "task":
+            o.submit(op[1].flat())
+        elif op[0] == "flush":
+            o.flush()
+    n = sum(len(o.graph(k)["instrs"]) for k in range(prog.nodes))
+    o.close()
+    return n
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    prog = _program_shape()
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        _oracle_lower(prog)
+    t0 = time.perf_counter()
+    total = 0
+    for _ in range(args.steps):
+        total += _oracle_lower(prog)
+    dt = time.perf_counter() - t0
+    value = total / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "what": "CPU oracle lowering of the whole program, single thread"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"whole program lowering ({STEPS} tasks, all {NODES} nodes), no execution"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    from paper_2503_10516_gb300 import igs
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    prog = _program()
+    bufs = prog.buffers
+    tasks = prog.tasks
+
+    def make_ctx(pinned=None, timing=True):
+        c = igs.Context(NODES, DEVICES, HSTEP, LOOKAHEAD, mode=igs.MODE_BATCHED, device=local, stream=sh)
+        c.set_timing(timing)
+        for i, b in enumerate(bufs):
+            init = None
+            if b.init is not None:
+                init = pinned[i] if pinned is not None else b.init
+            c.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, init)
+        return c
+
+    def submit_all(c):
+        for t in tasks:
+            c.submit(t)
+
+    def step(c):
+        c.flush()
+        c.execute()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident throughput: inputs uploaded and tasks staged before timing
+    ctxs = []
+    for _ in range(args.warmup + args.steps):
+        c = make_ctx()
+        submit_all(c)
+        ctxs.append(c)
+    for i in range(args.warmup):
+        step(ctxs[i])
+        ctxs[i].close()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    barrier()
+    with clocks:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            step(ctxs[args.warmup + i])
+        barrier()
+        t1 = time.perf_counter()
+    dt = t1 - t0
+    instrs = int(ctxs[-1].counters()["instructions"])
+    stats = [ctxs[args.warmup + i].stats() for i in range(args.steps)]
+    counters = ctxs[-1].counters()
+    if dist is not None:
+        t = torch.tensor([dt], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    value = instrs * args.steps * world / dt
+    lower_ms = statistics.mean(s["lower_ms"] for s in stats)
+    copy_ms = statistics.mean(s["copy_ms"] for s in stats)
+    work_ms = statistics.mean(s["workload_ms"] for s in stats)
+    copy_bytes = statistics.mean(s["copy_bytes"] for s in stats)
+    launches = stats[0]["lower_launches"] + stats[0]["copy_launches"] + stats[0]["workload_launches"]
+    for c in ctxs[args.warmup:]:
+        c.close()
+    ctxs = []
+
+    # ---- per-task lowering latency, one task per launch (plain mode)
+    plain = igs.Context(NODES, DEVICES, HSTEP, LOOKAHEAD, mode=igs.MODE_PLAIN, device=local, stream=sh)
+    plain.set_timing(True)
+    for b in bufs:
+        plain.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init)
+    lat = []
+    for t in tasks:
+        plain.submit(t)
+        lat.append(plain.stats()["last_lower_ms"])
+    plain.flush()
+    plain_stats = plain.stats()
+    plain_instrs = int(plain.counters()["instructions"])
+    plain.close()
+    lat_sorted = sorted(lat)
+    p50 = lat_sorted[len(lat) // 2]
+    p99 = lat_sorted[min(len(lat) - 1, int(len(lat) * 0.99))]
+
+    # ---- end to end through the public API: pinned host inputs, graph read back
+    pinned, keep = [], []
+    for b in bufs:
+        if b.init is not None:
+            t = torch.from_numpy(np.ascontiguousarray(b.init)).pin_memory()
+            keep.append(t)
+            pinned.append(t.numpy())
+        else:
+            pinned.append(None)
+    h2d = sum(int(b.init.nbytes) for b in bufs if b.init is not None) + len(tasks) * 492
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        c = make_ctx(pinned=pinned, timing=False)
+        submit_all(c)
+        step(c)
+        d2h = 0
+        for n in range(NODES):
+            g = c.graph(n)
+            d2h += sum(int(v.nbytes) for v in g.values())
+        c.close()
+    barrier()
+    e2e_dt = time.perf_counter() - t0
+    e2e_value = instrs * e2e_steps * world / e2e_dt
+
+    # ---- roofline of the dominant kernel (algorithmic bytes / event-timed duration)
+    peaks, src = _peaks()
+    hbm = float(peaks["hbm_gbs"])
+    elems = N * N * STEPS
+    parts = {
+        "workload": (work_ms, elems * 12.0, "wave stencil workload kernel: 12 B/element (u_prev, u, u_next)"),
+        "box_copy": (copy_ms, copy_bytes, "box-copy kernel: bytes read + written"),
+        "lowering": (lower_ms, float(counters["map_reads"] + counters["map_writes"]) * 40.0
+                     + instrs * 44.0 + counters["edges"] * 12.0 + counters["boxes"] * 24.0,
+                     "lowering kernel: region-map entries read + written x 40 B + output records"),
+    }
+    dom = max(parts, key=lambda k: parts[k][0])
+    ms, byts, what = parts[dom]
+    achieved = byts / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "kernel": dom, "what": what, "peak_source": src}
+    hot = {}
+    for k, (ms_k, b_k, w_k) in parts.items():
+        a = b_k / (ms_k * 1e-3) / 1e9 if ms_k > 0 else 0.0
+        hot[k] = {"ms_per_step": ms_k, "bytes_per_step": b_k, "achieved_gbs": a, "frac": a / hbm}
+
+    # ---- CPU baseline: the oracle on a bounded sample of the same workload
+    cpu = None
+    if rank == 0 and world == 1:
+        shape = _program_shape()
+        sample_tasks = 300
+        shape.ops = [op for op in shape.ops if op[0] == "buffer"] + \
+            [op for op in shape.ops if op[0] == "task"][:sample_tasks] + [("flush",)]
+        t0 = time.perf_counter()
+        n_or = _oracle_lower(shape)
+        cdt = time.perf_counter() - t0
+        cpu = {"value": n_or / cdt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {sample_tasks} of {STEPS} tasks lowered on all {NODES} nodes ({n_or} instructions)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lowering": "batched (one launch lowers the whole program)",
+                       "step": "lower all tasks + execute all instructions (allocs, box copies, stencil kernels)",
+                       "l2": "inputs larger than L2 (3 x 256 MiB buffers)",
+                       "instructions_per_step": instrs, "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "gpu_launches": launches * args.steps,
+            "roofline": roof,
+            "hot_path": hot,
+            "lowering": {"batched_instr_per_s": instrs / (lower_ms * 1e-3) if lower_ms else None,
+                         "plain_instr_per_s": plain_instrs / (plain_stats["lower_ms"] * 1e-3),
+                         "plain_launches": plain_stats["lower_launches"],
+                         "p50_task_ms": p50, "p99_task_ms": p99,
+                         "batched_ms_per_task": lower_ms / STEPS},
+            "box_copy_gbs": (copy_bytes / (copy_ms * 1e-3) / 1e9) if copy_ms else None,
+            "clocks": clocks.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="igs", choices=["igs", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

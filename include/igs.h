@@ -224,6 +224,14 @@ int igs_lower_batch(igs_ctx* const* ctxs, uint32_t n);
  * nodes. */
 int igs_counters(igs_ctx* ctx, uint64_t out[8]);
 
+/* Device-time accounting (CUDA events on the context's stream around every
+ * lowering launch, box-copy wave and workload-kernel wave), off by default.
+ * igs_stats: [0] lowering ms, [1] box-copy ms, [2] workload ms, [3] box-copy
+ * bytes (read + written), [4] lowering launches, [5] box-copy launches,
+ * [6] workload launches, [7] per-launch lowering ms of the last launch. */
+int igs_set_timing(igs_ctx* ctx, int on);
+int igs_stats(igs_ctx* ctx, double out[8]);
+
 const char* igs_last_error(const igs_ctx* ctx);
 
 /* ---- box copies (Table 1 "copy"; a11) ------------------------------------ */

@@ -76,6 +76,15 @@ struct igs_ctx {
   KernelJob* d_kjobs = nullptr;
   uint32_t cap_kjobs = 0;
   uint64_t launches = 0;
+  // device-time accounting
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> ev_pending;  // (class, index into ev_pool)
+  double ms[3] = {0, 0, 0};
+  double last_lower_ms = 0;
+  uint64_t n_launch[3] = {0, 0, 0};
+  double copy_bytes = 0;
 };
 
 namespace {
@@ -133,16 +142,47 @@ int upload_prog(igs_ctx* c) {
   return IGS_OK;
 }
 
+// Event pair around one launch of class k (0 lowering, 1 box copy, 2 workload).
+size_t ev_begin(igs_ctx* c) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    c->ev_pool.push_back({a, b});
+  }
+  cudaEventRecord(c->ev_pool[c->ev_used].first, c->stream);
+  return c->ev_used++;
+}
+void ev_end(igs_ctx* c, int k, size_t i) {
+  cudaEventRecord(c->ev_pool[i].second, c->stream);
+  c->ev_pending.push_back({k, i});
+}
+// Folds completed event pairs into the totals (after a stream sync).
+void ev_collect(igs_ctx* c) {
+  for (auto& p : c->ev_pending) {
+    float t = 0;
+    cudaEventElapsedTime(&t, c->ev_pool[p.second].first, c->ev_pool[p.second].second);
+    c->ms[p.first] += t;
+    if (p.first == 0) c->last_lower_ms = t;
+  }
+  c->ev_pending.clear();
+  c->ev_used = 0;
+}
+
 int launch_lower(igs_ctx* c) {
   int r = upload_prog(c);
   if (r) return r;
+  const size_t ev = c->timing ? ev_begin(c) : 0;
   if (igs_launch_lower(c->d_units, c->N, IGS_NONE, c->stream)) return fail_ctx(c, IGS_ERR_CUDA, "lowering launch failed");
+  if (c->timing) ev_end(c, 0, ev);
   c->launches++;
+  c->n_launch[0]++;
   return IGS_OK;
 }
 
 int download_nodes(igs_ctx* c) {
   CK(cudaStreamSynchronize(c->stream));
+  ev_collect(c);
   CK(cudaMemcpy(c->nodes_host.data(), c->d_nodes, sizeof(NodeDev) * c->N, cudaMemcpyDeviceToHost));
   return IGS_OK;
 }
@@ -303,6 +343,10 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
 void igs_destroy(igs_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& e : c->ev_pool) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
   for (auto& n : c->nh)
     for (auto& a : n.allocs)
       if (a.second.live && !a.second.user && a.second.ptr) cudaFree(a.second.ptr);
@@ -323,6 +367,27 @@ void igs_destroy(igs_ctx* c) {
 }
 
 const char* igs_last_error(const igs_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int igs_set_timing(igs_ctx* c, int on) {
+  if (!c) return IGS_ERR_INVALID_ARG;
+  c->timing = on != 0;
+  return IGS_OK;
+}
+
+int igs_stats(igs_ctx* c, double out[8]) {
+  if (!c || !out) return IGS_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  ev_collect(c);
+  out[0] = c->ms[0];
+  out[1] = c->ms[1];
+  out[2] = c->ms[2];
+  out[3] = c->copy_bytes;
+  out[4] = (double)c->n_launch[0];
+  out[5] = (double)c->n_launch[1];
+  out[6] = (double)c->n_launch[2];
+  out[7] = c->last_lower_ms;
+  return IGS_OK;
+}
 
 int igs_create_buffer(igs_ctx* c, uint32_t dims, const uint32_t extent[3], uint32_t elem_size, const void* host_init,
                       uint32_t* out_buffer) {
@@ -616,15 +681,23 @@ int run_pending(igs_ctx* c, Pending& p) {
   }
   for (const Action& a : p.actions) {
     if (a.kind == 0) {
+      const size_t ev = c->timing ? ev_begin(c) : 0;
       if (igs_launch_copies(c->d_cjobs + a.first, a.count, a.units, c->stream)) return fail_ctx(c, IGS_ERR_CUDA, "box copy launch");
+      if (c->timing) ev_end(c, 1, ev);
+      c->n_launch[1]++;
     } else if (a.kind == 1) {
+      const size_t ev = c->timing ? ev_begin(c) : 0;
       if (igs_launch_workload(c->d_kjobs + a.first, a.count, a.units, c->stream)) return fail_ctx(c, IGS_ERR_CUDA, "workload launch");
+      if (c->timing) ev_end(c, 2, ev);
+      c->n_launch[2]++;
     } else {
       CK(cudaFreeAsync(a.ptr, c->stream));
     }
   }
+  for (const CopyJob& j : p.copies) c->copy_bytes += 2.0 * j.extent[0] * j.extent[1] * j.extent[2];
   // the job arrays are reused by the next call
   CK(cudaStreamSynchronize(c->stream));
+  ev_collect(c);
   if (igs_exec_error(true)) return fail_ctx(c, IGS_ERR_STATE, "a workload kernel accessed outside its allocation");
   p.copies.clear();
   p.kernels.clear();
@@ -904,6 +977,7 @@ bool isect(const uint32_t alo[3], const uint32_t ahi[3], const uint32_t blo[3], 
 
 extern "C" int igs_read_buffer(igs_ctx* c, uint32_t b, const uint32_t lo[3], const uint32_t hi[3], void* host_dst) {
   if (!c || b >= c->bufs.size() || !lo || !hi || !host_dst) return fail_ctx(c, IGS_ERR_INVALID_ARG, "bad read");
+  if (!c->buf_live[b]) return fail_ctx(c, IGS_ERR_INVALID_ARG, "buffer was destroyed");
   const BufDesc& bf = c->bufs[b];
   uint64_t cnt = bf.elem;
   uint32_t rl[3], rh[3];

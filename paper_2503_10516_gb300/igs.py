@@ -25,7 +25,8 @@ LOOKAHEAD_INFINITE = 0xFFFFFFFF
 
 EXPORTS = ("igs_create", "igs_destroy", "igs_create_buffer", "igs_destroy_buffer", "igs_submit_task",
            "igs_set_lookahead", "igs_flush", "igs_sync", "igs_fetch_instructions", "igs_rejected_tasks",
-           "igs_execute", "igs_read_buffer", "igs_lower_batch", "igs_counters", "igs_last_error", "igs_box_copy")
+           "igs_execute", "igs_read_buffer", "igs_lower_batch", "igs_counters", "igs_last_error", "igs_box_copy",
+           "igs_set_timing", "igs_stats")
 
 
 class IgsError(RuntimeError):
@@ -89,6 +90,8 @@ def lib():
         L.igs_last_error.argtypes = [vp]
         L.igs_last_error.restype = ctypes.c_char_p
         L.igs_box_copy.argtypes = [ctypes.POINTER(CopyJob), u32, vp]
+        L.igs_set_timing.argtypes = [vp, ctypes.c_int]
+        L.igs_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         _lib = L
     return _lib
 
@@ -209,6 +212,21 @@ class Context:
         self._check(lib().igs_counters(self._h, c), "counters")
         return {"instructions": c[0], "edges": c[1], "boxes": c[2], "map_reads": c[3], "map_writes": c[4],
                 "launches": c[5]}
+
+
+def _stats(self) -> dict:
+    c = (ctypes.c_double * 8)()
+    self._check(lib().igs_stats(self._h, c), "stats")
+    return {"lower_ms": c[0], "copy_ms": c[1], "workload_ms": c[2], "copy_bytes": c[3], "lower_launches": int(c[4]),
+            "copy_launches": int(c[5]), "workload_launches": int(c[6]), "last_lower_ms": c[7]}
+
+
+def _set_timing(self, on: bool = True):
+    self._check(lib().igs_set_timing(self._h, 1 if on else 0), "set_timing")
+
+
+Context.stats = _stats
+Context.set_timing = _set_timing
 
 
 def lower_batch(ctxs: Sequence[Context]):

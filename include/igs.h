@@ -232,6 +232,14 @@ int igs_counters(igs_ctx* ctx, uint64_t out[8]);
 int igs_set_timing(igs_ctx* ctx, int on);
 int igs_stats(igs_ctx* ctx, double out[8]);
 
+/* Lowering-engine clock cycles summed over nodes, by phase: [0] chunking and
+ * range mappers, [1] overlapping-write check, [2] push / await push,
+ * [3] allocating test, [4] allocations, [5] pushes and sends, [6] receives,
+ * [7] coherence copies, [8] kernels, [9] remote-write bookkeeping,
+ * [10] horizon / epoch emission, [11] horizon / epoch compaction, [12] total
+ * inside the lowering kernel. */
+int igs_profile(igs_ctx* ctx, uint64_t out[16]);
+
 const char* igs_last_error(const igs_ctx* ctx);
 
 /* ---- box copies (Table 1 "copy"; a11) ------------------------------------ */

@@ -230,9 +230,10 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
   const uint32_t cap_edge = cfg->max_edges ? cfg->max_edges : 4 * cap_instr;
   const uint32_t cap_box = cfg->max_boxes ? cfg->max_boxes : 4 * cap_instr;
   const uint32_t cap_bind = 2 * cap_instr;
-  const uint32_t cap_map = cfg->map_capacity ? cfg->map_capacity : 16384;
-  const uint32_t cap_scr = cfg->scratch_capacity ? cfg->scratch_capacity : 8192;
-  const uint32_t cap_alloc = 8192, cap_queue = 1u << 16, cap_diag = 1u << 16, cap_rej = 1024;
+  const uint32_t cap_bmap = cfg->map_capacity ? cfg->map_capacity : 4096;
+  const uint32_t cap_scr = cfg->scratch_capacity ? cfg->scratch_capacity : 4096;
+  const uint32_t cap_buffers = 64, cap_slots = 1024, cap_amap = 256, cap_qr = 16384;
+  const uint32_t cap_alloc = 1u << 16, cap_queue = 1u << 16, cap_diag = 1u << 16, cap_rej = 1024;
   cudaError_t e = cudaSetDevice(cfg->device);
   if (e != cudaSuccess) {
     delete c;
@@ -254,7 +255,17 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
     per += (bytes + 255) & ~(size_t)255;
     return off;
   };
-  const size_t o_tab = take(table_bytes(cap_map) * 5);
+  const size_t o_own = take(table_bytes(cap_bmap) * cap_buffers);
+  const size_t o_bst = take(table_bytes(cap_bmap) * cap_buffers);
+  const size_t o_ownn = take(sizeof(uint32_t) * cap_buffers);
+  const size_t o_bstn = take(sizeof(uint32_t) * cap_buffers);
+  const size_t o_wr = take(table_bytes(cap_amap) * cap_slots);
+  const size_t o_rd = take(table_bytes(cap_amap) * cap_slots);
+  const size_t o_wrn = take(sizeof(uint32_t) * cap_slots);
+  const size_t o_rdn = take(sizeof(uint32_t) * cap_slots);
+  const size_t o_free = take(sizeof(uint32_t) * cap_slots);
+  const size_t o_live = take(sizeof(uint32_t) * cap_slots);
+  const size_t o_qr = take(table_bytes(cap_qr));
   const size_t o_alloc = take(sizeof(AllocRec) * cap_alloc);
   const size_t o_queue = take(sizeof(uint32_t) * cap_queue);
   const size_t o_succ = take(cap_instr);
@@ -273,6 +284,8 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
   }
   c->nodes_host.resize(c->N);
   std::vector<Unit> units(c->N);
+  std::vector<uint32_t> slots(cap_slots);
+  for (uint32_t i = 0; i < cap_slots; ++i) slots[i] = cap_slots - 1 - i;  // pops 0, 1, 2, ...
   for (uint32_t n = 0; n < c->N; ++n) {
     uint8_t* base = static_cast<uint8_t*>(c->d_arena) + per * n;
     NodeDev nd;
@@ -287,6 +300,7 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
     nd.last_horizon = NONE;
     nd.last_sync = 0;
     nd.n_instr = 1;
+    nd.n_free = cap_slots;
     nd.cap_instr = cap_instr;
     nd.cap_edge = cap_edge;
     nd.cap_box = cap_box;
@@ -295,14 +309,23 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
     nd.cap_rej = cap_rej;
     nd.cap_alloc = cap_alloc;
     nd.cap_queue = cap_queue;
-    nd.cap_map = cap_map;
+    nd.cap_buffers = cap_buffers;
+    nd.cap_bmap = cap_bmap;
+    nd.cap_slots = cap_slots;
+    nd.cap_amap = cap_amap;
+    nd.cap_qr = cap_qr;
     nd.cap_scratch = cap_scr;
-    Table* tabs[5] = {&nd.own, &nd.bst, &nd.wr, &nd.rd, &nd.qr};
-    for (int k = 0; k < 5; ++k) {
-      tabs[k]->base = reinterpret_cast<uint32_t*>(base + o_tab + table_bytes(cap_map) * k);
-      tabs[k]->n = 0;
-      tabs[k]->cap = cap_map;
-    }
+    nd.own_base = reinterpret_cast<uint32_t*>(base + o_own);
+    nd.bst_base = reinterpret_cast<uint32_t*>(base + o_bst);
+    nd.own_n = reinterpret_cast<uint32_t*>(base + o_ownn);
+    nd.bst_n = reinterpret_cast<uint32_t*>(base + o_bstn);
+    nd.wr_base = reinterpret_cast<uint32_t*>(base + o_wr);
+    nd.rd_base = reinterpret_cast<uint32_t*>(base + o_rd);
+    nd.wr_n = reinterpret_cast<uint32_t*>(base + o_wrn);
+    nd.rd_n = reinterpret_cast<uint32_t*>(base + o_rdn);
+    nd.free_slots = reinterpret_cast<uint32_t*>(base + o_free);
+    nd.live = reinterpret_cast<uint32_t*>(base + o_live);
+    nd.qr_base = reinterpret_cast<uint32_t*>(base + o_qr);
     nd.allocs = reinterpret_cast<AllocRec*>(base + o_alloc);
     nd.queue = reinterpret_cast<uint32_t*>(base + o_queue);
     nd.has_succ = base + o_succ;
@@ -312,18 +335,17 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
     nd.binds = reinterpret_cast<igs_binding*>(base + o_bind);
     nd.diags = reinterpret_cast<igs_diag*>(base + o_diag);
     nd.rejected = reinterpret_cast<uint32_t*>(base + o_rej);
-    for (int k = 0; k < 14; ++k) {
-      nd.s[k].base = reinterpret_cast<uint32_t*>(base + o_scr + table_bytes(cap_scr) * k);
-      nd.s[k].n = 0;
-      nd.s[k].cap = cap_scr;
-    }
+    nd.scratch_base = reinterpret_cast<uint32_t*>(base + o_scr);
     c->nodes_host[n] = nd;
     units[n].node = c->d_nodes + n;
     units[n].prog = c->d_prog;
-    // initial epoch I0
+    // initial epoch I0, empty tables, the slab free list
     igs_instruction i0{0, IGS_EPOCH, NONE, NONE, NONE, NONE, NONE, 0, 0, 0, 0};
     if (cudaMemcpy(nd.instrs, &i0, sizeof i0, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(nd.has_succ, 0, 1) != cudaSuccess) {
+        cudaMemset(nd.has_succ, 0, 1) != cudaSuccess ||
+        cudaMemset(nd.own_n, 0, sizeof(uint32_t) * cap_buffers) != cudaSuccess ||
+        cudaMemset(nd.bst_n, 0, sizeof(uint32_t) * cap_buffers) != cudaSuccess ||
+        cudaMemcpy(nd.free_slots, slots.data(), sizeof(uint32_t) * cap_slots, cudaMemcpyHostToDevice) != cudaSuccess) {
       igs_destroy(c);
       return IGS_ERR_CUDA;
     }
@@ -368,6 +390,16 @@ void igs_destroy(igs_ctx* c) {
 
 const char* igs_last_error(const igs_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
+int igs_profile(igs_ctx* c, uint64_t out[16]) {
+  if (!c || !out) return IGS_ERR_INVALID_ARG;
+  int r = download_nodes(c);
+  if (r) return r;
+  std::memset(out, 0, sizeof(uint64_t) * 16);
+  for (const NodeDev& nd : c->nodes_host)
+    for (int k = 0; k < 16; ++k) out[k] += nd.prof[k];
+  return IGS_OK;
+}
+
 int igs_set_timing(igs_ctx* c, int on) {
   if (!c) return IGS_ERR_INVALID_ARG;
   c->timing = on != 0;
@@ -403,6 +435,8 @@ int igs_create_buffer(igs_ctx* c, uint32_t dims, const uint32_t extent[3], uint3
   }
   b.elem = elem_size;
   b.init = host_init ? 1 : 0;
+  if (c->bufs.size() >= c->nodes_host[0].cap_buffers)
+    return fail_ctx(c, IGS_ERR_CAPACITY, "too many buffers for this context");
   uint8_t* dev = nullptr;
   if (host_init) {
     CK(cudaMalloc(&dev, count * elem_size));
@@ -809,6 +843,7 @@ extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
           const bool dep = depends_on_wave(c, h, i);
           switch (in.type) {
             case IGS_ALLOC: {
+              h.wave[i] = dep ? c->wave_id : 0;
               const igs_box& b = h.boxes[in.box_off];
               ExecAlloc a;
               a.buffer = in.c;
@@ -881,6 +916,11 @@ extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
             case IGS_AWAIT_RECEIVE:
               h.wave[i] = h.wave[in.b];
               break;
+            case IGS_HORIZON:
+            case IGS_EPOCH:
+              // no work of its own, but ordered after everything it waits for
+              h.wave[i] = dep ? c->wave_id : 0;
+              break;
             case IGS_KERNEL: {
               if (dep) close_wave(c, p);
               if (in.seq >= c->seq_task.size() || c->seq_task[in.seq] == NONE)
@@ -945,20 +985,23 @@ struct HEntry {
   uint32_t key, lo[3], hi[3], v[3];
 };
 
-int read_table(igs_ctx* c, const Table& t, uint32_t n, std::vector<HEntry>& out) {
-  std::vector<uint32_t> raw((size_t)F_COUNT * t.cap);
+// Reads slab `idx` (cap entries per slab) with its count from the device.
+int read_slab(igs_ctx* c, const uint32_t* base, const uint32_t* counts, uint32_t idx, uint32_t cap, std::vector<HEntry>& out) {
   out.clear();
+  uint32_t n = 0;
+  CK(cudaMemcpy(&n, counts + idx, sizeof n, cudaMemcpyDeviceToHost));
   if (n == 0) return IGS_OK;
-  for (int f = 0; f < F_COUNT; ++f)
-    CK(cudaMemcpy(raw.data() + (size_t)f * t.cap, t.base + (size_t)f * t.cap, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+  std::vector<uint32_t> raw((size_t)F_COUNT * cap);
+  const uint32_t* t = base + (size_t)idx * cap * F_COUNT;
+  CK(cudaMemcpy(raw.data(), t, sizeof(uint32_t) * F_COUNT * cap, cudaMemcpyDeviceToHost));
   for (uint32_t i = 0; i < n; ++i) {
     HEntry e;
     e.key = raw[i];
     for (int d = 0; d < 3; ++d) {
-      e.lo[d] = raw[(size_t)(F_LO + d) * t.cap + i];
-      e.hi[d] = raw[(size_t)(F_HI + d) * t.cap + i];
+      e.lo[d] = raw[(size_t)(F_LO + d) * cap + i];
+      e.hi[d] = raw[(size_t)(F_HI + d) * cap + i];
     }
-    for (int k = 0; k < 3; ++k) e.v[k] = raw[(size_t)(F_V + k) * t.cap + i];
+    for (int k = 0; k < 3; ++k) e.v[k] = raw[(size_t)(F_V + k) * cap + i];
     if (e.key != DEAD) out.push_back(e);
   }
   return IGS_OK;
@@ -993,11 +1036,13 @@ extern "C" int igs_read_buffer(igs_ctx* c, uint32_t b, const uint32_t lo[3], con
   CK(cudaMalloc(&stage, cnt));
   CK(cudaMemsetAsync(stage, 0, cnt, c->stream));
   std::vector<HEntry> own, bst;
-  r = read_table(c, c->nodes_host[0].own, c->nodes_host[0].tab_n[0], own);
-  if (r) return r;
+  {
+    const NodeDev& n0 = c->nodes_host[0];
+    r = read_slab(c, n0.own_base, n0.own_n, b, n0.cap_bmap, own);
+    if (r) return r;
+  }
   Pending p;
   for (const HEntry& e : own) {
-    if (e.key != b) continue;
     igs_box piece;
     if (!isect(e.lo, e.hi, rl, rh, piece)) continue;
     if (e.v[0] == HOST) {
@@ -1008,10 +1053,12 @@ extern "C" int igs_read_buffer(igs_ctx* c, uint32_t b, const uint32_t lo[3], con
     }
     if (e.v[0] >= c->N) continue;  // never written
     const uint32_t o = e.v[0];
-    r = read_table(c, c->nodes_host[o].bst, c->nodes_host[o].tab_n[1], bst);
-    if (r) return r;
+    {
+      const NodeDev& no = c->nodes_host[o];
+      r = read_slab(c, no.bst_base, no.bst_n, b, no.cap_bmap, bst);
+      if (r) return r;
+    }
     for (const HEntry& f : bst) {
-      if (f.key != b) continue;
       igs_box q;
       if (!isect(f.lo, f.hi, piece.lo, piece.hi, q)) continue;
       const uint32_t pmem = f.v[1];

@@ -32,13 +32,14 @@ enum TableField : int { F_KEY = 0, F_LO = 1, F_HI = 4, F_V = 7, F_COUNT = 10 };
 struct Table {
   uint32_t* base;  // F_COUNT * cap words
   uint32_t n, cap;
+  uint32_t* np;    // persistent count of a slab table (nullptr for scratch tables)
 };
 
 struct AllocRec {
   uint32_t buffer, mem, live, user;
   uint32_t lo[3], hi[3];
   uint32_t mark;  // scratch: cluster index during allocation planning
-  uint32_t pad;
+  uint32_t slot;  // slab of its writer / reader tables
 };
 
 // Persistent device state of one virtual node's lowering (one warp owns it).
@@ -48,15 +49,26 @@ struct NodeDev {
   // scalars (owned by the warp; written back after every item)
   uint32_t status, cursor, lookahead, epoch, last_horizon, last_sync, next_msg, n_alloc;
   uint32_t n_instr, n_edge, n_box, n_bind, n_diag, n_rej;
-  uint32_t q_head, q_count;
-  uint32_t tab_n[6];  // counts of the persistent tables (own, bst, wr, rd, qr, spare)
+  uint32_t q_head, q_count, qr_n, n_free, n_live, pad0;
   uint64_t map_reads, map_writes, launches;
+  uint64_t prof[16];   // clock cycles per lowering phase (see the engine)
   // capacities
   uint32_t cap_instr, cap_edge, cap_box, cap_bind, cap_diag, cap_rej, cap_alloc, cap_queue;
-  uint32_t cap_map, cap_scratch;
-  // persistent tables: node-level ownership, buffer state, per-allocation
-  // writers / readers, per-task push and await regions
-  Table own, bst, wr, rd, qr;
+  uint32_t cap_buffers, cap_bmap, cap_slots, cap_amap, cap_qr, cap_scratch;
+  // per-buffer slab tables: node-level ownership, local buffer state
+  uint32_t* own_base;  // cap_buffers slabs of cap_bmap entries
+  uint32_t* own_n;
+  uint32_t* bst_base;
+  uint32_t* bst_n;
+  // per-allocation slab tables: last writers, readers since the last write
+  uint32_t* wr_base;   // cap_slots slabs of cap_amap entries
+  uint32_t* wr_n;
+  uint32_t* rd_base;
+  uint32_t* rd_n;
+  uint32_t* free_slots;
+  uint32_t* live;      // ids of live allocations, ascending
+  // per-task push and await regions (key = task sequence number)
+  uint32_t* qr_base;
   AllocRec* allocs;
   uint32_t* queue;     // item indices (ring of cap_queue)
   uint8_t* has_succ;   // per instruction: has a successor
@@ -68,7 +80,7 @@ struct NodeDev {
   igs_diag* diags;
   uint32_t* rejected;
   // scratch tables for the warp
-  Table s[14];
+  uint32_t* scratch_base;  // 14 tables of cap_scratch entries
 };
 
 // Program-level inputs shared by all node warps of one context.

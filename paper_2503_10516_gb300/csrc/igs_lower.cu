@@ -85,10 +85,6 @@ __device__ __forceinline__ bool bx_less(const Bx& a, const Bx& b) {
     if (a.hi[d] != b.hi[d]) return a.hi[d] < b.hi[d];
   return false;
 }
-__device__ __forceinline__ bool bx_eq(const Bx& a, const Bx& b) {
-  return a.lo[0] == b.lo[0] && a.lo[1] == b.lo[1] && a.lo[2] == b.lo[2] && a.hi[0] == b.hi[0] &&
-         a.hi[1] == b.hi[1] && a.hi[2] == b.hi[2];
-}
 __device__ __forceinline__ uint64_t bx_volume(const Bx& b) {
   if (bx_empty(b)) return 0;
   return (uint64_t)(b.hi[0] - b.lo[0]) * (b.hi[1] - b.lo[1]) * (b.hi[2] - b.lo[2]);
@@ -169,16 +165,30 @@ struct Ctx {
   const ProgDev* pg;
   uint32_t lane, err;
   uint32_t node, N, D;
-  uint32_t epoch, last_horizon, last_sync, next_msg, n_alloc;
+  uint32_t epoch, last_horizon, last_sync, next_msg, n_alloc, n_free, n_live;
   uint32_t n_instr, n_edge, n_box, n_bind, n_diag, n_rej;
   uint32_t lookahead, q_head, q_count;
-  Table own, bst, wr, rd, qr;
+  Table qr;
   Table s[14];
   uint64_t map_reads, map_writes;
 };
 
 __device__ __forceinline__ void fail(Ctx& c, uint32_t code) {
   if (c.err == ST_OK) c.err = code;
+}
+
+// Phase cycle accounting (lane 0 adds to the node's counters).
+enum Phase : int {
+  PH_SPLIT = 0, PH_OVERLAP = 1, PH_A3 = 2, PH_ALLOCATING = 3, PH_P1 = 4, PH_P2 = 5, PH_P3 = 6, PH_P4 = 7,
+  PH_P5 = 8, PH_REMOTE = 9, PH_SYNC = 10, PH_APPLY = 11, PH_TOTAL = 12
+};
+struct PhaseTimer {
+  long long t0;
+};
+__device__ __forceinline__ PhaseTimer pt_start() {
+  PhaseTimer p;
+  p.t0 = clock64();
+  return p;
 }
 
 // Claims one slot per predicated lane (all lanes call). NONE on overflow.
@@ -192,6 +202,7 @@ __device__ __forceinline__ uint32_t t_claim(Ctx& c, Table& t, bool pred) {
   }
   t.n = nn;
   c.map_writes += __popc(m);
+  if (t.np && c.lane == 0) *t.np = nn;
   return pred ? slot : NONE;
 }
 // Claims k consecutive slots per lane; returns this lane's first slot.
@@ -210,6 +221,7 @@ __device__ __forceinline__ uint32_t t_claim_n(Ctx& c, Table& t, uint32_t k) {
   }
   t.n += total;
   c.map_writes += total;
+  if (t.np && c.lane == 0) *t.np = t.n;
   return first;
 }
 
@@ -259,6 +271,12 @@ __device__ __forceinline__ Bx warp_bbox(Bx b, bool valid) {
 }
 
 // Stable in-place removal of dead entries.
+__device__ void pt_lap(PhaseTimer& p, Ctx& c, int ph) {
+  const long long t1 = clock64();
+  if (c.lane == 0) c.nd->prof[ph] += (uint64_t)(t1 - p.t0);
+  p.t0 = t1;
+}
+
 __device__ void t_compact(Ctx& c, Table& t) {
   uint32_t w = 0;
   for (uint32_t base = 0; base < t.n; base += 32) {
@@ -281,6 +299,13 @@ __device__ void t_compact(Ctx& c, Table& t) {
     __syncwarp();
   }
   t.n = w;
+  if (t.np && c.lane == 0) *t.np = w;
+  __syncwarp();
+}
+
+// Compacts a persistent slab table once more than half of it is used.
+__device__ __forceinline__ void t_tidy(Ctx& c, Table& t) {
+  if (t.np && t.n > t.cap / 2) t_compact(c, t);
 }
 
 __device__ Bx t_bbox(const Ctx& c, const Table& t, uint32_t from, uint32_t to) {
@@ -331,6 +356,7 @@ __device__ void t_query(Ctx& c, const Table& src, uint32_t key, const Bx& q, Tab
 // Removes box r from every entry of `key` (NONE = any) that matches the
 // optional value filter; the remainders keep their values.
 __device__ void t_subtract(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t vfilter = NONE) {
+  t_tidy(c, t);
   const uint32_t n0 = t.n;
   for (uint32_t base = 0; base < n0; base += 32) {
     const uint32_t i = base + c.lane;
@@ -364,13 +390,14 @@ __device__ void t_subtract(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t
 
 // value[vidx] |= bits on box r for entries of `key`.
 __device__ void t_or(Ctx& c, Table& t, uint32_t key, const Bx& r, int vidx, uint32_t bits) {
+  t_tidy(c, t);
   const uint32_t n0 = t.n;
   for (uint32_t base = 0; base < n0; base += 32) {
     const uint32_t i = base + c.lane;
     bool hit = false;
     uint32_t v[3] = {0, 0, 0};
     Bx e{};
-    if (i < n0 && t_key(t, i) == key) {
+    if (i < n0 && t_key(t, i) != DEAD && (key == NONE || t_key(t, i) == key)) {
       e = t_box(t, i);
       v[0] = t_v(t, 0, i);
       v[1] = t_v(t, 1, i);
@@ -383,10 +410,11 @@ __device__ void t_or(Ctx& c, Table& t, uint32_t key, const Bx& r, int vidx, uint
     const uint32_t first = t_claim_n(c, t, hit ? (uint32_t)np + 1 : 0u);
     if (c.err) return;
     if (hit) {
+      const uint32_t k = t_key(t, i);
       t_kill(t, i);
-      for (int j = 0; j < np; ++j) t_put(t, first + j, key, pc[j], v[0], v[1], v[2]);
+      for (int j = 0; j < np; ++j) t_put(t, first + j, k, pc[j], v[0], v[1], v[2]);
       v[vidx] |= bits;
-      t_put(t, first + np, key, bx_isect(e, r), v[0], v[1], v[2]);
+      t_put(t, first + np, k, bx_isect(e, r), v[0], v[1], v[2]);
     }
   }
   __syncwarp();
@@ -397,7 +425,7 @@ __device__ void t_set(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t v0, 
   t_subtract(c, t, key, r);
   const uint32_t s = t_claim(c, t, c.lane == 0);
   if (c.err) return;
-  if (c.lane == 0) t_put(t, s, key, r, v0, v1, v2);
+  if (c.lane == 0) t_put(t, s, key == NONE ? 0u : key, r, v0, v1, v2);
   __syncwarp();
 }
 
@@ -587,6 +615,78 @@ __device__ uint32_t canonical(Ctx& c, const Table& in, uint32_t from, uint32_t t
 
 // ---- node state helpers ----------------------------------------------------
 
+__device__ __forceinline__ Table slab(uint32_t* base, uint32_t* ns, uint32_t idx, uint32_t cap) {
+  __syncwarp();
+  Table t;
+  t.base = base + (size_t)idx * cap * F_COUNT;
+  t.n = ns[idx];
+  t.cap = cap;
+  t.np = ns + idx;
+  return t;
+}
+// Node-level ownership map of a buffer (owner node, replication mask).
+__device__ __forceinline__ Table own_t(const Ctx& c, uint32_t b) {
+  return slab(c.nd->own_base, c.nd->own_n, b, c.nd->cap_bmap);
+}
+// Local state of a buffer (original producer, its memory, up-to-date memories).
+__device__ __forceinline__ Table bst_t(const Ctx& c, uint32_t b) {
+  return slab(c.nd->bst_base, c.nd->bst_n, b, c.nd->cap_bmap);
+}
+// Last writers / readers since the last write of an allocation.
+__device__ __forceinline__ Table wr_t(const Ctx& c, uint32_t aid) {
+  return slab(c.nd->wr_base, c.nd->wr_n, c.nd->allocs[aid].slot, c.nd->cap_amap);
+}
+__device__ __forceinline__ Table rd_t(const Ctx& c, uint32_t aid) {
+  return slab(c.nd->rd_base, c.nd->rd_n, c.nd->allocs[aid].slot, c.nd->cap_amap);
+}
+
+// Registers a new allocation record with an empty writer / reader slab.
+__device__ bool new_alloc(Ctx& c, uint32_t aid, uint32_t b, uint32_t m, const Bx& bb, uint32_t user) {
+  if (aid >= c.nd->cap_alloc || c.n_free == 0) {
+    fail(c, ST_CAPACITY);
+    return false;
+  }
+  c.n_free -= 1;
+  const uint32_t slot = c.nd->free_slots[c.n_free];
+  if (c.lane == 0) {
+    AllocRec rec;
+    rec.buffer = b;
+    rec.mem = m;
+    rec.live = 1;
+    rec.user = user;
+    for (int d = 0; d < 3; ++d) {
+      rec.lo[d] = bb.lo[d];
+      rec.hi[d] = bb.hi[d];
+    }
+    rec.mark = NONE;
+    rec.slot = slot;
+    c.nd->allocs[aid] = rec;
+    c.nd->wr_n[slot] = 0;
+    c.nd->rd_n[slot] = 0;
+    c.nd->live[c.n_live] = aid;  // ids grow: the list stays sorted
+  }
+  c.n_live += 1;
+  __syncwarp();
+  return true;
+}
+
+// Drops an allocation: its slab goes back to the free list.
+__device__ void drop_alloc(Ctx& c, uint32_t aid) {
+  const uint32_t slot = c.nd->allocs[aid].slot;
+  __syncwarp();
+  if (c.lane == 0) {
+    c.nd->allocs[aid].live = 0;
+    c.nd->free_slots[c.n_free] = slot;
+    uint32_t* L = c.nd->live;
+    uint32_t k = 0;
+    while (k < c.n_live && L[k] != aid) ++k;
+    for (; k + 1 < c.n_live; ++k) L[k] = L[k + 1];
+  }
+  c.n_free += 1;
+  c.n_live -= 1;
+  __syncwarp();
+}
+
 __device__ __forceinline__ Bx alloc_box(const AllocRec& a) {
   Bx b;
   for (int d = 0; d < 3; ++d) {
@@ -599,18 +699,21 @@ __device__ __forceinline__ Bx alloc_box(const AllocRec& a) {
 // The live allocation of (buffer, memory) containing box, or NONE.
 __device__ uint32_t find_alloc(const Ctx& c, uint32_t buf, uint32_t mem, const Bx& b) {
   const AllocRec* A = c.nd->allocs;
-  return warp_find_first(c, c.n_alloc, [&](uint32_t i) {
-    const AllocRec& a = A[i];
-    return a.live && a.buffer == buf && a.mem == mem && bx_contains(alloc_box(a), b);
+  const uint32_t* L = c.nd->live;
+  const uint32_t k = warp_find_first(c, c.n_live, [&](uint32_t i) {
+    const AllocRec& a = A[L[i]];
+    return a.buffer == buf && a.mem == mem && bx_contains(alloc_box(a), b);
   });
+  return k == NONE ? NONE : L[k];
 }
 
 // Per-lane variant (no warp collectives).
 __device__ bool covered_by_alloc(const Ctx& c, uint32_t buf, uint32_t mem, const Bx& b) {
   const AllocRec* A = c.nd->allocs;
-  for (uint32_t i = 0; i < c.n_alloc; ++i) {
-    const AllocRec& a = A[i];
-    if (a.live && a.buffer == buf && a.mem == mem && bx_contains(alloc_box(a), b)) return true;
+  const uint32_t* L = c.nd->live;
+  for (uint32_t i = 0; i < c.n_live; ++i) {
+    const AllocRec& a = A[L[i]];
+    if (a.buffer == buf && a.mem == mem && bx_contains(alloc_box(a), b)) return true;
   }
   return false;
 }
@@ -712,19 +815,24 @@ __device__ void task_mapped(Ctx& c, const igs_task& t, const Table& CH, Table& M
 
 // Sec. 4.4: chunks of one task writing overlapping regions.
 __device__ bool overlapping_writes(Ctx& c, const igs_task& t, const Table& CH, const Table& MP) {
-  const uint32_t na = t.num_accessors, nw = CH.n * na;
-  const uint64_t pairs = (uint64_t)nw * nw;
-  for (uint64_t base = 0; base < pairs; base += 32) {
-    const uint64_t p = base + c.lane;
-    bool bad = false;
-    if (p < pairs) {
-      const uint32_t x = (uint32_t)(p / nw), y = (uint32_t)(p % nw);
-      const uint32_t sx = x / na, ax = x % na, sy = y / na, ay = y % na;
-      if (sx < sy && (t.acc[ax].mode & IGS_WRITE) && (t.acc[ay].mode & IGS_WRITE) &&
-          t.acc[ax].buffer == t.acc[ay].buffer)
-        bad = bx_overlap(t_box(MP, x), t_box(MP, y));
+  const uint32_t na = t.num_accessors;
+  for (uint32_t a = 0; a < na; ++a) {
+    if (!(t.acc[a].mode & IGS_WRITE)) continue;
+    for (uint32_t b = a; b < na; ++b) {
+      if (!(t.acc[b].mode & IGS_WRITE) || t.acc[b].buffer != t.acc[a].buffer) continue;
+      // chunk x's accessor a against every later chunk y's accessor b (and a
+      // against b within the pair of accessors when a != b)
+      for (uint32_t x = 0; x < CH.n; ++x) {
+        const Bx bx = t_box(MP, x * na + a);
+        if (bx_empty(bx)) continue;
+        for (uint32_t base = 0; base < CH.n; base += 32) {
+          const uint32_t y = base + c.lane;
+          bool bad = false;
+          if (y < CH.n && y != x && (a != b || y > x)) bad = bx_overlap(bx, t_box(MP, y * na + b));
+          if (__ballot_sync(FULL, bad)) return true;
+        }
+      }
     }
-    if (__ballot_sync(FULL, bad)) return true;
   }
   return false;
 }
@@ -754,12 +862,12 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
       const Bx q = t_box(*A.t, r);
       // writers
       {
-        const Table& T = c.wr;
+        const Table T = wr_t(c, A.alloc);
         for (uint32_t base = 0; base < T.n; base += 32) {
           const uint32_t i = base + c.lane;
           bool hit = false;
           uint32_t w = 0, kind = 0;
-          if (i < T.n && t_key(T, i) == A.alloc && bx_overlap(t_box(T, i), q)) {
+          if (i < T.n && t_key(T, i) != DEAD && bx_overlap(t_box(T, i), q)) {
             hit = true;
             w = t_v(T, 0, i);
             if (instr_type(c, w) == IGS_ALLOC) kind = IGS_DEP_ALLOC;
@@ -775,10 +883,10 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
         }
       }
       if (A.mode & IGS_WRITE) {
-        const Table& T = c.rd;
+        const Table T = rd_t(c, A.alloc);
         for (uint32_t base = 0; base < T.n; base += 32) {
           const uint32_t i = base + c.lane;
-          bool hit = i < T.n && t_key(T, i) == A.alloc && bx_overlap(t_box(T, i), q);
+          bool hit = i < T.n && t_key(T, i) != DEAD && bx_overlap(t_box(T, i), q);
           c.map_reads += warp_sum(hit ? 1u : 0u);
           const uint32_t s = t_claim(c, D, hit);
           if (c.err) return NONE;
@@ -920,53 +1028,75 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
     bool again = false;
     for (int j = 0; j < k; ++j)
       if (acc[j].alloc == A.alloc && (acc[j].mode & IGS_READ)) again = true;
-    const uint32_t from = c.rd.n;
+    Table RD = rd_t(c, A.alloc);
+    t_tidy(c, RD);
+    const uint32_t from = RD.n;
     for (uint32_t r = A.from; r < A.to; ++r) {
       if (t_key(*A.t, r) == DEAD) continue;
       const Bx q = t_box(*A.t, r);
-      if (again) t_subtract(c, c.rd, A.alloc, q, id);
-      const uint32_t s = t_claim(c, c.rd, c.lane == 0);
+      if (again) t_subtract(c, RD, NONE, q, id);
+      const uint32_t s = t_claim(c, RD, c.lane == 0);
       if (c.err) return NONE;
-      if (c.lane == 0) t_put(c.rd, s, A.alloc, q, id, 0, 0);
+      if (c.lane == 0) t_put(RD, s, 0, q, id, 0, 0);
       __syncwarp();
     }
-    t_merge_from(c, c.rd, from);
+    t_merge_from(c, RD, from);
   }
   for (int k = 0; k < nacc; ++k) {
     const Acc& A = acc[k];
     if (!(A.mode & IGS_WRITE)) continue;
-    const uint32_t from = c.wr.n;
+    Table RD = rd_t(c, A.alloc);
+    Table WR = wr_t(c, A.alloc);
+    t_tidy(c, WR);
+    const uint32_t from = WR.n;
     for (uint32_t r = A.from; r < A.to; ++r) {
       if (t_key(*A.t, r) == DEAD) continue;
       const Bx q = t_box(*A.t, r);
-      t_subtract(c, c.rd, A.alloc, q);
-      t_set(c, c.wr, A.alloc, q, id, 0, 0);
+      t_subtract(c, RD, NONE, q);
+      t_set(c, WR, NONE, q, id, 0, 0);
       if (c.err) return NONE;
     }
-    t_merge_from(c, c.wr, from);
+    t_merge_from(c, WR, from);
   }
   return id;
 }
 
 // Replace every tracked instruction id older than h by h and re-merge (a9).
-__device__ void apply_epoch(Ctx& c, uint32_t h) {
-  Table* ts[3] = {&c.wr, &c.rd, &c.bst};
-  for (int k = 0; k < 3; ++k) {
-    Table& T = *ts[k];
-    for (uint32_t base = 0; base < T.n; base += 32) {
-      const uint32_t i = base + c.lane;
-      if (i < T.n && t_key(T, i) != DEAD) {
-        const uint32_t v = t_v(T, 0, i);
-        if (v < h) TP(T, F_V)[i] = h;
-      }
+__device__ void map_ids(Ctx& c, Table& T, uint32_t h) {
+  for (uint32_t base = 0; base < T.n; base += 32) {
+    const uint32_t i = base + c.lane;
+    if (i < T.n && t_key(T, i) != DEAD) {
+      const uint32_t v = t_v(T, 0, i);
+      if (v < h) TP(T, F_V)[i] = h;
     }
-    __syncwarp();
   }
-  t_make_disjoint(c, c.rd, h);
-  for (int k = 0; k < 3; ++k) {
-    t_compact(c, *ts[k]);
-    t_merge_from(c, *ts[k], 0);
-    t_compact(c, *ts[k]);
+  __syncwarp();
+}
+
+__device__ void apply_epoch(Ctx& c, uint32_t h) {
+  for (uint32_t li = 0; li < c.n_live; ++li) {
+    const uint32_t aid = c.nd->live[li];
+    Table WR = wr_t(c, aid);
+    map_ids(c, WR, h);
+    t_compact(c, WR);
+    t_merge_from(c, WR, 0);
+    t_compact(c, WR);
+    Table RD = rd_t(c, aid);
+    map_ids(c, RD, h);
+    t_make_disjoint(c, RD, h);
+    t_compact(c, RD);
+    t_merge_from(c, RD, 0);
+    t_compact(c, RD);
+    if (c.err) return;
+  }
+  const uint32_t nb = c.nd->cap_buffers;
+  for (uint32_t b = 0; b < nb; ++b) {
+    Table B = bst_t(c, b);
+    if (B.n == 0) continue;
+    map_ids(c, B, h);
+    t_compact(c, B);
+    t_merge_from(c, B, 0);
+    t_compact(c, B);
   }
   c.epoch = h;
 }
@@ -975,26 +1105,23 @@ __device__ void apply_epoch(Ctx& c, uint32_t h) {
 __device__ void emit_free(Ctx& c, uint32_t seq, uint32_t aid) {
   Table& D = c.s[S_DEP];
   D.n = 0;
-  Table* ts[2] = {&c.wr, &c.rd};
   for (int k = 0; k < 2; ++k) {
-    Table& T = *ts[k];
+    const Table T = k == 0 ? wr_t(c, aid) : rd_t(c, aid);
     for (uint32_t base = 0; base < T.n; base += 32) {
       const uint32_t i = base + c.lane;
-      const bool hit = i < T.n && t_key(T, i) == aid;
+      const bool hit = i < T.n && t_key(T, i) != DEAD;
       const uint32_t s = t_claim(c, D, hit);
       if (c.err) return;
       if (hit) {
         TP(D, F_V)[s] = t_v(T, 0, i);
         TP(D, F_V + 1)[s] = IGS_DEP_ALLOC;
-        t_kill(T, i);
       }
     }
   }
   __syncwarp();
   const AllocRec a = c.nd->allocs[aid];
   emit(c, IGS_FREE, seq, aid, a.mem, a.buffer, NONE, nullptr, 0, 0, nullptr, 0, true);
-  if (c.lane == 0) c.nd->allocs[aid].live = 0;
-  __syncwarp();
+  drop_alloc(c, aid);
 }
 
 // a5: coherence copies making need = T[from, to) (disjoint boxes) up to date
@@ -1009,13 +1136,16 @@ __device__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_t m, uint32_t
   Table& CN = c.s[S_T5];
   Q.n = 0;
   CP.n = 0;
-  for (uint32_t r = from; r < to; ++r) {
-    if (t_key(T, r) == DEAD) continue;
-    const Bx q = t_box(T, r);
-    t_query(c, c.bst, b, q, Q, [m](uint32_t prod, uint32_t, uint32_t mask) {
-      return !((mask >> m) & 1u) && prod != NONE;
-    });
-    if (c.err) return;
+  {
+    const Table B = bst_t(c, b);
+    for (uint32_t r = from; r < to; ++r) {
+      if (t_key(T, r) == DEAD) continue;
+      const Bx q = t_box(T, r);
+      t_query(c, B, NONE, q, Q, [m](uint32_t prod, uint32_t, uint32_t mask) {
+        return !((mask >> m) & 1u) && prod != NONE;
+      });
+      if (c.err) return;
+    }
   }
   uint64_t last = 0;
   bool first_round = true;
@@ -1048,9 +1178,10 @@ __device__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_t m, uint32_t
       if (hit) t_put(G, s, 0, t_box(Q, i), 0, 0, 0);
     }
     __syncwarp();
-    for (uint32_t src = 0; src < c.n_alloc; ++src) {
+    for (uint32_t li = 0; li < c.n_live; ++li) {
+      const uint32_t src = c.nd->live[li];
       const AllocRec a = c.nd->allocs[src];
-      if (!a.live || a.buffer != b || a.mem != pmem) continue;
+      if (a.buffer != b || a.mem != pmem) continue;
       P.n = 0;
       const Bx ab = alloc_box(a);
       for (uint32_t base = 0; base < G.n; base += 32) {
@@ -1084,12 +1215,14 @@ __device__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_t m, uint32_t
       __syncwarp();
     }
   }
-  const uint32_t from_bst = c.bst.n;
+  Table B = bst_t(c, b);
+  t_tidy(c, B);
+  const uint32_t from_bst = B.n;
   for (uint32_t i = 0; i < CP.n; ++i) {
-    t_or(c, c.bst, b, t_box(CP, i), 2, 1u << m);
+    t_or(c, B, NONE, t_box(CP, i), 2, 1u << m);
     if (c.err) return;
   }
-  t_merge_from(c, c.bst, from_bst);
+  t_merge_from(c, B, from_bst);
 }
 
 // ---- a3: push / await push (node level) ------------------------------------
@@ -1122,7 +1255,7 @@ __device__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH
           if (t.acc[a].buffer != b || !(t.acc[a].mode & IGS_READ)) continue;
           const Bx x = t_box(MP, slot * na + a);
           if (bx_empty(x)) continue;
-          t_query(c, c.own, b, x, TMP, [m](uint32_t, uint32_t repl, uint32_t) { return !((repl >> m) & 1u); });
+          t_query(c, own_t(c, b), NONE, x, TMP, [m](uint32_t, uint32_t repl, uint32_t) { return !((repl >> m) & 1u); });
           if (c.err) return;
         }
       }
@@ -1174,7 +1307,7 @@ __device__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH
       for (uint32_t i = 0; i < MISS.n; ++i) {
         if (t_v(MISS, 0, i) != m) continue;
         const uint32_t me = c.node;
-        t_query(c, c.own, b, t_box(MISS, i), PT, [me](uint32_t owner, uint32_t, uint32_t) { return owner == me; });
+        t_query(c, own_t(c, b), NONE, t_box(MISS, i), PT, [me](uint32_t owner, uint32_t, uint32_t) { return owner == me; });
         if (c.err) return;
       }
       if (PT.n == 0) continue;
@@ -1195,9 +1328,11 @@ __device__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH
       __syncwarp();
     }
     // replication: every node now holds what it awaited
-    const uint32_t from = c.own.n;
+    Table O = own_t(c, b);
+    t_tidy(c, O);
+    const uint32_t from = O.n;
     for (uint32_t i = 0; i < MISS.n; ++i) {
-      t_or(c, c.own, b, t_box(MISS, i), 1, 1u << t_v(MISS, 0, i));
+      t_or(c, O, NONE, t_box(MISS, i), 1, 1u << t_v(MISS, 0, i));
       if (c.err) return;
     }
     // writes: owner = writing node, replicated there only
@@ -1207,11 +1342,11 @@ __device__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH
         if (t.acc[a].buffer != b || !(t.acc[a].mode & IGS_WRITE)) continue;
         const Bx x = t_box(MP, slot * na + a);
         if (bx_empty(x)) continue;
-        t_set(c, c.own, b, x, wn, 1u << wn, 0);
+        t_set(c, O, NONE, x, wn, 1u << wn, 0);
         if (c.err) return;
       }
     }
-    t_merge_from(c, c.own, from);
+    t_merge_from(c, O, from);
   }
 }
 
@@ -1356,9 +1491,10 @@ __device__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq, const Table
     // and absorbing every overlapping live allocation of (b, m) [positive
     // volume, merely touching boxes stay apart]
     AllocRec* A = c.nd->allocs;
-    for (uint32_t base = 0; base < c.n_alloc; base += 32) {
+    const uint32_t* L = c.nd->live;
+    for (uint32_t base = 0; base < c.n_live; base += 32) {
       const uint32_t i = base + c.lane;
-      if (i < c.n_alloc) A[i].mark = NONE;
+      if (i < c.n_live) A[L[i]].mark = NONE;
     }
     __syncwarp();
     for (int guard = 0;; ++guard) {
@@ -1391,23 +1527,24 @@ __device__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq, const Table
           t_put(CL, i, 0, u, own, 0, 0);
           t_kill(CL, j);
         }
-        for (uint32_t base = 0; base < c.n_alloc; base += 32) {
+        for (uint32_t base = 0; base < c.n_live; base += 32) {
           const uint32_t x = base + c.lane;
-          if (x < c.n_alloc && A[x].mark == j) A[x].mark = i;
+          if (x < c.n_live && A[L[x]].mark == j) A[L[x]].mark = i;
         }
         __syncwarp();
         continue;
       }
       // a cluster overlapping an unabsorbed allocation
-      const uint64_t cp = (uint64_t)n * c.n_alloc;
+      const uint32_t nl = c.n_live;
+      const uint64_t cp = (uint64_t)n * nl;
       found = NONE;
       for (uint64_t base = 0; base < cp; base += 32) {
         const uint64_t p = base + c.lane;
         bool h = false;
         if (p < cp) {
-          const uint32_t i = (uint32_t)(p / c.n_alloc), x = (uint32_t)(p % c.n_alloc);
+          const uint32_t i = (uint32_t)(p / nl), x = L[(uint32_t)(p % nl)];
           const AllocRec& a = A[x];
-          h = t_key(CL, i) != DEAD && a.live && a.buffer == b && a.mem == m && a.mark == NONE &&
+          h = t_key(CL, i) != DEAD && a.buffer == b && a.mem == m && a.mark == NONE &&
               bx_overlap(t_box(CL, i), alloc_box(a));
         }
         const uint32_t mm = __ballot_sync(FULL, h);
@@ -1418,7 +1555,7 @@ __device__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq, const Table
       }
       if (found == NONE) break;
       {
-        const uint32_t i = found / c.n_alloc, x = found % c.n_alloc;
+        const uint32_t i = found / nl, x = L[found % nl];
         const Bx u = bx_union(t_box(CL, i), alloc_box(A[x]));
         const uint32_t own = t_v(CL, 0, i);
         __syncwarp();
@@ -1456,32 +1593,31 @@ __device__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq, const Table
       const uint32_t aid = c.n_alloc;
       const uint32_t iid = emit(c, IGS_ALLOC, seq, aid, m, b, NONE, &CL, ci, ci + 1, nullptr, 0, false);
       if (c.err) return;
-      if (c.lane == 0) {
-        AllocRec rec;
-        rec.buffer = b;
-        rec.mem = m;
-        rec.live = 1;
-        rec.user = 0;
-        for (int d = 0; d < 3; ++d) {
-          rec.lo[d] = bb.lo[d];
-          rec.hi[d] = bb.hi[d];
-        }
-        rec.mark = NONE;
-        rec.pad = 0;
-        A[aid] = rec;
-      }
+      if (!new_alloc(c, aid, b, m, bb, 0)) return;
       c.n_alloc += 1;
-      __syncwarp();
       {
-        const uint32_t s = t_claim(c, c.wr, c.lane == 0);
+        Table WR = wr_t(c, aid);
+        const uint32_t s = t_claim(c, WR, c.lane == 0);
         if (c.err) return;
-        if (c.lane == 0) t_put(c.wr, s, aid, bb, iid, 0, 0);
+        if (c.lane == 0) t_put(WR, s, 0, bb, iid, 0, 0);
         __syncwarp();
       }
-      for (uint32_t old = 0; old < aid; ++old) {
-        if (A[old].mark != ci || !A[old].live) continue;
+      // the absorbed allocations, ascending (the live list changes as they are freed)
+      Table& AB = c.s[S_T3];
+      AB.n = 0;
+      for (uint32_t base = 0; base < c.n_live; base += 32) {
+        const uint32_t x = base + c.lane;
+        const bool hit = x < c.n_live && L[x] != aid && A[L[x]].mark == ci;
+        const uint32_t s = t_claim(c, AB, hit);
+        if (c.err) return;
+        if (hit) TP(AB, F_V)[s] = L[x];
+      }
+      __syncwarp();
+      for (uint32_t ai = 0; ai < AB.n; ++ai) {
+        const uint32_t old = TP(AB, F_V)[ai];
         Q.n = 0;
-        t_query(c, c.bst, b, alloc_box(A[old]), Q, [m](uint32_t, uint32_t, uint32_t mask) { return ((mask >> m) & 1u) != 0; });
+        t_query(c, bst_t(c, b), NONE, alloc_box(A[old]), Q,
+                [m](uint32_t, uint32_t, uint32_t mask) { return ((mask >> m) & 1u) != 0; });
         if (c.err) return;
         CN.n = 0;
         canonical(c, Q, 0, Q.n, CN);
@@ -1506,12 +1642,15 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
   const uint32_t seq = it.seq, na = t.num_accessors;
   Table& CH = c.s[S_CH];
   Table& MP = c.s[S_MP];
+  PhaseTimer pt = pt_start();
   task_chunks(c, t, CH);
   task_mapped(c, t, CH, MP);
   if (c.err) return;
+  pt_lap(pt, c, PH_SPLIT);
   // P1
   alloc_phase(c, t, seq, CH, MP);
   if (c.err) return;
+  pt_lap(pt, c, PH_P1);
   uint32_t qs, qe;
   qr_block(c, seq, qs, qe);
   // P2: pushes, (buffer, target) ascending
@@ -1548,9 +1687,12 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
     if (c.err) return;
     // sends: one per (original producer, canonical box)
     Q.n = 0;
-    for (uint32_t r = 0; r < RG.n; ++r) {
-      t_query(c, c.bst, b, t_box(RG, r), Q, [](uint32_t, uint32_t, uint32_t) { return true; });
-      if (c.err) return;
+    {
+      const Table B = bst_t(c, b);
+      for (uint32_t r = 0; r < RG.n; ++r) {
+        t_query(c, B, NONE, t_box(RG, r), Q, [](uint32_t, uint32_t, uint32_t) { return true; });
+        if (c.err) return;
+      }
     }
     uint64_t last = 0;
     bool first_round = true;
@@ -1590,6 +1732,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
     }
     g0 = g1 + 1;
   }
+  pt_lap(pt, c, PH_P2);
   // P3: await push per buffer: one receive, or split receive + await receives
   Table& CONS = c.s[S_T4];
   Table& COV = c.s[S_CL];
@@ -1656,12 +1799,14 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
       Acc acc[1] = {{&RG, 0, RG.n, dst, IGS_WRITE}};
       const uint32_t id = emit(c, IGS_RECEIVE, seq, dst, NONE, b, NONE, &RG, 0, RG.n, acc, 1, false);
       if (c.err) return;
-      const uint32_t from = c.bst.n;
+      Table B = bst_t(c, b);
+      t_tidy(c, B);
+      const uint32_t from = B.n;
       for (uint32_t i = 0; i < RG.n; ++i) {
-        t_set(c, c.bst, b, t_box(RG, i), id, 1, 1u << 1);
+        t_set(c, B, NONE, t_box(RG, i), id, 1, 1u << 1);
         if (c.err) return;
       }
-      t_merge_from(c, c.bst, from);
+      t_merge_from(c, B, from);
     } else {
       Acc acc[1] = {{&RG, 0, RG.n, dst, IGS_WRITE}};
       const uint32_t sid = emit(c, IGS_SPLIT_RECEIVE, seq, dst, NONE, b, NONE, &RG, 0, RG.n, acc, 1, false);
@@ -1696,15 +1841,19 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
         __syncwarp();
         const uint32_t aid = emit(c, IGS_AWAIT_RECEIVE, seq, dst, sid, b, NONE, &CN, 0, CN.n, nullptr, 0, true);
         if (c.err) return;
-        const uint32_t fw = c.wr.n, fb = c.bst.n;
+        Table WR = wr_t(c, dst);
+        Table B = bst_t(c, b);
+        t_tidy(c, WR);
+        t_tidy(c, B);
+        const uint32_t fw = WR.n, fb = B.n;
         for (uint32_t i = 0; i < CN.n; ++i) {
           const Bx x = t_box(CN, i);
-          t_set(c, c.wr, dst, x, aid, 0, 0);
-          t_set(c, c.bst, b, x, aid, 1, 1u << 1);
+          t_set(c, WR, NONE, x, aid, 0, 0);
+          t_set(c, B, NONE, x, aid, 1, 1u << 1);
           if (c.err) return;
         }
-        t_merge_from(c, c.wr, fw);
-        t_merge_from(c, c.bst, fb);
+        t_merge_from(c, WR, fw);
+        t_merge_from(c, B, fb);
         for (uint32_t base = 0; base < CN.n; base += 32) {
           const uint32_t i = base + c.lane;
           const bool in = i < CN.n;
@@ -1717,6 +1866,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
     }
     g0 = g1 + 1;
   }
+  pt_lap(pt, c, PH_P3);
   // P4: coherence for every reading accessor, (chunk, accessor) order
   for (uint32_t slot = 0; slot < CH.n; ++slot) {
     if (t_v(CH, 0, slot) != c.node) continue;
@@ -1728,8 +1878,9 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
       if (bx_empty(x)) continue;
       // uninitialized read warning (Sec. 4.4)
       const uint32_t b = ac.buffer;
-      const uint32_t un = warp_find_first(c, c.bst.n, [&](uint32_t i) {
-        return t_key(c.bst, i) == b && t_v(c.bst, 0, i) == NONE && bx_overlap(t_box(c.bst, i), x);
+      const Table B = bst_t(c, b);
+      const uint32_t un = warp_find_first(c, B.n, [&](uint32_t i) {
+        return t_key(B, i) != DEAD && t_v(B, 0, i) == NONE && bx_overlap(t_box(B, i), x);
       });
       if (un != NONE) {
         if (c.n_diag >= c.nd->cap_diag) {
@@ -1762,6 +1913,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
       if (c.err) return;
     }
   }
+  pt_lap(pt, c, PH_P4);
   // P5: one device kernel per local chunk
   Table& BT = c.s[S_T4];
   for (uint32_t slot = 0; slot < CH.n; ++slot) {
@@ -1791,28 +1943,32 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
     const uint32_t kid = emit(c, IGS_KERNEL, seq, t_key(CH, slot), mem, t.kernel_id, NONE, &CH, slot, slot + 1, acc,
                               nacc, false, &BT, 0, na);
     if (c.err) return;
-    const uint32_t from = c.bst.n;
     for (uint32_t a = 0; a < na; ++a) {
       const Bx x = t_box(MP, slot * na + a);
       if (!(t.acc[a].mode & IGS_WRITE) || bx_empty(x)) continue;
-      t_set(c, c.bst, t.acc[a].buffer, x, kid, mem, 1u << mem);
+      Table B = bst_t(c, t.acc[a].buffer);
+      t_tidy(c, B);
+      const uint32_t from = B.n;
+      t_set(c, B, NONE, x, kid, mem, 1u << mem);
       if (c.err) return;
+      t_merge_from(c, B, from);
     }
-    t_merge_from(c, c.bst, from);
   }
+  pt_lap(pt, c, PH_P5);
   // writes of other nodes make the local copies stale
-  {
-    const uint32_t from = c.bst.n;
+  for (uint32_t a = 0; a < na; ++a) {
+    if (!(t.acc[a].mode & IGS_WRITE)) continue;
+    Table B = bst_t(c, t.acc[a].buffer);
+    t_tidy(c, B);
+    const uint32_t from = B.n;
     for (uint32_t slot = 0; slot < CH.n; ++slot) {
       if (t_v(CH, 0, slot) == c.node) continue;
-      for (uint32_t a = 0; a < na; ++a) {
-        const Bx x = t_box(MP, slot * na + a);
-        if (!(t.acc[a].mode & IGS_WRITE) || bx_empty(x)) continue;
-        t_set(c, c.bst, t.acc[a].buffer, x, REMOTE, 0, 0);
-        if (c.err) return;
-      }
+      const Bx x = t_box(MP, slot * na + a);
+      if (bx_empty(x)) continue;
+      t_set(c, B, NONE, x, REMOTE, 0, 0);
+      if (c.err) return;
     }
-    t_merge_from(c, c.bst, from);
+    t_merge_from(c, B, from);
   }
   // the task's push / await regions are consumed
   for (uint32_t base = qs; base < qe; base += 32) {
@@ -1820,6 +1976,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
     if (i < qe) t_kill(c.qr, i);
   }
   __syncwarp();
+  pt_lap(pt, c, PH_REMOTE);
 }
 
 // ---- items ---------------------------------------------------------------------
@@ -1830,38 +1987,28 @@ __device__ void process(Ctx& c, uint32_t item) {
     case IT_CREATE: {
       const BufDesc& bd = buf_of(c, it.arg);
       const Bx dom = buffer_box(bd);
+      if (it.arg >= c.nd->cap_buffers) {
+        fail(c, ST_CAPACITY);
+        return;
+      }
+      if (c.lane == 0) c.nd->bst_n[it.arg] = 0;
+      __syncwarp();
+      Table B = bst_t(c, it.arg);
       if (bd.init) {
-        if (c.n_alloc >= c.nd->cap_alloc) {
-          fail(c, ST_CAPACITY);
-          return;
-        }
         const uint32_t aid = c.n_alloc;
-        if (c.lane == 0) {
-          AllocRec rec;
-          rec.buffer = it.arg;
-          rec.mem = 0;
-          rec.live = 1;
-          rec.user = 1;
-          for (int d = 0; d < 3; ++d) {
-            rec.lo[d] = dom.lo[d];
-            rec.hi[d] = dom.hi[d];
-          }
-          rec.mark = NONE;
-          rec.pad = 0;
-          c.nd->allocs[aid] = rec;
-        }
+        if (!new_alloc(c, aid, it.arg, 0, dom, 1)) return;
         c.n_alloc += 1;
-        __syncwarp();
-        const uint32_t s = t_claim(c, c.wr, c.lane == 0);
+        Table WR = wr_t(c, aid);
+        const uint32_t s = t_claim(c, WR, c.lane == 0);
         if (c.err) return;
-        if (c.lane == 0) t_put(c.wr, s, aid, dom, c.epoch, 0, 0);
-        const uint32_t s2 = t_claim(c, c.bst, c.lane == 0);
+        if (c.lane == 0) t_put(WR, s, 0, dom, c.epoch, 0, 0);
+        const uint32_t s2 = t_claim(c, B, c.lane == 0);
         if (c.err) return;
-        if (c.lane == 0) t_put(c.bst, s2, it.arg, dom, c.epoch, 0, 1u);
+        if (c.lane == 0) t_put(B, s2, 0, dom, c.epoch, 0, 1u);
       } else {
-        const uint32_t s2 = t_claim(c, c.bst, c.lane == 0);
+        const uint32_t s2 = t_claim(c, B, c.lane == 0);
         if (c.err) return;
-        if (c.lane == 0) t_put(c.bst, s2, it.arg, dom, NONE, 0, 0);
+        if (c.lane == 0) t_put(B, s2, 0, dom, NONE, 0, 0);
       }
       __syncwarp();
       break;
@@ -1884,9 +2031,11 @@ __device__ void process(Ctx& c, uint32_t item) {
         }
       }
       __syncwarp();
+      PhaseTimer pt = pt_start();
       const uint32_t id = emit(c, it.kind == IT_EPOCH ? IGS_EPOCH : IGS_HORIZON, it.seq, NONE, NONE, NONE, NONE,
                                nullptr, 0, 0, nullptr, 0, true);
       if (c.err) return;
+      pt_lap(pt, c, PH_SYNC);
       c.last_sync = id;
       if (it.kind == IT_EPOCH) {
         apply_epoch(c, id);
@@ -1895,34 +2044,34 @@ __device__ void process(Ctx& c, uint32_t item) {
         if (c.last_horizon != NONE) apply_epoch(c, c.last_horizon);
         c.last_horizon = id;
       }
+      pt_lap(pt, c, PH_APPLY);
       break;
     }
     case IT_DESTROY: {
       const uint32_t b = it.arg;
+      Table& AB = c.s[S_T3];
+      AB.n = 0;
+      for (uint32_t base = 0; base < c.n_live; base += 32) {
+        const uint32_t x = base + c.lane;
+        const bool hit = x < c.n_live && c.nd->allocs[c.nd->live[x]].buffer == b;
+        const uint32_t s = t_claim(c, AB, hit);
+        if (c.err) return;
+        if (hit) TP(AB, F_V)[s] = c.nd->live[x];
+      }
+      __syncwarp();
       for (uint32_t m = 0; m < 2 + c.D; ++m)
-        for (uint32_t aid = 0; aid < c.n_alloc; ++aid) {
+        for (uint32_t ai = 0; ai < AB.n; ++ai) {
+          const uint32_t aid = TP(AB, F_V)[ai];
           const AllocRec a = c.nd->allocs[aid];
-          if (!a.live || a.buffer != b || a.mem != m) continue;
+          if (a.mem != m) continue;
           if (!a.user) {
             emit_free(c, it.seq, aid);
             if (c.err) return;
           } else {
-            for (uint32_t base = 0; base < c.wr.n; base += 32) {
-              const uint32_t i = base + c.lane;
-              if (i < c.wr.n && t_key(c.wr, i) == aid) t_kill(c.wr, i);
-            }
-            for (uint32_t base = 0; base < c.rd.n; base += 32) {
-              const uint32_t i = base + c.lane;
-              if (i < c.rd.n && t_key(c.rd, i) == aid) t_kill(c.rd, i);
-            }
-            if (c.lane == 0) c.nd->allocs[aid].live = 0;
-            __syncwarp();
+            drop_alloc(c, aid);
           }
         }
-      for (uint32_t base = 0; base < c.bst.n; base += 32) {
-        const uint32_t i = base + c.lane;
-        if (i < c.bst.n && t_key(c.bst, i) == b) t_kill(c.bst, i);
-      }
+      if (c.lane == 0) c.nd->bst_n[b] = 0;
       __syncwarp();
       break;
     }
@@ -1958,9 +2107,7 @@ __device__ void enqueue(Ctx& c, uint32_t item) {
 }
 
 __device__ void maintain(Ctx& c) {
-  Table* ts[5] = {&c.own, &c.bst, &c.wr, &c.rd, &c.qr};
-  for (int k = 0; k < 5; ++k)
-    if (ts[k]->n > ts[k]->cap / 4) t_compact(c, *ts[k]);
+  if (c.qr.n > c.qr.cap / 4) t_compact(c, c.qr);
 }
 
 // Scheduler lookahead (Sec. 4.3): a task is queued while an allocating task
@@ -1976,10 +2123,17 @@ __device__ void deliver(Ctx& c, uint32_t item) {
     return;
   }
   if (it.kind == IT_CREATE) {
+    if (it.arg >= c.nd->cap_buffers) {
+      fail(c, ST_CAPACITY);
+      return;
+    }
     const BufDesc& bd = buf_of(c, it.arg);
-    const uint32_t s = t_claim(c, c.own, c.lane == 0);
+    if (c.lane == 0) c.nd->own_n[it.arg] = 0;
+    __syncwarp();
+    Table O = own_t(c, it.arg);
+    const uint32_t s = t_claim(c, O, c.lane == 0);
     if (c.err) return;
-    if (c.lane == 0) t_put(c.own, s, it.arg, buffer_box(bd), bd.init ? HOST : NONE, 0xFFFFFFFFu, 0);
+    if (c.lane == 0) t_put(O, s, 0, buffer_box(bd), bd.init ? HOST : NONE, 0xFFFFFFFFu, 0);
     __syncwarp();
   }
   bool alloc_now = false;
@@ -1987,10 +2141,14 @@ __device__ void deliver(Ctx& c, uint32_t item) {
     const igs_task& t = c.pg->tasks[it.task];
     Table& CH = c.s[S_CH];
     Table& MP = c.s[S_MP];
+    PhaseTimer pt = pt_start();
     task_chunks(c, t, CH);
     task_mapped(c, t, CH, MP);
     if (c.err) return;
-    if (overlapping_writes(c, t, CH, MP)) {
+    pt_lap(pt, c, PH_SPLIT);
+    const bool bad = overlapping_writes(c, t, CH, MP);
+    pt_lap(pt, c, PH_OVERLAP);
+    if (bad) {
       if (c.n_rej < c.nd->cap_rej) {
         if (c.lane == 0) c.nd->rejected[c.n_rej] = it.seq;
         c.n_rej += 1;
@@ -2000,8 +2158,10 @@ __device__ void deliver(Ctx& c, uint32_t item) {
     }
     a3_task(c, t, it.seq, CH, MP);
     if (c.err) return;
+    pt_lap(pt, c, PH_A3);
     if (c.q_count == 0) alloc_now = allocating(c, t, it.seq, CH, MP);
     if (c.err) return;
+    pt_lap(pt, c, PH_ALLOCATING);
   }
   if (c.q_count == 0) {
     if (alloc_now) {
@@ -2016,10 +2176,7 @@ __device__ void deliver(Ctx& c, uint32_t item) {
   }
   if (c.err) return;
   if (it.kind == IT_DESTROY) {
-    for (uint32_t base = 0; base < c.own.n; base += 32) {
-      const uint32_t i = base + c.lane;
-      if (i < c.own.n && t_key(c.own, i) == it.arg) t_kill(c.own, i);
-    }
+    if (c.lane == 0) c.nd->own_n[it.arg] = 0;
     __syncwarp();
   }
 }
@@ -2037,6 +2194,8 @@ __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg) {
   c.last_sync = nd->last_sync;
   c.next_msg = nd->next_msg;
   c.n_alloc = nd->n_alloc;
+  c.n_free = nd->n_free;
+  c.n_live = nd->n_live;
   c.n_instr = nd->n_instr;
   c.n_edge = nd->n_edge;
   c.n_box = nd->n_box;
@@ -2046,17 +2205,16 @@ __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg) {
   c.lookahead = nd->lookahead;
   c.q_head = nd->q_head;
   c.q_count = nd->q_count;
-  c.own = nd->own;
-  c.bst = nd->bst;
-  c.wr = nd->wr;
-  c.rd = nd->rd;
-  c.qr = nd->qr;
-  c.own.n = nd->tab_n[0];
-  c.bst.n = nd->tab_n[1];
-  c.wr.n = nd->tab_n[2];
-  c.rd.n = nd->tab_n[3];
-  c.qr.n = nd->tab_n[4];
-  for (int k = 0; k < 14; ++k) c.s[k] = nd->s[k];
+  c.qr.base = nd->qr_base;
+  c.qr.n = nd->qr_n;
+  c.qr.cap = nd->cap_qr;
+  c.qr.np = nullptr;
+  for (int k = 0; k < 14; ++k) {
+    c.s[k].base = nd->scratch_base + (size_t)k * nd->cap_scratch * F_COUNT;
+    c.s[k].n = 0;
+    c.s[k].cap = nd->cap_scratch;
+    c.s[k].np = nullptr;
+  }
   c.map_reads = 0;
   c.map_writes = 0;
 }
@@ -2072,6 +2230,8 @@ __device__ void store_ctx(Ctx& c, uint32_t cursor) {
   nd->last_sync = c.last_sync;
   nd->next_msg = c.next_msg;
   nd->n_alloc = c.n_alloc;
+  nd->n_free = c.n_free;
+  nd->n_live = c.n_live;
   nd->n_instr = c.n_instr;
   nd->n_edge = c.n_edge;
   nd->n_box = c.n_box;
@@ -2081,11 +2241,7 @@ __device__ void store_ctx(Ctx& c, uint32_t cursor) {
   nd->lookahead = c.lookahead;
   nd->q_head = c.q_head;
   nd->q_count = c.q_count;
-  nd->tab_n[0] = c.own.n;
-  nd->tab_n[1] = c.bst.n;
-  nd->tab_n[2] = c.wr.n;
-  nd->tab_n[3] = c.rd.n;
-  nd->tab_n[4] = c.qr.n;
+  nd->qr_n = c.qr.n;
   nd->map_reads += c.map_reads;
   nd->map_writes += c.map_writes;
   nd->launches += 1;
@@ -2102,10 +2258,12 @@ __global__ void __launch_bounds__(128) lower_kernel(const Unit* units, uint32_t 
   const uint32_t avail = *u.prog->n_items;
   uint32_t end = avail;
   if (max_items != NONE && cursor + max_items < end) end = cursor + max_items;
+  PhaseTimer pt = pt_start();
   while (cursor < end && c.err == ST_OK) {
     deliver(c, cursor);
     ++cursor;
   }
+  pt_lap(pt, c, PH_TOTAL);
   store_ctx(c, cursor);
 }
 

@@ -26,7 +26,7 @@ LOOKAHEAD_INFINITE = 0xFFFFFFFF
 EXPORTS = ("igs_create", "igs_destroy", "igs_create_buffer", "igs_destroy_buffer", "igs_submit_task",
            "igs_set_lookahead", "igs_flush", "igs_sync", "igs_fetch_instructions", "igs_rejected_tasks",
            "igs_execute", "igs_read_buffer", "igs_lower_batch", "igs_counters", "igs_last_error", "igs_box_copy",
-           "igs_set_timing", "igs_stats")
+           "igs_set_timing", "igs_stats", "igs_profile")
 
 
 class IgsError(RuntimeError):
@@ -92,6 +92,7 @@ def lib():
         L.igs_box_copy.argtypes = [ctypes.POINTER(CopyJob), u32, vp]
         L.igs_set_timing.argtypes = [vp, ctypes.c_int]
         L.igs_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.igs_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         _lib = L
     return _lib
 
@@ -225,6 +226,17 @@ def _set_timing(self, on: bool = True):
     self._check(lib().igs_set_timing(self._h, 1 if on else 0), "set_timing")
 
 
+PHASES = ("split", "overlap", "push_await", "allocating", "alloc", "push", "receive", "coherence", "kernel",
+          "remote", "sync_emit", "sync_apply", "total")
+
+
+def _profile(self) -> dict:
+    c = (ctypes.c_uint64 * 16)()
+    self._check(lib().igs_profile(self._h, c), "profile")
+    return {name: int(c[i]) for i, name in enumerate(PHASES)}
+
+
+Context.profile = _profile
 Context.stats = _stats
 Context.set_timing = _set_timing
 

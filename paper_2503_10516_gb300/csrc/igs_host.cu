@@ -259,10 +259,14 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
   const size_t o_bst = take(table_bytes(cap_bmap) * cap_buffers);
   const size_t o_ownn = take(sizeof(uint32_t) * cap_buffers);
   const size_t o_bstn = take(sizeof(uint32_t) * cap_buffers);
+  const size_t o_ownl = take(sizeof(uint32_t) * cap_buffers);
+  const size_t o_bstl = take(sizeof(uint32_t) * cap_buffers);
   const size_t o_wr = take(table_bytes(cap_amap) * cap_slots);
   const size_t o_rd = take(table_bytes(cap_amap) * cap_slots);
   const size_t o_wrn = take(sizeof(uint32_t) * cap_slots);
   const size_t o_rdn = take(sizeof(uint32_t) * cap_slots);
+  const size_t o_wrl = take(sizeof(uint32_t) * cap_slots);
+  const size_t o_rdl = take(sizeof(uint32_t) * cap_slots);
   const size_t o_free = take(sizeof(uint32_t) * cap_slots);
   const size_t o_live = take(sizeof(uint32_t) * cap_slots);
   const size_t o_qr = take(table_bytes(cap_qr));
@@ -319,10 +323,14 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
     nd.bst_base = reinterpret_cast<uint32_t*>(base + o_bst);
     nd.own_n = reinterpret_cast<uint32_t*>(base + o_ownn);
     nd.bst_n = reinterpret_cast<uint32_t*>(base + o_bstn);
+    nd.own_live = reinterpret_cast<uint32_t*>(base + o_ownl);
+    nd.bst_live = reinterpret_cast<uint32_t*>(base + o_bstl);
     nd.wr_base = reinterpret_cast<uint32_t*>(base + o_wr);
     nd.rd_base = reinterpret_cast<uint32_t*>(base + o_rd);
     nd.wr_n = reinterpret_cast<uint32_t*>(base + o_wrn);
     nd.rd_n = reinterpret_cast<uint32_t*>(base + o_rdn);
+    nd.wr_live = reinterpret_cast<uint32_t*>(base + o_wrl);
+    nd.rd_live = reinterpret_cast<uint32_t*>(base + o_rdl);
     nd.free_slots = reinterpret_cast<uint32_t*>(base + o_free);
     nd.live = reinterpret_cast<uint32_t*>(base + o_live);
     nd.qr_base = reinterpret_cast<uint32_t*>(base + o_qr);
@@ -345,6 +353,8 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
         cudaMemset(nd.has_succ, 0, 1) != cudaSuccess ||
         cudaMemset(nd.own_n, 0, sizeof(uint32_t) * cap_buffers) != cudaSuccess ||
         cudaMemset(nd.bst_n, 0, sizeof(uint32_t) * cap_buffers) != cudaSuccess ||
+        cudaMemset(nd.own_live, 0, sizeof(uint32_t) * cap_buffers) != cudaSuccess ||
+        cudaMemset(nd.bst_live, 0, sizeof(uint32_t) * cap_buffers) != cudaSuccess ||
         cudaMemcpy(nd.free_slots, slots.data(), sizeof(uint32_t) * cap_slots, cudaMemcpyHostToDevice) != cudaSuccess) {
       igs_destroy(c);
       return IGS_ERR_CUDA;

@@ -33,6 +33,8 @@ struct Table {
   uint32_t* base;  // F_COUNT * cap words
   uint32_t n, cap;
   uint32_t* np;    // persistent count of a slab table (nullptr for scratch tables)
+  uint32_t live;   // entries not marked dead
+  uint32_t* lp;    // persistent live count (nullptr for scratch tables)
 };
 
 struct AllocRec {
@@ -49,7 +51,7 @@ struct NodeDev {
   // scalars (owned by the warp; written back after every item)
   uint32_t status, cursor, lookahead, epoch, last_horizon, last_sync, next_msg, n_alloc;
   uint32_t n_instr, n_edge, n_box, n_bind, n_diag, n_rej;
-  uint32_t q_head, q_count, qr_n, n_free, n_live, pad0;
+  uint32_t q_head, q_count, qr_n, n_free, n_live, qr_live;
   uint64_t map_reads, map_writes, launches;
   uint64_t prof[16];   // clock cycles per lowering phase (see the engine)
   // capacities
@@ -58,13 +60,17 @@ struct NodeDev {
   // per-buffer slab tables: node-level ownership, local buffer state
   uint32_t* own_base;  // cap_buffers slabs of cap_bmap entries
   uint32_t* own_n;
+  uint32_t* own_live;
   uint32_t* bst_base;
   uint32_t* bst_n;
+  uint32_t* bst_live;
   // per-allocation slab tables: last writers, readers since the last write
   uint32_t* wr_base;   // cap_slots slabs of cap_amap entries
   uint32_t* wr_n;
+  uint32_t* wr_live;
   uint32_t* rd_base;
   uint32_t* rd_n;
+  uint32_t* rd_live;
   uint32_t* free_slots;
   uint32_t* live;      // ids of live allocations, ascending
   // per-task push and await regions (key = task sequence number)

@@ -201,8 +201,12 @@ __device__ __forceinline__ uint32_t t_claim(Ctx& c, Table& t, bool pred) {
     return NONE;
   }
   t.n = nn;
+  t.live += __popc(m);
   c.map_writes += __popc(m);
-  if (t.np && c.lane == 0) *t.np = nn;
+  if (t.np && c.lane == 0) {
+    *t.np = nn;
+    *t.lp = t.live;
+  }
   return pred ? slot : NONE;
 }
 // Claims k consecutive slots per lane; returns this lane's first slot.
@@ -220,9 +224,24 @@ __device__ __forceinline__ uint32_t t_claim_n(Ctx& c, Table& t, uint32_t k) {
     return NONE;
   }
   t.n += total;
+  t.live += total;
   c.map_writes += total;
-  if (t.np && c.lane == 0) *t.np = t.n;
+  if (t.np && c.lane == 0) {
+    *t.np = t.n;
+    *t.lp = t.live;
+  }
   return first;
+}
+
+__device__ __forceinline__ void t_reset(Table& t) {
+  t.n = 0;
+  t.live = 0;
+}
+
+// k entries of t were marked dead.
+__device__ __forceinline__ void t_dead(Ctx& c, Table& t, uint32_t k) {
+  t.live -= k;
+  if (t.lp && c.lane == 0) *t.lp = t.live;
 }
 
 template <class P>
@@ -299,13 +318,17 @@ __device__ void t_compact(Ctx& c, Table& t) {
     __syncwarp();
   }
   t.n = w;
-  if (t.np && c.lane == 0) *t.np = w;
+  t.live = w;
+  if (t.np && c.lane == 0) {
+    *t.np = w;
+    *t.lp = w;
+  }
   __syncwarp();
 }
 
-// Compacts a persistent slab table once more than half of it is used.
+// Compacts a table once its dead entries outnumber the live ones.
 __device__ __forceinline__ void t_tidy(Ctx& c, Table& t) {
-  if (t.np && t.n > t.cap / 2) t_compact(c, t);
+  if (t.n > 2 * t.live + 32) t_compact(c, t);
 }
 
 __device__ Bx t_bbox(const Ctx& c, const Table& t, uint32_t from, uint32_t to) {
@@ -378,6 +401,7 @@ __device__ void t_subtract(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t
     Bx pc[6];
     int np = 0;
     if (hit) np = bx_minus(e, r, pc);
+    t_dead(c, t, __popc(__ballot_sync(FULL, hit)));
     const uint32_t first = t_claim_n(c, t, hit ? (uint32_t)np : 0u);
     if (c.err) return;
     if (hit) {
@@ -407,6 +431,7 @@ __device__ void t_or(Ctx& c, Table& t, uint32_t key, const Bx& r, int vidx, uint
     Bx pc[6];
     int np = 0;
     if (hit) np = bx_minus(e, r, pc);
+    t_dead(c, t, __popc(__ballot_sync(FULL, hit)));
     const uint32_t first = t_claim_n(c, t, hit ? (uint32_t)np + 1 : 0u);
     if (c.err) return;
     if (hit) {
@@ -450,6 +475,7 @@ __device__ void t_merge_from(Ctx& c, Table& t, uint32_t from) {
         t_put(t, j, k, u, v0, v1, v2);
         t_kill(t, cand);
       }
+      t_dead(c, t, 1);
       __syncwarp();
       cand = j;
     }
@@ -482,6 +508,7 @@ __device__ void t_make_disjoint(Ctx& c, Table& t, uint32_t val = NONE) {
       Bx pc[6];
       int np = 0;
       if (hit) np = bx_minus(f, e, pc);
+      t_dead(c, t, __popc(__ballot_sync(FULL, hit)));
       const uint32_t first = t_claim_n(c, t, hit ? (uint32_t)np : 0u);
       if (c.err) return;
       if (hit) {
@@ -501,7 +528,7 @@ __device__ void t_make_disjoint(Ctx& c, Table& t, uint32_t val = NONE) {
 // rectangles over the slowest dimension.
 __device__ uint32_t canonical(Ctx& c, const Table& in, uint32_t from, uint32_t to, Table& out) {
   Table& W = c.s[S_CAN];
-  W.n = 0;
+  t_reset(W);
   for (uint32_t base = from; base < to; base += 32) {
     const uint32_t i = base + c.lane;
     bool live = false;
@@ -615,29 +642,31 @@ __device__ uint32_t canonical(Ctx& c, const Table& in, uint32_t from, uint32_t t
 
 // ---- node state helpers ----------------------------------------------------
 
-__device__ __forceinline__ Table slab(uint32_t* base, uint32_t* ns, uint32_t idx, uint32_t cap) {
+__device__ __forceinline__ Table slab(uint32_t* base, uint32_t* ns, uint32_t* ls, uint32_t idx, uint32_t cap) {
   __syncwarp();
   Table t;
   t.base = base + (size_t)idx * cap * F_COUNT;
   t.n = ns[idx];
   t.cap = cap;
   t.np = ns + idx;
+  t.live = ls[idx];
+  t.lp = ls + idx;
   return t;
 }
 // Node-level ownership map of a buffer (owner node, replication mask).
 __device__ __forceinline__ Table own_t(const Ctx& c, uint32_t b) {
-  return slab(c.nd->own_base, c.nd->own_n, b, c.nd->cap_bmap);
+  return slab(c.nd->own_base, c.nd->own_n, c.nd->own_live, b, c.nd->cap_bmap);
 }
 // Local state of a buffer (original producer, its memory, up-to-date memories).
 __device__ __forceinline__ Table bst_t(const Ctx& c, uint32_t b) {
-  return slab(c.nd->bst_base, c.nd->bst_n, b, c.nd->cap_bmap);
+  return slab(c.nd->bst_base, c.nd->bst_n, c.nd->bst_live, b, c.nd->cap_bmap);
 }
 // Last writers / readers since the last write of an allocation.
 __device__ __forceinline__ Table wr_t(const Ctx& c, uint32_t aid) {
-  return slab(c.nd->wr_base, c.nd->wr_n, c.nd->allocs[aid].slot, c.nd->cap_amap);
+  return slab(c.nd->wr_base, c.nd->wr_n, c.nd->wr_live, c.nd->allocs[aid].slot, c.nd->cap_amap);
 }
 __device__ __forceinline__ Table rd_t(const Ctx& c, uint32_t aid) {
-  return slab(c.nd->rd_base, c.nd->rd_n, c.nd->allocs[aid].slot, c.nd->cap_amap);
+  return slab(c.nd->rd_base, c.nd->rd_n, c.nd->rd_live, c.nd->allocs[aid].slot, c.nd->cap_amap);
 }
 
 // Registers a new allocation record with an empty writer / reader slab.
@@ -663,6 +692,8 @@ __device__ bool new_alloc(Ctx& c, uint32_t aid, uint32_t b, uint32_t m, const Bx
     c.nd->allocs[aid] = rec;
     c.nd->wr_n[slot] = 0;
     c.nd->rd_n[slot] = 0;
+    c.nd->wr_live[slot] = 0;
+    c.nd->rd_live[slot] = 0;
     c.nd->live[c.n_live] = aid;  // ids grow: the list stays sorted
   }
   c.n_live += 1;
@@ -734,7 +765,7 @@ __device__ Bx buffer_box(const BufDesc& b) {
 
 // a1: chunks of a task: key = chunk index, v0 = node, v1 = memory (Sec. 3.1).
 __device__ void task_chunks(Ctx& c, const igs_task& t, Table& CH) {
-  CH.n = 0;
+  t_reset(CH);
   const uint64_t E0 = t.range[0], C = t.num_chunks, M = (uint64_t)c.N * c.D;
   for (uint32_t base = 0; base < t.num_chunks; base += 32) {
     const uint32_t i = base + c.lane;
@@ -853,7 +884,7 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
   if (c.err) return NONE;
   NodeDev* nd = c.nd;
   Table& D = c.s[S_DEP];
-  if (!keep_dep) D.n = 0;
+  if (!keep_dep) t_reset(D);
   const uint32_t id = c.n_instr;
   for (int k = 0; k < nacc; ++k) {
     const Acc& A = acc[k];
@@ -1104,7 +1135,7 @@ __device__ void apply_epoch(Ctx& c, uint32_t h) {
 // Free of an allocation: depends on every writer and reader (allocation lifetime).
 __device__ void emit_free(Ctx& c, uint32_t seq, uint32_t aid) {
   Table& D = c.s[S_DEP];
-  D.n = 0;
+  t_reset(D);
   for (int k = 0; k < 2; ++k) {
     const Table T = k == 0 ? wr_t(c, aid) : rd_t(c, aid);
     for (uint32_t base = 0; base < T.n; base += 32) {
@@ -1134,8 +1165,8 @@ __device__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_t m, uint32_t
   Table& P = c.s[S_T2];
   Table& CP = c.s[S_T3];
   Table& CN = c.s[S_T5];
-  Q.n = 0;
-  CP.n = 0;
+  t_reset(Q);
+  t_reset(CP);
   {
     const Table B = bst_t(c, b);
     for (uint32_t r = from; r < to; ++r) {
@@ -1169,7 +1200,7 @@ __device__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_t m, uint32_t
       fail(c, ST_INTERNAL);
       return;
     }
-    G.n = 0;
+    t_reset(G);
     for (uint32_t base = 0; base < Q.n; base += 32) {
       const uint32_t i = base + c.lane;
       const bool hit = i < Q.n && t_v(Q, 0, i) == prod && t_v(Q, 1, i) == pmem;
@@ -1182,7 +1213,7 @@ __device__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_t m, uint32_t
       const uint32_t src = c.nd->live[li];
       const AllocRec a = c.nd->allocs[src];
       if (a.buffer != b || a.mem != pmem) continue;
-      P.n = 0;
+      t_reset(P);
       const Bx ab = alloc_box(a);
       for (uint32_t base = 0; base < G.n; base += 32) {
         const uint32_t i = base + c.lane;
@@ -1198,7 +1229,7 @@ __device__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_t m, uint32_t
       }
       __syncwarp();
       if (P.n == 0) continue;
-      CN.n = 0;
+      t_reset(CN);
       canonical(c, P, 0, P.n, CN);
       if (c.err) return;
       Acc acc[2] = {{&CN, 0, CN.n, src, IGS_READ}, {&CN, 0, CN.n, dst, IGS_WRITE}};
@@ -1227,6 +1258,40 @@ __device__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_t m, uint32_t
 
 // ---- a3: push / await push (node level) ------------------------------------
 
+// NB[m] = bounding box of node m's chunks (key DEAD if it has none). The
+// chunks of a node are consecutive along the split dimension, so this box is
+// exactly their union.
+__device__ void node_bboxes(Ctx& c, const Table& CH, Table& NB) {
+  for (uint32_t m = 0; m < c.N; ++m) {
+    Bx acc;
+    acc.lo[0] = acc.lo[1] = acc.lo[2] = 0xFFFFFFFFu;
+    acc.hi[0] = acc.hi[1] = acc.hi[2] = 0;
+    bool any = false;
+    for (uint32_t base = 0; base < CH.n; base += 32) {
+      const uint32_t i = base + c.lane;
+      const bool in = i < CH.n && t_v(CH, 0, i) == m;
+      Bx b{};
+      if (in) b = t_box(CH, i);
+      acc = bx_union(acc, warp_bbox(b, in));
+      any = any || __ballot_sync(FULL, in) != 0;
+    }
+    if (c.lane == 0) t_put(NB, m, any ? 0u : DEAD, acc, 0, 0, 0);
+  }
+  NB.n = c.N;
+  __syncwarp();
+}
+
+// The union over a node's chunks of an accessor's mapped boxes is the mapped
+// box of the node's chunk range when at most one buffer dimension follows
+// kernel dimension 0 (the per-chunk images are then consecutive intervals in
+// that dimension and equal in the others).
+__device__ __forceinline__ bool union_is_image(const igs_accessor& a, const BufDesc& buf) {
+  int k = 0;
+  for (int d = 0; d < (int)buf.dims; ++d)
+    if (a.dim[d].kind == IGS_MAP_AFFINE && a.dim[d].a == 0) ++k;
+  return k <= 1;
+}
+
 // Per buffer: missing_m = reads of node m's chunks not replicated on m; this
 // node awaits missing_node and pushes missing_m n owned(node) to every m.
 // Results go to the QR table under key seq: v0 = 0 push boxes, 1 await boxes,
@@ -1237,6 +1302,8 @@ __device__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH
   Table& MISS = c.s[S_T1];
   Table& PT = c.s[S_T2];
   Table& CN = c.s[S_T3];
+  Table& NB = c.s[S_T4];
+  node_bboxes(c, CH, NB);
   uint32_t done = 0;  // bitmask over accessor indices whose buffer was handled
   for (;;) {
     // next buffer in ascending order
@@ -1246,18 +1313,26 @@ __device__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH
     if (b == NONE) break;
     for (uint32_t a = 0; a < na; ++a)
       if (t.acc[a].buffer == b) done |= 1u << a;
-    MISS.n = 0;
+    t_reset(MISS);
+    const BufDesc& bd = buf_of(c, b);
     for (uint32_t m = 0; m < c.N; ++m) {
-      TMP.n = 0;
-      for (uint32_t slot = 0; slot < CH.n; ++slot) {
-        if (t_v(CH, 0, slot) != m) continue;
-        for (uint32_t a = 0; a < na; ++a) {
-          if (t.acc[a].buffer != b || !(t.acc[a].mode & IGS_READ)) continue;
-          const Bx x = t_box(MP, slot * na + a);
-          if (bx_empty(x)) continue;
-          t_query(c, own_t(c, b), NONE, x, TMP, [m](uint32_t, uint32_t repl, uint32_t) { return !((repl >> m) & 1u); });
-          if (c.err) return;
+      t_reset(TMP);
+      if (t_key(NB, m) == DEAD) continue;
+      const Table O = own_t(c, b);
+      auto lacking = [m](uint32_t, uint32_t repl, uint32_t) { return !((repl >> m) & 1u); };
+      for (uint32_t a = 0; a < na; ++a) {
+        if (t.acc[a].buffer != b || !(t.acc[a].mode & IGS_READ)) continue;
+        if (union_is_image(t.acc[a], bd)) {
+          const Bx x = map_box(t.acc[a], t_box(NB, m), bd);
+          if (!bx_empty(x)) t_query(c, O, NONE, x, TMP, lacking);
+        } else {
+          for (uint32_t slot = 0; slot < CH.n; ++slot) {
+            if (t_v(CH, 0, slot) != m) continue;
+            const Bx x = t_box(MP, slot * na + a);
+            if (!bx_empty(x)) t_query(c, O, NONE, x, TMP, lacking);
+          }
         }
+        if (c.err) return;
       }
       t_make_disjoint(c, TMP);
       if (c.err) return;
@@ -1273,7 +1348,7 @@ __device__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH
     // this node's await (canonical) and bbox
     {
       Table& sel = TMP;
-      sel.n = 0;
+      t_reset(sel);
       for (uint32_t base = 0; base < MISS.n; base += 32) {
         const uint32_t i = base + c.lane;
         const bool hit = i < MISS.n && t_v(MISS, 0, i) == c.node;
@@ -1283,7 +1358,7 @@ __device__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH
       }
       __syncwarp();
       if (sel.n) {
-        CN.n = 0;
+        t_reset(CN);
         canonical(c, sel, 0, sel.n, CN);
         if (c.err) return;
         const Bx bb = t_bbox(c, CN, 0, CN.n);
@@ -1303,7 +1378,7 @@ __device__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH
     // this node's pushes to every other node
     for (uint32_t m = 0; m < c.N; ++m) {
       if (m == c.node) continue;
-      PT.n = 0;
+      t_reset(PT);
       for (uint32_t i = 0; i < MISS.n; ++i) {
         if (t_v(MISS, 0, i) != m) continue;
         const uint32_t me = c.node;
@@ -1311,7 +1386,7 @@ __device__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH
         if (c.err) return;
       }
       if (PT.n == 0) continue;
-      CN.n = 0;
+      t_reset(CN);
       canonical(c, PT, 0, PT.n, CN);
       if (c.err) return;
       const Bx bb = t_bbox(c, CN, 0, CN.n);
@@ -1336,15 +1411,22 @@ __device__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH
       if (c.err) return;
     }
     // writes: owner = writing node, replicated there only
-    for (uint32_t slot = 0; slot < CH.n; ++slot) {
-      const uint32_t wn = t_v(CH, 0, slot);
-      for (uint32_t a = 0; a < na; ++a) {
-        if (t.acc[a].buffer != b || !(t.acc[a].mode & IGS_WRITE)) continue;
-        const Bx x = t_box(MP, slot * na + a);
-        if (bx_empty(x)) continue;
-        t_set(c, O, NONE, x, wn, 1u << wn, 0);
-        if (c.err) return;
+    for (uint32_t a = 0; a < na; ++a) {
+      if (t.acc[a].buffer != b || !(t.acc[a].mode & IGS_WRITE)) continue;
+      if (union_is_image(t.acc[a], bd)) {
+        for (uint32_t wn = 0; wn < c.N; ++wn) {
+          if (t_key(NB, wn) == DEAD) continue;
+          const Bx x = map_box(t.acc[a], t_box(NB, wn), bd);
+          if (!bx_empty(x)) t_set(c, O, NONE, x, wn, 1u << wn, 0);
+        }
+      } else {
+        for (uint32_t slot = 0; slot < CH.n; ++slot) {
+          const uint32_t wn = t_v(CH, 0, slot);
+          const Bx x = t_box(MP, slot * na + a);
+          if (!bx_empty(x)) t_set(c, O, NONE, x, wn, 1u << wn, 0);
+        }
       }
+      if (c.err) return;
     }
     t_merge_from(c, O, from);
   }
@@ -1405,7 +1487,7 @@ __device__ void requirements(Ctx& c, const igs_task& t, uint32_t seq, const Tabl
 
 __device__ bool allocating(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP) {
   Table& RQ = c.s[S_CL];
-  RQ.n = 0;
+  t_reset(RQ);
   requirements(c, t, seq, CH, MP, RQ, NONE, 1);
   if (c.err) return false;
   for (uint32_t base = 0; base < RQ.n; base += 32) {
@@ -1427,7 +1509,7 @@ __device__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq, const Table
   Table& MP2 = c.s[S_MP2];
   Table& Q = c.s[S_T0];
   Table& CN = c.s[S_T5];
-  RQ.n = 0;
+  t_reset(RQ);
   requirements(c, t, seq, CH, MP, RQ, NONE, 1);
   if (c.err) return;
   uint32_t last_key = NONE;
@@ -1449,7 +1531,7 @@ __device__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq, const Table
     const uint32_t key = (uint32_t)best;
     last_key = key;
     const uint32_t b = key >> 5, m = key & 31u;
-    CL.n = 0;
+    t_reset(CL);
     for (uint32_t base = 0; base < RQ.n; base += 32) {
       const uint32_t i = base + c.lane;
       bool hit = false;
@@ -1604,7 +1686,7 @@ __device__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq, const Table
       }
       // the absorbed allocations, ascending (the live list changes as they are freed)
       Table& AB = c.s[S_T3];
-      AB.n = 0;
+      t_reset(AB);
       for (uint32_t base = 0; base < c.n_live; base += 32) {
         const uint32_t x = base + c.lane;
         const bool hit = x < c.n_live && L[x] != aid && A[L[x]].mark == ci;
@@ -1615,11 +1697,11 @@ __device__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq, const Table
       __syncwarp();
       for (uint32_t ai = 0; ai < AB.n; ++ai) {
         const uint32_t old = TP(AB, F_V)[ai];
-        Q.n = 0;
+        t_reset(Q);
         t_query(c, bst_t(c, b), NONE, alloc_box(A[old]), Q,
                 [m](uint32_t, uint32_t, uint32_t mask) { return ((mask >> m) & 1u) != 0; });
         if (c.err) return;
-        CN.n = 0;
+        t_reset(CN);
         canonical(c, Q, 0, Q.n, CN);
         if (c.err) return;
         if (CN.n) {
@@ -1674,7 +1756,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
       return;
     }
     // copy the push region into RG (coherence uses the scratch tables)
-    RG.n = 0;
+    t_reset(RG);
     for (uint32_t base = g0; base < g1; base += 32) {
       const uint32_t i = base + c.lane;
       const bool in = i < g1;
@@ -1686,7 +1768,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
     coherence(c, seq, b, 1, dst, RG, 0, RG.n);
     if (c.err) return;
     // sends: one per (original producer, canonical box)
-    Q.n = 0;
+    t_reset(Q);
     {
       const Table B = bst_t(c, b);
       for (uint32_t r = 0; r < RG.n; ++r) {
@@ -1711,7 +1793,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
       if (best == ~0ull) break;
       first_round = false;
       last = best;
-      G.n = 0;
+      t_reset(G);
       for (uint32_t base = 0; base < Q.n; base += 32) {
         const uint32_t i = base + c.lane;
         const bool hit = i < Q.n && (((uint64_t)t_v(Q, 0, i) << 32) | t_v(Q, 1, i)) == best;
@@ -1720,7 +1802,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
         if (hit) t_put(G, s, 0, t_box(Q, i), 0, 0, 0);
       }
       __syncwarp();
-      CN.n = 0;
+      t_reset(CN);
       canonical(c, G, 0, G.n, CN);
       if (c.err) return;
       for (uint32_t i = 0; i < CN.n; ++i) {
@@ -1751,7 +1833,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
       fail(c, ST_INTERNAL);
       return;
     }
-    RG.n = 0;
+    t_reset(RG);
     uint64_t wvol = 0;
     for (uint32_t base = g0; base < g1; base += 32) {
       const uint32_t i = base + c.lane;
@@ -1763,7 +1845,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
     __syncwarp();
     for (uint32_t i = 0; i < RG.n; ++i) wvol += bx_volume(t_box(RG, i));
     // consumers in (chunk, accessor) order: v0 = consumer index
-    CONS.n = 0;
+    t_reset(CONS);
     uint32_t ncons = 0;
     bool whole = true;
     for (uint32_t slot = 0; slot < CH.n; ++slot) {
@@ -1811,10 +1893,10 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
       Acc acc[1] = {{&RG, 0, RG.n, dst, IGS_WRITE}};
       const uint32_t sid = emit(c, IGS_SPLIT_RECEIVE, seq, dst, NONE, b, NONE, &RG, 0, RG.n, acc, 1, false);
       if (c.err) return;
-      COV.n = 0;
+      t_reset(COV);
       for (uint32_t k = 0; k < ncons; ++k) {
         // part = consumer k's region minus what earlier await receives cover
-        G.n = 0;
+        t_reset(G);
         for (uint32_t base = 0; base < CONS.n; base += 32) {
           const uint32_t i = base + c.lane;
           const bool hit = i < CONS.n && t_v(CONS, 0, i) == k;
@@ -1827,12 +1909,12 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
           t_subtract(c, G, NONE, t_box(COV, i));
           if (c.err) return;
         }
-        CN.n = 0;
+        t_reset(CN);
         canonical(c, G, 0, G.n, CN);
         if (c.err) return;
         if (CN.n == 0) continue;
         Table& D = c.s[S_DEP];
-        D.n = 0;
+        t_reset(D);
         if (c.lane == 0) {
           TP(D, F_V)[0] = sid;
           TP(D, F_V + 1)[0] = IGS_DEP_DATAFLOW;
@@ -1902,7 +1984,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
         fail(c, ST_INTERNAL);
         return;
       }
-      RG.n = 0;
+      t_reset(RG);
       {
         const uint32_t s = t_claim(c, RG, c.lane == 0);
         if (c.err) return;
@@ -1919,7 +2001,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
   for (uint32_t slot = 0; slot < CH.n; ++slot) {
     if (t_v(CH, 0, slot) != c.node) continue;
     const uint32_t mem = t_v(CH, 1, slot);
-    BT.n = 0;
+    t_reset(BT);
     Acc acc[IGS_MAX_ACCESSORS];
     int nacc = 0;
     for (uint32_t a = 0; a < na; ++a) {
@@ -1956,18 +2038,28 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
   }
   pt_lap(pt, c, PH_P5);
   // writes of other nodes make the local copies stale
+  Table& NB = c.s[S_T4];
+  node_bboxes(c, CH, NB);
   for (uint32_t a = 0; a < na; ++a) {
     if (!(t.acc[a].mode & IGS_WRITE)) continue;
+    const BufDesc& bd = buf_of(c, t.acc[a].buffer);
     Table B = bst_t(c, t.acc[a].buffer);
     t_tidy(c, B);
     const uint32_t from = B.n;
-    for (uint32_t slot = 0; slot < CH.n; ++slot) {
-      if (t_v(CH, 0, slot) == c.node) continue;
-      const Bx x = t_box(MP, slot * na + a);
-      if (bx_empty(x)) continue;
-      t_set(c, B, NONE, x, REMOTE, 0, 0);
-      if (c.err) return;
+    if (union_is_image(t.acc[a], bd)) {
+      for (uint32_t m = 0; m < c.N; ++m) {
+        if (m == c.node || t_key(NB, m) == DEAD) continue;
+        const Bx x = map_box(t.acc[a], t_box(NB, m), bd);
+        if (!bx_empty(x)) t_set(c, B, NONE, x, REMOTE, 0, 0);
+      }
+    } else {
+      for (uint32_t slot = 0; slot < CH.n; ++slot) {
+        if (t_v(CH, 0, slot) == c.node) continue;
+        const Bx x = t_box(MP, slot * na + a);
+        if (!bx_empty(x)) t_set(c, B, NONE, x, REMOTE, 0, 0);
+      }
     }
+    if (c.err) return;
     t_merge_from(c, B, from);
   }
   // the task's push / await regions are consumed
@@ -1975,6 +2067,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
     const uint32_t i = base + c.lane;
     if (i < qe) t_kill(c.qr, i);
   }
+  t_dead(c, c.qr, qe - qs);
   __syncwarp();
   pt_lap(pt, c, PH_REMOTE);
 }
@@ -1991,7 +2084,10 @@ __device__ void process(Ctx& c, uint32_t item) {
         fail(c, ST_CAPACITY);
         return;
       }
-      if (c.lane == 0) c.nd->bst_n[it.arg] = 0;
+      if (c.lane == 0) {
+        c.nd->bst_n[it.arg] = 0;
+        c.nd->bst_live[it.arg] = 0;
+      }
       __syncwarp();
       Table B = bst_t(c, it.arg);
       if (bd.init) {
@@ -2019,7 +2115,7 @@ __device__ void process(Ctx& c, uint32_t item) {
     case IT_HORIZON:
     case IT_EPOCH: {
       Table& D = c.s[S_DEP];
-      D.n = 0;
+      t_reset(D);
       for (uint32_t base = c.last_sync; base < c.n_instr; base += 32) {
         const uint32_t i = base + c.lane;
         const bool f = i < c.n_instr && !c.nd->has_succ[i];
@@ -2050,7 +2146,7 @@ __device__ void process(Ctx& c, uint32_t item) {
     case IT_DESTROY: {
       const uint32_t b = it.arg;
       Table& AB = c.s[S_T3];
-      AB.n = 0;
+      t_reset(AB);
       for (uint32_t base = 0; base < c.n_live; base += 32) {
         const uint32_t x = base + c.lane;
         const bool hit = x < c.n_live && c.nd->allocs[c.nd->live[x]].buffer == b;
@@ -2071,7 +2167,10 @@ __device__ void process(Ctx& c, uint32_t item) {
             drop_alloc(c, aid);
           }
         }
-      if (c.lane == 0) c.nd->bst_n[b] = 0;
+      if (c.lane == 0) {
+        c.nd->bst_n[b] = 0;
+        c.nd->bst_live[b] = 0;
+      }
       __syncwarp();
       break;
     }
@@ -2106,9 +2205,7 @@ __device__ void enqueue(Ctx& c, uint32_t item) {
   __syncwarp();
 }
 
-__device__ void maintain(Ctx& c) {
-  if (c.qr.n > c.qr.cap / 4) t_compact(c, c.qr);
-}
+__device__ void maintain(Ctx& c) { t_tidy(c, c.qr); }
 
 // Scheduler lookahead (Sec. 4.3): a task is queued while an allocating task
 // is queued; the queue is compiled when it holds more than `lookahead` tasks,
@@ -2128,7 +2225,10 @@ __device__ void deliver(Ctx& c, uint32_t item) {
       return;
     }
     const BufDesc& bd = buf_of(c, it.arg);
-    if (c.lane == 0) c.nd->own_n[it.arg] = 0;
+    if (c.lane == 0) {
+      c.nd->own_n[it.arg] = 0;
+      c.nd->own_live[it.arg] = 0;
+    }
     __syncwarp();
     Table O = own_t(c, it.arg);
     const uint32_t s = t_claim(c, O, c.lane == 0);
@@ -2176,7 +2276,10 @@ __device__ void deliver(Ctx& c, uint32_t item) {
   }
   if (c.err) return;
   if (it.kind == IT_DESTROY) {
-    if (c.lane == 0) c.nd->own_n[it.arg] = 0;
+    if (c.lane == 0) {
+      c.nd->own_n[it.arg] = 0;
+      c.nd->own_live[it.arg] = 0;
+    }
     __syncwarp();
   }
 }
@@ -2209,11 +2312,15 @@ __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg) {
   c.qr.n = nd->qr_n;
   c.qr.cap = nd->cap_qr;
   c.qr.np = nullptr;
+  c.qr.live = nd->qr_live;
+  c.qr.lp = nullptr;
   for (int k = 0; k < 14; ++k) {
     c.s[k].base = nd->scratch_base + (size_t)k * nd->cap_scratch * F_COUNT;
     c.s[k].n = 0;
     c.s[k].cap = nd->cap_scratch;
     c.s[k].np = nullptr;
+    c.s[k].live = 0;
+    c.s[k].lp = nullptr;
   }
   c.map_reads = 0;
   c.map_writes = 0;
@@ -2242,6 +2349,7 @@ __device__ void store_ctx(Ctx& c, uint32_t cursor) {
   nd->q_head = c.q_head;
   nd->q_count = c.q_count;
   nd->qr_n = c.qr.n;
+  nd->qr_live = c.qr.live;
   nd->map_reads += c.map_reads;
   nd->map_writes += c.map_writes;
   nd->launches += 1;

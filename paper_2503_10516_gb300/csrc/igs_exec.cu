@@ -252,8 +252,71 @@ __global__ void __launch_bounds__(256) workload_kernel(const KernelJob* __restri
   }
 }
 
+// 5-point stencils (Jacobi, wave) over whole chunks: one job per block row
+// (blockIdx.y), four consecutive columns per thread with 16-byte loads and
+// stores; the host has checked that the read allocation covers the chunk plus
+// its one-element halo (clamped to the buffer) and the others cover the chunk.
+__global__ void __launch_bounds__(256) stencil_kernel(const KernelJob* __restrict__ jobs) {
+  const KernelJob& J = jobs[blockIdx.y];
+  const bool wave = J.kernel == K_WAVE;
+  const KAcc& U = J.acc[wave ? 1 : 0];
+  const KAcc& O = J.acc[wave ? 2 : 1];
+  const KAcc& P = J.acc[0];
+  const uint32_t H = U.ext[0], W = U.ext[1];
+  const uint32_t y0 = J.lo[0], y1 = J.hi[0], x0 = J.lo[1], x1 = J.hi[1];
+  const uint32_t uw = U.hi[1] - U.lo[1], ow = O.hi[1] - O.lo[1], pw = P.hi[1] - P.lo[1];
+  const float* u = reinterpret_cast<const float*>(U.ptr);
+  const float* pv = reinterpret_cast<const float*>(P.ptr);
+  float* o = reinterpret_cast<float*>(O.ptr);
+  const uint32_t groups = (x1 - x0 + 3) / 4;
+  const uint64_t total = (uint64_t)(y1 - y0) * groups;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t y = y0 + (uint32_t)(g / groups);
+    const uint32_t xs = x0 + 4 * (uint32_t)(g % groups);
+    const float* ur = u + (size_t)(y - U.lo[0]) * uw - U.lo[1];
+    const float* urn = y > 0 ? u + (size_t)(y - 1 - U.lo[0]) * uw - U.lo[1] : ur;
+    const float* urs = y + 1 < H ? u + (size_t)(y + 1 - U.lo[0]) * uw - U.lo[1] : ur;
+    const float* pr = wave ? pv + (size_t)(y - P.lo[0]) * pw - P.lo[1] : nullptr;
+    float* orow = o + (size_t)(y - O.lo[0]) * ow - O.lo[1];
+    float out[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t x = xs + k;
+      if (x >= x1) break;
+      const float c = ur[x];
+      float v = c;
+      if (y > 0 && y + 1 < H && x > 0 && x + 1 < W) {
+        const float n = urn[x], s = urs[x], w = ur[x - 1], e = ur[x + 1];
+        if (!wave) {
+          v = ((n + s) + (w + e)) * 0.25f;
+        } else {
+          const float t2 = (2.0f * c) - pr[x];
+          const float t5 = (n + s) + (w + e);
+          const float t8 = 0.25f * (t5 - 4.0f * c);
+          v = t2 + t8;
+        }
+      }
+      out[k] = v;
+    }
+    if (xs + 4 <= x1 && ((reinterpret_cast<uintptr_t>(orow + xs) & 15u) == 0)) {
+      *reinterpret_cast<float4*>(orow + xs) = make_float4(out[0], out[1], out[2], out[3]);
+    } else {
+      for (int k = 0; k < 4 && xs + k < x1; ++k) orow[xs + k] = out[k];
+    }
+  }
+}
+
 }  // namespace
 }  // namespace igs
+
+int igs_launch_stencil(const igs::KernelJob* jobs_dev, uint32_t n_jobs, uint64_t max_items, void* stream) {
+  if (n_jobs == 0) return 0;
+  const uint64_t per_job_blocks = (max_items / 4 + 255) / 256;
+  const uint32_t gx = (uint32_t)(per_job_blocks < 64 ? (per_job_blocks ? per_job_blocks : 1) : 64);
+  dim3 grid(gx, n_jobs);
+  igs::stencil_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(jobs_dev);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 
 int igs_launch_copies(const igs::CopyJob* jobs_dev, uint32_t n_jobs, uint64_t n_units, void* stream) {
   if (n_units == 0) return 0;

@@ -28,5 +28,7 @@ struct KernelJob {
 }  // namespace igs
 
 int igs_launch_workload(const igs::KernelJob* jobs_dev, uint32_t n_jobs, uint64_t n_items, void* stream);
+// 5-point stencil jobs (Jacobi / wave), pre-validated by the host; n_jobs <= 65535.
+int igs_launch_stencil(const igs::KernelJob* jobs_dev, uint32_t n_jobs, uint64_t max_items, void* stream);
 // Workload out-of-allocation flag (0 = none); optionally clears it.
 int igs_exec_error(bool clear);

@@ -36,7 +36,7 @@ struct NodeHost {
   std::vector<uint32_t> first_edge;  // per instruction: index of its first edge
   uint32_t executed = 1;             // instruction 0 is the initial epoch
   std::map<uint32_t, ExecAlloc> allocs;
-  std::vector<uint32_t> wave;        // wave id per instruction
+  std::vector<uint32_t> level;       // topological level per instruction (current execute call)
 };
 
 }  // namespace
@@ -70,7 +70,6 @@ struct igs_ctx {
   std::vector<NodeDev> nodes_host;  // layout templates (pointers), refreshed by downloads
   // executor
   std::vector<NodeHost> nh;
-  uint32_t wave_id = 1;
   CopyJob* d_cjobs = nullptr;
   uint32_t cap_cjobs = 0;
   KernelJob* d_kjobs = nullptr;
@@ -603,22 +602,25 @@ int igs_counters(igs_ctx* c, uint64_t out[8]) {
 
 namespace {
 
-// Work collected by one execute call: waves of independent box copies or
-// workload kernels, and frees, replayed in order after one upload.
-struct Action {
-  int kind;  // 0 copy wave, 1 kernel wave, 2 free
-  uint32_t first, count;
-  uint64_t units;
-  void* ptr;
+// Work of one execute call, by topological level: an instruction's level is
+// one more than the highest level among its predecessors if it launches work
+// (copies, receives, kernels), equal to it otherwise (allocs, sends, horizons,
+// epochs). Instructions of one level are mutually independent, so every level
+// costs at most one box-copy launch, one stencil launch and one workload
+// launch; frees follow the launches of their level.
+struct LevelWork {
+  std::vector<CopyJob> copies;
+  std::vector<KernelJob> kernels, stencils;
+  std::vector<void*> frees;
+  uint64_t copy_units = 0, kernel_items = 0, stencil_max = 0;
 };
 
 struct Pending {
-  std::vector<CopyJob> copies;
-  std::vector<KernelJob> kernels;
-  std::vector<Action> actions;
-  uint32_t wave_first = 0;
-  uint64_t copy_units = 0, kernel_items = 0;
-  bool open_copy = false, open_kernel = false;
+  std::vector<LevelWork> levels;
+  LevelWork& at(uint32_t L) {
+    if (levels.size() <= L) levels.resize(L + 1);
+    return levels[L];
+  }
 };
 
 // Collapses a box copy between two row-major allocations into rows of
@@ -678,74 +680,81 @@ bool make_copy_job(const uint8_t* src, const uint32_t slo[3], const uint32_t shi
 }
 
 // Closes the open wave (if any): later instructions that depend on it go to a new one.
-void close_wave(igs_ctx* c, Pending& p) {
-  if (p.open_copy) p.actions.push_back(Action{0, p.wave_first, (uint32_t)p.copies.size() - p.wave_first, p.copy_units, nullptr});
-  if (p.open_kernel)
-    p.actions.push_back(Action{1, p.wave_first, (uint32_t)p.kernels.size() - p.wave_first, p.kernel_items, nullptr});
-  p.open_copy = p.open_kernel = false;
-  p.copy_units = p.kernel_items = 0;
-  c->wave_id++;
-}
-
-void add_copy(igs_ctx* c, Pending& p, const CopyJob& J) {
-  if (p.open_kernel) close_wave(c, p);
-  if (!p.open_copy) {
-    p.open_copy = true;
-    p.wave_first = (uint32_t)p.copies.size();
-  }
+void add_copy(Pending& p, uint32_t L, const CopyJob& J) {
+  LevelWork& w = p.at(L);
   CopyJob j = J;
-  j.unit_begin = p.copy_units;
+  j.unit_begin = w.copy_units;
   const uint64_t segs = (j.extent[2] + j.seg_bytes - 1) / j.seg_bytes;
-  p.copy_units += (uint64_t)j.extent[0] * j.extent[1] * segs;
-  p.copies.push_back(j);
+  w.copy_units += (uint64_t)j.extent[0] * j.extent[1] * segs;
+  w.copies.push_back(j);
 }
 
-void add_kernel(igs_ctx* c, Pending& p, KernelJob J, uint64_t items) {
-  if (p.open_copy) close_wave(c, p);
-  if (!p.open_kernel) {
-    p.open_kernel = true;
-    p.wave_first = (uint32_t)p.kernels.size();
+void add_kernel(Pending& p, uint32_t L, KernelJob J, uint64_t items, bool stencil) {
+  LevelWork& w = p.at(L);
+  if (stencil) {
+    w.stencils.push_back(J);
+    w.stencil_max = std::max(w.stencil_max, items);
+    return;
   }
-  J.item_begin = p.kernel_items;
-  p.kernel_items += items;
-  p.kernels.push_back(J);
+  J.item_begin = w.kernel_items;
+  w.kernel_items += items;
+  w.kernels.push_back(J);
 }
 
-// Uploads every job once and replays the actions on the stream.
+// Uploads every job once and launches level by level on the stream.
 int run_pending(igs_ctx* c, Pending& p) {
-  close_wave(c, p);
+  std::vector<CopyJob> cj;
+  std::vector<KernelJob> kj;
+  std::vector<size_t> co(p.levels.size()), ko(p.levels.size()), so(p.levels.size());
+  for (size_t L = 0; L < p.levels.size(); ++L) {
+    co[L] = cj.size();
+    cj.insert(cj.end(), p.levels[L].copies.begin(), p.levels[L].copies.end());
+    ko[L] = kj.size();
+    kj.insert(kj.end(), p.levels[L].kernels.begin(), p.levels[L].kernels.end());
+    so[L] = kj.size();
+    kj.insert(kj.end(), p.levels[L].stencils.begin(), p.levels[L].stencils.end());
+  }
   int r;
-  if (!p.copies.empty()) {
-    if ((r = grow_device(c, c->d_cjobs, c->cap_cjobs, (uint32_t)p.copies.size(), 0))) return r;
-    CK(cudaMemcpyAsync(c->d_cjobs, p.copies.data(), sizeof(CopyJob) * p.copies.size(), cudaMemcpyHostToDevice, c->stream));
+  if (!cj.empty()) {
+    if ((r = grow_device(c, c->d_cjobs, c->cap_cjobs, (uint32_t)cj.size(), 0))) return r;
+    CK(cudaMemcpyAsync(c->d_cjobs, cj.data(), sizeof(CopyJob) * cj.size(), cudaMemcpyHostToDevice, c->stream));
   }
-  if (!p.kernels.empty()) {
-    if ((r = grow_device(c, c->d_kjobs, c->cap_kjobs, (uint32_t)p.kernels.size(), 0))) return r;
-    CK(cudaMemcpyAsync(c->d_kjobs, p.kernels.data(), sizeof(KernelJob) * p.kernels.size(), cudaMemcpyHostToDevice, c->stream));
+  if (!kj.empty()) {
+    if ((r = grow_device(c, c->d_kjobs, c->cap_kjobs, (uint32_t)kj.size(), 0))) return r;
+    CK(cudaMemcpyAsync(c->d_kjobs, kj.data(), sizeof(KernelJob) * kj.size(), cudaMemcpyHostToDevice, c->stream));
   }
-  for (const Action& a : p.actions) {
-    if (a.kind == 0) {
+  for (size_t L = 0; L < p.levels.size(); ++L) {
+    LevelWork& w = p.levels[L];
+    if (!w.copies.empty()) {
       const size_t ev = c->timing ? ev_begin(c) : 0;
-      if (igs_launch_copies(c->d_cjobs + a.first, a.count, a.units, c->stream)) return fail_ctx(c, IGS_ERR_CUDA, "box copy launch");
+      if (igs_launch_copies(c->d_cjobs + co[L], (uint32_t)w.copies.size(), w.copy_units, c->stream))
+        return fail_ctx(c, IGS_ERR_CUDA, "box copy launch");
       if (c->timing) ev_end(c, 1, ev);
       c->n_launch[1]++;
-    } else if (a.kind == 1) {
+      for (const CopyJob& j : w.copies) c->copy_bytes += 2.0 * j.extent[0] * j.extent[1] * j.extent[2];
+    }
+    for (size_t first = 0; first < w.stencils.size(); first += 65535) {
+      const uint32_t n = (uint32_t)std::min<size_t>(65535, w.stencils.size() - first);
       const size_t ev = c->timing ? ev_begin(c) : 0;
-      if (igs_launch_workload(c->d_kjobs + a.first, a.count, a.units, c->stream)) return fail_ctx(c, IGS_ERR_CUDA, "workload launch");
+      if (igs_launch_stencil(c->d_kjobs + so[L] + first, n, w.stencil_max, c->stream))
+        return fail_ctx(c, IGS_ERR_CUDA, "stencil launch");
       if (c->timing) ev_end(c, 2, ev);
       c->n_launch[2]++;
-    } else {
-      CK(cudaFreeAsync(a.ptr, c->stream));
     }
+    if (!w.kernels.empty()) {
+      const size_t ev = c->timing ? ev_begin(c) : 0;
+      if (igs_launch_workload(c->d_kjobs + ko[L], (uint32_t)w.kernels.size(), w.kernel_items, c->stream))
+        return fail_ctx(c, IGS_ERR_CUDA, "workload launch");
+      if (c->timing) ev_end(c, 2, ev);
+      c->n_launch[2]++;
+    }
+    for (void* f : w.frees) CK(cudaFreeAsync(f, c->stream));
   }
-  for (const CopyJob& j : p.copies) c->copy_bytes += 2.0 * j.extent[0] * j.extent[1] * j.extent[2];
   // the job arrays are reused by the next call
   CK(cudaStreamSynchronize(c->stream));
   ev_collect(c);
   if (igs_exec_error(true)) return fail_ctx(c, IGS_ERR_STATE, "a workload kernel accessed outside its allocation");
-  p.copies.clear();
-  p.kernels.clear();
-  p.actions.clear();
+  p.levels.clear();
   return IGS_OK;
 }
 
@@ -788,7 +797,7 @@ int fetch_for_exec(igs_ctx* c) {
     if (nd.n_bind > ok)
       CK(cudaMemcpy(h.binds.data() + ok, nd.binds + ok, sizeof(igs_binding) * (nd.n_bind - ok), cudaMemcpyDeviceToHost));
     h.first_edge.resize(nd.n_instr + 1, 0);
-    h.wave.resize(nd.n_instr, 0);
+    h.level.resize(nd.n_instr, 0);
     // edges are grouped by successor in emission order
     size_t e = oe;
     for (uint32_t i = (uint32_t)oi; i < nd.n_instr; ++i) {
@@ -800,15 +809,43 @@ int fetch_for_exec(igs_ctx* c) {
   return IGS_OK;
 }
 
-bool depends_on_wave(const igs_ctx* c, const NodeHost& h, uint32_t id) {
-  const uint32_t e0 = h.first_edge[id], e1 = h.first_edge[id + 1];
-  for (uint32_t e = e0; e < e1; ++e)
-    if (h.wave[h.edges[e].from] == c->wave_id) return true;
-  return false;
+uint32_t pred_level(const NodeHost& h, uint32_t id) {
+  uint32_t L = 0;
+  for (uint32_t e = h.first_edge[id]; e < h.first_edge[id + 1]; ++e) L = std::max(L, h.level[h.edges[e].from]);
+  return L;
+}
+
+bool box_in(const uint32_t lo[3], const uint32_t hi[3], const uint32_t blo[3], const uint32_t bhi[3]) {
+  for (int d = 0; d < 3; ++d)
+    if (blo[d] < lo[d] || bhi[d] > hi[d]) return false;
+  return true;
+}
+
+// A Jacobi / wave chunk whose allocations cover what the stencil touches can
+// run on the vectorized stencil kernel.
+bool stencil_ok(const igs_ctx* c, const KernelJob& J) {
+  if (J.kernel != K_JACOBI && J.kernel != K_WAVE) return false;
+  const uint32_t nu = J.kernel == K_WAVE ? 1 : 0, no = J.kernel == K_WAVE ? 2 : 1;
+  if (J.nacc != no + 1) return false;
+  for (uint32_t a = 0; a < J.nacc; ++a)
+    if (!J.acc[a].valid || J.acc[a].elem != 4 || J.acc[a].dims != 2) return false;
+  const KAcc& U = J.acc[nu];
+  uint32_t lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = J.lo[d];
+    hi[d] = J.hi[d];
+  }
+  if (!box_in(J.acc[no].lo, J.acc[no].hi, lo, hi)) return false;
+  if (J.kernel == K_WAVE && !box_in(J.acc[0].lo, J.acc[0].hi, lo, hi)) return false;
+  for (int d = 0; d < 2; ++d) {
+    lo[d] = lo[d] > 0 ? lo[d] - 1 : 0;
+    hi[d] = std::min(hi[d] + 1, U.ext[d]);
+  }
+  return box_in(U.lo, U.hi, lo, hi);
 }
 
 struct SendRec {
-  uint32_t node, alloc, wave;
+  uint32_t node, alloc, level;
   igs_box box;
 };
 
@@ -818,11 +855,12 @@ extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
   if (!c) return IGS_ERR_INVALID_ARG;
   int r = fetch_for_exec(c);
   if (r) return r;
-  // global order: by submission sequence; within it, every node's part up to
-  // its first receive, then the rest (sends precede the matching receives)
-  std::map<uint32_t, std::vector<std::pair<uint32_t, std::pair<uint32_t, uint32_t>>>> order;  // seq -> (node, [i0, i1))
+  // walk: by submission sequence; within one, every node's part up to its
+  // first receive, then the rest (sends precede the matching receives)
+  std::map<uint32_t, std::vector<std::pair<uint32_t, std::pair<uint32_t, uint32_t>>>> order;
   for (uint32_t n = 0; n < c->N; ++n) {
     NodeHost& h = c->nh[n];
+    std::fill(h.level.begin(), h.level.end(), 0u);  // earlier calls: complete
     uint32_t i = h.executed;
     while (i < h.instrs.size()) {
       const uint32_t s = h.instrs[i].seq;
@@ -850,10 +888,10 @@ extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
         const uint32_t a0 = half == 0 ? i0 : cut, a1 = half == 0 ? cut : i1;
         for (uint32_t i = a0; i < a1; ++i) {
           const igs_instruction& in = h.instrs[i];
-          const bool dep = depends_on_wave(c, h, i);
+          const uint32_t L = pred_level(h, i);
+          h.level[i] = L;
           switch (in.type) {
             case IGS_ALLOC: {
-              h.wave[i] = dep ? c->wave_id : 0;
               const igs_box& b = h.boxes[in.box_off];
               ExecAlloc a;
               a.buffer = in.c;
@@ -870,16 +908,14 @@ extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
               break;
             }
             case IGS_FREE: {
-              if (dep) close_wave(c, p);
               auto it = h.allocs.find(in.a);
               if (it != h.allocs.end()) {
-                if (!it->second.user) p.actions.push_back(Action{2, 0, 0, 0, it->second.ptr});
+                if (!it->second.user) p.at(L).frees.push_back(it->second.ptr);
                 h.allocs.erase(it);
               }
               break;
             }
             case IGS_COPY: {
-              if (dep) close_wave(c, p);
               ExecAlloc* s = get_alloc(c, n, in.a, in.c);
               ExecAlloc* d = get_alloc(c, n, in.b, in.c);
               if (!s || !d) return fail_ctx(c, IGS_ERR_STATE, "copy between unknown allocations");
@@ -887,9 +923,9 @@ extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
                 CopyJob J{};
                 if (!make_copy_job(s->ptr, s->lo, s->hi, d->ptr, d->lo, d->hi, h.boxes[in.box_off + k], c->bufs[in.c].elem, J))
                   return fail_ctx(c, IGS_ERR_STATE, "bad copy box");
-                add_copy(c, p, J);
+                add_copy(p, L + 1, J);
               }
-              h.wave[i] = c->wave_id;
+              h.level[i] = L + 1;
               break;
             }
             case IGS_SEND: {
@@ -897,18 +933,15 @@ extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
               sr.node = n;
               sr.alloc = in.a;
               sr.box = h.boxes[in.box_off];
-              sr.wave = dep ? c->wave_id : 0;
+              sr.level = L;
               sends.insert({key_of(in.seq, in.c, in.b), sr});
-              h.wave[i] = sr.wave;
               break;
             }
             case IGS_RECEIVE:
             case IGS_SPLIT_RECEIVE: {
               auto range = sends.equal_range(key_of(in.seq, in.c, n));
-              bool need_flush = dep;
-              for (auto it = range.first; it != range.second; ++it)
-                if (it->second.wave == c->wave_id) need_flush = true;
-              if (need_flush) close_wave(c, p);
+              uint32_t Lr = L;
+              for (auto it = range.first; it != range.second; ++it) Lr = std::max(Lr, it->second.level);
               ExecAlloc* d = get_alloc(c, n, in.a, in.c);
               if (!d) return fail_ctx(c, IGS_ERR_STATE, "receive into unknown allocation");
               for (auto it = range.first; it != range.second; ++it) {
@@ -917,22 +950,13 @@ extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
                 CopyJob J{};
                 if (!make_copy_job(s->ptr, s->lo, s->hi, d->ptr, d->lo, d->hi, it->second.box, c->bufs[in.c].elem, J))
                   return fail_ctx(c, IGS_ERR_STATE, "bad send box");
-                add_copy(c, p, J);
+                add_copy(p, Lr + 1, J);
               }
               sends.erase(range.first, range.second);
-              h.wave[i] = c->wave_id;
+              h.level[i] = Lr + 1;
               break;
             }
-            case IGS_AWAIT_RECEIVE:
-              h.wave[i] = h.wave[in.b];
-              break;
-            case IGS_HORIZON:
-            case IGS_EPOCH:
-              // no work of its own, but ordered after everything it waits for
-              h.wave[i] = dep ? c->wave_id : 0;
-              break;
             case IGS_KERNEL: {
-              if (dep) close_wave(c, p);
               if (in.seq >= c->seq_task.size() || c->seq_task[in.seq] == NONE)
                 return fail_ctx(c, IGS_ERR_STATE, "kernel of unknown task");
               const igs_task& t = c->tasks[c->seq_task[in.seq]];
@@ -971,11 +995,11 @@ extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
                   A.valid = 1;
                 }
               }
-              if (J.kernel != K_NOP && items) add_kernel(c, p, J, items);
-              h.wave[i] = c->wave_id;
+              if (J.kernel != K_NOP && items) add_kernel(p, L + 1, J, items, stencil_ok(c, J));
+              h.level[i] = L + 1;
               break;
             }
-            default:
+            default:  // await receive, horizon, epoch: no work of their own
               break;
           }
         }
@@ -1058,7 +1082,7 @@ extern "C" int igs_read_buffer(igs_ctx* c, uint32_t b, const uint32_t lo[3], con
     if (e.v[0] == HOST) {
       CopyJob J{};
       uint32_t blo[3] = {0, 0, 0}, bhi[3] = {bf.extent[0], bf.extent[1], bf.extent[2]};
-      if (make_copy_job(c->init_dev[b], blo, bhi, stage, rl, rh, piece, bf.elem, J)) add_copy(c, p, J);
+      if (make_copy_job(c->init_dev[b], blo, bhi, stage, rl, rh, piece, bf.elem, J)) add_copy(p, 1, J);
       continue;
     }
     if (e.v[0] >= c->N) continue;  // never written
@@ -1078,7 +1102,7 @@ extern "C" int igs_read_buffer(igs_ctx* c, uint32_t b, const uint32_t lo[3], con
         igs_box z;
         if (!isect(A.lo, A.hi, q.lo, q.hi, z)) continue;
         CopyJob J{};
-        if (make_copy_job(A.ptr, A.lo, A.hi, stage, rl, rh, z, bf.elem, J)) add_copy(c, p, J);
+        if (make_copy_job(A.ptr, A.lo, A.hi, stage, rl, rh, z, bf.elem, J)) add_copy(p, 1, J);
       }
     }
   }

@@ -351,6 +351,7 @@ __device__ Bx t_bbox(const Ctx& c, const Table& t, uint32_t from, uint32_t to) {
 template <class P>
 __device__ void t_query(Ctx& c, const Table& src, uint32_t key, const Bx& q, Table& out, P pred) {
   const uint32_t n = src.n;
+  c.map_reads += n;
   for (uint32_t base = 0; base < n; base += 32) {
     const uint32_t i = base + c.lane;
     bool hit = false;
@@ -368,7 +369,6 @@ __device__ void t_query(Ctx& c, const Table& src, uint32_t key, const Bx& q, Tab
         }
       }
     }
-    c.map_reads += warp_sum(hit ? 1u : 0u);
     const uint32_t s = t_claim(c, out, hit);
     if (c.err) return;
     if (hit) t_put(out, s, 0, is, v0, v1, v2);
@@ -894,6 +894,7 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
       // writers
       {
         const Table T = wr_t(c, A.alloc);
+        c.map_reads += T.n;
         for (uint32_t base = 0; base < T.n; base += 32) {
           const uint32_t i = base + c.lane;
           bool hit = false;
@@ -904,7 +905,6 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
             if (instr_type(c, w) == IGS_ALLOC) kind = IGS_DEP_ALLOC;
             else kind = ((A.mode & IGS_READ) ? IGS_DEP_DATAFLOW : 0u) | ((A.mode & IGS_WRITE) ? IGS_DEP_ANTI : 0u);
           }
-          c.map_reads += warp_sum(hit ? 1u : 0u);
           const uint32_t s = t_claim(c, D, hit);
           if (c.err) return NONE;
           if (hit) {
@@ -915,10 +915,10 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
       }
       if (A.mode & IGS_WRITE) {
         const Table T = rd_t(c, A.alloc);
+        c.map_reads += T.n;
         for (uint32_t base = 0; base < T.n; base += 32) {
           const uint32_t i = base + c.lane;
           bool hit = i < T.n && t_key(T, i) != DEAD && bx_overlap(t_box(T, i), q);
-          c.map_reads += warp_sum(hit ? 1u : 0u);
           const uint32_t s = t_claim(c, D, hit);
           if (c.err) return NONE;
           if (hit) {
@@ -941,8 +941,47 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
   // unique predecessors in ascending order, kinds OR-ed
   const uint32_t nd0 = D.n;
   uint32_t n_unique = 0;
-  {
-    // count firsts
+  if (nd0 <= 32) {
+    // one entry per lane: group equal predecessors, then a bitonic sort of
+    // the group leaders by predecessor id
+    const bool in = c.lane < nd0;
+    const uint32_t p = in ? TP(D, F_V)[c.lane] : 0xFFFFFFFFu;
+    const uint32_t k = in ? TP(D, F_V + 1)[c.lane] : 0u;
+    bool lead = in;
+    uint32_t kind = 0;
+    for (int j = 0; j < 32; ++j) {
+      const uint32_t pj = __shfl_sync(FULL, p, j), kj = __shfl_sync(FULL, k, j);
+      if (pj == p) {
+        kind |= kj;
+        if (j < (int)c.lane) lead = false;
+      }
+    }
+    uint64_t key = lead ? (((uint64_t)p << 32) | kind) : ~0ull;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        const uint64_t other = __shfl_xor_sync(FULL, key, stride);
+        const bool up = ((c.lane & size) == 0);
+        const bool lower = (c.lane & stride) == 0;
+        const bool take_min = (lower == up);
+        key = take_min ? (other < key ? other : key) : (other < key ? key : other);
+      }
+    }
+    n_unique = __popc(__ballot_sync(FULL, lead));
+    if (c.n_edge + n_unique > nd->cap_edge || c.n_instr + 1 > nd->cap_instr) {
+      fail(c, ST_CAPACITY);
+      return NONE;
+    }
+    if (c.lane < n_unique) {
+      igs_edge e;
+      e.from = (uint32_t)(key >> 32);
+      e.to = id;
+      e.kind = (uint32_t)key;
+      nd->edges[c.n_edge + c.lane] = e;
+      nd->has_succ[e.from] = 1;
+    }
+  } else {
     for (uint32_t base = 0; base < nd0; base += 32) {
       const uint32_t i = base + c.lane;
       bool first = false;
@@ -957,39 +996,39 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
       }
       n_unique += __popc(__ballot_sync(FULL, first));
     }
-  }
-  if (c.n_edge + n_unique > nd->cap_edge || c.n_instr + 1 > nd->cap_instr) {
-    fail(c, ST_CAPACITY);
-    return NONE;
-  }
-  for (uint32_t base = 0; base < nd0; base += 32) {
-    const uint32_t i = base + c.lane;
-    if (i < nd0) {
-      const uint32_t p = TP(D, F_V)[i];
-      bool first = true;
-      uint32_t kind = 0, rank = 0;
-      for (uint32_t j = 0; j < nd0; ++j) {
-        const uint32_t q = TP(D, F_V)[j];
-        if (q == p) {
-          kind |= TP(D, F_V + 1)[j];
-          if (j < i) first = false;
-        } else if (q < p) {
-          bool qfirst = true;
-          for (uint32_t x = 0; x < j; ++x)
-            if (TP(D, F_V)[x] == q) {
-              qfirst = false;
-              break;
-            }
-          if (qfirst) ++rank;
+    if (c.n_edge + n_unique > nd->cap_edge || c.n_instr + 1 > nd->cap_instr) {
+      fail(c, ST_CAPACITY);
+      return NONE;
+    }
+    for (uint32_t base = 0; base < nd0; base += 32) {
+      const uint32_t i = base + c.lane;
+      if (i < nd0) {
+        const uint32_t p = TP(D, F_V)[i];
+        bool first = true;
+        uint32_t kind = 0, rank = 0;
+        for (uint32_t j = 0; j < nd0; ++j) {
+          const uint32_t q = TP(D, F_V)[j];
+          if (q == p) {
+            kind |= TP(D, F_V + 1)[j];
+            if (j < i) first = false;
+          } else if (q < p) {
+            bool qfirst = true;
+            for (uint32_t x = 0; x < j; ++x)
+              if (TP(D, F_V)[x] == q) {
+                qfirst = false;
+                break;
+              }
+            if (qfirst) ++rank;
+          }
         }
-      }
-      if (first) {
-        igs_edge e;
-        e.from = p;
-        e.to = id;
-        e.kind = kind;
-        nd->edges[c.n_edge + rank] = e;
-        nd->has_succ[p] = 1;
+        if (first) {
+          igs_edge e;
+          e.from = p;
+          e.to = id;
+          e.kind = kind;
+          nd->edges[c.n_edge + rank] = e;
+          nd->has_succ[p] = 1;
+        }
       }
     }
   }
@@ -1071,7 +1110,7 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
       if (c.lane == 0) t_put(RD, s, 0, q, id, 0, 0);
       __syncwarp();
     }
-    t_merge_from(c, RD, from);
+    (void)from;
   }
   for (int k = 0; k < nacc; ++k) {
     const Acc& A = acc[k];
@@ -1087,7 +1126,7 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
       t_set(c, WR, NONE, q, id, 0, 0);
       if (c.err) return NONE;
     }
-    t_merge_from(c, WR, from);
+    (void)from;
   }
   return id;
 }
@@ -2029,11 +2068,8 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
       const Bx x = t_box(MP, slot * na + a);
       if (!(t.acc[a].mode & IGS_WRITE) || bx_empty(x)) continue;
       Table B = bst_t(c, t.acc[a].buffer);
-      t_tidy(c, B);
-      const uint32_t from = B.n;
       t_set(c, B, NONE, x, kid, mem, 1u << mem);
       if (c.err) return;
-      t_merge_from(c, B, from);
     }
   }
   pt_lap(pt, c, PH_P5);

@@ -258,6 +258,49 @@ typedef struct igs_copy_job {
  * device. Jobs must not overlap in their destinations. */
 int igs_box_copy(const igs_copy_job* jobs, uint32_t n, void* stream);
 
+/* ---- lowering without allocation ------------------------------------------
+ * The paper has no counterpart to this entry point. It exists for callers that
+ * cannot allocate device memory themselves: a runtime whose device memory all
+ * comes from its own pool, or a latency-critical loop that must not enter the
+ * driver's allocator (which can block on or synchronize with other work on the
+ * device). igs_lower_static lowers a whole program (buffers, tasks, flushes,
+ * buffer destructions, lookahead changes, in `ops` order) on every node into
+ * caller-owned DEVICE output arrays, using a 32 MiB file-scope device array as
+ * its only scratch: it calls no cudaMalloc, cudaFree or other allocating
+ * routine. Every GPU that loads the library holds that array until exit.
+ *   Limits: at most 16 buffers; per node at most 128 live allocations, 512
+ *   entries in a buffer's region maps and 128 in an allocation's; the program's
+ *   staged inputs plus per-node state (about 2.7 MiB + instr_cap bytes per
+ *   node) must fit the array, else IGS_ERR_CAPACITY before anything runs.
+ *   Sharing: every call uses the same array and leaves its last contents there
+ *   (each call resets what must start at zero); calls that overlap on the GPU
+ *   race, so serialize them. The call returns after the lowering finished on
+ *   `stream` (cudaStream_t, NULL = default stream).
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Outputs: outs[n] for node n; counts (device, 6 words) receives the numbers
+ *   of instructions, edges, boxes, bindings, diagnostics, and the node's status
+ *   (0 = ok, 1 = a capacity was exceeded, 2 = internal error). */
+#define IGS_OP_CREATE_BUFFER 0u /* arg = buffer index (in creation order) */
+#define IGS_OP_TASK 1u          /* arg = index into tasks */
+#define IGS_OP_FLUSH 2u         /* an epoch */
+#define IGS_OP_DESTROY_BUFFER 3u
+#define IGS_OP_LOOKAHEAD 4u     /* arg = window */
+typedef struct igs_static_buffer { uint32_t dims, extent[3], elem_size, has_init; } igs_static_buffer;
+typedef struct igs_static_op { uint32_t kind, arg; } igs_static_op;
+typedef struct igs_static_output {
+  igs_instruction* instrs; uint32_t instr_cap;
+  igs_edge* edges;         uint32_t edge_cap;
+  igs_box* boxes;          uint32_t box_cap;
+  igs_binding* binds;      uint32_t bind_cap;
+  igs_diag* diags;         uint32_t diag_cap;
+  uint32_t* counts;
+} igs_static_output;
+int igs_lower_static(const igs_config* cfg, const igs_static_buffer* bufs, uint32_t num_buffers,
+                     const igs_task* tasks, uint32_t num_tasks, const igs_static_op* ops, uint32_t num_ops,
+                     igs_static_output* outs, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,7 @@ SOURCES = {
     "igs_lower.cu": [],
     "igs_exec.cu": ["-fmad=false"],
     "igs_host.cu": [],
+    "igs_static.cu": [],
 }
 
 

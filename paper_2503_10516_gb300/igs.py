@@ -26,7 +26,7 @@ LOOKAHEAD_INFINITE = 0xFFFFFFFF
 EXPORTS = ("igs_create", "igs_destroy", "igs_create_buffer", "igs_destroy_buffer", "igs_submit_task",
            "igs_set_lookahead", "igs_flush", "igs_sync", "igs_fetch_instructions", "igs_rejected_tasks",
            "igs_execute", "igs_read_buffer", "igs_lower_batch", "igs_counters", "igs_last_error", "igs_box_copy",
-           "igs_set_timing", "igs_stats", "igs_profile")
+           "igs_set_timing", "igs_stats", "igs_profile", "igs_lower_static")
 
 
 class IgsError(RuntimeError):
@@ -54,6 +54,24 @@ class GraphView(ctypes.Structure):
 
 class Box(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_uint32 * 3), ("hi", ctypes.c_uint32 * 3)]
+
+
+class StaticBuffer(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_uint32), ("extent", ctypes.c_uint32 * 3), ("elem_size", ctypes.c_uint32),
+                ("has_init", ctypes.c_uint32)]
+
+
+class StaticOp(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("arg", ctypes.c_uint32)]
+
+
+class StaticOutput(ctypes.Structure):
+    _fields_ = [("instrs", ctypes.c_void_p), ("instr_cap", ctypes.c_uint32),
+                ("edges", ctypes.c_void_p), ("edge_cap", ctypes.c_uint32),
+                ("boxes", ctypes.c_void_p), ("box_cap", ctypes.c_uint32),
+                ("binds", ctypes.c_void_p), ("bind_cap", ctypes.c_uint32),
+                ("diags", ctypes.c_void_p), ("diag_cap", ctypes.c_uint32),
+                ("counts", ctypes.c_void_p)]
 
 
 class CopyJob(ctypes.Structure):
@@ -93,6 +111,8 @@ def lib():
         L.igs_set_timing.argtypes = [vp, ctypes.c_int]
         L.igs_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.igs_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.igs_lower_static.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(StaticBuffer), u32, P32, u32,
+                                       ctypes.POINTER(StaticOp), u32, ctypes.POINTER(StaticOutput), vp]
         _lib = L
     return _lib
 
@@ -246,6 +266,45 @@ def lower_batch(ctxs: Sequence[Context]):
     r = lib().igs_lower_batch(arr, len(ctxs))
     if r not in (IGS_OK, -2):
         raise IgsError(r, "lower_batch")
+
+
+def lower_static(prog: W.Program, outs: Sequence[dict], stream: Optional[int] = None) -> int:
+    """Lowers a whole program through igs_lower_static (no allocation inside
+    the library). outs[n]: device pointers and capacities of node n's output
+    arrays: keys instrs, edges, boxes, binds, diags (pointer, capacity) and
+    counts (pointer to 6 device uint32 words)."""
+    bufs = prog.buffers
+    sb = (StaticBuffer * max(1, len(bufs)))()
+    for i, b in enumerate(bufs):
+        sb[i].dims, sb[i].elem_size, sb[i].has_init = b.dims, b.elem_size, int(b.init is not None)
+        for d in range(3):
+            sb[i].extent[d] = b.extent[d]
+    tasks = prog.tasks
+    words = np.concatenate([t.flat() for t in tasks]) if tasks else np.zeros(123, np.uint32)
+    words = np.ascontiguousarray(words, dtype=np.uint32)
+    ops, nb, nt = [], 0, 0
+    for op in prog.ops:
+        if op[0] == "buffer":
+            ops.append((0, nb)); nb += 1
+        elif op[0] == "task":
+            ops.append((1, nt)); nt += 1
+        elif op[0] == "flush":
+            ops.append((2, 0))
+        elif op[0] == "destroy":
+            ops.append((3, op[1]))
+        elif op[0] == "lookahead":
+            ops.append((4, op[1]))
+    so = (StaticOp * max(1, len(ops)))(*[StaticOp(k, a) for k, a in ops])
+    out = (StaticOutput * prog.nodes)()
+    for n, o in enumerate(outs):
+        out[n].instrs, out[n].instr_cap = o["instrs"]
+        out[n].edges, out[n].edge_cap = o["edges"]
+        out[n].boxes, out[n].box_cap = o["boxes"]
+        out[n].binds, out[n].bind_cap = o["binds"]
+        out[n].diags, out[n].diag_cap = o["diags"]
+        out[n].counts = o["counts"]
+    cfg = Config(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead, 0, 0, 0, 0, 0, 0, 0, None)
+    return lib().igs_lower_static(ctypes.byref(cfg), sb, len(bufs), _p32(words), len(tasks), so, len(ops), out, stream)
 
 
 def box_copy(jobs: Sequence[tuple], stream: Optional[int] = None):

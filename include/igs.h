@@ -237,7 +237,9 @@ int igs_stats(igs_ctx* ctx, double out[8]);
  * [3] allocating test, [4] allocations, [5] pushes and sends, [6] receives,
  * [7] coherence copies, [8] kernels, [9] remote-write bookkeeping,
  * [10] horizon / epoch emission, [11] horizon / epoch compaction, [12] total
- * inside the lowering kernel. */
+ * inside the lowering kernel; cycles spent inside [13] instruction emission,
+ * [14] canonical-form computation, [15] allocation lookup (these overlap the
+ * phases above). */
 int igs_profile(igs_ctx* ctx, uint64_t out[16]);
 
 const char* igs_last_error(const igs_ctx* ctx);

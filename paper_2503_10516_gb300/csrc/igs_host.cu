@@ -1025,17 +1025,18 @@ int read_slab(igs_ctx* c, const uint32_t* base, const uint32_t* counts, uint32_t
   uint32_t n = 0;
   CK(cudaMemcpy(&n, counts + idx, sizeof n, cudaMemcpyDeviceToHost));
   if (n == 0) return IGS_OK;
-  std::vector<uint32_t> raw((size_t)F_COUNT * cap);
+  std::vector<uint32_t> raw((size_t)F_COUNT * n);
   const uint32_t* t = base + (size_t)idx * cap * F_COUNT;
-  CK(cudaMemcpy(raw.data(), t, sizeof(uint32_t) * F_COUNT * cap, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(raw.data(), t, sizeof(uint32_t) * F_COUNT * n, cudaMemcpyDeviceToHost));
   for (uint32_t i = 0; i < n; ++i) {
+    const uint32_t* w = raw.data() + (size_t)i * F_COUNT;
     HEntry e;
-    e.key = raw[i];
+    e.key = w[F_KEY];
     for (int d = 0; d < 3; ++d) {
-      e.lo[d] = raw[(size_t)(F_LO + d) * cap + i];
-      e.hi[d] = raw[(size_t)(F_HI + d) * cap + i];
+      e.lo[d] = w[F_LO + d];
+      e.hi[d] = w[F_HI + d];
     }
-    for (int k = 0; k < 3; ++k) e.v[k] = raw[(size_t)(F_V + k) * cap + i];
+    for (int k = 0; k < 3; ++k) e.v[k] = w[F_V + k];
     if (e.key != DEAD) out.push_back(e);
   }
   return IGS_OK;

@@ -26,11 +26,12 @@ struct BufDesc {
 
 enum Status : uint32_t { ST_OK = 0, ST_CAPACITY = 1, ST_INTERNAL = 2, ST_TIMEOUT = 3 };
 
-// Field layout of a box table (structure of arrays, `cap` entries per field).
-enum TableField : int { F_KEY = 0, F_LO = 1, F_HI = 4, F_V = 7, F_COUNT = 10 };
+// Field layout of a box-table entry: 12 words (48 bytes, 16-byte aligned) so
+// an entry loads with three 16-byte vector loads; F_COUNT is the stride.
+enum TableField : int { F_KEY = 0, F_LO = 1, F_HI = 4, F_V = 7, F_COUNT = 12 };
 
 struct Table {
-  uint32_t* base;  // F_COUNT * cap words
+  uint32_t* base;  // cap entries of F_COUNT words
   uint32_t n, cap;
   uint32_t* np;    // persistent count of a slab table (nullptr for scratch tables)
   uint32_t live;   // entries not marked dead

@@ -129,31 +129,29 @@ __device__ __forceinline__ bool bx_mergeable(const Bx& a, const Bx& b) {
 
 // ---- tables ----------------------------------------------------------------
 
-__device__ __forceinline__ uint32_t* TP(const Table& t, int f) { return t.base + (size_t)f * t.cap; }
-__device__ __forceinline__ uint32_t t_key(const Table& t, uint32_t i) { return TP(t, F_KEY)[i]; }
-__device__ __forceinline__ uint32_t t_v(const Table& t, int k, uint32_t i) { return TP(t, F_V + k)[i]; }
+__device__ __forceinline__ uint32_t& FLD(const Table& t, int f, uint32_t i) { return t.base[(size_t)i * F_COUNT + f]; }
+__device__ __forceinline__ uint32_t t_key(const Table& t, uint32_t i) { return FLD(t, F_KEY, i); }
+__device__ __forceinline__ uint32_t t_v(const Table& t, int k, uint32_t i) { return FLD(t, F_V + k, i); }
 __device__ __forceinline__ Bx t_box(const Table& t, uint32_t i) {
-  Bx b;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    b.lo[d] = TP(t, F_LO + d)[i];
-    b.hi[d] = TP(t, F_HI + d)[i];
-  }
-  return b;
+  const uint4* e = reinterpret_cast<const uint4*>(t.base + (size_t)i * F_COUNT);
+  const uint4 a = e[0], b = e[1];
+  Bx r;
+  r.lo[0] = a.y;
+  r.lo[1] = a.z;
+  r.lo[2] = a.w;
+  r.hi[0] = b.x;
+  r.hi[1] = b.y;
+  r.hi[2] = b.z;
+  return r;
 }
 __device__ __forceinline__ void t_put(const Table& t, uint32_t i, uint32_t key, const Bx& b, uint32_t v0, uint32_t v1,
                                       uint32_t v2) {
-  TP(t, F_KEY)[i] = key;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    TP(t, F_LO + d)[i] = b.lo[d];
-    TP(t, F_HI + d)[i] = b.hi[d];
-  }
-  TP(t, F_V)[i] = v0;
-  TP(t, F_V + 1)[i] = v1;
-  TP(t, F_V + 2)[i] = v2;
+  uint4* e = reinterpret_cast<uint4*>(t.base + (size_t)i * F_COUNT);
+  e[0] = make_uint4(key, b.lo[0], b.lo[1], b.lo[2]);
+  e[1] = make_uint4(b.hi[0], b.hi[1], b.hi[2], v0);
+  e[2] = make_uint4(v1, v2, 0u, 0u);
 }
-__device__ __forceinline__ void t_kill(const Table& t, uint32_t i) { TP(t, F_KEY)[i] = DEAD; }
+__device__ __forceinline__ void t_kill(const Table& t, uint32_t i) { FLD(t, F_KEY, i) = DEAD; }
 
 struct Acc {
   const Table* t;
@@ -180,7 +178,7 @@ __device__ __forceinline__ void fail(Ctx& c, uint32_t code) {
 // Phase cycle accounting (lane 0 adds to the node's counters).
 enum Phase : int {
   PH_SPLIT = 0, PH_OVERLAP = 1, PH_A3 = 2, PH_ALLOCATING = 3, PH_P1 = 4, PH_P2 = 5, PH_P3 = 6, PH_P4 = 7,
-  PH_P5 = 8, PH_REMOTE = 9, PH_SYNC = 10, PH_APPLY = 11, PH_TOTAL = 12
+  PH_P5 = 8, PH_REMOTE = 9, PH_SYNC = 10, PH_APPLY = 11, PH_TOTAL = 12, PH_EMIT = 13, PH_CANON = 14, PH_FIND = 15
 };
 struct PhaseTimer {
   long long t0;
@@ -526,7 +524,14 @@ __device__ void t_make_disjoint(Ctx& c, Table& t, uint32_t val = NONE) {
 // fastest dimension maximal (splitting partially overlapping neighbours),
 // then merge identical intervals over the middle dimension, then identical
 // rectangles over the slowest dimension.
+__device__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_t from, uint32_t to, Table& out);
 __device__ uint32_t canonical(Ctx& c, const Table& in, uint32_t from, uint32_t to, Table& out) {
+  PhaseTimer pt = pt_start();
+  const uint32_t r = canonical_impl(c, in, from, to, out);
+  pt_lap(pt, c, PH_CANON);
+  return r;
+}
+__device__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_t from, uint32_t to, Table& out) {
   Table& W = c.s[S_CAN];
   t_reset(W);
   for (uint32_t base = from; base < to; base += 32) {
@@ -728,13 +733,15 @@ __device__ __forceinline__ Bx alloc_box(const AllocRec& a) {
 }
 
 // The live allocation of (buffer, memory) containing box, or NONE.
-__device__ uint32_t find_alloc(const Ctx& c, uint32_t buf, uint32_t mem, const Bx& b) {
+__device__ uint32_t find_alloc(Ctx& c, uint32_t buf, uint32_t mem, const Bx& b) {
+  PhaseTimer pt = pt_start();
   const AllocRec* A = c.nd->allocs;
   const uint32_t* L = c.nd->live;
   const uint32_t k = warp_find_first(c, c.n_live, [&](uint32_t i) {
     const AllocRec& a = A[L[i]];
     return a.buffer == buf && a.mem == mem && bx_contains(alloc_box(a), b);
   });
+  pt_lap(pt, c, PH_FIND);
   return k == NONE ? NONE : L[k];
 }
 
@@ -878,9 +885,20 @@ __device__ uint32_t instr_type(const Ctx& c, uint32_t id) { return c.nd->instrs[
 // writes, the readers since the last write (WAR anti); no predecessor at all
 // means an edge to the last epoch. Then reads, then writes are applied to
 // the per-allocation tracking tables.
+__device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint32_t fb, uint32_t fc, uint32_t fd,
+                              const Table* bt, uint32_t bfrom, uint32_t bto, const Acc* acc, int nacc, bool keep_dep,
+                              const Table* bindt, uint32_t bind_from, uint32_t bind_n);
 __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint32_t fb, uint32_t fc, uint32_t fd,
                          const Table* bt, uint32_t bfrom, uint32_t bto, const Acc* acc, int nacc, bool keep_dep,
                          const Table* bindt = nullptr, uint32_t bind_from = 0, uint32_t bind_n = 0) {
+  PhaseTimer pt = pt_start();
+  const uint32_t r = emit_impl(c, type, seq, fa, fb, fc, fd, bt, bfrom, bto, acc, nacc, keep_dep, bindt, bind_from, bind_n);
+  pt_lap(pt, c, PH_EMIT);
+  return r;
+}
+__device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint32_t fb, uint32_t fc, uint32_t fd,
+                              const Table* bt, uint32_t bfrom, uint32_t bto, const Acc* acc, int nacc, bool keep_dep,
+                              const Table* bindt, uint32_t bind_from, uint32_t bind_n) {
   if (c.err) return NONE;
   NodeDev* nd = c.nd;
   Table& D = c.s[S_DEP];
@@ -908,8 +926,8 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
           const uint32_t s = t_claim(c, D, hit);
           if (c.err) return NONE;
           if (hit) {
-            TP(D, F_V)[s] = w;
-            TP(D, F_V + 1)[s] = kind;
+            FLD(D, F_V, s) = w;
+            FLD(D, F_V + 1, s) = kind;
           }
         }
       }
@@ -922,8 +940,8 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
           const uint32_t s = t_claim(c, D, hit);
           if (c.err) return NONE;
           if (hit) {
-            TP(D, F_V)[s] = t_v(T, 0, i);
-            TP(D, F_V + 1)[s] = IGS_DEP_ANTI;
+            FLD(D, F_V, s) = t_v(T, 0, i);
+            FLD(D, F_V + 1, s) = IGS_DEP_ANTI;
           }
         }
       }
@@ -932,8 +950,8 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
   __syncwarp();
   if (D.n == 0) {
     if (c.lane == 0) {
-      TP(D, F_V)[0] = c.epoch;
-      TP(D, F_V + 1)[0] = IGS_DEP_EPOCH;
+      FLD(D, F_V, 0) = c.epoch;
+      FLD(D, F_V + 1, 0) = IGS_DEP_EPOCH;
     }
     D.n = 1;
     __syncwarp();
@@ -945,8 +963,8 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
     // one entry per lane: group equal predecessors, then a bitonic sort of
     // the group leaders by predecessor id
     const bool in = c.lane < nd0;
-    const uint32_t p = in ? TP(D, F_V)[c.lane] : 0xFFFFFFFFu;
-    const uint32_t k = in ? TP(D, F_V + 1)[c.lane] : 0u;
+    const uint32_t p = in ? FLD(D, F_V, c.lane) : 0xFFFFFFFFu;
+    const uint32_t k = in ? FLD(D, F_V + 1, c.lane) : 0u;
     bool lead = in;
     uint32_t kind = 0;
     for (int j = 0; j < 32; ++j) {
@@ -986,10 +1004,10 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
       const uint32_t i = base + c.lane;
       bool first = false;
       if (i < nd0) {
-        const uint32_t p = TP(D, F_V)[i];
+        const uint32_t p = FLD(D, F_V, i);
         first = true;
         for (uint32_t j = 0; j < i; ++j)
-          if (TP(D, F_V)[j] == p) {
+          if (FLD(D, F_V, j) == p) {
             first = false;
             break;
           }
@@ -1003,18 +1021,18 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
     for (uint32_t base = 0; base < nd0; base += 32) {
       const uint32_t i = base + c.lane;
       if (i < nd0) {
-        const uint32_t p = TP(D, F_V)[i];
+        const uint32_t p = FLD(D, F_V, i);
         bool first = true;
         uint32_t kind = 0, rank = 0;
         for (uint32_t j = 0; j < nd0; ++j) {
-          const uint32_t q = TP(D, F_V)[j];
+          const uint32_t q = FLD(D, F_V, j);
           if (q == p) {
-            kind |= TP(D, F_V + 1)[j];
+            kind |= FLD(D, F_V + 1, j);
             if (j < i) first = false;
           } else if (q < p) {
             bool qfirst = true;
             for (uint32_t x = 0; x < j; ++x)
-              if (TP(D, F_V)[x] == q) {
+              if (FLD(D, F_V, x) == q) {
                 qfirst = false;
                 break;
               }
@@ -1137,7 +1155,7 @@ __device__ void map_ids(Ctx& c, Table& T, uint32_t h) {
     const uint32_t i = base + c.lane;
     if (i < T.n && t_key(T, i) != DEAD) {
       const uint32_t v = t_v(T, 0, i);
-      if (v < h) TP(T, F_V)[i] = h;
+      if (v < h) FLD(T, F_V, i) = h;
     }
   }
   __syncwarp();
@@ -1183,8 +1201,8 @@ __device__ void emit_free(Ctx& c, uint32_t seq, uint32_t aid) {
       const uint32_t s = t_claim(c, D, hit);
       if (c.err) return;
       if (hit) {
-        TP(D, F_V)[s] = t_v(T, 0, i);
-        TP(D, F_V + 1)[s] = IGS_DEP_ALLOC;
+        FLD(D, F_V, s) = t_v(T, 0, i);
+        FLD(D, F_V + 1, s) = IGS_DEP_ALLOC;
       }
     }
   }
@@ -1604,7 +1622,7 @@ __device__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq, const Table
       __syncwarp();
       for (uint32_t base = from; base < CL.n; base += 32) {
         const uint32_t i = base + c.lane;
-        if (i < CL.n && t_key(CL, i) != DEAD) TP(CL, F_KEY)[i] = 0;
+        if (i < CL.n && t_key(CL, i) != DEAD) FLD(CL, F_KEY, i) = 0;
       }
       __syncwarp();
     }
@@ -1697,7 +1715,7 @@ __device__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq, const Table
         uint32_t rank = 0;
         for (uint32_t j = 0; j < n; ++j)
           if (j != i && t_key(CL, j) != DEAD && t_v(CL, 0, j) == 1 && bx_less(t_box(CL, j), bi)) ++rank;
-        TP(CL, F_V + 1)[i] = rank;
+        FLD(CL, F_V + 1, i) = rank;
       }
     }
     __syncwarp();
@@ -1731,11 +1749,11 @@ __device__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq, const Table
         const bool hit = x < c.n_live && L[x] != aid && A[L[x]].mark == ci;
         const uint32_t s = t_claim(c, AB, hit);
         if (c.err) return;
-        if (hit) TP(AB, F_V)[s] = L[x];
+        if (hit) FLD(AB, F_V, s) = L[x];
       }
       __syncwarp();
       for (uint32_t ai = 0; ai < AB.n; ++ai) {
-        const uint32_t old = TP(AB, F_V)[ai];
+        const uint32_t old = FLD(AB, F_V, ai);
         t_reset(Q);
         t_query(c, bst_t(c, b), NONE, alloc_box(A[old]), Q,
                 [m](uint32_t, uint32_t, uint32_t mask) { return ((mask >> m) & 1u) != 0; });
@@ -1955,8 +1973,8 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
         Table& D = c.s[S_DEP];
         t_reset(D);
         if (c.lane == 0) {
-          TP(D, F_V)[0] = sid;
-          TP(D, F_V + 1)[0] = IGS_DEP_DATAFLOW;
+          FLD(D, F_V, 0) = sid;
+          FLD(D, F_V + 1, 0) = IGS_DEP_DATAFLOW;
         }
         D.n = 1;
         __syncwarp();
@@ -2158,8 +2176,8 @@ __device__ void process(Ctx& c, uint32_t item) {
         const uint32_t s = t_claim(c, D, f);
         if (c.err) return;
         if (f) {
-          TP(D, F_V)[s] = i;
-          TP(D, F_V + 1)[s] = IGS_DEP_FRONT;
+          FLD(D, F_V, s) = i;
+          FLD(D, F_V + 1, s) = IGS_DEP_FRONT;
         }
       }
       __syncwarp();
@@ -2188,12 +2206,12 @@ __device__ void process(Ctx& c, uint32_t item) {
         const bool hit = x < c.n_live && c.nd->allocs[c.nd->live[x]].buffer == b;
         const uint32_t s = t_claim(c, AB, hit);
         if (c.err) return;
-        if (hit) TP(AB, F_V)[s] = c.nd->live[x];
+        if (hit) FLD(AB, F_V, s) = c.nd->live[x];
       }
       __syncwarp();
       for (uint32_t m = 0; m < 2 + c.D; ++m)
         for (uint32_t ai = 0; ai < AB.n; ++ai) {
-          const uint32_t aid = TP(AB, F_V)[ai];
+          const uint32_t aid = FLD(AB, F_V, ai);
           const AllocRec a = c.nd->allocs[aid];
           if (a.mem != m) continue;
           if (!a.user) {

@@ -247,7 +247,7 @@ def _set_timing(self, on: bool = True):
 
 
 PHASES = ("split", "overlap", "push_await", "allocating", "alloc", "push", "receive", "coherence", "kernel",
-          "remote", "sync_emit", "sync_apply", "total")
+          "remote", "sync_emit", "sync_apply", "total", "in_emit", "in_canonical", "in_find_alloc")
 
 
 def _profile(self) -> dict:

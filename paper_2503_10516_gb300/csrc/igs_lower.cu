@@ -904,46 +904,58 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
   Table& D = c.s[S_DEP];
   if (!keep_dep) t_reset(D);
   const uint32_t id = c.n_instr;
-  for (int k = 0; k < nacc; ++k) {
-    const Acc& A = acc[k];
-    for (uint32_t r = A.from; r < A.to; ++r) {
-      if (t_key(*A.t, r) == DEAD) continue;
-      const Bx q = t_box(*A.t, r);
-      // writers
-      {
-        const Table T = wr_t(c, A.alloc);
-        c.map_reads += T.n;
-        for (uint32_t base = 0; base < T.n; base += 32) {
-          const uint32_t i = base + c.lane;
-          bool hit = false;
-          uint32_t w = 0, kind = 0;
-          if (i < T.n && t_key(T, i) != DEAD && bx_overlap(t_box(T, i), q)) {
-            hit = true;
-            w = t_v(T, 0, i);
-            if (instr_type(c, w) == IGS_ALLOC) kind = IGS_DEP_ALLOC;
-            else kind = ((A.mode & IGS_READ) ? IGS_DEP_DATAFLOW : 0u) | ((A.mode & IGS_WRITE) ? IGS_DEP_ANTI : 0u);
+  // one probe per (access, region box, table): last writers for every access,
+  // readers for writes; then every probed entry in one lane-parallel pass
+  {
+    Table& PR = c.s[S_CAN];
+    t_reset(PR);
+    uint32_t total = 0;
+    for (int k = 0; k < nacc; ++k) {
+      const Acc& A = acc[k];
+      const uint32_t slot = nd->allocs[A.alloc].slot;
+      const uint32_t wn = nd->wr_n[slot], rn = nd->rd_n[slot];
+      for (uint32_t r = A.from; r < A.to; ++r) {
+        if (t_key(*A.t, r) == DEAD) continue;
+        const Bx q = t_box(*A.t, r);
+        for (int tab = 0; tab < ((A.mode & IGS_WRITE) ? 2 : 1); ++tab) {
+          if (PR.n >= PR.cap) {
+            fail(c, ST_CAPACITY);
+            return NONE;
           }
-          const uint32_t s = t_claim(c, D, hit);
-          if (c.err) return NONE;
-          if (hit) {
-            FLD(D, F_V, s) = w;
-            FLD(D, F_V + 1, s) = kind;
-          }
+          if (c.lane == 0) t_put(PR, PR.n, (uint32_t)tab, q, slot, total, A.mode);
+          PR.n += 1;
+          total += tab == 0 ? wn : rn;
         }
       }
-      if (A.mode & IGS_WRITE) {
-        const Table T = rd_t(c, A.alloc);
-        c.map_reads += T.n;
-        for (uint32_t base = 0; base < T.n; base += 32) {
-          const uint32_t i = base + c.lane;
-          bool hit = i < T.n && t_key(T, i) != DEAD && bx_overlap(t_box(T, i), q);
-          const uint32_t s = t_claim(c, D, hit);
-          if (c.err) return NONE;
-          if (hit) {
-            FLD(D, F_V, s) = t_v(T, 0, i);
-            FLD(D, F_V + 1, s) = IGS_DEP_ANTI;
-          }
+    }
+    __syncwarp();
+    c.map_reads += total;
+    const uint32_t np = PR.n;
+    for (uint32_t base = 0; base < total; base += 32) {
+      const uint32_t f = base + c.lane;
+      bool hit = false;
+      uint32_t w = 0, kind = 0;
+      if (f < total) {
+        uint32_t p = 0;
+        while (p + 1 < np && t_v(PR, 1, p + 1) <= f) ++p;
+        const uint32_t tab = t_key(PR, p), slot = t_v(PR, 0, p), mode = t_v(PR, 2, p);
+        Table T;
+        T.base = (tab == 0 ? nd->wr_base : nd->rd_base) + (size_t)slot * nd->cap_amap * F_COUNT;
+        T.cap = nd->cap_amap;
+        const uint32_t j = f - t_v(PR, 1, p);
+        if (t_key(T, j) != DEAD && bx_overlap(t_box(T, j), t_box(PR, p))) {
+          hit = true;
+          w = t_v(T, 0, j);
+          if (tab == 1) kind = IGS_DEP_ANTI;
+          else if (instr_type(c, w) == IGS_ALLOC) kind = IGS_DEP_ALLOC;
+          else kind = ((mode & IGS_READ) ? IGS_DEP_DATAFLOW : 0u) | ((mode & IGS_WRITE) ? IGS_DEP_ANTI : 0u);
         }
+      }
+      const uint32_t s = t_claim(c, D, hit);
+      if (c.err) return NONE;
+      if (hit) {
+        FLD(D, F_V, s) = w;
+        FLD(D, F_V + 1, s) = kind;
       }
     }
   }
@@ -2006,55 +2018,118 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
     g0 = g1 + 1;
   }
   pt_lap(pt, c, PH_P3);
-  // P4: coherence for every reading accessor, (chunk, accessor) order
-  for (uint32_t slot = 0; slot < CH.n; ++slot) {
-    if (t_v(CH, 0, slot) != c.node) continue;
-    const uint32_t mem = t_v(CH, 1, slot);
-    for (uint32_t a = 0; a < na; ++a) {
-      const igs_accessor& ac = t.acc[a];
-      if (!(ac.mode & IGS_READ)) continue;
-      const Bx x = t_box(MP, slot * na + a);
-      if (bx_empty(x)) continue;
-      // uninitialized read warning (Sec. 4.4)
-      const uint32_t b = ac.buffer;
-      const Table B = bst_t(c, b);
-      const uint32_t un = warp_find_first(c, B.n, [&](uint32_t i) {
-        return t_key(B, i) != DEAD && t_v(B, 0, i) == NONE && bx_overlap(t_box(B, i), x);
-      });
-      if (un != NONE) {
-        if (c.n_diag >= c.nd->cap_diag) {
-          fail(c, ST_CAPACITY);
-          return;
+  // P4: coherence for every reading accessor, (chunk, accessor) order.
+  // Pre-check, one lane per consumer: does its box overlap never-written data
+  // (bit 0) or data not up to date in its memory (bit 1)? Copies emitted in
+  // this phase only add up-to-date memories and leave producers unchanged, so
+  // a consumer with nothing stale now has nothing stale when its turn comes.
+  Table& PC = c.s[S_CL];
+  t_reset(PC);
+  {
+    const uint32_t total = CH.n * na;
+    for (uint32_t base = 0; base < total; base += 32) {
+      const uint32_t i = base + c.lane;
+      bool hit = false;
+      uint32_t flags = 0;
+      Bx x{};
+      if (i < total) {
+        const uint32_t slot = i / na, a = i % na;
+        if (t_v(CH, 0, slot) == c.node && (t.acc[a].mode & IGS_READ)) {
+          x = t_box(MP, i);
+          hit = !bx_empty(x);
+          if (hit) {
+            const uint32_t b = t.acc[a].buffer, m = t_v(CH, 1, slot);
+            Table B;
+            B.base = c.nd->bst_base + (size_t)b * c.nd->cap_bmap * F_COUNT;
+            B.n = c.nd->bst_n[b];
+            B.cap = c.nd->cap_bmap;
+            for (uint32_t j = 0; j < B.n; ++j) {
+              if (t_key(B, j) == DEAD || !bx_overlap(t_box(B, j), x)) continue;
+              const uint32_t prod = t_v(B, 0, j), mask = t_v(B, 2, j);
+              if (prod == NONE) flags |= 1u;
+              else if (!((mask >> m) & 1u)) flags |= 2u;
+            }
+          }
         }
-        if (c.lane == 0) {
-          igs_diag dg;
-          dg.seq = seq;
-          dg.chunk = t_key(CH, slot);
-          dg.accessor = a;
-          c.nd->diags[c.n_diag] = dg;
-        }
-        c.n_diag += 1;
-        __syncwarp();
       }
-      const uint32_t dst = find_alloc(c, b, mem, x);
-      if (dst == NONE) {
-        fail(c, ST_INTERNAL);
+      const uint32_t s = t_claim(c, PC, hit);
+      if (c.err) return;
+      if (hit) t_put(PC, s, flags, x, i, 0, 0);
+    }
+    __syncwarp();
+  }
+  for (uint32_t k = 0; k < PC.n; ++k) {
+    const uint32_t flags = t_key(PC, k), i = t_v(PC, 0, k);
+    if (!flags) continue;
+    const uint32_t slot = i / na, a = i % na;
+    const uint32_t mem = t_v(CH, 1, slot), b = t.acc[a].buffer;
+    const Bx x = t_box(PC, k);
+    if (flags & 1u) {  // uninitialized read warning (Sec. 4.4)
+      if (c.n_diag >= c.nd->cap_diag) {
+        fail(c, ST_CAPACITY);
         return;
       }
-      t_reset(RG);
-      {
-        const uint32_t s = t_claim(c, RG, c.lane == 0);
-        if (c.err) return;
-        if (c.lane == 0) t_put(RG, s, 0, x, 0, 0, 0);
-        __syncwarp();
+      if (c.lane == 0) {
+        igs_diag dg;
+        dg.seq = seq;
+        dg.chunk = t_key(CH, slot);
+        dg.accessor = a;
+        c.nd->diags[c.n_diag] = dg;
       }
-      coherence(c, seq, b, mem, dst, RG, 0, 1);
-      if (c.err) return;
+      c.n_diag += 1;
+      __syncwarp();
     }
+    if (!(flags & 2u)) continue;
+    const uint32_t dst = find_alloc(c, b, mem, x);
+    if (dst == NONE) {
+      fail(c, ST_INTERNAL);
+      return;
+    }
+    t_reset(RG);
+    {
+      const uint32_t s = t_claim(c, RG, c.lane == 0);
+      if (c.err) return;
+      if (c.lane == 0) t_put(RG, s, 0, x, 0, 0, 0);
+      __syncwarp();
+    }
+    coherence(c, seq, b, mem, dst, RG, 0, 1);
+    if (c.err) return;
   }
   pt_lap(pt, c, PH_P4);
-  // P5: one device kernel per local chunk
+  // P5: one device kernel per local chunk; every accessor's allocation is
+  // looked up first, one lane per (chunk, accessor)
   Table& BT = c.s[S_T4];
+  Table& AL = c.s[S_T5];
+  {
+    const uint32_t total = CH.n * na;
+    if (total > AL.cap) {
+      fail(c, ST_CAPACITY);
+      return;
+    }
+    const AllocRec* A = c.nd->allocs;
+    const uint32_t* L = c.nd->live;
+    for (uint32_t base = 0; base < total; base += 32) {
+      const uint32_t i = base + c.lane;
+      if (i < total) {
+        const uint32_t slot = i / na, a = i % na;
+        uint32_t al = NONE;
+        if (t_v(CH, 0, slot) == c.node) {
+          const Bx x = t_box(MP, i);
+          if (!bx_empty(x)) {
+            const uint32_t buf = t.acc[a].buffer, mem = t_v(CH, 1, slot);
+            for (uint32_t k = 0; k < c.n_live && al == NONE; ++k) {
+              const AllocRec& r = A[L[k]];
+              if (r.buffer == buf && r.mem == mem && bx_contains(alloc_box(r), x)) al = L[k];
+            }
+            if (al == NONE) al = NONE - 1;  // missing: an internal error
+          }
+        }
+        FLD(AL, F_KEY, i) = al;
+      }
+    }
+    AL.n = total;
+    __syncwarp();
+  }
   for (uint32_t slot = 0; slot < CH.n; ++slot) {
     if (t_v(CH, 0, slot) != c.node) continue;
     const uint32_t mem = t_v(CH, 1, slot);
@@ -2063,13 +2138,10 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
     int nacc = 0;
     for (uint32_t a = 0; a < na; ++a) {
       const Bx x = t_box(MP, slot * na + a);
-      uint32_t al = NONE;
-      if (!bx_empty(x)) {
-        al = find_alloc(c, t.acc[a].buffer, mem, x);
-        if (al == NONE) {
-          fail(c, ST_INTERNAL);
-          return;
-        }
+      const uint32_t al = FLD(AL, F_KEY, slot * na + a);
+      if (al == NONE - 1) {
+        fail(c, ST_INTERNAL);
+        return;
       }
       if (c.lane == 0) {
         Bx z{};

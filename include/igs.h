@@ -91,11 +91,16 @@ typedef struct igs_config {
   uint32_t horizon_step;     /* a horizon after every k submitted tasks; 0 = none (Sec. 3.5) */
   uint32_t lookahead;        /* scheduler lookahead window in tasks (Sec. 4.3); IGS_LOOKAHEAD_INFINITE */
   uint32_t mode;             /* IGS_MODE_PLAIN or IGS_MODE_BATCHED */
-  uint32_t max_instructions; /* per node output capacity; 0 = default (1 << 20) */
+  uint32_t max_instructions; /* per node output capacity; 0 = default (1 << 18) */
   uint32_t max_edges;        /* per node; 0 = default (4 x max_instructions) */
   uint32_t max_boxes;        /* per node; 0 = default (4 x max_instructions) */
-  uint32_t map_capacity;     /* entries per device-side region map; 0 = default (16384) */
-  uint32_t scratch_capacity; /* boxes per device-side scratch table; 0 = default (8192) */
+  uint32_t map_capacity;     /* entries per buffer region map (per node); 0 = default (4096) */
+  uint32_t scratch_capacity; /* boxes per device-side scratch table; 0 = default (4096) */
+  uint32_t max_buffers;      /* buffers per context; 0 = default (64) */
+  uint32_t max_live_allocs;  /* live allocations per node; 0 = default (1024) */
+  uint32_t alloc_map_capacity; /* entries per allocation's writer / reader map; 0 = default (256) */
+  uint32_t max_allocations;  /* allocation ids per node over the context's life; 0 = default (65536) */
+  uint32_t max_queue;        /* submissions held by the lookahead queue; 0 = default (65536) */
   int device;                /* CUDA device ordinal */
   void* stream;              /* cudaStream_t to launch on; NULL = the library's own stream */
 } igs_config;
@@ -195,6 +200,11 @@ int igs_flush(igs_ctx* ctx);
 /* Lowers pending submissions (no epoch) and waits for the device. */
 int igs_sync(igs_ctx* ctx);
 
+/* Submits an epoch like igs_flush but, in IGS_MODE_BATCHED, only stages it:
+ * the next igs_sync / igs_flush / igs_lower_batch lowers it. In
+ * IGS_MODE_PLAIN it is lowered at once (without waiting). */
+int igs_submit_epoch(igs_ctx* ctx);
+
 /* Copies node view->node's graph (everything emitted so far) into the
  * caller's arrays. IGS_ERR_TRUNCATED if a capacity is too small (counts are
  * still filled in). */
@@ -218,6 +228,41 @@ int igs_read_buffer(igs_ctx* ctx, uint32_t buffer, const uint32_t lo[3], const u
 /* Lowers the pending submissions of n contexts in ONE persistent launch (all
  * contexts must share a device). Waits for completion. */
 int igs_lower_batch(igs_ctx* const* ctxs, uint32_t n);
+
+/* ---- served lowering ------------------------------------------------------
+ * A device-resident request loop (one persistent kernel, one warp per slot =
+ * one node of one attached context) lowers submissions of many concurrent
+ * program streams as they arrive: region maps stay on the device between
+ * requests, and no launch happens per request. Contexts are admitted while the
+ * slots and the HBM budget allow (footprint = the context's device arena plus
+ * every buffer's bytes on every memory of every node plus its host data).
+ * After igs_serve_attach, igs_submit_task / igs_submit_epoch / igs_destroy_buffer
+ * on that context only publish the submission (host-mapped memory); create
+ * the context's buffers before attaching. Every device wait is bounded: the
+ * loop exits after idle_timeout_ms without work (restart it with
+ * igs_serve_start) or when stopped. */
+typedef struct igs_serve_config {
+  uint32_t max_slots;         /* warps of the loop (node units), e.g. 256 */
+  uint32_t idle_timeout_ms;   /* loop exits after this long without work; 0 = 10000 */
+  uint64_t hbm_budget_bytes;  /* admission budget; 0 = unlimited */
+  int device;
+} igs_serve_config;
+typedef struct igs_server igs_server;
+int igs_serve_create(const igs_serve_config* cfg, igs_server** out);
+void igs_serve_destroy(igs_server* srv);
+/* Admits ctx (up to max_items submissions in all): IGS_ERR_BUDGET if its
+ * footprint does not fit the remaining budget or too few slots are free. */
+int igs_serve_attach(igs_server* srv, igs_ctx* ctx, uint32_t max_items);
+/* Launches the loop if it is not running. */
+int igs_serve_start(igs_server* srv);
+/* Submissions published by ctx, and the number taken by every node (min over
+ * its nodes). Reads host-mapped words only. */
+int igs_serve_progress(const igs_ctx* ctx, uint32_t* submitted, uint32_t* taken);
+/* Waits (bounded by timeout_ms) until every submission of ctx is taken, then
+ * releases its slots and budget. IGS_ERR_TIMEOUT if the wait gave up. */
+int igs_serve_detach(igs_server* srv, igs_ctx* ctx, uint32_t timeout_ms);
+/* Stops the loop and waits for it. */
+int igs_serve_stop(igs_server* srv);
 
 /* Counters: [0] instructions, [1] edges, [2] boxes, [3] map entries read,
  * [4] map entries written, [5] launches of the lowering kernel, summed over

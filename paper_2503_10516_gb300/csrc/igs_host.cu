@@ -7,7 +7,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cstdio>
+#include <thread>
 #include <cstring>
 #include <map>
 #include <string>
@@ -75,6 +78,15 @@ struct igs_ctx {
   KernelJob* d_kjobs = nullptr;
   uint32_t cap_kjobs = 0;
   uint64_t launches = 0;
+  size_t arena_bytes = 0;
+  // serving: submissions live in host-mapped memory the loop polls
+  igs_server* server = nullptr;
+  std::vector<uint32_t> slot_ids;
+  Item* m_items = nullptr;
+  igs_task* m_tasks = nullptr;
+  BufDesc* m_bufs = nullptr;
+  uint32_t* m_nitems = nullptr;
+  uint32_t serve_cap = 0;
   // device-time accounting
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
@@ -84,6 +96,20 @@ struct igs_ctx {
   double last_lower_ms = 0;
   uint64_t n_launch[3] = {0, 0, 0};
   double copy_bytes = 0;
+};
+
+struct igs_server {
+  igs_serve_config cfg{};
+  cudaStream_t stream = nullptr;
+  ServeSlot* slots = nullptr;  // host-mapped
+  ServeSlot* d_slots = nullptr;
+  uint32_t* stop = nullptr;    // host-mapped
+  uint32_t* d_stop = nullptr;
+  cudaEvent_t done_ev = nullptr;
+  bool launched = false;
+  std::vector<uint32_t> free_slots;
+  double used = 0;
+  std::vector<std::pair<igs_ctx*, double>> attached;
 };
 
 namespace {
@@ -169,6 +195,7 @@ void ev_collect(igs_ctx* c) {
 }
 
 int launch_lower(igs_ctx* c) {
+  if (c->server) return IGS_OK;  // the serving loop lowers it
   int r = upload_prog(c);
   if (r) return r;
   const size_t ev = c->timing ? ev_begin(c) : 0;
@@ -199,14 +226,26 @@ int check_status(igs_ctx* c) {
   return IGS_OK;
 }
 
-void push_item(igs_ctx* c, uint32_t kind, uint32_t arg, uint32_t task) {
+int push_item(igs_ctx* c, uint32_t kind, uint32_t arg, uint32_t task) {
   Item it;
   it.kind = kind;
+  if (c->server && c->items.size() >= c->serve_cap) return fail_ctx(c, IGS_ERR_CAPACITY, "serving capacity of this context exceeded");
   if (kind != IT_LOOKAHEAD) c->seq_task.push_back(kind == IT_TASK ? task : NONE);
   it.seq = kind == IT_LOOKAHEAD ? c->seq : c->seq++;
   it.arg = arg;
   it.task = task;
   c->items.push_back(it);
+  if (c->server) {
+    // the record, then (after a release fence) the count the loop polls
+    if (kind == IT_TASK) c->m_tasks[task] = c->tasks[task];
+    c->m_items[c->items.size() - 1] = it;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    *reinterpret_cast<volatile uint32_t*>(c->m_nitems) = (uint32_t)c->items.size();
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    c->items_up = (uint32_t)c->items.size();
+    c->tasks_up = (uint32_t)c->tasks.size();
+  }
+  return IGS_OK;
 }
 
 size_t table_bytes(uint32_t cap) { return (size_t)F_COUNT * cap * sizeof(uint32_t); }
@@ -231,8 +270,13 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
   const uint32_t cap_bind = 2 * cap_instr;
   const uint32_t cap_bmap = cfg->map_capacity ? cfg->map_capacity : 4096;
   const uint32_t cap_scr = cfg->scratch_capacity ? cfg->scratch_capacity : 4096;
-  const uint32_t cap_buffers = 64, cap_slots = 1024, cap_amap = 256, cap_qr = 16384;
-  const uint32_t cap_alloc = 1u << 16, cap_queue = 1u << 16, cap_diag = 1u << 16, cap_rej = 1024;
+  const uint32_t cap_buffers = cfg->max_buffers ? cfg->max_buffers : 64;
+  const uint32_t cap_slots = cfg->max_live_allocs ? cfg->max_live_allocs : 1024;
+  const uint32_t cap_amap = cfg->alloc_map_capacity ? cfg->alloc_map_capacity : 256;
+  const uint32_t cap_alloc = cfg->max_allocations ? cfg->max_allocations : (1u << 16);
+  const uint32_t cap_queue = cfg->max_queue ? cfg->max_queue : (1u << 16);
+  const uint32_t cap_qr = std::max<uint32_t>(4096, std::min<uint32_t>(1u << 16, 4 * cap_queue));
+  const uint32_t cap_diag = std::min<uint32_t>(1u << 16, cap_instr), cap_rej = 1024;
   cudaError_t e = cudaSetDevice(cfg->device);
   if (e != cudaSuccess) {
     delete c;
@@ -279,6 +323,7 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
   const size_t o_diag = take(sizeof(igs_diag) * cap_diag);
   const size_t o_rej = take(sizeof(uint32_t) * cap_rej);
   const size_t o_scr = take(table_bytes(cap_scr) * 14);
+  c->arena_bytes = per * c->N;
   if (cudaMalloc(&c->d_arena, per * c->N) != cudaSuccess || cudaMalloc(&c->d_nodes, sizeof(NodeDev) * c->N) != cudaSuccess ||
       cudaMalloc(&c->d_units, sizeof(Unit) * c->N) != cudaSuccess || cudaMalloc(&c->d_prog, sizeof(ProgDev)) != cudaSuccess ||
       cudaMalloc(&c->d_nitems, sizeof(uint32_t)) != cudaSuccess) {
@@ -393,6 +438,10 @@ void igs_destroy(igs_ctx* c) {
   cudaFree(c->d_arena);
   cudaFree(c->d_cjobs);
   cudaFree(c->d_kjobs);
+  if (c->m_items) cudaFreeHost(c->m_items);
+  if (c->m_tasks) cudaFreeHost(c->m_tasks);
+  if (c->m_bufs) cudaFreeHost(c->m_bufs);
+  if (c->m_nitems) cudaFreeHost(c->m_nitems);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -451,6 +500,7 @@ int igs_create_buffer(igs_ctx* c, uint32_t dims, const uint32_t extent[3], uint3
     CK(cudaMalloc(&dev, count * elem_size));
     CK(cudaMemcpy(dev, host_init, count * elem_size, cudaMemcpyHostToDevice));
   }
+  if (c->server) return fail_ctx(c, IGS_ERR_STATE, "create buffers before attaching the context to a server");
   const uint32_t id = (uint32_t)c->bufs.size();
   c->bufs.push_back(b);
   c->init_dev.push_back(dev);
@@ -464,7 +514,7 @@ int igs_create_buffer(igs_ctx* c, uint32_t dims, const uint32_t extent[3], uint3
 int igs_destroy_buffer(igs_ctx* c, uint32_t b) {
   if (!c || b >= c->bufs.size() || !c->buf_live[b]) return fail_ctx(c, IGS_ERR_INVALID_ARG, "unknown buffer");
   c->buf_live[b] = false;
-  push_item(c, IT_DESTROY, b, 0);
+  if (int r = push_item(c, IT_DESTROY, b, 0)) return r;
   if (c->cfg.mode == IGS_MODE_PLAIN) return launch_lower(c);
   return IGS_OK;
 }
@@ -483,6 +533,8 @@ int igs_submit_task(igs_ctx* c, const igs_task* t, uint64_t* out_seq) {
       if (ac.dim[d].kind > IGS_MAP_FIXED || (ac.dim[d].kind == IGS_MAP_AFFINE && ac.dim[d].a > 2))
         return fail_ctx(c, IGS_ERR_INVALID_ARG, "bad range mapper");
   }
+  if (c->server && c->items.size() + 2 > c->serve_cap)
+    return fail_ctx(c, IGS_ERR_CAPACITY, "serving capacity of this context exceeded");
   const uint32_t ti = (uint32_t)c->tasks.size();
   c->tasks.push_back(*t);
   const uint32_t s = c->seq;
@@ -496,13 +548,14 @@ int igs_submit_task(igs_ctx* c, const igs_task* t, uint64_t* out_seq) {
 
 int igs_set_lookahead(igs_ctx* c, uint32_t L) {
   if (!c) return IGS_ERR_INVALID_ARG;
-  push_item(c, IT_LOOKAHEAD, L, 0);
+  if (int r = push_item(c, IT_LOOKAHEAD, L, 0)) return r;
   if (c->cfg.mode == IGS_MODE_PLAIN) return launch_lower(c);
   return IGS_OK;
 }
 
 int igs_sync(igs_ctx* c) {
   if (!c) return IGS_ERR_INVALID_ARG;
+  if (c->server) return fail_ctx(c, IGS_ERR_STATE, "the context is served");
   if (c->items_up < c->items.size() || c->cfg.mode == IGS_MODE_BATCHED) {
     int r = launch_lower(c);
     if (r) return r;
@@ -510,8 +563,16 @@ int igs_sync(igs_ctx* c) {
   return check_status(c);
 }
 
+int igs_submit_epoch(igs_ctx* c) {
+  if (!c) return IGS_ERR_INVALID_ARG;
+  if (int r = push_item(c, IT_EPOCH, 0, 0)) return r;
+  if (c->cfg.mode == IGS_MODE_PLAIN) return launch_lower(c);
+  return IGS_OK;
+}
+
 int igs_flush(igs_ctx* c) {
   if (!c) return IGS_ERR_INVALID_ARG;
+  if (c->server) return fail_ctx(c, IGS_ERR_STATE, "the context is served: use igs_submit_epoch");
   push_item(c, IT_EPOCH, 0, 0);
   int r = launch_lower(c);
   if (r) return r;
@@ -522,6 +583,8 @@ int igs_lower_batch(igs_ctx* const* ctxs, uint32_t n) {
   if (!ctxs || n == 0) return IGS_ERR_INVALID_ARG;
   igs_ctx* c = ctxs[0];
   std::vector<Unit> units;
+  for (uint32_t i = 0; i < n; ++i)
+    if (!ctxs[i] || ctxs[i]->server) return fail_ctx(ctxs[i], IGS_ERR_STATE, "a served context cannot be batch-lowered");
   for (uint32_t i = 0; i < n; ++i) {
     int r = upload_prog(ctxs[i]);
     if (r) return r;
@@ -560,6 +623,7 @@ int igs_rejected_tasks(igs_ctx* c, uint64_t* seqs, uint32_t cap, uint32_t* count
 
 int igs_fetch_instructions(igs_ctx* c, igs_graph_view* v) {
   if (!c || !v || v->node >= c->N) return fail_ctx(c, IGS_ERR_INVALID_ARG, "bad view");
+  if (c->server) return fail_ctx(c, IGS_ERR_STATE, "detach the context from its server first");
   int r = download_nodes(c);
   if (r) return r;
   const NodeDev& nd = c->nodes_host[v->node];
@@ -853,6 +917,7 @@ struct SendRec {
 
 extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
   if (!c) return IGS_ERR_INVALID_ARG;
+  if (c->server) return fail_ctx(c, IGS_ERR_STATE, "detach the context from its server first");
   int r = fetch_for_exec(c);
   if (r) return r;
   // walk: by submission sequence; within one, every node's part up to its
@@ -1146,4 +1211,182 @@ extern "C" int igs_box_copy(const igs_copy_job* jobs, uint32_t n, void* stream) 
   if (igs_launch_copies(d_jobs, (uint32_t)v.size(), units, stream)) return IGS_ERR_CUDA;
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return IGS_OK;
+}
+
+// ---- served lowering ----------------------------------------------------------
+
+extern "C" int igs_serve_create(const igs_serve_config* cfg, igs_server** out) {
+  if (!cfg || !out || cfg->max_slots == 0) return IGS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(cfg->device) != cudaSuccess) return IGS_ERR_CUDA;
+  igs_server* s = new igs_server();
+  s->cfg = *cfg;
+  if (s->cfg.idle_timeout_ms == 0) s->cfg.idle_timeout_ms = 10000;
+  if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaHostAlloc(&s->slots, sizeof(ServeSlot) * cfg->max_slots, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostAlloc(&s->stop, sizeof(uint32_t), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&s->d_slots, s->slots, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&s->d_stop, s->stop, 0) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->done_ev, cudaEventDisableTiming) != cudaSuccess) {
+    igs_serve_destroy(s);
+    return IGS_ERR_CUDA;
+  }
+  std::memset((void*)s->slots, 0, sizeof(ServeSlot) * cfg->max_slots);
+  *s->stop = 0;
+  for (uint32_t i = cfg->max_slots; i > 0; --i) s->free_slots.push_back(i - 1);
+  *out = s;
+  return IGS_OK;
+}
+
+extern "C" int igs_serve_stop(igs_server* s) {
+  if (!s) return IGS_ERR_INVALID_ARG;
+  *reinterpret_cast<volatile uint32_t*>(s->stop) = 1;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  if (s->launched) {
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return IGS_ERR_CUDA;
+    s->launched = false;
+  }
+  *reinterpret_cast<volatile uint32_t*>(s->stop) = 0;
+  return IGS_OK;
+}
+
+extern "C" void igs_serve_destroy(igs_server* s) {
+  if (!s) return;
+  igs_serve_stop(s);
+  for (auto& a : s->attached) a.first->server = nullptr;
+  if (s->slots) cudaFreeHost((void*)s->slots);
+  if (s->stop) cudaFreeHost(s->stop);
+  if (s->done_ev) cudaEventDestroy(s->done_ev);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+extern "C" int igs_serve_start(igs_server* s) {
+  if (!s) return IGS_ERR_INVALID_ARG;
+  if (s->launched) {
+    if (cudaEventQuery(s->done_ev) == cudaErrorNotReady) return IGS_OK;  // still running
+    s->launched = false;
+  }
+  const uint64_t idle = (uint64_t)s->cfg.idle_timeout_ms * 500;  // polls of about 2 us
+  if (igs_launch_serve(s->d_slots, s->cfg.max_slots, s->d_stop, idle, s->stream)) return IGS_ERR_CUDA;
+  if (cudaEventRecord(s->done_ev, s->stream) != cudaSuccess) return IGS_ERR_CUDA;
+  s->launched = true;
+  return IGS_OK;
+}
+
+extern "C" int igs_serve_attach(igs_server* s, igs_ctx* c, uint32_t max_items) {
+  if (!s || !c || c->server || max_items < c->items.size() + 1) return IGS_ERR_INVALID_ARG;
+  double foot = (double)c->arena_bytes;
+  for (size_t b = 0; b < c->bufs.size(); ++b) {
+    double bytes = c->bufs[b].elem;
+    for (int d = 0; d < 3; ++d) bytes *= c->bufs[b].extent[d];
+    foot += bytes * c->N * (c->D + 1) + (c->init_dev[b] ? bytes : 0.0);
+  }
+  if (s->free_slots.size() < c->N) return fail_ctx(c, IGS_ERR_BUDGET, "no free serving slots");
+  if (s->cfg.hbm_budget_bytes && s->used + foot > (double)s->cfg.hbm_budget_bytes)
+    return fail_ctx(c, IGS_ERR_BUDGET, "HBM budget exceeded");
+  // everything submitted so far must be lowered before the loop takes over
+  if (c->items_up < c->items.size() || c->cfg.mode == IGS_MODE_BATCHED) {
+    int r = launch_lower(c);
+    if (r) return r;
+  }
+  if (int r = check_status(c)) {
+    if (r != IGS_ERR_OVERLAPPING_WRITE) return r;
+  }
+  const uint32_t cap = max_items;
+  CK(cudaHostAlloc(&c->m_items, sizeof(Item) * cap, cudaHostAllocMapped));
+  CK(cudaHostAlloc(&c->m_tasks, sizeof(igs_task) * cap, cudaHostAllocMapped));
+  CK(cudaHostAlloc(&c->m_bufs, sizeof(BufDesc) * std::max<size_t>(1, c->bufs.size()), cudaHostAllocMapped));
+  CK(cudaHostAlloc(&c->m_nitems, sizeof(uint32_t), cudaHostAllocMapped));
+  std::memcpy(c->m_items, c->items.data(), sizeof(Item) * c->items.size());
+  std::memcpy(c->m_tasks, c->tasks.data(), sizeof(igs_task) * c->tasks.size());
+  std::memcpy(c->m_bufs, c->bufs.data(), sizeof(BufDesc) * c->bufs.size());
+  *reinterpret_cast<volatile uint32_t*>(c->m_nitems) = (uint32_t)c->items.size();
+  ProgDev p;
+  CK(cudaHostGetDevicePointer((void**)&p.items, c->m_items, 0));
+  CK(cudaHostGetDevicePointer((void**)&p.tasks, c->m_tasks, 0));
+  CK(cudaHostGetDevicePointer((void**)&p.bufs, c->m_bufs, 0));
+  uint32_t* dn = nullptr;
+  CK(cudaHostGetDevicePointer((void**)&dn, c->m_nitems, 0));
+  p.n_items = dn;
+  CK(cudaMemcpy(c->d_prog, &p, sizeof p, cudaMemcpyHostToDevice));
+  c->serve_cap = cap;
+  c->items_up = (uint32_t)c->items.size();
+  c->tasks_up = (uint32_t)c->tasks.size();
+  c->slot_ids.clear();
+  for (uint32_t n = 0; n < c->N; ++n) {
+    const uint32_t id = s->free_slots.back();
+    s->free_slots.pop_back();
+    c->slot_ids.push_back(id);
+    ServeSlot& S = s->slots[id];
+    S.unit.node = c->d_nodes + n;
+    S.unit.prog = c->d_prog;
+    S.done = (uint32_t)c->items.size();
+    S.status = 0;
+    S.exit = 0;
+    S.busy = 0;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    S.state = SLOT_ACTIVE;
+  }
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  c->server = s;
+  s->used += foot;
+  s->attached.push_back({c, foot});
+  return IGS_OK;
+}
+
+extern "C" int igs_serve_progress(const igs_ctx* c, uint32_t* submitted, uint32_t* taken) {
+  if (!c || !c->server) return IGS_ERR_INVALID_ARG;
+  uint32_t t = 0xFFFFFFFFu, st = 0;
+  for (uint32_t id : c->slot_ids) {
+    const ServeSlot& S = c->server->slots[id];
+    const uint32_t d = S.done, e = S.status;
+    t = std::min(t, d);
+    st |= e;
+  }
+  if (submitted) *submitted = (uint32_t)c->items.size();
+  if (taken) *taken = t;
+  return st ? IGS_ERR_CAPACITY : IGS_OK;
+}
+
+extern "C" int igs_serve_detach(igs_server* s, igs_ctx* c, uint32_t timeout_ms) {
+  if (!s || !c || c->server != s) return IGS_ERR_INVALID_ARG;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    uint32_t sub = 0, tk = 0;
+    const int r = igs_serve_progress(c, &sub, &tk);
+    if (r) break;
+    if (tk >= sub) break;
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms))
+      return fail_ctx(c, IGS_ERR_TIMEOUT, "serving loop did not take every submission in time");
+    if (s->launched && cudaEventQuery(s->done_ev) == cudaSuccess) {
+      s->launched = false;  // the loop left (idle or error): restart it
+      if (int e = igs_serve_start(s)) return e;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  for (uint32_t id : c->slot_ids) s->slots[id].state = SLOT_EMPTY;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  // a warp marks its slot busy before it re-reads the state and processes;
+  // once busy reads 0 after the state was cleared, no warp touches the context
+  for (uint32_t id : c->slot_ids) {
+    const auto t1 = std::chrono::steady_clock::now();
+    while (s->slots[id].busy) {
+      if (std::chrono::steady_clock::now() - t1 > std::chrono::milliseconds(timeout_ms))
+        return fail_ctx(c, IGS_ERR_TIMEOUT, "serving warp did not leave its slot");
+      std::this_thread::yield();
+    }
+    s->free_slots.push_back(id);
+  }
+  for (size_t i = 0; i < s->attached.size(); ++i)
+    if (s->attached[i].first == c) {
+      s->used -= s->attached[i].second;
+      s->attached.erase(s->attached.begin() + i);
+      break;
+    }
+  c->server = nullptr;
+  c->slot_ids.clear();
+  // later submissions go through the launch path again
+  const int r = check_status(c);
+  return r == IGS_ERR_OVERLAPPING_WRITE ? IGS_OK : r;
 }

@@ -104,6 +104,16 @@ struct Unit {
   ProgDev* prog;
 };
 
+// One slot of the serving loop (host-mapped memory): a warp serves the unit
+// while `state` is SLOT_ACTIVE and publishes how many submissions it has
+// taken in `done`.
+enum SlotState : uint32_t { SLOT_EMPTY = 0, SLOT_ACTIVE = 1 };
+enum SlotExit : uint32_t { EXIT_NONE = 0, EXIT_STOPPED = 1, EXIT_IDLE = 2, EXIT_ERROR = 3 };
+struct ServeSlot {
+  Unit unit;
+  volatile uint32_t state, done, status, exit, busy, pad;
+};
+
 // Box-copy work descriptor (device side).
 struct CopyJob {
   const uint8_t* src;
@@ -118,4 +128,7 @@ struct CopyJob {
 
 // Device entry points implemented in the .cu translation units.
 int igs_launch_lower(const igs::Unit* units_dev, uint32_t n_units, uint32_t max_items, void* stream);
+// Persistent serving loop over n_slots slots; exits when *stop is set or a
+// warp stays idle for idle_polls polls (about 2 us each).
+int igs_launch_serve(igs::ServeSlot* slots, uint32_t n_slots, volatile uint32_t* stop, uint64_t idle_polls, void* stream);
 int igs_launch_copies(const igs::CopyJob* jobs_dev, uint32_t n_jobs, uint64_t n_units, void* stream);

@@ -2501,8 +2501,88 @@ __global__ void __launch_bounds__(128) lower_kernel(const Unit* units, uint32_t 
   store_ctx(c, cursor);
 }
 
+// Serving loop: warp w serves slot w; it takes every submission published so
+// far, then publishes its progress. Waits are bounded: after idle_polls empty
+// polls (about 2 us each) the warp leaves with EXIT_IDLE; a set stop flag ends
+// it with EXIT_STOPPED.
+__global__ void __launch_bounds__(128) serve_kernel(ServeSlot* slots, uint32_t n_slots, volatile uint32_t* stop,
+                                                    uint64_t idle_polls) {
+  const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= n_slots) return;
+  ServeSlot& S = slots[w];
+  uint64_t idle = 0;
+  uint32_t exit_code = EXIT_IDLE;
+  const bool leader = (threadIdx.x & 31u) == 0;
+  for (;;) {
+    // host-written words are read once by lane 0 and broadcast, so every lane
+    // takes the same path
+    uint32_t st = 0, stp = 0;
+    if (leader) {
+      st = S.state;
+      stp = *stop;
+    }
+    st = __shfl_sync(FULL, st, 0);
+    stp = __shfl_sync(FULL, stp, 0);
+    if (stp) {
+      exit_code = EXIT_STOPPED;
+      break;
+    }
+    bool worked = false;
+    if (st == SLOT_ACTIVE) {
+      // mark the slot busy, then confirm it is still active: the host clears
+      // the state first and then waits for busy == 0
+      if (leader) S.busy = 1;
+      __threadfence_system();
+      uint32_t st2 = 0;
+      if (leader) st2 = S.state;
+      st2 = __shfl_sync(FULL, st2, 0);
+      const Unit u = S.unit;
+      uint32_t avail = 0;
+      if (leader && st2 == SLOT_ACTIVE) avail = *u.prog->n_items;
+      avail = __shfl_sync(FULL, avail, 0);
+      __threadfence_system();
+      if (st2 == SLOT_ACTIVE && u.node->cursor < avail && u.node->status == ST_OK) {
+        Ctx c;
+        load_ctx(c, u.node, u.prog);
+        uint32_t cursor = u.node->cursor;
+        while (cursor < avail && c.err == ST_OK) {
+          deliver(c, cursor);
+          ++cursor;
+        }
+        store_ctx(c, cursor);
+        __threadfence_system();
+        if (leader) {
+          S.status = c.err;
+          S.done = cursor;
+        }
+        __threadfence_system();
+        worked = true;
+      }
+      __threadfence_system();
+      if (leader) S.busy = 0;
+    }
+    __syncwarp();
+    if (worked) {
+      idle = 0;
+      continue;
+    }
+    if (++idle > idle_polls) break;
+    __nanosleep(2000);
+  }
+  if (leader) S.exit = exit_code;
+  __threadfence_system();
+}
+
 }  // namespace
 }  // namespace igs
+
+int igs_launch_serve(igs::ServeSlot* slots, uint32_t n_slots, volatile uint32_t* stop, uint64_t idle_polls, void* stream) {
+  if (n_slots == 0) return 0;
+  const uint32_t threads = 128, warps = threads / 32;
+  const uint32_t blocks = (n_slots + warps - 1) / warps;
+  igs::serve_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(slots, n_slots, stop, idle_polls);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 
 int igs_launch_lower(const igs::Unit* units_dev, uint32_t n_units, uint32_t max_items, void* stream) {
   if (n_units == 0) return 0;

@@ -26,7 +26,9 @@ LOOKAHEAD_INFINITE = 0xFFFFFFFF
 EXPORTS = ("igs_create", "igs_destroy", "igs_create_buffer", "igs_destroy_buffer", "igs_submit_task",
            "igs_set_lookahead", "igs_flush", "igs_sync", "igs_fetch_instructions", "igs_rejected_tasks",
            "igs_execute", "igs_read_buffer", "igs_lower_batch", "igs_counters", "igs_last_error", "igs_box_copy",
-           "igs_set_timing", "igs_stats", "igs_profile", "igs_lower_static")
+           "igs_set_timing", "igs_stats", "igs_profile", "igs_lower_static", "igs_submit_epoch",
+           "igs_serve_create", "igs_serve_destroy", "igs_serve_attach", "igs_serve_start", "igs_serve_progress",
+           "igs_serve_detach", "igs_serve_stop")
 
 
 class IgsError(RuntimeError):
@@ -40,7 +42,10 @@ class Config(ctypes.Structure):
                 ("horizon_step", ctypes.c_uint32), ("lookahead", ctypes.c_uint32), ("mode", ctypes.c_uint32),
                 ("max_instructions", ctypes.c_uint32), ("max_edges", ctypes.c_uint32),
                 ("max_boxes", ctypes.c_uint32), ("map_capacity", ctypes.c_uint32),
-                ("scratch_capacity", ctypes.c_uint32), ("device", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("scratch_capacity", ctypes.c_uint32), ("max_buffers", ctypes.c_uint32),
+                ("max_live_allocs", ctypes.c_uint32), ("alloc_map_capacity", ctypes.c_uint32),
+                ("max_allocations", ctypes.c_uint32), ("max_queue", ctypes.c_uint32),
+                ("device", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class GraphView(ctypes.Structure):
@@ -54,6 +59,11 @@ class GraphView(ctypes.Structure):
 
 class Box(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_uint32 * 3), ("hi", ctypes.c_uint32 * 3)]
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_uint32), ("idle_timeout_ms", ctypes.c_uint32),
+                ("hbm_budget_bytes", ctypes.c_uint64), ("device", ctypes.c_int)]
 
 
 class StaticBuffer(ctypes.Structure):
@@ -99,6 +109,15 @@ def lib():
         L.igs_set_lookahead.argtypes = [vp, u32]
         L.igs_flush.argtypes = [vp]
         L.igs_sync.argtypes = [vp]
+        L.igs_submit_epoch.argtypes = [vp]
+        L.igs_serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(vp)]
+        L.igs_serve_destroy.argtypes = [vp]
+        L.igs_serve_destroy.restype = None
+        L.igs_serve_attach.argtypes = [vp, vp, u32]
+        L.igs_serve_start.argtypes = [vp]
+        L.igs_serve_progress.argtypes = [vp, P32, P32]
+        L.igs_serve_detach.argtypes = [vp, vp, u32]
+        L.igs_serve_stop.argtypes = [vp]
         L.igs_fetch_instructions.argtypes = [vp, ctypes.POINTER(GraphView)]
         L.igs_rejected_tasks.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), u32, P32]
         L.igs_execute.argtypes = [vp, u32]
@@ -126,10 +145,13 @@ class Context:
 
     def __init__(self, nodes: int, devices: int, horizon_step: int = 4, lookahead: int = 0,
                  mode: int = MODE_PLAIN, device: int = 0, stream: Optional[int] = None,
-                 max_instructions: int = 0, map_capacity: int = 0, scratch_capacity: int = 0):
+                 max_instructions: int = 0, map_capacity: int = 0, scratch_capacity: int = 0,
+                 max_buffers: int = 0, max_live_allocs: int = 0, alloc_map_capacity: int = 0,
+                 max_allocations: int = 0, max_queue: int = 0):
         self.nodes = nodes
         cfg = Config(nodes, devices, horizon_step, lookahead, mode, max_instructions, 0, 0, map_capacity,
-                     scratch_capacity, device, stream)
+                     scratch_capacity, max_buffers, max_live_allocs, alloc_map_capacity, max_allocations,
+                     max_queue, device, stream)
         h = ctypes.c_void_p()
         r = lib().igs_create(ctypes.byref(cfg), ctypes.byref(h))
         if r != IGS_OK:
@@ -190,6 +212,9 @@ class Context:
         if r == -2 and allow_rejected:
             return r
         return self._check(r, "sync")
+
+    def submit_epoch(self):
+        self._check(lib().igs_submit_epoch(self._h), "submit_epoch")
 
     def graph(self, node: int) -> dict:
         v = GraphView()
@@ -261,6 +286,53 @@ Context.stats = _stats
 Context.set_timing = _set_timing
 
 
+class Server:
+    """Device-resident serving loop over attached contexts."""
+
+    def __init__(self, max_slots: int = 256, hbm_budget_bytes: int = 0, idle_timeout_ms: int = 10000, device: int = 0):
+        cfg = ServeConfig(max_slots, idle_timeout_ms, hbm_budget_bytes, device)
+        h = ctypes.c_void_p()
+        r = lib().igs_serve_create(ctypes.byref(cfg), ctypes.byref(h))
+        if r != IGS_OK:
+            raise IgsError(r, "serve_create")
+        self._h = h
+
+    def attach(self, ctx: Context, max_items: int) -> int:
+        """IGS_OK, or the error code (e.g. -7 BUDGET) without raising."""
+        return lib().igs_serve_attach(self._h, ctx.handle, max_items)
+
+    def start(self):
+        r = lib().igs_serve_start(self._h)
+        if r != IGS_OK:
+            raise IgsError(r, "serve_start")
+
+    @staticmethod
+    def progress(ctx: Context):
+        sub = np.zeros(1, np.uint32)
+        tk = np.zeros(1, np.uint32)
+        r = lib().igs_serve_progress(ctx.handle, _p32(sub), _p32(tk))
+        return int(sub[0]), int(tk[0]), r
+
+    def detach(self, ctx: Context, timeout_ms: int = 60000):
+        r = lib().igs_serve_detach(self._h, ctx.handle, timeout_ms)
+        if r != IGS_OK:
+            raise IgsError(r, "serve_detach: " + lib().igs_last_error(ctx.handle).decode())
+
+    def stop(self):
+        lib().igs_serve_stop(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().igs_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def lower_batch(ctxs: Sequence[Context]):
     arr = (ctypes.c_void_p * len(ctxs))(*[c.handle.value for c in ctxs])
     r = lib().igs_lower_batch(arr, len(ctxs))
@@ -303,7 +375,7 @@ def lower_static(prog: W.Program, outs: Sequence[dict], stream: Optional[int] = 
         out[n].binds, out[n].bind_cap = o["binds"]
         out[n].diags, out[n].diag_cap = o["diags"]
         out[n].counts = o["counts"]
-    cfg = Config(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead, 0, 0, 0, 0, 0, 0, 0, None)
+    cfg = Config(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, None)
     return lib().igs_lower_static(ctypes.byref(cfg), sb, len(bufs), _p32(words), len(tasks), so, len(ops), out, stream)
 
 
@@ -319,6 +391,18 @@ def box_copy(jobs: Sequence[tuple], stream: Optional[int] = None):
     r = lib().igs_box_copy(arr, len(jobs), stream)
     if r != IGS_OK:
         raise IgsError(r, "box_copy")
+
+
+def small_caps(prog: W.Program, instructions: int = 0) -> dict:
+    """Context capacities sized for one program (for many contexts at once)."""
+    tasks = prog.tasks
+    chunks = max((t.chunks for t in tasks), default=1)
+    nacc = max((len(t.accessors) for t in tasks), default=1)
+    est = instructions or (len(tasks) * (chunks * (nacc + 3) + 16) + 256)
+    est = max(1024, int(est * 1.25))
+    return {"max_instructions": est, "map_capacity": 2048, "scratch_capacity": max(2048, 4 * chunks * nacc),
+            "max_buffers": max(1, len(prog.buffers)), "max_live_allocs": 256, "alloc_map_capacity": 128,
+            "max_allocations": 8192, "max_queue": max(256, 2 * len(prog.ops) + 16)}
 
 
 class GpuImpl:

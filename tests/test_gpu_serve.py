@@ -1,0 +1,114 @@
+"""Served lowering: a persistent device loop lowers the submissions of many
+concurrent program streams as they arrive. Every stream's graph is the same
+in the mix as alone (the oracle's, and plain per-task lowering's)."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2503_10516_gb300 import workloads as W
+from tests.harness import assert_same_graph, oracle_graphs
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(prog, mode=0):
+    from paper_2503_10516_gb300 import igs
+    c = igs.Context(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead, mode=mode, **igs.small_caps(prog))
+    for op in prog.ops:
+        if op[0] == "buffer":
+            b = op[1]
+            c.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init)
+    return c
+
+
+def _streams():
+    progs = [W.growing_program(rows_max=200, cols=16, grow=(1, 12), devices=2, chunks=2, lookahead=L, seed=100 + i)
+             for i, L in enumerate([0, 4, 0xFFFFFFFF, 0, 8])]
+    progs += [W.wave_program(n=32, steps=12, nodes=2, devices=2, chunks=8, lookahead=2),
+              W.growing_program(rows_max=96, cols=1, grow=(1, 9), nodes=2, devices=2, chunks=4, lookahead=3, seed=7)]
+    return progs
+
+
+def _interleaved(progs, rng):
+    """(stream, op) in a random interleaving that keeps each stream's order."""
+    pos = [0] * len(progs)
+    bodies = [[op for op in p.ops if op[0] != "buffer"] for p in progs]
+    out = []
+    while any(pos[i] < len(bodies[i]) for i in range(len(progs))):
+        i = int(rng.choice([k for k in range(len(progs)) if pos[k] < len(bodies[k])]))
+        out.append((i, bodies[i][pos[i]]))
+        pos[i] += 1
+    return out
+
+
+def test_served_streams_match_alone():
+    from paper_2503_10516_gb300 import igs
+    progs = _streams()
+    srv = igs.Server(max_slots=64)
+    ctxs = [_ctx(p) for p in progs]
+    for c, p in zip(ctxs, progs):
+        assert srv.attach(c, 4 * len(p.ops) + 16) == 0
+    srv.start()
+    for i, op in _interleaved(progs, np.random.default_rng(1)):
+        if op[0] == "task":
+            ctxs[i].submit(op[1])
+        elif op[0] == "flush":
+            ctxs[i].submit_epoch()
+    for c in ctxs:
+        srv.detach(c)
+    srv.stop()
+    for c, p in zip(ctxs, progs):
+        ref, rej = oracle_graphs(p)
+        alone = _ctx(p)
+        for op in p.ops:
+            if op[0] == "task":
+                alone.submit(op[1])
+            elif op[0] == "flush":
+                alone.flush()
+        for n in range(p.nodes):
+            g = c.graph(n)
+            assert_same_graph(g, ref[n], f"{p.name} node {n} (served vs oracle)")
+            assert_same_graph(g, alone.graph(n), f"{p.name} node {n} (served vs alone)")
+        alone.close()
+        c.close()
+    srv.close()
+
+
+def test_admission_by_hbm_budget():
+    from paper_2503_10516_gb300 import igs
+    p = W.growing_program(rows_max=64, cols=16, grow=(1, 8), devices=2, chunks=2)
+    a, b = _ctx(p), _ctx(p)
+    probe = igs.Server(max_slots=8)
+    assert probe.attach(a, 1024) == 0
+    probe.detach(a)
+    probe.close()
+    # a budget that fits one of them only
+    from paper_2503_10516_gb300.igs import lib
+    srv = igs.Server(max_slots=8, hbm_budget_bytes=1)
+    assert srv.attach(b, 1024) == -7
+    srv.close()
+    a.close()
+    b.close()
+
+
+def test_served_after_idle_exit():
+    """The loop leaves after its idle timeout; detach restarts it for the
+    submissions that arrived meanwhile, and the graph is still exact."""
+    from paper_2503_10516_gb300 import igs
+    p = W.growing_program(rows_max=80, cols=8, grow=(1, 6), devices=2, chunks=2, lookahead=0, seed=3)
+    c = _ctx(p)
+    srv = igs.Server(max_slots=8, idle_timeout_ms=20)
+    assert srv.attach(c, 4 * len(p.ops) + 16) == 0
+    srv.start()
+    time.sleep(0.3)  # the loop has left by now
+    for op in p.ops:
+        if op[0] == "task":
+            c.submit(op[1])
+        elif op[0] == "flush":
+            c.submit_epoch()
+    srv.detach(c)
+    ref, _ = oracle_graphs(p)
+    assert_same_graph(c.graph(0), ref[0], "served after idle exit")
+    c.close()
+    srv.close()

@@ -148,6 +148,135 @@ def run_reference(args):
     return 0
 
 
+def _stage_ctx(igs, prog, mode, stream):
+    c = igs.Context(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead, mode=mode, stream=stream,
+                    **igs.small_caps(prog))
+    for op in prog.ops:
+        if op[0] == "buffer":
+            b = op[1]
+            c.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init)
+    return c
+
+
+def measure_batched(igs, torch, stream, count=128, scale=0.01):
+    """Uneven programs (1-8 buffers of 2^10-2^24 elements, 1-128 chunks, 2-32
+    memories, lookahead 0-16; task counts scaled down): one persistent launch
+    over all of them vs one task per launch."""
+    progs = W.batch_programs(count=count, scale=scale, seed=0x5EED + 3)
+    res = {}
+    for mode_name, mode in (("plain", igs.MODE_PLAIN), ("batched", igs.MODE_BATCHED)):
+        ctxs = [_stage_ctx(igs, p, mode, stream) for p in progs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for p, c in zip(progs, ctxs):
+            for op in p.ops:
+                if op[0] == "task":
+                    c.submit(op[1])
+                elif op[0] == "flush":
+                    c.submit_epoch()
+        if mode == igs.MODE_BATCHED:
+            igs.lower_batch(ctxs)
+        else:
+            for c in ctxs:
+                c.sync()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        instrs = sum(int(c.counters()["instructions"]) for c in ctxs)
+        launches = sum(int(c.counters()["launches"]) for c in ctxs)
+        res[mode_name] = {"instr_per_s": instrs / dt, "seconds": dt, "instructions": instrs, "launches": launches}
+        for c in ctxs:
+            c.close()
+    res["programs"] = count
+    res["task_scale"] = scale
+    res["speedup"] = res["batched"]["instr_per_s"] / res["plain"]["instr_per_s"]
+    return res
+
+
+def measure_served(igs, torch, stream, streams=16, rate=2000.0, rows_max=2048, cols=1024, lookahead=0):
+    """Growing-row program streams (rows appended 1-64 at a time, each task
+    reading every earlier row) submitting with Poisson arrivals; per-task
+    latency = submission -> every node of its program has taken it. Compared
+    with one task per launch (submit, then wait for that launch)."""
+    rng = np.random.default_rng(0x5EED + 5)
+    progs = [W.growing_program(rows_max=rows_max, cols=cols, grow=(1, 64), devices=2, chunks=2,
+                               lookahead=lookahead, seed=500 + i) for i in range(streams)]
+    order = []
+    for i, p in enumerate(progs):
+        for op in p.ops:
+            if op[0] in ("task", "flush"):
+                order.append(i)
+    rng.shuffle(order)
+    gaps = rng.exponential(1.0 / rate, size=len(order))
+    bodies = [[op for op in p.ops if op[0] in ("task", "flush")] for p in progs]
+    out = {}
+    # served
+    srv = igs.Server(max_slots=max(32, 2 * streams))
+    ctxs = [_stage_ctx(igs, p, igs.MODE_PLAIN, None) for p in progs]
+    for c, p in zip(ctxs, progs):
+        assert srv.attach(c, 4 * len(p.ops) + 16) == 0
+    srv.start()
+    pos = [0] * streams
+    pending = []  # (ctx index, item count after submit, t_submit)
+    lat = []
+    t_next = time.perf_counter()
+    for k, i in enumerate(order):
+        t_next += gaps[k]
+        while time.perf_counter() < t_next:
+            pending = [x for x in pending if not _done(srv, ctxs, x, lat)]
+        op = bodies[i][pos[i]]
+        pos[i] += 1
+        if op[0] == "task":
+            ctxs[i].submit(op[1])
+        else:
+            ctxs[i].submit_epoch()
+        sub, _, _ = srv.progress(ctxs[i])
+        pending.append((i, sub, time.perf_counter()))
+    t_end = time.perf_counter() + 30
+    while pending and time.perf_counter() < t_end:
+        pending = [x for x in pending if not _done(srv, ctxs, x, lat)]
+    for c in ctxs:
+        srv.detach(c)
+    srv.stop()
+    instrs = sum(int(c.counters()["instructions"]) for c in ctxs)
+    for c in ctxs:
+        c.close()
+    srv.close()
+    lat.sort()
+    out["served"] = {"p50_ms": lat[len(lat) // 2] * 1e3, "p99_ms": lat[int(len(lat) * 0.99)] * 1e3,
+                     "tasks": len(lat), "instructions": instrs}
+    # one task per launch, same programs and order, no arrival gaps
+    ctxs = [_stage_ctx(igs, p, igs.MODE_PLAIN, None) for p in progs]
+    pos = [0] * streams
+    lat = []
+    for i in order:
+        op = bodies[i][pos[i]]
+        pos[i] += 1
+        t0 = time.perf_counter()
+        if op[0] == "task":
+            ctxs[i].submit(op[1])
+        else:
+            ctxs[i].submit_epoch()
+        ctxs[i].sync()
+        lat.append(time.perf_counter() - t0)
+    for c in ctxs:
+        c.close()
+    lat.sort()
+    out["plain"] = {"p50_ms": lat[len(lat) // 2] * 1e3, "p99_ms": lat[int(len(lat) * 0.99)] * 1e3}
+    out["streams"] = streams
+    out["rate_tasks_per_s"] = rate
+    out["workload"] = f"{streams} streams, growing {rows_max}x{cols} fp32 rows, 2 devices, lookahead {lookahead}"
+    return out
+
+
+def _done(srv, ctxs, x, lat):
+    i, want, t0 = x
+    _, taken, _ = srv.progress(ctxs[i])
+    if taken >= want:
+        lat.append(time.perf_counter() - t0)
+        return True
+    return False
+
+
 def run_gpu(args):
     import torch
     from paper_2503_10516_gb300 import igs
@@ -290,6 +419,10 @@ def run_gpu(args):
         a = b_k / (ms_k * 1e-3) / 1e9 if ms_k > 0 else 0.0
         hot[k] = {"ms_per_step": ms_k, "bytes_per_step": b_k, "achieved_gbs": a, "frac": a / hbm}
 
+    # ---- batched lowering of many programs, served lowering of many streams
+    batched = measure_batched(igs, torch, sh) if world == 1 else None
+    served = measure_served(igs, torch, sh) if world == 1 else None
+
     # ---- CPU baseline: the oracle on a bounded sample of the same workload
     cpu = None
     if rank == 0 and world == 1:
@@ -323,6 +456,8 @@ def run_gpu(args):
                          "p50_task_ms": p50, "p99_task_ms": p99,
                          "batched_ms_per_task": lower_ms / STEPS},
             "box_copy_gbs": (copy_bytes / (copy_ms * 1e-3) / 1e9) if copy_ms else None,
+            "batched_programs": batched,
+            "served": served,
             "clocks": clocks.summary(),
             "cpu_baseline": cpu,
         }

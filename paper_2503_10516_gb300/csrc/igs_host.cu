@@ -218,7 +218,9 @@ int check_status(igs_ctx* c) {
   if (r) return r;
   for (uint32_t n = 0; n < c->N; ++n) {
     const NodeDev& nd = c->nodes_host[n];
-    if (nd.status == ST_CAPACITY) return fail_ctx(c, IGS_ERR_CAPACITY, "device table or output capacity exceeded on node " + std::to_string(n));
+    if (nd.status == ST_CAPACITY)
+      return fail_ctx(c, IGS_ERR_CAPACITY, "device table or output capacity exceeded on node " + std::to_string(n) +
+                                               " (table capacity " + std::to_string(nd.err_info) + ")");
     if (nd.status == ST_TIMEOUT) return fail_ctx(c, IGS_ERR_TIMEOUT, "device wait timed out");
     if (nd.status != ST_OK) return fail_ctx(c, IGS_ERR_CUDA, "lowering engine internal error on node " + std::to_string(n));
   }
@@ -604,7 +606,7 @@ int igs_lower_batch(igs_ctx* const* ctxs, uint32_t n) {
   for (uint32_t i = 0; i < n; ++i) {
     ctxs[i]->launches++;
     int r = check_status(ctxs[i]);
-    if (r && r != IGS_ERR_OVERLAPPING_WRITE) return r;
+    if (r && r != IGS_ERR_OVERLAPPING_WRITE) return fail_ctx(c, r, "context " + std::to_string(i) + ": " + ctxs[i]->err);
   }
   return IGS_OK;
 }

@@ -50,7 +50,7 @@ struct NodeDev {
   // configuration
   uint32_t node, N, D, prog;
   // scalars (owned by the warp; written back after every item)
-  uint32_t status, cursor, lookahead, epoch, last_horizon, last_sync, next_msg, n_alloc;
+  uint32_t status, err_info, cursor, lookahead, epoch, last_horizon, last_sync, next_msg, n_alloc;
   uint32_t n_instr, n_edge, n_box, n_bind, n_diag, n_rej;
   uint32_t q_head, q_count, qr_n, n_free, n_live, qr_live;
   uint64_t map_reads, map_writes, launches;

@@ -161,7 +161,7 @@ struct Acc {
 struct Ctx {
   NodeDev* nd;
   const ProgDev* pg;
-  uint32_t lane, err;
+  uint32_t lane, err, err_info;
   uint32_t node, N, D;
   uint32_t epoch, last_horizon, last_sync, next_msg, n_alloc, n_free, n_live;
   uint32_t n_instr, n_edge, n_box, n_bind, n_diag, n_rej;
@@ -196,6 +196,7 @@ __device__ __forceinline__ uint32_t t_claim(Ctx& c, Table& t, bool pred) {
   const uint32_t nn = t.n + __popc(m);
   if (nn > t.cap) {
     fail(c, ST_CAPACITY);
+    c.err_info = t.cap;
     return NONE;
   }
   t.n = nn;
@@ -219,6 +220,7 @@ __device__ __forceinline__ uint32_t t_claim_n(Ctx& c, Table& t, uint32_t k) {
   const uint32_t first = t.n + x - k;
   if (t.n + total > t.cap) {
     fail(c, ST_CAPACITY);
+    c.err_info = t.cap;
     return NONE;
   }
   t.n += total;
@@ -1140,6 +1142,9 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
       if (c.lane == 0) t_put(RD, s, 0, q, id, 0, 0);
       __syncwarp();
     }
+    // re-merge only a table that has grown: keeps hot paths short and bounds
+    // fragmentation between horizons
+    if (RD.live > 48) t_merge_from(c, RD, 0);
     (void)from;
   }
   for (int k = 0; k < nacc; ++k) {
@@ -1156,6 +1161,8 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
       t_set(c, WR, NONE, q, id, 0, 0);
       if (c.err) return NONE;
     }
+    if (WR.live > 48) t_merge_from(c, WR, 0);
+    if (RD.live > 48) t_merge_from(c, RD, 0);
     (void)from;
   }
   return id;
@@ -2160,6 +2167,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
       Table B = bst_t(c, t.acc[a].buffer);
       t_set(c, B, NONE, x, kid, mem, 1u << mem);
       if (c.err) return;
+      if (B.live > 4 * CH.n + 64) t_merge_from(c, B, 0);
     }
   }
   pt_lap(pt, c, PH_P5);
@@ -2415,6 +2423,7 @@ __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg) {
   c.pg = pg;
   c.lane = threadIdx.x & 31u;
   c.err = nd->status;
+  c.err_info = nd->err_info;
   c.node = nd->node;
   c.N = nd->N;
   c.D = nd->D;
@@ -2457,6 +2466,7 @@ __device__ void store_ctx(Ctx& c, uint32_t cursor) {
   if (c.lane != 0) return;
   NodeDev* nd = c.nd;
   nd->status = c.err;
+  nd->err_info = c.err_info;
   nd->cursor = cursor;
   nd->epoch = c.epoch;
   nd->last_horizon = c.last_horizon;

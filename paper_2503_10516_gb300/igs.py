@@ -147,9 +147,9 @@ class Context:
                  mode: int = MODE_PLAIN, device: int = 0, stream: Optional[int] = None,
                  max_instructions: int = 0, map_capacity: int = 0, scratch_capacity: int = 0,
                  max_buffers: int = 0, max_live_allocs: int = 0, alloc_map_capacity: int = 0,
-                 max_allocations: int = 0, max_queue: int = 0):
+                 max_allocations: int = 0, max_queue: int = 0, max_edges: int = 0, max_boxes: int = 0):
         self.nodes = nodes
-        cfg = Config(nodes, devices, horizon_step, lookahead, mode, max_instructions, 0, 0, map_capacity,
+        cfg = Config(nodes, devices, horizon_step, lookahead, mode, max_instructions, max_edges, max_boxes, map_capacity,
                      scratch_capacity, max_buffers, max_live_allocs, alloc_map_capacity, max_allocations,
                      max_queue, device, stream)
         h = ctypes.c_void_p()
@@ -337,7 +337,7 @@ def lower_batch(ctxs: Sequence[Context]):
     arr = (ctypes.c_void_p * len(ctxs))(*[c.handle.value for c in ctxs])
     r = lib().igs_lower_batch(arr, len(ctxs))
     if r not in (IGS_OK, -2):
-        raise IgsError(r, "lower_batch")
+        raise IgsError(r, "lower_batch: " + lib().igs_last_error(ctxs[0].handle).decode())
 
 
 def lower_static(prog: W.Program, outs: Sequence[dict], stream: Optional[int] = None) -> int:
@@ -393,16 +393,24 @@ def box_copy(jobs: Sequence[tuple], stream: Optional[int] = None):
         raise IgsError(r, "box_copy")
 
 
-def small_caps(prog: W.Program, instructions: int = 0) -> dict:
-    """Context capacities sized for one program (for many contexts at once)."""
+def small_caps(prog: W.Program, counts: Optional[dict] = None) -> dict:
+    """Context capacities sized for one program (so that many contexts fit at
+    once). counts: exact per-node maxima {"instrs", "edges", "boxes"} when
+    known; otherwise generous estimates from the program's shape."""
     tasks = prog.tasks
     chunks = max((t.chunks for t in tasks), default=1)
     nacc = max((len(t.accessors) for t in tasks), default=1)
-    est = instructions or (len(tasks) * (chunks * (nacc + 3) + 16) + 256)
-    est = max(1024, int(est * 1.25))
-    return {"max_instructions": est, "map_capacity": 2048, "scratch_capacity": max(2048, 4 * chunks * nacc),
-            "max_buffers": max(1, len(prog.buffers)), "max_live_allocs": 256, "alloc_map_capacity": 128,
-            "max_allocations": 8192, "max_queue": max(256, 2 * len(prog.ops) + 16)}
+    look = min(prog.lookahead, len(tasks)) if prog.lookahead != LOOKAHEAD_INFINITE else len(tasks)
+    if counts:
+        ni, ne, nb = (int(counts[k] * 1.25) + 256 for k in ("instrs", "edges", "boxes"))
+    else:
+        ni = len(tasks) * (chunks * (nacc + 3) + 16) + 256
+        ne, nb = ni * (chunks + 8), ni * 8
+    return {"max_instructions": ni, "max_edges": ne, "max_boxes": nb, "map_capacity": 4096,
+            "scratch_capacity": max(4096, (look + 2) * chunks * nacc * 2),
+            "max_buffers": max(1, len(prog.buffers)), "max_live_allocs": 256,
+            "alloc_map_capacity": max(512, 4 * chunks * nacc + 64), "max_allocations": 16384,
+            "max_queue": max(256, 2 * len(prog.ops) + 16)}
 
 
 class GpuImpl:

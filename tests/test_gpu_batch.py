@@ -8,10 +8,15 @@ from tests.harness import assert_same_graph, oracle_graphs
 pytestmark = pytest.mark.gpu
 
 
+def _counts(prog):
+    ref, _ = oracle_graphs(prog)
+    return {k: max(len(g[k]) for g in ref) for k in ("instrs", "edges", "boxes")}
+
+
 def _stage(prog, mode, stream=None):
     from paper_2503_10516_gb300 import igs
     c = igs.Context(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead, mode=mode, stream=stream,
-                    **igs.small_caps(prog))
+                    **igs.small_caps(prog, _counts(prog)))
     for op in prog.ops:
         if op[0] == "buffer":
             b = op[1]

@@ -94,11 +94,12 @@ typedef struct igs_config {
   uint32_t max_instructions; /* per node output capacity; 0 = default (1 << 18) */
   uint32_t max_edges;        /* per node; 0 = default (4 x max_instructions) */
   uint32_t max_boxes;        /* per node; 0 = default (4 x max_instructions) */
-  uint32_t map_capacity;     /* entries per buffer region map (per node); 0 = default (4096) */
+  uint32_t map_heap;         /* entries (48 bytes each) of each node's region-map heap, which holds every
+                                buffer's and allocation's box tables; a table grows on demand by moving to a
+                                larger slab of the heap; 0 = default (1 << 20) */
   uint32_t scratch_capacity; /* boxes per device-side scratch table; 0 = default (4096) */
   uint32_t max_buffers;      /* buffers per context; 0 = default (64) */
   uint32_t max_live_allocs;  /* live allocations per node; 0 = default (1024) */
-  uint32_t alloc_map_capacity; /* entries per allocation's writer / reader map; 0 = default (256) */
   uint32_t max_allocations;  /* allocation ids per node over the context's life; 0 = default (65536) */
   uint32_t max_queue;        /* submissions held by the lookahead queue; 0 = default (65536) */
   int device;                /* CUDA device ordinal */
@@ -315,10 +316,11 @@ int igs_box_copy(const igs_copy_job* jobs, uint32_t n, void* stream);
  * caller-owned DEVICE output arrays, using a 32 MiB file-scope device array as
  * its only scratch: it calls no cudaMalloc, cudaFree or other allocating
  * routine. Every GPU that loads the library holds that array until exit.
- *   Limits: at most 16 buffers; per node at most 128 live allocations, 512
- *   entries in a buffer's region maps and 128 in an allocation's; the program's
- *   staged inputs plus per-node state (about 2.7 MiB + instr_cap bytes per
- *   node) must fit the array, else IGS_ERR_CAPACITY before anything runs.
+ *   Limits: at most 16 buffers; per node at most 128 live allocations and a
+ *   region-map heap of 32768 entries shared by all its box tables; the
+ *   program's staged inputs plus per-node state (about 2.6 MiB + instr_cap
+ *   bytes per node) must fit the array, else IGS_ERR_CAPACITY before anything
+ *   runs (a heap that fills up during lowering reports IGS_ERR_CAPACITY).
  *   Sharing: every call uses the same array and leaves its last contents there
  *   (each call resets what must start at zero); calls that overlap on the GPU
  *   race, so serialize them. The call returns after the lowering finished on

@@ -218,9 +218,16 @@ int check_status(igs_ctx* c) {
   if (r) return r;
   for (uint32_t n = 0; n < c->N; ++n) {
     const NodeDev& nd = c->nodes_host[n];
-    if (nd.status == ST_CAPACITY)
-      return fail_ctx(c, IGS_ERR_CAPACITY, "device table or output capacity exceeded on node " + std::to_string(n) +
-                                               " (table capacity " + std::to_string(nd.err_info) + ")");
+    if (nd.status == ST_CAPACITY) {
+      static const char* kinds[] = {"?", "scratch table (scratch_capacity)", "region-map heap (map_heap)",
+                                    "allocations (max_allocations / max_live_allocs)", "instructions / edges",
+                                    "boxes (max_boxes)", "bindings", "diagnostics", "buffers (max_buffers)",
+                                    "lookahead queue (max_queue)"};
+      const uint32_t k = nd.err_info >> 24;
+      return fail_ctx(c, IGS_ERR_CAPACITY, std::string("capacity exceeded on node ") + std::to_string(n) + ": " +
+                                               kinds[k < 10 ? k : 0] + ", capacity " +
+                                               std::to_string(nd.err_info & 0xFFFFFFu));
+    }
     if (nd.status == ST_TIMEOUT) return fail_ctx(c, IGS_ERR_TIMEOUT, "device wait timed out");
     if (nd.status != ST_OK) return fail_ctx(c, IGS_ERR_CUDA, "lowering engine internal error on node " + std::to_string(n));
   }
@@ -270,11 +277,10 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
   const uint32_t cap_edge = cfg->max_edges ? cfg->max_edges : 4 * cap_instr;
   const uint32_t cap_box = cfg->max_boxes ? cfg->max_boxes : 4 * cap_instr;
   const uint32_t cap_bind = 2 * cap_instr;
-  const uint32_t cap_bmap = cfg->map_capacity ? cfg->map_capacity : 4096;
+  const uint32_t cap_heap = cfg->map_heap ? cfg->map_heap : (1u << 20);
   const uint32_t cap_scr = cfg->scratch_capacity ? cfg->scratch_capacity : 4096;
   const uint32_t cap_buffers = cfg->max_buffers ? cfg->max_buffers : 64;
   const uint32_t cap_slots = cfg->max_live_allocs ? cfg->max_live_allocs : 1024;
-  const uint32_t cap_amap = cfg->alloc_map_capacity ? cfg->alloc_map_capacity : 256;
   const uint32_t cap_alloc = cfg->max_allocations ? cfg->max_allocations : (1u << 16);
   const uint32_t cap_queue = cfg->max_queue ? cfg->max_queue : (1u << 16);
   const uint32_t cap_qr = std::max<uint32_t>(4096, std::min<uint32_t>(1u << 16, 4 * cap_queue));
@@ -300,18 +306,8 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
     per += (bytes + 255) & ~(size_t)255;
     return off;
   };
-  const size_t o_own = take(table_bytes(cap_bmap) * cap_buffers);
-  const size_t o_bst = take(table_bytes(cap_bmap) * cap_buffers);
-  const size_t o_ownn = take(sizeof(uint32_t) * cap_buffers);
-  const size_t o_bstn = take(sizeof(uint32_t) * cap_buffers);
-  const size_t o_ownl = take(sizeof(uint32_t) * cap_buffers);
-  const size_t o_bstl = take(sizeof(uint32_t) * cap_buffers);
-  const size_t o_wr = take(table_bytes(cap_amap) * cap_slots);
-  const size_t o_rd = take(table_bytes(cap_amap) * cap_slots);
-  const size_t o_wrn = take(sizeof(uint32_t) * cap_slots);
-  const size_t o_rdn = take(sizeof(uint32_t) * cap_slots);
-  const size_t o_wrl = take(sizeof(uint32_t) * cap_slots);
-  const size_t o_rdl = take(sizeof(uint32_t) * cap_slots);
+  const size_t o_heap = take(table_bytes(cap_heap));
+  const size_t o_desc = take(sizeof(uint32_t) * 4 * (2 * cap_buffers + 2 * cap_slots));
   const size_t o_free = take(sizeof(uint32_t) * cap_slots);
   const size_t o_live = take(sizeof(uint32_t) * cap_slots);
   const size_t o_qr = take(table_bytes(cap_qr));
@@ -360,23 +356,17 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
     nd.cap_alloc = cap_alloc;
     nd.cap_queue = cap_queue;
     nd.cap_buffers = cap_buffers;
-    nd.cap_bmap = cap_bmap;
     nd.cap_slots = cap_slots;
-    nd.cap_amap = cap_amap;
     nd.cap_qr = cap_qr;
     nd.cap_scratch = cap_scr;
-    nd.own_base = reinterpret_cast<uint32_t*>(base + o_own);
-    nd.bst_base = reinterpret_cast<uint32_t*>(base + o_bst);
-    nd.own_n = reinterpret_cast<uint32_t*>(base + o_ownn);
-    nd.bst_n = reinterpret_cast<uint32_t*>(base + o_bstn);
-    nd.own_live = reinterpret_cast<uint32_t*>(base + o_ownl);
-    nd.bst_live = reinterpret_cast<uint32_t*>(base + o_bstl);
-    nd.wr_base = reinterpret_cast<uint32_t*>(base + o_wr);
-    nd.rd_base = reinterpret_cast<uint32_t*>(base + o_rd);
-    nd.wr_n = reinterpret_cast<uint32_t*>(base + o_wrn);
-    nd.rd_n = reinterpret_cast<uint32_t*>(base + o_rdn);
-    nd.wr_live = reinterpret_cast<uint32_t*>(base + o_wrl);
-    nd.rd_live = reinterpret_cast<uint32_t*>(base + o_rdl);
+    nd.heap = reinterpret_cast<uint32_t*>(base + o_heap);
+    nd.cap_heap = cap_heap;
+    nd.heap_top = 0;
+    for (int k = 0; k < kHeapClasses; ++k) nd.free_head[k] = NONE;
+    nd.own_d = reinterpret_cast<uint32_t*>(base + o_desc);
+    nd.bst_d = nd.own_d + 4 * cap_buffers;
+    nd.wr_d = nd.bst_d + 4 * cap_buffers;
+    nd.rd_d = nd.wr_d + 4 * cap_slots;
     nd.free_slots = reinterpret_cast<uint32_t*>(base + o_free);
     nd.live = reinterpret_cast<uint32_t*>(base + o_live);
     nd.qr_base = reinterpret_cast<uint32_t*>(base + o_qr);
@@ -397,10 +387,7 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
     igs_instruction i0{0, IGS_EPOCH, NONE, NONE, NONE, NONE, NONE, 0, 0, 0, 0};
     if (cudaMemcpy(nd.instrs, &i0, sizeof i0, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(nd.has_succ, 0, 1) != cudaSuccess ||
-        cudaMemset(nd.own_n, 0, sizeof(uint32_t) * cap_buffers) != cudaSuccess ||
-        cudaMemset(nd.bst_n, 0, sizeof(uint32_t) * cap_buffers) != cudaSuccess ||
-        cudaMemset(nd.own_live, 0, sizeof(uint32_t) * cap_buffers) != cudaSuccess ||
-        cudaMemset(nd.bst_live, 0, sizeof(uint32_t) * cap_buffers) != cudaSuccess ||
+        cudaMemset(nd.own_d, 0, sizeof(uint32_t) * 4 * (2 * cap_buffers + 2 * cap_slots)) != cudaSuccess ||
         cudaMemcpy(nd.free_slots, slots.data(), sizeof(uint32_t) * cap_slots, cudaMemcpyHostToDevice) != cudaSuccess) {
       igs_destroy(c);
       return IGS_ERR_CUDA;
@@ -1086,14 +1073,16 @@ struct HEntry {
   uint32_t key, lo[3], hi[3], v[3];
 };
 
-// Reads slab `idx` (cap entries per slab) with its count from the device.
-int read_slab(igs_ctx* c, const uint32_t* base, const uint32_t* counts, uint32_t idx, uint32_t cap, std::vector<HEntry>& out) {
+// Reads the heap table behind descriptor `desc` {offset, cap, n, live} of a
+// node from the device.
+int read_slab(igs_ctx* c, const NodeDev& nd, const uint32_t* desc, std::vector<HEntry>& out) {
   out.clear();
-  uint32_t n = 0;
-  CK(cudaMemcpy(&n, counts + idx, sizeof n, cudaMemcpyDeviceToHost));
-  if (n == 0) return IGS_OK;
+  uint32_t d[4];
+  CK(cudaMemcpy(d, desc, sizeof d, cudaMemcpyDeviceToHost));
+  const uint32_t n = d[2];
+  if (d[1] == 0 || n == 0) return IGS_OK;
   std::vector<uint32_t> raw((size_t)F_COUNT * n);
-  const uint32_t* t = base + (size_t)idx * cap * F_COUNT;
+  const uint32_t* t = nd.heap + (size_t)d[0] * F_COUNT;
   CK(cudaMemcpy(raw.data(), t, sizeof(uint32_t) * F_COUNT * n, cudaMemcpyDeviceToHost));
   for (uint32_t i = 0; i < n; ++i) {
     const uint32_t* w = raw.data() + (size_t)i * F_COUNT;
@@ -1140,7 +1129,7 @@ extern "C" int igs_read_buffer(igs_ctx* c, uint32_t b, const uint32_t lo[3], con
   std::vector<HEntry> own, bst;
   {
     const NodeDev& n0 = c->nodes_host[0];
-    r = read_slab(c, n0.own_base, n0.own_n, b, n0.cap_bmap, own);
+    r = read_slab(c, n0, n0.own_d + 4 * b, own);
     if (r) return r;
   }
   Pending p;
@@ -1157,7 +1146,7 @@ extern "C" int igs_read_buffer(igs_ctx* c, uint32_t b, const uint32_t lo[3], con
     const uint32_t o = e.v[0];
     {
       const NodeDev& no = c->nodes_host[o];
-      r = read_slab(c, no.bst_base, no.bst_n, b, no.cap_bmap, bst);
+      r = read_slab(c, no, no.bst_d + 4 * b, bst);
       if (r) return r;
     }
     for (const HEntry& f : bst) {

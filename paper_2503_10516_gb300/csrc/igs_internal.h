@@ -26,6 +26,12 @@ struct BufDesc {
 
 enum Status : uint32_t { ST_OK = 0, ST_CAPACITY = 1, ST_INTERNAL = 2, ST_TIMEOUT = 3 };
 
+// What ran out on ST_CAPACITY: NodeDev::err_info = kind << 24 | capacity.
+enum CapKind : uint32_t {
+  CAP_TABLE = 1, CAP_HEAP = 2, CAP_ALLOC = 3, CAP_EDGE = 4, CAP_BOX = 5, CAP_BIND = 6, CAP_DIAG = 7,
+  CAP_BUFFERS = 8, CAP_QUEUE = 9
+};
+
 // Field layout of a box-table entry: 12 words (48 bytes, 16-byte aligned) so
 // an entry loads with three 16-byte vector loads; F_COUNT is the stride.
 enum TableField : int { F_KEY = 0, F_LO = 1, F_HI = 4, F_V = 7, F_COUNT = 12 };
@@ -33,10 +39,12 @@ enum TableField : int { F_KEY = 0, F_LO = 1, F_HI = 4, F_V = 7, F_COUNT = 12 };
 struct Table {
   uint32_t* base;  // cap entries of F_COUNT words
   uint32_t n, cap;
-  uint32_t* np;    // persistent count of a slab table (nullptr for scratch tables)
   uint32_t live;   // entries not marked dead
-  uint32_t* lp;    // persistent live count (nullptr for scratch tables)
+  uint32_t* dp;    // heap table descriptor {offset, cap, n, live}; nullptr for scratch tables
 };
+
+// Size classes of the per-node entry heap: 32 << k entries.
+constexpr int kHeapClasses = 24;
 
 struct AllocRec {
   uint32_t buffer, mem, live, user;
@@ -57,21 +65,19 @@ struct NodeDev {
   uint64_t prof[16];   // clock cycles per lowering phase (see the engine)
   // capacities
   uint32_t cap_instr, cap_edge, cap_box, cap_bind, cap_diag, cap_rej, cap_alloc, cap_queue;
-  uint32_t cap_buffers, cap_bmap, cap_slots, cap_amap, cap_qr, cap_scratch;
-  // per-buffer slab tables: node-level ownership, local buffer state
-  uint32_t* own_base;  // cap_buffers slabs of cap_bmap entries
-  uint32_t* own_n;
-  uint32_t* own_live;
-  uint32_t* bst_base;
-  uint32_t* bst_n;
-  uint32_t* bst_live;
-  // per-allocation slab tables: last writers, readers since the last write
-  uint32_t* wr_base;   // cap_slots slabs of cap_amap entries
-  uint32_t* wr_n;
-  uint32_t* wr_live;
-  uint32_t* rd_base;
-  uint32_t* rd_n;
-  uint32_t* rd_live;
+  uint32_t cap_buffers, cap_slots, cap_qr, cap_scratch;
+  // entry heap holding every region-map table of the node (size classes,
+  // free lists threaded through the first word of a free slab)
+  uint32_t* heap;      // cap_heap entries of F_COUNT words
+  uint32_t cap_heap, heap_top;
+  uint32_t free_head[kHeapClasses];
+  // table descriptors {offset, cap, n, live}: per buffer the node-level
+  // ownership map and the local buffer state; per allocation slot its last
+  // writers and readers since the last write
+  uint32_t* own_d;
+  uint32_t* bst_d;
+  uint32_t* wr_d;
+  uint32_t* rd_d;
   uint32_t* free_slots;
   uint32_t* live;      // ids of live allocations, ascending
   // per-task push and await regions (key = task sequence number)

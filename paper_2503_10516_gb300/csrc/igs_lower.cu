@@ -163,7 +163,7 @@ struct Ctx {
   const ProgDev* pg;
   uint32_t lane, err, err_info;
   uint32_t node, N, D;
-  uint32_t epoch, last_horizon, last_sync, next_msg, n_alloc, n_free, n_live;
+  uint32_t epoch, last_horizon, last_sync, next_msg, n_alloc, n_free, n_live, heap_top;
   uint32_t n_instr, n_edge, n_box, n_bind, n_diag, n_rej;
   uint32_t lookahead, q_head, q_count;
   Table qr;
@@ -173,6 +173,13 @@ struct Ctx {
 
 __device__ __forceinline__ void fail(Ctx& c, uint32_t code) {
   if (c.err == ST_OK) c.err = code;
+}
+// A capacity failure records what ran out and its capacity for the host.
+__device__ __forceinline__ void fail_cap(Ctx& c, CapKind what, uint32_t cap) {
+  if (c.err == ST_OK) {
+    c.err = ST_CAPACITY;
+    c.err_info = ((uint32_t)what << 24) | (cap < 0xFFFFFFu ? cap : 0xFFFFFFu);
+  }
 }
 
 // Phase cycle accounting (lane 0 adds to the node's counters).
@@ -189,23 +196,91 @@ __device__ __forceinline__ PhaseTimer pt_start() {
   return p;
 }
 
+// ---- the node's entry heap ---------------------------------------------------
+
+__device__ __forceinline__ int heap_class(uint32_t entries) {
+  int k = 0;
+  while ((32u << k) < entries && k < kHeapClasses - 1) ++k;
+  return k;
+}
+
+// A slab of at least `entries` entries (uniform); NONE when the heap is full.
+__device__ uint32_t heap_alloc(Ctx& c, uint32_t entries, uint32_t& cap) {
+  const int k = heap_class(entries);
+  cap = 32u << k;
+  NodeDev* nd = c.nd;
+  __syncwarp();
+  const uint32_t head = nd->free_head[k];
+  if (head != NONE) {
+    const uint32_t next = nd->heap[(size_t)head * F_COUNT];
+    __syncwarp();
+    if (c.lane == 0) nd->free_head[k] = next;
+    __syncwarp();
+    return head;
+  }
+  if ((uint64_t)c.heap_top + cap > nd->cap_heap) {
+    fail_cap(c, CAP_HEAP, nd->cap_heap);
+    return NONE;
+  }
+  const uint32_t off = c.heap_top;
+  c.heap_top += cap;
+  return off;
+}
+
+__device__ void heap_free(Ctx& c, uint32_t off, uint32_t cap) {
+  const int k = heap_class(cap);
+  NodeDev* nd = c.nd;
+  __syncwarp();
+  if (c.lane == 0) {
+    nd->heap[(size_t)off * F_COUNT] = nd->free_head[k];
+    nd->free_head[k] = off;
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void t_publish(Ctx& c, Table& t) {
+  if (t.dp && c.lane == 0) {
+    t.dp[2] = t.n;
+    t.dp[3] = t.live;
+  }
+}
+
+// Grows a heap table to hold `need` entries: the entries move to a bigger
+// slab at the same indices (a scan in progress stays valid through `t`).
+__device__ bool t_grow(Ctx& c, Table& t, uint32_t need) {
+  if (!t.dp) {
+    fail_cap(c, CAP_TABLE, t.cap);
+    return false;
+  }
+  uint32_t cap = 0;
+  const uint32_t off = heap_alloc(c, need > 2 * t.cap ? need : 2 * t.cap, cap);
+  if (off == NONE) return false;
+  uint4* dst = reinterpret_cast<uint4*>(c.nd->heap + (size_t)off * F_COUNT);
+  const uint4* src = reinterpret_cast<const uint4*>(t.base);
+  const uint32_t words4 = t.n * (F_COUNT / 4);
+  for (uint32_t i = c.lane; i < words4; i += 32) dst[i] = src[i];
+  __syncwarp();
+  heap_free(c, t.dp[0], t.cap);
+  if (c.lane == 0) {
+    t.dp[0] = off;
+    t.dp[1] = cap;
+  }
+  __syncwarp();
+  t.base = c.nd->heap + (size_t)off * F_COUNT;
+  t.cap = cap;
+  return true;
+}
+
 // Claims one slot per predicated lane (all lanes call). NONE on overflow.
 __device__ __forceinline__ uint32_t t_claim(Ctx& c, Table& t, bool pred) {
   const uint32_t m = __ballot_sync(FULL, pred);
   const uint32_t slot = t.n + __popc(m & lanemask_lt());
   const uint32_t nn = t.n + __popc(m);
-  if (nn > t.cap) {
-    fail(c, ST_CAPACITY);
-    c.err_info = t.cap;
-    return NONE;
-  }
+  if (nn > t.cap && !t_grow(c, t, nn)) return NONE;
   t.n = nn;
   t.live += __popc(m);
   c.map_writes += __popc(m);
-  if (t.np && c.lane == 0) {
-    *t.np = nn;
-    *t.lp = t.live;
-  }
+  t_publish(c, t);
   return pred ? slot : NONE;
 }
 // Claims k consecutive slots per lane; returns this lane's first slot.
@@ -218,18 +293,11 @@ __device__ __forceinline__ uint32_t t_claim_n(Ctx& c, Table& t, uint32_t k) {
   }
   const uint32_t total = __shfl_sync(FULL, x, 31);
   const uint32_t first = t.n + x - k;
-  if (t.n + total > t.cap) {
-    fail(c, ST_CAPACITY);
-    c.err_info = t.cap;
-    return NONE;
-  }
+  if (t.n + total > t.cap && !t_grow(c, t, t.n + total)) return NONE;
   t.n += total;
   t.live += total;
   c.map_writes += total;
-  if (t.np && c.lane == 0) {
-    *t.np = t.n;
-    *t.lp = t.live;
-  }
+  t_publish(c, t);
   return first;
 }
 
@@ -241,7 +309,7 @@ __device__ __forceinline__ void t_reset(Table& t) {
 // k entries of t were marked dead.
 __device__ __forceinline__ void t_dead(Ctx& c, Table& t, uint32_t k) {
   t.live -= k;
-  if (t.lp && c.lane == 0) *t.lp = t.live;
+  t_publish(c, t);
 }
 
 template <class P>
@@ -319,10 +387,7 @@ __device__ void t_compact(Ctx& c, Table& t) {
   }
   t.n = w;
   t.live = w;
-  if (t.np && c.lane == 0) {
-    *t.np = w;
-    *t.lp = w;
-  }
+  t_publish(c, t);
   __syncwarp();
 }
 
@@ -549,15 +614,11 @@ __device__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_t from, uint3
     if (live) t_put(W, s, 0, b, 0, 0, 0);
   }
   __syncwarp();
-  if (W.n > 512) {  // the pairwise rewrite is quadratic per step: bound its input
-    fail(c, ST_CAPACITY);
-    return 0;
-  }
   if (W.n > 1) {
     for (int phase = 0; phase < 3; ++phase) {
       const int md = 2 - phase;  // dimension merged in this phase
-      for (int guard = 0;; ++guard) {
-        if (guard > 20000) {
+      for (uint32_t guard = 0;; ++guard) {
+        if (guard > 64u * W.cap) {  // every step merges or splits: unreachable for valid input
           fail(c, ST_INTERNAL);
           return 0;
         }
@@ -629,7 +690,7 @@ __device__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_t from, uint3
   // rank sort into out
   const uint32_t n = W.n;
   if (out.n + n > out.cap) {
-    fail(c, ST_CAPACITY);
+    fail_cap(c, CAP_TABLE, out.cap);
     return 0;
   }
   for (uint32_t base = 0; base < n; base += 32) {
@@ -649,41 +710,65 @@ __device__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_t from, uint3
 
 // ---- node state helpers ----------------------------------------------------
 
-__device__ __forceinline__ Table slab(uint32_t* base, uint32_t* ns, uint32_t* ls, uint32_t idx, uint32_t cap) {
-  __syncwarp();
+// A heap table from its descriptor {offset, cap, n, live} (no warp sync: safe
+// in divergent code).
+__device__ __forceinline__ Table heap_table(const NodeDev* nd, uint32_t* d) {
   Table t;
-  t.base = base + (size_t)idx * cap * F_COUNT;
-  t.n = ns[idx];
-  t.cap = cap;
-  t.np = ns + idx;
-  t.live = ls[idx];
-  t.lp = ls + idx;
+  t.base = nd->heap + (size_t)d[0] * F_COUNT;
+  t.cap = d[1];
+  t.n = d[2];
+  t.live = d[3];
+  t.dp = d;
   return t;
 }
+__device__ __forceinline__ Table slab(const Ctx& c, uint32_t* d) {
+  __syncwarp();
+  return heap_table(c.nd, d);
+}
 // Node-level ownership map of a buffer (owner node, replication mask).
-__device__ __forceinline__ Table own_t(const Ctx& c, uint32_t b) {
-  return slab(c.nd->own_base, c.nd->own_n, c.nd->own_live, b, c.nd->cap_bmap);
-}
+__device__ __forceinline__ Table own_t(const Ctx& c, uint32_t b) { return slab(c, c.nd->own_d + 4 * b); }
 // Local state of a buffer (original producer, its memory, up-to-date memories).
-__device__ __forceinline__ Table bst_t(const Ctx& c, uint32_t b) {
-  return slab(c.nd->bst_base, c.nd->bst_n, c.nd->bst_live, b, c.nd->cap_bmap);
-}
+__device__ __forceinline__ Table bst_t(const Ctx& c, uint32_t b) { return slab(c, c.nd->bst_d + 4 * b); }
 // Last writers / readers since the last write of an allocation.
 __device__ __forceinline__ Table wr_t(const Ctx& c, uint32_t aid) {
-  return slab(c.nd->wr_base, c.nd->wr_n, c.nd->wr_live, c.nd->allocs[aid].slot, c.nd->cap_amap);
+  return slab(c, c.nd->wr_d + 4 * c.nd->allocs[aid].slot);
 }
 __device__ __forceinline__ Table rd_t(const Ctx& c, uint32_t aid) {
-  return slab(c.nd->rd_base, c.nd->rd_n, c.nd->rd_live, c.nd->allocs[aid].slot, c.nd->cap_amap);
+  return slab(c, c.nd->rd_d + 4 * c.nd->allocs[aid].slot);
+}
+
+// A fresh empty heap table behind descriptor d.
+__device__ bool table_new(Ctx& c, uint32_t* d, uint32_t entries) {
+  uint32_t cap = 0;
+  const uint32_t off = heap_alloc(c, entries, cap);
+  if (off == NONE) return false;
+  __syncwarp();
+  if (c.lane == 0) {
+    d[0] = off;
+    d[1] = cap;
+    d[2] = 0;
+    d[3] = 0;
+  }
+  __syncwarp();
+  return true;
+}
+__device__ void table_free(Ctx& c, uint32_t* d) {
+  __syncwarp();
+  const uint32_t off = d[0], cap = d[1];
+  if (cap) heap_free(c, off, cap);
+  if (c.lane == 0) d[1] = 0;
+  __syncwarp();
 }
 
 // Registers a new allocation record with an empty writer / reader slab.
 __device__ bool new_alloc(Ctx& c, uint32_t aid, uint32_t b, uint32_t m, const Bx& bb, uint32_t user) {
   if (aid >= c.nd->cap_alloc || c.n_free == 0) {
-    fail(c, ST_CAPACITY);
+    fail_cap(c, CAP_ALLOC, c.n_free == 0 ? c.nd->cap_slots : c.nd->cap_alloc);
     return false;
   }
   c.n_free -= 1;
   const uint32_t slot = c.nd->free_slots[c.n_free];
+  if (!table_new(c, c.nd->wr_d + 4 * slot, 32) || !table_new(c, c.nd->rd_d + 4 * slot, 32)) return false;
   if (c.lane == 0) {
     AllocRec rec;
     rec.buffer = b;
@@ -697,10 +782,6 @@ __device__ bool new_alloc(Ctx& c, uint32_t aid, uint32_t b, uint32_t m, const Bx
     rec.mark = NONE;
     rec.slot = slot;
     c.nd->allocs[aid] = rec;
-    c.nd->wr_n[slot] = 0;
-    c.nd->rd_n[slot] = 0;
-    c.nd->wr_live[slot] = 0;
-    c.nd->rd_live[slot] = 0;
     c.nd->live[c.n_live] = aid;  // ids grow: the list stays sorted
   }
   c.n_live += 1;
@@ -711,6 +792,8 @@ __device__ bool new_alloc(Ctx& c, uint32_t aid, uint32_t b, uint32_t m, const Bx
 // Drops an allocation: its slab goes back to the free list.
 __device__ void drop_alloc(Ctx& c, uint32_t aid) {
   const uint32_t slot = c.nd->allocs[aid].slot;
+  table_free(c, c.nd->wr_d + 4 * slot);
+  table_free(c, c.nd->rd_d + 4 * slot);
   __syncwarp();
   if (c.lane == 0) {
     c.nd->allocs[aid].live = 0;
@@ -838,7 +921,7 @@ __device__ Bx map_box(const igs_accessor& a, const Bx& ch, const BufDesc& buf) {
 __device__ void task_mapped(Ctx& c, const igs_task& t, const Table& CH, Table& MP) {
   const uint32_t na = t.num_accessors, total = CH.n * na;
   if (total > MP.cap) {
-    fail(c, ST_CAPACITY);
+    fail_cap(c, CAP_TABLE, MP.cap);
     return;
   }
   for (uint32_t base = 0; base < total; base += 32) {
@@ -915,13 +998,13 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
     for (int k = 0; k < nacc; ++k) {
       const Acc& A = acc[k];
       const uint32_t slot = nd->allocs[A.alloc].slot;
-      const uint32_t wn = nd->wr_n[slot], rn = nd->rd_n[slot];
+      const uint32_t wn = nd->wr_d[4 * slot + 2], rn = nd->rd_d[4 * slot + 2];
       for (uint32_t r = A.from; r < A.to; ++r) {
         if (t_key(*A.t, r) == DEAD) continue;
         const Bx q = t_box(*A.t, r);
         for (int tab = 0; tab < ((A.mode & IGS_WRITE) ? 2 : 1); ++tab) {
           if (PR.n >= PR.cap) {
-            fail(c, ST_CAPACITY);
+            fail_cap(c, CAP_TABLE, PR.cap);
             return NONE;
           }
           if (c.lane == 0) t_put(PR, PR.n, (uint32_t)tab, q, slot, total, A.mode);
@@ -941,9 +1024,7 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
         uint32_t p = 0;
         while (p + 1 < np && t_v(PR, 1, p + 1) <= f) ++p;
         const uint32_t tab = t_key(PR, p), slot = t_v(PR, 0, p), mode = t_v(PR, 2, p);
-        Table T;
-        T.base = (tab == 0 ? nd->wr_base : nd->rd_base) + (size_t)slot * nd->cap_amap * F_COUNT;
-        T.cap = nd->cap_amap;
+        const Table T = heap_table(nd, (tab == 0 ? nd->wr_d : nd->rd_d) + 4 * slot);
         const uint32_t j = f - t_v(PR, 1, p);
         if (t_key(T, j) != DEAD && bx_overlap(t_box(T, j), t_box(PR, p))) {
           hit = true;
@@ -1002,7 +1083,7 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
     }
     n_unique = __popc(__ballot_sync(FULL, lead));
     if (c.n_edge + n_unique > nd->cap_edge || c.n_instr + 1 > nd->cap_instr) {
-      fail(c, ST_CAPACITY);
+      fail_cap(c, CAP_EDGE, nd->cap_edge);
       return NONE;
     }
     if (c.lane < n_unique) {
@@ -1029,7 +1110,7 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
       n_unique += __popc(__ballot_sync(FULL, first));
     }
     if (c.n_edge + n_unique > nd->cap_edge || c.n_instr + 1 > nd->cap_instr) {
-      fail(c, ST_CAPACITY);
+      fail_cap(c, CAP_EDGE, nd->cap_edge);
       return NONE;
     }
     for (uint32_t base = 0; base < nd0; base += 32) {
@@ -1073,7 +1154,7 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
       const bool live = i < bto && t_key(*bt, i) != DEAD;
       const uint32_t m = __ballot_sync(FULL, live);
       if (c.n_box + nb + __popc(m) > nd->cap_box) {
-        fail(c, ST_CAPACITY);
+        fail_cap(c, CAP_BOX, nd->cap_box);
         return NONE;
       }
       if (live) {
@@ -1089,7 +1170,7 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
     }
   }
   if (c.n_bind + bind_n > nd->cap_bind) {
-    fail(c, ST_CAPACITY);
+    fail_cap(c, CAP_BIND, nd->cap_bind);
     return NONE;
   }
   if (bindt && c.lane < bind_n) {
@@ -1198,6 +1279,7 @@ __device__ void apply_epoch(Ctx& c, uint32_t h) {
   }
   const uint32_t nb = c.nd->cap_buffers;
   for (uint32_t b = 0; b < nb; ++b) {
+    if (c.nd->bst_d[4 * b + 1] == 0) continue;  // no table (never created or destroyed)
     Table B = bst_t(c, b);
     if (B.n == 0) continue;
     map_ids(c, B, h);
@@ -1745,7 +1827,7 @@ __device__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq, const Table
       if (ci == NONE) break;
       const Bx bb = t_box(CL, ci);
       if (c.n_alloc >= c.nd->cap_alloc) {
-        fail(c, ST_CAPACITY);
+        fail_cap(c, CAP_ALLOC, c.nd->cap_alloc);
         return;
       }
       const uint32_t aid = c.n_alloc;
@@ -2046,10 +2128,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
           hit = !bx_empty(x);
           if (hit) {
             const uint32_t b = t.acc[a].buffer, m = t_v(CH, 1, slot);
-            Table B;
-            B.base = c.nd->bst_base + (size_t)b * c.nd->cap_bmap * F_COUNT;
-            B.n = c.nd->bst_n[b];
-            B.cap = c.nd->cap_bmap;
+            const Table B = heap_table(c.nd, c.nd->bst_d + 4 * b);
             for (uint32_t j = 0; j < B.n; ++j) {
               if (t_key(B, j) == DEAD || !bx_overlap(t_box(B, j), x)) continue;
               const uint32_t prod = t_v(B, 0, j), mask = t_v(B, 2, j);
@@ -2073,7 +2152,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
     const Bx x = t_box(PC, k);
     if (flags & 1u) {  // uninitialized read warning (Sec. 4.4)
       if (c.n_diag >= c.nd->cap_diag) {
-        fail(c, ST_CAPACITY);
+        fail_cap(c, CAP_DIAG, c.nd->cap_diag);
         return;
       }
       if (c.lane == 0) {
@@ -2110,7 +2189,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
   {
     const uint32_t total = CH.n * na;
     if (total > AL.cap) {
-      fail(c, ST_CAPACITY);
+      fail_cap(c, CAP_TABLE, AL.cap);
       return;
     }
     const AllocRec* A = c.nd->allocs;
@@ -2215,14 +2294,10 @@ __device__ void process(Ctx& c, uint32_t item) {
       const BufDesc& bd = buf_of(c, it.arg);
       const Bx dom = buffer_box(bd);
       if (it.arg >= c.nd->cap_buffers) {
-        fail(c, ST_CAPACITY);
+        fail_cap(c, CAP_BUFFERS, c.nd->cap_buffers);
         return;
       }
-      if (c.lane == 0) {
-        c.nd->bst_n[it.arg] = 0;
-        c.nd->bst_live[it.arg] = 0;
-      }
-      __syncwarp();
+      if (!table_new(c, c.nd->bst_d + 4 * it.arg, 32)) return;
       Table B = bst_t(c, it.arg);
       if (bd.init) {
         const uint32_t aid = c.n_alloc;
@@ -2301,11 +2376,7 @@ __device__ void process(Ctx& c, uint32_t item) {
             drop_alloc(c, aid);
           }
         }
-      if (c.lane == 0) {
-        c.nd->bst_n[b] = 0;
-        c.nd->bst_live[b] = 0;
-      }
-      __syncwarp();
+      table_free(c, c.nd->bst_d + 4 * b);
       break;
     }
     default:
@@ -2331,7 +2402,7 @@ __device__ void flush_queue(Ctx& c) {
 
 __device__ void enqueue(Ctx& c, uint32_t item) {
   if (c.q_count >= c.nd->cap_queue) {
-    fail(c, ST_CAPACITY);
+    fail_cap(c, CAP_QUEUE, c.nd->cap_queue);
     return;
   }
   if (c.lane == 0) c.nd->queue[(c.q_head + c.q_count) % c.nd->cap_queue] = item;
@@ -2355,15 +2426,11 @@ __device__ void deliver(Ctx& c, uint32_t item) {
   }
   if (it.kind == IT_CREATE) {
     if (it.arg >= c.nd->cap_buffers) {
-      fail(c, ST_CAPACITY);
+      fail_cap(c, CAP_BUFFERS, c.nd->cap_buffers);
       return;
     }
     const BufDesc& bd = buf_of(c, it.arg);
-    if (c.lane == 0) {
-      c.nd->own_n[it.arg] = 0;
-      c.nd->own_live[it.arg] = 0;
-    }
-    __syncwarp();
+    if (!table_new(c, c.nd->own_d + 4 * it.arg, 32)) return;
     Table O = own_t(c, it.arg);
     const uint32_t s = t_claim(c, O, c.lane == 0);
     if (c.err) return;
@@ -2409,13 +2476,7 @@ __device__ void deliver(Ctx& c, uint32_t item) {
     if (it.kind == IT_EPOCH || it.kind == IT_DESTROY || queued_tasks(c) > c.lookahead) flush_queue(c);
   }
   if (c.err) return;
-  if (it.kind == IT_DESTROY) {
-    if (c.lane == 0) {
-      c.nd->own_n[it.arg] = 0;
-      c.nd->own_live[it.arg] = 0;
-    }
-    __syncwarp();
-  }
+  if (it.kind == IT_DESTROY) table_free(c, c.nd->own_d + 4 * it.arg);
 }
 
 __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg) {
@@ -2434,6 +2495,7 @@ __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg) {
   c.n_alloc = nd->n_alloc;
   c.n_free = nd->n_free;
   c.n_live = nd->n_live;
+  c.heap_top = nd->heap_top;
   c.n_instr = nd->n_instr;
   c.n_edge = nd->n_edge;
   c.n_box = nd->n_box;
@@ -2446,16 +2508,14 @@ __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg) {
   c.qr.base = nd->qr_base;
   c.qr.n = nd->qr_n;
   c.qr.cap = nd->cap_qr;
-  c.qr.np = nullptr;
   c.qr.live = nd->qr_live;
-  c.qr.lp = nullptr;
+  c.qr.dp = nullptr;
   for (int k = 0; k < 14; ++k) {
     c.s[k].base = nd->scratch_base + (size_t)k * nd->cap_scratch * F_COUNT;
     c.s[k].n = 0;
     c.s[k].cap = nd->cap_scratch;
-    c.s[k].np = nullptr;
     c.s[k].live = 0;
-    c.s[k].lp = nullptr;
+    c.s[k].dp = nullptr;
   }
   c.map_reads = 0;
   c.map_writes = 0;
@@ -2475,6 +2535,7 @@ __device__ void store_ctx(Ctx& c, uint32_t cursor) {
   nd->n_alloc = c.n_alloc;
   nd->n_free = c.n_free;
   nd->n_live = c.n_live;
+  nd->heap_top = c.heap_top;
   nd->n_instr = c.n_instr;
   nd->n_edge = c.n_edge;
   nd->n_box = c.n_box;

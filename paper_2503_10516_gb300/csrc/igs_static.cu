@@ -26,14 +26,13 @@ std::mutex g_mu;
 uint8_t* g_base[kMaxDevices] = {};
 
 // Per-node capacities of this variant (modest, fixed).
-constexpr uint32_t kBuffers = 16, kBmap = 512, kSlots = 128, kAmap = 128, kQr = 2048, kScratch = 1024;
+constexpr uint32_t kBuffers = 16, kHeap = 1u << 15, kSlots = 128, kQr = 2048, kScratch = 1024;
 constexpr uint32_t kAlloc = 4096, kQueue = 4096, kRej = 256;
 
 size_t tbytes(uint32_t cap) { return (size_t)igs::F_COUNT * cap * sizeof(uint32_t); }
 
 struct Layout {
-  size_t per_node, o_own, o_bst, o_ownn, o_bstn, o_ownl, o_bstl, o_wr, o_rd, o_wrn, o_rdn, o_wrl, o_rdl, o_free,
-      o_live, o_qr, o_alloc, o_queue, o_succ, o_rej, o_scr;
+  size_t per_node, o_heap, o_desc, o_free, o_live, o_qr, o_alloc, o_queue, o_succ, o_rej, o_scr;
 };
 
 Layout layout(uint32_t cap_instr) {
@@ -44,18 +43,8 @@ Layout layout(uint32_t cap_instr) {
     p += (b + 255) & ~(size_t)255;
     return o;
   };
-  L.o_own = take(tbytes(kBmap) * kBuffers);
-  L.o_bst = take(tbytes(kBmap) * kBuffers);
-  L.o_ownn = take(4 * kBuffers);
-  L.o_bstn = take(4 * kBuffers);
-  L.o_ownl = take(4 * kBuffers);
-  L.o_bstl = take(4 * kBuffers);
-  L.o_wr = take(tbytes(kAmap) * kSlots);
-  L.o_rd = take(tbytes(kAmap) * kSlots);
-  L.o_wrn = take(4 * kSlots);
-  L.o_rdn = take(4 * kSlots);
-  L.o_wrl = take(4 * kSlots);
-  L.o_rdl = take(4 * kSlots);
+  L.o_heap = take(tbytes(kHeap));
+  L.o_desc = take(16 * (2 * kBuffers + 2 * kSlots));
   L.o_free = take(4 * kSlots);
   L.o_live = take(4 * kSlots);
   L.o_qr = take(tbytes(kQr));
@@ -192,23 +181,17 @@ extern "C" int igs_lower_static(const igs_config* cfg, const igs_static_buffer* 
     nd.cap_alloc = kAlloc;
     nd.cap_queue = kQueue;
     nd.cap_buffers = kBuffers;
-    nd.cap_bmap = kBmap;
     nd.cap_slots = kSlots;
-    nd.cap_amap = kAmap;
     nd.cap_qr = kQr;
     nd.cap_scratch = kScratch;
-    nd.own_base = reinterpret_cast<uint32_t*>(nb + L.o_own);
-    nd.bst_base = reinterpret_cast<uint32_t*>(nb + L.o_bst);
-    nd.own_n = reinterpret_cast<uint32_t*>(nb + L.o_ownn);
-    nd.bst_n = reinterpret_cast<uint32_t*>(nb + L.o_bstn);
-    nd.own_live = reinterpret_cast<uint32_t*>(nb + L.o_ownl);
-    nd.bst_live = reinterpret_cast<uint32_t*>(nb + L.o_bstl);
-    nd.wr_base = reinterpret_cast<uint32_t*>(nb + L.o_wr);
-    nd.rd_base = reinterpret_cast<uint32_t*>(nb + L.o_rd);
-    nd.wr_n = reinterpret_cast<uint32_t*>(nb + L.o_wrn);
-    nd.rd_n = reinterpret_cast<uint32_t*>(nb + L.o_rdn);
-    nd.wr_live = reinterpret_cast<uint32_t*>(nb + L.o_wrl);
-    nd.rd_live = reinterpret_cast<uint32_t*>(nb + L.o_rdl);
+    nd.heap = reinterpret_cast<uint32_t*>(nb + L.o_heap);
+    nd.cap_heap = kHeap;
+    nd.heap_top = 0;
+    for (int k = 0; k < igs::kHeapClasses; ++k) nd.free_head[k] = NONE;
+    nd.own_d = reinterpret_cast<uint32_t*>(nb + L.o_desc);
+    nd.bst_d = nd.own_d + 4 * kBuffers;
+    nd.wr_d = nd.bst_d + 4 * kBuffers;
+    nd.rd_d = nd.wr_d + 4 * kSlots;
     nd.free_slots = reinterpret_cast<uint32_t*>(nb + L.o_free);
     nd.live = reinterpret_cast<uint32_t*>(nb + L.o_live);
     nd.qr_base = reinterpret_cast<uint32_t*>(nb + L.o_qr);
@@ -246,10 +229,7 @@ extern "C" int igs_lower_static(const igs_config* cfg, const igs_static_buffer* 
   if (num_buffers) CKS(cudaMemcpyAsync(base + o_bufs, bd.data(), sizeof(BufDesc) * num_buffers, cudaMemcpyHostToDevice, stream));
   for (uint32_t n = 0; n < N; ++n) {
     uint8_t* nb = base + o_state + L.per_node * n;
-    CKS(cudaMemsetAsync(nb + L.o_ownn, 0, 4 * kBuffers, stream));
-    CKS(cudaMemsetAsync(nb + L.o_bstn, 0, 4 * kBuffers, stream));
-    CKS(cudaMemsetAsync(nb + L.o_ownl, 0, 4 * kBuffers, stream));
-    CKS(cudaMemsetAsync(nb + L.o_bstl, 0, 4 * kBuffers, stream));
+    CKS(cudaMemsetAsync(nb + L.o_desc, 0, 16 * (2 * kBuffers + 2 * kSlots), stream));
     CKS(cudaMemsetAsync(nb + L.o_succ, 0, 1, stream));
     CKS(cudaMemcpyAsync(nb + L.o_free, slots.data(), 4 * kSlots, cudaMemcpyHostToDevice, stream));
     CKS(cudaMemcpyAsync(outs[n].instrs, &i0, sizeof i0, cudaMemcpyHostToDevice, stream));

@@ -18,6 +18,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libigs.so")
 
 IGS_OK = 0
+IGS_ERR_INVALID_ARG, IGS_ERR_OVERLAPPING_WRITE, IGS_ERR_CAPACITY, IGS_ERR_TRUNCATED = -1, -2, -3, -4
+IGS_ERR_TIMEOUT, IGS_ERR_CUDA, IGS_ERR_BUDGET, IGS_ERR_STATE = -5, -6, -7, -8
 ERRORS = {-1: "INVALID_ARG", -2: "OVERLAPPING_WRITE", -3: "CAPACITY", -4: "TRUNCATED", -5: "TIMEOUT",
           -6: "CUDA", -7: "BUDGET", -8: "STATE"}
 MODE_PLAIN, MODE_BATCHED = 0, 1
@@ -41,9 +43,9 @@ class Config(ctypes.Structure):
     _fields_ = [("num_nodes", ctypes.c_uint32), ("devices_per_node", ctypes.c_uint32),
                 ("horizon_step", ctypes.c_uint32), ("lookahead", ctypes.c_uint32), ("mode", ctypes.c_uint32),
                 ("max_instructions", ctypes.c_uint32), ("max_edges", ctypes.c_uint32),
-                ("max_boxes", ctypes.c_uint32), ("map_capacity", ctypes.c_uint32),
+                ("max_boxes", ctypes.c_uint32), ("map_heap", ctypes.c_uint32),
                 ("scratch_capacity", ctypes.c_uint32), ("max_buffers", ctypes.c_uint32),
-                ("max_live_allocs", ctypes.c_uint32), ("alloc_map_capacity", ctypes.c_uint32),
+                ("max_live_allocs", ctypes.c_uint32),
                 ("max_allocations", ctypes.c_uint32), ("max_queue", ctypes.c_uint32),
                 ("device", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
@@ -145,12 +147,12 @@ class Context:
 
     def __init__(self, nodes: int, devices: int, horizon_step: int = 4, lookahead: int = 0,
                  mode: int = MODE_PLAIN, device: int = 0, stream: Optional[int] = None,
-                 max_instructions: int = 0, map_capacity: int = 0, scratch_capacity: int = 0,
-                 max_buffers: int = 0, max_live_allocs: int = 0, alloc_map_capacity: int = 0,
+                 max_instructions: int = 0, map_heap: int = 0, scratch_capacity: int = 0,
+                 max_buffers: int = 0, max_live_allocs: int = 0,
                  max_allocations: int = 0, max_queue: int = 0, max_edges: int = 0, max_boxes: int = 0):
         self.nodes = nodes
-        cfg = Config(nodes, devices, horizon_step, lookahead, mode, max_instructions, max_edges, max_boxes, map_capacity,
-                     scratch_capacity, max_buffers, max_live_allocs, alloc_map_capacity, max_allocations,
+        cfg = Config(nodes, devices, horizon_step, lookahead, mode, max_instructions, max_edges, max_boxes, map_heap,
+                     scratch_capacity, max_buffers, max_live_allocs, max_allocations,
                      max_queue, device, stream)
         h = ctypes.c_void_p()
         r = lib().igs_create(ctypes.byref(cfg), ctypes.byref(h))
@@ -375,7 +377,7 @@ def lower_static(prog: W.Program, outs: Sequence[dict], stream: Optional[int] = 
         out[n].binds, out[n].bind_cap = o["binds"]
         out[n].diags, out[n].diag_cap = o["diags"]
         out[n].counts = o["counts"]
-    cfg = Config(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, None)
+    cfg = Config(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, None)
     return lib().igs_lower_static(ctypes.byref(cfg), sb, len(bufs), _p32(words), len(tasks), so, len(ops), out, stream)
 
 
@@ -406,10 +408,10 @@ def small_caps(prog: W.Program, counts: Optional[dict] = None) -> dict:
     else:
         ni = len(tasks) * (chunks * (nacc + 3) + 16) + 256
         ne, nb = ni * (chunks + 8), ni * 8
-    return {"max_instructions": ni, "max_edges": ne, "max_boxes": nb, "map_capacity": 4096,
+    return {"max_instructions": ni, "max_edges": ne, "max_boxes": nb, "map_heap": 1 << 17,
             "scratch_capacity": max(4096, (look + 2) * chunks * nacc * 2),
-            "max_buffers": max(1, len(prog.buffers)), "max_live_allocs": 256,
-            "alloc_map_capacity": max(512, 4 * chunks * nacc + 64), "max_allocations": 16384,
+            "max_buffers": max(1, len(prog.buffers)), "max_live_allocs": 1024,
+            "max_allocations": 16384,
             "max_queue": max(256, 2 * len(prog.ops) + 16)}
 
 

@@ -268,6 +268,38 @@ def measure_served(igs, torch, stream, streams=16, rate=2000.0, rows_max=2048, c
     return out
 
 
+def measure_box_copy(igs, torch, stream, reps=20):
+    """Resize-shaped box copies of 2^27 fp32 elements (512 MiB, the largest
+    growing allocation's live data): rows [0, 8192) x cols [0, 16384) from the
+    old allocation into a new one, either with the same row pitch (one
+    contiguous run) or growing along the fastest dimension (16384 -> 16448
+    columns: one strided run per row). Bytes = read + written; inputs exceed L2."""
+    rows, cols, grow = 8192, 16384, 64
+    out = {}
+    src = torch.empty(rows * cols, dtype=torch.float32, device="cuda")
+    src.copy_(torch.arange(rows * cols, dtype=torch.float32, device="cuda"))
+    for name, dcols in (("contiguous", cols), ("pitched", cols + grow)):
+        dst = torch.zeros(rows * dcols, dtype=torch.float32, device="cuda")
+        job = (src.data_ptr(), (0, 0, 0, rows, cols, 1), dst.data_ptr(), (0, 0, 0, rows, dcols, 1),
+               (0, 0, 0, rows, cols, 1), 4)
+        for _ in range(3):
+            igs.box_copy([job], stream.cuda_stream)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            igs.box_copy([job], stream.cuda_stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / reps
+        byts = 2.0 * rows * cols * 4
+        ok = bool(torch.equal(dst.view(rows, dcols)[:, :cols], src.view(rows, cols)))
+        out[name] = {"ms": ms, "bytes": byts, "gbs": byts / (ms * 1e-3) / 1e9, "checked": ok}
+        del dst
+    del src
+    return out
+
+
 def _done(srv, ctxs, x, lat):
     i, want, t0 = x
     _, taken, _ = srv.progress(ctxs[i])
@@ -275,6 +307,17 @@ def _done(srv, ctxs, x, lat):
         lat.append(time.perf_counter() - t0)
         return True
     return False
+
+
+def _nvtx(torch, name, push):
+    """Marks the timed region for profilers (a no-op where NVTX is absent)."""
+    try:
+        if push:
+            torch.cuda.nvtx.range_push(name)
+        else:
+            torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
 
 
 def run_gpu(args):
@@ -331,11 +374,13 @@ def run_gpu(args):
     clocks = Clocks(local)
     barrier()
     with clocks:
+        _nvtx(torch, "timed_steps", True)
         t0 = time.perf_counter()
         for i in range(args.steps):
             step(ctxs[args.warmup + i])
         barrier()
         t1 = time.perf_counter()
+        _nvtx(torch, "timed_steps", False)
     dt = t1 - t0
     instrs = int(ctxs[-1].counters()["instructions"])
     stats = [ctxs[args.warmup + i].stats() for i in range(args.steps)]
@@ -420,6 +465,7 @@ def run_gpu(args):
         hot[k] = {"ms_per_step": ms_k, "bytes_per_step": b_k, "achieved_gbs": a, "frac": a / hbm}
 
     # ---- batched lowering of many programs, served lowering of many streams
+    big_copy = measure_box_copy(igs, torch, stream)
     batched = measure_batched(igs, torch, sh) if world == 1 else None
     served = measure_served(igs, torch, sh) if world == 1 else None
 
@@ -456,6 +502,7 @@ def run_gpu(args):
                          "p50_task_ms": p50, "p99_task_ms": p99,
                          "batched_ms_per_task": lower_ms / STEPS},
             "box_copy_gbs": (copy_bytes / (copy_ms * 1e-3) / 1e9) if copy_ms else None,
+            "box_copy_resize_512MiB": {k: dict(v, frac=v["gbs"] / hbm) for k, v in big_copy.items()},
             "batched_programs": batched,
             "served": served,
             "clocks": clocks.summary(),

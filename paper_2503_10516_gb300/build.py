@@ -41,10 +41,13 @@ def _deps_mtime() -> float:
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime() and not extra_flags:
+    if (not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime() and not extra_flags
+            and not os.environ.get("IGS_PROFILE_DETAIL")):
         return LIB
     nvcc = _nvcc()
     common = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC] + ARCH + list(extra_flags)
+    if os.environ.get("IGS_PROFILE_DETAIL"):
+        common.append("-DIGS_PROFILE_DETAIL")
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))

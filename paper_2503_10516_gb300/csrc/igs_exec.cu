@@ -46,10 +46,20 @@ __global__ void __launch_bounds__(256) box_copy_kernel(const CopyJob* __restrict
     const uint8_t* s = J.src + r0 * J.src_stride[0] + r1 * J.src_stride[1] + off;
     uint8_t* d = J.dst + r0 * J.dst_stride[0] + r1 * J.dst_stride[1] + off;
     if ((((uintptr_t)s | (uintptr_t)d | len) & 15u) == 0) {
+      // four independent 16-byte loads in flight per thread before the stores
       const uint4* s4 = reinterpret_cast<const uint4*>(s);
       uint4* d4 = reinterpret_cast<uint4*>(d);
-      const uint32_t n4 = len >> 4;
-      for (uint32_t i = threadIdx.x; i < n4; i += blockDim.x) d4[i] = __ldcs(s4 + i);
+      const uint32_t n4 = len >> 4, bd = blockDim.x;
+      uint32_t i = threadIdx.x;
+      for (; i + 3 * bd < n4; i += 4 * bd) {
+        const uint4 a = __ldcs(s4 + i), b = __ldcs(s4 + i + bd), c = __ldcs(s4 + i + 2 * bd),
+                    e = __ldcs(s4 + i + 3 * bd);
+        __stcs(d4 + i, a);
+        __stcs(d4 + i + bd, b);
+        __stcs(d4 + i + 2 * bd, c);
+        __stcs(d4 + i + 3 * bd, e);
+      }
+      for (; i < n4; i += bd) __stcs(d4 + i, __ldcs(s4 + i));
     } else if ((((uintptr_t)s | (uintptr_t)d | len) & 3u) == 0) {
       const uint32_t* s1 = reinterpret_cast<const uint32_t*>(s);
       uint32_t* d1 = reinterpret_cast<uint32_t*>(d);

@@ -84,9 +84,9 @@ struct igs_ctx {
   std::vector<uint32_t> slot_ids;
   Item* m_items = nullptr;
   igs_task* m_tasks = nullptr;
-  BufDesc* m_bufs = nullptr;
   uint32_t* m_nitems = nullptr;
   uint32_t serve_cap = 0;
+  uint32_t m_cap = 0;  // entries of m_items / m_tasks
   // device-time accounting
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
@@ -161,6 +161,8 @@ int upload_prog(igs_ctx* c) {
   p.tasks = c->d_tasks;
   p.bufs = c->d_bufs;
   p.n_items = c->d_nitems;
+  p.src_items = nullptr;
+  p.src_tasks = nullptr;
   CK(cudaMemcpyAsync(c->d_prog, &p, sizeof p, cudaMemcpyHostToDevice, c->stream));
   const uint32_t n = (uint32_t)c->items.size();
   CK(cudaMemcpyAsync(c->d_nitems, &n, sizeof n, cudaMemcpyHostToDevice, c->stream));
@@ -307,7 +309,7 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
     return off;
   };
   const size_t o_heap = take(table_bytes(cap_heap));
-  const size_t o_desc = take(sizeof(uint32_t) * 4 * (2 * cap_buffers + 2 * cap_slots));
+  const size_t o_desc = take(sizeof(uint32_t) * kDesc * (2 * cap_buffers + 2 * cap_slots));
   const size_t o_free = take(sizeof(uint32_t) * cap_slots);
   const size_t o_live = take(sizeof(uint32_t) * cap_slots);
   const size_t o_qr = take(table_bytes(cap_qr));
@@ -364,9 +366,9 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
     nd.heap_top = 0;
     for (int k = 0; k < kHeapClasses; ++k) nd.free_head[k] = NONE;
     nd.own_d = reinterpret_cast<uint32_t*>(base + o_desc);
-    nd.bst_d = nd.own_d + 4 * cap_buffers;
-    nd.wr_d = nd.bst_d + 4 * cap_buffers;
-    nd.rd_d = nd.wr_d + 4 * cap_slots;
+    nd.bst_d = nd.own_d + kDesc * cap_buffers;
+    nd.wr_d = nd.bst_d + kDesc * cap_buffers;
+    nd.rd_d = nd.wr_d + kDesc * cap_slots;
     nd.free_slots = reinterpret_cast<uint32_t*>(base + o_free);
     nd.live = reinterpret_cast<uint32_t*>(base + o_live);
     nd.qr_base = reinterpret_cast<uint32_t*>(base + o_qr);
@@ -387,7 +389,7 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
     igs_instruction i0{0, IGS_EPOCH, NONE, NONE, NONE, NONE, NONE, 0, 0, 0, 0};
     if (cudaMemcpy(nd.instrs, &i0, sizeof i0, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(nd.has_succ, 0, 1) != cudaSuccess ||
-        cudaMemset(nd.own_d, 0, sizeof(uint32_t) * 4 * (2 * cap_buffers + 2 * cap_slots)) != cudaSuccess ||
+        cudaMemset(nd.own_d, 0, sizeof(uint32_t) * kDesc * (2 * cap_buffers + 2 * cap_slots)) != cudaSuccess ||
         cudaMemcpy(nd.free_slots, slots.data(), sizeof(uint32_t) * cap_slots, cudaMemcpyHostToDevice) != cudaSuccess) {
       igs_destroy(c);
       return IGS_ERR_CUDA;
@@ -429,7 +431,6 @@ void igs_destroy(igs_ctx* c) {
   cudaFree(c->d_kjobs);
   if (c->m_items) cudaFreeHost(c->m_items);
   if (c->m_tasks) cudaFreeHost(c->m_tasks);
-  if (c->m_bufs) cudaFreeHost(c->m_bufs);
   if (c->m_nitems) cudaFreeHost(c->m_nitems);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -437,13 +438,13 @@ void igs_destroy(igs_ctx* c) {
 
 const char* igs_last_error(const igs_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
-int igs_profile(igs_ctx* c, uint64_t out[16]) {
+int igs_profile(igs_ctx* c, uint64_t out[32]) {
   if (!c || !out) return IGS_ERR_INVALID_ARG;
   int r = download_nodes(c);
   if (r) return r;
-  std::memset(out, 0, sizeof(uint64_t) * 16);
+  std::memset(out, 0, sizeof(uint64_t) * 32);
   for (const NodeDev& nd : c->nodes_host)
-    for (int k = 0; k < 16; ++k) out[k] += nd.prof[k];
+    for (int k = 0; k < 32; ++k) out[k] += nd.prof[k];
   return IGS_OK;
 }
 
@@ -1129,7 +1130,7 @@ extern "C" int igs_read_buffer(igs_ctx* c, uint32_t b, const uint32_t lo[3], con
   std::vector<HEntry> own, bst;
   {
     const NodeDev& n0 = c->nodes_host[0];
-    r = read_slab(c, n0, n0.own_d + 4 * b, own);
+    r = read_slab(c, n0, n0.own_d + kDesc * b, own);
     if (r) return r;
   }
   Pending p;
@@ -1146,7 +1147,7 @@ extern "C" int igs_read_buffer(igs_ctx* c, uint32_t b, const uint32_t lo[3], con
     const uint32_t o = e.v[0];
     {
       const NodeDev& no = c->nodes_host[o];
-      r = read_slab(c, no, no.bst_d + 4 * b, bst);
+      r = read_slab(c, no, no.bst_d + kDesc * b, bst);
       if (r) return r;
     }
     for (const HEntry& f : bst) {
@@ -1285,18 +1286,32 @@ extern "C" int igs_serve_attach(igs_server* s, igs_ctx* c, uint32_t max_items) {
     if (r != IGS_ERR_OVERLAPPING_WRITE) return r;
   }
   const uint32_t cap = max_items;
-  CK(cudaHostAlloc(&c->m_items, sizeof(Item) * cap, cudaHostAllocMapped));
-  CK(cudaHostAlloc(&c->m_tasks, sizeof(igs_task) * cap, cudaHostAllocMapped));
-  CK(cudaHostAlloc(&c->m_bufs, sizeof(BufDesc) * std::max<size_t>(1, c->bufs.size()), cudaHostAllocMapped));
-  CK(cudaHostAlloc(&c->m_nitems, sizeof(uint32_t), cudaHostAllocMapped));
+  // device arrays for every submission the context can take while served
+  // (the loop stages new ones into them), host-mapped arrays the host
+  // publishes into
+  if (int r = grow_device(c, c->d_items, c->cap_items, cap, c->items_up)) return r;
+  if (int r = grow_device(c, c->d_tasks, c->cap_tasks, cap, c->tasks_up)) return r;
+  if (c->m_items && cap > c->m_cap) {  // an earlier attach's arrays are too small
+    cudaFreeHost(c->m_items);
+    cudaFreeHost(c->m_tasks);
+    c->m_items = nullptr;
+    c->m_tasks = nullptr;
+  }
+  if (!c->m_items) {
+    CK(cudaHostAlloc(&c->m_items, sizeof(Item) * cap, cudaHostAllocMapped));
+    CK(cudaHostAlloc(&c->m_tasks, sizeof(igs_task) * cap, cudaHostAllocMapped));
+    c->m_cap = cap;
+  }
+  if (!c->m_nitems) CK(cudaHostAlloc(&c->m_nitems, sizeof(uint32_t), cudaHostAllocMapped));
   std::memcpy(c->m_items, c->items.data(), sizeof(Item) * c->items.size());
   std::memcpy(c->m_tasks, c->tasks.data(), sizeof(igs_task) * c->tasks.size());
-  std::memcpy(c->m_bufs, c->bufs.data(), sizeof(BufDesc) * c->bufs.size());
   *reinterpret_cast<volatile uint32_t*>(c->m_nitems) = (uint32_t)c->items.size();
   ProgDev p;
-  CK(cudaHostGetDevicePointer((void**)&p.items, c->m_items, 0));
-  CK(cudaHostGetDevicePointer((void**)&p.tasks, c->m_tasks, 0));
-  CK(cudaHostGetDevicePointer((void**)&p.bufs, c->m_bufs, 0));
+  p.items = c->d_items;
+  p.tasks = c->d_tasks;
+  p.bufs = c->d_bufs;
+  CK(cudaHostGetDevicePointer((void**)&p.src_items, c->m_items, 0));
+  CK(cudaHostGetDevicePointer((void**)&p.src_tasks, c->m_tasks, 0));
   uint32_t* dn = nullptr;
   CK(cudaHostGetDevicePointer((void**)&dn, c->m_nitems, 0));
   p.n_items = dn;

@@ -40,11 +40,13 @@ struct Table {
   uint32_t* base;  // cap entries of F_COUNT words
   uint32_t n, cap;
   uint32_t live;   // entries not marked dead
-  uint32_t* dp;    // heap table descriptor {offset, cap, n, live}; nullptr for scratch tables
+  uint32_t* dp;    // heap table descriptor {offset, cap, n, live, merge mark}; nullptr for scratch tables
 };
 
 // Size classes of the per-node entry heap: 32 << k entries.
 constexpr int kHeapClasses = 24;
+// Words per heap-table descriptor: {offset, cap, n, live, merge mark, 3 spare}.
+constexpr uint32_t kDesc = 8;
 
 struct AllocRec {
   uint32_t buffer, mem, live, user;
@@ -62,7 +64,7 @@ struct NodeDev {
   uint32_t n_instr, n_edge, n_box, n_bind, n_diag, n_rej;
   uint32_t q_head, q_count, qr_n, n_free, n_live, qr_live;
   uint64_t map_reads, map_writes, launches;
-  uint64_t prof[16];   // clock cycles per lowering phase (see the engine)
+  uint64_t prof[32];   // clock cycles per lowering phase and detail counters (see the engine)
   // capacities
   uint32_t cap_instr, cap_edge, cap_box, cap_bind, cap_diag, cap_rej, cap_alloc, cap_queue;
   uint32_t cap_buffers, cap_slots, cap_qr, cap_scratch;
@@ -71,7 +73,7 @@ struct NodeDev {
   uint32_t* heap;      // cap_heap entries of F_COUNT words
   uint32_t cap_heap, heap_top;
   uint32_t free_head[kHeapClasses];
-  // table descriptors {offset, cap, n, live}: per buffer the node-level
+  // table descriptors (kDesc words, {offset, cap, n, live, merge mark}): per buffer the node-level
   // ownership map and the local buffer state; per allocation slot its last
   // writers and readers since the last write
   uint32_t* own_d;
@@ -102,6 +104,11 @@ struct ProgDev {
   const igs_task* tasks;
   const BufDesc* bufs;
   volatile uint32_t* n_items;  // number of valid items (host-mapped in serving)
+  // serving: submissions arrive in host-mapped memory; a warp copies each
+  // new item and its task into `items` / `tasks` (device memory) once and
+  // lowers from there. nullptr when not served.
+  const Item* src_items;
+  const igs_task* src_tasks;
 };
 
 // A unit of lowering work: one node of one program.

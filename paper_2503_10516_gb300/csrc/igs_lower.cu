@@ -196,6 +196,32 @@ __device__ __forceinline__ PhaseTimer pt_start() {
   return p;
 }
 
+// Detail counters (cycles inside region-map primitives and parts of
+// emission, call counts), compiled in with IGS_PROFILE_DETAIL only.
+enum Detail : int {
+  D_MERGE = 16, D_SUBTRACT = 17, D_QUERY = 18, D_COMPACT = 19, D_PROBE = 20, D_DEDUP = 21, D_RECORD = 22,
+  D_APPLY = 23, N_MERGE = 24, N_MERGE_PROBE = 25, N_SUBTRACT = 26, N_EMIT = 27, N_PROBE_ENTRIES = 28, N_TIDY = 29,
+  N_GROW = 30
+};
+#ifdef IGS_PROFILE_DETAIL
+#define DT_START(v) PhaseTimer v = pt_start()
+#define DT_LAP(v, ph) pt_lap(v, c, ph)
+#define DT_COUNT(k, x)                          \
+  do {                                          \
+    if (c.lane == 0) c.nd->prof[k] += (x);      \
+  } while (0)
+#else
+#define DT_START(v) \
+  do {              \
+  } while (0)
+#define DT_LAP(v, ph) \
+  do {                \
+  } while (0)
+#define DT_COUNT(k, x) \
+  do {                 \
+  } while (0)
+#endif
+
 // ---- the node's entry heap ---------------------------------------------------
 
 __device__ __forceinline__ int heap_class(uint32_t entries) {
@@ -255,6 +281,7 @@ __device__ bool t_grow(Ctx& c, Table& t, uint32_t need) {
   uint32_t cap = 0;
   const uint32_t off = heap_alloc(c, need > 2 * t.cap ? need : 2 * t.cap, cap);
   if (off == NONE) return false;
+  DT_COUNT(N_GROW, 1);
   uint4* dst = reinterpret_cast<uint4*>(c.nd->heap + (size_t)off * F_COUNT);
   const uint4* src = reinterpret_cast<const uint4*>(t.base);
   const uint32_t words4 = t.n * (F_COUNT / 4);
@@ -357,14 +384,15 @@ __device__ __forceinline__ Bx warp_bbox(Bx b, bool valid) {
   return r;
 }
 
-// Stable in-place removal of dead entries.
 __device__ void pt_lap(PhaseTimer& p, Ctx& c, int ph) {
   const long long t1 = clock64();
   if (c.lane == 0) c.nd->prof[ph] += (uint64_t)(t1 - p.t0);
   p.t0 = t1;
 }
 
+// Stable in-place removal of dead entries.
 __device__ void t_compact(Ctx& c, Table& t) {
+  DT_START(dt);
   uint32_t w = 0;
   for (uint32_t base = 0; base < t.n; base += 32) {
     const uint32_t i = base + c.lane;
@@ -389,11 +417,15 @@ __device__ void t_compact(Ctx& c, Table& t) {
   t.live = w;
   t_publish(c, t);
   __syncwarp();
+  DT_LAP(dt, D_COMPACT);
 }
 
 // Compacts a table once its dead entries outnumber the live ones.
 __device__ __forceinline__ void t_tidy(Ctx& c, Table& t) {
-  if (t.n > 2 * t.live + 32) t_compact(c, t);
+  if (t.n > 2 * t.live + 32) {
+    DT_COUNT(N_TIDY, 1);
+    t_compact(c, t);
+  }
 }
 
 __device__ Bx t_bbox(const Ctx& c, const Table& t, uint32_t from, uint32_t to) {
@@ -415,6 +447,7 @@ __device__ Bx t_bbox(const Ctx& c, const Table& t, uint32_t from, uint32_t to) {
 // (NONE = any) that overlaps q and satisfies pred(values).
 template <class P>
 __device__ void t_query(Ctx& c, const Table& src, uint32_t key, const Bx& q, Table& out, P pred) {
+  DT_START(dt);
   const uint32_t n = src.n;
   c.map_reads += n;
   for (uint32_t base = 0; base < n; base += 32) {
@@ -439,11 +472,14 @@ __device__ void t_query(Ctx& c, const Table& src, uint32_t key, const Bx& q, Tab
     if (hit) t_put(out, s, 0, is, v0, v1, v2);
   }
   __syncwarp();
+  DT_LAP(dt, D_QUERY);
 }
 
 // Removes box r from every entry of `key` (NONE = any) that matches the
 // optional value filter; the remainders keep their values.
 __device__ void t_subtract(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t vfilter = NONE) {
+  DT_START(dt);
+  DT_COUNT(N_SUBTRACT, 1);
   t_tidy(c, t);
   const uint32_t n0 = t.n;
   for (uint32_t base = 0; base < n0; base += 32) {
@@ -475,6 +511,7 @@ __device__ void t_subtract(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t
     }
   }
   __syncwarp();
+  DT_LAP(dt, D_SUBTRACT);
 }
 
 // value[vidx] |= bits on box r for entries of `key`.
@@ -522,9 +559,12 @@ __device__ void t_set(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t v0, 
 // Merges entries from index `from` on with equal key and values into
 // adjacent entries whose union is a box (keeps the tables small).
 __device__ void t_merge_from(Ctx& c, Table& t, uint32_t from) {
+  DT_START(dt);
+  DT_COUNT(N_MERGE, 1);
   for (uint32_t i = from; i < t.n; ++i) {
     uint32_t cand = i;
     for (int guard = 0; guard < 4096; ++guard) {
+      DT_COUNT(N_MERGE_PROBE, 1);
       const uint32_t k = t_key(t, cand);
       if (k == DEAD) break;
       const Bx e = t_box(t, cand);
@@ -545,6 +585,22 @@ __device__ void t_merge_from(Ctx& c, Table& t, uint32_t from) {
       cand = j;
     }
   }
+  DT_LAP(dt, D_MERGE);
+}
+
+// Re-merges a heap table once its live entries exceed max(floor, twice the
+// count after its previous re-merge): fragmentation stays bounded while the
+// quadratic merge runs a logarithmic number of times as a table grows.
+__device__ void t_set_mark(Ctx& c, Table& t) {
+  __syncwarp();
+  if (t.dp && c.lane == 0) t.dp[4] = t.live;
+  __syncwarp();
+}
+__device__ void t_maybe_merge(Ctx& c, Table& t, uint32_t floor) {
+  const uint32_t mark = t.dp ? t.dp[4] : 0;
+  if (t.live <= floor || t.live <= 2 * mark) return;
+  t_merge_from(c, t, 0);
+  t_set_mark(c, t);
 }
 
 // Makes the live entries with value v0 == val (NONE = all) of each key
@@ -614,77 +670,109 @@ __device__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_t from, uint3
     if (live) t_put(W, s, 0, b, 0, 0, 0);
   }
   __syncwarp();
+  // Phase md rewrites until no box a has a neighbour b with a.hi[md] ==
+  // b.lo[md], equal extents in the faster dimensions and overlapping extents
+  // in the slower ones. One pass finds, for every box, its successor with
+  // equal extents in all other dimensions (unique: the boxes are disjoint)
+  // and the first pair that needs a split; whole successor chains merge at
+  // once, else one pair is split so that its slower extents coincide. The
+  // fixpoint of each phase is unique, so the order of rewrites does not
+  // change the result.
   if (W.n > 1) {
     for (int phase = 0; phase < 3; ++phase) {
       const int md = 2 - phase;  // dimension merged in this phase
       for (uint32_t guard = 0;; ++guard) {
-        if (guard > 64u * W.cap) {  // every step merges or splits: unreachable for valid input
+        if (guard > 64u * W.cap) {  // every round merges or splits: unreachable for valid input
           fail(c, ST_INTERNAL);
           return 0;
         }
-        const uint32_t n = W.n;
-        uint32_t found = NONE;
-        const uint64_t pairs = (uint64_t)n * n;
-        for (uint64_t base = 0; base < pairs; base += 32) {
-          const uint64_t p = base + c.lane;
-          bool act = false;
-          if (p < pairs) {
-            const uint32_t i = (uint32_t)(p / n), j = (uint32_t)(p % n);
-            if (i != j && t_key(W, i) != DEAD && t_key(W, j) != DEAD) {
-              const Bx a = t_box(W, i), b = t_box(W, j);
-              act = a.hi[md] == b.lo[md];
-              for (int d = 0; d < 3 && act; ++d) {
+        const uint32_t n = W.n;  // compacted: every entry is live
+        uint64_t split = ~0ull;
+        bool any_succ = false;
+        for (uint32_t base = 0; base < n; base += 32) {
+          const uint32_t i = base + c.lane;
+          uint32_t succ = NONE;
+          uint64_t sp = ~0ull;
+          if (i < n) {
+            const Bx a = t_box(W, i);
+            for (uint32_t j = 0; j < n; ++j) {
+              if (j == i) continue;
+              const Bx b = t_box(W, j);
+              if (a.hi[md] != b.lo[md]) continue;
+              bool faster_eq = true, slower_ov = true, slower_eq = true;
+              for (int d = 0; d < 3; ++d) {
                 if (d == md) continue;
-                if (d > md) act = a.lo[d] == b.lo[d] && a.hi[d] == b.hi[d];  // equal in faster dims
-                else act = max(a.lo[d], b.lo[d]) < min(a.hi[d], b.hi[d]);  // overlap in slower dims
+                const bool eq = a.lo[d] == b.lo[d] && a.hi[d] == b.hi[d];
+                if (d > md) {
+                  faster_eq = faster_eq && eq;
+                } else {
+                  slower_ov = slower_ov && max(a.lo[d], b.lo[d]) < min(a.hi[d], b.hi[d]);
+                  slower_eq = slower_eq && eq;
+                }
               }
+              if (!faster_eq || !slower_ov) continue;
+              if (slower_eq) succ = j;
+              else if (sp == ~0ull) sp = (uint64_t)i * n + j;
+            }
+            FLD(W, F_V, i) = succ;
+            FLD(W, F_V + 1, i) = 0;
+          }
+          any_succ = any_succ || __any_sync(FULL, succ != NONE);
+          sp = warp_min64(sp);
+          split = sp < split ? sp : split;
+        }
+        __syncwarp();
+        if (any_succ) {
+          // mark boxes that have a predecessor; each chain head absorbs its chain
+          for (uint32_t base = 0; base < n; base += 32) {
+            const uint32_t i = base + c.lane;
+            if (i < n) {
+              const uint32_t sc = t_v(W, 0, i);
+              if (sc != NONE) FLD(W, F_V + 1, sc) = 1;
             }
           }
-          const uint32_t m = __ballot_sync(FULL, act);
-          if (m) {
-            found = (uint32_t)(base + __ffs(m) - 1);
-            break;
-          }
-        }
-        if (found == NONE) break;
-        const uint32_t i = found / n, j = found % n;
-        const Bx a = t_box(W, i), b = t_box(W, j);
-        bool same = true;
-        for (int d = 0; d < md; ++d) same = same && a.lo[d] == b.lo[d] && a.hi[d] == b.hi[d];
-        __syncwarp();
-        if (same) {
-          if (c.lane == 0) {
-            Bx u = a;
-            u.hi[md] = b.hi[md];
-            t_put(W, i, 0, u, 0, 0, 0);
-            t_kill(W, j);
-          }
           __syncwarp();
-        } else {
-          // split a and b so that their slower-dimension extents coincide
-          Bx ia = a, ib = b;
-          for (int d = 0; d < md; ++d) {
-            ia.lo[d] = ib.lo[d] = max(a.lo[d], b.lo[d]);
-            ia.hi[d] = ib.hi[d] = min(a.hi[d], b.hi[d]);
-          }
-          Bx pa[6], pb[6];
-          const int na = bx_minus(a, ia, pa), nb = bx_minus(b, ib, pb);
-          const uint32_t first = t_claim_n(c, W, c.lane == 0 ? (uint32_t)(na + nb + 2) : 0u);
-          if (c.err) return 0;
-          if (c.lane == 0) {
-            t_kill(W, i);
-            t_kill(W, j);
-            uint32_t q = first;
-            t_put(W, q++, 0, ia, 0, 0, 0);
-            t_put(W, q++, 0, ib, 0, 0, 0);
-            for (int x = 0; x < na; ++x) t_put(W, q++, 0, pa[x], 0, 0, 0);
-            for (int x = 0; x < nb; ++x) t_put(W, q++, 0, pb[x], 0, 0, 0);
+          for (uint32_t base = 0; base < n; base += 32) {
+            const uint32_t i = base + c.lane;
+            if (i < n && t_v(W, 0, i) != NONE && t_v(W, 1, i) == 0) {
+              uint32_t cur = i, hi = 0;
+              while (t_v(W, 0, cur) != NONE) {
+                cur = t_v(W, 0, cur);
+                hi = t_box(W, cur).hi[md];
+                t_kill(W, cur);
+              }
+              FLD(W, F_HI + md, i) = hi;
+            }
           }
           __syncwarp();
           t_compact(c, W);
+          continue;
         }
+        if (split == ~0ull) break;
+        const uint32_t i = (uint32_t)(split / n), j = (uint32_t)(split % n);
+        const Bx a = t_box(W, i), b = t_box(W, j);
+        // split a and b so that their slower-dimension extents coincide
+        Bx ia = a, ib = b;
+        for (int d = 0; d < md; ++d) {
+          ia.lo[d] = ib.lo[d] = max(a.lo[d], b.lo[d]);
+          ia.hi[d] = ib.hi[d] = min(a.hi[d], b.hi[d]);
+        }
+        Bx pa[6], pb[6];
+        const int na = bx_minus(a, ia, pa), nb = bx_minus(b, ib, pb);
+        const uint32_t first = t_claim_n(c, W, c.lane == 0 ? (uint32_t)(na + nb + 2) : 0u);
+        if (c.err) return 0;
+        if (c.lane == 0) {
+          t_kill(W, i);
+          t_kill(W, j);
+          uint32_t q = first;
+          t_put(W, q++, 0, ia, 0, 0, 0);
+          t_put(W, q++, 0, ib, 0, 0, 0);
+          for (int x = 0; x < na; ++x) t_put(W, q++, 0, pa[x], 0, 0, 0);
+          for (int x = 0; x < nb; ++x) t_put(W, q++, 0, pb[x], 0, 0, 0);
+        }
+        __syncwarp();
+        t_compact(c, W);
       }
-      t_compact(c, W);
     }
   }
   // rank sort into out
@@ -726,15 +814,15 @@ __device__ __forceinline__ Table slab(const Ctx& c, uint32_t* d) {
   return heap_table(c.nd, d);
 }
 // Node-level ownership map of a buffer (owner node, replication mask).
-__device__ __forceinline__ Table own_t(const Ctx& c, uint32_t b) { return slab(c, c.nd->own_d + 4 * b); }
+__device__ __forceinline__ Table own_t(const Ctx& c, uint32_t b) { return slab(c, c.nd->own_d + kDesc * b); }
 // Local state of a buffer (original producer, its memory, up-to-date memories).
-__device__ __forceinline__ Table bst_t(const Ctx& c, uint32_t b) { return slab(c, c.nd->bst_d + 4 * b); }
+__device__ __forceinline__ Table bst_t(const Ctx& c, uint32_t b) { return slab(c, c.nd->bst_d + kDesc * b); }
 // Last writers / readers since the last write of an allocation.
 __device__ __forceinline__ Table wr_t(const Ctx& c, uint32_t aid) {
-  return slab(c, c.nd->wr_d + 4 * c.nd->allocs[aid].slot);
+  return slab(c, c.nd->wr_d + kDesc * c.nd->allocs[aid].slot);
 }
 __device__ __forceinline__ Table rd_t(const Ctx& c, uint32_t aid) {
-  return slab(c, c.nd->rd_d + 4 * c.nd->allocs[aid].slot);
+  return slab(c, c.nd->rd_d + kDesc * c.nd->allocs[aid].slot);
 }
 
 // A fresh empty heap table behind descriptor d.
@@ -748,6 +836,7 @@ __device__ bool table_new(Ctx& c, uint32_t* d, uint32_t entries) {
     d[1] = cap;
     d[2] = 0;
     d[3] = 0;
+    d[4] = 0;
   }
   __syncwarp();
   return true;
@@ -768,7 +857,7 @@ __device__ bool new_alloc(Ctx& c, uint32_t aid, uint32_t b, uint32_t m, const Bx
   }
   c.n_free -= 1;
   const uint32_t slot = c.nd->free_slots[c.n_free];
-  if (!table_new(c, c.nd->wr_d + 4 * slot, 32) || !table_new(c, c.nd->rd_d + 4 * slot, 32)) return false;
+  if (!table_new(c, c.nd->wr_d + kDesc * slot, 32) || !table_new(c, c.nd->rd_d + kDesc * slot, 32)) return false;
   if (c.lane == 0) {
     AllocRec rec;
     rec.buffer = b;
@@ -792,8 +881,8 @@ __device__ bool new_alloc(Ctx& c, uint32_t aid, uint32_t b, uint32_t m, const Bx
 // Drops an allocation: its slab goes back to the free list.
 __device__ void drop_alloc(Ctx& c, uint32_t aid) {
   const uint32_t slot = c.nd->allocs[aid].slot;
-  table_free(c, c.nd->wr_d + 4 * slot);
-  table_free(c, c.nd->rd_d + 4 * slot);
+  table_free(c, c.nd->wr_d + kDesc * slot);
+  table_free(c, c.nd->rd_d + kDesc * slot);
   __syncwarp();
   if (c.lane == 0) {
     c.nd->allocs[aid].live = 0;
@@ -962,7 +1051,6 @@ __device__ bool overlapping_writes(Ctx& c, const igs_task& t, const Table& CH, c
 
 // ---- emission with dependency tracking (a8, a10) --------------------------
 
-__device__ uint32_t instr_type(const Ctx& c, uint32_t id) { return c.nd->instrs[id].type; }
 
 // Emits one instruction. Dependencies: extra edges already in S_DEP (when
 // keep_dep) plus, per access, the last writers (RAW dataflow; WAW anti; a
@@ -989,6 +1077,8 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
   Table& D = c.s[S_DEP];
   if (!keep_dep) t_reset(D);
   const uint32_t id = c.n_instr;
+  DT_START(dt);
+  DT_COUNT(N_EMIT, 1);
   // one probe per (access, region box, table): last writers for every access,
   // readers for writes; then every probed entry in one lane-parallel pass
   {
@@ -998,7 +1088,7 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
     for (int k = 0; k < nacc; ++k) {
       const Acc& A = acc[k];
       const uint32_t slot = nd->allocs[A.alloc].slot;
-      const uint32_t wn = nd->wr_d[4 * slot + 2], rn = nd->rd_d[4 * slot + 2];
+      const uint32_t wn = nd->wr_d[kDesc * slot + 2], rn = nd->rd_d[kDesc * slot + 2];
       for (uint32_t r = A.from; r < A.to; ++r) {
         if (t_key(*A.t, r) == DEAD) continue;
         const Bx q = t_box(*A.t, r);
@@ -1015,6 +1105,7 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
     }
     __syncwarp();
     c.map_reads += total;
+    DT_COUNT(N_PROBE_ENTRIES, total);
     const uint32_t np = PR.n;
     for (uint32_t base = 0; base < total; base += 32) {
       const uint32_t f = base + c.lane;
@@ -1024,13 +1115,13 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
         uint32_t p = 0;
         while (p + 1 < np && t_v(PR, 1, p + 1) <= f) ++p;
         const uint32_t tab = t_key(PR, p), slot = t_v(PR, 0, p), mode = t_v(PR, 2, p);
-        const Table T = heap_table(nd, (tab == 0 ? nd->wr_d : nd->rd_d) + 4 * slot);
+        const Table T = heap_table(nd, (tab == 0 ? nd->wr_d : nd->rd_d) + kDesc * slot);
         const uint32_t j = f - t_v(PR, 1, p);
         if (t_key(T, j) != DEAD && bx_overlap(t_box(T, j), t_box(PR, p))) {
           hit = true;
           w = t_v(T, 0, j);
           if (tab == 1) kind = IGS_DEP_ANTI;
-          else if (instr_type(c, w) == IGS_ALLOC) kind = IGS_DEP_ALLOC;
+          else if (t_v(T, 1, j) == 1) kind = IGS_DEP_ALLOC;  // an allocation writer
           else kind = ((mode & IGS_READ) ? IGS_DEP_DATAFLOW : 0u) | ((mode & IGS_WRITE) ? IGS_DEP_ANTI : 0u);
         }
       }
@@ -1043,6 +1134,7 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
     }
   }
   __syncwarp();
+  DT_LAP(dt, D_PROBE);
   if (D.n == 0) {
     if (c.lane == 0) {
       FLD(D, F_V, 0) = c.epoch;
@@ -1146,6 +1238,7 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
     }
   }
   c.n_edge += n_unique;
+  DT_LAP(dt, D_DEDUP);
   // instruction record, its boxes and bindings
   uint32_t nb = 0;
   if (bt) {
@@ -1204,6 +1297,7 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
   c.n_bind += bind_n;
   c.n_instr += 1;
   __syncwarp();
+  DT_LAP(dt, D_RECORD);
   // apply reads, then writes
   for (int k = 0; k < nacc; ++k) {
     const Acc& A = acc[k];
@@ -1225,7 +1319,7 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
     }
     // re-merge only a table that has grown: keeps hot paths short and bounds
     // fragmentation between horizons
-    if (RD.live > 48) t_merge_from(c, RD, 0);
+    t_maybe_merge(c, RD, 48);
     (void)from;
   }
   for (int k = 0; k < nacc; ++k) {
@@ -1242,20 +1336,26 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
       t_set(c, WR, NONE, q, id, 0, 0);
       if (c.err) return NONE;
     }
-    if (WR.live > 48) t_merge_from(c, WR, 0);
-    if (RD.live > 48) t_merge_from(c, RD, 0);
+    t_maybe_merge(c, WR, 48);
+    t_maybe_merge(c, RD, 48);
     (void)from;
   }
+  DT_LAP(dt, D_APPLY);
   return id;
 }
 
 // Replace every tracked instruction id older than h by h and re-merge (a9).
-__device__ void map_ids(Ctx& c, Table& T, uint32_t h) {
+// In writer tables (writers = true) v1 marks allocation writers; a replaced
+// writer is the horizon, which is not one.
+__device__ void map_ids(Ctx& c, Table& T, uint32_t h, bool writers = false) {
   for (uint32_t base = 0; base < T.n; base += 32) {
     const uint32_t i = base + c.lane;
     if (i < T.n && t_key(T, i) != DEAD) {
       const uint32_t v = t_v(T, 0, i);
-      if (v < h) FLD(T, F_V, i) = h;
+      if (v < h) {
+        FLD(T, F_V, i) = h;
+        if (writers) FLD(T, F_V + 1, i) = 0;
+      }
     }
   }
   __syncwarp();
@@ -1265,27 +1365,30 @@ __device__ void apply_epoch(Ctx& c, uint32_t h) {
   for (uint32_t li = 0; li < c.n_live; ++li) {
     const uint32_t aid = c.nd->live[li];
     Table WR = wr_t(c, aid);
-    map_ids(c, WR, h);
+    map_ids(c, WR, h, true);
     t_compact(c, WR);
     t_merge_from(c, WR, 0);
     t_compact(c, WR);
+    t_set_mark(c, WR);
     Table RD = rd_t(c, aid);
     map_ids(c, RD, h);
     t_make_disjoint(c, RD, h);
     t_compact(c, RD);
     t_merge_from(c, RD, 0);
     t_compact(c, RD);
+    t_set_mark(c, RD);
     if (c.err) return;
   }
   const uint32_t nb = c.nd->cap_buffers;
   for (uint32_t b = 0; b < nb; ++b) {
-    if (c.nd->bst_d[4 * b + 1] == 0) continue;  // no table (never created or destroyed)
+    if (c.nd->bst_d[kDesc * b + 1] == 0) continue;  // no table (never created or destroyed)
     Table B = bst_t(c, b);
     if (B.n == 0) continue;
     map_ids(c, B, h);
     t_compact(c, B);
     t_merge_from(c, B, 0);
     t_compact(c, B);
+    t_set_mark(c, B);
   }
   c.epoch = h;
 }
@@ -1839,7 +1942,7 @@ __device__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq, const Table
         Table WR = wr_t(c, aid);
         const uint32_t s = t_claim(c, WR, c.lane == 0);
         if (c.err) return;
-        if (c.lane == 0) t_put(WR, s, 0, bb, iid, 0, 0);
+        if (c.lane == 0) t_put(WR, s, 0, bb, iid, 1, 0);  // v1 = 1: the writer is an allocation
         __syncwarp();
       }
       // the absorbed allocations, ascending (the live list changes as they are freed)
@@ -2128,7 +2231,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
           hit = !bx_empty(x);
           if (hit) {
             const uint32_t b = t.acc[a].buffer, m = t_v(CH, 1, slot);
-            const Table B = heap_table(c.nd, c.nd->bst_d + 4 * b);
+            const Table B = heap_table(c.nd, c.nd->bst_d + kDesc * b);
             for (uint32_t j = 0; j < B.n; ++j) {
               if (t_key(B, j) == DEAD || !bx_overlap(t_box(B, j), x)) continue;
               const uint32_t prod = t_v(B, 0, j), mask = t_v(B, 2, j);
@@ -2246,7 +2349,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
       Table B = bst_t(c, t.acc[a].buffer);
       t_set(c, B, NONE, x, kid, mem, 1u << mem);
       if (c.err) return;
-      if (B.live > 4 * CH.n + 64) t_merge_from(c, B, 0);
+      t_maybe_merge(c, B, 4 * CH.n + 64);
     }
   }
   pt_lap(pt, c, PH_P5);
@@ -2297,7 +2400,7 @@ __device__ void process(Ctx& c, uint32_t item) {
         fail_cap(c, CAP_BUFFERS, c.nd->cap_buffers);
         return;
       }
-      if (!table_new(c, c.nd->bst_d + 4 * it.arg, 32)) return;
+      if (!table_new(c, c.nd->bst_d + kDesc * it.arg, 32)) return;
       Table B = bst_t(c, it.arg);
       if (bd.init) {
         const uint32_t aid = c.n_alloc;
@@ -2376,7 +2479,7 @@ __device__ void process(Ctx& c, uint32_t item) {
             drop_alloc(c, aid);
           }
         }
-      table_free(c, c.nd->bst_d + 4 * b);
+      table_free(c, c.nd->bst_d + kDesc * b);
       break;
     }
     default:
@@ -2430,7 +2533,7 @@ __device__ void deliver(Ctx& c, uint32_t item) {
       return;
     }
     const BufDesc& bd = buf_of(c, it.arg);
-    if (!table_new(c, c.nd->own_d + 4 * it.arg, 32)) return;
+    if (!table_new(c, c.nd->own_d + kDesc * it.arg, 32)) return;
     Table O = own_t(c, it.arg);
     const uint32_t s = t_claim(c, O, c.lane == 0);
     if (c.err) return;
@@ -2476,7 +2579,7 @@ __device__ void deliver(Ctx& c, uint32_t item) {
     if (it.kind == IT_EPOCH || it.kind == IT_DESTROY || queued_tasks(c) > c.lookahead) flush_queue(c);
   }
   if (c.err) return;
-  if (it.kind == IT_DESTROY) table_free(c, c.nd->own_d + 4 * it.arg);
+  if (it.kind == IT_DESTROY) table_free(c, c.nd->own_d + kDesc * it.arg);
 }
 
 __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg) {
@@ -2553,7 +2656,7 @@ __device__ void store_ctx(Ctx& c, uint32_t cursor) {
 }
 
 // One warp per unit; each lowers the unit's pending items (at most max_items).
-__global__ void __launch_bounds__(128) lower_kernel(const Unit* units, uint32_t n_units, uint32_t max_items) {
+__global__ void __launch_bounds__(32) lower_kernel(const Unit* units, uint32_t n_units, uint32_t max_items) {
   const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= n_units) return;
   const Unit u = units[w];
@@ -2572,11 +2675,36 @@ __global__ void __launch_bounds__(128) lower_kernel(const Unit* units, uint32_t 
   store_ctx(c, cursor);
 }
 
+// Copies submissions [from, to) and their tasks from the host-mapped arrays
+// into the program's device arrays (16-byte words, all lanes). Every node warp
+// of a program stages the same records; the copies write equal bytes.
+__device__ void stage_submissions(const ProgDev* pg, uint32_t from, uint32_t to) {
+  // host-written records are read with cache-volatile loads (never from a
+  // line cached before the host wrote it)
+  static_assert(sizeof(Item) == 16, "an item is one 16-byte word");
+  const uint4* src = reinterpret_cast<const uint4*>(pg->src_items);
+  uint4* dst = reinterpret_cast<uint4*>(const_cast<Item*>(pg->items));
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint32_t i = from + lane; i < to; i += 32) dst[i] = __ldcv(src + i);
+  __syncwarp();
+  static_assert(sizeof(igs_task) % 4 == 0, "task record is a whole number of words");
+  constexpr uint32_t words = sizeof(igs_task) / 4;
+  for (uint32_t i = from; i < to; ++i) {
+    const Item it = pg->items[i];
+    if (it.kind != IT_TASK) continue;
+    const uint32_t* s = reinterpret_cast<const uint32_t*>(pg->src_tasks + it.task);
+    uint32_t* d = reinterpret_cast<uint32_t*>(const_cast<igs_task*>(pg->tasks + it.task));
+    for (uint32_t w = lane; w < words; w += 32) d[w] = __ldcv(s + w);
+  }
+  __threadfence_block();
+  __syncwarp();
+}
+
 // Serving loop: warp w serves slot w; it takes every submission published so
 // far, then publishes its progress. Waits are bounded: after idle_polls empty
 // polls (about 2 us each) the warp leaves with EXIT_IDLE; a set stop flag ends
 // it with EXIT_STOPPED.
-__global__ void __launch_bounds__(128) serve_kernel(ServeSlot* slots, uint32_t n_slots, volatile uint32_t* stop,
+__global__ void __launch_bounds__(32) serve_kernel(ServeSlot* slots, uint32_t n_slots, volatile uint32_t* stop,
                                                     uint64_t idle_polls) {
   const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= n_slots) return;
@@ -2613,9 +2741,10 @@ __global__ void __launch_bounds__(128) serve_kernel(ServeSlot* slots, uint32_t n
       avail = __shfl_sync(FULL, avail, 0);
       __threadfence_system();
       if (st2 == SLOT_ACTIVE && u.node->cursor < avail && u.node->status == ST_OK) {
+        uint32_t cursor = u.node->cursor;
+        stage_submissions(u.prog, cursor, avail);
         Ctx c;
         load_ctx(c, u.node, u.prog);
-        uint32_t cursor = u.node->cursor;
         while (cursor < avail && c.err == ST_OK) {
           deliver(c, cursor);
           ++cursor;
@@ -2649,16 +2778,26 @@ __global__ void __launch_bounds__(128) serve_kernel(ServeSlot* slots, uint32_t n
 
 int igs_launch_serve(igs::ServeSlot* slots, uint32_t n_slots, volatile uint32_t* stop, uint64_t idle_polls, void* stream) {
   if (n_slots == 0) return 0;
-  const uint32_t threads = 128, warps = threads / 32;
-  const uint32_t blocks = (n_slots + warps - 1) / warps;
-  igs::serve_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(slots, n_slots, stop, idle_polls);
+  // one warp per block: each slot's warp gets an SM (and its L1) to itself
+  // while there are fewer slots than SMs
+  static bool carveout = false;
+  if (!carveout) {
+    cudaFuncSetAttribute(igs::serve_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    carveout = true;
+  }
+  igs::serve_kernel<<<n_slots, 32, 0, (cudaStream_t)stream>>>(slots, n_slots, stop, idle_polls);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int igs_launch_lower(const igs::Unit* units_dev, uint32_t n_units, uint32_t max_items, void* stream) {
   if (n_units == 0) return 0;
-  const uint32_t threads = 128, warps = threads / 32;
-  const uint32_t blocks = (n_units + warps - 1) / warps;
-  igs::lower_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(units_dev, n_units, max_items);
+  // one warp per block, so that units spread over the SMs (each node's
+  // tables then share an L1 with as few other units as possible)
+  static bool carveout = false;
+  if (!carveout) {
+    cudaFuncSetAttribute(igs::lower_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    carveout = true;
+  }
+  igs::lower_kernel<<<n_units, 32, 0, (cudaStream_t)stream>>>(units_dev, n_units, max_items);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -44,7 +44,7 @@ Layout layout(uint32_t cap_instr) {
     return o;
   };
   L.o_heap = take(tbytes(kHeap));
-  L.o_desc = take(16 * (2 * kBuffers + 2 * kSlots));
+  L.o_desc = take(4 * igs::kDesc * (2 * kBuffers + 2 * kSlots));
   L.o_free = take(4 * kSlots);
   L.o_live = take(4 * kSlots);
   L.o_qr = take(tbytes(kQr));
@@ -189,9 +189,9 @@ extern "C" int igs_lower_static(const igs_config* cfg, const igs_static_buffer* 
     nd.heap_top = 0;
     for (int k = 0; k < igs::kHeapClasses; ++k) nd.free_head[k] = NONE;
     nd.own_d = reinterpret_cast<uint32_t*>(nb + L.o_desc);
-    nd.bst_d = nd.own_d + 4 * kBuffers;
-    nd.wr_d = nd.bst_d + 4 * kBuffers;
-    nd.rd_d = nd.wr_d + 4 * kSlots;
+    nd.bst_d = nd.own_d + igs::kDesc * kBuffers;
+    nd.wr_d = nd.bst_d + igs::kDesc * kBuffers;
+    nd.rd_d = nd.wr_d + igs::kDesc * kSlots;
     nd.free_slots = reinterpret_cast<uint32_t*>(nb + L.o_free);
     nd.live = reinterpret_cast<uint32_t*>(nb + L.o_live);
     nd.qr_base = reinterpret_cast<uint32_t*>(nb + L.o_qr);
@@ -229,7 +229,7 @@ extern "C" int igs_lower_static(const igs_config* cfg, const igs_static_buffer* 
   if (num_buffers) CKS(cudaMemcpyAsync(base + o_bufs, bd.data(), sizeof(BufDesc) * num_buffers, cudaMemcpyHostToDevice, stream));
   for (uint32_t n = 0; n < N; ++n) {
     uint8_t* nb = base + o_state + L.per_node * n;
-    CKS(cudaMemsetAsync(nb + L.o_desc, 0, 16 * (2 * kBuffers + 2 * kSlots), stream));
+    CKS(cudaMemsetAsync(nb + L.o_desc, 0, 4 * igs::kDesc * (2 * kBuffers + 2 * kSlots), stream));
     CKS(cudaMemsetAsync(nb + L.o_succ, 0, 1, stream));
     CKS(cudaMemcpyAsync(nb + L.o_free, slots.data(), 4 * kSlots, cudaMemcpyHostToDevice, stream));
     CKS(cudaMemcpyAsync(outs[n].instrs, &i0, sizeof i0, cudaMemcpyHostToDevice, stream));

@@ -274,11 +274,14 @@ def _set_timing(self, on: bool = True):
 
 
 PHASES = ("split", "overlap", "push_await", "allocating", "alloc", "push", "receive", "coherence", "kernel",
-          "remote", "sync_emit", "sync_apply", "total", "in_emit", "in_canonical", "in_find_alloc")
+          "remote", "sync_emit", "sync_apply", "total", "in_emit", "in_canonical", "in_find_alloc",
+          "in_merge", "in_subtract", "in_query", "in_compact", "emit_probe", "emit_dedup", "emit_record",
+          "emit_apply", "n_merge", "n_merge_probe", "n_subtract", "n_emit", "n_probe_entries", "n_tidy",
+          "n_grow", "spare")
 
 
 def _profile(self) -> dict:
-    c = (ctypes.c_uint64 * 16)()
+    c = (ctypes.c_uint64 * 32)()
     self._check(lib().igs_profile(self._h, c), "profile")
     return {name: int(c[i]) for i, name in enumerate(PHASES)}
 

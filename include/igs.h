@@ -215,12 +215,32 @@ int igs_fetch_instructions(igs_ctx* ctx, igs_graph_view* view);
 int igs_rejected_tasks(igs_ctx* ctx, uint64_t* seqs, uint32_t cap, uint32_t* count);
 
 /* Executes every instruction emitted and not yet executed, on the device, in
- * an order that respects the graph: allocations from a stream-ordered pool,
- * copies and send/receive pairs (matched by task, buffer and receiver) as
- * box-copy kernels, device kernels as the workload kernels. Asynchronous on
- * the context's stream unless IGS_EXEC_SYNC. */
+ * an order that respects the graph (Sec. 3.7: out-of-order execution of the
+ * instruction graph, here by topological level): allocations from a
+ * stream-ordered pool, coherence copies as box-copy kernels, device kernels
+ * as the workload kernels. A send copies its box into a mailbox (device
+ * memory of its own) when it executes; the receive matched to it by (task,
+ * buffer, receiver) copies the mailbox into its allocation and frees it. A
+ * receive whose sends have not all been lowered yet stops its node; a later
+ * call continues from there. Returns when the work has completed (flags:
+ * IGS_EXEC_SYNC, accepted for compatibility; execution is always complete on
+ * return). */
 #define IGS_EXEC_SYNC 1u
 int igs_execute(igs_ctx* ctx, uint32_t flags);
+
+/* Lowers every pending submission and executes the whole graph with the
+ * scheduler running ahead of the executor (Sec. 4: instruction generation
+ * runs concurrently with execution, off the critical path): one launch on the
+ * context's stream lowers all pending submissions, each node publishing its
+ * progress after every submission to host-mapped memory; meanwhile the
+ * executor fetches what has been emitted whenever every node has advanced by
+ * `window` submissions and executes it on a second stream of the library's
+ * own. The lowering blocks keep the executor's kernels off their SMs. The
+ * emitted graph is the same as for igs_flush + igs_execute. For
+ * IGS_MODE_BATCHED contexts (plain contexts lower at submission: this then
+ * equals igs_execute). Returns when execution has completed;
+ * IGS_ERR_OVERLAPPING_WRITE if a task was rejected (the rest ran). */
+int igs_run(igs_ctx* ctx, uint32_t window);
 
 /* Reads box [lo, hi) of a buffer, after execute, from the memory holding the
  * newest version of each element, into host_dst (row-major, elem_size each). */

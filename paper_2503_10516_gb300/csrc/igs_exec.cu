@@ -293,14 +293,16 @@ __global__ void __launch_bounds__(256) stencil_kernel(const KernelJob* __restric
     for (int k = 0; k < 4; ++k) {
       const uint32_t x = xs + k;
       if (x >= x1) break;
-      const float c = ur[x];
+      // streaming (evict-first) loads and stores: the stencil's data passes
+      // through L2 once per step and should not displace other kernels' lines
+      const float c = __ldcs(ur + x);
       float v = c;
       if (y > 0 && y + 1 < H && x > 0 && x + 1 < W) {
-        const float n = urn[x], s = urs[x], w = ur[x - 1], e = ur[x + 1];
+        const float n = __ldcs(urn + x), s = __ldcs(urs + x), w = __ldcs(ur + x - 1), e = __ldcs(ur + x + 1);
         if (!wave) {
           v = ((n + s) + (w + e)) * 0.25f;
         } else {
-          const float t2 = (2.0f * c) - pr[x];
+          const float t2 = (2.0f * c) - __ldcs(pr + x);
           const float t5 = (n + s) + (w + e);
           const float t8 = 0.25f * (t5 - 4.0f * c);
           v = t2 + t8;
@@ -309,9 +311,9 @@ __global__ void __launch_bounds__(256) stencil_kernel(const KernelJob* __restric
       out[k] = v;
     }
     if (xs + 4 <= x1 && ((reinterpret_cast<uintptr_t>(orow + xs) & 15u) == 0)) {
-      *reinterpret_cast<float4*>(orow + xs) = make_float4(out[0], out[1], out[2], out[3]);
+      __stcs(reinterpret_cast<float4*>(orow + xs), make_float4(out[0], out[1], out[2], out[3]));
     } else {
-      for (int k = 0; k < 4 && xs + k < x1; ++k) orow[xs + k] = out[k];
+      for (int k = 0; k < 4 && xs + k < x1; ++k) __stcs(orow + xs + k, out[k]);
     }
   }
 }

@@ -30,6 +30,15 @@ struct ExecAlloc {
   bool live = false, user = false;
 };
 
+// A send the executor has carried out: its data sits in a mailbox (device
+// memory of its own) until the matching receive copies it out.
+struct SendRec {
+  uint32_t node, level;
+  uint64_t call;  // execute call that copied the data into the mailbox
+  igs_box box;
+  uint8_t* mail;
+};
+
 struct NodeHost {
   // fetched graph (everything so far) for execution
   std::vector<igs_instruction> instrs;
@@ -73,10 +82,24 @@ struct igs_ctx {
   std::vector<NodeDev> nodes_host;  // layout templates (pointers), refreshed by downloads
   // executor
   std::vector<NodeHost> nh;
-  CopyJob* d_cjobs = nullptr;
-  uint32_t cap_cjobs = 0;
-  KernelJob* d_kjobs = nullptr;
-  uint32_t cap_kjobs = 0;
+  cudaStream_t xstream = nullptr;  // executor stream of pipelined runs (own, created on first use)
+  cudaStream_t cstream = nullptr;  // copies of graph records to the host during pipelined runs
+  volatile uint32_t* m_progress = nullptr;  // host-mapped progress records (PR_WORDS per node)
+  uint32_t* d_progress = nullptr;
+  bool pipelined = false;          // a pipelined run is in progress: launches go to xstream
+  std::multimap<uint64_t, SendRec> sends;  // (seq, buffer, receiver) -> sends not yet received
+  uint64_t exec_call = 0;
+  // job arrays: two sets, used alternately; a set is reused once the event
+  // recorded after its last launch has completed
+  CopyJob* d_cjobs[2] = {nullptr, nullptr};
+  uint32_t cap_cjobs[2] = {0, 0};
+  KernelJob* d_kjobs[2] = {nullptr, nullptr};
+  uint32_t cap_kjobs[2] = {0, 0};
+  CopyJob* h_cjobs[2] = {nullptr, nullptr};  // pinned staging of the job arrays
+  KernelJob* h_kjobs[2] = {nullptr, nullptr};
+  uint32_t hcap_cjobs[2] = {0, 0}, hcap_kjobs[2] = {0, 0};
+  cudaEvent_t jobs_done[2] = {nullptr, nullptr};
+  int jobs_set = 0;
   uint64_t launches = 0;
   size_t arena_bytes = 0;
   // serving: submissions live in host-mapped memory the loop polls
@@ -170,22 +193,24 @@ int upload_prog(igs_ctx* c) {
 }
 
 // Event pair around one launch of class k (0 lowering, 1 box copy, 2 workload).
-size_t ev_begin(igs_ctx* c) {
+size_t ev_begin(igs_ctx* c, cudaStream_t s = nullptr) {
   if (c->ev_used == c->ev_pool.size()) {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     c->ev_pool.push_back({a, b});
   }
-  cudaEventRecord(c->ev_pool[c->ev_used].first, c->stream);
+  cudaEventRecord(c->ev_pool[c->ev_used].first, s ? s : c->stream);
   return c->ev_used++;
 }
-void ev_end(igs_ctx* c, int k, size_t i) {
-  cudaEventRecord(c->ev_pool[i].second, c->stream);
+void ev_end(igs_ctx* c, int k, size_t i, cudaStream_t s = nullptr) {
+  cudaEventRecord(c->ev_pool[i].second, s ? s : c->stream);
   c->ev_pending.push_back({k, i});
 }
-// Folds completed event pairs into the totals (after a stream sync).
+// Folds completed event pairs into the totals (after a stream sync; held
+// back while a pipelined run still has executor work in flight).
 void ev_collect(igs_ctx* c) {
+  if (c->pipelined) return;
   for (auto& p : c->ev_pending) {
     float t = 0;
     cudaEventElapsedTime(&t, c->ev_pool[p.second].first, c->ev_pool[p.second].second);
@@ -196,12 +221,13 @@ void ev_collect(igs_ctx* c) {
   c->ev_used = 0;
 }
 
-int launch_lower(igs_ctx* c) {
+int launch_lower(igs_ctx* c, uint32_t max_items = IGS_NONE, bool reserve = false, uint32_t* progress = nullptr) {
   if (c->server) return IGS_OK;  // the serving loop lowers it
   int r = upload_prog(c);
   if (r) return r;
   const size_t ev = c->timing ? ev_begin(c) : 0;
-  if (igs_launch_lower(c->d_units, c->N, IGS_NONE, c->stream)) return fail_ctx(c, IGS_ERR_CUDA, "lowering launch failed");
+  if (igs_launch_lower(c->d_units, c->N, max_items, c->stream, reserve, progress))
+    return fail_ctx(c, IGS_ERR_CUDA, "lowering launch failed");
   if (c->timing) ev_end(c, 0, ev);
   c->launches++;
   c->n_launch[0]++;
@@ -410,6 +436,19 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
 void igs_destroy(igs_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->xstream) cudaStreamSynchronize(c->xstream);
+  for (auto& sr : c->sends)
+    if (sr.second.mail) cudaFree(sr.second.mail);
+  for (int k = 0; k < 2; ++k) {
+    if (c->d_cjobs[k]) cudaFreeAsync(c->d_cjobs[k], c->stream);
+    if (c->d_kjobs[k]) cudaFreeAsync(c->d_kjobs[k], c->stream);
+    if (c->h_cjobs[k]) cudaFreeHost(c->h_cjobs[k]);
+    if (c->h_kjobs[k]) cudaFreeHost(c->h_kjobs[k]);
+    if (c->jobs_done[k]) cudaEventDestroy(c->jobs_done[k]);
+  }
+  if (c->xstream) cudaStreamDestroy(c->xstream);
+  if (c->cstream) cudaStreamDestroy(c->cstream);
+  if (c->m_progress) cudaFreeHost((void*)c->m_progress);
   for (auto& e : c->ev_pool) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);
@@ -427,8 +466,6 @@ void igs_destroy(igs_ctx* c) {
   cudaFree(c->d_nodes);
   cudaFree(c->d_units);
   cudaFree(c->d_arena);
-  cudaFree(c->d_cjobs);
-  cudaFree(c->d_kjobs);
   if (c->m_items) cudaFreeHost(c->m_items);
   if (c->m_tasks) cudaFreeHost(c->m_tasks);
   if (c->m_nitems) cudaFreeHost(c->m_nitems);
@@ -755,60 +792,101 @@ void add_kernel(Pending& p, uint32_t L, KernelJob J, uint64_t items, bool stenci
   w.kernels.push_back(J);
 }
 
-// Uploads every job once and launches level by level on the stream.
-int run_pending(igs_ctx* c, Pending& p) {
-  std::vector<CopyJob> cj;
-  std::vector<KernelJob> kj;
+// Stream-ordered growth of a device array whose contents need not survive
+// (no device-wide synchronization, unlike cudaFree).
+template <class T>
+int grow_device_async(igs_ctx* c, T*& ptr, uint32_t& cap, size_t need, cudaStream_t s) {
+  if (need <= cap) return IGS_OK;
+  const uint32_t ncap = (uint32_t)std::max<size_t>(need, std::max<size_t>(4096, (size_t)cap * 2));
+  if (ptr) CK(cudaFreeAsync(ptr, s));
+  ptr = nullptr;
+  CK(cudaMallocAsync((void**)&ptr, sizeof(T) * (size_t)ncap, s));
+  cap = ncap;
+  return IGS_OK;
+}
+
+template <class T>
+int grow_pinned(igs_ctx* c, T*& ptr, uint32_t& cap, size_t need) {
+  if (need <= cap) return IGS_OK;
+  const uint32_t ncap = (uint32_t)std::max<size_t>(need, std::max<size_t>(4096, (size_t)cap * 2));
+  if (ptr) CK(cudaFreeHost(ptr));
+  ptr = nullptr;
+  CK(cudaHostAlloc((void**)&ptr, sizeof(T) * (size_t)ncap, cudaHostAllocDefault));
+  cap = ncap;
+  return IGS_OK;
+}
+
+// Uploads every job once and launches level by level on stream s. The job
+// arrays alternate between two sets; with wait == false the call returns
+// once everything is enqueued.
+int run_pending(igs_ctx* c, Pending& p, cudaStream_t s, bool wait) {
+  const int k = c->jobs_set;
+  c->jobs_set ^= 1;
+  if (!c->jobs_done[k]) CK(cudaEventCreateWithFlags(&c->jobs_done[k], cudaEventDisableTiming));
+  CK(cudaEventSynchronize(c->jobs_done[k]));  // the set's previous launches are done
+  size_t ncj = 0, nkj = 0;
+  for (const LevelWork& w : p.levels) {
+    ncj += w.copies.size();
+    nkj += w.kernels.size() + w.stencils.size();
+  }
   std::vector<size_t> co(p.levels.size()), ko(p.levels.size()), so(p.levels.size());
-  for (size_t L = 0; L < p.levels.size(); ++L) {
-    co[L] = cj.size();
-    cj.insert(cj.end(), p.levels[L].copies.begin(), p.levels[L].copies.end());
-    ko[L] = kj.size();
-    kj.insert(kj.end(), p.levels[L].kernels.begin(), p.levels[L].kernels.end());
-    so[L] = kj.size();
-    kj.insert(kj.end(), p.levels[L].stencils.begin(), p.levels[L].stencils.end());
-  }
   int r;
-  if (!cj.empty()) {
-    if ((r = grow_device(c, c->d_cjobs, c->cap_cjobs, (uint32_t)cj.size(), 0))) return r;
-    CK(cudaMemcpyAsync(c->d_cjobs, cj.data(), sizeof(CopyJob) * cj.size(), cudaMemcpyHostToDevice, c->stream));
+  if ((r = grow_pinned(c, c->h_cjobs[k], c->hcap_cjobs[k], std::max<size_t>(ncj, 1)))) return r;
+  if ((r = grow_pinned(c, c->h_kjobs[k], c->hcap_kjobs[k], std::max<size_t>(nkj, 1)))) return r;
+  size_t nc = 0, nk = 0;
+  for (size_t L = 0; L < p.levels.size(); ++L) {
+    const LevelWork& w = p.levels[L];
+    co[L] = nc;
+    std::copy(w.copies.begin(), w.copies.end(), c->h_cjobs[k] + nc);
+    nc += w.copies.size();
+    ko[L] = nk;
+    std::copy(w.kernels.begin(), w.kernels.end(), c->h_kjobs[k] + nk);
+    nk += w.kernels.size();
+    so[L] = nk;
+    std::copy(w.stencils.begin(), w.stencils.end(), c->h_kjobs[k] + nk);
+    nk += w.stencils.size();
   }
-  if (!kj.empty()) {
-    if ((r = grow_device(c, c->d_kjobs, c->cap_kjobs, (uint32_t)kj.size(), 0))) return r;
-    CK(cudaMemcpyAsync(c->d_kjobs, kj.data(), sizeof(KernelJob) * kj.size(), cudaMemcpyHostToDevice, c->stream));
+  if (nc) {
+    if ((r = grow_device_async(c, c->d_cjobs[k], c->cap_cjobs[k], nc, s))) return r;
+    CK(cudaMemcpyAsync(c->d_cjobs[k], c->h_cjobs[k], sizeof(CopyJob) * nc, cudaMemcpyHostToDevice, s));
+  }
+  if (nk) {
+    if ((r = grow_device_async(c, c->d_kjobs[k], c->cap_kjobs[k], nk, s))) return r;
+    CK(cudaMemcpyAsync(c->d_kjobs[k], c->h_kjobs[k], sizeof(KernelJob) * nk, cudaMemcpyHostToDevice, s));
   }
   for (size_t L = 0; L < p.levels.size(); ++L) {
     LevelWork& w = p.levels[L];
     if (!w.copies.empty()) {
-      const size_t ev = c->timing ? ev_begin(c) : 0;
-      if (igs_launch_copies(c->d_cjobs + co[L], (uint32_t)w.copies.size(), w.copy_units, c->stream))
+      const size_t ev = c->timing ? ev_begin(c, s) : 0;
+      if (igs_launch_copies(c->d_cjobs[k] + co[L], (uint32_t)w.copies.size(), w.copy_units, s))
         return fail_ctx(c, IGS_ERR_CUDA, "box copy launch");
-      if (c->timing) ev_end(c, 1, ev);
+      if (c->timing) ev_end(c, 1, ev, s);
       c->n_launch[1]++;
       for (const CopyJob& j : w.copies) c->copy_bytes += 2.0 * j.extent[0] * j.extent[1] * j.extent[2];
     }
     for (size_t first = 0; first < w.stencils.size(); first += 65535) {
       const uint32_t n = (uint32_t)std::min<size_t>(65535, w.stencils.size() - first);
-      const size_t ev = c->timing ? ev_begin(c) : 0;
-      if (igs_launch_stencil(c->d_kjobs + so[L] + first, n, w.stencil_max, c->stream))
+      const size_t ev = c->timing ? ev_begin(c, s) : 0;
+      if (igs_launch_stencil(c->d_kjobs[k] + so[L] + first, n, w.stencil_max, s))
         return fail_ctx(c, IGS_ERR_CUDA, "stencil launch");
-      if (c->timing) ev_end(c, 2, ev);
+      if (c->timing) ev_end(c, 2, ev, s);
       c->n_launch[2]++;
     }
     if (!w.kernels.empty()) {
-      const size_t ev = c->timing ? ev_begin(c) : 0;
-      if (igs_launch_workload(c->d_kjobs + ko[L], (uint32_t)w.kernels.size(), w.kernel_items, c->stream))
+      const size_t ev = c->timing ? ev_begin(c, s) : 0;
+      if (igs_launch_workload(c->d_kjobs[k] + ko[L], (uint32_t)w.kernels.size(), w.kernel_items, s))
         return fail_ctx(c, IGS_ERR_CUDA, "workload launch");
-      if (c->timing) ev_end(c, 2, ev);
+      if (c->timing) ev_end(c, 2, ev, s);
       c->n_launch[2]++;
     }
-    for (void* f : w.frees) CK(cudaFreeAsync(f, c->stream));
+    for (void* f : w.frees) CK(cudaFreeAsync(f, s));
   }
-  // the job arrays are reused by the next call
-  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaEventRecord(c->jobs_done[k], s));
+  p.levels.clear();
+  if (!wait) return IGS_OK;
+  CK(cudaStreamSynchronize(s));
   ev_collect(c);
   if (igs_exec_error(true)) return fail_ctx(c, IGS_ERR_STATE, "a workload kernel accessed outside its allocation");
-  p.levels.clear();
   return IGS_OK;
 }
 
@@ -831,34 +909,44 @@ ExecAlloc* get_alloc(igs_ctx* c, uint32_t node, uint32_t aid, uint32_t buffer_hi
   return &(m[aid] = a);
 }
 
+// Brings node n's records up to the given counts to the host (on stream s,
+// which is then synchronized).
+int fetch_node(igs_ctx* c, uint32_t n, uint32_t ni, uint32_t ne, uint32_t nbx, uint32_t nbd, cudaStream_t s) {
+  const NodeDev& nd = c->nodes_host[n];
+  NodeHost& h = c->nh[n];
+  const size_t oi = h.instrs.size(), oe = h.edges.size(), ob = h.boxes.size(), ok = h.binds.size();
+  if (ni < oi || ne < oe || nbx < ob || nbd < ok) return fail_ctx(c, IGS_ERR_STATE, "graph counts went back");
+  h.instrs.resize(ni);
+  h.edges.resize(ne);
+  h.boxes.resize(nbx);
+  h.binds.resize(nbd);
+  if (ni > oi)
+    CK(cudaMemcpyAsync(h.instrs.data() + oi, nd.instrs + oi, sizeof(igs_instruction) * (ni - oi), cudaMemcpyDeviceToHost, s));
+  if (ne > oe)
+    CK(cudaMemcpyAsync(h.edges.data() + oe, nd.edges + oe, sizeof(igs_edge) * (ne - oe), cudaMemcpyDeviceToHost, s));
+  if (nbx > ob)
+    CK(cudaMemcpyAsync(h.boxes.data() + ob, nd.boxes + ob, sizeof(igs_box) * (nbx - ob), cudaMemcpyDeviceToHost, s));
+  if (nbd > ok)
+    CK(cudaMemcpyAsync(h.binds.data() + ok, nd.binds + ok, sizeof(igs_binding) * (nbd - ok), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  h.first_edge.resize(ni + 1, 0);
+  h.level.resize(ni, 0);
+  // edges are grouped by successor in emission order
+  size_t e = oe;
+  for (uint32_t i = (uint32_t)oi; i < ni; ++i) {
+    while (e < h.edges.size() && h.edges[e].to < i) ++e;
+    h.first_edge[i] = (uint32_t)e;
+  }
+  h.first_edge[ni] = (uint32_t)h.edges.size();
+  return IGS_OK;
+}
+
 int fetch_for_exec(igs_ctx* c) {
   int r = download_nodes(c);
   if (r) return r;
   for (uint32_t n = 0; n < c->N; ++n) {
     const NodeDev& nd = c->nodes_host[n];
-    NodeHost& h = c->nh[n];
-    const size_t oi = h.instrs.size(), oe = h.edges.size(), ob = h.boxes.size(), ok = h.binds.size();
-    h.instrs.resize(nd.n_instr);
-    h.edges.resize(nd.n_edge);
-    h.boxes.resize(nd.n_box);
-    h.binds.resize(nd.n_bind);
-    if (nd.n_instr > oi)
-      CK(cudaMemcpy(h.instrs.data() + oi, nd.instrs + oi, sizeof(igs_instruction) * (nd.n_instr - oi), cudaMemcpyDeviceToHost));
-    if (nd.n_edge > oe)
-      CK(cudaMemcpy(h.edges.data() + oe, nd.edges + oe, sizeof(igs_edge) * (nd.n_edge - oe), cudaMemcpyDeviceToHost));
-    if (nd.n_box > ob)
-      CK(cudaMemcpy(h.boxes.data() + ob, nd.boxes + ob, sizeof(igs_box) * (nd.n_box - ob), cudaMemcpyDeviceToHost));
-    if (nd.n_bind > ok)
-      CK(cudaMemcpy(h.binds.data() + ok, nd.binds + ok, sizeof(igs_binding) * (nd.n_bind - ok), cudaMemcpyDeviceToHost));
-    h.first_edge.resize(nd.n_instr + 1, 0);
-    h.level.resize(nd.n_instr, 0);
-    // edges are grouped by successor in emission order
-    size_t e = oe;
-    for (uint32_t i = (uint32_t)oi; i < nd.n_instr; ++i) {
-      while (e < h.edges.size() && h.edges[e].to < i) ++e;
-      h.first_edge[i] = (uint32_t)e;
-    }
-    h.first_edge[nd.n_instr] = (uint32_t)h.edges.size();
+    if ((r = fetch_node(c, n, nd.n_instr, nd.n_edge, nd.n_box, nd.n_bind, c->stream))) return r;
   }
   return IGS_OK;
 }
@@ -898,41 +986,34 @@ bool stencil_ok(const igs_ctx* c, const KernelJob& J) {
   return box_in(U.lo, U.hi, lo, hi);
 }
 
-struct SendRec {
-  uint32_t node, alloc, level;
-  igs_box box;
-};
-
-}  // namespace
-
-extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
-  if (!c) return IGS_ERR_INVALID_ARG;
-  if (c->server) return fail_ctx(c, IGS_ERR_STATE, "detach the context from its server first");
-  int r = fetch_for_exec(c);
-  if (r) return r;
-  // walk: by submission sequence; within one, every node's part up to its
-  // first receive, then the rest (sends precede the matching receives)
+// One walk over the fetched, not yet executed instructions of every node,
+// by submission sequence; within one, every node's part up to its first
+// receive, then the rest (sends precede the matching receives). A receive
+// whose sends have not all been carried out stops its node for this walk.
+// Sets *halted_any when some node stopped early.
+int exec_walk(igs_ctx* c, Pending& p, cudaStream_t xs, bool* halted_any, bool* progress) {
+  c->exec_call += 1;
   std::map<uint32_t, std::vector<std::pair<uint32_t, std::pair<uint32_t, uint32_t>>>> order;
+  std::vector<bool> halted(c->N, false);
+  std::vector<uint32_t> stop_at(c->N, 0);
   for (uint32_t n = 0; n < c->N; ++n) {
     NodeHost& h = c->nh[n];
-    std::fill(h.level.begin(), h.level.end(), 0u);  // earlier calls: complete
+    std::fill(h.level.begin(), h.level.end(), 0u);  // earlier calls: complete (stream order)
     uint32_t i = h.executed;
     while (i < h.instrs.size()) {
-      const uint32_t s = h.instrs[i].seq;
+      const uint32_t sq = h.instrs[i].seq;
       uint32_t j = i;
-      while (j < h.instrs.size() && h.instrs[j].seq == s) ++j;
-      order[s].push_back({n, {i, j}});
+      while (j < h.instrs.size() && h.instrs[j].seq == sq) ++j;
+      order[sq].push_back({n, {i, j}});
       i = j;
     }
-    h.executed = (uint32_t)h.instrs.size();
   }
-  Pending p;
-  std::multimap<uint64_t, SendRec> sends;  // key: (seq << 32) | (buffer << 8) | receiver
   auto key_of = [](uint32_t seq, uint32_t buf, uint32_t recv) { return ((uint64_t)seq << 32) | ((uint64_t)buf << 8) | recv; };
   for (auto& so : order) {
     for (int half = 0; half < 2; ++half) {
       for (auto& part : so.second) {
         const uint32_t n = part.first;
+        if (halted[n]) continue;
         NodeHost& h = c->nh[n];
         uint32_t i0 = part.second.first, i1 = part.second.second, cut = i1;
         for (uint32_t i = i0; i < i1; ++i)
@@ -941,7 +1022,7 @@ extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
             break;
           }
         const uint32_t a0 = half == 0 ? i0 : cut, a1 = half == 0 ? cut : i1;
-        for (uint32_t i = a0; i < a1; ++i) {
+        for (uint32_t i = a0; i < a1 && !halted[n]; ++i) {
           const igs_instruction& in = h.instrs[i];
           const uint32_t L = pred_level(h, i);
           h.level[i] = L;
@@ -957,7 +1038,7 @@ extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
                 a.hi[d] = b.hi[d];
                 cnt *= (b.hi[d] - b.lo[d]);
               }
-              CK(cudaMallocAsync((void**)&a.ptr, cnt ? cnt : 1, c->stream));
+              CK(cudaMallocAsync((void**)&a.ptr, cnt ? cnt : 1, xs));
               a.live = true;
               h.allocs[in.a] = a;
               break;
@@ -984,30 +1065,60 @@ extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
               break;
             }
             case IGS_SEND: {
+              // the data moves at the send: into a mailbox of its own, one
+              // level after the send's predecessors
+              ExecAlloc* sa = get_alloc(c, n, in.a, in.c);
+              if (!sa) return fail_ctx(c, IGS_ERR_STATE, "send from unknown allocation");
               SendRec sr;
               sr.node = n;
-              sr.alloc = in.a;
               sr.box = h.boxes[in.box_off];
-              sr.level = L;
-              sends.insert({key_of(in.seq, in.c, in.b), sr});
+              sr.level = L + 1;
+              sr.call = c->exec_call;
+              const uint32_t elem = c->bufs[in.c].elem;
+              uint64_t bytes = elem;
+              for (int d = 0; d < 3; ++d) bytes *= sr.box.hi[d] - sr.box.lo[d];
+              CK(cudaMallocAsync((void**)&sr.mail, bytes ? bytes : 1, xs));
+              CopyJob J{};
+              if (!make_copy_job(sa->ptr, sa->lo, sa->hi, sr.mail, sr.box.lo, sr.box.hi, sr.box, elem, J))
+                return fail_ctx(c, IGS_ERR_STATE, "bad send box");
+              add_copy(p, L + 1, J);
+              c->sends.insert({key_of(in.seq, in.c, in.b), sr});
+              h.level[i] = L + 1;
               break;
             }
             case IGS_RECEIVE:
             case IGS_SPLIT_RECEIVE: {
-              auto range = sends.equal_range(key_of(in.seq, in.c, n));
+              // every send of this (task, buffer) to this node must have been
+              // carried out; otherwise the node stops here until a later call
+              auto range = c->sends.equal_range(key_of(in.seq, in.c, n));
+              uint64_t need = 0, have = 0;
+              for (uint32_t k = 0; k < in.box_cnt; ++k) {
+                const igs_box& b = h.boxes[in.box_off + k];
+                need += (uint64_t)(b.hi[0] - b.lo[0]) * (b.hi[1] - b.lo[1]) * (b.hi[2] - b.lo[2]);
+              }
+              for (auto it = range.first; it != range.second; ++it) {
+                const igs_box& b = it->second.box;
+                have += (uint64_t)(b.hi[0] - b.lo[0]) * (b.hi[1] - b.lo[1]) * (b.hi[2] - b.lo[2]);
+              }
+              if (have < need) {
+                halted[n] = true;
+                stop_at[n] = i;
+                break;
+              }
               uint32_t Lr = L;
-              for (auto it = range.first; it != range.second; ++it) Lr = std::max(Lr, it->second.level);
+              for (auto it = range.first; it != range.second; ++it)
+                if (it->second.call == c->exec_call) Lr = std::max(Lr, it->second.level);
               ExecAlloc* d = get_alloc(c, n, in.a, in.c);
               if (!d) return fail_ctx(c, IGS_ERR_STATE, "receive into unknown allocation");
               for (auto it = range.first; it != range.second; ++it) {
-                ExecAlloc* s = get_alloc(c, it->second.node, it->second.alloc, in.c);
-                if (!s) return fail_ctx(c, IGS_ERR_STATE, "send from unknown allocation");
+                const igs_box& b = it->second.box;
                 CopyJob J{};
-                if (!make_copy_job(s->ptr, s->lo, s->hi, d->ptr, d->lo, d->hi, it->second.box, c->bufs[in.c].elem, J))
-                  return fail_ctx(c, IGS_ERR_STATE, "bad send box");
+                if (!make_copy_job(it->second.mail, b.lo, b.hi, d->ptr, d->lo, d->hi, b, c->bufs[in.c].elem, J))
+                  return fail_ctx(c, IGS_ERR_STATE, "bad receive box");
                 add_copy(p, Lr + 1, J);
+                p.at(Lr + 1).frees.push_back(it->second.mail);
               }
-              sends.erase(range.first, range.second);
+              c->sends.erase(range.first, range.second);
               h.level[i] = Lr + 1;
               break;
             }
@@ -1061,10 +1172,126 @@ extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
       }
     }
   }
-  r = run_pending(c, p);
+  *halted_any = false;
+  *progress = false;
+  for (uint32_t n = 0; n < c->N; ++n) {
+    NodeHost& h = c->nh[n];
+    const uint32_t upto = halted[n] ? stop_at[n] : (uint32_t)h.instrs.size();
+    if (upto > h.executed) *progress = true;
+    h.executed = upto;
+    if (halted[n]) *halted_any = true;
+  }
+  return IGS_OK;
+}
+
+}  // namespace
+
+extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
+  if (!c) return IGS_ERR_INVALID_ARG;
+  if (c->server) return fail_ctx(c, IGS_ERR_STATE, "detach the context from its server first");
+  int r = fetch_for_exec(c);
   if (r) return r;
+  for (;;) {
+    Pending p;
+    bool halted = false, progress = false;
+    if ((r = exec_walk(c, p, c->stream, &halted, &progress))) return r;
+    if ((r = run_pending(c, p, c->stream, true))) return r;
+    if (!halted) break;
+    if (!progress) break;  // a receive waits for sends not lowered yet: a later call executes it
+  }
   (void)flags;
   return IGS_OK;
+}
+
+extern "C" int igs_run(igs_ctx* c, uint32_t window) {
+  if (!c || window == 0) return IGS_ERR_INVALID_ARG;
+  if (c->server) return fail_ctx(c, IGS_ERR_STATE, "detach the context from its server first");
+  if (c->cfg.mode != IGS_MODE_BATCHED) return igs_execute(c, 0);  // already lowered at submission
+  if (!c->xstream) CK(cudaStreamCreateWithFlags(&c->xstream, cudaStreamNonBlocking));
+  if (!c->cstream) CK(cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking));
+  if (!c->m_progress) {
+    CK(cudaHostAlloc((void**)&c->m_progress, sizeof(uint32_t) * PR_WORDS * c->N, cudaHostAllocMapped));
+    CK(cudaHostGetDevicePointer((void**)&c->d_progress, (void*)c->m_progress, 0));
+  }
+  int r = download_nodes(c);
+  if (r) return r;
+  for (uint32_t n = 0; n < c->N; ++n) {
+    const NodeDev& nd = c->nodes_host[n];
+    volatile uint32_t* pr = c->m_progress + (size_t)n * PR_WORDS;
+    pr[PR_INSTR] = nd.n_instr;
+    pr[PR_EDGE] = nd.n_edge;
+    pr[PR_BOX] = nd.n_box;
+    pr[PR_BIND] = nd.n_bind;
+    pr[PR_STATUS] = nd.status;
+    pr[PR_CURSOR] = nd.cursor;
+  }
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  // the executor stream starts after everything already enqueued on the context's stream
+  cudaEvent_t ready;
+  CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  CK(cudaEventRecord(ready, c->stream));
+  CK(cudaStreamWaitEvent(c->xstream, ready, 0));
+  CK(cudaEventDestroy(ready));
+  c->pipelined = true;
+  auto finish = [&](int code) {
+    cudaStreamSynchronize(c->xstream);
+    cudaStreamSynchronize(c->stream);
+    c->pipelined = false;
+    ev_collect(c);
+    if (code == IGS_OK && igs_exec_error(true))
+      return fail_ctx(c, IGS_ERR_STATE, "a workload kernel accessed outside its allocation");
+    return code;
+  };
+  // one launch lowers every pending submission; each node's warp publishes
+  // its progress, and the executor follows behind on its own stream
+  if ((r = launch_lower(c, IGS_NONE, true, c->d_progress))) return finish(r);
+  const uint32_t total = (uint32_t)c->items.size();
+  std::vector<uint32_t> cur(c->N), cnt(4 * c->N);
+  uint32_t executed_upto = 0;
+  for (;;) {
+    bool done = true, failed = false;
+    uint32_t low = 0xFFFFFFFFu;
+    for (uint32_t n = 0; n < c->N; ++n) {
+      volatile uint32_t* pr = c->m_progress + (size_t)n * PR_WORDS;
+      cur[n] = pr[PR_CURSOR];
+      std::atomic_thread_fence(std::memory_order_acquire);
+      cnt[4 * n] = pr[PR_INSTR];
+      cnt[4 * n + 1] = pr[PR_EDGE];
+      cnt[4 * n + 2] = pr[PR_BOX];
+      cnt[4 * n + 3] = pr[PR_BIND];
+      if (pr[PR_STATUS] != ST_OK) failed = true;
+      if (cur[n] < total) done = false;
+      low = std::min(low, cur[n]);
+    }
+    if (failed) break;  // the status check below reports it
+    if (!done && cudaStreamQuery(c->stream) != cudaErrorNotReady) break;  // the launch ended early
+    if (!done && low < executed_upto + window) {
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      continue;
+    }
+    executed_upto = low;
+    for (uint32_t n = 0; n < c->N; ++n)
+      if ((r = fetch_node(c, n, cnt[4 * n], cnt[4 * n + 1], cnt[4 * n + 2], cnt[4 * n + 3], c->cstream)))
+        return finish(r);
+    Pending p;
+    bool halted = false, progress = false;
+    if ((r = exec_walk(c, p, c->xstream, &halted, &progress))) return finish(r);
+    if ((r = run_pending(c, p, c->xstream, false))) return finish(r);
+    if (done) break;
+  }
+  // the lowering launch has ended (or failed): its final state, then the rest
+  r = check_status(c);
+  if (r && r != IGS_ERR_OVERLAPPING_WRITE) return finish(r);
+  const int rejected = r;
+  if ((r = fetch_for_exec(c))) return finish(r);
+  for (;;) {
+    Pending p;
+    bool halted = false, progress = false;
+    if ((r = exec_walk(c, p, c->xstream, &halted, &progress))) return finish(r);
+    if ((r = run_pending(c, p, c->xstream, false))) return finish(r);
+    if (!halted || !progress) break;
+  }
+  return finish(rejected);
 }
 
 namespace {
@@ -1164,7 +1391,7 @@ extern "C" int igs_read_buffer(igs_ctx* c, uint32_t b, const uint32_t lo[3], con
       }
     }
   }
-  r = run_pending(c, p);
+  r = run_pending(c, p, c->stream, true);
   if (r) return r;
   CK(cudaMemcpyAsync(host_dst, stage, cnt, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));

@@ -117,6 +117,10 @@ struct Unit {
   ProgDev* prog;
 };
 
+// Progress record of one lowering unit (host-mapped): written by the unit's
+// warp after each submission, cursor last.
+enum ProgressWord : uint32_t { PR_CURSOR = 0, PR_INSTR = 1, PR_EDGE = 2, PR_BOX = 3, PR_BIND = 4, PR_STATUS = 5, PR_WORDS = 8 };
+
 // One slot of the serving loop (host-mapped memory): a warp serves the unit
 // while `state` is SLOT_ACTIVE and publishes how many submissions it has
 // taken in `done`.
@@ -140,7 +144,12 @@ struct CopyJob {
 }  // namespace igs
 
 // Device entry points implemented in the .cu translation units.
-int igs_launch_lower(const igs::Unit* units_dev, uint32_t n_units, uint32_t max_items, void* stream);
+// reserve: each unit's block also holds most of its SM's registers, keeping
+// other kernels off the SMs that lower (used while the executor runs concurrently).
+// progress (host-mapped, PR_WORDS per unit, or null): each unit publishes its
+// cursor and output counts after every submission it lowers.
+int igs_launch_lower(const igs::Unit* units_dev, uint32_t n_units, uint32_t max_items, void* stream,
+                     bool reserve = false, volatile uint32_t* progress = nullptr);
 // Persistent serving loop over n_slots slots; exits when *stop is set or a
 // warp stays idle for idle_polls polls (about 2 us each).
 int igs_launch_serve(igs::ServeSlot* slots, uint32_t n_slots, volatile uint32_t* stop, uint64_t idle_polls, void* stream);

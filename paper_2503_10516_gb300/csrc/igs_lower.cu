@@ -2656,8 +2656,25 @@ __device__ void store_ctx(Ctx& c, uint32_t cursor) {
 }
 
 // One warp per unit; each lowers the unit's pending items (at most max_items).
-__global__ void __launch_bounds__(32) lower_kernel(const Unit* units, uint32_t n_units, uint32_t max_items) {
-  const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// Publishes a node's progress to host-mapped memory: every record it counts
+// is written (and fenced) before the counts.
+__device__ void publish_progress(const Ctx& c, volatile uint32_t* pr, uint32_t cursor) {
+  __syncwarp();
+  if (c.lane == 0) {
+    __threadfence_system();
+    pr[PR_INSTR] = c.n_instr;
+    pr[PR_EDGE] = c.n_edge;
+    pr[PR_BOX] = c.n_box;
+    pr[PR_BIND] = c.n_bind;
+    pr[PR_STATUS] = c.err;
+    __threadfence_system();
+    pr[PR_CURSOR] = cursor;  // last: the host reads it first
+  }
+  __syncwarp();
+}
+
+__device__ void lower_unit(const Unit* units, uint32_t n_units, uint32_t max_items, uint32_t w,
+                           volatile uint32_t* progress) {
   if (w >= n_units) return;
   const Unit u = units[w];
   Ctx c;
@@ -2666,13 +2683,27 @@ __global__ void __launch_bounds__(32) lower_kernel(const Unit* units, uint32_t n
   const uint32_t avail = *u.prog->n_items;
   uint32_t end = avail;
   if (max_items != NONE && cursor + max_items < end) end = cursor + max_items;
+  volatile uint32_t* pr = progress ? progress + (size_t)w * PR_WORDS : nullptr;
   PhaseTimer pt = pt_start();
   while (cursor < end && c.err == ST_OK) {
     deliver(c, cursor);
     ++cursor;
+    if (pr) publish_progress(c, pr, cursor);
   }
   pt_lap(pt, c, PH_TOTAL);
   store_ctx(c, cursor);
+  if (pr) publish_progress(c, pr, cursor);
+}
+
+// Block b lowers unit b with its first warp. Blocks launched with more warps
+// (kReserveThreads) park the others at the barrier: they hold most of the
+// SM's registers, so no block of another kernel (the executor's copies and
+// kernels running concurrently) shares the SM, its issue slots or its L1.
+constexpr uint32_t kReserveThreads = 640;
+__global__ void __launch_bounds__(kReserveThreads) lower_kernel(const Unit* units, uint32_t n_units, uint32_t max_items,
+                                                               volatile uint32_t* progress) {
+  if (threadIdx.x < 32) lower_unit(units, n_units, max_items, blockIdx.x, progress);
+  __syncthreads();
 }
 
 // Copies submissions [from, to) and their tasks from the host-mapped arrays
@@ -2789,15 +2820,17 @@ int igs_launch_serve(igs::ServeSlot* slots, uint32_t n_slots, volatile uint32_t*
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int igs_launch_lower(const igs::Unit* units_dev, uint32_t n_units, uint32_t max_items, void* stream) {
+int igs_launch_lower(const igs::Unit* units_dev, uint32_t n_units, uint32_t max_items, void* stream, bool reserve,
+                     volatile uint32_t* progress) {
   if (n_units == 0) return 0;
-  // one warp per block, so that units spread over the SMs (each node's
+  // one unit per block, so that units spread over the SMs (each node's
   // tables then share an L1 with as few other units as possible)
   static bool carveout = false;
   if (!carveout) {
     cudaFuncSetAttribute(igs::lower_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     carveout = true;
   }
-  igs::lower_kernel<<<n_units, 32, 0, (cudaStream_t)stream>>>(units_dev, n_units, max_items);
+  const uint32_t threads = reserve ? igs::kReserveThreads : 32;
+  igs::lower_kernel<<<n_units, threads, 0, (cudaStream_t)stream>>>(units_dev, n_units, max_items, progress);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -30,7 +30,7 @@ EXPORTS = ("igs_create", "igs_destroy", "igs_create_buffer", "igs_destroy_buffer
            "igs_execute", "igs_read_buffer", "igs_lower_batch", "igs_counters", "igs_last_error", "igs_box_copy",
            "igs_set_timing", "igs_stats", "igs_profile", "igs_lower_static", "igs_submit_epoch",
            "igs_serve_create", "igs_serve_destroy", "igs_serve_attach", "igs_serve_start", "igs_serve_progress",
-           "igs_serve_detach", "igs_serve_stop")
+           "igs_serve_detach", "igs_serve_stop", "igs_run")
 
 
 class IgsError(RuntimeError):
@@ -110,6 +110,7 @@ def lib():
         L.igs_submit_task.argtypes = [vp, P32, ctypes.POINTER(ctypes.c_uint64)]
         L.igs_set_lookahead.argtypes = [vp, u32]
         L.igs_flush.argtypes = [vp]
+        L.igs_run.argtypes = [vp, u32]
         L.igs_sync.argtypes = [vp]
         L.igs_submit_epoch.argtypes = [vp]
         L.igs_serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(vp)]
@@ -243,6 +244,14 @@ class Context:
 
     def execute(self, sync: bool = True):
         self._check(lib().igs_execute(self._h, 1 if sync else 0), "execute")
+
+    def run(self, window: int = 64):
+        """Lowers the pending submissions in windows of `window` items while the
+        previous window's instructions execute (igs_run)."""
+        r = lib().igs_run(self._h, window)
+        if r not in (IGS_OK, IGS_ERR_OVERLAPPING_WRITE):
+            self._check(r, "run")
+        return r
 
     def read_buffer(self, b: int, lo, hi, elem_size: int) -> np.ndarray:
         lo3 = np.zeros(3, np.uint32)

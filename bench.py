@@ -159,7 +159,7 @@ def _stage_ctx(igs, prog, mode, stream):
     return c
 
 
-def measure_batched(igs, torch, stream, count=128, scale=0.01):
+def measure_batched(igs, torch, stream, count=512, scale=0.01):
     """Uneven programs (1-8 buffers of 2^10-2^24 elements, 1-128 chunks, 2-32
     memories, lookahead 0-16; task counts scaled down): one persistent launch
     over all of them vs one task per launch."""
@@ -193,7 +193,7 @@ def measure_batched(igs, torch, stream, count=128, scale=0.01):
     return res
 
 
-def measure_served(igs, torch, stream, streams=16, rate=2000.0, rows_max=2048, cols=1024, lookahead=0):
+def measure_served(igs, torch, stream, streams=64, rate=1e4, rows_max=2048, cols=1024, lookahead=0):
     """Growing-row program streams (rows appended 1-64 at a time, each task
     reading every earlier row) submitting with Poisson arrivals; per-task
     latency = arrival -> every node of its program has lowered it. Compared
@@ -480,7 +480,7 @@ def run_gpu(args):
     # ---- batched lowering of many programs, served lowering of many streams
     big_copy = measure_box_copy(igs, torch, stream)
     batched = measure_batched(igs, torch, sh) if world == 1 else None
-    served = {f"{int(r)}_per_s": measure_served(igs, torch, sh, rate=r) for r in (1000.0, 4000.0)} \
+    served = {f"{int(r)}_per_s": measure_served(igs, torch, sh, rate=r) for r in (1e4, 1e5)} \
         if world == 1 else None
 
     # ---- CPU baseline: the oracle on a bounded sample of the same workload

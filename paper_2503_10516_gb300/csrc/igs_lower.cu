@@ -231,7 +231,7 @@ __device__ __forceinline__ int heap_class(uint32_t entries) {
 }
 
 // A slab of at least `entries` entries (uniform); NONE when the heap is full.
-__device__ uint32_t heap_alloc(Ctx& c, uint32_t entries, uint32_t& cap) {
+__device__ __noinline__ uint32_t heap_alloc(Ctx& c, uint32_t entries, uint32_t& cap) {
   const int k = heap_class(entries);
   cap = 32u << k;
   NodeDev* nd = c.nd;
@@ -273,7 +273,7 @@ __device__ __forceinline__ void t_publish(Ctx& c, Table& t) {
 
 // Grows a heap table to hold `need` entries: the entries move to a bigger
 // slab at the same indices (a scan in progress stays valid through `t`).
-__device__ bool t_grow(Ctx& c, Table& t, uint32_t need) {
+__device__ __noinline__ bool t_grow(Ctx& c, Table& t, uint32_t need) {
   if (!t.dp) {
     fail_cap(c, CAP_TABLE, t.cap);
     return false;
@@ -391,7 +391,7 @@ __device__ void pt_lap(PhaseTimer& p, Ctx& c, int ph) {
 }
 
 // Stable in-place removal of dead entries.
-__device__ void t_compact(Ctx& c, Table& t) {
+__device__ __noinline__ void t_compact(Ctx& c, Table& t) {
   DT_START(dt);
   uint32_t w = 0;
   for (uint32_t base = 0; base < t.n; base += 32) {
@@ -467,6 +467,7 @@ __device__ void t_query(Ctx& c, const Table& src, uint32_t key, const Bx& q, Tab
         }
       }
     }
+    if (!__any_sync(FULL, hit)) continue;
     const uint32_t s = t_claim(c, out, hit);
     if (c.err) return;
     if (hit) t_put(out, s, 0, is, v0, v1, v2);
@@ -477,7 +478,7 @@ __device__ void t_query(Ctx& c, const Table& src, uint32_t key, const Bx& q, Tab
 
 // Removes box r from every entry of `key` (NONE = any) that matches the
 // optional value filter; the remainders keep their values.
-__device__ void t_subtract(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t vfilter = NONE) {
+__device__ __noinline__ void t_subtract(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t vfilter = NONE) {
   DT_START(dt);
   DT_COUNT(N_SUBTRACT, 1);
   t_tidy(c, t);
@@ -499,10 +500,12 @@ __device__ void t_subtract(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t
         }
       }
     }
+    const uint32_t hits = __ballot_sync(FULL, hit);
+    if (!hits) continue;  // nothing to remove in these 32 entries
     Bx pc[6];
     int np = 0;
     if (hit) np = bx_minus(e, r, pc);
-    t_dead(c, t, __popc(__ballot_sync(FULL, hit)));
+    t_dead(c, t, __popc(hits));
     const uint32_t first = t_claim_n(c, t, hit ? (uint32_t)np : 0u);
     if (c.err) return;
     if (hit) {
@@ -515,7 +518,7 @@ __device__ void t_subtract(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t
 }
 
 // value[vidx] |= bits on box r for entries of `key`.
-__device__ void t_or(Ctx& c, Table& t, uint32_t key, const Bx& r, int vidx, uint32_t bits) {
+__device__ __noinline__ void t_or(Ctx& c, Table& t, uint32_t key, const Bx& r, int vidx, uint32_t bits) {
   t_tidy(c, t);
   const uint32_t n0 = t.n;
   for (uint32_t base = 0; base < n0; base += 32) {
@@ -530,10 +533,12 @@ __device__ void t_or(Ctx& c, Table& t, uint32_t key, const Bx& r, int vidx, uint
       v[2] = t_v(t, 2, i);
       hit = bx_overlap(e, r) && (v[vidx] & bits) != bits;
     }
+    const uint32_t hits = __ballot_sync(FULL, hit);
+    if (!hits) continue;
     Bx pc[6];
     int np = 0;
     if (hit) np = bx_minus(e, r, pc);
-    t_dead(c, t, __popc(__ballot_sync(FULL, hit)));
+    t_dead(c, t, __popc(hits));
     const uint32_t first = t_claim_n(c, t, hit ? (uint32_t)np + 1 : 0u);
     if (c.err) return;
     if (hit) {
@@ -548,7 +553,7 @@ __device__ void t_or(Ctx& c, Table& t, uint32_t key, const Bx& r, int vidx, uint
 }
 
 // Sets the values of box r for `key`.
-__device__ void t_set(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t v0, uint32_t v1, uint32_t v2) {
+__device__ __noinline__ void t_set(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t v0, uint32_t v1, uint32_t v2) {
   t_subtract(c, t, key, r);
   const uint32_t s = t_claim(c, t, c.lane == 0);
   if (c.err) return;
@@ -558,7 +563,7 @@ __device__ void t_set(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t v0, 
 
 // Merges entries from index `from` on with equal key and values into
 // adjacent entries whose union is a box (keeps the tables small).
-__device__ void t_merge_from(Ctx& c, Table& t, uint32_t from) {
+__device__ __noinline__ void t_merge_from(Ctx& c, Table& t, uint32_t from) {
   DT_START(dt);
   DT_COUNT(N_MERGE, 1);
   for (uint32_t i = from; i < t.n; ++i) {
@@ -605,7 +610,7 @@ __device__ void t_maybe_merge(Ctx& c, Table& t, uint32_t floor) {
 
 // Makes the live entries with value v0 == val (NONE = all) of each key
 // pairwise disjoint by subtracting earlier entries from later ones.
-__device__ void t_make_disjoint(Ctx& c, Table& t, uint32_t val = NONE) {
+__device__ __noinline__ void t_make_disjoint(Ctx& c, Table& t, uint32_t val = NONE) {
   for (uint32_t i = 0; i < t.n; ++i) {
     const uint32_t k = t_key(t, i);
     if (k == DEAD) continue;
@@ -626,10 +631,12 @@ __device__ void t_make_disjoint(Ctx& c, Table& t, uint32_t val = NONE) {
           w2 = t_v(t, 2, j);
         }
       }
+      const uint32_t hits = __ballot_sync(FULL, hit);
+      if (!hits) continue;
       Bx pc[6];
       int np = 0;
       if (hit) np = bx_minus(f, e, pc);
-      t_dead(c, t, __popc(__ballot_sync(FULL, hit)));
+      t_dead(c, t, __popc(hits));
       const uint32_t first = t_claim_n(c, t, hit ? (uint32_t)np : 0u);
       if (c.err) return;
       if (hit) {
@@ -647,14 +654,14 @@ __device__ void t_make_disjoint(Ctx& c, Table& t, uint32_t val = NONE) {
 // fastest dimension maximal (splitting partially overlapping neighbours),
 // then merge identical intervals over the middle dimension, then identical
 // rectangles over the slowest dimension.
-__device__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_t from, uint32_t to, Table& out);
+__device__ __noinline__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_t from, uint32_t to, Table& out);
 __device__ uint32_t canonical(Ctx& c, const Table& in, uint32_t from, uint32_t to, Table& out) {
   PhaseTimer pt = pt_start();
   const uint32_t r = canonical_impl(c, in, from, to, out);
   pt_lap(pt, c, PH_CANON);
   return r;
 }
-__device__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_t from, uint32_t to, Table& out) {
+__device__ __noinline__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_t from, uint32_t to, Table& out) {
   Table& W = c.s[S_CAN];
   t_reset(W);
   for (uint32_t base = from; base < to; base += 32) {
@@ -670,6 +677,26 @@ __device__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_t from, uint3
     if (live) t_put(W, s, 0, b, 0, 0, 0);
   }
   __syncwarp();
+  // A region whose boxes fill their bounding box exactly (the boxes are
+  // disjoint, so equal volumes suffice) is that one box.
+  if (W.n > 1) {
+    uint64_t vol = 0;
+    for (uint32_t base = 0; base < W.n; base += 32) {
+      const uint32_t i = base + c.lane;
+      uint64_t v = i < W.n ? bx_volume(t_box(W, i)) : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+      vol += v;
+    }
+    const Bx bb = t_bbox(c, W, 0, W.n);
+    if (vol == bx_volume(bb)) {
+      __syncwarp();
+      if (c.lane == 0) t_put(W, 0, 0, bb, 0, 0, 0);
+      W.n = 1;
+      W.live = 1;
+      __syncwarp();
+    }
+  }
   // Phase md rewrites until no box a has a neighbour b with a.hi[md] ==
   // b.lo[md], equal extents in the faster dimensions and overlapping extents
   // in the slower ones. One pass finds, for every box, its successor with
@@ -945,7 +972,7 @@ __device__ Bx buffer_box(const BufDesc& b) {
 }
 
 // a1: chunks of a task: key = chunk index, v0 = node, v1 = memory (Sec. 3.1).
-__device__ void task_chunks(Ctx& c, const igs_task& t, Table& CH) {
+__device__ __noinline__ void task_chunks(Ctx& c, const igs_task& t, Table& CH) {
   t_reset(CH);
   const uint64_t E0 = t.range[0], C = t.num_chunks, M = (uint64_t)c.N * c.D;
   for (uint32_t base = 0; base < t.num_chunks; base += 32) {
@@ -1007,7 +1034,7 @@ __device__ Bx map_box(const igs_accessor& a, const Bx& ch, const BufDesc& buf) {
 }
 
 // Mapped boxes for every (chunk slot, accessor): MP[slot * nacc + a].
-__device__ void task_mapped(Ctx& c, const igs_task& t, const Table& CH, Table& MP) {
+__device__ __noinline__ void task_mapped(Ctx& c, const igs_task& t, const Table& CH, Table& MP) {
   const uint32_t na = t.num_accessors, total = CH.n * na;
   if (total > MP.cap) {
     fail_cap(c, CAP_TABLE, MP.cap);
@@ -1026,7 +1053,7 @@ __device__ void task_mapped(Ctx& c, const igs_task& t, const Table& CH, Table& M
 }
 
 // Sec. 4.4: chunks of one task writing overlapping regions.
-__device__ bool overlapping_writes(Ctx& c, const igs_task& t, const Table& CH, const Table& MP) {
+__device__ __noinline__ bool overlapping_writes(Ctx& c, const igs_task& t, const Table& CH, const Table& MP) {
   const uint32_t na = t.num_accessors;
   for (uint32_t a = 0; a < na; ++a) {
     if (!(t.acc[a].mode & IGS_WRITE)) continue;
@@ -1058,7 +1085,7 @@ __device__ bool overlapping_writes(Ctx& c, const igs_task& t, const Table& CH, c
 // writes, the readers since the last write (WAR anti); no predecessor at all
 // means an edge to the last epoch. Then reads, then writes are applied to
 // the per-allocation tracking tables.
-__device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint32_t fb, uint32_t fc, uint32_t fd,
+__device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint32_t fb, uint32_t fc, uint32_t fd,
                               const Table* bt, uint32_t bfrom, uint32_t bto, const Acc* acc, int nacc, bool keep_dep,
                               const Table* bindt, uint32_t bind_from, uint32_t bind_n);
 __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint32_t fb, uint32_t fc, uint32_t fd,
@@ -1069,7 +1096,7 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
   pt_lap(pt, c, PH_EMIT);
   return r;
 }
-__device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint32_t fb, uint32_t fc, uint32_t fd,
+__device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint32_t fb, uint32_t fc, uint32_t fd,
                               const Table* bt, uint32_t bfrom, uint32_t bto, const Acc* acc, int nacc, bool keep_dep,
                               const Table* bindt, uint32_t bind_from, uint32_t bind_n) {
   if (c.err) return NONE;
@@ -1080,58 +1107,93 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
   DT_START(dt);
   DT_COUNT(N_EMIT, 1);
   // one probe per (access, region box, table): last writers for every access,
-  // readers for writes; then every probed entry in one lane-parallel pass
+  // readers for writes; every probed entry is tested in a lane-parallel pass.
+  // Probes are gathered 32 at a time, probe j in lane j's registers (table
+  // base, first entry index of the batch, region box, kind); a lane finds
+  // the probe of its entry with shuffles instead of loads.
   {
-    Table& PR = c.s[S_CAN];
-    t_reset(PR);
-    uint32_t total = 0;
+    uint32_t np = 0, total = 0;
+    const uint32_t* my_base = nullptr;
+    uint32_t my_start = 0xFFFFFFFFu, my_tab = 0, my_mode = 0;
+    Bx my_q{};
+    auto run_batch = [&]() -> bool {
+      c.map_reads += total;
+      DT_COUNT(N_PROBE_ENTRIES, total);
+      const unsigned long long my_b = (unsigned long long)(uintptr_t)my_base;
+      for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t f = base + c.lane;
+        // probe of entry f: the last probe starting at or before f
+        uint32_t p = 0;
+        for (uint32_t q = 1; q < np; ++q)
+          if (__shfl_sync(FULL, my_start, q) <= f) p = q;
+        const uint32_t start = __shfl_sync(FULL, my_start, p), tab = __shfl_sync(FULL, my_tab, p),
+                       mode = __shfl_sync(FULL, my_mode, p);
+        const uint32_t* tb = reinterpret_cast<const uint32_t*>((uintptr_t)__shfl_sync(FULL, my_b, p));
+        Bx q;
+        for (int d = 0; d < 3; ++d) {
+          q.lo[d] = __shfl_sync(FULL, my_q.lo[d], p);
+          q.hi[d] = __shfl_sync(FULL, my_q.hi[d], p);
+        }
+        bool hit = false;
+        uint32_t w = 0, kind = 0;
+        if (f < total) {
+          const uint4* e = reinterpret_cast<const uint4*>(tb + (size_t)(f - start) * F_COUNT);
+          const uint4 e0 = e[0], e1 = e[1], e2 = e[2];
+          Bx eb;
+          eb.lo[0] = e0.y;
+          eb.lo[1] = e0.z;
+          eb.lo[2] = e0.w;
+          eb.hi[0] = e1.x;
+          eb.hi[1] = e1.y;
+          eb.hi[2] = e1.z;
+          if (e0.x != DEAD && bx_overlap(eb, q)) {
+            hit = true;
+            w = e1.w;  // v0
+            if (tab == 1) kind = IGS_DEP_ANTI;
+            else if (e2.x == 1) kind = IGS_DEP_ALLOC;  // v1: an allocation writer
+            else kind = ((mode & IGS_READ) ? IGS_DEP_DATAFLOW : 0u) | ((mode & IGS_WRITE) ? IGS_DEP_ANTI : 0u);
+          }
+        }
+        if (!__any_sync(FULL, hit)) continue;
+        const uint32_t s = t_claim(c, D, hit);
+        if (c.err) return false;
+        if (hit) {
+          FLD(D, F_V, s) = w;
+          FLD(D, F_V + 1, s) = kind;
+        }
+      }
+      np = 0;
+      total = 0;
+      return true;
+    };
     for (int k = 0; k < nacc; ++k) {
       const Acc& A = acc[k];
       const uint32_t slot = nd->allocs[A.alloc].slot;
-      const uint32_t wn = nd->wr_d[kDesc * slot + 2], rn = nd->rd_d[kDesc * slot + 2];
+      const uint32_t* wd = nd->wr_d + kDesc * slot;
+      const uint32_t* rdd = nd->rd_d + kDesc * slot;
+      const uint32_t wn = wd[2], rn = rdd[2];
+      const uint32_t* wb = nd->heap + (size_t)wd[0] * F_COUNT;
+      const uint32_t* rb = nd->heap + (size_t)rdd[0] * F_COUNT;
       for (uint32_t r = A.from; r < A.to; ++r) {
         if (t_key(*A.t, r) == DEAD) continue;
         const Bx q = t_box(*A.t, r);
         for (int tab = 0; tab < ((A.mode & IGS_WRITE) ? 2 : 1); ++tab) {
-          if (PR.n >= PR.cap) {
-            fail_cap(c, CAP_TABLE, PR.cap);
-            return NONE;
+          const uint32_t n = tab == 0 ? wn : rn;
+          if (n == 0) continue;
+          if (np == 32 && !run_batch()) return NONE;
+          if (c.lane == np) {
+            my_base = tab == 0 ? wb : rb;
+            my_start = total;
+            my_tab = (uint32_t)tab;
+            my_mode = A.mode;
+            my_q = q;
           }
-          if (c.lane == 0) t_put(PR, PR.n, (uint32_t)tab, q, slot, total, A.mode);
-          PR.n += 1;
-          total += tab == 0 ? wn : rn;
+          np += 1;
+          total += n;
         }
       }
     }
-    __syncwarp();
-    c.map_reads += total;
-    DT_COUNT(N_PROBE_ENTRIES, total);
-    const uint32_t np = PR.n;
-    for (uint32_t base = 0; base < total; base += 32) {
-      const uint32_t f = base + c.lane;
-      bool hit = false;
-      uint32_t w = 0, kind = 0;
-      if (f < total) {
-        uint32_t p = 0;
-        while (p + 1 < np && t_v(PR, 1, p + 1) <= f) ++p;
-        const uint32_t tab = t_key(PR, p), slot = t_v(PR, 0, p), mode = t_v(PR, 2, p);
-        const Table T = heap_table(nd, (tab == 0 ? nd->wr_d : nd->rd_d) + kDesc * slot);
-        const uint32_t j = f - t_v(PR, 1, p);
-        if (t_key(T, j) != DEAD && bx_overlap(t_box(T, j), t_box(PR, p))) {
-          hit = true;
-          w = t_v(T, 0, j);
-          if (tab == 1) kind = IGS_DEP_ANTI;
-          else if (t_v(T, 1, j) == 1) kind = IGS_DEP_ALLOC;  // an allocation writer
-          else kind = ((mode & IGS_READ) ? IGS_DEP_DATAFLOW : 0u) | ((mode & IGS_WRITE) ? IGS_DEP_ANTI : 0u);
-        }
-      }
-      const uint32_t s = t_claim(c, D, hit);
-      if (c.err) return NONE;
-      if (hit) {
-        FLD(D, F_V, s) = w;
-        FLD(D, F_V + 1, s) = kind;
-      }
-    }
+    if (np && !run_batch()) return NONE;
   }
   __syncwarp();
   DT_LAP(dt, D_PROBE);
@@ -1347,7 +1409,7 @@ __device__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, 
 // Replace every tracked instruction id older than h by h and re-merge (a9).
 // In writer tables (writers = true) v1 marks allocation writers; a replaced
 // writer is the horizon, which is not one.
-__device__ void map_ids(Ctx& c, Table& T, uint32_t h, bool writers = false) {
+__device__ __noinline__ void map_ids(Ctx& c, Table& T, uint32_t h, bool writers = false) {
   for (uint32_t base = 0; base < T.n; base += 32) {
     const uint32_t i = base + c.lane;
     if (i < T.n && t_key(T, i) != DEAD) {
@@ -1361,7 +1423,7 @@ __device__ void map_ids(Ctx& c, Table& T, uint32_t h, bool writers = false) {
   __syncwarp();
 }
 
-__device__ void apply_epoch(Ctx& c, uint32_t h) {
+__device__ __noinline__ void apply_epoch(Ctx& c, uint32_t h) {
   for (uint32_t li = 0; li < c.n_live; ++li) {
     const uint32_t aid = c.nd->live[li];
     Table WR = wr_t(c, aid);
@@ -1394,7 +1456,7 @@ __device__ void apply_epoch(Ctx& c, uint32_t h) {
 }
 
 // Free of an allocation: depends on every writer and reader (allocation lifetime).
-__device__ void emit_free(Ctx& c, uint32_t seq, uint32_t aid) {
+__device__ __noinline__ void emit_free(Ctx& c, uint32_t seq, uint32_t aid) {
   Table& D = c.s[S_DEP];
   t_reset(D);
   for (int k = 0; k < 2; ++k) {
@@ -1419,7 +1481,7 @@ __device__ void emit_free(Ctx& c, uint32_t seq, uint32_t aid) {
 // a5: coherence copies making need = T[from, to) (disjoint boxes) up to date
 // in memory m, allocation dst: stale parts split by original producer, then
 // by source allocation, one copy per (producer, source allocation).
-__device__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_t m, uint32_t dst, const Table& T, uint32_t from,
+__device__ __noinline__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_t m, uint32_t dst, const Table& T, uint32_t from,
                           uint32_t to) {
   Table& Q = c.s[S_T0];
   Table& G = c.s[S_T1];
@@ -1522,7 +1584,7 @@ __device__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_t m, uint32_t
 // NB[m] = bounding box of node m's chunks (key DEAD if it has none). The
 // chunks of a node are consecutive along the split dimension, so this box is
 // exactly their union.
-__device__ void node_bboxes(Ctx& c, const Table& CH, Table& NB) {
+__device__ __noinline__ void node_bboxes(Ctx& c, const Table& CH, Table& NB) {
   for (uint32_t m = 0; m < c.N; ++m) {
     Bx acc;
     acc.lo[0] = acc.lo[1] = acc.lo[2] = 0xFFFFFFFFu;
@@ -1557,7 +1619,7 @@ __device__ __forceinline__ bool union_is_image(const igs_accessor& a, const BufD
 // node awaits missing_node and pushes missing_m n owned(node) to every m.
 // Results go to the QR table under key seq: v0 = 0 push boxes, 1 await boxes,
 // 2 push bbox, 3 await bbox; v1 = buffer; v2 = target node.
-__device__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP) {
+__device__ __noinline__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP) {
   const uint32_t na = t.num_accessors;
   Table& TMP = c.s[S_T0];
   Table& MISS = c.s[S_T1];
@@ -1708,7 +1770,7 @@ __device__ void qr_block(const Ctx& c, uint32_t seq, uint32_t& qs, uint32_t& qe)
 
 // Appends the requirements (key = buffer * 32 + memory, box) of a task on this
 // node: every non-empty mapped box of a local chunk, plus the staging bboxes.
-__device__ void requirements(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP, Table& RQ,
+__device__ __noinline__ void requirements(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP, Table& RQ,
                              uint32_t only_key, uint32_t own_flag) {
   const uint32_t na = t.num_accessors, total = CH.n * na;
   for (uint32_t base = 0; base < total; base += 32) {
@@ -1746,7 +1808,7 @@ __device__ void requirements(Ctx& c, const igs_task& t, uint32_t seq, const Tabl
   __syncwarp();
 }
 
-__device__ bool allocating(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP) {
+__device__ __noinline__ bool allocating(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP) {
   Table& RQ = c.s[S_CL];
   t_reset(RQ);
   requirements(c, t, seq, CH, MP, RQ, NONE, 1);
@@ -1763,7 +1825,7 @@ __device__ bool allocating(Ctx& c, const igs_task& t, uint32_t seq, const Table&
   return false;
 }
 
-__device__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP) {
+__device__ __noinline__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP) {
   Table& RQ = c.s[S_T4];
   Table& CL = c.s[S_CL];
   Table& CH2 = c.s[S_CH2];
@@ -1979,7 +2041,7 @@ __device__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq, const Table
 
 // ---- compile one task (P1..P5) ----------------------------------------------
 
-__device__ void compile_task(Ctx& c, uint32_t item) {
+__device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
   const Item it = c.pg->items[item];
   const igs_task& t = c.pg->tasks[it.task];
   const uint32_t seq = it.seq, na = t.num_accessors;
@@ -1990,8 +2052,8 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
   task_mapped(c, t, CH, MP);
   if (c.err) return;
   pt_lap(pt, c, PH_SPLIT);
-  // P1
-  alloc_phase(c, t, seq, CH, MP);
+  // P1 (nothing to do unless some requirement lies outside every allocation)
+  if (allocating(c, t, seq, CH, MP)) alloc_phase(c, t, seq, CH, MP);
   if (c.err) return;
   pt_lap(pt, c, PH_P1);
   uint32_t qs, qe;
@@ -2390,7 +2452,7 @@ __device__ void compile_task(Ctx& c, uint32_t item) {
 
 // ---- items ---------------------------------------------------------------------
 
-__device__ void process(Ctx& c, uint32_t item) {
+__device__ __noinline__ void process(Ctx& c, uint32_t item) {
   const Item it = c.pg->items[item];
   switch (it.kind) {
     case IT_CREATE: {
@@ -2518,7 +2580,7 @@ __device__ void maintain(Ctx& c) { t_tidy(c, c.qr); }
 // Scheduler lookahead (Sec. 4.3): a task is queued while an allocating task
 // is queued; the queue is compiled when it holds more than `lookahead` tasks,
 // at an epoch, or when a buffer is destroyed.
-__device__ void deliver(Ctx& c, uint32_t item) {
+__device__ __noinline__ void deliver(Ctx& c, uint32_t item) {
   const Item it = c.pg->items[item];
   maintain(c);
   if (c.err) return;
@@ -2658,7 +2720,7 @@ __device__ void store_ctx(Ctx& c, uint32_t cursor) {
 // One warp per unit; each lowers the unit's pending items (at most max_items).
 // Publishes a node's progress to host-mapped memory: every record it counts
 // is written (and fenced) before the counts.
-__device__ void publish_progress(const Ctx& c, volatile uint32_t* pr, uint32_t cursor) {
+__device__ __noinline__ void publish_progress(const Ctx& c, volatile uint32_t* pr, uint32_t cursor) {
   __syncwarp();
   if (c.lane == 0) {
     __threadfence_system();
@@ -2709,7 +2771,7 @@ __global__ void __launch_bounds__(kReserveThreads) lower_kernel(const Unit* unit
 // Copies submissions [from, to) and their tasks from the host-mapped arrays
 // into the program's device arrays (16-byte words, all lanes). Every node warp
 // of a program stages the same records; the copies write equal bytes.
-__device__ void stage_submissions(const ProgDev* pg, uint32_t from, uint32_t to) {
+__device__ __noinline__ void stage_submissions(const ProgDev* pg, uint32_t from, uint32_t to) {
   // host-written records are read with cache-volatile loads (never from a
   // line cached before the host wrote it)
   static_assert(sizeof(Item) == 16, "an item is one 16-byte word");

@@ -96,11 +96,11 @@ def test_heap_exhaustion_reports_capacity():
 
 
 def test_timed_batch_workload_parity():
-    """The 128 uneven programs the batched-lowering measurement times (task
+    """The 512 uneven programs the batched-lowering measurement times (task
     counts scaled to 1 %), all in one launch, in the configuration the
     measurement uses (capacities estimated from the program shapes)."""
     from paper_2503_10516_gb300 import igs
-    progs = W.batch_programs(count=128, scale=0.01, seed=0x5EED + 3)
+    progs = W.batch_programs(count=512, scale=0.01, seed=0x5EED + 3)
     ctxs = []
     for p in progs:
         c = igs.Context(p.nodes, p.devices, p.horizon_step, p.lookahead, mode=igs.MODE_BATCHED, **igs.small_caps(p))

@@ -563,10 +563,12 @@ __device__ __noinline__ void t_set(Ctx& c, Table& t, uint32_t key, const Bx& r, 
 
 // Merges entries from index `from` on with equal key and values into
 // adjacent entries whose union is a box (keeps the tables small).
-__device__ __noinline__ void t_merge_from(Ctx& c, Table& t, uint32_t from) {
+// only_v0 != NONE: only entries whose first value is only_v0 take part.
+__device__ __noinline__ void t_merge_from(Ctx& c, Table& t, uint32_t from, uint32_t only_v0 = NONE) {
   DT_START(dt);
   DT_COUNT(N_MERGE, 1);
   for (uint32_t i = from; i < t.n; ++i) {
+    if (only_v0 != NONE && t_v(t, 0, i) != only_v0) continue;
     uint32_t cand = i;
     for (int guard = 0; guard < 4096; ++guard) {
       DT_COUNT(N_MERGE_PROBE, 1);
@@ -1408,37 +1410,46 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
 
 // Replace every tracked instruction id older than h by h and re-merge (a9).
 // In writer tables (writers = true) v1 marks allocation writers; a replaced
-// writer is the horizon, which is not one.
-__device__ __noinline__ void map_ids(Ctx& c, Table& T, uint32_t h, bool writers = false) {
+// writer is the horizon, which is not one. Returns whether any id changed.
+__device__ __noinline__ bool map_ids(Ctx& c, Table& T, uint32_t h, bool writers = false) {
+  bool any = false;
   for (uint32_t base = 0; base < T.n; base += 32) {
     const uint32_t i = base + c.lane;
+    bool ch = false;
     if (i < T.n && t_key(T, i) != DEAD) {
       const uint32_t v = t_v(T, 0, i);
       if (v < h) {
         FLD(T, F_V, i) = h;
         if (writers) FLD(T, F_V + 1, i) = 0;
+        ch = true;
       }
     }
+    any = any || __any_sync(FULL, ch);
   }
   __syncwarp();
+  return any;
 }
 
 __device__ __noinline__ void apply_epoch(Ctx& c, uint32_t h) {
   for (uint32_t li = 0; li < c.n_live; ++li) {
     const uint32_t aid = c.nd->live[li];
+    // tables whose ids all stay are left as they are (re-merging is a matter
+    // of table size, not of content)
     Table WR = wr_t(c, aid);
-    map_ids(c, WR, h, true);
-    t_compact(c, WR);
-    t_merge_from(c, WR, 0);
-    t_compact(c, WR);
-    t_set_mark(c, WR);
+    if (map_ids(c, WR, h, true)) {
+      t_compact(c, WR);
+      t_merge_from(c, WR, 0);
+      t_compact(c, WR);
+      t_set_mark(c, WR);
+    }
     Table RD = rd_t(c, aid);
-    map_ids(c, RD, h);
-    t_make_disjoint(c, RD, h);
-    t_compact(c, RD);
-    t_merge_from(c, RD, 0);
-    t_compact(c, RD);
-    t_set_mark(c, RD);
+    if (map_ids(c, RD, h)) {
+      t_make_disjoint(c, RD, h);
+      t_compact(c, RD);
+      t_merge_from(c, RD, 0);
+      t_compact(c, RD);
+      t_set_mark(c, RD);
+    }
     if (c.err) return;
   }
   const uint32_t nb = c.nd->cap_buffers;
@@ -1446,7 +1457,7 @@ __device__ __noinline__ void apply_epoch(Ctx& c, uint32_t h) {
     if (c.nd->bst_d[kDesc * b + 1] == 0) continue;  // no table (never created or destroyed)
     Table B = bst_t(c, b);
     if (B.n == 0) continue;
-    map_ids(c, B, h);
+    if (!map_ids(c, B, h)) continue;
     t_compact(c, B);
     t_merge_from(c, B, 0);
     t_compact(c, B);
@@ -1532,10 +1543,9 @@ __device__ __noinline__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_
       if (hit) t_put(G, s, 0, t_box(Q, i), 0, 0, 0);
     }
     __syncwarp();
-    for (uint32_t li = 0; li < c.n_live; ++li) {
-      const uint32_t src = c.nd->live[li];
+    // one copy per source allocation of (b, pmem), in live (ascending id) order
+    auto copy_from = [&](uint32_t src) -> bool {
       const AllocRec a = c.nd->allocs[src];
-      if (a.buffer != b || a.mem != pmem) continue;
       t_reset(P);
       const Bx ab = alloc_box(a);
       for (uint32_t base = 0; base < G.n; base += 32) {
@@ -1547,26 +1557,38 @@ __device__ __noinline__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_
           hit = !bx_empty(is);
         }
         const uint32_t s = t_claim(c, P, hit);
-        if (c.err) return;
+        if (c.err) return false;
         if (hit) t_put(P, s, 0, is, 0, 0, 0);
       }
       __syncwarp();
-      if (P.n == 0) continue;
+      if (P.n == 0) return true;
       t_reset(CN);
       canonical(c, P, 0, P.n, CN);
-      if (c.err) return;
+      if (c.err) return false;
       Acc acc[2] = {{&CN, 0, CN.n, src, IGS_READ}, {&CN, 0, CN.n, dst, IGS_WRITE}};
       emit(c, IGS_COPY, seq, src, dst, b, 0, &CN, 0, CN.n, acc, 2, false);
-      if (c.err) return;
+      if (c.err) return false;
       // remember the copied region
       for (uint32_t base = 0; base < CN.n; base += 32) {
         const uint32_t i = base + c.lane;
         const bool in = i < CN.n;
         const uint32_t s = t_claim(c, CP, in);
-        if (c.err) return;
+        if (c.err) return false;
         if (in) t_put(CP, s, 0, t_box(CN, i), 0, 0, 0);
       }
       __syncwarp();
+      return true;
+    };
+    for (uint32_t lb = 0; lb < c.n_live; lb += 32) {
+      const uint32_t li = lb + c.lane;
+      uint32_t mine = NONE;
+      if (li < c.n_live) {
+        mine = c.nd->live[li];
+        const AllocRec& r = c.nd->allocs[mine];
+        if (r.buffer != b || r.mem != pmem) mine = NONE;
+      }
+      for (uint32_t set = __ballot_sync(FULL, mine != NONE); set; set &= set - 1)
+        if (!copy_from(__shfl_sync(FULL, mine, __ffs(set) - 1))) return;
     }
   }
   Table B = bst_t(c, b);

@@ -2427,18 +2427,17 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     const uint32_t kid = emit(c, IGS_KERNEL, seq, t_key(CH, slot), mem, t.kernel_id, NONE, &CH, slot, slot + 1, acc,
                               nacc, false, &BT, 0, na);
     if (c.err) return;
-    for (uint32_t a = 0; a < na; ++a) {
-      const Bx x = t_box(MP, slot * na + a);
-      if (!(t.acc[a].mode & IGS_WRITE) || bx_empty(x)) continue;
-      Table B = bst_t(c, t.acc[a].buffer);
-      t_set(c, B, NONE, x, kid, mem, 1u << mem);
-      if (c.err) return;
-      t_maybe_merge(c, B, 4 * CH.n + 64);
-    }
+    __syncwarp();
+    if (c.lane == 0) FLD(AL, F_V, slot * na) = kid;  // the chunk's kernel, for the buffer state below
+    __syncwarp();
   }
   pt_lap(pt, c, PH_P5);
-  // writes of other nodes make the local copies stale
-  Table& NB = c.s[S_T4];
+  // buffer state of every written region: a local chunk's kernel is its
+  // original producer in the chunk's memory; writes of other nodes make the
+  // local copies stale. The written regions of one accessor are disjoint
+  // (overlapping writes were rejected), so the order of these updates does
+  // not matter.
+  Table& NB = c.s[S_T3];
   node_bboxes(c, CH, NB);
   for (uint32_t a = 0; a < na; ++a) {
     if (!(t.acc[a].mode & IGS_WRITE)) continue;
@@ -2447,20 +2446,54 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     t_tidy(c, B);
     const uint32_t from = B.n;
     if (union_is_image(t.acc[a], bd)) {
+      // all chunks' writes form the image of the task's range: one subtraction
+      Bx all;
+      all.lo[0] = all.lo[1] = all.lo[2] = 0xFFFFFFFFu;
+      all.hi[0] = all.hi[1] = all.hi[2] = 0;
+      for (uint32_t m = 0; m < c.N; ++m)
+        if (t_key(NB, m) != DEAD) all = bx_union(all, t_box(NB, m));
+      const Bx U = map_box(t.acc[a], all, bd);
+      if (!bx_empty(U)) t_subtract(c, B, NONE, U);
+      for (uint32_t base = 0; base < CH.n; base += 32) {
+        const uint32_t slot = base + c.lane;
+        bool hit = false;
+        Bx x{};
+        uint32_t kid = 0, mem = 0;
+        if (slot < CH.n && t_v(CH, 0, slot) == c.node) {
+          x = t_box(MP, slot * na + a);
+          hit = !bx_empty(x);
+          kid = FLD(AL, F_V, slot * na);
+          mem = t_v(CH, 1, slot);
+        }
+        const uint32_t s = t_claim(c, B, hit);
+        if (c.err) return;
+        if (hit) t_put(B, s, 0, x, kid, mem, 1u << mem);
+      }
       for (uint32_t m = 0; m < c.N; ++m) {
         if (m == c.node || t_key(NB, m) == DEAD) continue;
         const Bx x = map_box(t.acc[a], t_box(NB, m), bd);
-        if (!bx_empty(x)) t_set(c, B, NONE, x, REMOTE, 0, 0);
+        if (bx_empty(x)) continue;
+        const uint32_t s = t_claim(c, B, c.lane == 0);
+        if (c.err) return;
+        if (c.lane == 0) t_put(B, s, 0, x, REMOTE, 0, 0);
+        __syncwarp();
       }
     } else {
       for (uint32_t slot = 0; slot < CH.n; ++slot) {
-        if (t_v(CH, 0, slot) == c.node) continue;
         const Bx x = t_box(MP, slot * na + a);
-        if (!bx_empty(x)) t_set(c, B, NONE, x, REMOTE, 0, 0);
+        if (bx_empty(x)) continue;
+        if (t_v(CH, 0, slot) == c.node) {
+          const uint32_t mem = t_v(CH, 1, slot);
+          t_set(c, B, NONE, x, FLD(AL, F_V, slot * na), mem, 1u << mem);
+        } else {
+          t_set(c, B, NONE, x, REMOTE, 0, 0);
+        }
+        if (c.err) return;
       }
     }
-    if (c.err) return;
+    __syncwarp();
     t_merge_from(c, B, from);
+    t_maybe_merge(c, B, 4 * CH.n + 64);
   }
   // the task's push / await regions are consumed
   for (uint32_t base = qs; base < qe; base += 32) {

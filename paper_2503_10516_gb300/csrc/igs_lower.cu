@@ -1433,23 +1433,20 @@ __device__ __noinline__ bool map_ids(Ctx& c, Table& T, uint32_t h, bool writers 
 __device__ __noinline__ void apply_epoch(Ctx& c, uint32_t h) {
   for (uint32_t li = 0; li < c.n_live; ++li) {
     const uint32_t aid = c.nd->live[li];
-    // tables whose ids all stay are left as they are (re-merging is a matter
-    // of table size, not of content)
+    // re-merging (also of pieces that region subtraction left with equal
+    // values) keeps the tables small; it does not change their content
     Table WR = wr_t(c, aid);
-    if (map_ids(c, WR, h, true)) {
-      t_compact(c, WR);
-      t_merge_from(c, WR, 0);
-      t_compact(c, WR);
-      t_set_mark(c, WR);
-    }
+    map_ids(c, WR, h, true);
+    t_compact(c, WR);
+    t_merge_from(c, WR, 0);
+    t_compact(c, WR);
+    t_set_mark(c, WR);
     Table RD = rd_t(c, aid);
-    if (map_ids(c, RD, h)) {
-      t_make_disjoint(c, RD, h);
-      t_compact(c, RD);
-      t_merge_from(c, RD, 0);
-      t_compact(c, RD);
-      t_set_mark(c, RD);
-    }
+    if (map_ids(c, RD, h)) t_make_disjoint(c, RD, h);
+    t_compact(c, RD);
+    t_merge_from(c, RD, 0);
+    t_compact(c, RD);
+    t_set_mark(c, RD);
     if (c.err) return;
   }
   const uint32_t nb = c.nd->cap_buffers;
@@ -1457,7 +1454,7 @@ __device__ __noinline__ void apply_epoch(Ctx& c, uint32_t h) {
     if (c.nd->bst_d[kDesc * b + 1] == 0) continue;  // no table (never created or destroyed)
     Table B = bst_t(c, b);
     if (B.n == 0) continue;
-    if (!map_ids(c, B, h)) continue;
+    map_ids(c, B, h);
     t_compact(c, B);
     t_merge_from(c, B, 0);
     t_compact(c, B);

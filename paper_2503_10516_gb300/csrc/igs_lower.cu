@@ -1098,16 +1098,16 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
   pt_lap(pt, c, PH_EMIT);
   return r;
 }
-__device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint32_t fb, uint32_t fc, uint32_t fd,
-                              const Table* bt, uint32_t bfrom, uint32_t bto, const Acc* acc, int nacc, bool keep_dep,
-                              const Table* bindt, uint32_t bind_from, uint32_t bind_n) {
-  if (c.err) return NONE;
+// Dependencies of the next instruction into S_DEP (after the extra edges
+// already there when keep_dep): per access the last writers (RAW dataflow;
+// WAW anti; a fresh allocation's own alloc instruction: allocation
+// lifetime) and, for writes, the readers since the last write (WAR anti); no
+// predecessor at all means an edge to the last epoch.
+__device__ __noinline__ bool emit_deps(Ctx& c, const Acc* acc, int nacc, bool keep_dep) {
+  if (c.err) return false;
   NodeDev* nd = c.nd;
   Table& D = c.s[S_DEP];
   if (!keep_dep) t_reset(D);
-  const uint32_t id = c.n_instr;
-  DT_START(dt);
-  DT_COUNT(N_EMIT, 1);
   // one probe per (access, region box, table): last writers for every access,
   // readers for writes; every probed entry is tested in a lane-parallel pass.
   // Probes are gathered 32 at a time, probe j in lane j's registers (table
@@ -1182,7 +1182,7 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
         for (int tab = 0; tab < ((A.mode & IGS_WRITE) ? 2 : 1); ++tab) {
           const uint32_t n = tab == 0 ? wn : rn;
           if (n == 0) continue;
-          if (np == 32 && !run_batch()) return NONE;
+          if (np == 32 && !run_batch()) return false;
           if (c.lane == np) {
             my_base = tab == 0 ? wb : rb;
             my_start = total;
@@ -1195,10 +1195,9 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
         }
       }
     }
-    if (np && !run_batch()) return NONE;
+    if (np && !run_batch()) return false;
   }
   __syncwarp();
-  DT_LAP(dt, D_PROBE);
   if (D.n == 0) {
     if (c.lane == 0) {
       FLD(D, F_V, 0) = c.epoch;
@@ -1207,6 +1206,18 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
     D.n = 1;
     __syncwarp();
   }
+  return true;
+}
+
+// The unique predecessors in S_DEP, ascending, kinds OR-ed, as edges into
+// instruction id, written to out[0, count) (at most cap of them, else a
+// capacity failure of kind cap_kind); marks each predecessor as having a
+// successor. Returns the count (NONE on failure).
+__device__ __noinline__ uint32_t emit_edges(Ctx& c, uint32_t id, igs_edge* out, uint32_t cap, CapKind cap_kind,
+                                            uint32_t cap_report) {
+  if (c.err) return NONE;
+  NodeDev* nd = c.nd;
+  const Table& D = c.s[S_DEP];
   // unique predecessors in ascending order, kinds OR-ed
   const uint32_t nd0 = D.n;
   uint32_t n_unique = 0;
@@ -1238,8 +1249,8 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
       }
     }
     n_unique = __popc(__ballot_sync(FULL, lead));
-    if (c.n_edge + n_unique > nd->cap_edge || c.n_instr + 1 > nd->cap_instr) {
-      fail_cap(c, CAP_EDGE, nd->cap_edge);
+    if (n_unique > cap) {
+      fail_cap(c, cap_kind, cap_report);
       return NONE;
     }
     if (c.lane < n_unique) {
@@ -1247,7 +1258,7 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
       e.from = (uint32_t)(key >> 32);
       e.to = id;
       e.kind = (uint32_t)key;
-      nd->edges[c.n_edge + c.lane] = e;
+      out[c.lane] = e;
       nd->has_succ[e.from] = 1;
     }
   } else {
@@ -1265,8 +1276,8 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
       }
       n_unique += __popc(__ballot_sync(FULL, first));
     }
-    if (c.n_edge + n_unique > nd->cap_edge || c.n_instr + 1 > nd->cap_instr) {
-      fail_cap(c, CAP_EDGE, nd->cap_edge);
+    if (n_unique > cap) {
+      fail_cap(c, cap_kind, cap_report);
       return NONE;
     }
     for (uint32_t base = 0; base < nd0; base += 32) {
@@ -1295,14 +1306,29 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
           e.from = p;
           e.to = id;
           e.kind = kind;
-          nd->edges[c.n_edge + rank] = e;
+          out[rank] = e;
           nd->has_succ[p] = 1;
         }
       }
     }
   }
-  c.n_edge += n_unique;
-  DT_LAP(dt, D_DEDUP);
+  __syncwarp();
+  return n_unique;
+}
+
+// The record of instruction c.n_instr with its boxes (bt[bfrom, bto)) and
+// bindings (bindt[bind_from, +bind_n)). clear_succ: mark it as having no
+// successor yet (callers that emitted its successors' edges already pass false).
+__device__ __noinline__ bool emit_record(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint32_t fb, uint32_t fc,
+                                         uint32_t fd, const Table* bt, uint32_t bfrom, uint32_t bto, const Table* bindt,
+                                         uint32_t bind_from, uint32_t bind_n, bool clear_succ) {
+  if (c.err) return false;
+  NodeDev* nd = c.nd;
+  const uint32_t id = c.n_instr;
+  if (c.n_instr + 1 > nd->cap_instr) {
+    fail_cap(c, CAP_EDGE, nd->cap_edge);
+    return false;
+  }
   // instruction record, its boxes and bindings
   uint32_t nb = 0;
   if (bt) {
@@ -1312,7 +1338,7 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
       const uint32_t m = __ballot_sync(FULL, live);
       if (c.n_box + nb + __popc(m) > nd->cap_box) {
         fail_cap(c, CAP_BOX, nd->cap_box);
-        return NONE;
+        return false;
       }
       if (live) {
         const Bx b = t_box(*bt, i);
@@ -1328,7 +1354,7 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
   }
   if (c.n_bind + bind_n > nd->cap_bind) {
     fail_cap(c, CAP_BIND, nd->cap_bind);
-    return NONE;
+    return false;
   }
   if (bindt && c.lane < bind_n) {
     const uint32_t i = bind_from + c.lane;
@@ -1355,13 +1381,19 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
     r.bind_off = c.n_bind;
     r.bind_cnt = bind_n;
     nd->instrs[id] = r;
-    nd->has_succ[id] = 0;
+    if (clear_succ) nd->has_succ[id] = 0;
   }
   c.n_box += nb;
   c.n_bind += bind_n;
   c.n_instr += 1;
   __syncwarp();
-  DT_LAP(dt, D_RECORD);
+  return true;
+}
+
+// Applies an instruction's accesses to the per-allocation tables: reads
+// join the readers, writes replace the writers and clear the readers.
+__device__ __noinline__ bool emit_apply(Ctx& c, const Acc* acc, int nacc, uint32_t id) {
+  if (c.err) return false;
   // apply reads, then writes
   for (int k = 0; k < nacc; ++k) {
     const Acc& A = acc[k];
@@ -1377,7 +1409,7 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
       const Bx q = t_box(*A.t, r);
       if (again) t_subtract(c, RD, NONE, q, id);
       const uint32_t s = t_claim(c, RD, c.lane == 0);
-      if (c.err) return NONE;
+      if (c.err) return false;
       if (c.lane == 0) t_put(RD, s, 0, q, id, 0, 0);
       __syncwarp();
     }
@@ -1398,12 +1430,32 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
       const Bx q = t_box(*A.t, r);
       t_subtract(c, RD, NONE, q);
       t_set(c, WR, NONE, q, id, 0, 0);
-      if (c.err) return NONE;
+      if (c.err) return false;
     }
     t_maybe_merge(c, WR, 48);
     t_maybe_merge(c, RD, 48);
     (void)from;
   }
+  return true;
+}
+
+__device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint32_t fb, uint32_t fc, uint32_t fd,
+                              const Table* bt, uint32_t bfrom, uint32_t bto, const Acc* acc, int nacc, bool keep_dep,
+                              const Table* bindt, uint32_t bind_from, uint32_t bind_n) {
+  if (c.err) return NONE;
+  NodeDev* nd = c.nd;
+  const uint32_t id = c.n_instr;
+  DT_START(dt);
+  DT_COUNT(N_EMIT, 1);
+  if (!emit_deps(c, acc, nacc, keep_dep)) return NONE;
+  DT_LAP(dt, D_PROBE);
+  const uint32_t ne = emit_edges(c, id, nd->edges + c.n_edge, nd->cap_edge - c.n_edge, CAP_EDGE, nd->cap_edge);
+  if (ne == NONE) return NONE;
+  c.n_edge += ne;
+  DT_LAP(dt, D_DEDUP);
+  if (!emit_record(c, type, seq, fa, fb, fc, fd, bt, bfrom, bto, bindt, bind_from, bind_n, true)) return NONE;
+  DT_LAP(dt, D_RECORD);
+  if (!emit_apply(c, acc, nacc, id)) return NONE;
   DT_LAP(dt, D_APPLY);
   return id;
 }
@@ -1433,20 +1485,23 @@ __device__ __noinline__ bool map_ids(Ctx& c, Table& T, uint32_t h, bool writers 
 __device__ __noinline__ void apply_epoch(Ctx& c, uint32_t h) {
   for (uint32_t li = 0; li < c.n_live; ++li) {
     const uint32_t aid = c.nd->live[li];
-    // re-merging (also of pieces that region subtraction left with equal
-    // values) keeps the tables small; it does not change their content
+    // tables whose ids all stay are left as they are; the others are
+    // re-merged (a matter of table size, not of content)
     Table WR = wr_t(c, aid);
-    map_ids(c, WR, h, true);
-    t_compact(c, WR);
-    t_merge_from(c, WR, 0);
-    t_compact(c, WR);
-    t_set_mark(c, WR);
+    if (map_ids(c, WR, h, true)) {
+      t_compact(c, WR);
+      t_merge_from(c, WR, 0);
+      t_compact(c, WR);
+      t_set_mark(c, WR);
+    }
     Table RD = rd_t(c, aid);
-    if (map_ids(c, RD, h)) t_make_disjoint(c, RD, h);
-    t_compact(c, RD);
-    t_merge_from(c, RD, 0);
-    t_compact(c, RD);
-    t_set_mark(c, RD);
+    if (map_ids(c, RD, h)) {
+      t_make_disjoint(c, RD, h);
+      t_compact(c, RD);
+      t_merge_from(c, RD, 0);
+      t_compact(c, RD);
+      t_set_mark(c, RD);
+    }
     if (c.err) return;
   }
   const uint32_t nb = c.nd->cap_buffers;
@@ -1454,7 +1509,7 @@ __device__ __noinline__ void apply_epoch(Ctx& c, uint32_t h) {
     if (c.nd->bst_d[kDesc * b + 1] == 0) continue;  // no table (never created or destroyed)
     Table B = bst_t(c, b);
     if (B.n == 0) continue;
-    map_ids(c, B, h);
+    if (!map_ids(c, B, h)) continue;
     t_compact(c, B);
     t_merge_from(c, B, 0);
     t_compact(c, B);

@@ -86,6 +86,7 @@ struct igs_ctx {
   cudaStream_t cstream = nullptr;  // copies of graph records to the host during pipelined runs
   volatile uint32_t* m_progress = nullptr;  // host-mapped progress records (PR_WORDS per node)
   uint32_t* d_progress = nullptr;
+  uint32_t* d_helpers = nullptr;  // helper warps' scratch of every node (pipelined runs)
   bool pipelined = false;          // a pipelined run is in progress: launches go to xstream
   std::multimap<uint64_t, SendRec> sends;  // (seq, buffer, receiver) -> sends not yet received
   uint64_t exec_call = 0;
@@ -448,6 +449,7 @@ void igs_destroy(igs_ctx* c) {
   }
   if (c->xstream) cudaStreamDestroy(c->xstream);
   if (c->cstream) cudaStreamDestroy(c->cstream);
+  if (c->d_helpers) cudaFree(c->d_helpers);
   if (c->m_progress) cudaFreeHost((void*)c->m_progress);
   for (auto& e : c->ev_pool) {
     cudaEventDestroy(e.first);
@@ -1215,6 +1217,16 @@ extern "C" int igs_run(igs_ctx* c, uint32_t window) {
   }
   int r = download_nodes(c);
   if (r) return r;
+  if (!c->d_helpers && c->D > 1) {
+    // scratch for the helper warps that share each node's kernel phase
+    const size_t per = (size_t)(kMaxWorkers - 1) * 3 * c->nodes_host[0].cap_scratch * F_COUNT;
+    CK(cudaMalloc((void**)&c->d_helpers, sizeof(uint32_t) * per * c->N));
+    for (uint32_t n = 0; n < c->N; ++n) {
+      uint32_t* p = c->d_helpers + per * n;
+      CK(cudaMemcpy(&c->d_nodes[n].helper_scratch, &p, sizeof p, cudaMemcpyHostToDevice));
+      c->nodes_host[n].helper_scratch = p;
+    }
+  }
   for (uint32_t n = 0; n < c->N; ++n) {
     const NodeDev& nd = c->nodes_host[n];
     volatile uint32_t* pr = c->m_progress + (size_t)n * PR_WORDS;

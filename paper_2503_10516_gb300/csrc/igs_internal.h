@@ -43,6 +43,9 @@ struct Table {
   uint32_t* dp;    // heap table descriptor {offset, cap, n, live, merge mark}; nullptr for scratch tables
 };
 
+// Warps that share a node's kernel phase (warp 0 and up to 7 helpers).
+constexpr uint32_t kMaxWorkers = 8;
+
 // Size classes of the per-node entry heap: 32 << k entries.
 constexpr int kHeapClasses = 24;
 // Words per heap-table descriptor: {offset, cap, n, live, merge mark, 3 spare}.
@@ -96,6 +99,9 @@ struct NodeDev {
   uint32_t* rejected;
   // scratch tables for the warp
   uint32_t* scratch_base;  // 14 tables of cap_scratch entries
+  // scratch of the helper warps that share the kernel phase when a node is
+  // lowered by several warps (3 tables of cap_scratch entries per helper), or null
+  uint32_t* helper_scratch;
 };
 
 // Program-level inputs shared by all node warps of one context.

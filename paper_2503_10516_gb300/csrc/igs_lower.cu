@@ -169,6 +169,9 @@ struct Ctx {
   Table qr;
   Table s[14];
   uint64_t map_reads, map_writes;
+  int* lock;  // block's heap lock (shared memory) when several warps of the block lower, else null
+  void* block;       // the block's shared control (BlockShared) when it has helper warps, else null
+  uint32_t workers;  // warps sharing the kernel phase (1 = warp 0 alone)
 };
 
 __device__ __forceinline__ void fail(Ctx& c, uint32_t code) {
@@ -231,37 +234,80 @@ __device__ __forceinline__ int heap_class(uint32_t entries) {
 }
 
 // A slab of at least `entries` entries (uniform); NONE when the heap is full.
+// With several warps lowering one node, the heap (free lists and top, then
+// kept in NodeDev) is shared: a warp takes the block's lock around every heap
+// operation. The wait is bounded; a lock not obtained fails the node.
+__device__ bool heap_lock(Ctx& c) {
+  if (!c.lock) return true;
+  uint32_t ok = 1;
+  if (c.lane == 0) {
+    uint32_t spins = 0;
+    while (atomicCAS(c.lock, 0, 1) != 0) {
+      if (++spins > (1u << 20)) {
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence_block();
+  }
+  ok = __shfl_sync(FULL, ok, 0);
+  if (!ok) fail(c, ST_TIMEOUT);
+  return ok != 0;
+}
+__device__ void heap_unlock(Ctx& c) {
+  if (!c.lock) return;
+  __syncwarp();
+  if (c.lane == 0) {
+    __threadfence_block();
+    atomicExch(c.lock, 0);
+  }
+  __syncwarp();
+}
+
 __device__ __noinline__ uint32_t heap_alloc(Ctx& c, uint32_t entries, uint32_t& cap) {
   const int k = heap_class(entries);
   cap = 32u << k;
   NodeDev* nd = c.nd;
+  if (!heap_lock(c)) return NONE;
+  volatile uint32_t* fh = nd->free_head;
   __syncwarp();
-  const uint32_t head = nd->free_head[k];
+  const uint32_t head = fh[k];
   if (head != NONE) {
-    const uint32_t next = nd->heap[(size_t)head * F_COUNT];
+    const uint32_t next = reinterpret_cast<volatile uint32_t*>(nd->heap)[(size_t)head * F_COUNT];
     __syncwarp();
-    if (c.lane == 0) nd->free_head[k] = next;
-    __syncwarp();
+    if (c.lane == 0) fh[k] = next;
+    heap_unlock(c);
     return head;
   }
-  if ((uint64_t)c.heap_top + cap > nd->cap_heap) {
+  volatile uint32_t* vtop = &nd->heap_top;
+  const uint32_t top = c.lock ? *vtop : c.heap_top;
+  if ((uint64_t)top + cap > nd->cap_heap) {
+    heap_unlock(c);
     fail_cap(c, CAP_HEAP, nd->cap_heap);
     return NONE;
   }
-  const uint32_t off = c.heap_top;
-  c.heap_top += cap;
-  return off;
+  if (c.lock) {
+    __syncwarp();
+    if (c.lane == 0) *vtop = top + cap;
+  } else {
+    c.heap_top = top + cap;
+  }
+  heap_unlock(c);
+  return top;
 }
 
 __device__ void heap_free(Ctx& c, uint32_t off, uint32_t cap) {
   const int k = heap_class(cap);
   NodeDev* nd = c.nd;
+  if (!heap_lock(c)) return;
+  volatile uint32_t* fh = nd->free_head;
   __syncwarp();
   if (c.lane == 0) {
-    nd->heap[(size_t)off * F_COUNT] = nd->free_head[k];
-    nd->free_head[k] = off;
+    reinterpret_cast<volatile uint32_t*>(nd->heap)[(size_t)off * F_COUNT] = fh[k];
+    fh[k] = off;
   }
-  __syncwarp();
+  heap_unlock(c);
 }
 
 __device__ __forceinline__ void t_publish(Ctx& c, Table& t) {
@@ -2113,6 +2159,195 @@ __device__ __noinline__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq
   }
 }
 
+// ---- kernel phase shared by several warps ----------------------------------
+
+// Kernels of different devices touch disjoint allocation tables and depend on
+// nothing the others emit in the same phase; their ids are known in advance
+// (one per local chunk, in chunk order). So each worker warp takes the chunks
+// of the devices d with d mod workers == its index: their dependencies (edges
+// staged per worker) and their table updates. Warp 0 then writes edges,
+// boxes, bindings and records in chunk order, exactly as the single-warp path.
+enum BlockCmd : uint32_t { CMD_NONE = 0, CMD_P5 = 1, CMD_EXIT = 2 };
+__device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg);
+
+struct P5Job {
+  NodeDev* nd;
+  const ProgDev* pg;
+  const igs_task* task;
+  Table CH, MP, AL;  // warp 0's tables; AL[slot * na] v0 = kernel id, v1/v2 = staged edges
+  uint32_t na, epoch, node, workers, stage_cap;
+  igs_edge* stage0;  // worker 0's staged edges (warp 0's scratch)
+};
+
+struct BlockShared {
+  int lock;
+  volatile uint32_t cmd, err, err_info;
+  P5Job job;
+};
+
+__device__ __forceinline__ void worker_bar(uint32_t workers) {
+  asm volatile("bar.sync 1, %0;" ::"r"(workers * 32) : "memory");
+}
+
+__device__ __forceinline__ uint32_t* helper_table(const NodeDev* nd, uint32_t w, uint32_t k) {
+  return nd->helper_scratch + ((size_t)(w - 1) * 3 + k) * nd->cap_scratch * F_COUNT;
+}
+
+__device__ __forceinline__ igs_edge* stage_of(const P5Job& j, uint32_t w) {
+  return w == 0 ? j.stage0 : reinterpret_cast<igs_edge*>(helper_table(j.nd, w, 2));
+}
+
+// The kernel's bindings / accesses of local chunk `slot` into BT and acc.
+__device__ bool p5_accesses(Ctx& c, const igs_task& t, const Table& MP, const Table& AL, uint32_t slot, uint32_t na,
+                            Table& BT, Acc* acc, int& nacc) {
+  t_reset(BT);
+  nacc = 0;
+  for (uint32_t a = 0; a < na; ++a) {
+    const Bx x = t_box(MP, slot * na + a);
+    const uint32_t al = FLD(AL, F_KEY, slot * na + a);
+    if (al == NONE - 1) {
+      fail(c, ST_INTERNAL);
+      return false;
+    }
+    if (c.lane == 0) {
+      Bx z{};
+      t_put(BT, a, 0, bx_empty(x) ? z : x, al, 0, 0);
+    }
+    if (al != NONE) acc[nacc++] = Acc{&BT, a, a + 1, al, t.acc[a].mode};
+  }
+  BT.n = na;
+  __syncwarp();
+  return true;
+}
+
+__device__ __noinline__ void p5_share(Ctx& c, const P5Job& j, uint32_t w) {
+  const Table& CH = j.CH;
+  const Table& MP = j.MP;
+  const Table& AL = j.AL;
+  const uint32_t na = j.na;
+  Table& BT = c.s[S_T4];
+  igs_edge* stage = stage_of(j, w);
+  uint32_t off = 0;
+  for (uint32_t slot = 0; slot < CH.n && !c.err; ++slot) {
+    if (t_v(CH, 0, slot) != j.node) continue;
+    const uint32_t mem = t_v(CH, 1, slot);
+    if ((mem - 2) % j.workers != w) continue;
+    const uint32_t kid = FLD(AL, F_V, slot * na);
+    __syncwarp();
+    if (c.lane == 0) c.nd->has_succ[kid] = 0;  // before a later kernel of this worker marks it
+    Acc acc[IGS_MAX_ACCESSORS];
+    int nacc = 0;
+    if (!p5_accesses(c, *j.task, MP, AL, slot, na, BT, acc, nacc)) break;
+    if (!emit_deps(c, acc, nacc, false)) break;
+    const uint32_t ne = emit_edges(c, kid, stage + off, j.stage_cap - off, CAP_TABLE, j.stage_cap);
+    if (ne == NONE) break;
+    __syncwarp();
+    if (c.lane == 0) {
+      FLD(AL, F_V + 1, slot * na) = off;
+      FLD(AL, F_V + 2, slot * na) = ne;
+    }
+    off += ne;
+    if (!emit_apply(c, acc, nacc, kid)) break;
+  }
+  __syncwarp();
+}
+
+// Helper warp w: waits for work from warp 0, does its share, reports.
+__device__ void helper_loop(BlockShared& sh, uint32_t w, uint32_t workers) {
+  for (;;) {
+    worker_bar(workers);
+    const uint32_t cmd = sh.cmd;
+    if (cmd == CMD_EXIT) break;
+    if (cmd == CMD_P5) {
+      const P5Job& j = sh.job;
+      Ctx hc;
+      load_ctx(hc, j.nd, j.pg);
+      hc.err = ST_OK;
+      hc.epoch = j.epoch;
+      hc.node = j.node;
+      hc.lock = &sh.lock;
+      hc.s[S_DEP].base = helper_table(j.nd, w, 0);
+      hc.s[S_T4].base = helper_table(j.nd, w, 1);
+      p5_share(hc, j, w);
+      if (hc.lane == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&j.nd->map_reads), (unsigned long long)hc.map_reads);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&j.nd->map_writes), (unsigned long long)hc.map_writes);
+        if (hc.err != ST_OK) {
+          sh.err_info = hc.err_info;
+          sh.err = hc.err;
+        }
+      }
+      __syncwarp();
+    }
+    worker_bar(workers);
+  }
+}
+
+// Warp 0: the kernel phase with the helpers, then the records in chunk order.
+__device__ __noinline__ void p5_parallel(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP,
+                                         Table& AL, uint32_t na) {
+  BlockShared& sh = *static_cast<BlockShared*>(c.block);
+  uint32_t next = c.n_instr;
+  for (uint32_t slot = 0; slot < CH.n; ++slot) {
+    if (t_v(CH, 0, slot) != c.node) continue;
+    if (c.lane == 0) FLD(AL, F_V, slot * na) = next;
+    ++next;
+  }
+  __syncwarp();
+  if (c.lane == 0) {
+    P5Job& j = sh.job;
+    j.nd = c.nd;
+    j.pg = c.pg;
+    j.task = &t;
+    j.CH = CH;
+    j.MP = MP;
+    j.AL = AL;
+    j.na = na;
+    j.epoch = c.epoch;
+    j.node = c.node;
+    j.workers = c.workers;
+    j.stage_cap = c.nd->cap_scratch * (F_COUNT * 4 / (uint32_t)sizeof(igs_edge));
+    j.stage0 = reinterpret_cast<igs_edge*>(c.s[S_T0].base);
+    sh.err = ST_OK;
+    sh.cmd = CMD_P5;
+    __threadfence_block();
+  }
+  __syncwarp();
+  worker_bar(c.workers);  // helpers start
+  p5_share(c, sh.job, 0);
+  worker_bar(c.workers);  // every share done
+  if (sh.err != ST_OK && c.err == ST_OK) {
+    c.err = sh.err;
+    c.err_info = sh.err_info;
+  }
+  if (c.err) return;
+  const P5Job& j = sh.job;
+  Table& BT = c.s[S_T4];
+  NodeDev* nd = c.nd;
+  for (uint32_t slot = 0; slot < CH.n; ++slot) {
+    if (t_v(CH, 0, slot) != c.node) continue;
+    const uint32_t mem = t_v(CH, 1, slot);
+    const uint32_t kid = FLD(AL, F_V, slot * na), off = FLD(AL, F_V + 1, slot * na), ne = FLD(AL, F_V + 2, slot * na);
+    if (kid != c.n_instr) {
+      fail(c, ST_INTERNAL);
+      return;
+    }
+    if (c.n_edge + ne > nd->cap_edge) {
+      fail_cap(c, CAP_EDGE, nd->cap_edge);
+      return;
+    }
+    const igs_edge* stage = stage_of(j, (mem - 2) % j.workers);
+    for (uint32_t i = c.lane; i < ne; i += 32) nd->edges[c.n_edge + i] = stage[off + i];
+    c.n_edge += ne;
+    Acc acc[IGS_MAX_ACCESSORS];
+    int nacc = 0;
+    if (!p5_accesses(c, t, MP, AL, slot, na, BT, acc, nacc)) return;
+    if (!emit_record(c, IGS_KERNEL, seq, t_key(CH, slot), mem, t.kernel_id, NONE, &CH, slot, slot + 1, &BT, 0, na,
+                     false))
+      return;
+  }
+}
+
 // ---- compile one task (P1..P5) ----------------------------------------------
 
 __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
@@ -2455,33 +2690,23 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     AL.n = total;
     __syncwarp();
   }
-  for (uint32_t slot = 0; slot < CH.n; ++slot) {
-    if (t_v(CH, 0, slot) != c.node) continue;
-    const uint32_t mem = t_v(CH, 1, slot);
-    t_reset(BT);
-    Acc acc[IGS_MAX_ACCESSORS];
-    int nacc = 0;
-    for (uint32_t a = 0; a < na; ++a) {
-      const Bx x = t_box(MP, slot * na + a);
-      const uint32_t al = FLD(AL, F_KEY, slot * na + a);
-      if (al == NONE - 1) {
-        fail(c, ST_INTERNAL);
-        return;
-      }
-      if (c.lane == 0) {
-        Bx z{};
-        t_put(BT, a, 0, bx_empty(x) ? z : x, al, 0, 0);
-      }
-      if (al != NONE) acc[nacc++] = Acc{&BT, a, a + 1, al, t.acc[a].mode};
-    }
-    BT.n = na;
-    __syncwarp();
-    const uint32_t kid = emit(c, IGS_KERNEL, seq, t_key(CH, slot), mem, t.kernel_id, NONE, &CH, slot, slot + 1, acc,
-                              nacc, false, &BT, 0, na);
+  if (c.block && c.workers > 1 && c.nd->helper_scratch) {
+    p5_parallel(c, t, seq, CH, MP, AL, na);
     if (c.err) return;
-    __syncwarp();
-    if (c.lane == 0) FLD(AL, F_V, slot * na) = kid;  // the chunk's kernel, for the buffer state below
-    __syncwarp();
+  } else {
+    for (uint32_t slot = 0; slot < CH.n; ++slot) {
+      if (t_v(CH, 0, slot) != c.node) continue;
+      const uint32_t mem = t_v(CH, 1, slot);
+      Acc acc[IGS_MAX_ACCESSORS];
+      int nacc = 0;
+      if (!p5_accesses(c, t, MP, AL, slot, na, BT, acc, nacc)) return;
+      const uint32_t kid = emit(c, IGS_KERNEL, seq, t_key(CH, slot), mem, t.kernel_id, NONE, &CH, slot, slot + 1, acc,
+                                nacc, false, &BT, 0, na);
+      if (c.err) return;
+      __syncwarp();
+      if (c.lane == 0) FLD(AL, F_V, slot * na) = kid;  // the chunk's kernel, for the buffer state below
+      __syncwarp();
+    }
   }
   pt_lap(pt, c, PH_P5);
   // buffer state of every written region: a local chunk's kernel is its
@@ -2791,6 +3016,9 @@ __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg) {
   }
   c.map_reads = 0;
   c.map_writes = 0;
+  c.lock = nullptr;
+  c.block = nullptr;
+  c.workers = 1;
 }
 
 __device__ void store_ctx(Ctx& c, uint32_t cursor) {
@@ -2807,7 +3035,7 @@ __device__ void store_ctx(Ctx& c, uint32_t cursor) {
   nd->n_alloc = c.n_alloc;
   nd->n_free = c.n_free;
   nd->n_live = c.n_live;
-  nd->heap_top = c.heap_top;
+  if (!c.lock) nd->heap_top = c.heap_top;  // with a lock, NodeDev holds the top throughout
   nd->n_instr = c.n_instr;
   nd->n_edge = c.n_edge;
   nd->n_box = c.n_box;
@@ -2843,11 +3071,16 @@ __device__ __noinline__ void publish_progress(const Ctx& c, volatile uint32_t* p
 }
 
 __device__ void lower_unit(const Unit* units, uint32_t n_units, uint32_t max_items, uint32_t w,
-                           volatile uint32_t* progress) {
+                           volatile uint32_t* progress, BlockShared* sh, uint32_t workers) {
   if (w >= n_units) return;
   const Unit u = units[w];
   Ctx c;
   load_ctx(c, u.node, u.prog);
+  if (sh) {
+    c.lock = &sh->lock;
+    c.block = sh;
+    c.workers = workers;
+  }
   uint32_t cursor = u.node->cursor;
   const uint32_t avail = *u.prog->n_items;
   uint32_t end = avail;
@@ -2871,7 +3104,28 @@ __device__ void lower_unit(const Unit* units, uint32_t n_units, uint32_t max_ite
 constexpr uint32_t kReserveThreads = 640;
 __global__ void __launch_bounds__(kReserveThreads) lower_kernel(const Unit* units, uint32_t n_units, uint32_t max_items,
                                                                volatile uint32_t* progress) {
-  if (threadIdx.x < 32) lower_unit(units, n_units, max_items, blockIdx.x, progress);
+  __shared__ BlockShared sh;
+  const uint32_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t workers = nw < kMaxWorkers ? nw : kMaxWorkers;
+  if (threadIdx.x == 0) {
+    sh.lock = 0;
+    sh.cmd = CMD_NONE;
+    sh.err = ST_OK;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    lower_unit(units, n_units, max_items, blockIdx.x, progress, workers > 1 ? &sh : nullptr, workers);
+    if (workers > 1) {
+      if ((threadIdx.x & 31u) == 0) {
+        sh.cmd = CMD_EXIT;
+        __threadfence_block();
+      }
+      __syncwarp();
+      worker_bar(workers);  // the helpers leave their loop
+    }
+  } else if (warp < workers) {
+    helper_loop(sh, warp, workers);
+  }
   __syncthreads();
 }
 

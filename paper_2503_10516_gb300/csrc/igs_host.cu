@@ -222,12 +222,31 @@ void ev_collect(igs_ctx* c) {
   c->ev_used = 0;
 }
 
+// Scratch for the helper warps that share each node's kernel phase (nodes
+// with more than one device only).
+int ensure_helpers(igs_ctx* c) {
+  if (c->d_helpers || c->D < 2) return IGS_OK;
+  const size_t per = (size_t)(kMaxWorkers - 1) * 3 * c->nodes_host[0].cap_scratch * F_COUNT;
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMalloc((void**)&c->d_helpers, sizeof(uint32_t) * per * c->N));
+  for (uint32_t n = 0; n < c->N; ++n) {
+    uint32_t* p = c->d_helpers + per * n;
+    CK(cudaMemcpy(&c->d_nodes[n].helper_scratch, &p, sizeof p, cudaMemcpyHostToDevice));
+    c->nodes_host[n].helper_scratch = p;
+  }
+  return IGS_OK;
+}
+
 int launch_lower(igs_ctx* c, uint32_t max_items = IGS_NONE, bool reserve = false, uint32_t* progress = nullptr) {
   if (c->server) return IGS_OK;  // the serving loop lowers it
   int r = upload_prog(c);
   if (r) return r;
+  // one task per launch: the launch is the latency, so helper warps share
+  // each node's kernel phase
+  const bool workers = c->cfg.mode == IGS_MODE_PLAIN && c->D > 1;
+  if (workers && (r = ensure_helpers(c))) return r;
   const size_t ev = c->timing ? ev_begin(c) : 0;
-  if (igs_launch_lower(c->d_units, c->N, max_items, c->stream, reserve, progress))
+  if (igs_launch_lower(c->d_units, c->N, max_items, c->stream, reserve, progress, workers))
     return fail_ctx(c, IGS_ERR_CUDA, "lowering launch failed");
   if (c->timing) ev_end(c, 0, ev);
   c->launches++;
@@ -1217,16 +1236,7 @@ extern "C" int igs_run(igs_ctx* c, uint32_t window) {
   }
   int r = download_nodes(c);
   if (r) return r;
-  if (!c->d_helpers && c->D > 1) {
-    // scratch for the helper warps that share each node's kernel phase
-    const size_t per = (size_t)(kMaxWorkers - 1) * 3 * c->nodes_host[0].cap_scratch * F_COUNT;
-    CK(cudaMalloc((void**)&c->d_helpers, sizeof(uint32_t) * per * c->N));
-    for (uint32_t n = 0; n < c->N; ++n) {
-      uint32_t* p = c->d_helpers + per * n;
-      CK(cudaMemcpy(&c->d_nodes[n].helper_scratch, &p, sizeof p, cudaMemcpyHostToDevice));
-      c->nodes_host[n].helper_scratch = p;
-    }
-  }
+  if ((r = ensure_helpers(c))) return r;
   for (uint32_t n = 0; n < c->N; ++n) {
     const NodeDev& nd = c->nodes_host[n];
     volatile uint32_t* pr = c->m_progress + (size_t)n * PR_WORDS;

@@ -154,8 +154,10 @@ struct CopyJob {
 // other kernels off the SMs that lower (used while the executor runs concurrently).
 // progress (host-mapped, PR_WORDS per unit, or null): each unit publishes its
 // cursor and output counts after every submission it lowers.
+// workers: blocks of kMaxWorkers warps, so that helper warps share each
+// node's kernel phase (when the node has helper scratch).
 int igs_launch_lower(const igs::Unit* units_dev, uint32_t n_units, uint32_t max_items, void* stream,
-                     bool reserve = false, volatile uint32_t* progress = nullptr);
+                     bool reserve = false, volatile uint32_t* progress = nullptr, bool workers = false);
 // Persistent serving loop over n_slots slots; exits when *stop is set or a
 // warp stays idle for idle_polls polls (about 2 us each).
 int igs_launch_serve(igs::ServeSlot* slots, uint32_t n_slots, volatile uint32_t* stop, uint64_t idle_polls, void* stream);

@@ -3244,7 +3244,7 @@ int igs_launch_serve(igs::ServeSlot* slots, uint32_t n_slots, volatile uint32_t*
 }
 
 int igs_launch_lower(const igs::Unit* units_dev, uint32_t n_units, uint32_t max_items, void* stream, bool reserve,
-                     volatile uint32_t* progress) {
+                     volatile uint32_t* progress, bool workers) {
   if (n_units == 0) return 0;
   // one unit per block, so that units spread over the SMs (each node's
   // tables then share an L1 with as few other units as possible)
@@ -3253,7 +3253,7 @@ int igs_launch_lower(const igs::Unit* units_dev, uint32_t n_units, uint32_t max_
     cudaFuncSetAttribute(igs::lower_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     carveout = true;
   }
-  const uint32_t threads = reserve ? igs::kReserveThreads : 32;
+  const uint32_t threads = reserve ? igs::kReserveThreads : (workers ? 32 * igs::kMaxWorkers : 32);
   igs::lower_kernel<<<n_units, threads, 0, (cudaStream_t)stream>>>(units_dev, n_units, max_items, progress);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

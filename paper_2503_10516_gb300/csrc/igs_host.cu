@@ -226,7 +226,7 @@ void ev_collect(igs_ctx* c) {
 // with more than one device only).
 int ensure_helpers(igs_ctx* c) {
   if (c->d_helpers || c->D < 2) return IGS_OK;
-  const size_t per = (size_t)(kMaxWorkers - 1) * 3 * c->nodes_host[0].cap_scratch * F_COUNT;
+  const size_t per = (size_t)(kMaxWorkers - 1) * kHelperTables * c->nodes_host[0].cap_scratch * F_COUNT;
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaMalloc((void**)&c->d_helpers, sizeof(uint32_t) * per * c->N));
   for (uint32_t n = 0; n < c->N; ++n) {
@@ -277,7 +277,9 @@ int check_status(igs_ctx* c) {
                                                std::to_string(nd.err_info & 0xFFFFFFu));
     }
     if (nd.status == ST_TIMEOUT) return fail_ctx(c, IGS_ERR_TIMEOUT, "device wait timed out");
-    if (nd.status != ST_OK) return fail_ctx(c, IGS_ERR_CUDA, "lowering engine internal error on node " + std::to_string(n));
+    if (nd.status != ST_OK)
+      return fail_ctx(c, IGS_ERR_CUDA, "lowering engine internal error on node " + std::to_string(n) + " (status " +
+                                           std::to_string(nd.status) + ", check " + std::to_string(nd.err_info) + ")");
   }
   if (c->nodes_host[0].n_rej) return fail_ctx(c, IGS_ERR_OVERLAPPING_WRITE, "a task with overlapping writes was rejected");
   return IGS_OK;

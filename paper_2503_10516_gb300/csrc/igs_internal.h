@@ -43,8 +43,10 @@ struct Table {
   uint32_t* dp;    // heap table descriptor {offset, cap, n, live, merge mark}; nullptr for scratch tables
 };
 
-// Warps that share a node's kernel phase (warp 0 and up to 7 helpers).
+// Warps that share parts of a node's lowering (warp 0 and up to 7 helpers),
+// and the scratch tables of each helper.
 constexpr uint32_t kMaxWorkers = 8;
+constexpr uint32_t kHelperTables = 6;
 
 // Size classes of the per-node entry heap: 32 << k entries.
 constexpr int kHeapClasses = 24;
@@ -99,8 +101,8 @@ struct NodeDev {
   uint32_t* rejected;
   // scratch tables for the warp
   uint32_t* scratch_base;  // 14 tables of cap_scratch entries
-  // scratch of the helper warps that share the kernel phase when a node is
-  // lowered by several warps (3 tables of cap_scratch entries per helper), or null
+  // scratch of the helper warps that share parts of the lowering when a node
+  // is lowered by several warps (kHelperTables of cap_scratch entries each), or null
   uint32_t* helper_scratch;
 };
 

@@ -177,6 +177,13 @@ struct Ctx {
 __device__ __forceinline__ void fail(Ctx& c, uint32_t code) {
   if (c.err == ST_OK) c.err = code;
 }
+// An internal failure records which check failed (err_info = site).
+__device__ __forceinline__ void fail_internal(Ctx& c, uint32_t site) {
+  if (c.err == ST_OK) {
+    c.err = ST_INTERNAL;
+    c.err_info = site;
+  }
+}
 // A capacity failure records what ran out and its capacity for the host.
 __device__ __forceinline__ void fail_cap(Ctx& c, CapKind what, uint32_t cap) {
   if (c.err == ST_OK) {
@@ -758,7 +765,7 @@ __device__ __noinline__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_
       const int md = 2 - phase;  // dimension merged in this phase
       for (uint32_t guard = 0;; ++guard) {
         if (guard > 64u * W.cap) {  // every round merges or splits: unreachable for valid input
-          fail(c, ST_INTERNAL);
+          fail_internal(c, 1);
           return 0;
         }
         const uint32_t n = W.n;  // compacted: every entry is live
@@ -1629,7 +1636,7 @@ __device__ __noinline__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_
     last = best;
     const uint32_t prod = (uint32_t)(best >> 32), pmem = (uint32_t)best;
     if (prod == REMOTE) {
-      fail(c, ST_INTERNAL);
+      fail_internal(c, 2);
       return;
     }
     t_reset(G);
@@ -1735,143 +1742,273 @@ __device__ __forceinline__ bool union_is_image(const igs_accessor& a, const BufD
   return k <= 1;
 }
 
+// ---- several warps per node ---------------------------------------------------
+
+// Warp 0 of a block lowers its node; in blocks with helper warps, phases whose
+// parts touch disjoint tables and emit nothing whose id depends on another
+// part are shared: warp 0 posts a job, every worker does its share, warp 0
+// then appends the parts' results in the order of the single-warp path.
+enum BlockCmd : uint32_t { CMD_NONE = 0, CMD_P5 = 1, CMD_A3 = 2, CMD_EXIT = 3 };
+__device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg);
+
+struct WorkJob {
+  NodeDev* nd;
+  const ProgDev* pg;
+  const igs_task* task;
+  Table CH, MP, AL, NB;  // warp 0's tables (AL[slot * na]: v0 kernel id, v1/v2 staged edges)
+  uint32_t na, epoch, node, workers, stage_cap, seq;
+  igs_edge* stage0;  // worker 0's staged edges (warp 0's scratch)
+  Table out0;        // worker 0's staged push / await entries (warp 0's scratch)
+  uint32_t nbuf;     // push / await: buffers in ascending order, their staged entries
+  uint32_t buf[IGS_MAX_ACCESSORS], buf_off[IGS_MAX_ACCESSORS], buf_cnt[IGS_MAX_ACCESSORS];
+};
+
+struct BlockShared {
+  int lock;
+  volatile uint32_t cmd, err, err_info;
+  WorkJob job;
+};
+
+__device__ __forceinline__ void worker_bar(uint32_t workers) {
+  asm volatile("bar.sync 1, %0;" ::"r"(workers * 32) : "memory");
+}
+
+// Helper w's scratch table k (kHelperTables per helper).
+__device__ __forceinline__ uint32_t* helper_table(const NodeDev* nd, uint32_t w, uint32_t k) {
+  return nd->helper_scratch + ((size_t)(w - 1) * kHelperTables + k) * nd->cap_scratch * F_COUNT;
+}
+
+__device__ __forceinline__ igs_edge* stage_of(const WorkJob& j, uint32_t w) {
+  return w == 0 ? j.stage0 : reinterpret_cast<igs_edge*>(helper_table(j.nd, w, 2));
+}
+
+__device__ __forceinline__ Table scratch_table(uint32_t* base, uint32_t cap) {
+  Table t;
+  t.base = base;
+  t.n = 0;
+  t.cap = cap;
+  t.live = 0;
+  t.dp = nullptr;
+  return t;
+}
+
+// Posts a job (lane 0 has filled sh.job) and runs warp 0's share between the
+// start and end barriers; returns false on a failure of any worker.
+template <class F>
+__device__ bool run_shared(Ctx& c, BlockShared& sh, uint32_t cmd, F share0) {
+  __syncwarp();
+  if (c.lane == 0) {
+    sh.err = ST_OK;
+    sh.cmd = cmd;
+    __threadfence_block();
+  }
+  __syncwarp();
+  worker_bar(c.workers);  // helpers start
+  share0();
+  worker_bar(c.workers);  // every share done
+  if (sh.err != ST_OK && c.err == ST_OK) {
+    c.err = sh.err;
+    c.err_info = sh.err_info;
+  }
+  return c.err == ST_OK;
+}
+
 // Per buffer: missing_m = reads of node m's chunks not replicated on m; this
 // node awaits missing_node and pushes missing_m n owned(node) to every m.
 // Results go to the QR table under key seq: v0 = 0 push boxes, 1 await boxes,
 // 2 push bbox, 3 await bbox; v1 = buffer; v2 = target node.
-__device__ __noinline__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP) {
+// Push / await of one buffer b; the QR entries go to OUT.
+__device__ __noinline__ void a3_buffer(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP,
+                                       const Table& NB, uint32_t b, Table& OUT) {
   const uint32_t na = t.num_accessors;
   Table& TMP = c.s[S_T0];
   Table& MISS = c.s[S_T1];
   Table& PT = c.s[S_T2];
   Table& CN = c.s[S_T3];
+  t_reset(MISS);
+  const BufDesc& bd = buf_of(c, b);
+  for (uint32_t m = 0; m < c.N; ++m) {
+    t_reset(TMP);
+    if (t_key(NB, m) == DEAD) continue;
+    const Table O = own_t(c, b);
+    auto lacking = [m](uint32_t, uint32_t repl, uint32_t) { return !((repl >> m) & 1u); };
+    for (uint32_t a = 0; a < na; ++a) {
+      if (t.acc[a].buffer != b || !(t.acc[a].mode & IGS_READ)) continue;
+      if (union_is_image(t.acc[a], bd)) {
+        const Bx x = map_box(t.acc[a], t_box(NB, m), bd);
+        if (!bx_empty(x)) t_query(c, O, NONE, x, TMP, lacking);
+      } else {
+        for (uint32_t slot = 0; slot < CH.n; ++slot) {
+          if (t_v(CH, 0, slot) != m) continue;
+          const Bx x = t_box(MP, slot * na + a);
+          if (!bx_empty(x)) t_query(c, O, NONE, x, TMP, lacking);
+        }
+      }
+      if (c.err) return;
+    }
+    t_make_disjoint(c, TMP);
+    if (c.err) return;
+    for (uint32_t base = 0; base < TMP.n; base += 32) {
+      const uint32_t i = base + c.lane;
+      const bool live = i < TMP.n && t_key(TMP, i) != DEAD;
+      const uint32_t s = t_claim(c, MISS, live);
+      if (c.err) return;
+      if (live) t_put(MISS, s, 0, t_box(TMP, i), m, 0, 0);
+    }
+    __syncwarp();
+  }
+  // this node's await (canonical) and bbox
+  {
+    Table& sel = TMP;
+    t_reset(sel);
+    for (uint32_t base = 0; base < MISS.n; base += 32) {
+      const uint32_t i = base + c.lane;
+      const bool hit = i < MISS.n && t_v(MISS, 0, i) == c.node;
+      const uint32_t s = t_claim(c, sel, hit);
+      if (c.err) return;
+      if (hit) t_put(sel, s, 0, t_box(MISS, i), 0, 0, 0);
+    }
+    __syncwarp();
+    if (sel.n) {
+      t_reset(CN);
+      canonical(c, sel, 0, sel.n, CN);
+      if (c.err) return;
+      const Bx bb = t_bbox(c, CN, 0, CN.n);
+      for (uint32_t base = 0; base < CN.n + 1; base += 32) {
+        const uint32_t i = base + c.lane;
+        const bool in = i < CN.n + 1;
+        const uint32_t s = t_claim(c, OUT, in);
+        if (c.err) return;
+        if (in) {
+          if (i < CN.n) t_put(OUT, s, seq, t_box(CN, i), 1, b, NONE);
+          else t_put(OUT, s, seq, bb, 3, b, NONE);
+        }
+      }
+      __syncwarp();
+    }
+  }
+  // this node's pushes to every other node
+  for (uint32_t m = 0; m < c.N; ++m) {
+    if (m == c.node) continue;
+    t_reset(PT);
+    for (uint32_t i = 0; i < MISS.n; ++i) {
+      if (t_v(MISS, 0, i) != m) continue;
+      const uint32_t me = c.node;
+      t_query(c, own_t(c, b), NONE, t_box(MISS, i), PT, [me](uint32_t owner, uint32_t, uint32_t) { return owner == me; });
+      if (c.err) return;
+    }
+    if (PT.n == 0) continue;
+    t_reset(CN);
+    canonical(c, PT, 0, PT.n, CN);
+    if (c.err) return;
+    const Bx bb = t_bbox(c, CN, 0, CN.n);
+    for (uint32_t base = 0; base < CN.n + 1; base += 32) {
+      const uint32_t i = base + c.lane;
+      const bool in = i < CN.n + 1;
+      const uint32_t s = t_claim(c, OUT, in);
+      if (c.err) return;
+      if (in) {
+        if (i < CN.n) t_put(OUT, s, seq, t_box(CN, i), 0, b, m);
+        else t_put(OUT, s, seq, bb, 2, b, m);
+      }
+    }
+    __syncwarp();
+  }
+  // replication: every node now holds what it awaited
+  Table O = own_t(c, b);
+  t_tidy(c, O);
+  const uint32_t from = O.n;
+  for (uint32_t i = 0; i < MISS.n; ++i) {
+    t_or(c, O, NONE, t_box(MISS, i), 1, 1u << t_v(MISS, 0, i));
+    if (c.err) return;
+  }
+  // writes: owner = writing node, replicated there only
+  for (uint32_t a = 0; a < na; ++a) {
+    if (t.acc[a].buffer != b || !(t.acc[a].mode & IGS_WRITE)) continue;
+    if (union_is_image(t.acc[a], bd)) {
+      for (uint32_t wn = 0; wn < c.N; ++wn) {
+        if (t_key(NB, wn) == DEAD) continue;
+        const Bx x = map_box(t.acc[a], t_box(NB, wn), bd);
+        if (!bx_empty(x)) t_set(c, O, NONE, x, wn, 1u << wn, 0);
+      }
+    } else {
+      for (uint32_t slot = 0; slot < CH.n; ++slot) {
+        const uint32_t wn = t_v(CH, 0, slot);
+        const Bx x = t_box(MP, slot * na + a);
+        if (!bx_empty(x)) t_set(c, O, NONE, x, wn, 1u << wn, 0);
+      }
+    }
+    if (c.err) return;
+  }
+  t_merge_from(c, O, from);
+}
+
+// Worker w's buffers of a push / await job: i mod workers == w.
+__device__ __noinline__ void a3_share(Ctx& c, WorkJob& j, uint32_t w, Table& OUT) {
+  for (uint32_t i = w; i < j.nbuf && !c.err; i += j.workers) {
+    const uint32_t from = OUT.n;
+    a3_buffer(c, *j.task, j.seq, j.CH, j.MP, j.NB, j.buf[i], OUT);
+    __syncwarp();
+    if (c.lane == 0) {
+      j.buf_off[i] = from;
+      j.buf_cnt[i] = OUT.n - from;
+    }
+    __syncwarp();
+  }
+}
+
+__device__ __noinline__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP) {
+  const uint32_t na = t.num_accessors;
   Table& NB = c.s[S_T4];
   node_bboxes(c, CH, NB);
-  uint32_t done = 0;  // bitmask over accessor indices whose buffer was handled
-  for (;;) {
-    // next buffer in ascending order
+  // the task's buffers, ascending
+  uint32_t bufs[IGS_MAX_ACCESSORS], nbuf = 0;
+  for (uint32_t done = 0;;) {
     uint32_t b = NONE;
     for (uint32_t a = 0; a < na; ++a)
       if (!(done >> a & 1u) && (b == NONE || t.acc[a].buffer < b)) b = t.acc[a].buffer;
     if (b == NONE) break;
     for (uint32_t a = 0; a < na; ++a)
       if (t.acc[a].buffer == b) done |= 1u << a;
-    t_reset(MISS);
-    const BufDesc& bd = buf_of(c, b);
-    for (uint32_t m = 0; m < c.N; ++m) {
-      t_reset(TMP);
-      if (t_key(NB, m) == DEAD) continue;
-      const Table O = own_t(c, b);
-      auto lacking = [m](uint32_t, uint32_t repl, uint32_t) { return !((repl >> m) & 1u); };
-      for (uint32_t a = 0; a < na; ++a) {
-        if (t.acc[a].buffer != b || !(t.acc[a].mode & IGS_READ)) continue;
-        if (union_is_image(t.acc[a], bd)) {
-          const Bx x = map_box(t.acc[a], t_box(NB, m), bd);
-          if (!bx_empty(x)) t_query(c, O, NONE, x, TMP, lacking);
-        } else {
-          for (uint32_t slot = 0; slot < CH.n; ++slot) {
-            if (t_v(CH, 0, slot) != m) continue;
-            const Bx x = t_box(MP, slot * na + a);
-            if (!bx_empty(x)) t_query(c, O, NONE, x, TMP, lacking);
-          }
-        }
-        if (c.err) return;
-      }
-      t_make_disjoint(c, TMP);
+    bufs[nbuf++] = b;
+  }
+  if (c.block && c.workers > 1 && c.nd->helper_scratch && nbuf > 1) {
+    BlockShared& sh = *static_cast<BlockShared*>(c.block);
+    WorkJob& j = sh.job;
+    Table& OUT0 = c.s[S_T5];
+    t_reset(OUT0);
+    __syncwarp();
+    if (c.lane == 0) {
+      j.nd = c.nd;
+      j.pg = c.pg;
+      j.task = &t;
+      j.CH = CH;
+      j.MP = MP;
+      j.NB = NB;
+      j.seq = seq;
+      j.epoch = c.epoch;
+      j.node = c.node;
+      j.workers = c.workers;
+      j.nbuf = nbuf;
+      for (uint32_t i = 0; i < nbuf; ++i) j.buf[i] = bufs[i];
+    }
+    if (!run_shared(c, sh, CMD_A3, [&]() { a3_share(c, j, 0, OUT0); })) return;
+    // the QR entries in buffer order, as the single-warp path appends them
+    for (uint32_t i = 0; i < nbuf; ++i) {
+      const uint32_t w = i % c.workers, off = j.buf_off[i], cnt = j.buf_cnt[i];
+      const uint32_t* src = w == 0 ? OUT0.base : helper_table(c.nd, w, 5);
+      const uint32_t first = __shfl_sync(FULL, t_claim_n(c, c.qr, c.lane == 0 ? cnt : 0u), 0);  // lane 0's slot
       if (c.err) return;
-      for (uint32_t base = 0; base < TMP.n; base += 32) {
-        const uint32_t i = base + c.lane;
-        const bool live = i < TMP.n && t_key(TMP, i) != DEAD;
-        const uint32_t s = t_claim(c, MISS, live);
-        if (c.err) return;
-        if (live) t_put(MISS, s, 0, t_box(TMP, i), m, 0, 0);
-      }
+      const uint4* s4 = reinterpret_cast<const uint4*>(src + (size_t)off * F_COUNT);
+      uint4* d4 = reinterpret_cast<uint4*>(c.qr.base + (size_t)first * F_COUNT);
+      for (uint32_t k = c.lane; k < cnt * (F_COUNT / 4); k += 32) d4[k] = s4[k];
       __syncwarp();
     }
-    // this node's await (canonical) and bbox
-    {
-      Table& sel = TMP;
-      t_reset(sel);
-      for (uint32_t base = 0; base < MISS.n; base += 32) {
-        const uint32_t i = base + c.lane;
-        const bool hit = i < MISS.n && t_v(MISS, 0, i) == c.node;
-        const uint32_t s = t_claim(c, sel, hit);
-        if (c.err) return;
-        if (hit) t_put(sel, s, 0, t_box(MISS, i), 0, 0, 0);
-      }
-      __syncwarp();
-      if (sel.n) {
-        t_reset(CN);
-        canonical(c, sel, 0, sel.n, CN);
-        if (c.err) return;
-        const Bx bb = t_bbox(c, CN, 0, CN.n);
-        for (uint32_t base = 0; base < CN.n + 1; base += 32) {
-          const uint32_t i = base + c.lane;
-          const bool in = i < CN.n + 1;
-          const uint32_t s = t_claim(c, c.qr, in);
-          if (c.err) return;
-          if (in) {
-            if (i < CN.n) t_put(c.qr, s, seq, t_box(CN, i), 1, b, NONE);
-            else t_put(c.qr, s, seq, bb, 3, b, NONE);
-          }
-        }
-        __syncwarp();
-      }
-    }
-    // this node's pushes to every other node
-    for (uint32_t m = 0; m < c.N; ++m) {
-      if (m == c.node) continue;
-      t_reset(PT);
-      for (uint32_t i = 0; i < MISS.n; ++i) {
-        if (t_v(MISS, 0, i) != m) continue;
-        const uint32_t me = c.node;
-        t_query(c, own_t(c, b), NONE, t_box(MISS, i), PT, [me](uint32_t owner, uint32_t, uint32_t) { return owner == me; });
-        if (c.err) return;
-      }
-      if (PT.n == 0) continue;
-      t_reset(CN);
-      canonical(c, PT, 0, PT.n, CN);
-      if (c.err) return;
-      const Bx bb = t_bbox(c, CN, 0, CN.n);
-      for (uint32_t base = 0; base < CN.n + 1; base += 32) {
-        const uint32_t i = base + c.lane;
-        const bool in = i < CN.n + 1;
-        const uint32_t s = t_claim(c, c.qr, in);
-        if (c.err) return;
-        if (in) {
-          if (i < CN.n) t_put(c.qr, s, seq, t_box(CN, i), 0, b, m);
-          else t_put(c.qr, s, seq, bb, 2, b, m);
-        }
-      }
-      __syncwarp();
-    }
-    // replication: every node now holds what it awaited
-    Table O = own_t(c, b);
-    t_tidy(c, O);
-    const uint32_t from = O.n;
-    for (uint32_t i = 0; i < MISS.n; ++i) {
-      t_or(c, O, NONE, t_box(MISS, i), 1, 1u << t_v(MISS, 0, i));
-      if (c.err) return;
-    }
-    // writes: owner = writing node, replicated there only
-    for (uint32_t a = 0; a < na; ++a) {
-      if (t.acc[a].buffer != b || !(t.acc[a].mode & IGS_WRITE)) continue;
-      if (union_is_image(t.acc[a], bd)) {
-        for (uint32_t wn = 0; wn < c.N; ++wn) {
-          if (t_key(NB, wn) == DEAD) continue;
-          const Bx x = map_box(t.acc[a], t_box(NB, wn), bd);
-          if (!bx_empty(x)) t_set(c, O, NONE, x, wn, 1u << wn, 0);
-        }
-      } else {
-        for (uint32_t slot = 0; slot < CH.n; ++slot) {
-          const uint32_t wn = t_v(CH, 0, slot);
-          const Bx x = t_box(MP, slot * na + a);
-          if (!bx_empty(x)) t_set(c, O, NONE, x, wn, 1u << wn, 0);
-        }
-      }
-      if (c.err) return;
-    }
-    t_merge_from(c, O, from);
+    return;
+  }
+  for (uint32_t i = 0; i < nbuf; ++i) {
+    a3_buffer(c, t, seq, CH, MP, NB, bufs[i], c.qr);
+    if (c.err) return;
   }
 }
 
@@ -2024,7 +2161,7 @@ __device__ __noinline__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq
     __syncwarp();
     for (int guard = 0;; ++guard) {
       if (guard > 1 << 20) {
-        fail(c, ST_INTERNAL);
+        fail_internal(c, 3);
         return;
       }
       const uint32_t n = CL.n;
@@ -2167,36 +2304,6 @@ __device__ __noinline__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq
 // of the devices d with d mod workers == its index: their dependencies (edges
 // staged per worker) and their table updates. Warp 0 then writes edges,
 // boxes, bindings and records in chunk order, exactly as the single-warp path.
-enum BlockCmd : uint32_t { CMD_NONE = 0, CMD_P5 = 1, CMD_EXIT = 2 };
-__device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg);
-
-struct P5Job {
-  NodeDev* nd;
-  const ProgDev* pg;
-  const igs_task* task;
-  Table CH, MP, AL;  // warp 0's tables; AL[slot * na] v0 = kernel id, v1/v2 = staged edges
-  uint32_t na, epoch, node, workers, stage_cap;
-  igs_edge* stage0;  // worker 0's staged edges (warp 0's scratch)
-};
-
-struct BlockShared {
-  int lock;
-  volatile uint32_t cmd, err, err_info;
-  P5Job job;
-};
-
-__device__ __forceinline__ void worker_bar(uint32_t workers) {
-  asm volatile("bar.sync 1, %0;" ::"r"(workers * 32) : "memory");
-}
-
-__device__ __forceinline__ uint32_t* helper_table(const NodeDev* nd, uint32_t w, uint32_t k) {
-  return nd->helper_scratch + ((size_t)(w - 1) * 3 + k) * nd->cap_scratch * F_COUNT;
-}
-
-__device__ __forceinline__ igs_edge* stage_of(const P5Job& j, uint32_t w) {
-  return w == 0 ? j.stage0 : reinterpret_cast<igs_edge*>(helper_table(j.nd, w, 2));
-}
-
 // The kernel's bindings / accesses of local chunk `slot` into BT and acc.
 __device__ bool p5_accesses(Ctx& c, const igs_task& t, const Table& MP, const Table& AL, uint32_t slot, uint32_t na,
                             Table& BT, Acc* acc, int& nacc) {
@@ -2206,7 +2313,7 @@ __device__ bool p5_accesses(Ctx& c, const igs_task& t, const Table& MP, const Ta
     const Bx x = t_box(MP, slot * na + a);
     const uint32_t al = FLD(AL, F_KEY, slot * na + a);
     if (al == NONE - 1) {
-      fail(c, ST_INTERNAL);
+      fail_internal(c, 4);
       return false;
     }
     if (c.lane == 0) {
@@ -2220,7 +2327,7 @@ __device__ bool p5_accesses(Ctx& c, const igs_task& t, const Table& MP, const Ta
   return true;
 }
 
-__device__ __noinline__ void p5_share(Ctx& c, const P5Job& j, uint32_t w) {
+__device__ __noinline__ void p5_share(Ctx& c, const WorkJob& j, uint32_t w) {
   const Table& CH = j.CH;
   const Table& MP = j.MP;
   const Table& AL = j.AL;
@@ -2258,17 +2365,27 @@ __device__ void helper_loop(BlockShared& sh, uint32_t w, uint32_t workers) {
     worker_bar(workers);
     const uint32_t cmd = sh.cmd;
     if (cmd == CMD_EXIT) break;
-    if (cmd == CMD_P5) {
-      const P5Job& j = sh.job;
+    if (cmd == CMD_P5 || cmd == CMD_A3) {
+      WorkJob& j = sh.job;
       Ctx hc;
       load_ctx(hc, j.nd, j.pg);
       hc.err = ST_OK;
       hc.epoch = j.epoch;
       hc.node = j.node;
       hc.lock = &sh.lock;
-      hc.s[S_DEP].base = helper_table(j.nd, w, 0);
-      hc.s[S_T4].base = helper_table(j.nd, w, 1);
-      p5_share(hc, j, w);
+      if (cmd == CMD_P5) {
+        hc.s[S_DEP].base = helper_table(j.nd, w, 0);
+        hc.s[S_T4].base = helper_table(j.nd, w, 1);
+        p5_share(hc, j, w);
+      } else {
+        hc.s[S_T0].base = helper_table(j.nd, w, 0);
+        hc.s[S_T1].base = helper_table(j.nd, w, 1);
+        hc.s[S_T2].base = helper_table(j.nd, w, 2);
+        hc.s[S_T3].base = helper_table(j.nd, w, 3);
+        hc.s[S_CAN].base = helper_table(j.nd, w, 4);
+        Table out = scratch_table(helper_table(j.nd, w, 5), j.nd->cap_scratch);
+        a3_share(hc, j, w, out);
+      }
       if (hc.lane == 0) {
         atomicAdd(reinterpret_cast<unsigned long long*>(&j.nd->map_reads), (unsigned long long)hc.map_reads);
         atomicAdd(reinterpret_cast<unsigned long long*>(&j.nd->map_writes), (unsigned long long)hc.map_writes);
@@ -2295,7 +2412,7 @@ __device__ __noinline__ void p5_parallel(Ctx& c, const igs_task& t, uint32_t seq
   }
   __syncwarp();
   if (c.lane == 0) {
-    P5Job& j = sh.job;
+    WorkJob& j = sh.job;
     j.nd = c.nd;
     j.pg = c.pg;
     j.task = &t;
@@ -2321,7 +2438,7 @@ __device__ __noinline__ void p5_parallel(Ctx& c, const igs_task& t, uint32_t seq
     c.err_info = sh.err_info;
   }
   if (c.err) return;
-  const P5Job& j = sh.job;
+  const WorkJob& j = sh.job;
   Table& BT = c.s[S_T4];
   NodeDev* nd = c.nd;
   for (uint32_t slot = 0; slot < CH.n; ++slot) {
@@ -2329,7 +2446,7 @@ __device__ __noinline__ void p5_parallel(Ctx& c, const igs_task& t, uint32_t seq
     const uint32_t mem = t_v(CH, 1, slot);
     const uint32_t kid = FLD(AL, F_V, slot * na), off = FLD(AL, F_V + 1, slot * na), ne = FLD(AL, F_V + 2, slot * na);
     if (kid != c.n_instr) {
-      fail(c, ST_INTERNAL);
+      fail_internal(c, 5);
       return;
     }
     if (c.n_edge + ne > nd->cap_edge) {
@@ -2384,7 +2501,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     const Bx bb = t_box(c.qr, g1);  // the bbox entry follows the boxes
     const uint32_t dst = find_alloc(c, b, 1, bb);
     if (dst == NONE) {
-      fail(c, ST_INTERNAL);
+      fail_internal(c, 6);
       return;
     }
     // copy the push region into RG (coherence uses the scratch tables)
@@ -2462,7 +2579,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     const Bx bb = t_box(c.qr, g1);
     const uint32_t dst = find_alloc(c, b, 1, bb);
     if (dst == NONE) {
-      fail(c, ST_INTERNAL);
+      fail_internal(c, 7);
       return;
     }
     t_reset(RG);
@@ -2642,7 +2759,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     if (!(flags & 2u)) continue;
     const uint32_t dst = find_alloc(c, b, mem, x);
     if (dst == NONE) {
-      fail(c, ST_INTERNAL);
+      fail_internal(c, 8);
       return;
     }
     t_reset(RG);

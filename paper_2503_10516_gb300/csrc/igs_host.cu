@@ -226,7 +226,7 @@ void ev_collect(igs_ctx* c) {
 // with more than one device only).
 int ensure_helpers(igs_ctx* c) {
   if (c->d_helpers || c->D < 2) return IGS_OK;
-  const size_t per = (size_t)(kMaxWorkers - 1) * kHelperTables * c->nodes_host[0].cap_scratch * F_COUNT;
+  const size_t per = (size_t)kMaxWorkers * kHelperTables * c->nodes_host[0].cap_scratch * F_COUNT;
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaMalloc((void**)&c->d_helpers, sizeof(uint32_t) * per * c->N));
   for (uint32_t n = 0; n < c->N; ++n) {

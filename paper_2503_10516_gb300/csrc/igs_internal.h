@@ -46,7 +46,7 @@ struct Table {
 // Warps that share parts of a node's lowering (warp 0 and up to 7 helpers),
 // and the scratch tables of each helper.
 constexpr uint32_t kMaxWorkers = 8;
-constexpr uint32_t kHelperTables = 6;
+constexpr uint32_t kHelperTables = 12;
 
 // Size classes of the per-node entry heap: 32 << k entries.
 constexpr int kHeapClasses = 24;
@@ -101,8 +101,9 @@ struct NodeDev {
   uint32_t* rejected;
   // scratch tables for the warp
   uint32_t* scratch_base;  // 14 tables of cap_scratch entries
-  // scratch of the helper warps that share parts of the lowering when a node
-  // is lowered by several warps (kHelperTables of cap_scratch entries each), or null
+  // scratch of the warps that share parts of the lowering when a node is
+  // lowered by several warps (kMaxWorkers x kHelperTables tables of
+  // cap_scratch entries), or null
   uint32_t* helper_scratch;
 };
 

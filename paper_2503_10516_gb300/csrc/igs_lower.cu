@@ -172,6 +172,20 @@ struct Ctx {
   int* lock;  // block's heap lock (shared memory) when several warps of the block lower, else null
   void* block;       // the block's shared control (BlockShared) when it has helper warps, else null
   uint32_t workers;  // warps sharing the kernel phase (1 = warp 0 alone)
+  struct Stage* stage;  // emit into this staging area with provisional ids (coherence workers), else null
+  bool helper;          // a helper warp (keeps off the node's profile counters)
+};
+
+// Instructions a coherence worker emits before their final ids are known:
+// provisional id = PROV | worker << 24 | index. Records carry their edges'
+// range in bind_off / bind_cnt (staged instructions have no bindings).
+constexpr uint32_t PROV = 0x80000000u;
+struct Stage {
+  igs_instruction* instrs;
+  igs_edge* edges;
+  igs_box* boxes;
+  uint32_t* map;  // index -> final id (filled when warp 0 appends the records)
+  uint32_t n_instr, n_edge, n_box, cap_instr, cap_edge, cap_box, id_base;
 };
 
 __device__ __forceinline__ void fail(Ctx& c, uint32_t code) {
@@ -439,7 +453,7 @@ __device__ __forceinline__ Bx warp_bbox(Bx b, bool valid) {
 
 __device__ void pt_lap(PhaseTimer& p, Ctx& c, int ph) {
   const long long t1 = clock64();
-  if (c.lane == 0) c.nd->prof[ph] += (uint64_t)(t1 - p.t0);
+  if (c.lane == 0 && !c.helper) c.nd->prof[ph] += (uint64_t)(t1 - p.t0);
   p.t0 = t1;
 }
 
@@ -1312,7 +1326,7 @@ __device__ __noinline__ uint32_t emit_edges(Ctx& c, uint32_t id, igs_edge* out, 
       e.to = id;
       e.kind = (uint32_t)key;
       out[c.lane] = e;
-      nd->has_succ[e.from] = 1;
+      if (!(e.from & PROV)) nd->has_succ[e.from] = 1;
     }
   } else {
     for (uint32_t base = 0; base < nd0; base += 32) {
@@ -1360,7 +1374,7 @@ __device__ __noinline__ uint32_t emit_edges(Ctx& c, uint32_t id, igs_edge* out, 
           e.to = id;
           e.kind = kind;
           out[rank] = e;
-          nd->has_succ[p] = 1;
+          if (!(p & PROV)) nd->has_succ[p] = 1;
         }
       }
     }
@@ -1497,6 +1511,61 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
                               const Table* bindt, uint32_t bind_from, uint32_t bind_n) {
   if (c.err) return NONE;
   NodeDev* nd = c.nd;
+  if (c.stage) {
+    // a coherence worker: record, edges and boxes into its stage
+    Stage& st = *c.stage;
+    if (bind_n || st.n_instr + 1 > st.cap_instr) {
+      fail_cap(c, CAP_TABLE, st.cap_instr);
+      return NONE;
+    }
+    const uint32_t pid = st.id_base | st.n_instr;
+    if (!emit_deps(c, acc, nacc, keep_dep)) return NONE;
+    const uint32_t ne = emit_edges(c, pid, st.edges + st.n_edge, st.cap_edge - st.n_edge, CAP_TABLE, st.cap_edge);
+    if (ne == NONE) return NONE;
+    uint32_t nb = 0;
+    if (bt) {
+      for (uint32_t base = bfrom; base < bto; base += 32) {
+        const uint32_t i = base + c.lane;
+        const bool live = i < bto && t_key(*bt, i) != DEAD;
+        const uint32_t m = __ballot_sync(FULL, live);
+        if (st.n_box + nb + __popc(m) > st.cap_box) {
+          fail_cap(c, CAP_TABLE, st.cap_box);
+          return NONE;
+        }
+        if (live) {
+          const Bx b = t_box(*bt, i);
+          igs_box o;
+          for (int d = 0; d < 3; ++d) {
+            o.lo[d] = b.lo[d];
+            o.hi[d] = b.hi[d];
+          }
+          st.boxes[st.n_box + nb + __popc(m & lanemask_lt())] = o;
+        }
+        nb += __popc(m);
+      }
+    }
+    if (c.lane == 0) {
+      igs_instruction r;
+      r.id = pid;
+      r.type = type;
+      r.seq = seq;
+      r.a = fa;
+      r.b = fb;
+      r.c = fc;
+      r.d = fd;
+      r.box_off = st.n_box;
+      r.box_cnt = nb;
+      r.bind_off = st.n_edge;
+      r.bind_cnt = ne;
+      st.instrs[st.n_instr] = r;
+    }
+    __syncwarp();
+    st.n_edge += ne;
+    st.n_box += nb;
+    st.n_instr += 1;
+    if (!emit_apply(c, acc, nacc, pid)) return NONE;
+    return pid;
+  }
   const uint32_t id = c.n_instr;
   DT_START(dt);
   DT_COUNT(N_EMIT, 1);
@@ -1748,7 +1817,7 @@ __device__ __forceinline__ bool union_is_image(const igs_accessor& a, const BufD
 // parts touch disjoint tables and emit nothing whose id depends on another
 // part are shared: warp 0 posts a job, every worker does its share, warp 0
 // then appends the parts' results in the order of the single-warp path.
-enum BlockCmd : uint32_t { CMD_NONE = 0, CMD_P5 = 1, CMD_A3 = 2, CMD_EXIT = 3 };
+enum BlockCmd : uint32_t { CMD_NONE = 0, CMD_P5 = 1, CMD_A3 = 2, CMD_P4 = 3, CMD_P4_IDS = 4, CMD_EXIT = 5 };
 __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg);
 
 struct WorkJob {
@@ -1759,8 +1828,10 @@ struct WorkJob {
   uint32_t na, epoch, node, workers, stage_cap, seq;
   igs_edge* stage0;  // worker 0's staged edges (warp 0's scratch)
   Table out0;        // worker 0's staged push / await entries (warp 0's scratch)
-  uint32_t nbuf;     // push / await: buffers in ascending order, their staged entries
+  uint32_t nbuf;     // push / await, coherence: buffers in ascending order, their staged entries
   uint32_t buf[IGS_MAX_ACCESSORS], buf_off[IGS_MAX_ACCESSORS], buf_cnt[IGS_MAX_ACCESSORS];
+  Table PC;          // coherence: the consumers (flags, box, v0 = chunk slot * na + accessor)
+  uint32_t n_live;   // coherence: live allocations (NodeDev's count is stale during a launch)
 };
 
 struct BlockShared {
@@ -1773,9 +1844,10 @@ __device__ __forceinline__ void worker_bar(uint32_t workers) {
   asm volatile("bar.sync 1, %0;" ::"r"(workers * 32) : "memory");
 }
 
-// Helper w's scratch table k (kHelperTables per helper).
+// Worker w's scratch table k (kHelperTables per worker; worker 0 = warp 0
+// uses only its staging tables 8-11).
 __device__ __forceinline__ uint32_t* helper_table(const NodeDev* nd, uint32_t w, uint32_t k) {
-  return nd->helper_scratch + ((size_t)(w - 1) * kHelperTables + k) * nd->cap_scratch * F_COUNT;
+  return nd->helper_scratch + ((size_t)w * kHelperTables + k) * nd->cap_scratch * F_COUNT;
 }
 
 __device__ __forceinline__ igs_edge* stage_of(const WorkJob& j, uint32_t w) {
@@ -2359,13 +2431,226 @@ __device__ __noinline__ void p5_share(Ctx& c, const WorkJob& j, uint32_t w) {
   __syncwarp();
 }
 
+// ---- coherence shared by several warps ---------------------------------------
+
+// One consumer of the coherence phase: PC entry k (flags bit 0 uninitialized
+// read, bit 1 stale data). diag: write its warning here (single-warp path).
+__device__ bool p4_consumer(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& PC, uint32_t k,
+                            uint32_t na, bool diag) {
+  const uint32_t flags = t_key(PC, k), i = t_v(PC, 0, k);
+  const uint32_t slot = i / na, a = i % na;
+  const uint32_t mem = t_v(CH, 1, slot), b = t.acc[a].buffer;
+  const Bx x = t_box(PC, k);
+  if (diag && (flags & 1u)) {  // uninitialized read warning (Sec. 4.4)
+    if (c.n_diag >= c.nd->cap_diag) {
+      fail_cap(c, CAP_DIAG, c.nd->cap_diag);
+      return false;
+    }
+    if (c.lane == 0) {
+      igs_diag dg;
+      dg.seq = seq;
+      dg.chunk = t_key(CH, slot);
+      dg.accessor = a;
+      c.nd->diags[c.n_diag] = dg;
+    }
+    c.n_diag += 1;
+    __syncwarp();
+  }
+  if (!(flags & 2u)) return true;
+  const uint32_t dst = find_alloc(c, b, mem, x);
+  if (dst == NONE) {
+    fail_internal(c, 9);
+    return false;
+  }
+  Table& RG = c.s[S_RG];
+  t_reset(RG);
+  const uint32_t s = t_claim(c, RG, c.lane == 0);
+  if (c.err) return false;
+  if (c.lane == 0) t_put(RG, s, 0, x, 0, 0, 0);
+  __syncwarp();
+  coherence(c, seq, b, mem, dst, RG, 0, 1);
+  return c.err == ST_OK;
+}
+
+// Consumers of different buffers touch disjoint state (the buffer's state
+// table and allocations); only the ids of their copies depend on one another.
+// Worker w takes the consumers of buffers i with i mod workers == w, in
+// consumer order, emitting into its stage with provisional ids.
+__device__ __forceinline__ uint32_t buffer_worker(const WorkJob& j, uint32_t b) {
+  for (uint32_t i = 0; i < j.nbuf; ++i)
+    if (j.buf[i] == b) return i % j.workers;
+  return 0;
+}
+
+__device__ Stage make_stage(const NodeDev* nd, uint32_t w) {
+  Stage st;
+  const uint32_t words = nd->cap_scratch * F_COUNT;  // words per table
+  st.instrs = reinterpret_cast<igs_instruction*>(helper_table(nd, w, 8));
+  st.edges = reinterpret_cast<igs_edge*>(helper_table(nd, w, 9));
+  st.boxes = reinterpret_cast<igs_box*>(helper_table(nd, w, 10));
+  st.map = helper_table(nd, w, 11);
+  st.cap_instr = words * 4 / (uint32_t)sizeof(igs_instruction);
+  st.cap_edge = words * 4 / (uint32_t)sizeof(igs_edge);
+  st.cap_box = words * 4 / (uint32_t)sizeof(igs_box);
+  st.n_instr = st.n_edge = st.n_box = 0;
+  st.id_base = PROV | (w << 24);
+  return st;
+}
+
+__device__ __noinline__ void p4_share(Ctx& c, WorkJob& j, uint32_t w) {
+  Stage st = make_stage(c.nd, w);
+  c.stage = &st;
+  const Table& PC = j.PC;
+  const igs_task& t = *j.task;
+  for (uint32_t k = 0; k < PC.n && !c.err; ++k) {
+    const uint32_t flags = t_key(PC, k);
+    if (!flags) continue;
+    const uint32_t a = t_v(PC, 0, k) % j.na;
+    if (buffer_worker(j, t.acc[a].buffer) != w) continue;
+    const uint32_t first = st.n_instr;
+    if (!p4_consumer(c, t, j.seq, j.CH, PC, k, j.na, false)) break;
+    __syncwarp();
+    if (c.lane == 0) {
+      FLD(PC, F_V + 1, k) = first;
+      FLD(PC, F_V + 2, k) = st.n_instr - first;
+    }
+    __syncwarp();
+  }
+  c.stage = nullptr;
+}
+
+// After warp 0 has given the staged copies their ids: the provisional ids in
+// the allocation tables of worker w's buffers become final.
+__device__ __noinline__ void p4_final_ids(Ctx& c, const WorkJob& j, uint32_t w) {
+  const uint32_t* map = helper_table(c.nd, w, 11);
+  for (uint32_t li = 0; li < j.n_live; ++li) {
+    const uint32_t aid = c.nd->live[li];
+    const uint32_t b = c.nd->allocs[aid].buffer;
+    bool mine = false;
+    for (uint32_t i = 0; i < j.nbuf; ++i)
+      if (j.buf[i] == b) mine = (i % j.workers) == w;
+    if (!mine) continue;
+    for (int k = 0; k < 2; ++k) {
+      const Table T = k == 0 ? wr_t(c, aid) : rd_t(c, aid);
+      for (uint32_t base = 0; base < T.n; base += 32) {
+        const uint32_t i = base + c.lane;
+        if (i < T.n && t_key(T, i) != DEAD) {
+          const uint32_t v = t_v(T, 0, i);
+          if (v & PROV) FLD(T, F_V, i) = map[v & 0xFFFFFFu];
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// Warp 0: coherence with the helpers, then the staged copies in consumer
+// order (final ids, edges, boxes, records), then the ids in the tables.
+__device__ __noinline__ void p4_parallel(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, Table& PC,
+                                         uint32_t na) {
+  BlockShared& sh = *static_cast<BlockShared*>(c.block);
+  WorkJob& j = sh.job;
+  uint32_t bufs[IGS_MAX_ACCESSORS], nbuf = 0;
+  for (uint32_t done = 0;;) {
+    uint32_t b = NONE;
+    for (uint32_t a = 0; a < na; ++a)
+      if (!(done >> a & 1u) && (t.acc[a].mode & IGS_READ) && (b == NONE || t.acc[a].buffer < b)) b = t.acc[a].buffer;
+    if (b == NONE) break;
+    for (uint32_t a = 0; a < na; ++a)
+      if (t.acc[a].buffer == b) done |= 1u << a;
+    bufs[nbuf++] = b;
+  }
+  __syncwarp();
+  if (c.lane == 0) {
+    j.nd = c.nd;
+    j.pg = c.pg;
+    j.task = &t;
+    j.CH = CH;
+    j.PC = PC;
+    j.na = na;
+    j.seq = seq;
+    j.epoch = c.epoch;
+    j.node = c.node;
+    j.workers = c.workers;
+    j.n_live = c.n_live;
+    j.nbuf = nbuf;
+    for (uint32_t i = 0; i < nbuf; ++i) j.buf[i] = bufs[i];
+  }
+  if (!run_shared(c, sh, CMD_P4, [&]() { p4_share(c, j, 0); })) return;
+  NodeDev* nd = c.nd;
+  for (uint32_t k = 0; k < PC.n; ++k) {
+    const uint32_t flags = t_key(PC, k);
+    if (!flags) continue;
+    if (flags & 1u) {
+      const uint32_t i = t_v(PC, 0, k), slot = i / na, a = i % na;
+      if (c.n_diag >= nd->cap_diag) {
+        fail_cap(c, CAP_DIAG, nd->cap_diag);
+        return;
+      }
+      if (c.lane == 0) {
+        igs_diag dg;
+        dg.seq = seq;
+        dg.chunk = t_key(CH, slot);
+        dg.accessor = a;
+        nd->diags[c.n_diag] = dg;
+      }
+      c.n_diag += 1;
+      __syncwarp();
+    }
+    if (!(flags & 2u)) continue;
+    const uint32_t a = t_v(PC, 0, k) % na;
+    const uint32_t w = buffer_worker(j, t.acc[a].buffer);
+    const Stage st = make_stage(nd, w);
+    const uint32_t first = FLD(PC, F_V + 1, k), cnt = FLD(PC, F_V + 2, k);
+    for (uint32_t q = first; q < first + cnt; ++q) {
+      const igs_instruction r = st.instrs[q];
+      const uint32_t id = c.n_instr;
+      if (c.n_instr + 1 > nd->cap_instr || c.n_edge + r.bind_cnt > nd->cap_edge) {
+        fail_cap(c, CAP_EDGE, nd->cap_edge);
+        return;
+      }
+      if (c.n_box + r.box_cnt > nd->cap_box) {
+        fail_cap(c, CAP_BOX, nd->cap_box);
+        return;
+      }
+      __syncwarp();
+      if (c.lane == 0) {
+        st.map[q] = id;
+        nd->has_succ[id] = 0;
+      }
+      __syncwarp();
+      for (uint32_t e = c.lane; e < r.bind_cnt; e += 32) {
+        igs_edge ed = st.edges[r.bind_off + e];
+        if (ed.from & PROV) ed.from = st.map[ed.from & 0xFFFFFFu];  // an earlier copy of this worker
+        ed.to = id;
+        nd->edges[c.n_edge + e] = ed;
+        nd->has_succ[ed.from] = 1;
+      }
+      for (uint32_t e = c.lane; e < r.box_cnt; e += 32) nd->boxes[c.n_box + e] = st.boxes[r.box_off + e];
+      if (c.lane == 0) {
+        igs_instruction o = r;
+        o.id = id;
+        o.box_off = c.n_box;
+        o.bind_off = c.n_bind;
+        o.bind_cnt = 0;
+        nd->instrs[id] = o;
+      }
+      c.n_edge += r.bind_cnt;
+      c.n_box += r.box_cnt;
+      c.n_instr += 1;
+      __syncwarp();
+    }
+  }
+  run_shared(c, sh, CMD_P4_IDS, [&]() { p4_final_ids(c, j, 0); });
+}
+
 // Helper warp w: waits for work from warp 0, does its share, reports.
 __device__ void helper_loop(BlockShared& sh, uint32_t w, uint32_t workers) {
   for (;;) {
     worker_bar(workers);
     const uint32_t cmd = sh.cmd;
     if (cmd == CMD_EXIT) break;
-    if (cmd == CMD_P5 || cmd == CMD_A3) {
+    if (cmd == CMD_P5 || cmd == CMD_A3 || cmd == CMD_P4 || cmd == CMD_P4_IDS) {
       WorkJob& j = sh.job;
       Ctx hc;
       load_ctx(hc, j.nd, j.pg);
@@ -2373,7 +2658,14 @@ __device__ void helper_loop(BlockShared& sh, uint32_t w, uint32_t workers) {
       hc.epoch = j.epoch;
       hc.node = j.node;
       hc.lock = &sh.lock;
-      if (cmd == CMD_P5) {
+      hc.helper = true;
+      if (cmd == CMD_P4 || cmd == CMD_P4_IDS) {
+        hc.n_live = j.n_live;
+        const int tabs[8] = {S_T0, S_T1, S_T2, S_T3, S_T5, S_RG, S_CAN, S_DEP};
+        for (int k = 0; k < 8; ++k) hc.s[tabs[k]].base = helper_table(j.nd, w, k);
+        if (cmd == CMD_P4) p4_share(hc, j, w);
+        else p4_final_ids(hc, j, w);
+      } else if (cmd == CMD_P5) {
         hc.s[S_DEP].base = helper_table(j.nd, w, 0);
         hc.s[S_T4].base = helper_table(j.nd, w, 1);
         p5_share(hc, j, w);
@@ -2735,42 +3027,25 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     }
     __syncwarp();
   }
-  for (uint32_t k = 0; k < PC.n; ++k) {
-    const uint32_t flags = t_key(PC, k), i = t_v(PC, 0, k);
-    if (!flags) continue;
-    const uint32_t slot = i / na, a = i % na;
-    const uint32_t mem = t_v(CH, 1, slot), b = t.acc[a].buffer;
-    const Bx x = t_box(PC, k);
-    if (flags & 1u) {  // uninitialized read warning (Sec. 4.4)
-      if (c.n_diag >= c.nd->cap_diag) {
-        fail_cap(c, CAP_DIAG, c.nd->cap_diag);
-        return;
-      }
-      if (c.lane == 0) {
-        igs_diag dg;
-        dg.seq = seq;
-        dg.chunk = t_key(CH, slot);
-        dg.accessor = a;
-        c.nd->diags[c.n_diag] = dg;
-      }
-      c.n_diag += 1;
-      __syncwarp();
+  // stale consumers of several buffers: shared by the helper warps
+  bool multi = false;
+  if (c.block && c.workers > 1 && c.nd->helper_scratch) {
+    uint32_t first_b = NONE;
+    for (uint32_t k = 0; k < PC.n && !multi; ++k) {
+      if (!(t_key(PC, k) & 2u)) continue;
+      const uint32_t b = t.acc[t_v(PC, 0, k) % na].buffer;
+      if (first_b == NONE) first_b = b;
+      else if (b != first_b) multi = true;
     }
-    if (!(flags & 2u)) continue;
-    const uint32_t dst = find_alloc(c, b, mem, x);
-    if (dst == NONE) {
-      fail_internal(c, 8);
-      return;
-    }
-    t_reset(RG);
-    {
-      const uint32_t s = t_claim(c, RG, c.lane == 0);
-      if (c.err) return;
-      if (c.lane == 0) t_put(RG, s, 0, x, 0, 0, 0);
-      __syncwarp();
-    }
-    coherence(c, seq, b, mem, dst, RG, 0, 1);
+  }
+  if (multi) {
+    p4_parallel(c, t, seq, CH, PC, na);
     if (c.err) return;
+  } else {
+    for (uint32_t k = 0; k < PC.n; ++k) {
+      if (!t_key(PC, k)) continue;
+      if (!p4_consumer(c, t, seq, CH, PC, k, na, true)) return;
+    }
   }
   pt_lap(pt, c, PH_P4);
   // P5: one device kernel per local chunk; every accessor's allocation is
@@ -3136,6 +3411,8 @@ __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg) {
   c.lock = nullptr;
   c.block = nullptr;
   c.workers = 1;
+  c.stage = nullptr;
+  c.helper = false;
 }
 
 __device__ void store_ctx(Ctx& c, uint32_t cursor) {

@@ -305,9 +305,10 @@ int igs_stats(igs_ctx* ctx, double out[8]);
  * [10] horizon / epoch emission, [11] horizon / epoch compaction, [12] total
  * inside the lowering kernel; cycles spent inside [13] instruction emission,
  * [14] canonical-form computation, [15] allocation lookup (these overlap the
- * phases above). [16..31] are detail counters (region-map primitives, parts
+ * phases above). [16..30] are detail counters (region-map primitives, parts
  * of emission, call counts); they stay zero unless the library was compiled
- * with IGS_PROFILE_DETAIL. */
+ * with IGS_PROFILE_DETAIL. [31] counts the phases that helper warps shared
+ * with a node's first warp. */
 int igs_profile(igs_ctx* ctx, uint64_t out[32]);
 
 const char* igs_last_error(const igs_ctx* ctx);

@@ -1870,6 +1870,7 @@ template <class F>
 __device__ bool run_shared(Ctx& c, BlockShared& sh, uint32_t cmd, F share0) {
   __syncwarp();
   if (c.lane == 0) {
+    c.nd->prof[31] += 1;  // shared phases run (profile counter)
     sh.err = ST_OK;
     sh.cmd = cmd;
     __threadfence_block();
@@ -2717,19 +2718,8 @@ __device__ __noinline__ void p5_parallel(Ctx& c, const igs_task& t, uint32_t seq
     j.workers = c.workers;
     j.stage_cap = c.nd->cap_scratch * (F_COUNT * 4 / (uint32_t)sizeof(igs_edge));
     j.stage0 = reinterpret_cast<igs_edge*>(c.s[S_T0].base);
-    sh.err = ST_OK;
-    sh.cmd = CMD_P5;
-    __threadfence_block();
   }
-  __syncwarp();
-  worker_bar(c.workers);  // helpers start
-  p5_share(c, sh.job, 0);
-  worker_bar(c.workers);  // every share done
-  if (sh.err != ST_OK && c.err == ST_OK) {
-    c.err = sh.err;
-    c.err_info = sh.err_info;
-  }
-  if (c.err) return;
+  if (!run_shared(c, sh, CMD_P5, [&]() { p5_share(c, sh.job, 0); })) return;
   const WorkJob& j = sh.job;
   Table& BT = c.s[S_T4];
   NodeDev* nd = c.nd;

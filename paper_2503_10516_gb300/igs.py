@@ -286,7 +286,7 @@ PHASES = ("split", "overlap", "push_await", "allocating", "alloc", "push", "rece
           "remote", "sync_emit", "sync_apply", "total", "in_emit", "in_canonical", "in_find_alloc",
           "in_merge", "in_subtract", "in_query", "in_compact", "emit_probe", "emit_dedup", "emit_record",
           "emit_apply", "n_merge", "n_merge_probe", "n_subtract", "n_emit", "n_probe_entries", "n_tidy",
-          "n_grow", "spare")
+          "n_grow", "n_shared_phases")
 
 
 def _profile(self) -> dict:

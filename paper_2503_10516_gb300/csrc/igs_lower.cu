@@ -1121,6 +1121,15 @@ __device__ __noinline__ void task_mapped(Ctx& c, const igs_task& t, const Table&
   __syncwarp();
 }
 
+// Chunks are disjoint along kernel dimension 0; an accessor that maps that
+// dimension one to one (radius 0) onto some buffer dimension gives them
+// disjoint images there, so one accessor's chunks cannot overlap each other.
+__device__ __forceinline__ bool split_dim_injective(const igs_accessor& acc, uint32_t dims) {
+  for (uint32_t d = 0; d < dims; ++d)
+    if (acc.dim[d].kind == IGS_MAP_AFFINE && acc.dim[d].a == 0 && acc.dim[d].c == 0) return true;
+  return false;
+}
+
 // Sec. 4.4: chunks of one task writing overlapping regions.
 __device__ __noinline__ bool overlapping_writes(Ctx& c, const igs_task& t, const Table& CH, const Table& MP) {
   const uint32_t na = t.num_accessors;
@@ -1128,6 +1137,7 @@ __device__ __noinline__ bool overlapping_writes(Ctx& c, const igs_task& t, const
     if (!(t.acc[a].mode & IGS_WRITE)) continue;
     for (uint32_t b = a; b < na; ++b) {
       if (!(t.acc[b].mode & IGS_WRITE) || t.acc[b].buffer != t.acc[a].buffer) continue;
+      if (a == b && split_dim_injective(t.acc[a], buf_of(c, t.acc[a].buffer).dims)) continue;
       // chunk x's accessor a against every later chunk y's accessor b (and a
       // against b within the pair of accessors when a != b)
       for (uint32_t x = 0; x < CH.n; ++x) {
@@ -2875,6 +2885,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     }
     __syncwarp();
     for (uint32_t i = 0; i < RG.n; ++i) wvol += bx_volume(t_box(RG, i));
+    const Bx rg_bb = t_bbox(c, RG, 0, RG.n);
     // consumers in (chunk, accessor) order: v0 = consumer index
     t_reset(CONS);
     uint32_t ncons = 0;
@@ -2884,7 +2895,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
       for (uint32_t a = 0; a < na; ++a) {
         if (t.acc[a].buffer != b || !(t.acc[a].mode & IGS_READ)) continue;
         const Bx x = t_box(MP, slot * na + a);
-        if (bx_empty(x)) continue;
+        if (bx_empty(x) || !bx_overlap(x, rg_bb)) continue;  // reads nothing awaited
         uint64_t vol = 0;
         const uint32_t from = CONS.n;
         for (uint32_t base = 0; base < RG.n; base += 32) {
@@ -2895,7 +2906,6 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
             is = bx_isect(t_box(RG, i), x);
             hit = !bx_empty(is);
           }
-          vol += warp_sum(hit ? (uint32_t)0 : 0u);
           const uint32_t s = t_claim(c, CONS, hit);
           if (c.err) return;
           if (hit) t_put(CONS, s, 0, is, ncons, 0, 0);

@@ -793,7 +793,7 @@ bool make_copy_job(const uint8_t* src, const uint32_t slo[3], const uint32_t shi
   return true;
 }
 
-// Closes the open wave (if any): later instructions that depend on it go to a new one.
+// Appends a copy job to level L's box-copy launch (its work units follow the level's earlier jobs).
 void add_copy(Pending& p, uint32_t L, const CopyJob& J) {
   LevelWork& w = p.at(L);
   CopyJob j = J;

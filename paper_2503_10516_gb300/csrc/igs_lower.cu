@@ -430,11 +430,6 @@ __device__ __forceinline__ uint32_t warp_or(uint32_t v) {
   for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(FULL, v, o);
   return v;
 }
-__device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-  return v;
-}
 __device__ __forceinline__ Bx warp_bbox(Bx b, bool valid) {
   Bx r;
 #pragma unroll
@@ -630,12 +625,10 @@ __device__ __noinline__ void t_set(Ctx& c, Table& t, uint32_t key, const Bx& r, 
 
 // Merges entries from index `from` on with equal key and values into
 // adjacent entries whose union is a box (keeps the tables small).
-// only_v0 != NONE: only entries whose first value is only_v0 take part.
-__device__ __noinline__ void t_merge_from(Ctx& c, Table& t, uint32_t from, uint32_t only_v0 = NONE) {
+__device__ __noinline__ void t_merge_from(Ctx& c, Table& t, uint32_t from) {
   DT_START(dt);
   DT_COUNT(N_MERGE, 1);
   for (uint32_t i = from; i < t.n; ++i) {
-    if (only_v0 != NONE && t_v(t, 0, i) != only_v0) continue;
     uint32_t cand = i;
     for (int guard = 0; guard < 4096; ++guard) {
       DT_COUNT(N_MERGE_PROBE, 1);

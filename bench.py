@@ -323,6 +323,22 @@ def _done(srv, ctxs, x, lat):
     return False
 
 
+def _max_over_ranks(torch, dist, x, device):
+    """The largest value of x over all ranks (x itself on one rank): a job's
+    time is its slowest rank's."""
+    if dist is None:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units every rank processed over the job's time
+    (replicas: each rank runs the same workload)."""
+    return units_per_rank * world / seconds
+
+
 def _nvtx(torch, name, push):
     """Marks the timed region for profilers (a no-op where NVTX is absent)."""
     try:
@@ -398,11 +414,8 @@ def run_gpu(args):
     instrs = int(ctxs[-1].counters()["instructions"])
     stats = [ctxs[args.warmup + i].stats() for i in range(args.steps)]
     counters = ctxs[-1].counters()
-    if dist is not None:
-        t = torch.tensor([dt], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
-    value = instrs * args.steps * world / dt
+    dt = _max_over_ranks(torch, dist, dt, "cuda")
+    value = _job_rate(instrs * args.steps, world, dt)
     lower_ms = statistics.mean(s["lower_ms"] for s in stats)
     copy_ms = statistics.mean(s["copy_ms"] for s in stats)
     work_ms = statistics.mean(s["workload_ms"] for s in stats)
@@ -453,8 +466,8 @@ def run_gpu(args):
             d2h += sum(int(v.nbytes) for v in g.values())
         c.close()
     barrier()
-    e2e_dt = time.perf_counter() - t0
-    e2e_value = instrs * e2e_steps * world / e2e_dt
+    e2e_dt = _max_over_ranks(torch, dist, time.perf_counter() - t0, "cuda")
+    e2e_value = _job_rate(instrs * e2e_steps, world, e2e_dt)
 
     # ---- roofline of the dominant kernel (algorithmic bytes / event-timed duration)
     peaks, src = _peaks()

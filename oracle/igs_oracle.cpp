@@ -22,8 +22,8 @@
 //   a8 dependencies, edge kinds ........ Fig. 5 legend; Sec. 3.6; Sec. 4.2
 //   a9 horizons / epochs ............... Sec. 3.5; Sec. 2.4
 //   debug checks ....................... Sec. 4.4 (uninitialized read, overlapping write)
-// The readings taken where the paper is silent are listed in the design doc
-// ("Readings of the paper"); each is marked below as [R<n>].
+// Where the paper is silent the rules take a fixed reading; each is marked
+// [R<n>] and stated in words where it is applied.
 //
 // Parity status: pinned against a per-element brute-force generator, graph
 // invariants, sequential execution and the paper's worked examples (tests/).

@@ -655,6 +655,12 @@ __device__ __noinline__ void t_merge_from(Ctx& c, Table& t, uint32_t from) {
   DT_LAP(dt, D_MERGE);
 }
 
+// Live entries above which an allocation's writer / reader table is
+// re-merged after an access (tunable at compile time).
+#ifndef IGS_MERGE_FLOOR
+#define IGS_MERGE_FLOOR 48
+#endif
+
 // Re-merges a heap table once its live entries exceed max(floor, twice the
 // count after its previous re-merge): fragmentation stays bounded while the
 // quadratic merge runs a logarithmic number of times as a table grows.
@@ -1485,7 +1491,7 @@ __device__ __noinline__ bool emit_apply(Ctx& c, const Acc* acc, int nacc, uint32
     }
     // re-merge only a table that has grown: keeps hot paths short and bounds
     // fragmentation between horizons
-    t_maybe_merge(c, RD, 48);
+    t_maybe_merge(c, RD, IGS_MERGE_FLOOR);
     (void)from;
   }
   for (int k = 0; k < nacc; ++k) {
@@ -1502,8 +1508,8 @@ __device__ __noinline__ bool emit_apply(Ctx& c, const Acc* acc, int nacc, uint32
       t_set(c, WR, NONE, q, id, 0, 0);
       if (c.err) return false;
     }
-    t_maybe_merge(c, WR, 48);
-    t_maybe_merge(c, RD, 48);
+    t_maybe_merge(c, WR, IGS_MERGE_FLOOR);
+    t_maybe_merge(c, RD, IGS_MERGE_FLOOR);
     (void)from;
   }
   return true;

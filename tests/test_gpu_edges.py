@@ -37,6 +37,41 @@ def _check(prog, mode=0):
     g.ctx.close()
 
 
+class _Staged:
+    """Batched adapter whose flush only submits the epoch (igs_run lowers)."""
+
+    def __init__(self, prog):
+        from paper_2503_10516_gb300 import igs
+        self.g = igs.GpuImpl(prog, mode=igs.MODE_BATCHED)
+        self.ctx = self.g.ctx
+
+    def __getattr__(self, name):
+        return getattr(self.g, name)
+
+    def flush(self):
+        self.ctx.submit_epoch()
+
+
+def _check_run(prog, window=3):
+    """The same through igs_run (lowering overlapped with execution)."""
+    ref, rej = oracle_graphs(prog)
+    s = _Staged(prog)
+    feed(s, prog)
+    s.ctx.run(window)
+    assert s.g.rejected() == rej
+    for n in range(prog.nodes):
+        assert_same_graph(s.g.graph(n), ref[n], f"{prog.name} node {n} (run)")
+    want, known = sequential_run(prog, set(rej))
+    gone = {op[1] for op in prog.ops if op[0] == "destroy"}
+    for b, buf in enumerate(prog.buffers):
+        if b in gone:
+            continue
+        got = s.ctx.read_buffer(b, (0, 0, 0), buf.extent, buf.elem_size)
+        k = known[b]
+        assert np.array_equal(got[k], want[b][k]), f"{prog.name}: buffer {b} differs (run)"
+    s.ctx.close()
+
+
 def _task(dims, rng, chunks, accs):
     return W.Task(dims, rng, chunks, W.K_GENERIC, accs)
 
@@ -46,6 +81,7 @@ def test_no_tasks():
     p = W.Program("empty", 2, 2, 4, 0, [("buffer", b), ("flush",)])
     _check(p)
     _check(p, mode=1)
+    _check_run(p)
 
 
 def test_one_element_buffers():
@@ -58,6 +94,7 @@ def test_one_element_buffers():
         ops.append(("task", _task(1, (1, 1, 1), 3, [W.Accessor(0, W.READ_WRITE, W.one_to_one())])))
     ops.append(("flush",))
     _check(W.Program("one-element", 2, 2, 2, 1, ops))
+    _check_run(W.Program("one-element", 2, 2, 2, 1, ops))
 
 
 def test_more_chunks_than_rows():
@@ -71,10 +108,12 @@ def test_more_chunks_than_rows():
                                                       W.Accessor(1, W.READ, W.neighborhood(1, 1))])))
     ops.append(("flush",))
     _check(W.Program("chunks>rows", 4, 2, 4, 2, ops))
+    _check_run(W.Program("chunks>rows", 4, 2, 4, 2, ops))
 
 
 def test_thirty_two_nodes():
     _check(W.wave_program(n=64, steps=6, nodes=32, devices=1, chunks=64, lookahead=2))
+    _check_run(W.wave_program(n=64, steps=6, nodes=32, devices=1, chunks=64, lookahead=2))
 
 
 def test_twenty_nine_devices():
@@ -82,6 +121,7 @@ def test_twenty_nine_devices():
     up-to-date masks is used."""
     _check(W.wave_program(n=58, steps=5, nodes=1, devices=29, chunks=29, lookahead=0))
     _check(W.wave_program(n=58, steps=5, nodes=2, devices=29, chunks=58, lookahead=3), mode=1)
+    _check_run(W.wave_program(n=58, steps=5, nodes=2, devices=29, chunks=58, lookahead=3))
 
 
 def test_eight_accessors():
@@ -97,6 +137,7 @@ def test_eight_accessors():
                                                       W.Accessor(7, W.READ, W.neighborhood(1, 1))])))
     ops.append(("flush",))
     _check(W.Program("eight-accessors", 3, 2, 3, 4, ops))
+    _check_run(W.Program("eight-accessors", 3, 2, 3, 4, ops))
 
 
 def test_empty_mapped_boxes():
@@ -110,6 +151,7 @@ def test_empty_mapped_boxes():
                                             W.Accessor(1, W.READ, W.all_mapper())])),
            ("flush",)]
     _check(W.Program("empty-boxes", 2, 2, 4, 0, ops))
+    _check_run(W.Program("empty-boxes", 2, 2, 4, 0, ops))
 
 
 def test_flush_between_phases():
@@ -123,3 +165,4 @@ def test_flush_between_phases():
     p.ops = ops
     _check(p)
     _check(p, mode=1)
+    _check_run(p, window=1)

@@ -241,9 +241,9 @@ int launch_lower(igs_ctx* c, uint32_t max_items = IGS_NONE, bool reserve = false
   if (c->server) return IGS_OK;  // the serving loop lowers it
   int r = upload_prog(c);
   if (r) return r;
-  // one task per launch: the launch is the latency, so helper warps share
-  // each node's kernel phase
-  const bool workers = c->cfg.mode == IGS_MODE_PLAIN && c->D > 1;
+  // one context's launch has few units (its nodes): helper warps share
+  // parts of each node's lowering (nodes with several devices)
+  const bool workers = c->D > 1;
   if (workers && (r = ensure_helpers(c))) return r;
   const size_t ev = c->timing ? ev_begin(c) : 0;
   if (igs_launch_lower(c->d_units, c->N, max_items, c->stream, reserve, progress, workers))

@@ -280,6 +280,12 @@ __global__ void __launch_bounds__(256) stencil_kernel(const KernelJob* __restric
   float* o = reinterpret_cast<float*>(O.ptr);
   const uint32_t groups = (x1 - x0 + 3) / 4;
   const uint64_t total = (uint64_t)(y1 - y0) * groups;
+  // 16-byte loads of the four columns when every row of every allocation
+  // starts on a 16-byte boundary at x0
+  const bool vec = ((x0 - U.lo[1]) % 4 == 0) && uw % 4 == 0 && ((x0 - O.lo[1]) % 4 == 0) && ow % 4 == 0 &&
+                   (!wave || (((x0 - P.lo[1]) % 4 == 0) && pw % 4 == 0)) &&
+                   ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(o) |
+                     (wave ? reinterpret_cast<uintptr_t>(pv) : 0u)) & 15u) == 0;
   for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t y = y0 + (uint32_t)(g / groups);
     const uint32_t xs = x0 + 4 * (uint32_t)(g % groups);
@@ -289,6 +295,38 @@ __global__ void __launch_bounds__(256) stencil_kernel(const KernelJob* __restric
     const float* pr = wave ? pv + (size_t)(y - P.lo[0]) * pw - P.lo[1] : nullptr;
     float* orow = o + (size_t)(y - O.lo[0]) * ow - O.lo[1];
     float out[4];
+    if (vec && xs + 4 <= x1) {
+      // the same arithmetic, in the same order, on registers
+      const float4 c4 = __ldcs(reinterpret_cast<const float4*>(ur + xs));
+      const float4 n4 = __ldcs(reinterpret_cast<const float4*>(urn + xs));
+      const float4 s4 = __ldcs(reinterpret_cast<const float4*>(urs + xs));
+      const float4 p4 = wave ? __ldcs(reinterpret_cast<const float4*>(pr + xs)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float cs[6] = {xs > 0 ? __ldcs(ur + xs - 1) : 0.f, c4.x, c4.y, c4.z, c4.w,
+                           xs + 4 < W ? __ldcs(ur + xs + 4) : 0.f};
+      const float ns[4] = {n4.x, n4.y, n4.z, n4.w}, ss[4] = {s4.x, s4.y, s4.z, s4.w},
+                  ps[4] = {p4.x, p4.y, p4.z, p4.w};
+      const bool row_in = y > 0 && y + 1 < H;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t x = xs + k;
+        const float c = cs[k + 1];
+        float v = c;
+        if (row_in && x > 0 && x + 1 < W) {
+          const float n = ns[k], s = ss[k], w = cs[k], e = cs[k + 2];
+          if (!wave) {
+            v = ((n + s) + (w + e)) * 0.25f;
+          } else {
+            const float t2 = (2.0f * c) - ps[k];
+            const float t5 = (n + s) + (w + e);
+            const float t8 = 0.25f * (t5 - 4.0f * c);
+            v = t2 + t8;
+          }
+        }
+        out[k] = v;
+      }
+      __stcs(reinterpret_cast<float4*>(orow + xs), make_float4(out[0], out[1], out[2], out[3]));
+      continue;
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const uint32_t x = xs + k;

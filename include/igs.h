@@ -79,6 +79,12 @@ enum igs_dependency_kind {
 
 #define IGS_MAX_ACCESSORS 8
 #define IGS_LOOKAHEAD_INFINITE 0xFFFFFFFFu
+/* lookahead value selecting the paper's horizon-count heuristic (Sec. 4.3):
+ * the queue of tasks held back by an allocating task is compiled once two
+ * horizons have been queued after the last task whose requirements neither a
+ * live allocation nor a queued task's requirement box covers (or at an epoch
+ * or a buffer destruction) */
+#define IGS_LOOKAHEAD_HORIZONS 0xFFFFFFFEu
 #define IGS_NONE 0xFFFFFFFFu
 
 /* lowering modes */
@@ -89,7 +95,8 @@ typedef struct igs_config {
   uint32_t num_nodes;        /* virtual nodes, 1..32 */
   uint32_t devices_per_node; /* virtual devices per node, 1..29 */
   uint32_t horizon_step;     /* a horizon after every k submitted tasks; 0 = none (Sec. 3.5) */
-  uint32_t lookahead;        /* scheduler lookahead window in tasks (Sec. 4.3); IGS_LOOKAHEAD_INFINITE */
+  uint32_t lookahead;        /* scheduler lookahead window in tasks (Sec. 4.3); IGS_LOOKAHEAD_INFINITE or
+                                IGS_LOOKAHEAD_HORIZONS */
   uint32_t mode;             /* IGS_MODE_PLAIN or IGS_MODE_BATCHED */
   uint32_t max_instructions; /* per node output capacity; 0 = default (1 << 18) */
   uint32_t max_edges;        /* per node; 0 = default (4 x max_instructions) */

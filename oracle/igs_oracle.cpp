@@ -357,6 +357,7 @@ struct Node {
   uint32_t epoch = 0, last_horizon = NONE, next_msg = 0;
   uint32_t lookahead = 0;
   std::deque<Item> queue;
+  uint32_t horizons_after_alloc = 0;  // horizon-count heuristic: horizons queued since the last allocating task
 };
 
 struct Ctx {
@@ -532,6 +533,24 @@ static std::vector<Req> requirements(const NodeTask& nt) {
 static bool allocating(const Node& n, const NodeTask& nt) {
   for (const Req& r : requirements(nt))
     if (find_alloc(n, r.buffer, r.mem, r.box) == NONE) return true;
+  return false;
+}
+
+// [R24] With the queue non-empty (horizon-count heuristic), a task is
+// allocating when one of its requirement boxes lies neither inside a live
+// allocation nor inside a requirement box of a queued task of the same
+// (buffer, memory): compiling the queue would not make room for it.
+static bool allocating_queued(const Node& n, const NodeTask& nt) {
+  for (const Req& r : requirements(nt)) {
+    if (find_alloc(n, r.buffer, r.mem, r.box) != NONE) continue;
+    bool covered = false;
+    for (const Item& q : n.queue) {
+      if (q.kind != I_TASK) continue;
+      for (const Req& x : requirements(q.nt))
+        if (x.buffer == r.buffer && x.mem == r.mem && contains(x.box, r.box)) covered = true;
+    }
+    if (!covered) return true;
+  }
   return false;
 }
 
@@ -851,22 +870,39 @@ static void flush_queue(Ctx& c, Node& n) {
 // Scheduler lookahead [R17]: a task is queued while any queued task is
 // allocating; the queue is compiled once it holds more than L tasks, or on an
 // epoch or a buffer destruction.
+// The horizon-count heuristic (Sec. 4.3 "Lookahead Heuristic") [R24], L =
+// LOOKAHEAD_HORIZONS: the queue is compiled once two horizons have been
+// queued after the last allocating task (allocating_queued), or on an epoch
+// or a destruction. Switching to it compiles a non-empty queue first.
+constexpr uint32_t LOOKAHEAD_HORIZONS = 0xFFFFFFFEu;
+
 static void deliver(Ctx& c, Node& n, Item it) {
   if (it.kind == I_LOOKAHEAD) {
+    if (it.arg == LOOKAHEAD_HORIZONS && !n.queue.empty()) flush_queue(c, n);
     n.lookahead = it.arg;
+    n.horizons_after_alloc = 0;
     if (!n.queue.empty() && queued_tasks(n) > n.lookahead) flush_queue(c, n);
     return;
   }
+  const bool horizons = n.lookahead == LOOKAHEAD_HORIZONS;
   if (n.queue.empty()) {
     if (it.kind == I_TASK && allocating(n, it.nt)) {
       n.queue.push_back(it);
-      if (queued_tasks(n) > n.lookahead) flush_queue(c, n);
+      n.horizons_after_alloc = 0;
+      if (!horizons && queued_tasks(n) > n.lookahead) flush_queue(c, n);
     } else {
       process(c, n, it, {});
     }
     return;
   }
   const bool force = it.kind == I_EPOCH || it.kind == I_DESTROY;
+  if (horizons) {
+    if (it.kind == I_TASK && allocating_queued(n, it.nt)) n.horizons_after_alloc = 0;
+    n.queue.push_back(it);
+    if (it.kind == I_HORIZON) n.horizons_after_alloc += 1;
+    if (force || n.horizons_after_alloc >= 2) flush_queue(c, n);
+    return;
+  }
   n.queue.push_back(it);
   if (force || queued_tasks(n) > n.lookahead) flush_queue(c, n);
 }

@@ -68,6 +68,7 @@ struct NodeDev {
   uint32_t status, err_info, cursor, lookahead, epoch, last_horizon, last_sync, next_msg, n_alloc;
   uint32_t n_instr, n_edge, n_box, n_bind, n_diag, n_rej;
   uint32_t q_head, q_count, qr_n, n_free, n_live, qr_live;
+  uint32_t q_hzn;  // horizon-count lookahead: horizons queued since the last allocating task
   uint64_t map_reads, map_writes, launches;
   uint64_t prof[32];   // clock cycles per lowering phase and detail counters (see the engine)
   // capacities

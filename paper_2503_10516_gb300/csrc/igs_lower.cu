@@ -165,7 +165,7 @@ struct Ctx {
   uint32_t node, N, D;
   uint32_t epoch, last_horizon, last_sync, next_msg, n_alloc, n_free, n_live, heap_top;
   uint32_t n_instr, n_edge, n_box, n_bind, n_diag, n_rej;
-  uint32_t lookahead, q_head, q_count;
+  uint32_t lookahead, q_head, q_count, q_hzn;
   Table qr;
   Table s[14];
   uint64_t map_reads, map_writes;
@@ -3300,6 +3300,57 @@ __device__ void enqueue(Ctx& c, uint32_t item) {
 
 __device__ void maintain(Ctx& c) { t_tidy(c, c.qr); }
 
+// Horizon-count lookahead (Sec. 4.3 "Lookahead Heuristic"). The requirement
+// boxes of every task queued in this mode are kept in the QR table (kind 4,
+// v1 = buffer * 32 + memory) until the task is compiled. A task is allocating
+// while the queue is non-empty when one of its requirement boxes lies neither
+// inside a live allocation nor inside a queued requirement box of the same
+// (buffer, memory).
+constexpr uint32_t QR_QUEUED_REQ = 4;
+
+__device__ bool covered_by_queued(const Ctx& c, uint32_t key, const Bx& b) {
+  for (uint32_t i = 0; i < c.qr.n; ++i)
+    if (t_key(c.qr, i) != DEAD && t_v(c.qr, 0, i) == QR_QUEUED_REQ && t_v(c.qr, 1, i) == key &&
+        bx_contains(t_box(c.qr, i), b))
+      return true;
+  return false;
+}
+
+__device__ __noinline__ bool allocating_queued(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH,
+                                                const Table& MP) {
+  Table& RQ = c.s[S_CL];
+  t_reset(RQ);
+  requirements(c, t, seq, CH, MP, RQ, NONE, 1);
+  if (c.err) return false;
+  for (uint32_t base = 0; base < RQ.n; base += 32) {
+    const uint32_t i = base + c.lane;
+    bool need = false;
+    if (i < RQ.n) {
+      const uint32_t key = t_key(RQ, i);
+      const Bx x = t_box(RQ, i);
+      need = !covered_by_alloc(c, key >> 5, key & 31u, x) && !covered_by_queued(c, key, x);
+    }
+    if (__ballot_sync(FULL, need)) return true;
+  }
+  return false;
+}
+
+// Appends a queued task's requirement boxes to its QR block.
+__device__ __noinline__ void record_queued_reqs(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH,
+                                                 const Table& MP) {
+  Table& RQ = c.s[S_CL];
+  t_reset(RQ);
+  requirements(c, t, seq, CH, MP, RQ, NONE, 1);
+  for (uint32_t base = 0; base < RQ.n && !c.err; base += 32) {
+    const uint32_t i = base + c.lane;
+    const bool in = i < RQ.n;
+    const uint32_t s = t_claim(c, c.qr, in);
+    if (c.err) return;
+    if (in) t_put(c.qr, s, seq, t_box(RQ, i), QR_QUEUED_REQ, t_key(RQ, i), 0);
+  }
+  __syncwarp();
+}
+
 // Scheduler lookahead (Sec. 4.3): a task is queued while an allocating task
 // is queued; the queue is compiled when it holds more than `lookahead` tasks,
 // at an epoch, or when a buffer is destroyed.
@@ -3308,7 +3359,10 @@ __device__ __noinline__ void deliver(Ctx& c, uint32_t item) {
   maintain(c);
   if (c.err) return;
   if (it.kind == IT_LOOKAHEAD) {
+    // switching to the horizon count compiles the queue first
+    if (it.arg == IGS_LOOKAHEAD_HORIZONS && c.q_count > 0) flush_queue(c);
     c.lookahead = it.arg;
+    c.q_hzn = 0;
     if (c.q_count > 0 && queued_tasks(c) > c.lookahead) flush_queue(c);
     return;
   }
@@ -3349,16 +3403,29 @@ __device__ __noinline__ void deliver(Ctx& c, uint32_t item) {
     if (c.err) return;
     pt_lap(pt, c, PH_A3);
     if (c.q_count == 0) alloc_now = allocating(c, t, it.seq, CH, MP);
+    else if (c.lookahead == IGS_LOOKAHEAD_HORIZONS) alloc_now = allocating_queued(c, t, it.seq, CH, MP);
     if (c.err) return;
     pt_lap(pt, c, PH_ALLOCATING);
   }
+  const bool horizons = c.lookahead == IGS_LOOKAHEAD_HORIZONS;
   if (c.q_count == 0) {
     if (alloc_now) {
       enqueue(c, item);
-      if (queued_tasks(c) > c.lookahead) flush_queue(c);
+      c.q_hzn = 0;
+      if (horizons) record_queued_reqs(c, c.pg->tasks[it.task], it.seq, c.s[S_CH], c.s[S_MP]);
+      else if (queued_tasks(c) > c.lookahead) flush_queue(c);
     } else {
       process(c, item);
     }
+  } else if (horizons) {
+    // compile once two horizons follow the last task the queue would not make room for
+    enqueue(c, item);
+    if (it.kind == IT_TASK) {
+      record_queued_reqs(c, c.pg->tasks[it.task], it.seq, c.s[S_CH], c.s[S_MP]);
+      if (alloc_now) c.q_hzn = 0;
+    }
+    if (it.kind == IT_HORIZON) c.q_hzn += 1;
+    if (it.kind == IT_EPOCH || it.kind == IT_DESTROY || c.q_hzn >= 2) flush_queue(c);
   } else {
     enqueue(c, item);
     if (it.kind == IT_EPOCH || it.kind == IT_DESTROY || queued_tasks(c) > c.lookahead) flush_queue(c);
@@ -3393,6 +3460,7 @@ __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg) {
   c.lookahead = nd->lookahead;
   c.q_head = nd->q_head;
   c.q_count = nd->q_count;
+  c.q_hzn = nd->q_hzn;
   c.qr.base = nd->qr_base;
   c.qr.n = nd->qr_n;
   c.qr.cap = nd->cap_qr;
@@ -3438,6 +3506,7 @@ __device__ void store_ctx(Ctx& c, uint32_t cursor) {
   nd->lookahead = c.lookahead;
   nd->q_head = c.q_head;
   nd->q_count = c.q_count;
+  nd->q_hzn = c.q_hzn;
   nd->qr_n = c.qr.n;
   nd->qr_live = c.qr.live;
   nd->map_reads += c.map_reads;

@@ -24,6 +24,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "OVERLAPPING_WRITE", -3: "CAPACITY", -4: "TRUNC
           -6: "CUDA", -7: "BUDGET", -8: "STATE"}
 MODE_PLAIN, MODE_BATCHED = 0, 1
 LOOKAHEAD_INFINITE = 0xFFFFFFFF
+LOOKAHEAD_HORIZONS = 0xFFFFFFFE  # the horizon-count heuristic (IGS_LOOKAHEAD_HORIZONS)
 
 EXPORTS = ("igs_create", "igs_destroy", "igs_create_buffer", "igs_destroy_buffer", "igs_submit_task",
            "igs_set_lookahead", "igs_flush", "igs_sync", "igs_fetch_instructions", "igs_rejected_tasks",

@@ -26,6 +26,11 @@ TASK_HDR = 11
 ACC_W = 14
 MAX_ACC = 8
 
+# Lookahead values: a task-count window, or the paper's horizon-count
+# heuristic (Sec. 4.3), or compile only at epochs.
+LOOKAHEAD_HORIZONS = 0xFFFFFFFE
+LOOKAHEAD_INFINITE = 0xFFFFFFFF
+
 MapDim = Tuple[int, int, int, int]  # (kind, a, b, c): 0 affine(k, offset, radius), 1 all, 2 fixed[a, b)
 
 
@@ -255,7 +260,7 @@ def nbody_example_program(n: int = 64, iterations: int = 4, lookahead: int = 0) 
 
 def random_program(seed: int, max_extent: int = 12, max_tasks: int = 10, allow_3d: bool = True,
                    allow_bad: bool = True, max_nodes: int = 3, max_devices: int = 2,
-                   uninit_reads: bool = False) -> Program:
+                   uninit_reads: bool = False, horizon_lookahead: bool = False) -> Program:
     """A small random program over all mapper kinds.
 
     Writes go through one_to_one or transposed mappers only (injective), and a
@@ -270,6 +275,8 @@ def random_program(seed: int, max_extent: int = 12, max_tasks: int = 10, allow_3
     devices = int(rng.integers(1, max_devices + 1))
     hstep = int(rng.integers(1, 5))
     look = int(rng.choice([0, 0, 1, 2, 4, 0xFFFFFFFF]))
+    if horizon_lookahead:
+        look = int(rng.choice([LOOKAHEAD_HORIZONS, LOOKAHEAD_HORIZONS, 0, 2]))
     ops = []
     bufs: List[Buffer] = []
     written = []
@@ -291,7 +298,8 @@ def random_program(seed: int, max_extent: int = 12, max_tasks: int = 10, allow_3
             ops.append(("flush",))
             continue
         if r < 0.08:
-            ops.append(("lookahead", int(rng.choice([0, 1, 3, 0xFFFFFFFF]))))
+            choices = [0, 1, 3, 0xFFFFFFFF] + ([LOOKAHEAD_HORIZONS] * 3 if horizon_lookahead else [])
+            ops.append(("lookahead", int(rng.choice(choices))))
             continue
         # pick the written buffer
         wb = int(rng.integers(0, len(bufs)))

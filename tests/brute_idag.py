@@ -14,6 +14,7 @@ import numpy as np
 NONE = 0xFFFFFFFF
 REMOTE = 0xFFFFFFFE
 HOST = 0xFFFFFFFE
+LOOKAHEAD_HORIZONS = 0xFFFFFFFE  # lookahead value selecting the horizon-count heuristic
 EPOCH, HORIZON, ALLOC, FREE, COPY, SEND, RECEIVE, SPLIT_RECEIVE, AWAIT_RECEIVE, KERNEL = range(10)
 K_DATAFLOW, K_ANTI, K_ALLOC, K_EPOCH, K_FRONT = 1, 2, 4, 8, 16
 M_READ, M_WRITE = 1, 2
@@ -131,6 +132,7 @@ class BruteNode:
         self.next_msg = 0
         self.lookahead = lookahead
         self.queue = []
+        self.h_after = 0   # horizons queued since the last allocating task
         self.allocs = []   # dicts
         self.bstate = {}   # buffer -> (prod, pmem, mask) int64 arrays
 
@@ -161,7 +163,10 @@ class Brute:
 
     def set_lookahead(self, L):
         for n in self.nodes:
+            if L == LOOKAHEAD_HORIZONS and n.queue:
+                self._flush(n)
             n.lookahead = L
+            n.h_after = 0
             if n.queue and self._queued(n) > n.lookahead:
                 self._flush(n)
 
@@ -262,13 +267,26 @@ class Brute:
             self._process(n, it, look)
 
     def _deliver(self, n, it):
+        horizons = n.lookahead == LOOKAHEAD_HORIZONS
         if not n.queue:
             if it["kind"] == "task" and self._allocating(n, it["nt"]):
                 n.queue.append(it)
-                if self._queued(n) > n.lookahead:
+                n.h_after = 0
+                if not horizons and self._queued(n) > n.lookahead:
                     self._flush(n)
             else:
                 self._process(n, it, [])
+            return
+        if horizons:
+            # compile once two horizons follow the last task that the queue
+            # would not make room for
+            if it["kind"] == "task" and self._allocating_queued(n, it["nt"]):
+                n.h_after = 0
+            n.queue.append(it)
+            if it["kind"] == "horizon":
+                n.h_after += 1
+            if it["kind"] in ("epoch", "destroy") or n.h_after >= 2:
+                self._flush(n)
             return
         n.queue.append(it)
         if it["kind"] in ("epoch", "destroy") or self._queued(n) > n.lookahead:
@@ -296,6 +314,15 @@ class Brute:
 
     def _allocating(self, n, nt):
         return any(self._find_alloc(n, b, m, mk) is None for b, m, mk in self._reqs(nt))
+
+    def _allocating_queued(self, n, nt):
+        queued = [r for q in n.queue if q["kind"] == "task" for r in self._reqs(q["nt"])]
+        for b, m, mk in self._reqs(nt):
+            if self._find_alloc(n, b, m, mk) is not None:
+                continue
+            if not any(qb == b and qm == m and not (mk & ~qmk).any() for qb, qm, qmk in queued):
+                return True
+        return False
 
     # -- emission --
     def _emit(self, n, rec, masks, accesses, extra, binds=None):

@@ -205,3 +205,53 @@ def test_split_receive_when_consumers_differ():
     kinds = [int(r[1]) for r in g["instrs"]]
     assert kinds.count(SPLIT_RECEIVE) == 1
     assert kinds.count(AWAIT_RECEIVE) == 2
+
+
+def _emitted_after_each_task(p):
+    """Node 0's instruction count after every submitted task (lowering as it
+    happens, not only at the end)."""
+    import oracle
+    o = oracle.Oracle(p.nodes, p.devices, p.horizon_step, p.lookahead)
+    seen = []
+    for op in p.ops:
+        if op[0] == "buffer":
+            b = op[1]
+            o.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init is not None)
+        elif op[0] == "task":
+            o.submit(op[1].flat())
+            seen.append(len(o.graph(0)["instrs"]))
+        elif op[0] == "flush":
+            o.flush()
+    g = o.graph(0)
+    o.close()
+    return seen, g
+
+
+def test_horizon_heuristic_never_flushes_growing_rows():
+    """Sec. 4.3: with requirements growing every step the horizon-count
+    heuristic never flushes the queue before the end, so no allocation is
+    ever resized (the RSim case, Sec. 5)."""
+    p = W.growing_program(rows_max=96, cols=4, grow=(1, 6), devices=2, chunks=2, lookahead=W.LOOKAHEAD_HORIZONS)
+    seen, g = _emitted_after_each_task(p)
+    assert all(x == 1 for x in seen), "instructions were generated before the end"
+    assert not any(r[1] == FREE for r in g["instrs"])
+    assert not any(r[1] == COPY and r[6] == 1 for r in g["instrs"])
+
+
+def test_horizon_heuristic_flushes_stable_patterns():
+    """Sec. 4.3: once the access pattern is steady, two horizons after the
+    last allocating task compile the queue (concurrency is kept), and the
+    allocations made then cover what the queue saw: no resize."""
+    p = W.wave_program(n=32, steps=24, nodes=2, devices=2, chunks=8, lookahead=W.LOOKAHEAD_HORIZONS, horizon_step=4)
+    seen, g = _emitted_after_each_task(p)
+    first = next(i for i, x in enumerate(seen) if x > 1)
+    # the rotating buffers' halos make tasks 1-3 allocating; horizons follow
+    # tasks 4 and 8, so the queue is compiled with the horizon after task 8
+    # (index 7): one horizon too few would compile after task 4, one too many
+    # after task 12
+    assert first == 7
+    assert all(x > 1 for x in seen[first:])
+    assert not any(r[1] == FREE for r in g["instrs"])
+    _, ref = _emitted_after_each_task(W.wave_program(n=32, steps=24, nodes=2, devices=2, chunks=8,
+                                                     lookahead=W.LOOKAHEAD_INFINITE, horizon_step=4))
+    assert sum(1 for r in g["instrs"] if r[1] == ALLOC) == sum(1 for r in ref["instrs"] if r[1] == ALLOC)

@@ -37,3 +37,19 @@ def test_random_programs_uninitialized_reads(seed):
 ], ids=lambda p: f"{p.name}-L{p.lookahead}")
 def test_paper_shaped_programs(prog):
     _check(prog)
+
+
+@pytest.mark.parametrize("seed", range(150))
+def test_random_programs_horizon_lookahead(seed):
+    """The horizon-count lookahead heuristic (Sec. 4.3), switched on and off
+    within programs, in both generators."""
+    _check(W.random_program(200_000 + seed, max_extent=10, max_tasks=12, horizon_lookahead=True))
+
+
+@pytest.mark.parametrize("prog", [
+    W.growing_program(rows_max=40, cols=4, grow=(1, 5), lookahead=W.LOOKAHEAD_HORIZONS),
+    W.wave_program(n=16, steps=14, nodes=2, devices=2, chunks=8, lookahead=W.LOOKAHEAD_HORIZONS),
+    W.listing2_program(8, W.LOOKAHEAD_HORIZONS, devices=2, chunks=2),
+], ids=lambda p: p.name)
+def test_paper_shaped_programs_horizon_lookahead(prog):
+    _check(prog)

@@ -314,6 +314,56 @@ def measure_box_copy(igs, torch, stream, reps=20):
     return out
 
 
+def measure_lookahead(igs):
+    """Scheduler lookahead policies (Sec. 4.3) on a growing-row stream (the
+    RSim pattern, 2048 x 1024 fp32, rows appended 1-64 at a time, 2 devices)
+    and on the steady wave pattern (64 tasks of the benchmark program's
+    shape): allocations, resize copies, and how many tasks were submitted
+    before the first instruction existed (one task per launch, counted after
+    every submission)."""
+    progs = {"growing_rows": W.growing_program(rows_max=2048, cols=1024, grow=(1, 64), devices=2, chunks=2,
+                                               seed=500),
+             "wave_steady": W.wave_program(n=8, steps=64, nodes=NODES, devices=DEVICES, chunks=CHUNKS)}
+    for op in progs["wave_steady"].ops:
+        if op[0] == "buffer":
+            op[1].extent = (N, N, 1)
+            if op[1].init is not None:
+                op[1].init = np.zeros((N, N), np.float32)
+        elif op[0] == "task":
+            op[1].range = (N, N, 1)
+    out = {}
+    for name, p in progs.items():
+        res = {}
+        for label, L in (("L0", 0), ("L8", 8), ("horizons", W.LOOKAHEAD_HORIZONS), ("infinite", W.LOOKAHEAD_INFINITE)):
+            c = igs.Context(p.nodes, p.devices, p.horizon_step, L, mode=igs.MODE_PLAIN)
+            c.set_timing(True)
+            first = None
+            k = 0
+            for op in p.ops:
+                if op[0] == "buffer":
+                    b = op[1]
+                    c.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init)
+                elif op[0] == "task":
+                    c.submit(op[1])
+                    k += 1
+                    if first is None and int(c.counters()["instructions"]) > p.nodes:
+                        first = k
+                elif op[0] == "flush":
+                    c.submit_epoch()
+            c.sync()
+            g = c.graph(0)
+            t = g["instrs"][:, 1]
+            res[label] = {"allocs_node0": int((t == 2).sum()),
+                          "resize_copies_node0": int(((t == 4) & (g["instrs"][:, 6] == 1)).sum()),
+                          "instructions": int(c.counters()["instructions"]),
+                          "tasks_before_first_instruction": first if first is not None else k,
+                          "lower_ms": c.stats()["lower_ms"]}
+            c.close()
+        res["tasks"] = len(p.tasks)
+        out[name] = res
+    return out
+
+
 def _done(srv, ctxs, x, lat):
     i, want, t0 = x
     _, taken, _ = srv.progress(ctxs[i])
@@ -492,6 +542,7 @@ def run_gpu(args):
 
     # ---- batched lowering of many programs, served lowering of many streams
     big_copy = measure_box_copy(igs, torch, stream)
+    lookahead = measure_lookahead(igs) if world == 1 else None
     batched = measure_batched(igs, torch, sh) if world == 1 else None
     served = {f"{int(r)}_per_s": measure_served(igs, torch, sh, rate=r) for r in (1e4, 1e5)} \
         if world == 1 else None
@@ -531,6 +582,7 @@ def run_gpu(args):
             "box_copy_gbs": (copy_bytes / (copy_ms * 1e-3) / 1e9) if copy_ms else None,
             "box_copy_resize_512MiB": {k: dict(v, frac=v["gbs"] / hbm) for k, v in big_copy.items()},
             "batched_programs": batched,
+            "lookahead": lookahead,
             "served": served,
             "clocks": clocks.summary(),
             "cpu_baseline": cpu,

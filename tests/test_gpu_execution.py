@@ -117,3 +117,12 @@ def test_pipelined_random(seed):
 ], ids=lambda p: f"{p.name}-L{p.lookahead}")
 def test_pipelined_paper_shaped(prog, window):
     _run_pipelined(prog, window)
+
+
+@pytest.mark.parametrize("prog", [
+    W.growing_program(rows_max=128, cols=32, grow=(1, 16), devices=2, chunks=2, lookahead=W.LOOKAHEAD_HORIZONS),
+    W.wave_program(n=64, steps=20, nodes=4, devices=4, chunks=64, lookahead=W.LOOKAHEAD_HORIZONS),
+], ids=lambda p: p.name)
+def test_pipelined_horizon_lookahead(prog):
+    _run_pipelined(prog, window=4)
+    _run(prog)

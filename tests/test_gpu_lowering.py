@@ -109,3 +109,20 @@ def test_nbody_1m_full_config():
     p = W.nbody_program(n=8, steps=200, nodes=8, devices=4, chunks=128, lookahead=4)
     _shape_only(p, (n, 1, 1), (n, 1, 1))
     _check_full(p, lambda b: np.zeros((n, 4), np.float32))
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_random_programs_horizon_lookahead(seed):
+    """The horizon-count lookahead heuristic (Sec. 4.3) on the GPU."""
+    p = W.random_program(200_000 + seed, max_extent=10, max_tasks=12, horizon_lookahead=True)
+    _check(p, mode=seed % 2)
+
+
+@pytest.mark.parametrize("prog", [
+    W.growing_program(rows_max=64, cols=8, grow=(1, 6), devices=2, chunks=2, lookahead=W.LOOKAHEAD_HORIZONS),
+    W.wave_program(n=64, steps=24, nodes=4, devices=4, chunks=64, lookahead=W.LOOKAHEAD_HORIZONS),
+    W.nbody_program(n=256, steps=6, nodes=8, devices=4, chunks=128, lookahead=W.LOOKAHEAD_HORIZONS),
+], ids=lambda p: p.name)
+def test_paper_shaped_horizon_lookahead(prog):
+    _check(prog)
+    _check(prog, mode=1)

@@ -161,10 +161,34 @@ def _stage_ctx(igs, prog, mode, stream):
 
 def measure_batched(igs, torch, stream, count=512, scale=0.01):
     """Uneven programs (1-8 buffers of 2^10-2^24 elements, 1-128 chunks, 2-32
-    memories, lookahead 0-16; task counts scaled down): one persistent launch
-    over all of them vs one task per launch."""
+    memories, lookahead 0-16; task counts scaled down): one launch over all
+    of them vs one task per launch. The batch shape is picked first by
+    timing every candidate on a fresh copy of the batch."""
     progs = W.batch_programs(count=count, scale=scale, seed=0x5EED + 3)
     res = {}
+
+    def staged():
+        ctxs = [_stage_ctx(igs, p, igs.MODE_BATCHED, stream) for p in progs]
+        for p, c in zip(progs, ctxs):
+            for op in p.ops:
+                if op[0] == "task":
+                    c.submit(op[1])
+                elif op[0] == "flush":
+                    c.submit_epoch()
+        return ctxs
+
+    def timer():
+        torch.cuda.synchronize()
+        return time.perf_counter()
+
+    # the batch shape (one block per unit, or a work queue of persistent
+    # blocks in submission / longest-first order) is picked by timing
+    units = sum(p.nodes for p in progs)
+    t_tune = time.perf_counter()
+    cands = igs.batch_shape_candidates(units, torch.cuda.get_device_properties(0).multi_processor_count)
+    shape, times = igs.tune_lower_batch(staged, cands, timer)
+    res["tuning"] = {"units": units, "seconds": time.perf_counter() - t_tune, "chosen": shape,
+                     "launch_seconds": [{"shape": s, "seconds": t} for s, t in times]}
     for mode_name, mode in (("plain", igs.MODE_PLAIN), ("batched", igs.MODE_BATCHED)):
         ctxs = [_stage_ctx(igs, p, mode, stream) for p in progs]
         torch.cuda.synchronize()
@@ -176,7 +200,7 @@ def measure_batched(igs, torch, stream, count=512, scale=0.01):
                 elif op[0] == "flush":
                     c.submit_epoch()
         if mode == igs.MODE_BATCHED:
-            igs.lower_batch(ctxs)
+            igs.lower_batch(ctxs, shape)
         else:
             for c in ctxs:
                 c.sync()
@@ -185,6 +209,11 @@ def measure_batched(igs, torch, stream, count=512, scale=0.01):
         instrs = sum(int(c.counters()["instructions"]) for c in ctxs)
         launches = sum(int(c.counters()["launches"]) for c in ctxs)
         res[mode_name] = {"instr_per_s": instrs / dt, "seconds": dt, "instructions": instrs, "launches": launches}
+        if mode == igs.MODE_BATCHED:
+            # the longest unit bounds the launch: the slowest program's mean
+            # per-node lowering time (SM cycles at the sampled clock)
+            cyc = max(c.profile()["total"] / p.nodes for p, c in zip(progs, ctxs))
+            res[mode_name]["slowest_program_node_cycles"] = cyc
         for c in ctxs:
             c.close()
     res["programs"] = count

@@ -257,6 +257,31 @@ int igs_read_buffer(igs_ctx* ctx, uint32_t buffer, const uint32_t lo[3], const u
  * contexts must share a device). Waits for completion. */
 int igs_lower_batch(igs_ctx* const* ctxs, uint32_t n);
 
+/* Batched lowering shapes. persistent_blocks = 0: one block per (program,
+ * node) unit, as igs_lower_batch (the other fields are ignored). Otherwise
+ * that many persistent blocks of `warps` warps (1..8; 0 counts as 1) take
+ * units from a device work queue, in the order `order` gives:
+ * IGS_ORDER_SUBMISSION (contexts, then nodes) or IGS_ORDER_LONGEST_FIRST
+ * (estimated pending work, descending; the host estimates it as pending
+ * submissions plus chunk-accessor pairs per node). With warps > 1 the
+ * `helped` heaviest contexts that have several devices per node get helper
+ * scratch (about 4.5 KiB per scratch entry of every node, kept until the
+ * context is destroyed), and the block's other warps share the per-device
+ * and per-buffer phases of those contexts' nodes; other nodes are lowered by
+ * the first warp alone. The graphs do not depend on the shape; the binding's
+ * tune_lower_batch picks a shape by timing candidates on copies of a batch.
+ * IGS_ERR_INVALID_ARG for an unknown order or more than 8 warps. Waits for
+ * completion. */
+#define IGS_ORDER_SUBMISSION 0u
+#define IGS_ORDER_LONGEST_FIRST 1u
+typedef struct igs_batch_shape {
+  uint32_t persistent_blocks;
+  uint32_t order;
+  uint32_t warps;
+  uint32_t helped;
+} igs_batch_shape;
+int igs_lower_batch_shaped(igs_ctx* const* ctxs, uint32_t n, const igs_batch_shape* shape);
+
 /* ---- served lowering ------------------------------------------------------
  * A device-resident request loop (one persistent kernel, one warp per slot =
  * one node of one attached context) lowers submissions of many concurrent

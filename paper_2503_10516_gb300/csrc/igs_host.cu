@@ -629,27 +629,75 @@ int igs_flush(igs_ctx* c) {
   return check_status(c);
 }
 
-int igs_lower_batch(igs_ctx* const* ctxs, uint32_t n) {
+int igs_lower_batch(igs_ctx* const* ctxs, uint32_t n) { return igs_lower_batch_shaped(ctxs, n, nullptr); }
+
+int igs_lower_batch_shaped(igs_ctx* const* ctxs, uint32_t n, const igs_batch_shape* shape) {
   if (!ctxs || n == 0) return IGS_ERR_INVALID_ARG;
   igs_ctx* c = ctxs[0];
+  if (shape && (shape->order > IGS_ORDER_LONGEST_FIRST || shape->warps > kMaxWorkers))
+    return fail_ctx(c, IGS_ERR_INVALID_ARG, "bad batch shape");
+  const bool queue = shape && shape->persistent_blocks;
+  const uint32_t warps = queue && shape->warps > 1 ? shape->warps : 1;
   std::vector<Unit> units;
+  std::vector<double> work;  // estimated work per unit: pending items plus chunk-accessor pairs per node
+  std::vector<std::pair<double, uint32_t>> heavy;  // (work, context) of contexts with several devices
   for (uint32_t i = 0; i < n; ++i)
     if (!ctxs[i] || ctxs[i]->server) return fail_ctx(ctxs[i], IGS_ERR_STATE, "a served context cannot be batch-lowered");
   for (uint32_t i = 0; i < n; ++i) {
-    int r = upload_prog(ctxs[i]);
+    igs_ctx* x = ctxs[i];
+    int r = upload_prog(x);
     if (r) return r;
-    if (cudaStreamSynchronize(ctxs[i]->stream) != cudaSuccess) return IGS_ERR_CUDA;
-    for (uint32_t k = 0; k < ctxs[i]->N; ++k) units.push_back(Unit{ctxs[i]->d_nodes + k, ctxs[i]->d_prog});
+    if (cudaStreamSynchronize(x->stream) != cudaSuccess) return IGS_ERR_CUDA;
+    double w = 0;
+    for (size_t k = x->nodes_host[0].cursor; k < x->items.size(); ++k) {
+      w += 1;
+      if (x->items[k].kind == IT_TASK) {
+        const igs_task& t = x->tasks[x->items[k].task];
+        w += (double)t.num_chunks * t.num_accessors / x->N;
+      }
+    }
+    for (uint32_t k = 0; k < x->N; ++k) {
+      units.push_back(Unit{x->d_nodes + k, x->d_prog});
+      work.push_back(w);
+    }
+    if (x->D > 1) heavy.push_back({w, i});
+  }
+  if (warps > 1 && shape->helped) {
+    std::stable_sort(heavy.begin(), heavy.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    for (size_t h = 0; h < heavy.size() && h < shape->helped; ++h) {
+      int r = ensure_helpers(ctxs[heavy[h].second]);
+      if (r) return r;
+    }
   }
   static thread_local Unit* d_units = nullptr;
+  static thread_local uint32_t* d_order = nullptr;  // followed by the queue head
   static thread_local size_t cap_units = 0;
   if (units.size() > cap_units) {
     if (d_units) cudaFree(d_units);
+    if (d_order) cudaFree(d_order);
+    d_units = nullptr;
+    d_order = nullptr;
     cap_units = units.size() * 2;
-    if (cudaMalloc(&d_units, sizeof(Unit) * cap_units) != cudaSuccess) return fail_ctx(c, IGS_ERR_CUDA, "alloc units");
+    if (cudaMalloc(&d_units, sizeof(Unit) * cap_units) != cudaSuccess ||
+        cudaMalloc(&d_order, sizeof(uint32_t) * (cap_units + 1)) != cudaSuccess)
+      return fail_ctx(c, IGS_ERR_CUDA, "alloc units");
   }
   CK(cudaMemcpyAsync(d_units, units.data(), sizeof(Unit) * units.size(), cudaMemcpyHostToDevice, c->stream));
-  if (igs_launch_lower(d_units, (uint32_t)units.size(), IGS_NONE, c->stream)) return fail_ctx(c, IGS_ERR_CUDA, "batch launch");
+  const uint32_t nu = (uint32_t)units.size();
+  if (queue) {
+    // the device work queue: unit order, then the head the blocks advance
+    std::vector<uint32_t> order(nu + 1);
+    for (uint32_t u = 0; u < nu; ++u) order[u] = u;
+    if (shape->order == IGS_ORDER_LONGEST_FIRST)
+      std::stable_sort(order.begin(), order.begin() + nu, [&](uint32_t a, uint32_t b) { return work[a] > work[b]; });
+    order[nu] = 0;
+    CK(cudaMemcpyAsync(d_order, order.data(), sizeof(uint32_t) * (nu + 1), cudaMemcpyHostToDevice, c->stream));
+    const uint32_t blocks = std::min(shape->persistent_blocks, nu);
+    if (igs_launch_lower_queue(d_units, nu, d_order, d_order + nu, blocks, warps, c->stream))
+      return fail_ctx(c, IGS_ERR_CUDA, "batch launch");
+  } else if (igs_launch_lower(d_units, nu, IGS_NONE, c->stream)) {
+    return fail_ctx(c, IGS_ERR_CUDA, "batch launch");
+  }
   CK(cudaStreamSynchronize(c->stream));
   for (uint32_t i = 0; i < n; ++i) {
     ctxs[i]->launches++;

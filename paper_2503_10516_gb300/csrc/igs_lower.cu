@@ -3538,7 +3538,7 @@ __device__ void lower_unit(const Unit* units, uint32_t n_units, uint32_t max_ite
   const Unit u = units[w];
   Ctx c;
   load_ctx(c, u.node, u.prog);
-  if (sh) {
+  if (sh && c.nd->helper_scratch) {  // nodes without helper scratch lower alone
     c.lock = &sh->lock;
     c.block = sh;
     c.workers = workers;
@@ -3584,6 +3584,46 @@ __global__ void __launch_bounds__(kReserveThreads) lower_kernel(const Unit* unit
       }
       __syncwarp();
       worker_bar(workers);  // the helpers leave their loop
+    }
+  } else if (warp < workers) {
+    helper_loop(sh, warp, workers);
+  }
+  __syncthreads();
+}
+
+// Batched lowering with a device work queue: the first warp of each
+// persistent block takes the next unit (a node of one program) from *head, in
+// the order `order` gives (longest estimated work first, say), until every
+// unit is lowered. The block's other warps (if any) help with the shared
+// phases of units whose node has helper scratch, and wait at the block
+// barrier otherwise.
+__global__ void __launch_bounds__(32 * kMaxWorkers) lower_queue_kernel(const Unit* units, uint32_t n_units,
+                                                                      const uint32_t* order, uint32_t* head) {
+  __shared__ BlockShared sh;
+  const uint32_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t workers = nw < kMaxWorkers ? nw : kMaxWorkers;
+  if (threadIdx.x == 0) {
+    sh.lock = 0;
+    sh.cmd = CMD_NONE;
+    sh.err = ST_OK;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (;;) {
+      uint32_t u = 0;
+      __syncwarp();
+      if ((threadIdx.x & 31u) == 0) u = atomicAdd(head, 1u);
+      u = __shfl_sync(FULL, u, 0);
+      if (u >= n_units) break;
+      lower_unit(units, n_units, NONE, order ? order[u] : u, nullptr, workers > 1 ? &sh : nullptr, workers);
+    }
+    if (workers > 1) {
+      if ((threadIdx.x & 31u) == 0) {
+        sh.cmd = CMD_EXIT;
+        __threadfence_block();
+      }
+      __syncwarp();
+      worker_bar(workers);
     }
   } else if (warp < workers) {
     helper_loop(sh, warp, workers);
@@ -3702,6 +3742,19 @@ int igs_launch_serve(igs::ServeSlot* slots, uint32_t n_slots, volatile uint32_t*
     carveout = true;
   }
   igs::serve_kernel<<<n_slots, 32, 0, (cudaStream_t)stream>>>(slots, n_slots, stop, idle_polls);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int igs_launch_lower_queue(const igs::Unit* units_dev, uint32_t n_units, const uint32_t* order_dev, uint32_t* head_dev,
+                           uint32_t blocks, uint32_t warps, void* stream) {
+  if (warps < 1 || warps > igs::kMaxWorkers) return -1;
+  if (n_units == 0) return 0;
+  static bool carveout = false;
+  if (!carveout) {
+    cudaFuncSetAttribute(igs::lower_queue_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    carveout = true;
+  }
+  igs::lower_queue_kernel<<<blocks, 32 * warps, 0, (cudaStream_t)stream>>>(units_dev, n_units, order_dev, head_dev);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from typing import Optional, Sequence
+from typing import Callable, List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -31,7 +31,8 @@ EXPORTS = ("igs_create", "igs_destroy", "igs_create_buffer", "igs_destroy_buffer
            "igs_execute", "igs_read_buffer", "igs_lower_batch", "igs_counters", "igs_last_error", "igs_box_copy",
            "igs_set_timing", "igs_stats", "igs_profile", "igs_lower_static", "igs_submit_epoch",
            "igs_serve_create", "igs_serve_destroy", "igs_serve_attach", "igs_serve_start", "igs_serve_progress",
-           "igs_serve_detach", "igs_serve_stop", "igs_run")
+           "igs_serve_detach", "igs_serve_stop", "igs_run", "igs_lower_batch_shaped")
+ORDER_SUBMISSION, ORDER_LONGEST_FIRST = 0, 1  # IGS_ORDER_*
 
 
 class IgsError(RuntimeError):
@@ -92,6 +93,11 @@ class CopyJob(ctypes.Structure):
                 ("box", Box), ("elem_size", ctypes.c_uint32)]
 
 
+class BatchShape(ctypes.Structure):
+    _fields_ = [("persistent_blocks", ctypes.c_uint32), ("order", ctypes.c_uint32), ("warps", ctypes.c_uint32),
+                ("helped", ctypes.c_uint32)]
+
+
 _lib = None
 
 
@@ -127,6 +133,7 @@ def lib():
         L.igs_execute.argtypes = [vp, u32]
         L.igs_read_buffer.argtypes = [vp, u32, P32, P32, vp]
         L.igs_lower_batch.argtypes = [ctypes.POINTER(vp), u32]
+        L.igs_lower_batch_shaped.argtypes = [ctypes.POINTER(vp), u32, ctypes.POINTER(BatchShape)]
         L.igs_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         L.igs_last_error.argtypes = [vp]
         L.igs_last_error.restype = ctypes.c_char_p
@@ -348,11 +355,62 @@ class Server:
             pass
 
 
-def lower_batch(ctxs: Sequence[Context]):
+def lower_batch(ctxs: Sequence[Context], shape: Optional[Tuple[int, ...]] = None):
+    """One launch over the pending submissions of every context. shape =
+    (persistent_blocks, order[, warps[, helped]]) takes the device work queue
+    (igs_batch_shape); None or blocks 0: one block per (program, node)."""
     arr = (ctypes.c_void_p * len(ctxs))(*[c.handle.value for c in ctxs])
-    r = lib().igs_lower_batch(arr, len(ctxs))
+    if shape is None:
+        r = lib().igs_lower_batch(arr, len(ctxs))
+    else:
+        f = list(shape) + [0] * (4 - len(shape))
+        s = BatchShape(*[int(v) for v in f])
+        r = lib().igs_lower_batch_shaped(arr, len(ctxs), ctypes.byref(s))
     if r not in (IGS_OK, -2):
         raise IgsError(r, "lower_batch: " + lib().igs_last_error(ctxs[0].handle).decode())
+
+
+def batch_shape_candidates(n_units: int, sms: int) -> List[Optional[Tuple[int, int, int, int]]]:
+    """Shapes worth timing for a batch of n_units (program, node) units on a
+    GPU with `sms` SMs: one block per unit; work queues of 1-8 one-warp
+    blocks per SM in longest-first order, and 1 and 4 per SM in submission
+    order; 1-4 blocks per SM of 4 and 8 warps whose helpers serve the 8 to
+    128 heaviest multi-device programs. Never more blocks than units."""
+    out: List[Optional[Tuple[int, int, int, int]]] = [None]
+
+    def add(per_sm, order, warps, helped):
+        g = min(n_units, per_sm * sms)
+        if (g, order, warps, helped) not in out:
+            out.append((g, order, warps, helped))
+
+    for per_sm in (1, 2, 4, 8):
+        add(per_sm, ORDER_LONGEST_FIRST, 1, 0)
+    for per_sm in (1, 4):
+        add(per_sm, ORDER_SUBMISSION, 1, 0)
+    for per_sm, warps, helped in ((1, 4, 8), (2, 4, 32), (2, 8, 32), (2, 4, 128), (4, 4, 64), (4, 2, 128)):
+        add(per_sm, ORDER_LONGEST_FIRST, warps, helped)
+    return out
+
+
+def tune_lower_batch(make_batch: Callable[[], Sequence[Context]], candidates: Sequence[Optional[Tuple[int, int]]],
+                     timer: Callable[[], float], repeats: int = 1):
+    """Picks a batch shape by timing: for every candidate, make_batch() stages
+    a fresh copy of the batch (identical pending submissions) and one
+    lower_batch launch over it is timed with timer() (which must synchronise
+    the device). Returns (best shape, [(shape, seconds), ...]); each
+    candidate's time is its fastest of `repeats` copies."""
+    times = []
+    for shape in candidates:
+        best = float("inf")
+        for _ in range(repeats):
+            ctxs = make_batch()
+            t0 = timer()
+            lower_batch(ctxs, shape)
+            best = min(best, timer() - t0)
+            for c in ctxs:
+                c.close()
+        times.append((shape, best))
+    return min(times, key=lambda t: t[1])[0], times
 
 
 def lower_static(prog: W.Program, outs: Sequence[dict], stream: Optional[int] = None) -> int:

@@ -13,10 +13,11 @@ def _counts(prog):
     return {k: max(len(g[k]) for g in ref) for k in ("instrs", "edges", "boxes")}
 
 
-def _stage(prog, mode, stream=None):
+def _stage(prog, mode, stream=None, caps_from=None):
     from paper_2503_10516_gb300 import igs
+    big = caps_from or prog
     c = igs.Context(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead, mode=mode, stream=stream,
-                    **igs.small_caps(prog, _counts(prog)))
+                    **igs.small_caps(big, _counts(big)))
     for op in prog.ops:
         if op[0] == "buffer":
             b = op[1]
@@ -120,3 +121,77 @@ def test_timed_batch_workload_parity():
         for n in range(p.nodes):
             assert_same_graph(c.graph(n), ref[n], f"{p.name} node {n}")
         c.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (3, 0), (7, 1), (152, 1), (4096, 0), (2, 1, 4, 4), (5, 1, 8, 100),
+                                   (3, 0, 2, 1), (1, 1, 8, 0)])
+def test_work_queue_shapes_match_oracle(shape):
+    """The device work queue (persistent blocks taking units in submission
+    or longest-first order) gives the oracle's graphs for every shape: fewer
+    blocks than units, one block, more blocks than units, multi-warp blocks
+    whose helpers serve some, all or none of the multi-device programs."""
+    from paper_2503_10516_gb300 import igs
+    progs = W.batch_programs(count=16, scale=0.01, seed=31 + shape[0])
+    ctxs = [_stage(p, igs.MODE_BATCHED) for p in progs]
+    igs.lower_batch(ctxs, shape)
+    for p, c in zip(progs, ctxs):
+        ref, rej = oracle_graphs(p)
+        assert c.rejected() == rej
+        for n in range(p.nodes):
+            assert_same_graph(c.graph(n), ref[n], f"{p.name} node {n} shape {shape}")
+        c.close()
+
+
+def test_work_queue_twice_in_one_context():
+    """A second batched launch over the same contexts resumes where the first
+    stopped (the queue head starts at zero again)."""
+    from paper_2503_10516_gb300 import igs
+    progs = W.batch_programs(count=6, scale=0.01, seed=91)
+    longer = [W.Program(p.name, p.nodes, p.devices, p.horizon_step, p.lookahead,
+                        list(p.ops) + [("task", t) for t in p.tasks[:3]] + [("flush",)]) for p in progs]
+    ctxs = [_stage(p, igs.MODE_BATCHED, caps_from=q) for p, q in zip(progs, longer)]
+    igs.lower_batch(ctxs, (2, igs.ORDER_LONGEST_FIRST))
+    for p, c in zip(progs, ctxs):
+        for t in p.tasks[:3]:
+            c.submit(t)
+        c.submit_epoch()
+    igs.lower_batch(ctxs, (5, igs.ORDER_SUBMISSION, 4, 3))
+    for p, q, c in zip(progs, longer, ctxs):
+        ref, rej = oracle_graphs(q)
+        assert c.rejected() == rej
+        for n in range(p.nodes):
+            assert_same_graph(c.graph(n), ref[n], f"{p.name} node {n} (second launch)")
+        c.close()
+
+
+def test_tuner_picks_a_timed_candidate():
+    import time
+
+    import torch
+    from paper_2503_10516_gb300 import igs
+    progs = W.batch_programs(count=12, scale=0.01, seed=5)
+    units = sum(p.nodes for p in progs)
+    cands = igs.batch_shape_candidates(units, torch.cuda.get_device_properties(0).multi_processor_count)
+    assert cands[0] is None and all(1 <= c[0] <= units and 1 <= c[2] <= 8 for c in cands[1:])
+
+    def timer():
+        torch.cuda.synchronize()
+        return time.perf_counter()
+
+    best, times = igs.tune_lower_batch(lambda: [_stage(p, igs.MODE_BATCHED) for p in progs], cands, timer)
+    assert [s for s, _ in times] == list(cands) and best in cands
+    assert all(t > 0 for _, t in times)
+
+
+def test_bad_shape_is_rejected():
+    from paper_2503_10516_gb300 import igs
+    p = W.batch_programs(count=1, scale=0.01, seed=3)[0]
+    c = _stage(p, igs.MODE_BATCHED)
+    for shape in ((4, 2), (4, 1, 9, 0)):
+        with pytest.raises(igs.IgsError):
+            igs.lower_batch([c], shape)
+    igs.lower_batch([c], (4, 1, 2, 1))
+    ref, _ = oracle_graphs(p)
+    for n in range(p.nodes):
+        assert_same_graph(c.graph(n), ref[n], f"{p.name} node {n}")
+    c.close()

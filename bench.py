@@ -343,6 +343,67 @@ def measure_box_copy(igs, torch, stream, reps=20):
     return out
 
 
+def measure_executors(igs, torch, stream, prog, make_ctx, wave_tasks=200, nbody_n=1 << 16, nbody_steps=10):
+    """Execution alone (each graph fully lowered first) on the level executor
+    and on the dataflow executor: the first `wave_tasks` tasks of the wave
+    program, and N-body (nbody_n bodies, 8 nodes x 4 devices, 128 chunks,
+    lookahead 4). Then the whole bench step (igs_run) on each executor. The
+    dataflow executor's node timestamps give the copy / kernel overlap (a
+    separate run with timing on)."""
+    wave = W.Program("wave-head", NODES, DEVICES, HSTEP, LOOKAHEAD,
+                     [op for op in prog.ops if op[0] == "buffer"] + [("task", t) for t in prog.tasks[:wave_tasks]]
+                     + [("flush",)])
+    nbody = W.nbody_program(n=nbody_n, steps=nbody_steps, nodes=8, devices=4, chunks=128, lookahead=4)
+    out = {}
+    for name, p in ((f"wave{N}_{wave_tasks}_tasks", wave), (f"nbody{nbody_n}_{nbody_steps}_steps", nbody)):
+        res = {}
+        for ex_name, ex in (("levels", igs.EXEC_LEVELS), ("dataflow", igs.EXEC_DATAFLOW)):
+            times = []
+            for rep in range(3 if ex == igs.EXEC_DATAFLOW else 2):
+                c = igs.Context(p.nodes, p.devices, p.horizon_step, p.lookahead, mode=igs.MODE_BATCHED, stream=stream)
+                c.set_executor(ex)
+                timing = rep == 2
+                c.set_timing(timing)
+                for op in p.ops:
+                    if op[0] == "buffer":
+                        b = op[1]
+                        c.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init)
+                    elif op[0] == "task":
+                        c.submit(op[1])
+                c.flush()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                c.execute()
+                dt = time.perf_counter() - t0
+                instrs = int(c.counters()["instructions"])
+                if timing:
+                    res["dataflow_stats"] = c.exec_stats()
+                else:
+                    times.append(dt)
+                c.close()
+            res[ex_name] = {"execute_ms": min(times[1:] or times) * 1e3, "instructions": instrs,
+                            "instr_per_s": instrs / min(times[1:] or times)}
+        res["speedup"] = res["levels"]["execute_ms"] / res["dataflow"]["execute_ms"]
+        out[name] = res
+    # the whole bench step on each executor
+    step = {}
+    for ex_name, ex in (("levels", igs.EXEC_LEVELS), ("dataflow", igs.EXEC_DATAFLOW)):
+        ts = []
+        for _ in range(2):
+            c = make_ctx(timing=False)
+            c.set_executor(ex)
+            for t in prog.tasks:
+                c.submit(t)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c.run(WINDOW)
+            ts.append(time.perf_counter() - t0)
+            c.close()
+        step[ex_name] = {"ms": min(ts) * 1e3}
+    out["bench_step"] = step
+    return out
+
+
 def measure_lookahead(igs):
     """Scheduler lookahead policies (Sec. 4.3) on a growing-row stream (the
     RSim pattern, 2048 x 1024 fp32, rows appended 1-64 at a time, 2 devices)
@@ -571,6 +632,7 @@ def run_gpu(args):
 
     # ---- batched lowering of many programs, served lowering of many streams
     big_copy = measure_box_copy(igs, torch, stream)
+    executors = measure_executors(igs, torch, sh, prog, make_ctx) if world == 1 else None
     lookahead = measure_lookahead(igs) if world == 1 else None
     batched = measure_batched(igs, torch, sh) if world == 1 else None
     served = {f"{int(r)}_per_s": measure_served(igs, torch, sh, rate=r) for r in (1e4, 1e5)} \
@@ -610,6 +672,7 @@ def run_gpu(args):
                          "batched_ms_per_task": lower_ms / STEPS},
             "box_copy_gbs": (copy_bytes / (copy_ms * 1e-3) / 1e9) if copy_ms else None,
             "box_copy_resize_512MiB": {k: dict(v, frac=v["gbs"] / hbm) for k, v in big_copy.items()},
+            "executors": executors,
             "batched_programs": batched,
             "lookahead": lookahead,
             "served": served,

@@ -222,8 +222,8 @@ int igs_fetch_instructions(igs_ctx* ctx, igs_graph_view* view);
 int igs_rejected_tasks(igs_ctx* ctx, uint64_t* seqs, uint32_t cap, uint32_t* count);
 
 /* Executes every instruction emitted and not yet executed, on the device, in
- * an order that respects the graph (Sec. 3.7: out-of-order execution of the
- * instruction graph, here by topological level): allocations from a
+ * an order that respects the graph (Sec. 3.7; by topological level or out of
+ * order, see igs_set_executor): allocations from a
  * stream-ordered pool, coherence copies as box-copy kernels, device kernels
  * as the workload kernels. A send copies its box into a mailbox (device
  * memory of its own) when it executes; the receive matched to it by (task,
@@ -234,6 +234,32 @@ int igs_rejected_tasks(igs_ctx* ctx, uint64_t* seqs, uint32_t cap, uint32_t* cou
  * return). */
 #define IGS_EXEC_SYNC 1u
 int igs_execute(igs_ctx* ctx, uint32_t flags);
+
+/* Which executor igs_execute and igs_run use (default IGS_EXEC_LEVELS).
+ * IGS_EXEC_LEVELS: the instructions of one call are grouped by topological
+ * level; each level costs at most one box-copy, one stencil and one workload
+ * launch, in stream order. IGS_EXEC_DATAFLOW: out-of-order execution (Sec.
+ * 3.7 / 4.1: an instruction becomes ready once its predecessors have
+ * completed) in ONE persistent launch per call: every instruction is a node
+ * with a predecessor count and a successor list (its graph edges within the
+ * call, plus send -> matching receive), its work is split into tiles (64 KiB
+ * copy segments, 16384-element stencil tiles, 1024-item workload tiles, 256
+ * N-body bodies) and blocks take tiles of whichever nodes are ready, so
+ * copies, kernels and transfers of different devices, nodes and tasks run
+ * concurrently. Frees of the call run after the launch. Results are
+ * identical. A launch in which no tile finishes for 2 s (a broken graph)
+ * returns IGS_ERR_TIMEOUT. IGS_ERR_STATE during a pipelined run. */
+#define IGS_EXEC_LEVELS 0u
+#define IGS_EXEC_DATAFLOW 1u
+int igs_set_executor(igs_ctx* ctx, uint32_t executor);
+
+/* Dataflow executor statistics since the context was created: [0] launches,
+ * [1] nodes, [2] tiles, [3] edges; with igs_set_timing on, from node
+ * timestamps (global timer) of each launch: [4] span ms (first tile claimed to
+ * last node completed), [5] ms during which some copy node was running,
+ * [6] the same for kernel nodes, [7] ms during which both were (copy / kernel
+ * overlap). Waits for the context's streams. */
+int igs_exec_stats(igs_ctx* ctx, double out[8]);
 
 /* Lowers every pending submission and executes the whole graph with the
  * scheduler running ahead of the executor (Sec. 4: instruction generation

@@ -14,6 +14,23 @@ __device__ uint32_t g_exec_error = 0;
 
 namespace {
 
+// Load policies. Kernels of the level executor read through L1 (plain) or
+// with streaming hints; the dataflow executor's blocks read data that other
+// blocks of the same launch wrote, so every data load there goes to L2
+// (L1 is not coherent between SMs within a launch).
+struct LdPlain {
+  template <class T>
+  __device__ __forceinline__ static T ld(const T* p) { return *p; }
+};
+struct LdStream {
+  template <class T>
+  __device__ __forceinline__ static T ld(const T* p) { return __ldcs(p); }
+};
+struct LdL2 {
+  template <class T>
+  __device__ __forceinline__ static T ld(const T* p) { return __ldcg(p); }
+};
+
 // ---- box copy ---------------------------------------------------------------
 //
 // A job is a 3-level strided copy: rows0 x rows1 rows of `run` contiguous
@@ -31,12 +48,10 @@ __device__ __forceinline__ uint32_t find_job(const CopyJob* jobs, uint32_t n, ui
   return lo;
 }
 
-__global__ void __launch_bounds__(256) box_copy_kernel(const CopyJob* __restrict__ jobs, uint32_t n_jobs,
-                                                       uint64_t n_units) {
-  for (uint64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
-    const uint32_t j = find_job(jobs, n_jobs, u);
-    const CopyJob& J = jobs[j];
-    const uint64_t local = u - J.unit_begin;
+// One work unit (row segment) of a copy job, by the whole block.
+template <class Ld>
+__device__ __forceinline__ void copy_unit(const CopyJob& J, uint64_t local) {
+  {
     const uint32_t segs = (J.extent[2] + J.seg_bytes - 1) / J.seg_bytes;
     const uint64_t row = local / segs;
     const uint32_t seg = (uint32_t)(local % segs);
@@ -52,22 +67,31 @@ __global__ void __launch_bounds__(256) box_copy_kernel(const CopyJob* __restrict
       const uint32_t n4 = len >> 4, bd = blockDim.x;
       uint32_t i = threadIdx.x;
       for (; i + 3 * bd < n4; i += 4 * bd) {
-        const uint4 a = __ldcs(s4 + i), b = __ldcs(s4 + i + bd), c = __ldcs(s4 + i + 2 * bd),
-                    e = __ldcs(s4 + i + 3 * bd);
+        const uint4 a = Ld::ld(s4 + i), b = Ld::ld(s4 + i + bd), c = Ld::ld(s4 + i + 2 * bd),
+                    e = Ld::ld(s4 + i + 3 * bd);
         __stcs(d4 + i, a);
         __stcs(d4 + i + bd, b);
         __stcs(d4 + i + 2 * bd, c);
         __stcs(d4 + i + 3 * bd, e);
       }
-      for (; i < n4; i += bd) __stcs(d4 + i, __ldcs(s4 + i));
+      for (; i < n4; i += bd) __stcs(d4 + i, Ld::ld(s4 + i));
     } else if ((((uintptr_t)s | (uintptr_t)d | len) & 3u) == 0) {
       const uint32_t* s1 = reinterpret_cast<const uint32_t*>(s);
       uint32_t* d1 = reinterpret_cast<uint32_t*>(d);
       const uint32_t n1 = len >> 2;
-      for (uint32_t i = threadIdx.x; i < n1; i += blockDim.x) d1[i] = s1[i];
+      for (uint32_t i = threadIdx.x; i < n1; i += blockDim.x) d1[i] = Ld::ld(s1 + i);
     } else {
-      for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) d[i] = s[i];
+      for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) d[i] = Ld::ld(s + i);
     }
+  }
+}
+
+__global__ void __launch_bounds__(256) box_copy_kernel(const CopyJob* __restrict__ jobs, uint32_t n_jobs,
+                                                       uint64_t n_units) {
+  for (uint64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+    const uint32_t j = find_job(jobs, n_jobs, u);
+    const CopyJob& J = jobs[j];
+    copy_unit<LdStream>(J, u - J.unit_begin);
   }
 }
 
@@ -119,23 +143,48 @@ __device__ __forceinline__ uint32_t mix(uint32_t seq, uint32_t w, uint32_t lin) 
   return h;
 }
 
+template <class Ld>
 __device__ __forceinline__ float ldf(const KAcc& a, uint32_t y, uint32_t x) {
   const uint8_t* p = elem_ptr(a, y, x, 0);
-  return p ? *reinterpret_cast<const float*>(p) : 0.0f;
+  return p ? Ld::ld(reinterpret_cast<const float*>(p)) : 0.0f;
 }
 __device__ __forceinline__ void stf(const KAcc& a, uint32_t y, uint32_t x, float v) {
   uint8_t* p = elem_ptr(a, y, x, 0);
   if (p) *reinterpret_cast<float*>(p) = v;
 }
+template <class Ld>
 __device__ __forceinline__ float4 ld4(const KAcc& a, uint32_t i) {
   const uint8_t* p = elem_ptr(a, i, 0, 0);
-  return p ? *reinterpret_cast<const float4*>(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+  return p ? Ld::ld(reinterpret_cast<const float4*>(p)) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 __device__ __forceinline__ void st4(const KAcc& a, uint32_t i, float4 v) {
   uint8_t* p = elem_ptr(a, i, 0, 0);
   if (p) *reinterpret_cast<float4*>(p) = v;
 }
 
+// The N-body step's update of body y from the accelerations (same order of
+// operations everywhere it is used).
+__device__ __forceinline__ float4 nbody_kick(float4 v, float ax, float ay, float az) {
+  v.x = v.x + ax * 0.01f;
+  v.y = v.y + ay * 0.01f;
+  v.z = v.z + az * 0.01f;
+  return v;
+}
+
+// Adds body pj's pull on pi to the running sums (one term of the sequential
+// j-sum).
+__device__ __forceinline__ void nbody_term(const float4 pi, const float4 pj, float& ax, float& ay, float& az) {
+  const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+  const float r2 = ((dx * dx + dy * dy) + dz * dz) + 1e-6f;
+  const float s = sqrtf(r2);
+  const float inv = 1.0f / (r2 * s);
+  const float wgt = pj.w * inv;
+  ax = ax + dx * wgt;
+  ay = ay + dy * wgt;
+  az = az + dz * wgt;
+}
+
+template <class Ld>
 __device__ void run_item(const KernelJob& J, uint32_t y, uint32_t x, uint32_t z) {
   switch (J.kernel) {
     case K_JACOBI:
@@ -144,14 +193,14 @@ __device__ void run_item(const KernelJob& J, uint32_t y, uint32_t x, uint32_t z)
       const KAcc& U = J.acc[wave ? 1 : 0];
       const KAcc& O = J.acc[wave ? 2 : 1];
       const uint32_t H = U.ext[0], W = U.ext[1];
-      const float c = ldf(U, y, x);
+      const float c = ldf<Ld>(U, y, x);
       float v = c;
       if (y > 0 && y + 1 < H && x > 0 && x + 1 < W) {
-        const float n = ldf(U, y - 1, x), s = ldf(U, y + 1, x), w = ldf(U, y, x - 1), e = ldf(U, y, x + 1);
+        const float n = ldf<Ld>(U, y - 1, x), s = ldf<Ld>(U, y + 1, x), w = ldf<Ld>(U, y, x - 1), e = ldf<Ld>(U, y, x + 1);
         if (!wave) {
           v = ((n + s) + (w + e)) * 0.25f;
         } else {
-          const float pv = ldf(J.acc[0], y, x);
+          const float pv = ldf<Ld>(J.acc[0], y, x);
           const float t2 = (2.0f * c) - pv;
           const float t5 = (n + s) + (w + e);
           const float t8 = 0.25f * (t5 - 4.0f * c);
@@ -165,29 +214,15 @@ __device__ void run_item(const KernelJob& J, uint32_t y, uint32_t x, uint32_t z)
       const KAcc& P = J.acc[0];
       const KAcc& V = J.acc[1];
       const uint32_t n = P.ext[0];
-      const float4 pi = ld4(P, y);
+      const float4 pi = ld4<Ld>(P, y);
       float ax = 0.f, ay = 0.f, az = 0.f;
-      for (uint32_t j = 0; j < n; ++j) {
-        const float4 pj = ld4(P, j);
-        const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-        const float r2 = ((dx * dx + dy * dy) + dz * dz) + 1e-6f;
-        const float s = sqrtf(r2);
-        const float inv = 1.0f / (r2 * s);
-        const float wgt = pj.w * inv;
-        ax = ax + dx * wgt;
-        ay = ay + dy * wgt;
-        az = az + dz * wgt;
-      }
-      float4 v = ld4(V, y);
-      v.x = v.x + ax * 0.01f;
-      v.y = v.y + ay * 0.01f;
-      v.z = v.z + az * 0.01f;
-      st4(V, y, v);
+      for (uint32_t j = 0; j < n; ++j) nbody_term(pi, ld4<Ld>(P, j), ax, ay, az);
+      st4(V, y, nbody_kick(ld4<Ld>(V, y), ax, ay, az));
       break;
     }
     case K_NBODY_UPDATE: {
-      const float4 v = ld4(J.acc[0], y);
-      float4 p = ld4(J.acc[1], y);
+      const float4 v = ld4<Ld>(J.acc[0], y);
+      float4 p = ld4<Ld>(J.acc[1], y);
       p.x = p.x + v.x * 0.01f;
       p.y = p.y + v.y * 0.01f;
       p.z = p.z + v.z * 0.01f;
@@ -201,7 +236,7 @@ __device__ void run_item(const KernelJob& J, uint32_t y, uint32_t x, uint32_t z)
       } else {
         const uint32_t r = J.params[0];
         const uint32_t yy = y + r;
-        const float last = ldf(J.acc[0], r - 1, x);
+        const float last = ldf<Ld>(J.acc[0], r - 1, x);
         const float v = last * 0.5f + (float)(yy & 255u);
         stf(J.acc[1], yy, x, v);
       }
@@ -216,7 +251,7 @@ __device__ void run_item(const KernelJob& J, uint32_t y, uint32_t x, uint32_t z)
         uint32_t p[3];
         if (!item_lo(A, item, p)) continue;
         const uint8_t* q = elem_ptr(A, p[0], p[1], p[2]);
-        if (q) s += *reinterpret_cast<const uint32_t*>(q);
+        if (q) s += Ld::ld(reinterpret_cast<const uint32_t*>(q));
       }
       for (uint32_t a = 0; a < J.nacc; ++a) {
         const KAcc& A = J.acc[a];
@@ -258,7 +293,7 @@ __global__ void __launch_bounds__(256) workload_kernel(const KernelJob* __restri
     local /= e2;
     const uint32_t x = J.lo[1] + (uint32_t)(local % e1);
     const uint32_t y = J.lo[0] + (uint32_t)(local / e1);
-    run_item(J, y, x, z);
+    run_item<LdPlain>(J, y, x, z);
   }
 }
 
@@ -266,27 +301,32 @@ __global__ void __launch_bounds__(256) workload_kernel(const KernelJob* __restri
 // (blockIdx.y), four consecutive columns per thread with 16-byte loads and
 // stores; the host has checked that the read allocation covers the chunk plus
 // its one-element halo (clamped to the buffer) and the others cover the chunk.
-__global__ void __launch_bounds__(256) stencil_kernel(const KernelJob* __restrict__ jobs) {
-  const KernelJob& J = jobs[blockIdx.y];
+__device__ __forceinline__ uint64_t stencil_groups(const KernelJob& J) {
+  return (uint64_t)(J.hi[0] - J.lo[0]) * ((J.hi[1] - J.lo[1] + 3) / 4);
+}
+
+// Groups g0, g0 + stride, ... below g1 of one stencil job (a group is four
+// consecutive columns of one row).
+template <class Ld>
+__device__ __forceinline__ void stencil_range(const KernelJob& J, uint64_t g0, uint64_t g1, uint64_t stride) {
   const bool wave = J.kernel == K_WAVE;
   const KAcc& U = J.acc[wave ? 1 : 0];
   const KAcc& O = J.acc[wave ? 2 : 1];
   const KAcc& P = J.acc[0];
   const uint32_t H = U.ext[0], W = U.ext[1];
-  const uint32_t y0 = J.lo[0], y1 = J.hi[0], x0 = J.lo[1], x1 = J.hi[1];
+  const uint32_t y0 = J.lo[0], x0 = J.lo[1], x1 = J.hi[1];
   const uint32_t uw = U.hi[1] - U.lo[1], ow = O.hi[1] - O.lo[1], pw = P.hi[1] - P.lo[1];
   const float* u = reinterpret_cast<const float*>(U.ptr);
   const float* pv = reinterpret_cast<const float*>(P.ptr);
   float* o = reinterpret_cast<float*>(O.ptr);
   const uint32_t groups = (x1 - x0 + 3) / 4;
-  const uint64_t total = (uint64_t)(y1 - y0) * groups;
   // 16-byte loads of the four columns when every row of every allocation
   // starts on a 16-byte boundary at x0
   const bool vec = ((x0 - U.lo[1]) % 4 == 0) && uw % 4 == 0 && ((x0 - O.lo[1]) % 4 == 0) && ow % 4 == 0 &&
                    (!wave || (((x0 - P.lo[1]) % 4 == 0) && pw % 4 == 0)) &&
                    ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(o) |
                      (wave ? reinterpret_cast<uintptr_t>(pv) : 0u)) & 15u) == 0;
-  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (uint64_t)gridDim.x * blockDim.x) {
+  for (uint64_t g = g0; g < g1; g += stride) {
     const uint32_t y = y0 + (uint32_t)(g / groups);
     const uint32_t xs = x0 + 4 * (uint32_t)(g % groups);
     const float* ur = u + (size_t)(y - U.lo[0]) * uw - U.lo[1];
@@ -297,12 +337,12 @@ __global__ void __launch_bounds__(256) stencil_kernel(const KernelJob* __restric
     float out[4];
     if (vec && xs + 4 <= x1) {
       // the same arithmetic, in the same order, on registers
-      const float4 c4 = __ldcs(reinterpret_cast<const float4*>(ur + xs));
-      const float4 n4 = __ldcs(reinterpret_cast<const float4*>(urn + xs));
-      const float4 s4 = __ldcs(reinterpret_cast<const float4*>(urs + xs));
-      const float4 p4 = wave ? __ldcs(reinterpret_cast<const float4*>(pr + xs)) : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float cs[6] = {xs > 0 ? __ldcs(ur + xs - 1) : 0.f, c4.x, c4.y, c4.z, c4.w,
-                           xs + 4 < W ? __ldcs(ur + xs + 4) : 0.f};
+      const float4 c4 = Ld::ld(reinterpret_cast<const float4*>(ur + xs));
+      const float4 n4 = Ld::ld(reinterpret_cast<const float4*>(urn + xs));
+      const float4 s4 = Ld::ld(reinterpret_cast<const float4*>(urs + xs));
+      const float4 p4 = wave ? Ld::ld(reinterpret_cast<const float4*>(pr + xs)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float cs[6] = {xs > 0 ? Ld::ld(ur + xs - 1) : 0.f, c4.x, c4.y, c4.z, c4.w,
+                           xs + 4 < W ? Ld::ld(ur + xs + 4) : 0.f};
       const float ns[4] = {n4.x, n4.y, n4.z, n4.w}, ss[4] = {s4.x, s4.y, s4.z, s4.w},
                   ps[4] = {p4.x, p4.y, p4.z, p4.w};
       const bool row_in = y > 0 && y + 1 < H;
@@ -333,14 +373,14 @@ __global__ void __launch_bounds__(256) stencil_kernel(const KernelJob* __restric
       if (x >= x1) break;
       // streaming (evict-first) loads and stores: the stencil's data passes
       // through L2 once per step and should not displace other kernels' lines
-      const float c = __ldcs(ur + x);
+      const float c = Ld::ld(ur + x);
       float v = c;
       if (y > 0 && y + 1 < H && x > 0 && x + 1 < W) {
-        const float n = __ldcs(urn + x), s = __ldcs(urs + x), w = __ldcs(ur + x - 1), e = __ldcs(ur + x + 1);
+        const float n = Ld::ld(urn + x), s = Ld::ld(urs + x), w = Ld::ld(ur + x - 1), e = Ld::ld(ur + x + 1);
         if (!wave) {
           v = ((n + s) + (w + e)) * 0.25f;
         } else {
-          const float t2 = (2.0f * c) - __ldcs(pr + x);
+          const float t2 = (2.0f * c) - Ld::ld(pr + x);
           const float t5 = (n + s) + (w + e);
           const float t8 = 0.25f * (t5 - 4.0f * c);
           v = t2 + t8;
@@ -352,6 +392,172 @@ __global__ void __launch_bounds__(256) stencil_kernel(const KernelJob* __restric
       __stcs(reinterpret_cast<float4*>(orow + xs), make_float4(out[0], out[1], out[2], out[3]));
     } else {
       for (int k = 0; k < 4 && xs + k < x1; ++k) __stcs(orow + xs + k, out[k]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) stencil_kernel(const KernelJob* __restrict__ jobs) {
+  const KernelJob& J = jobs[blockIdx.y];
+  stencil_range<LdStream>(J, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, stencil_groups(J),
+                          (uint64_t)gridDim.x * blockDim.x);
+}
+
+// ---- dataflow executor -----------------------------------------------------
+//
+// Out-of-order execution of an instruction graph (Sec. 3.7 / 4.1: an
+// instruction may run once its predecessors have completed) inside one
+// persistent launch: ready instructions are handed out tile by tile to
+// whichever block asks next, so copies, kernels and transfers of different
+// nodes, devices and tasks overlap without level barriers or host round trips.
+// A block only ever waits when nothing is ready; every claimed tile runs to
+// completion without waiting, so the launch progresses whether or not all of
+// its blocks are resident.
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// N-body step over one tile of up to kFlowBodies bodies: the block stages
+// kFlowBodies bodies of P at a time in shared memory (loaded from L2); each
+// thread sums the terms in the same sequential j order as run_item.
+__device__ __forceinline__ void nbody_tile(const KernelJob& J, uint32_t y_first, uint32_t y_end, float4* s_body) {
+  const KAcc& P = J.acc[0];
+  const KAcc& V = J.acc[1];
+  const uint32_t n = P.ext[0];
+  const uint32_t y = y_first + threadIdx.x;
+  const bool mine = y < y_end;
+  const float4 pi = mine ? ld4<LdL2>(P, y) : make_float4(0.f, 0.f, 0.f, 0.f);
+  float ax = 0.f, ay = 0.f, az = 0.f;
+  for (uint32_t j0 = 0; j0 < n; j0 += kFlowBodies) {
+    const uint32_t cnt = min(kFlowBodies, n - j0);
+    __syncthreads();
+    if (threadIdx.x < cnt) s_body[threadIdx.x] = ld4<LdL2>(P, j0 + threadIdx.x);
+    __syncthreads();
+    if (mine)
+      for (uint32_t k = 0; k < cnt; ++k) nbody_term(pi, s_body[k], ax, ay, az);
+  }
+  if (mine) st4(V, y, nbody_kick(ld4<LdL2>(V, y), ax, ay, az));
+}
+
+// Tile t of node F, by the whole block.
+__device__ void run_tile(const FlowNode& F, uint32_t t, const CopyJob* __restrict__ cjobs,
+                         const KernelJob* __restrict__ kjobs, float4* s_body) {
+  if (F.kind == FK_COPY) {
+    const uint32_t j = F.first + find_job(cjobs + F.first, F.count, t);
+    copy_unit<LdL2>(cjobs[j], t - cjobs[j].unit_begin);
+  } else if (F.kind == FK_STENCIL) {
+    const KernelJob& J = kjobs[F.first];
+    const uint64_t g0 = (uint64_t)t * kFlowStencilGroups;
+    const uint64_t g1 = min(g0 + kFlowStencilGroups, stencil_groups(J));
+    stencil_range<LdL2>(J, g0 + threadIdx.x, g1, blockDim.x);
+  } else if (F.kind == FK_WORKLOAD) {
+    const KernelJob& J = kjobs[F.first];
+    const uint32_t e1 = J.hi[1] - J.lo[1], e2 = J.hi[2] - J.lo[2];
+    const uint64_t items = (uint64_t)(J.hi[0] - J.lo[0]) * e1 * e2;
+    if (J.kernel == K_NBODY_STEP) {
+      // one item per body (the range is 1D)
+      const uint32_t y0 = J.lo[0] + t * kFlowBodies;
+      nbody_tile(J, y0, min(y0 + kFlowBodies, J.hi[0]), s_body);
+      return;
+    }
+    const uint64_t i0 = (uint64_t)t * kFlowItems, i1 = min(i0 + kFlowItems, items);
+    for (uint64_t local = i0 + threadIdx.x; local < i1; local += blockDim.x) {
+      uint64_t l = local;
+      const uint32_t z = J.lo[2] + (uint32_t)(l % e2);
+      l /= e2;
+      const uint32_t x = J.lo[1] + (uint32_t)(l % e1);
+      const uint32_t y = J.lo[0] + (uint32_t)(l / e1);
+      run_item<LdL2>(J, y, x, z);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kFlowThreads) flow_kernel(FlowCtl* ctl, FlowNode* nodes, uint32_t n_nodes,
+                                                            const uint32_t* __restrict__ succ, uint32_t* pending,
+                                                            uint32_t* claimed, uint32_t* finished,
+                                                            volatile uint32_t* ready,
+                                                            const CopyJob* __restrict__ cjobs,
+                                                            const KernelJob* __restrict__ kjobs, uint64_t wait_ns) {
+  __shared__ uint32_t s_node, s_tile, s_stop;
+  __shared__ float4 s_body[kFlowBodies];
+  volatile FlowCtl* vc = ctl;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      uint32_t stop = 0, node = 0, tile = 0, polls = 0, nap = 32;
+      unsigned long long seen = vc->tiles_done, since = gtimer();
+      for (;;) {
+        const uint32_t h = vc->head;
+        if (h >= n_nodes) {
+          stop = 1;
+          break;
+        }
+        const uint32_t q = ready[h];
+        if (q != 0xFFFFFFFFu) {
+          __threadfence();  // the tile's loads come after its predecessors' stores
+          const uint32_t tiles = nodes[q].tiles;
+          // a plain look first, so that blocks arriving late at a node whose
+          // tiles are all taken do not pile atomics onto it
+          const uint32_t t = *(volatile uint32_t*)&claimed[q] < tiles ? atomicAdd(&claimed[q], 1u) : tiles;
+          if (t < tiles) {
+            node = q;
+            tile = t;
+            if (t == 0) nodes[q].t_start = gtimer();
+            break;
+          }
+          atomicCAS(&ctl->head, h, h + 1);  // every tile of q is taken
+          nap = 32;
+          continue;
+        }
+        // nothing ready: back off (up to about 4 us between looks, so that
+        // waiting blocks do not crowd the queue's cache lines), and give up
+        // if no tile finishes anywhere for wait_ns
+        if ((++polls & 15u) == 0) {
+          if (vc->abort) {
+            stop = 1;
+            break;
+          }
+          const unsigned long long d = vc->tiles_done, now = gtimer();
+          if (d != seen) {
+            seen = d;
+            since = now;
+          } else if (now - since > wait_ns) {
+            atomicExch(&ctl->error, 1u);
+            atomicExch(&ctl->abort, 1u);
+            atomicOr(&g_exec_error, 2u);
+            stop = 1;
+            break;
+          }
+        }
+        __nanosleep(nap);
+        nap = nap < 4096 ? 2 * nap : 4096;
+      }
+      s_stop = stop;
+      s_node = node;
+      s_tile = tile;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const uint32_t q = s_node;
+    run_tile(nodes[q], s_tile, cjobs, kjobs, s_body);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();  // this tile's stores before its count
+      const uint32_t f = atomicAdd(&finished[q], 1u) + 1u;
+      atomicAdd(&ctl->tiles_done, 1ull);
+      const FlowNode& F = nodes[q];
+      if (f == F.tiles) {
+        nodes[q].t_end = gtimer();
+        __threadfence();
+        for (uint32_t k = 0; k < F.succ_cnt; ++k) {
+          const uint32_t sn = succ[F.succ_off + k];
+          if (atomicSub(&pending[sn], 1u) == 1u) {
+            const uint32_t pos = atomicAdd(&ctl->tail, 1u);
+            ready[pos] = sn;
+          }
+        }
+      }
     }
   }
 }
@@ -399,4 +605,32 @@ int igs_launch_workload(const igs::KernelJob* jobs_dev, uint32_t n_jobs, uint64_
   const uint32_t grid = (uint32_t)(blocks < cap ? blocks : cap);
   igs::workload_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(jobs_dev, n_jobs, n_items);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int igs_launch_flow(igs::FlowCtl* ctl, igs::FlowNode* nodes, uint32_t n_nodes, const uint32_t* succ, uint32_t* pending,
+                    uint32_t* claimed, uint32_t* finished, uint32_t* ready, const igs::CopyJob* cjobs,
+                    const igs::KernelJob* kjobs, uint64_t wait_ns, void* stream) {
+  if (n_nodes == 0) return 0;
+  static int grid = 0;
+  if (!grid) {
+    int dev = 0, sms = 152, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, igs::flow_kernel, igs::kFlowThreads, 0);
+    grid = sms * (per > 0 ? per : 1);
+  }
+  igs::flow_kernel<<<grid, igs::kFlowThreads, 0, (cudaStream_t)stream>>>(ctl, nodes, n_nodes, succ, pending, claimed,
+                                                                        finished, ready, cjobs, kjobs, wait_ns);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+void igs_exec_preload() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncAttributes a;
+  cudaFuncGetAttributes(&a, igs::box_copy_kernel);
+  cudaFuncGetAttributes(&a, igs::stencil_kernel);
+  cudaFuncGetAttributes(&a, igs::workload_kernel);
+  cudaFuncGetAttributes(&a, igs::flow_kernel);
+  done = true;
 }

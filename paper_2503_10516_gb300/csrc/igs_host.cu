@@ -34,6 +34,7 @@ struct ExecAlloc {
 // memory of its own) until the matching receive copies it out.
 struct SendRec {
   uint32_t node, level;
+  uint32_t fid = 0;  // its dataflow node (execute call `call`)
   uint64_t call;  // execute call that copied the data into the mailbox
   igs_box box;
   uint8_t* mail;
@@ -49,6 +50,14 @@ struct NodeHost {
   uint32_t executed = 1;             // instruction 0 is the initial epoch
   std::map<uint32_t, ExecAlloc> allocs;
   std::vector<uint32_t> level;       // topological level per instruction (current execute call)
+  std::vector<uint32_t> fid;         // dataflow node per instruction (current execute call)
+};
+
+// A dataflow launch kept until its node timestamps have been read back.
+struct FlowKeep {
+  void* arena;
+  size_t off_nodes;
+  uint32_t n_nodes;
 };
 
 }  // namespace
@@ -101,6 +110,17 @@ struct igs_ctx {
   uint32_t hcap_cjobs[2] = {0, 0}, hcap_kjobs[2] = {0, 0};
   cudaEvent_t jobs_done[2] = {nullptr, nullptr};
   int jobs_set = 0;
+  // dataflow executor: pinned staging of each launch's arrays (two sets, as
+  // the job arrays), launches kept for timestamp read-back, statistics
+  uint32_t executor = IGS_EXEC_LEVELS;
+  uint8_t* h_flow[2] = {nullptr, nullptr};
+  size_t hcap_flow[2] = {0, 0};
+  std::vector<FlowKeep> flow_keep;
+  // outgrown pinned staging, freed with the context: freeing page-locked
+  // memory waits for the whole device, which would stall the host loop of a
+  // pipelined run behind the lowering launch
+  std::vector<void*> retired_pinned;
+  double flow_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   uint64_t launches = 0;
   size_t arena_bytes = 0;
   // serving: submissions live in host-mapped memory the loop polls
@@ -311,6 +331,10 @@ size_t table_bytes(uint32_t cap) { return (size_t)F_COUNT * cap * sizeof(uint32_
 
 }  // namespace
 
+namespace {
+int flow_collect(igs_ctx* c);
+}  // namespace
+
 extern "C" {
 
 int igs_create(const igs_config* cfg, igs_ctx** out) {
@@ -340,6 +364,9 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
     delete c;
     return IGS_ERR_CUDA;
   }
+  // kernels load on first use otherwise, and loading one while the lowering
+  // launch runs would hold up the first pipelined run until that launch ends
+  igs_exec_preload();
   if (cfg->stream) {
     c->stream = (cudaStream_t)cfg->stream;
   } else {
@@ -461,7 +488,10 @@ void igs_destroy(igs_ctx* c) {
   if (c->xstream) cudaStreamSynchronize(c->xstream);
   for (auto& sr : c->sends)
     if (sr.second.mail) cudaFree(sr.second.mail);
+  for (auto& f : c->flow_keep) cudaFree(f.arena);
+  for (void* p : c->retired_pinned) cudaFreeHost(p);
   for (int k = 0; k < 2; ++k) {
+    if (c->h_flow[k]) cudaFreeHost(c->h_flow[k]);
     if (c->d_cjobs[k]) cudaFreeAsync(c->d_cjobs[k], c->stream);
     if (c->d_kjobs[k]) cudaFreeAsync(c->d_kjobs[k], c->stream);
     if (c->h_cjobs[k]) cudaFreeHost(c->h_cjobs[k]);
@@ -505,6 +535,23 @@ int igs_profile(igs_ctx* c, uint64_t out[32]) {
   std::memset(out, 0, sizeof(uint64_t) * 32);
   for (const NodeDev& nd : c->nodes_host)
     for (int k = 0; k < 32; ++k) out[k] += nd.prof[k];
+  return IGS_OK;
+}
+
+int igs_set_executor(igs_ctx* c, uint32_t executor) {
+  if (!c || executor > IGS_EXEC_DATAFLOW) return IGS_ERR_INVALID_ARG;
+  if (c->pipelined) return fail_ctx(c, IGS_ERR_STATE, "a pipelined run is in progress");
+  c->executor = executor;
+  return IGS_OK;
+}
+
+int igs_exec_stats(igs_ctx* c, double out[8]) {
+  if (!c || !out) return IGS_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->xstream) CK(cudaStreamSynchronize(c->xstream));
+  int r = flow_collect(c);
+  if (r) return r;
+  for (int k = 0; k < 8; ++k) out[k] = c->flow_stats[k];
   return IGS_OK;
 }
 
@@ -777,7 +824,34 @@ struct LevelWork {
   uint64_t copy_units = 0, kernel_items = 0, stencil_max = 0;
 };
 
+// The dataflow graph of one execute call: a node per walked instruction, its
+// copy or kernel jobs, (predecessor, successor) pairs, deferred frees.
+struct FlowBuild {
+  std::vector<FlowNode> nodes;
+  std::vector<std::pair<uint32_t, uint32_t>> edges;
+  std::vector<CopyJob> copies;
+  std::vector<KernelJob> kernels;
+  std::vector<void*> frees;
+  uint32_t add_node(uint32_t kind) {
+    FlowNode f{};
+    f.kind = kind;
+    f.first = (uint32_t)(kind == FK_COPY ? copies.size() : kernels.size());
+    nodes.push_back(f);
+    return (uint32_t)nodes.size() - 1;
+  }
+  // appends a copy job to node F (the last node added); tiles counts units so far
+  void add_copy(uint32_t F, CopyJob J) {
+    FlowNode& f = nodes[F];
+    J.unit_begin = f.tiles;
+    const uint64_t segs = (J.extent[2] + J.seg_bytes - 1) / J.seg_bytes;
+    f.tiles += (uint32_t)((uint64_t)J.extent[0] * J.extent[1] * segs);
+    copies.push_back(J);
+    f.count++;
+  }
+};
+
 struct Pending {
+  FlowBuild* flow = nullptr;  // set: build the dataflow graph instead of levels
   std::vector<LevelWork> levels;
   LevelWork& at(uint32_t L) {
     if (levels.size() <= L) levels.resize(L + 1);
@@ -880,10 +954,19 @@ template <class T>
 int grow_pinned(igs_ctx* c, T*& ptr, uint32_t& cap, size_t need) {
   if (need <= cap) return IGS_OK;
   const uint32_t ncap = (uint32_t)std::max<size_t>(need, std::max<size_t>(4096, (size_t)cap * 2));
-  if (ptr) CK(cudaFreeHost(ptr));
+  if (ptr) c->retired_pinned.push_back(ptr);
   ptr = nullptr;
   CK(cudaHostAlloc((void**)&ptr, sizeof(T) * (size_t)ncap, cudaHostAllocDefault));
   cap = ncap;
+  return IGS_OK;
+}
+
+// Reads and clears the execution error flags (after the stream has completed).
+int exec_error_status(igs_ctx* c) {
+  const int e = igs_exec_error(true);
+  if (e < 0) return fail_ctx(c, IGS_ERR_CUDA, "reading the execution error flags");
+  if (e & 2) return fail_ctx(c, IGS_ERR_TIMEOUT, "the dataflow executor saw no tile finish for 2 s and gave up");
+  if (e & 1) return fail_ctx(c, IGS_ERR_STATE, "a workload kernel accessed outside its allocation");
   return IGS_OK;
 }
 
@@ -957,8 +1040,165 @@ int run_pending(igs_ctx* c, Pending& p, cudaStream_t s, bool wait) {
   if (!wait) return IGS_OK;
   CK(cudaStreamSynchronize(s));
   ev_collect(c);
-  if (igs_exec_error(true)) return fail_ctx(c, IGS_ERR_STATE, "a workload kernel accessed outside its allocation");
+  return exec_error_status(c);
+}
+
+int run_flow(igs_ctx* c, FlowBuild& g, cudaStream_t s, bool wait);
+
+// Runs what the walk collected, on the executor the context uses.
+int run_walk(igs_ctx* c, Pending& p, cudaStream_t s, bool wait) {
+  return p.flow ? run_flow(c, *p.flow, s, wait) : run_pending(c, p, s, wait);
+}
+
+// Length of the union of intervals (sorted in place).
+double union_ns(std::vector<std::pair<uint64_t, uint64_t>>& v) {
+  std::sort(v.begin(), v.end());
+  double total = 0;
+  uint64_t lo = 0, hi = 0;
+  bool open = false;
+  for (const auto& x : v) {
+    if (!open || x.first > hi) {
+      if (open) total += (double)(hi - lo);
+      lo = x.first;
+      hi = x.second;
+      open = true;
+    } else {
+      hi = std::max(hi, x.second);
+    }
+  }
+  if (open) total += (double)(hi - lo);
+  return total;
+}
+
+// Reads back the node timestamps of kept dataflow launches (their streams
+// have completed) and adds span, copy-busy, kernel-busy and overlap times.
+int flow_collect(igs_ctx* c) {
+  for (const FlowKeep& f : c->flow_keep) {
+    std::vector<FlowNode> nodes(f.n_nodes);
+    CK(cudaMemcpy(nodes.data(), (uint8_t*)f.arena + f.off_nodes, sizeof(FlowNode) * f.n_nodes, cudaMemcpyDeviceToHost));
+    CK(cudaFree(f.arena));
+    std::vector<std::pair<uint64_t, uint64_t>> cp, kn, all;
+    uint64_t t0 = ~0ull, t1 = 0;
+    for (const FlowNode& n : nodes) {
+      if (n.kind == FK_NONE || n.t_end < n.t_start) continue;
+      (n.kind == FK_COPY ? cp : kn).push_back({n.t_start, n.t_end});
+      all.push_back({n.t_start, n.t_end});
+      t0 = std::min<uint64_t>(t0, n.t_start);
+      t1 = std::max<uint64_t>(t1, n.t_end);
+    }
+    const double uc = union_ns(cp), uk = union_ns(kn), ua = union_ns(all);
+    if (t1 > t0) c->flow_stats[4] += (double)(t1 - t0) * 1e-6;
+    c->flow_stats[5] += uc * 1e-6;
+    c->flow_stats[6] += uk * 1e-6;
+    c->flow_stats[7] += (uc + uk - ua) * 1e-6;
+  }
+  c->flow_keep.clear();
   return IGS_OK;
+}
+
+// Lays the dataflow graph out in one device arena (control block, nodes,
+// successor CSR, predecessor counts, claim / finish counters, ready queue,
+// jobs), uploads it and launches it on stream s; frees follow the launch.
+int run_flow(igs_ctx* c, FlowBuild& g, cudaStream_t s, bool wait) {
+  const uint32_t n = (uint32_t)g.nodes.size();
+  if (n == 0) {
+    for (void* f : g.frees) CK(cudaFreeAsync(f, s));
+    return IGS_OK;
+  }
+  std::vector<uint32_t> pend(n, 0), off(n + 1, 0);
+  for (const auto& e : g.edges) {
+    off[e.first + 1]++;
+    pend[e.second]++;
+  }
+  for (uint32_t i = 0; i < n; ++i) off[i + 1] += off[i];
+  uint64_t tiles = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    FlowNode& f = g.nodes[i];
+    f.succ_off = off[i];
+    f.succ_cnt = off[i + 1] - off[i];
+    if (f.kind == FK_COPY && f.count == 0) f.kind = FK_NONE;
+    if (f.kind == FK_STENCIL) {
+      const KernelJob& J = g.kernels[f.first];
+      const uint64_t groups = (uint64_t)(J.hi[0] - J.lo[0]) * ((J.hi[1] - J.lo[1] + 3) / 4);
+      f.tiles = (uint32_t)((groups + kFlowStencilGroups - 1) / kFlowStencilGroups);
+    } else if (f.kind == FK_WORKLOAD) {
+      const KernelJob& J = g.kernels[f.first];
+      const uint64_t items = (uint64_t)(J.hi[0] - J.lo[0]) * (J.hi[1] - J.lo[1]) * (J.hi[2] - J.lo[2]);
+      f.tiles = J.kernel == K_NBODY_STEP ? (J.hi[0] - J.lo[0] + kFlowBodies - 1) / kFlowBodies
+                                         : (uint32_t)((items + kFlowItems - 1) / kFlowItems);
+    } else if (f.kind == FK_NONE) {
+      f.tiles = 1;
+    }
+    if (f.tiles == 0) {
+      f.kind = FK_NONE;
+      f.tiles = 1;
+    }
+    f.t_start = f.t_end = 0;
+    tiles += f.tiles;
+  }
+  const uint32_t m = (uint32_t)g.edges.size();
+  auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
+  const size_t o_ctl = 0, o_nodes = al(sizeof(FlowCtl)), o_succ = al(o_nodes + sizeof(FlowNode) * n),
+               o_pend = al(o_succ + 4ull * std::max(m, 1u)), o_claim = al(o_pend + 4ull * n),
+               o_fin = al(o_claim + 4ull * n), o_ready = al(o_fin + 4ull * n), o_cj = al(o_ready + 4ull * n),
+               o_kj = al(o_cj + sizeof(CopyJob) * g.copies.size()), total = al(o_kj + sizeof(KernelJob) * g.kernels.size());
+  const int k = c->jobs_set;
+  c->jobs_set ^= 1;
+  if (!c->jobs_done[k]) CK(cudaEventCreateWithFlags(&c->jobs_done[k], cudaEventDisableTiming));
+  CK(cudaEventSynchronize(c->jobs_done[k]));  // the set's staging is free again
+  if (c->hcap_flow[k] < total) {
+    if (c->h_flow[k]) c->retired_pinned.push_back(c->h_flow[k]);
+    c->h_flow[k] = nullptr;
+    c->hcap_flow[k] = std::max(total, std::max<size_t>(2 * c->hcap_flow[k], 4u << 20));
+    CK(cudaHostAlloc((void**)&c->h_flow[k], c->hcap_flow[k], cudaHostAllocDefault));
+  }
+  uint8_t* H = c->h_flow[k];
+  std::memset(H, 0, o_succ);
+  FlowCtl* ctl = reinterpret_cast<FlowCtl*>(H + o_ctl);
+  std::memcpy(H + o_nodes, g.nodes.data(), sizeof(FlowNode) * n);
+  uint32_t* succ = reinterpret_cast<uint32_t*>(H + o_succ);
+  {
+    std::vector<uint32_t> pos(off.begin(), off.end() - 1);
+    for (const auto& e : g.edges) succ[pos[e.first]++] = e.second;
+  }
+  std::memcpy(H + o_pend, pend.data(), 4ull * n);
+  std::memset(H + o_claim, 0, o_ready - o_claim);
+  uint32_t* ready = reinterpret_cast<uint32_t*>(H + o_ready);
+  uint32_t nready = 0;
+  for (uint32_t i = 0; i < n; ++i)
+    if (pend[i] == 0) ready[nready++] = i;
+  for (uint32_t i = nready; i < n; ++i) ready[i] = 0xFFFFFFFFu;
+  if (nready == 0) return fail_ctx(c, IGS_ERR_STATE, "dataflow graph without a ready node");
+  ctl->tail = nready;
+  if (!g.copies.empty()) std::memcpy(H + o_cj, g.copies.data(), sizeof(CopyJob) * g.copies.size());
+  if (!g.kernels.empty()) std::memcpy(H + o_kj, g.kernels.data(), sizeof(KernelJob) * g.kernels.size());
+  uint8_t* D = nullptr;
+  CK(cudaMallocAsync((void**)&D, total, s));
+  CK(cudaMemcpyAsync(D, H, total, cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(c->jobs_done[k], s));
+  const size_t ev = c->timing ? ev_begin(c, s) : 0;
+  if (igs_launch_flow(reinterpret_cast<FlowCtl*>(D + o_ctl), reinterpret_cast<FlowNode*>(D + o_nodes), n,
+                      reinterpret_cast<uint32_t*>(D + o_succ), reinterpret_cast<uint32_t*>(D + o_pend),
+                      reinterpret_cast<uint32_t*>(D + o_claim), reinterpret_cast<uint32_t*>(D + o_fin),
+                      reinterpret_cast<uint32_t*>(D + o_ready), reinterpret_cast<CopyJob*>(D + o_cj),
+                      reinterpret_cast<KernelJob*>(D + o_kj), 2000000000ull, s))
+    return fail_ctx(c, IGS_ERR_CUDA, "dataflow launch");
+  if (c->timing) ev_end(c, 2, ev, s);
+  c->n_launch[2]++;
+  for (const CopyJob& j : g.copies) c->copy_bytes += 2.0 * j.extent[0] * j.extent[1] * j.extent[2];
+  c->flow_stats[0] += 1;
+  c->flow_stats[1] += n;
+  c->flow_stats[2] += (double)tiles;
+  c->flow_stats[3] += m;
+  if (c->timing) c->flow_keep.push_back(FlowKeep{D, o_nodes, n});
+  else CK(cudaFreeAsync(D, s));
+  for (void* f : g.frees) CK(cudaFreeAsync(f, s));
+  if (!wait) return IGS_OK;
+  CK(cudaStreamSynchronize(s));
+  ev_collect(c);
+  int r = flow_collect(c);
+  if (r) return r;
+  return exec_error_status(c);
 }
 
 ExecAlloc* get_alloc(igs_ctx* c, uint32_t node, uint32_t aid, uint32_t buffer_hint) {
@@ -1064,6 +1304,24 @@ bool stencil_ok(const igs_ctx* c, const KernelJob& J) {
 // Sets *halted_any when some node stopped early.
 int exec_walk(igs_ctx* c, Pending& p, cudaStream_t xs, bool* halted_any, bool* progress) {
   c->exec_call += 1;
+  FlowBuild* g = p.flow;
+  std::vector<uint32_t> walk_start(c->N);
+  for (uint32_t n = 0; n < c->N; ++n) {
+    walk_start[n] = c->nh[n].executed;
+    if (g) c->nh[n].fid.resize(c->nh[n].instrs.size());
+  }
+  // the dataflow node of instruction i of node n; its predecessors walked in
+  // this call become its predecessor nodes (earlier ones have completed)
+  auto flow_node = [&](uint32_t n, uint32_t i, uint32_t kind) -> uint32_t {
+    NodeHost& h = c->nh[n];
+    const uint32_t F = g->add_node(kind);
+    for (uint32_t e = h.first_edge[i]; e < h.first_edge[i + 1]; ++e) {
+      const uint32_t from = h.edges[e].from;
+      if (from >= walk_start[n]) g->edges.push_back({h.fid[from], F});
+    }
+    h.fid[i] = F;
+    return F;
+  };
   std::map<uint32_t, std::vector<std::pair<uint32_t, std::pair<uint32_t, uint32_t>>>> order;
   std::vector<bool> halted(c->N, false);
   std::vector<uint32_t> stop_at(c->N, 0);
@@ -1112,25 +1370,32 @@ int exec_walk(igs_ctx* c, Pending& p, cudaStream_t xs, bool* halted_any, bool* p
               CK(cudaMallocAsync((void**)&a.ptr, cnt ? cnt : 1, xs));
               a.live = true;
               h.allocs[in.a] = a;
+              if (g) flow_node(n, i, FK_NONE);
               break;
             }
             case IGS_FREE: {
               auto it = h.allocs.find(in.a);
               if (it != h.allocs.end()) {
-                if (!it->second.user) p.at(L).frees.push_back(it->second.ptr);
+                if (!it->second.user) {
+                  if (g) g->frees.push_back(it->second.ptr);  // after the launch
+                  else p.at(L).frees.push_back(it->second.ptr);
+                }
                 h.allocs.erase(it);
               }
+              if (g) flow_node(n, i, FK_NONE);
               break;
             }
             case IGS_COPY: {
               ExecAlloc* s = get_alloc(c, n, in.a, in.c);
               ExecAlloc* d = get_alloc(c, n, in.b, in.c);
               if (!s || !d) return fail_ctx(c, IGS_ERR_STATE, "copy between unknown allocations");
+              const uint32_t F = g ? flow_node(n, i, FK_COPY) : 0;
               for (uint32_t k = 0; k < in.box_cnt; ++k) {
                 CopyJob J{};
                 if (!make_copy_job(s->ptr, s->lo, s->hi, d->ptr, d->lo, d->hi, h.boxes[in.box_off + k], c->bufs[in.c].elem, J))
                   return fail_ctx(c, IGS_ERR_STATE, "bad copy box");
-                add_copy(p, L + 1, J);
+                if (g) g->add_copy(F, J);
+                else add_copy(p, L + 1, J);
               }
               h.level[i] = L + 1;
               break;
@@ -1152,7 +1417,12 @@ int exec_walk(igs_ctx* c, Pending& p, cudaStream_t xs, bool* halted_any, bool* p
               CopyJob J{};
               if (!make_copy_job(sa->ptr, sa->lo, sa->hi, sr.mail, sr.box.lo, sr.box.hi, sr.box, elem, J))
                 return fail_ctx(c, IGS_ERR_STATE, "bad send box");
-              add_copy(p, L + 1, J);
+              if (g) {
+                sr.fid = flow_node(n, i, FK_COPY);
+                g->add_copy(sr.fid, J);
+              } else {
+                add_copy(p, L + 1, J);
+              }
               c->sends.insert({key_of(in.seq, in.c, in.b), sr});
               h.level[i] = L + 1;
               break;
@@ -1181,13 +1451,24 @@ int exec_walk(igs_ctx* c, Pending& p, cudaStream_t xs, bool* halted_any, bool* p
                 if (it->second.call == c->exec_call) Lr = std::max(Lr, it->second.level);
               ExecAlloc* d = get_alloc(c, n, in.a, in.c);
               if (!d) return fail_ctx(c, IGS_ERR_STATE, "receive into unknown allocation");
+              uint32_t F = 0;
+              if (g) {
+                F = flow_node(n, i, FK_COPY);
+                for (auto it = range.first; it != range.second; ++it)
+                  if (it->second.call == c->exec_call) g->edges.push_back({it->second.fid, F});
+              }
               for (auto it = range.first; it != range.second; ++it) {
                 const igs_box& b = it->second.box;
                 CopyJob J{};
                 if (!make_copy_job(it->second.mail, b.lo, b.hi, d->ptr, d->lo, d->hi, b, c->bufs[in.c].elem, J))
                   return fail_ctx(c, IGS_ERR_STATE, "bad receive box");
-                add_copy(p, Lr + 1, J);
-                p.at(Lr + 1).frees.push_back(it->second.mail);
+                if (g) {
+                  g->add_copy(F, J);
+                  g->frees.push_back(it->second.mail);
+                } else {
+                  add_copy(p, Lr + 1, J);
+                  p.at(Lr + 1).frees.push_back(it->second.mail);
+                }
               }
               c->sends.erase(range.first, range.second);
               h.level[i] = Lr + 1;
@@ -1232,11 +1513,21 @@ int exec_walk(igs_ctx* c, Pending& p, cudaStream_t xs, bool* halted_any, bool* p
                   A.valid = 1;
                 }
               }
-              if (J.kernel != K_NOP && items) add_kernel(p, L + 1, J, items, stencil_ok(c, J));
+              if (g) {
+                const bool work = J.kernel != K_NOP && items;
+                flow_node(n, i, !work ? FK_NONE : stencil_ok(c, J) ? FK_STENCIL : FK_WORKLOAD);
+                if (work) {
+                  g->kernels.push_back(J);
+                  g->nodes.back().count = 1;
+                }
+              } else if (J.kernel != K_NOP && items) {
+                add_kernel(p, L + 1, J, items, stencil_ok(c, J));
+              }
               h.level[i] = L + 1;
               break;
             }
             default:  // await receive, horizon, epoch: no work of their own
+              if (g) flow_node(n, i, FK_NONE);
               break;
           }
         }
@@ -1264,9 +1555,11 @@ extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
   if (r) return r;
   for (;;) {
     Pending p;
+    FlowBuild g;
+    if (c->executor == IGS_EXEC_DATAFLOW) p.flow = &g;
     bool halted = false, progress = false;
     if ((r = exec_walk(c, p, c->stream, &halted, &progress))) return r;
-    if ((r = run_pending(c, p, c->stream, true))) return r;
+    if ((r = run_walk(c, p, c->stream, true))) return r;
     if (!halted) break;
     if (!progress) break;  // a receive waits for sends not lowered yet: a later call executes it
   }
@@ -1310,9 +1603,9 @@ extern "C" int igs_run(igs_ctx* c, uint32_t window) {
     cudaStreamSynchronize(c->stream);
     c->pipelined = false;
     ev_collect(c);
-    if (code == IGS_OK && igs_exec_error(true))
-      return fail_ctx(c, IGS_ERR_STATE, "a workload kernel accessed outside its allocation");
-    return code;
+    const int fr = flow_collect(c);
+    const int er = exec_error_status(c);
+    return code != IGS_OK ? code : fr != IGS_OK ? fr : er;
   };
   // one launch lowers every pending submission; each node's warp publishes
   // its progress, and the executor follows behind on its own stream
@@ -1346,9 +1639,11 @@ extern "C" int igs_run(igs_ctx* c, uint32_t window) {
       if ((r = fetch_node(c, n, cnt[4 * n], cnt[4 * n + 1], cnt[4 * n + 2], cnt[4 * n + 3], c->cstream)))
         return finish(r);
     Pending p;
+    FlowBuild g;
+    if (c->executor == IGS_EXEC_DATAFLOW) p.flow = &g;
     bool halted = false, progress = false;
     if ((r = exec_walk(c, p, c->xstream, &halted, &progress))) return finish(r);
-    if ((r = run_pending(c, p, c->xstream, false))) return finish(r);
+    if ((r = run_walk(c, p, c->xstream, false))) return finish(r);
     if (done) break;
   }
   // the lowering launch has ended (or failed): its final state, then the rest
@@ -1358,9 +1653,11 @@ extern "C" int igs_run(igs_ctx* c, uint32_t window) {
   if ((r = fetch_for_exec(c))) return finish(r);
   for (;;) {
     Pending p;
+    FlowBuild g;
+    if (c->executor == IGS_EXEC_DATAFLOW) p.flow = &g;
     bool halted = false, progress = false;
     if ((r = exec_walk(c, p, c->xstream, &halted, &progress))) return finish(r);
-    if ((r = run_pending(c, p, c->xstream, false))) return finish(r);
+    if ((r = run_walk(c, p, c->xstream, false))) return finish(r);
     if (!halted || !progress) break;
   }
   return finish(rejected);

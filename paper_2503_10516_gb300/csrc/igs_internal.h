@@ -154,17 +154,18 @@ struct CopyJob {
 }  // namespace igs
 
 // Device entry points implemented in the .cu translation units.
+// Persistent blocks of `warps` warps (1..kMaxWorkers) pulling units from a
+// device work queue (*head, zero before the launch) in the order order_dev
+// (null = index order); extra warps help nodes that have helper scratch.
+int igs_launch_lower_queue(const igs::Unit* units_dev, uint32_t n_units, const uint32_t* order_dev, uint32_t* head_dev,
+                           uint32_t blocks, uint32_t warps, void* stream);
+// One block per unit.
 // reserve: each unit's block also holds most of its SM's registers, keeping
 // other kernels off the SMs that lower (used while the executor runs concurrently).
 // progress (host-mapped, PR_WORDS per unit, or null): each unit publishes its
 // cursor and output counts after every submission it lowers.
 // workers: blocks of kMaxWorkers warps, so that helper warps share each
 // node's kernel phase (when the node has helper scratch).
-// Persistent blocks of `warps` warps (1..kMaxWorkers) pulling units from a
-// device work queue (*head, zero before the launch) in the order order_dev
-// (null = index order); extra warps help nodes that have helper scratch.
-int igs_launch_lower_queue(const igs::Unit* units_dev, uint32_t n_units, const uint32_t* order_dev, uint32_t* head_dev,
-                           uint32_t blocks, uint32_t warps, void* stream);
 int igs_launch_lower(const igs::Unit* units_dev, uint32_t n_units, uint32_t max_items, void* stream,
                      bool reserve = false, volatile uint32_t* progress = nullptr, bool workers = false);
 // Persistent serving loop over n_slots slots; exits when *stop is set or a

@@ -31,7 +31,9 @@ EXPORTS = ("igs_create", "igs_destroy", "igs_create_buffer", "igs_destroy_buffer
            "igs_execute", "igs_read_buffer", "igs_lower_batch", "igs_counters", "igs_last_error", "igs_box_copy",
            "igs_set_timing", "igs_stats", "igs_profile", "igs_lower_static", "igs_submit_epoch",
            "igs_serve_create", "igs_serve_destroy", "igs_serve_attach", "igs_serve_start", "igs_serve_progress",
-           "igs_serve_detach", "igs_serve_stop", "igs_run", "igs_lower_batch_shaped")
+           "igs_serve_detach", "igs_serve_stop", "igs_run", "igs_lower_batch_shaped", "igs_set_executor",
+           "igs_exec_stats")
+EXEC_LEVELS, EXEC_DATAFLOW = 0, 1  # IGS_EXEC_*
 ORDER_SUBMISSION, ORDER_LONGEST_FIRST = 0, 1  # IGS_ORDER_*
 
 
@@ -118,6 +120,8 @@ def lib():
         L.igs_set_lookahead.argtypes = [vp, u32]
         L.igs_flush.argtypes = [vp]
         L.igs_run.argtypes = [vp, u32]
+        L.igs_set_executor.argtypes = [vp, u32]
+        L.igs_exec_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.igs_sync.argtypes = [vp]
         L.igs_submit_epoch.argtypes = [vp]
         L.igs_serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(vp)]
@@ -252,6 +256,17 @@ class Context:
 
     def execute(self, sync: bool = True):
         self._check(lib().igs_execute(self._h, 1 if sync else 0), "execute")
+
+    def set_executor(self, executor: int):
+        """EXEC_LEVELS (by topological level) or EXEC_DATAFLOW (one
+        persistent out-of-order launch per call)."""
+        self._check(lib().igs_set_executor(self._h, executor), "set_executor")
+
+    def exec_stats(self) -> dict:
+        out = (ctypes.c_double * 8)()
+        self._check(lib().igs_exec_stats(self._h, out), "exec_stats")
+        keys = ("launches", "nodes", "tiles", "edges", "span_ms", "copy_busy_ms", "kernel_busy_ms", "overlap_ms")
+        return dict(zip(keys, list(out)))
 
     def run(self, window: int = 64):
         """Lowers the pending submissions in windows of `window` items while the

@@ -243,7 +243,7 @@ int igs_execute(igs_ctx* ctx, uint32_t flags);
  * completed) in ONE persistent launch per call: every instruction is a node
  * with a predecessor count and a successor list (its graph edges within the
  * call, plus send -> matching receive), its work is split into tiles (64 KiB
- * copy segments, 16384-element stencil tiles, 1024-item workload tiles, 256
+ * copy segments, stencil tiles of 16 rows x 1024 columns, 1024-item workload tiles, 256
  * N-body bodies) and blocks take tiles of whichever nodes are ready, so
  * copies, kernels and transfers of different devices, nodes and tasks run
  * concurrently. Frees of the call run after the launch. Results are
@@ -260,6 +260,14 @@ int igs_set_executor(igs_ctx* ctx, uint32_t executor);
  * [6] the same for kernel nodes, [7] ms during which both were (copy / kernel
  * overlap). Waits for the context's streams. */
 int igs_exec_stats(igs_ctx* ctx, double out[8]);
+
+/* Self-test of the dataflow executor's bounded wait on the current device:
+ * launches it over a two-node cycle (a graph no lowering emits, so no node
+ * ever becomes ready) with a wait limit of wait_ms (1..10000). Returns
+ * IGS_ERR_TIMEOUT when every block gave up waiting and the launch ended, as
+ * designed (the device stays usable), IGS_OK if the launch ended without
+ * giving up (a defect), IGS_ERR_INVALID_ARG / IGS_ERR_CUDA otherwise. */
+int igs_selftest_flow_wait(uint32_t wait_ms);
 
 /* Lowers every pending submission and executes the whole graph with the
  * scheduler running ahead of the executor (Sec. 4: instruction generation

@@ -14,6 +14,8 @@ __device__ uint32_t g_exec_error = 0;
 
 namespace {
 
+constexpr unsigned FULL_MASK = 0xFFFFFFFFu;
+
 // Load policies. Kernels of the level executor read through L1 (plain) or
 // with streaming hints; the dataflow executor's blocks read data that other
 // blocks of the same launch wrote, so every data load there goes to L2
@@ -396,6 +398,99 @@ __device__ __forceinline__ void stencil_range(const KernelJob& J, uint64_t g0, u
   }
 }
 
+// One dataflow tile of a stencil job: rows [ya, ya + kFlowStencilRows) of a
+// strip of kFlowThreads groups. Each thread walks down its four columns,
+// keeping the north and centre rows in registers, and takes the west and east
+// neighbours from the adjacent lanes, so u is read about once per element;
+// the arithmetic and its order are those of stencil_range. Warps whose groups
+// are not all full 16-byte vectors take stencil_range row by row.
+template <class Ld>
+__device__ __forceinline__ void stencil_tile(const KernelJob& J, uint32_t t) {
+  const bool wave = J.kernel == K_WAVE;
+  const KAcc& U = J.acc[wave ? 1 : 0];
+  const KAcc& O = J.acc[wave ? 2 : 1];
+  const KAcc& P = J.acc[0];
+  const uint32_t H = U.ext[0], W = U.ext[1];
+  const uint32_t y0 = J.lo[0], y1 = J.hi[0], x0 = J.lo[1], x1 = J.hi[1];
+  const uint32_t groups = (x1 - x0 + 3) / 4;
+  const uint32_t strips = (groups + kFlowThreads - 1) / kFlowThreads;
+  const uint32_t ya = y0 + (t / strips) * kFlowStencilRows, yb = min(ya + kFlowStencilRows, y1);
+  const uint32_t gi = (t % strips) * kFlowThreads + threadIdx.x;
+  const uint32_t glast = (t % strips) * kFlowThreads + (threadIdx.x | 31u);  // this warp's last group
+  const uint32_t uw = U.hi[1] - U.lo[1], ow = O.hi[1] - O.lo[1], pw = P.hi[1] - P.lo[1];
+  const float* u = reinterpret_cast<const float*>(U.ptr);
+  const float* pv = reinterpret_cast<const float*>(P.ptr);
+  float* o = reinterpret_cast<float*>(O.ptr);
+  const bool vec = ((x0 - U.lo[1]) % 4 == 0) && uw % 4 == 0 && ((x0 - O.lo[1]) % 4 == 0) && ow % 4 == 0 &&
+                   (!wave || (((x0 - P.lo[1]) % 4 == 0) && pw % 4 == 0)) &&
+                   ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(o) |
+                     (wave ? reinterpret_cast<uintptr_t>(pv) : 0u)) & 15u) == 0;
+  if (!(vec && x0 + 4 * glast + 4 <= x1)) {
+    for (uint32_t y = ya; y < yb; ++y)
+      if (gi < groups) {
+        const uint64_t g = (uint64_t)(y - y0) * groups + gi;
+        stencil_range<Ld>(J, g, g + 1, 1);
+      }
+    return;
+  }
+  const uint32_t xs = x0 + 4 * gi, lane = threadIdx.x & 31u;
+  const float* ubase = u - U.lo[1] + xs;
+  const float* pbase = pv - P.lo[1] + xs;
+  float4 c4 = Ld::ld(reinterpret_cast<const float4*>(ubase + (size_t)(ya - U.lo[0]) * uw));
+  float4 n4 = ya > 0 ? Ld::ld(reinterpret_cast<const float4*>(ubase + (size_t)(ya - 1 - U.lo[0]) * uw)) : c4;
+  // rows in batches of kRows: every load of a batch is issued before the
+  // first row of the batch is computed (more bytes in flight per thread)
+  constexpr uint32_t kRows = 4;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (uint32_t y = ya; y < yb; y += kRows) {
+    float4 sx[kRows], px[kRows];
+#pragma unroll
+    for (uint32_t r = 0; r < kRows; ++r) {
+      const uint32_t yr = y + r;
+      sx[r] = yr < yb && yr + 1 < H ? Ld::ld(reinterpret_cast<const float4*>(ubase + (size_t)(yr + 1 - U.lo[0]) * uw))
+                                    : zero;
+      px[r] = wave && yr < yb ? Ld::ld(reinterpret_cast<const float4*>(pbase + (size_t)(yr - P.lo[0]) * pw)) : zero;
+    }
+#pragma unroll
+    for (uint32_t r = 0; r < kRows; ++r) {
+      const uint32_t yr = y + r;
+      if (yr >= yb) break;
+      const float4 s4 = yr + 1 < H ? sx[r] : c4;
+      const float* ur = ubase + (size_t)(yr - U.lo[0]) * uw;  // column xs of row yr
+      float west = __shfl_up_sync(FULL_MASK, c4.w, 1), east = __shfl_down_sync(FULL_MASK, c4.x, 1);
+      if (lane == 0) west = xs > 0 ? Ld::ld(ur - 1) : 0.f;
+      if (lane == 31) east = xs + 4 < W ? Ld::ld(ur + 4) : 0.f;
+      const float cs[6] = {west, c4.x, c4.y, c4.z, c4.w, east};
+      const float ns[4] = {n4.x, n4.y, n4.z, n4.w}, ss[4] = {s4.x, s4.y, s4.z, s4.w},
+                  ps[4] = {px[r].x, px[r].y, px[r].z, px[r].w};
+      const bool row_in = yr > 0 && yr + 1 < H;
+      float out[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t x = xs + k;
+        const float c = cs[k + 1];
+        float v = c;
+        if (row_in && x > 0 && x + 1 < W) {
+          const float n = ns[k], s = ss[k], w = cs[k], e = cs[k + 2];
+          if (!wave) {
+            v = ((n + s) + (w + e)) * 0.25f;
+          } else {
+            const float t2 = (2.0f * c) - ps[k];
+            const float t5 = (n + s) + (w + e);
+            const float t8 = 0.25f * (t5 - 4.0f * c);
+            v = t2 + t8;
+          }
+        }
+        out[k] = v;
+      }
+      float* orow = o + (size_t)(yr - O.lo[0]) * ow - O.lo[1];
+      __stcs(reinterpret_cast<float4*>(orow + xs), make_float4(out[0], out[1], out[2], out[3]));
+      n4 = c4;
+      c4 = s4;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) stencil_kernel(const KernelJob* __restrict__ jobs) {
   const KernelJob& J = jobs[blockIdx.y];
   stencil_range<LdStream>(J, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, stencil_groups(J),
@@ -448,10 +543,7 @@ __device__ void run_tile(const FlowNode& F, uint32_t t, const CopyJob* __restric
     const uint32_t j = F.first + find_job(cjobs + F.first, F.count, t);
     copy_unit<LdL2>(cjobs[j], t - cjobs[j].unit_begin);
   } else if (F.kind == FK_STENCIL) {
-    const KernelJob& J = kjobs[F.first];
-    const uint64_t g0 = (uint64_t)t * kFlowStencilGroups;
-    const uint64_t g1 = min(g0 + kFlowStencilGroups, stencil_groups(J));
-    stencil_range<LdL2>(J, g0 + threadIdx.x, g1, blockDim.x);
+    stencil_tile<LdL2>(kjobs[F.first], t);
   } else if (F.kind == FK_WORKLOAD) {
     const KernelJob& J = kjobs[F.first];
     const uint32_t e1 = J.hi[1] - J.lo[1], e2 = J.hi[2] - J.lo[2];
@@ -474,18 +566,18 @@ __device__ void run_tile(const FlowNode& F, uint32_t t, const CopyJob* __restric
   }
 }
 
-__global__ void __launch_bounds__(kFlowThreads) flow_kernel(FlowCtl* ctl, FlowNode* nodes, uint32_t n_nodes,
+__global__ void __launch_bounds__(kFlowThreads, 3) flow_kernel(FlowCtl* ctl, FlowNode* nodes, uint32_t n_nodes,
                                                             const uint32_t* __restrict__ succ, uint32_t* pending,
                                                             uint32_t* claimed, uint32_t* finished,
                                                             volatile uint32_t* ready,
                                                             const CopyJob* __restrict__ cjobs,
                                                             const KernelJob* __restrict__ kjobs, uint64_t wait_ns) {
-  __shared__ uint32_t s_node, s_tile, s_stop;
+  __shared__ uint32_t s_node, s_tile, s_cnt, s_stop;
   __shared__ float4 s_body[kFlowBodies];
   volatile FlowCtl* vc = ctl;
   for (;;) {
     if (threadIdx.x == 0) {
-      uint32_t stop = 0, node = 0, tile = 0, polls = 0, nap = 32;
+      uint32_t stop = 0, node = 0, tile = 0, cnt = 0, polls = 0, nap = 32;
       unsigned long long seen = vc->tiles_done, since = gtimer();
       for (;;) {
         const uint32_t h = vc->head;
@@ -497,12 +589,15 @@ __global__ void __launch_bounds__(kFlowThreads) flow_kernel(FlowCtl* ctl, FlowNo
         if (q != 0xFFFFFFFFu) {
           __threadfence();  // the tile's loads come after its predecessors' stores
           const uint32_t tiles = nodes[q].tiles;
-          // a plain look first, so that blocks arriving late at a node whose
-          // tiles are all taken do not pile atomics onto it
-          const uint32_t t = *(volatile uint32_t*)&claimed[q] < tiles ? atomicAdd(&claimed[q], 1u) : tiles;
+          // several consecutive tiles per claim on large nodes (fewer round
+          // trips per byte); a plain look first, so that blocks arriving late
+          // at a node whose tiles are all taken do not pile atomics onto it
+          const uint32_t k = tiles >= 64 ? 4u : tiles >= 16 ? 2u : 1u;
+          const uint32_t t = *(volatile uint32_t*)&claimed[q] < tiles ? atomicAdd(&claimed[q], k) : tiles;
           if (t < tiles) {
             node = q;
             tile = t;
+            cnt = min(k, tiles - t);
             if (t == 0) nodes[q].t_start = gtimer();
             break;
           }
@@ -536,16 +631,17 @@ __global__ void __launch_bounds__(kFlowThreads) flow_kernel(FlowCtl* ctl, FlowNo
       s_stop = stop;
       s_node = node;
       s_tile = tile;
+      s_cnt = cnt;
     }
     __syncthreads();
     if (s_stop) break;
-    const uint32_t q = s_node;
-    run_tile(nodes[q], s_tile, cjobs, kjobs, s_body);
+    const uint32_t q = s_node, n_run = s_cnt;
+    for (uint32_t i = 0; i < n_run; ++i) run_tile(nodes[q], s_tile + i, cjobs, kjobs, s_body);
     __syncthreads();
     if (threadIdx.x == 0) {
-      __threadfence();  // this tile's stores before its count
-      const uint32_t f = atomicAdd(&finished[q], 1u) + 1u;
-      atomicAdd(&ctl->tiles_done, 1ull);
+      __threadfence();  // these tiles' stores before their count
+      const uint32_t f = atomicAdd(&finished[q], n_run) + n_run;
+      atomicAdd(&ctl->tiles_done, (unsigned long long)n_run);
       const FlowNode& F = nodes[q];
       if (f == F.tiles) {
         nodes[q].t_end = gtimer();

@@ -30,9 +30,10 @@ struct KernelJob {
 // tiles that any block may run once every predecessor node has finished.
 enum FlowKind : uint32_t { FK_NONE = 0, FK_COPY = 1, FK_STENCIL = 2, FK_WORKLOAD = 3 };
 
-// Tile sizes: stencil groups of four columns, workload items, N-body bodies.
+// Tile sizes: a stencil tile is kFlowStencilRows rows of a strip of
+// kFlowThreads groups of four columns; workload items; N-body bodies.
 constexpr uint32_t kFlowThreads = 256;
-constexpr uint32_t kFlowStencilGroups = 4096;
+constexpr uint32_t kFlowStencilRows = 16;
 constexpr uint32_t kFlowItems = 1024;
 constexpr uint32_t kFlowBodies = kFlowThreads;
 

@@ -555,6 +555,50 @@ int igs_exec_stats(igs_ctx* c, double out[8]) {
   return IGS_OK;
 }
 
+int igs_selftest_flow_wait(uint32_t wait_ms) {
+  if (wait_ms < 1 || wait_ms > 10000) return IGS_ERR_INVALID_ARG;
+  // layout: control block, two nodes, successor list {1, 0}, pending {1, 1},
+  // claimed, finished, ready (both empty)
+  const size_t o_nodes = 64, o_succ = o_nodes + 2 * sizeof(FlowNode), o_pend = o_succ + 16, o_claim = o_pend + 16,
+               o_fin = o_claim + 16, o_ready = o_fin + 16, total = o_ready + 16;
+  std::vector<uint8_t> H(total, 0);
+  FlowNode* nodes = reinterpret_cast<FlowNode*>(H.data() + o_nodes);
+  for (int i = 0; i < 2; ++i) {
+    nodes[i].kind = FK_NONE;
+    nodes[i].tiles = 1;
+    nodes[i].succ_off = (uint32_t)i;
+    nodes[i].succ_cnt = 1;
+  }
+  uint32_t* succ = reinterpret_cast<uint32_t*>(H.data() + o_succ);
+  succ[0] = 1;
+  succ[1] = 0;
+  uint32_t* pend = reinterpret_cast<uint32_t*>(H.data() + o_pend);
+  pend[0] = pend[1] = 1;
+  uint32_t* ready = reinterpret_cast<uint32_t*>(H.data() + o_ready);
+  ready[0] = ready[1] = 0xFFFFFFFFu;
+  uint8_t* D = nullptr;
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return IGS_ERR_CUDA;
+  int r = IGS_ERR_CUDA;
+  if (cudaMalloc((void**)&D, total) == cudaSuccess &&
+      cudaMemcpy(D, H.data(), total, cudaMemcpyHostToDevice) == cudaSuccess &&
+      igs_launch_flow(reinterpret_cast<FlowCtl*>(D), reinterpret_cast<FlowNode*>(D + o_nodes), 2,
+                      reinterpret_cast<uint32_t*>(D + o_succ), reinterpret_cast<uint32_t*>(D + o_pend),
+                      reinterpret_cast<uint32_t*>(D + o_claim), reinterpret_cast<uint32_t*>(D + o_fin),
+                      reinterpret_cast<uint32_t*>(D + o_ready), nullptr, nullptr, (uint64_t)wait_ms * 1000000ull,
+                      s) == 0 &&
+      cudaStreamSynchronize(s) == cudaSuccess) {
+    FlowCtl ctl;
+    if (cudaMemcpy(&ctl, D, sizeof ctl, cudaMemcpyDeviceToHost) == cudaSuccess) {
+      const int e = igs_exec_error(true);
+      r = (ctl.error && e >= 0 && (e & 2)) ? IGS_ERR_TIMEOUT : IGS_OK;
+    }
+  }
+  if (D) cudaFree(D);
+  cudaStreamDestroy(s);
+  return r;
+}
+
 int igs_set_timing(igs_ctx* c, int on) {
   if (!c) return IGS_ERR_INVALID_ARG;
   c->timing = on != 0;
@@ -1119,8 +1163,8 @@ int run_flow(igs_ctx* c, FlowBuild& g, cudaStream_t s, bool wait) {
     if (f.kind == FK_COPY && f.count == 0) f.kind = FK_NONE;
     if (f.kind == FK_STENCIL) {
       const KernelJob& J = g.kernels[f.first];
-      const uint64_t groups = (uint64_t)(J.hi[0] - J.lo[0]) * ((J.hi[1] - J.lo[1] + 3) / 4);
-      f.tiles = (uint32_t)((groups + kFlowStencilGroups - 1) / kFlowStencilGroups);
+      const uint32_t strips = ((J.hi[1] - J.lo[1] + 3) / 4 + kFlowThreads - 1) / kFlowThreads;
+      f.tiles = strips * ((J.hi[0] - J.lo[0] + kFlowStencilRows - 1) / kFlowStencilRows);
     } else if (f.kind == FK_WORKLOAD) {
       const KernelJob& J = g.kernels[f.first];
       const uint64_t items = (uint64_t)(J.hi[0] - J.lo[0]) * (J.hi[1] - J.lo[1]) * (J.hi[2] - J.lo[2]);

@@ -32,7 +32,7 @@ EXPORTS = ("igs_create", "igs_destroy", "igs_create_buffer", "igs_destroy_buffer
            "igs_set_timing", "igs_stats", "igs_profile", "igs_lower_static", "igs_submit_epoch",
            "igs_serve_create", "igs_serve_destroy", "igs_serve_attach", "igs_serve_start", "igs_serve_progress",
            "igs_serve_detach", "igs_serve_stop", "igs_run", "igs_lower_batch_shaped", "igs_set_executor",
-           "igs_exec_stats")
+           "igs_exec_stats", "igs_selftest_flow_wait")
 EXEC_LEVELS, EXEC_DATAFLOW = 0, 1  # IGS_EXEC_*
 ORDER_SUBMISSION, ORDER_LONGEST_FIRST = 0, 1  # IGS_ORDER_*
 
@@ -122,6 +122,7 @@ def lib():
         L.igs_run.argtypes = [vp, u32]
         L.igs_set_executor.argtypes = [vp, u32]
         L.igs_exec_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.igs_selftest_flow_wait.argtypes = [u32]
         L.igs_sync.argtypes = [vp]
         L.igs_submit_epoch.argtypes = [vp]
         L.igs_serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(vp)]
@@ -368,6 +369,13 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def selftest_flow_wait(wait_ms: int) -> int:
+    """Runs the dataflow executor's bounded-wait self-test (a graph in which
+    nothing ever becomes ready); returns the status code (IGS_ERR_TIMEOUT
+    when the wait gave up as designed)."""
+    return lib().igs_selftest_flow_wait(wait_ms)
 
 
 def lower_batch(ctxs: Sequence[Context], shape: Optional[Tuple[int, ...]] = None):

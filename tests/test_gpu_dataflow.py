@@ -170,3 +170,18 @@ def test_bad_executor_is_rejected():
     with pytest.raises(igs.IgsError):
         g.ctx.set_executor(7)
     g.ctx.close()
+
+
+def test_bounded_wait_gives_up_and_device_stays_usable():
+    """A graph in which nothing ever becomes ready: every block waits, gives
+    up after the limit, and the launch ends with the timeout status; the
+    device then runs a normal dataflow execute."""
+    import time
+
+    from paper_2503_10516_gb300 import igs
+    t0 = time.perf_counter()
+    r = igs.selftest_flow_wait(200)
+    dt = time.perf_counter() - t0
+    assert r == igs.IGS_ERR_TIMEOUT
+    assert 0.15 < dt < 10.0
+    _run(W.jacobi_program())

@@ -685,13 +685,41 @@ def run_gpu(args):
     return 0
 
 
+def run_profile_case(args):
+    """Small fixed cases for profiler captures (no timing, no JSON metric):
+    flow_wave16 = the first 16 wave tasks on 8192^2 buffers, lowered, then
+    executed by the dataflow executor; done twice (capture the second)."""
+    from paper_2503_10516_gb300 import igs
+    p = W.wave_program(n=N, steps=16, nodes=NODES, devices=DEVICES, chunks=CHUNKS, lookahead=LOOKAHEAD,
+                       horizon_step=HSTEP)
+    for _ in range(2):
+        c = igs.Context(p.nodes, p.devices, p.horizon_step, p.lookahead, mode=igs.MODE_BATCHED)
+        c.set_executor(igs.EXEC_DATAFLOW)
+        for op in p.ops:
+            if op[0] == "buffer":
+                b = op[1]
+                c.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init)
+            elif op[0] == "task":
+                c.submit(op[1])
+        c.flush()
+        c.execute()
+        n = int(c.counters()["instructions"])
+        c.close()
+    print(json.dumps({"case": args.profile_case, "instructions": n}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="igs", choices=["igs", "reference"])
+    ap.add_argument("--profile-case", default=None, choices=["flow_wave16"],
+                    help="run one small fixed case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -53,6 +53,7 @@ extern "C" {
 #define IGS_ERR_CUDA -6             /* a CUDA runtime call failed */
 #define IGS_ERR_BUDGET -7           /* HBM admission budget exceeded (serving) */
 #define IGS_ERR_STATE -8            /* call not valid in the context's current state */
+#define IGS_ERR_OUT_OF_BOUNDS -9    /* a kernel accessed outside its accessor's range (Sec. 4.4) */
 
 /* ---- instruction types (Table 1) and dependency kinds (Fig. 5 legend) ---- */
 enum igs_instruction_type {
@@ -260,6 +261,26 @@ int igs_set_executor(igs_ctx* ctx, uint32_t executor);
  * [6] the same for kernel nodes, [7] ms during which both were (copy / kernel
  * overlap). Waits for the context's streams. */
 int igs_exec_stats(igs_ctx* ctx, double out[8]);
+
+/* Accessor bounds checking (Sec. 4.4): every element a workload kernel
+ * reads or writes through an accessor is checked against the box the
+ * accessor's range mapper grants the kernel's chunk (the binding box of its
+ * instruction). Indices outside it are collected per (kernel instruction,
+ * accessor) into a bounding box; the access itself is carried out when it lies
+ * inside the allocation, skipped otherwise. After an igs_execute / igs_run
+ * whose kernels produced such indices, that call returns
+ * IGS_ERR_OUT_OF_BOUNDS once all work has run, and igs_bounds_errors lists
+ * every record so far (the stencil fast path is only taken where the
+ * permitted boxes cover everything it touches). Writes up to cap records;
+ * *count = total. */
+typedef struct igs_bounds_error {
+  uint32_t seq;       /* submission sequence number of the task */
+  uint32_t node;      /* virtual node of the kernel instruction */
+  uint32_t chunk;     /* chunk index */
+  uint32_t accessor;  /* accessor index within the task */
+  uint32_t lo[3], hi[3];  /* bounding box of the out-of-range indices */
+} igs_bounds_error;
+int igs_bounds_errors(igs_ctx* ctx, igs_bounds_error* out, uint32_t cap, uint32_t* count);
 
 /* Self-test of the dataflow executor's bounded wait on the current device:
  * launches it over a two-node cycle (a graph no lowering emits, so no node

@@ -99,11 +99,24 @@ __global__ void __launch_bounds__(256) box_copy_kernel(const CopyJob* __restrict
 
 // ---- workload kernels ---------------------------------------------------------
 
-// Address of element p in an allocation; nullptr (and the error flag) if p
-// lies outside the allocation's box or the accessor has no allocation.
+// Address of element p in an allocation. An index outside the accessor's
+// permitted box (its range mapper's box for this chunk; Sec. 4.4 accessor
+// bounds checking) is added to the accessor's out-of-bounds record. An index
+// outside the allocation is skipped (nullptr); if it was permitted, that is
+// an executor defect and sets the error flag.
 __device__ __forceinline__ uint8_t* elem_ptr(const KAcc& a, uint32_t p0, uint32_t p1, uint32_t p2) {
+  const bool permitted = a.valid && p0 >= a.plo[0] && p0 < a.phi[0] && p1 >= a.plo[1] && p1 < a.phi[1] &&
+                         p2 >= a.plo[2] && p2 < a.phi[2];
+  if (!permitted && a.oob) {
+    atomicMax(a.oob + 0, ~p0);
+    atomicMax(a.oob + 1, ~p1);
+    atomicMax(a.oob + 2, ~p2);
+    atomicMax(a.oob + 3, p0 + 1);
+    atomicMax(a.oob + 4, p1 + 1);
+    atomicMax(a.oob + 5, p2 + 1);
+  }
   if (!a.valid || p0 < a.lo[0] || p0 >= a.hi[0] || p1 < a.lo[1] || p1 >= a.hi[1] || p2 < a.lo[2] || p2 >= a.hi[2]) {
-    atomicOr(&g_exec_error, 1u);
+    if (permitted) atomicOr(&g_exec_error, 1u);
     return nullptr;
   }
   const uint64_t w1 = a.hi[1] - a.lo[1], w2 = a.hi[2] - a.lo[2];
@@ -242,6 +255,20 @@ __device__ void run_item(const KernelJob& J, uint32_t y, uint32_t x, uint32_t z)
         const float v = last * 0.5f + (float)(yy & 255u);
         stf(J.acc[1], yy, x, v);
       }
+      break;
+    }
+    case K_SHIFT: {
+      // a test kernel that may reach past its accessor's range on purpose
+      const int64_t q0 = (int64_t)y + (int32_t)J.params[0], q1 = (int64_t)x + (int32_t)J.params[1],
+                    q2 = (int64_t)z + (int32_t)J.params[2];
+      const KAcc& A = J.acc[0];
+      float v = 0.0f;
+      if (q0 >= 0 && q1 >= 0 && q2 >= 0 && q0 < A.ext[0] && q1 < A.ext[1] && q2 < A.ext[2]) {
+        const uint8_t* p = elem_ptr(A, (uint32_t)q0, (uint32_t)q1, (uint32_t)q2);
+        if (p) v = Ld::ld(reinterpret_cast<const float*>(p));
+      }
+      uint8_t* d = elem_ptr(J.acc[1], y, x, z);
+      if (d) *reinterpret_cast<float*>(d) = v;
       break;
     }
     case K_GENERIC: {

@@ -7,18 +7,29 @@
 namespace igs {
 
 // Workload kernels run by device-kernel instructions.
-enum WorkloadKernel : uint32_t { K_NOP = 0, K_JACOBI = 1, K_WAVE = 2, K_NBODY_STEP = 3, K_NBODY_UPDATE = 4, K_GROW = 5, K_GENERIC = 6 };
+enum WorkloadKernel : uint32_t {
+  K_NOP = 0, K_JACOBI = 1, K_WAVE = 2, K_NBODY_STEP = 3, K_NBODY_UPDATE = 4, K_GROW = 5, K_GENERIC = 6,
+  K_SHIFT = 7  // reads accessor 0 at item + offset (params 0-2, int32), writes it to accessor 1 at item
+};
+
+// Words of one accessor's out-of-bounds record: ~lo[3] then hi[3], both
+// combined with atomicMax from zero (so the record is the bounding box of
+// every index outside the accessor's permitted box; all zero = none).
+constexpr uint32_t kOobWords = 6;
 
 struct KAcc {
   uint8_t* ptr;            // allocation base
   uint32_t lo[3], hi[3];   // allocation box
+  uint32_t plo[3], phi[3]; // permitted box: what the range mapper grants this chunk
+  uint32_t* oob;           // out-of-bounds record (kOobWords), or null
   uint32_t ext[3];         // buffer extent
   uint32_t dims, mode, elem, valid;
   igs_map_dim map[3];
 };
 
 struct KernelJob {
-  uint32_t kernel, seq, nacc, pad;
+  uint32_t kernel, seq, nacc;
+  uint32_t oob_slot;  // index of the job's out-of-bounds records (IGS_MAX_ACCESSORS of them)
   uint32_t lo[3], hi[3];  // chunk box (kernel index space)
   uint32_t params[4];
   uint64_t item_begin;

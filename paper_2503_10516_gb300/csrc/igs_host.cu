@@ -53,6 +53,17 @@ struct NodeHost {
   std::vector<uint32_t> fid;         // dataflow node per instruction (current execute call)
 };
 
+// Which kernel instruction an out-of-bounds record slot belongs to.
+struct OobMeta {
+  uint32_t seq, node, chunk, nacc;
+};
+
+// A call's out-of-bounds records, kept until they have been read back.
+struct OobKeep {
+  uint32_t* rec;
+  uint32_t first, count;  // slots [first, first + count)
+};
+
 // A dataflow launch kept until its node timestamps have been read back.
 struct FlowKeep {
   void* arena;
@@ -120,6 +131,11 @@ struct igs_ctx {
   // memory waits for the whole device, which would stall the host loop of a
   // pipelined run behind the lowering launch
   std::vector<void*> retired_pinned;
+  // accessor bounds checking: one slot per kernel job, read back at sync points
+  std::vector<OobMeta> oob_meta;
+  std::vector<OobKeep> oob_keep;
+  std::vector<igs_bounds_error> bounds;
+  bool oob_pending = false;  // violations found since the last execute / run returned
   double flow_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   uint64_t launches = 0;
   size_t arena_bytes = 0;
@@ -333,6 +349,8 @@ size_t table_bytes(uint32_t cap) { return (size_t)F_COUNT * cap * sizeof(uint32_
 
 namespace {
 int flow_collect(igs_ctx* c);
+int oob_collect(igs_ctx* c);
+int oob_status(igs_ctx* c);
 }  // namespace
 
 extern "C" {
@@ -489,6 +507,7 @@ void igs_destroy(igs_ctx* c) {
   for (auto& sr : c->sends)
     if (sr.second.mail) cudaFree(sr.second.mail);
   for (auto& f : c->flow_keep) cudaFree(f.arena);
+  for (auto& o : c->oob_keep) cudaFree(o.rec);
   for (void* p : c->retired_pinned) cudaFreeHost(p);
   for (int k = 0; k < 2; ++k) {
     if (c->h_flow[k]) cudaFreeHost(c->h_flow[k]);
@@ -535,6 +554,17 @@ int igs_profile(igs_ctx* c, uint64_t out[32]) {
   std::memset(out, 0, sizeof(uint64_t) * 32);
   for (const NodeDev& nd : c->nodes_host)
     for (int k = 0; k < 32; ++k) out[k] += nd.prof[k];
+  return IGS_OK;
+}
+
+int igs_bounds_errors(igs_ctx* c, igs_bounds_error* out, uint32_t cap, uint32_t* count) {
+  if (!c || !count || (cap && !out)) return IGS_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->xstream) CK(cudaStreamSynchronize(c->xstream));
+  int r = oob_collect(c);
+  if (r) return r;
+  *count = (uint32_t)c->bounds.size();
+  for (uint32_t i = 0; i < cap && i < c->bounds.size(); ++i) out[i] = c->bounds[i];
   return IGS_OK;
 }
 
@@ -871,6 +901,7 @@ struct LevelWork {
 // The dataflow graph of one execute call: a node per walked instruction, its
 // copy or kernel jobs, (predecessor, successor) pairs, deferred frees.
 struct FlowBuild {
+  uint32_t oob_first = 0;  // first out-of-bounds slot of this call
   std::vector<FlowNode> nodes;
   std::vector<std::pair<uint32_t, uint32_t>> edges;
   std::vector<CopyJob> copies;
@@ -896,6 +927,7 @@ struct FlowBuild {
 
 struct Pending {
   FlowBuild* flow = nullptr;  // set: build the dataflow graph instead of levels
+  uint32_t oob_first = 0;     // first out-of-bounds slot of this call
   std::vector<LevelWork> levels;
   LevelWork& at(uint32_t L) {
     if (levels.size() <= L) levels.resize(L + 1);
@@ -1005,8 +1037,64 @@ int grow_pinned(igs_ctx* c, T*& ptr, uint32_t& cap, size_t need) {
   return IGS_OK;
 }
 
+// Allocates (zeroed, on stream s) the out-of-bounds records of kernel job
+// slots [first, c->oob_meta.size()) and points every accessor of the given
+// jobs at its record.
+int oob_prepare(igs_ctx* c, KernelJob* jobs, size_t n, uint32_t first, cudaStream_t s) {
+  const uint32_t count = (uint32_t)c->oob_meta.size() - first;
+  if (count == 0 || n == 0) return IGS_OK;
+  const size_t words = (size_t)count * IGS_MAX_ACCESSORS * kOobWords;
+  uint32_t* rec = nullptr;
+  CK(cudaMallocAsync((void**)&rec, words * sizeof(uint32_t), s));
+  CK(cudaMemsetAsync(rec, 0, words * sizeof(uint32_t), s));
+  for (size_t j = 0; j < n; ++j)
+    for (uint32_t a = 0; a < IGS_MAX_ACCESSORS; ++a)
+      jobs[j].acc[a].oob = rec + ((size_t)(jobs[j].oob_slot - first) * IGS_MAX_ACCESSORS + a) * kOobWords;
+  c->oob_keep.push_back(OobKeep{rec, first, count});
+  return IGS_OK;
+}
+
+// Reads back the out-of-bounds records of completed calls into c->bounds.
+int oob_collect(igs_ctx* c) {
+  for (const OobKeep& k : c->oob_keep) {
+    std::vector<uint32_t> h((size_t)k.count * IGS_MAX_ACCESSORS * kOobWords);
+    CK(cudaMemcpy(h.data(), k.rec, h.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    CK(cudaFree(k.rec));
+    for (uint32_t i = 0; i < k.count; ++i) {
+      const OobMeta& m = c->oob_meta[k.first + i];
+      for (uint32_t a = 0; a < m.nacc && a < IGS_MAX_ACCESSORS; ++a) {
+        const uint32_t* w = h.data() + ((size_t)i * IGS_MAX_ACCESSORS + a) * kOobWords;
+        if (!w[3]) continue;
+        igs_bounds_error e{};
+        e.seq = m.seq;
+        e.node = m.node;
+        e.chunk = m.chunk;
+        e.accessor = a;
+        for (int d = 0; d < 3; ++d) {
+          e.lo[d] = ~w[d];
+          e.hi[d] = w[3 + d];
+        }
+        c->bounds.push_back(e);
+        c->oob_pending = true;
+      }
+    }
+  }
+  c->oob_keep.clear();
+  return IGS_OK;
+}
+
+// IGS_ERR_OUT_OF_BOUNDS once per execute / run that met accessor violations.
+int oob_status(igs_ctx* c) {
+  if (!c->oob_pending) return IGS_OK;
+  c->oob_pending = false;
+  return fail_ctx(c, IGS_ERR_OUT_OF_BOUNDS,
+                  "a kernel accessed elements outside its accessor's range-mapper box (igs_bounds_errors lists them)");
+}
+
 // Reads and clears the execution error flags (after the stream has completed).
 int exec_error_status(igs_ctx* c) {
+  const int ro = oob_collect(c);
+  if (ro) return ro;
   const int e = igs_exec_error(true);
   if (e < 0) return fail_ctx(c, IGS_ERR_CUDA, "reading the execution error flags");
   if (e & 2) return fail_ctx(c, IGS_ERR_TIMEOUT, "the dataflow executor saw no tile finish for 2 s and gave up");
@@ -1044,6 +1132,7 @@ int run_pending(igs_ctx* c, Pending& p, cudaStream_t s, bool wait) {
     std::copy(w.stencils.begin(), w.stencils.end(), c->h_kjobs[k] + nk);
     nk += w.stencils.size();
   }
+  if ((r = oob_prepare(c, c->h_kjobs[k], nk, p.oob_first, s))) return r;
   if (nc) {
     if ((r = grow_device_async(c, c->d_cjobs[k], c->cap_cjobs[k], nc, s))) return r;
     CK(cudaMemcpyAsync(c->d_cjobs[k], c->h_cjobs[k], sizeof(CopyJob) * nc, cudaMemcpyHostToDevice, s));
@@ -1215,6 +1304,8 @@ int run_flow(igs_ctx* c, FlowBuild& g, cudaStream_t s, bool wait) {
   if (nready == 0) return fail_ctx(c, IGS_ERR_STATE, "dataflow graph without a ready node");
   ctl->tail = nready;
   if (!g.copies.empty()) std::memcpy(H + o_cj, g.copies.data(), sizeof(CopyJob) * g.copies.size());
+  int ro = oob_prepare(c, g.kernels.data(), g.kernels.size(), g.oob_first, s);
+  if (ro) return ro;
   if (!g.kernels.empty()) std::memcpy(H + o_kj, g.kernels.data(), sizeof(KernelJob) * g.kernels.size());
   uint8_t* D = nullptr;
   CK(cudaMallocAsync((void**)&D, total, s));
@@ -1332,13 +1423,16 @@ bool stencil_ok(const igs_ctx* c, const KernelJob& J) {
     lo[d] = J.lo[d];
     hi[d] = J.hi[d];
   }
-  if (!box_in(J.acc[no].lo, J.acc[no].hi, lo, hi)) return false;
-  if (J.kernel == K_WAVE && !box_in(J.acc[0].lo, J.acc[0].hi, lo, hi)) return false;
+  // the fast kernels do not check single accesses: the allocations AND the
+  // boxes the range mappers permit must cover everything they touch
+  if (!box_in(J.acc[no].lo, J.acc[no].hi, lo, hi) || !box_in(J.acc[no].plo, J.acc[no].phi, lo, hi)) return false;
+  if (J.kernel == K_WAVE && (!box_in(J.acc[0].lo, J.acc[0].hi, lo, hi) || !box_in(J.acc[0].plo, J.acc[0].phi, lo, hi)))
+    return false;
   for (int d = 0; d < 2; ++d) {
     lo[d] = lo[d] > 0 ? lo[d] - 1 : 0;
     hi[d] = std::min(hi[d] + 1, U.ext[d]);
   }
-  return box_in(U.lo, U.hi, lo, hi);
+  return box_in(U.lo, U.hi, lo, hi) && box_in(U.plo, U.phi, lo, hi);
 }
 
 // One walk over the fetched, not yet executed instructions of every node,
@@ -1349,6 +1443,8 @@ bool stencil_ok(const igs_ctx* c, const KernelJob& J) {
 int exec_walk(igs_ctx* c, Pending& p, cudaStream_t xs, bool* halted_any, bool* progress) {
   c->exec_call += 1;
   FlowBuild* g = p.flow;
+  p.oob_first = (uint32_t)c->oob_meta.size();
+  if (g) g->oob_first = p.oob_first;
   std::vector<uint32_t> walk_start(c->N);
   for (uint32_t n = 0; n < c->N; ++n) {
     walk_start[n] = c->nh[n].executed;
@@ -1546,6 +1642,10 @@ int exec_walk(igs_ctx* c, Pending& p, cudaStream_t xs, bool* halted_any, bool* p
                   A.map[d] = t.acc[a].dim[d];
                 }
                 A.valid = 0;
+                for (int d = 0; d < 3; ++d) {
+                  A.plo[d] = bd.lo[d];
+                  A.phi[d] = bd.hi[d];
+                }
                 if (bd.alloc != IGS_NONE) {
                   ExecAlloc* al = get_alloc(c, n, bd.alloc, t.acc[a].buffer);
                   if (!al) return fail_ctx(c, IGS_ERR_STATE, "kernel on unknown allocation");
@@ -1556,6 +1656,10 @@ int exec_walk(igs_ctx* c, Pending& p, cudaStream_t xs, bool* halted_any, bool* p
                   }
                   A.valid = 1;
                 }
+              }
+              if (J.kernel != K_NOP && items) {
+                J.oob_slot = (uint32_t)c->oob_meta.size();
+                c->oob_meta.push_back(OobMeta{in.seq, n, in.a, J.nacc});
               }
               if (g) {
                 const bool work = J.kernel != K_NOP && items;
@@ -1608,7 +1712,7 @@ extern "C" int igs_execute(igs_ctx* c, uint32_t flags) {
     if (!progress) break;  // a receive waits for sends not lowered yet: a later call executes it
   }
   (void)flags;
-  return IGS_OK;
+  return oob_status(c);
 }
 
 extern "C" int igs_run(igs_ctx* c, uint32_t window) {
@@ -1649,7 +1753,8 @@ extern "C" int igs_run(igs_ctx* c, uint32_t window) {
     ev_collect(c);
     const int fr = flow_collect(c);
     const int er = exec_error_status(c);
-    return code != IGS_OK ? code : fr != IGS_OK ? fr : er;
+    const int orr = oob_status(c);
+    return code != IGS_OK ? code : fr != IGS_OK ? fr : er != IGS_OK ? er : orr;
   };
   // one launch lowers every pending submission; each node's warp publishes
   // its progress, and the executor follows behind on its own stream

@@ -20,8 +20,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libigs.so")
 IGS_OK = 0
 IGS_ERR_INVALID_ARG, IGS_ERR_OVERLAPPING_WRITE, IGS_ERR_CAPACITY, IGS_ERR_TRUNCATED = -1, -2, -3, -4
 IGS_ERR_TIMEOUT, IGS_ERR_CUDA, IGS_ERR_BUDGET, IGS_ERR_STATE = -5, -6, -7, -8
+IGS_ERR_OUT_OF_BOUNDS = -9
 ERRORS = {-1: "INVALID_ARG", -2: "OVERLAPPING_WRITE", -3: "CAPACITY", -4: "TRUNCATED", -5: "TIMEOUT",
-          -6: "CUDA", -7: "BUDGET", -8: "STATE"}
+          -6: "CUDA", -7: "BUDGET", -8: "STATE", -9: "OUT_OF_BOUNDS"}
 MODE_PLAIN, MODE_BATCHED = 0, 1
 LOOKAHEAD_INFINITE = 0xFFFFFFFF
 LOOKAHEAD_HORIZONS = 0xFFFFFFFE  # the horizon-count heuristic (IGS_LOOKAHEAD_HORIZONS)
@@ -32,7 +33,7 @@ EXPORTS = ("igs_create", "igs_destroy", "igs_create_buffer", "igs_destroy_buffer
            "igs_set_timing", "igs_stats", "igs_profile", "igs_lower_static", "igs_submit_epoch",
            "igs_serve_create", "igs_serve_destroy", "igs_serve_attach", "igs_serve_start", "igs_serve_progress",
            "igs_serve_detach", "igs_serve_stop", "igs_run", "igs_lower_batch_shaped", "igs_set_executor",
-           "igs_exec_stats", "igs_selftest_flow_wait")
+           "igs_exec_stats", "igs_selftest_flow_wait", "igs_bounds_errors")
 EXEC_LEVELS, EXEC_DATAFLOW = 0, 1  # IGS_EXEC_*
 ORDER_SUBMISSION, ORDER_LONGEST_FIRST = 0, 1  # IGS_ORDER_*
 
@@ -123,6 +124,7 @@ def lib():
         L.igs_set_executor.argtypes = [vp, u32]
         L.igs_exec_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.igs_selftest_flow_wait.argtypes = [u32]
+        L.igs_bounds_errors.argtypes = [vp, vp, u32, P32]
         L.igs_sync.argtypes = [vp]
         L.igs_submit_epoch.argtypes = [vp]
         L.igs_serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(vp)]
@@ -268,6 +270,18 @@ class Context:
         self._check(lib().igs_exec_stats(self._h, out), "exec_stats")
         keys = ("launches", "nodes", "tiles", "edges", "span_ms", "copy_busy_ms", "kernel_busy_ms", "overlap_ms")
         return dict(zip(keys, list(out)))
+
+    def bounds_errors(self) -> list:
+        """Accessor bounds violations recorded so far: dicts with seq, node,
+        chunk, accessor and the bounding box (lo, hi) of the indices outside
+        the accessor's permitted box."""
+        cnt = np.zeros(1, np.uint32)
+        self._check(lib().igs_bounds_errors(self._h, None, 0, _p32(cnt)), "bounds_errors")
+        rec = np.zeros((max(1, int(cnt[0])), 10), np.uint32)
+        self._check(lib().igs_bounds_errors(self._h, rec.ctypes.data, int(cnt[0]), _p32(cnt)), "bounds_errors")
+        return [{"seq": int(r[0]), "node": int(r[1]), "chunk": int(r[2]), "accessor": int(r[3]),
+                 "lo": tuple(int(v) for v in r[4:7]), "hi": tuple(int(v) for v in r[7:10])}
+                for r in rec[:int(cnt[0])]]
 
     def run(self, window: int = 64):
         """Lowers the pending submissions in windows of `window` items while the

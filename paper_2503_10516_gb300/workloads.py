@@ -21,6 +21,7 @@ READ, WRITE, READ_WRITE = 1, 2, 3
 
 # Workload kernels run by device-kernel instructions at execute time.
 K_NOP, K_JACOBI, K_WAVE, K_NBODY_STEP, K_NBODY_UPDATE, K_GROW, K_GENERIC = 0, 1, 2, 3, 4, 5, 6
+K_SHIFT = 7  # reads accessor 0 at item + (params 0-2 as int32), writes the value to accessor 1 at item
 
 TASK_HDR = 11
 ACC_W = 14

@@ -13,6 +13,7 @@
 #include <thread>
 #include <cstring>
 #include <map>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -1450,6 +1451,8 @@ int exec_walk(igs_ctx* c, Pending& p, cudaStream_t xs, bool* halted_any, bool* p
     walk_start[n] = c->nh[n].executed;
     if (g) c->nh[n].fid.resize(c->nh[n].instrs.size());
   }
+  // per split receive of this call: (send box, its copy node)
+  std::unordered_map<uint64_t, std::vector<std::pair<igs_box, uint32_t>>> split_parts;
   // the dataflow node of instruction i of node n; its predecessors walked in
   // this call become its predecessor nodes (earlier ones have completed)
   auto flow_node = [&](uint32_t n, uint32_t i, uint32_t kind) -> uint32_t {
@@ -1592,6 +1595,33 @@ int exec_walk(igs_ctx* c, Pending& p, cudaStream_t xs, bool* halted_any, bool* p
               ExecAlloc* d = get_alloc(c, n, in.a, in.c);
               if (!d) return fail_ctx(c, IGS_ERR_STATE, "receive into unknown allocation");
               uint32_t F = 0;
+              if (g && in.type == IGS_SPLIT_RECEIVE) {
+                // receive arbitration (Sec. 3.4 "Inbound Transfers", cases a
+                // and c): one copy node per incoming send, gated by the split
+                // receive's own predecessors and by that send; the split
+                // receive completes with the last of them, and each await
+                // receive as soon as the sends meeting its region have landed
+                const uint32_t gate = flow_node(n, i, FK_NONE);  // carries the split receive's predecessors
+                const uint32_t sid = g->add_node(FK_NONE);       // the split receive itself
+                h.fid[i] = sid;
+                auto& parts = split_parts[((uint64_t)n << 32) | i];
+                for (auto it = range.first; it != range.second; ++it) {
+                  const igs_box& b = it->second.box;
+                  CopyJob J{};
+                  if (!make_copy_job(it->second.mail, b.lo, b.hi, d->ptr, d->lo, d->hi, b, c->bufs[in.c].elem, J))
+                    return fail_ctx(c, IGS_ERR_STATE, "bad receive box");
+                  const uint32_t cf = g->add_node(FK_COPY);
+                  g->add_copy(cf, J);
+                  g->edges.push_back({gate, cf});
+                  if (it->second.call == c->exec_call) g->edges.push_back({it->second.fid, cf});
+                  g->edges.push_back({cf, sid});
+                  g->frees.push_back(it->second.mail);
+                  parts.push_back({b, cf});
+                }
+                c->sends.erase(range.first, range.second);
+                h.level[i] = Lr + 1;
+                break;
+              }
               if (g) {
                 F = flow_node(n, i, FK_COPY);
                 for (auto it = range.first; it != range.second; ++it)
@@ -1674,7 +1704,38 @@ int exec_walk(igs_ctx* c, Pending& p, cudaStream_t xs, bool* halted_any, bool* p
               h.level[i] = L + 1;
               break;
             }
-            default:  // await receive, horizon, epoch: no work of their own
+            case IGS_AWAIT_RECEIVE: {
+              if (!g) break;
+              // completes once the received copies meeting its region are in
+              // (instead of waiting for the whole split receive)
+              const auto sp = split_parts.find(((uint64_t)n << 32) | in.b);
+              if (sp == split_parts.end()) {  // split receive of an earlier call: complete
+                flow_node(n, i, FK_NONE);
+                break;
+              }
+              const uint32_t F = g->add_node(FK_NONE);
+              for (uint32_t e = h.first_edge[i]; e < h.first_edge[i + 1]; ++e) {
+                const uint32_t from = h.edges[e].from;
+                if (from >= walk_start[n] && from != in.b) g->edges.push_back({h.fid[from], F});
+              }
+              bool any = false;
+              for (const auto& part : sp->second)
+                for (uint32_t k = 0; k < in.box_cnt; ++k) {
+                  const igs_box& a = h.boxes[in.box_off + k];
+                  bool meet = true;
+                  for (int dd = 0; dd < 3; ++dd)
+                    if (std::max(a.lo[dd], part.first.lo[dd]) >= std::min(a.hi[dd], part.first.hi[dd])) meet = false;
+                  if (meet) {
+                    g->edges.push_back({part.second, F});
+                    any = true;
+                    break;
+                  }
+                }
+              if (!any) g->edges.push_back({h.fid[in.b], F});
+              h.fid[i] = F;
+              break;
+            }
+            default:  // horizon, epoch: no work of their own
               if (g) flow_node(n, i, FK_NONE);
               break;
           }

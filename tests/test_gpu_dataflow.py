@@ -185,3 +185,30 @@ def test_bounded_wait_gives_up_and_device_stays_usable():
     assert r == igs.IGS_ERR_TIMEOUT
     assert 0.15 < dt < 10.0
     _run(W.jacobi_program())
+
+
+def _split_receive_seeds(count=16, start=5000):
+    """Seeds of small random programs whose graphs hold split receives (the
+    oracle decides), for the receive-arbitration path."""
+    out, seed = [], start
+    while len(out) < count and seed < start + 4000:
+        p = W.random_program(seed, max_extent=10, max_tasks=12)
+        ref, _ = oracle_graphs(p)
+        if sum(int((g["instrs"][:, 1] == 7).sum()) for g in ref):
+            out.append(seed)
+        seed += 1
+    return out
+
+
+_SPLIT = _split_receive_seeds()
+
+
+@pytest.mark.parametrize("seed", _SPLIT)
+def test_split_receives_arbitrated(seed):
+    """Programs with split receives: each send's data lands through a copy of
+    its own and an await receive completes once the sends meeting its region
+    have landed; contents equal the sequential run (plain execute and
+    pipelined run)."""
+    p = W.random_program(seed, max_extent=10, max_tasks=12)
+    _run(p)
+    _run_pipelined(p, window=1 + seed % 3)

@@ -372,6 +372,27 @@ int igs_serve_detach(igs_server* srv, igs_ctx* ctx, uint32_t timeout_ms);
 /* Stops the loop and waits for it. */
 int igs_serve_stop(igs_server* srv);
 
+/* Replays a timed trace of submissions against the served loop from a host
+ * loop in the library, so that a trace is not limited by the caller's
+ * submission rate: item k is submitted (igs_submit_task, or igs_submit_epoch
+ * when `epoch` is 1) to ctxs[item.ctx] once arrival_ns nanoseconds have passed
+ * since the call began (or at once if later), items in array order
+ * (arrival_ns non-decreasing); latency_ns[k] receives the time from item k's
+ * arrival until every node of its context has taken it (igs_serve_progress),
+ * polled continuously. Restarts the loop if it went idle. Every context must
+ * be attached to srv. IGS_ERR_TIMEOUT if the trace has not completed
+ * timeout_ms after its last arrival; IGS_ERR_CAPACITY if a slot failed.
+ * *wall_ns receives the time from the call's start until the last item was
+ * taken. */
+typedef struct igs_replay_item {
+  uint32_t ctx;         /* index into ctxs */
+  uint32_t epoch;       /* 1: an epoch, 0: the task `task` */
+  const igs_task* task; /* caller-owned for the duration of the call */
+  uint64_t arrival_ns;  /* since the start of the call */
+} igs_replay_item;
+int igs_serve_replay(igs_server* srv, igs_ctx* const* ctxs, uint32_t n_ctx, const igs_replay_item* items, uint32_t n,
+                     uint32_t timeout_ms, uint64_t* latency_ns, uint64_t* wall_ns);
+
 /* Counters: [0] instructions, [1] edges, [2] boxes, [3] map entries read,
  * [4] map entries written, [5] launches of the lowering kernel, summed over
  * nodes. */

@@ -2161,6 +2161,67 @@ extern "C" int igs_serve_progress(const igs_ctx* c, uint32_t* submitted, uint32_
   return st ? IGS_ERR_CAPACITY : IGS_OK;
 }
 
+extern "C" int igs_serve_replay(igs_server* s, igs_ctx* const* ctxs, uint32_t n_ctx, const igs_replay_item* items,
+                                uint32_t n, uint32_t timeout_ms, uint64_t* latency_ns, uint64_t* wall_ns) {
+  if (!s || !ctxs || (n && (!items || !latency_ns))) return IGS_ERR_INVALID_ARG;
+  for (uint32_t i = 0; i < n_ctx; ++i)
+    if (!ctxs[i] || ctxs[i]->server != s) return IGS_ERR_INVALID_ARG;
+  for (uint32_t k = 0; k < n; ++k)
+    if (items[k].ctx >= n_ctx || (!items[k].epoch && !items[k].task) || (k && items[k].arrival_ns < items[k - 1].arrival_ns))
+      return IGS_ERR_INVALID_ARG;
+  using clock = std::chrono::steady_clock;
+  const auto t0 = clock::now();
+  auto now_ns = [&]() { return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(clock::now() - t0).count(); };
+  // per context: (submission count that completes the item, item index), in order
+  std::vector<std::vector<std::pair<uint32_t, uint32_t>>> fifo(n_ctx);
+  std::vector<size_t> head(n_ctx, 0);
+  std::vector<uint32_t> busy;  // contexts with items in flight
+  uint32_t next = 0, done = 0;
+  uint64_t last = 0;
+  const uint64_t limit = (n ? items[n - 1].arrival_ns : 0) + (uint64_t)timeout_ms * 1000000ull;
+  for (;;) {
+    uint64_t t = now_ns();
+    while (next < n && items[next].arrival_ns <= t) {
+      const igs_replay_item& it = items[next];
+      igs_ctx* c = ctxs[it.ctx];
+      uint64_t seq = 0;
+      const int r = it.epoch ? igs_submit_epoch(c) : igs_submit_task(c, it.task, &seq);
+      if (r && r != IGS_ERR_OVERLAPPING_WRITE) return r;
+      if (head[it.ctx] == fifo[it.ctx].size()) busy.push_back(it.ctx);
+      fifo[it.ctx].push_back({(uint32_t)c->items.size(), next});
+      ++next;
+    }
+    t = now_ns();
+    for (size_t b = 0; b < busy.size();) {
+      const uint32_t ci = busy[b];
+      uint32_t sub = 0, taken = 0;
+      if (igs_serve_progress(ctxs[ci], &sub, &taken)) return fail_ctx(ctxs[ci], IGS_ERR_CAPACITY, "a serving slot failed");
+      auto& q = fifo[ci];
+      while (head[ci] < q.size() && q[head[ci]].first <= taken) {
+        const uint32_t k = q[head[ci]].second;
+        latency_ns[k] = t > items[k].arrival_ns ? t - items[k].arrival_ns : 0;
+        last = t;
+        ++head[ci];
+        ++done;
+      }
+      if (head[ci] == q.size()) {
+        busy[b] = busy.back();
+        busy.pop_back();
+      } else {
+        ++b;
+      }
+    }
+    if (done == n) break;
+    if (t > limit) return IGS_ERR_TIMEOUT;
+    if (s->launched && cudaEventQuery(s->done_ev) == cudaSuccess) {
+      s->launched = false;  // the loop went idle: restart it
+      if (int e = igs_serve_start(s)) return e;
+    }
+  }
+  if (wall_ns) *wall_ns = last;
+  return IGS_OK;
+}
+
 extern "C" int igs_serve_detach(igs_server* s, igs_ctx* c, uint32_t timeout_ms) {
   if (!s || !c || c->server != s) return IGS_ERR_INVALID_ARG;
   const auto t0 = std::chrono::steady_clock::now();

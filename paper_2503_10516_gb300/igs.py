@@ -24,6 +24,7 @@ IGS_ERR_OUT_OF_BOUNDS = -9
 ERRORS = {-1: "INVALID_ARG", -2: "OVERLAPPING_WRITE", -3: "CAPACITY", -4: "TRUNCATED", -5: "TIMEOUT",
           -6: "CUDA", -7: "BUDGET", -8: "STATE", -9: "OUT_OF_BOUNDS"}
 MODE_PLAIN, MODE_BATCHED = 0, 1
+TASK_WORDS = W.TASK_HDR + W.ACC_W * W.MAX_ACC  # igs_task as uint32 words
 LOOKAHEAD_INFINITE = 0xFFFFFFFF
 LOOKAHEAD_HORIZONS = 0xFFFFFFFE  # the horizon-count heuristic (IGS_LOOKAHEAD_HORIZONS)
 
@@ -33,7 +34,7 @@ EXPORTS = ("igs_create", "igs_destroy", "igs_create_buffer", "igs_destroy_buffer
            "igs_set_timing", "igs_stats", "igs_profile", "igs_lower_static", "igs_submit_epoch",
            "igs_serve_create", "igs_serve_destroy", "igs_serve_attach", "igs_serve_start", "igs_serve_progress",
            "igs_serve_detach", "igs_serve_stop", "igs_run", "igs_lower_batch_shaped", "igs_set_executor",
-           "igs_exec_stats", "igs_selftest_flow_wait", "igs_bounds_errors")
+           "igs_exec_stats", "igs_selftest_flow_wait", "igs_bounds_errors", "igs_serve_replay")
 EXEC_LEVELS, EXEC_DATAFLOW = 0, 1  # IGS_EXEC_*
 ORDER_SUBMISSION, ORDER_LONGEST_FIRST = 0, 1  # IGS_ORDER_*
 
@@ -125,6 +126,7 @@ def lib():
         L.igs_exec_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.igs_selftest_flow_wait.argtypes = [u32]
         L.igs_bounds_errors.argtypes = [vp, vp, u32, P32]
+        L.igs_serve_replay.argtypes = [vp, ctypes.POINTER(vp), u32, vp, u32, u32, vp, vp]
         L.igs_sync.argtypes = [vp]
         L.igs_submit_epoch.argtypes = [vp]
         L.igs_serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(vp)]
@@ -372,6 +374,33 @@ class Server:
 
     def stop(self):
         lib().igs_serve_stop(self._h)
+
+    def replay(self, ctxs: Sequence[Context], trace, timeout_ms: int = 60000):
+        """igs_serve_replay: trace = [(context index, Task or None for an
+        epoch, arrival in ns since the call)] in arrival order. Returns
+        (per-item latency in ns as a numpy array, ns until the last item was
+        taken)."""
+        n = len(trace)
+        words = np.zeros((max(1, n), TASK_WORDS), np.uint32)
+        items = np.zeros(max(1, n), dtype=np.dtype([("ctx", np.uint32), ("epoch", np.uint32), ("task", np.uint64),
+                                                     ("arrival", np.uint64)]))
+        base = words.ctypes.data
+        for k, (ci, task, t_ns) in enumerate(trace):
+            items[k]["ctx"] = ci
+            items[k]["arrival"] = int(t_ns)
+            if task is None:
+                items[k]["epoch"] = 1
+            else:
+                words[k] = task.flat()
+                items[k]["task"] = base + k * TASK_WORDS * 4
+        arr = (ctypes.c_void_p * len(ctxs))(*[c.handle.value for c in ctxs])
+        lat = np.zeros(max(1, n), np.uint64)
+        wall = np.zeros(1, np.uint64)
+        r = lib().igs_serve_replay(self._h, arr, len(ctxs), items.ctypes.data, n, timeout_ms, lat.ctypes.data,
+                                   wall.ctypes.data)
+        if r != IGS_OK:
+            raise IgsError(r, "serve_replay")
+        return lat[:n], int(wall[0])
 
     def close(self):
         if getattr(self, "_h", None):

@@ -112,3 +112,34 @@ def test_served_after_idle_exit():
     assert_same_graph(c.graph(0), ref[0], "served after idle exit")
     c.close()
     srv.close()
+
+
+@pytest.mark.parametrize("rate", [2e4, 1e6])
+def test_replayed_trace_matches_alone(rate):
+    """A timed trace replayed by the library's own submission loop
+    (igs_serve_replay) at 2e4 and 1e6 arrivals/s: every item completes with
+    a latency, and every stream's graph equals the oracle's."""
+    from paper_2503_10516_gb300 import igs
+    progs = _streams()
+    srv = igs.Server(max_slots=64)
+    ctxs = [_ctx(p) for p in progs]
+    for c, p in zip(ctxs, progs):
+        assert srv.attach(c, 4 * len(p.ops) + 16) == 0
+    srv.start()
+    rng = np.random.default_rng(3)
+    order = _interleaved(progs, rng)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=len(order))) * 1e9
+    trace = [(i, op[1] if op[0] == "task" else None, int(t[k])) for k, (i, op) in enumerate(order)]
+    lat, wall = srv.replay(ctxs, trace, timeout_ms=60000)
+    assert len(lat) == len(trace) and wall > 0
+    assert int(lat.max()) <= wall
+    for c in ctxs:
+        srv.detach(c)
+    srv.stop()
+    for p, c in zip(progs, ctxs):
+        ref, rej = oracle_graphs(p)
+        assert c.rejected() == rej
+        for n in range(p.nodes):
+            assert_same_graph(c.graph(n), ref[n], f"{p.name} node {n} (replayed at {rate:g}/s)")
+        c.close()
+    srv.close()

@@ -398,6 +398,41 @@ def measure_executors(igs, torch, stream, prog, make_ctx, wave_tasks=200, nbody_
     return out
 
 
+def measure_nbody_lowering(igs, torch, stream, tasks=100):
+    """The all-pairs N-body configuration (2^20 float4 bodies, 8 nodes x 4
+    devices, 128 chunks, lookahead 4, two tasks per step): the first `tasks`
+    tasks lowered in one launch (device time by CUDA events), and the same
+    tasks one per launch (per-task latency)."""
+    n = 1 << 20
+    p = W.nbody_program(n=n, steps=tasks // 2, nodes=8, devices=4, chunks=128, lookahead=4)
+    out = {}
+    for name, mode in (("batched", igs.MODE_BATCHED), ("plain", igs.MODE_PLAIN)):
+        c = igs.Context(p.nodes, p.devices, p.horizon_step, p.lookahead, mode=mode, stream=stream)
+        c.set_timing(True)
+        for op in p.ops:
+            if op[0] == "buffer":
+                b = op[1]
+                c.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init)
+        lat = []
+        for op in p.ops:
+            if op[0] == "task":
+                c.submit(op[1])
+                if mode == igs.MODE_PLAIN:
+                    lat.append(c.stats()["last_lower_ms"])
+        c.flush()
+        st = c.stats()
+        instrs = int(c.counters()["instructions"])
+        out[name] = {"instructions": instrs, "lower_ms": st["lower_ms"], "launches": st["lower_launches"],
+                     "instr_per_s": instrs / (st["lower_ms"] * 1e-3)}
+        if lat:
+            lat.sort()
+            out[name]["p50_task_ms"] = lat[len(lat) // 2]
+            out[name]["p99_task_ms"] = lat[min(len(lat) - 1, int(len(lat) * 0.99))]
+        c.close()
+    out["workload"] = f"nbody: 2 x {n} float4 bodies, 8 nodes x 4 devices, 128 chunks, lookahead 4, first {tasks} tasks"
+    return out
+
+
 def measure_lookahead(igs):
     """Scheduler lookahead policies (Sec. 4.3) on a growing-row stream (the
     RSim pattern, 2048 x 1024 fp32, rows appended 1-64 at a time, 2 devices)
@@ -618,6 +653,7 @@ def run_gpu(args):
     # ---- batched lowering of many programs, served lowering of many streams
     big_copy = measure_box_copy(igs, torch, stream)
     executors = measure_executors(igs, torch, sh, prog, make_ctx) if world == 1 else None
+    nbody = measure_nbody_lowering(igs, torch, sh) if world == 1 else None
     lookahead = measure_lookahead(igs) if world == 1 else None
     batched = measure_batched(igs, torch, sh) if world == 1 else None
     served = {f"{int(r)}_per_s": measure_served(igs, torch, sh, rate=r) for r in (1e4, 1e5, 1e6)} \
@@ -658,6 +694,7 @@ def run_gpu(args):
             "box_copy_gbs": (copy_bytes / (copy_ms * 1e-3) / 1e9) if copy_ms else None,
             "box_copy_resize_512MiB": {k: dict(v, frac=v["gbs"] / hbm) for k, v in big_copy.items()},
             "executors": executors,
+            "nbody_lowering": nbody,
             "batched_programs": batched,
             "lookahead": lookahead,
             "served": served,

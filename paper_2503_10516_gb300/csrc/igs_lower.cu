@@ -1338,6 +1338,8 @@ __device__ __noinline__ uint32_t emit_edges(Ctx& c, uint32_t id, igs_edge* out, 
       if (!(e.from & PROV)) nd->has_succ[e.from] = 1;
     }
   } else {
+    // pass 1: mark each entry that is the first of its predecessor id (the
+    // mark lives in the entry's third value word)
     for (uint32_t base = 0; base < nd0; base += 32) {
       const uint32_t i = base + c.lane;
       bool first = false;
@@ -1349,34 +1351,29 @@ __device__ __noinline__ uint32_t emit_edges(Ctx& c, uint32_t id, igs_edge* out, 
             first = false;
             break;
           }
+        FLD(D, F_V + 2, i) = first ? 1u : 0u;
       }
       n_unique += __popc(__ballot_sync(FULL, first));
     }
+    __syncwarp();
     if (n_unique > cap) {
       fail_cap(c, cap_kind, cap_report);
       return NONE;
     }
+    // pass 2: a first entry's rank is the number of first entries with a
+    // smaller id; its kind ORs the kinds of every entry with its id
     for (uint32_t base = 0; base < nd0; base += 32) {
       const uint32_t i = base + c.lane;
       if (i < nd0) {
         const uint32_t p = FLD(D, F_V, i);
-        bool first = true;
+        const bool first = FLD(D, F_V + 2, i) != 0;
         uint32_t kind = 0, rank = 0;
-        for (uint32_t j = 0; j < nd0; ++j) {
-          const uint32_t q = FLD(D, F_V, j);
-          if (q == p) {
-            kind |= FLD(D, F_V + 1, j);
-            if (j < i) first = false;
-          } else if (q < p) {
-            bool qfirst = true;
-            for (uint32_t x = 0; x < j; ++x)
-              if (FLD(D, F_V, x) == q) {
-                qfirst = false;
-                break;
-              }
-            if (qfirst) ++rank;
+        if (first)
+          for (uint32_t j = 0; j < nd0; ++j) {
+            const uint32_t q = FLD(D, F_V, j);
+            if (q == p) kind |= FLD(D, F_V + 1, j);
+            else if (q < p && FLD(D, F_V + 2, j)) ++rank;
           }
-        }
         if (first) {
           igs_edge e;
           e.from = p;

@@ -52,6 +52,7 @@ def lib():
             L.orc_submit_task.argtypes = [vp, P]
             L.orc_submit_task.restype = ctypes.c_int
             L.orc_set_lookahead.argtypes = [vp, u32]
+            L.orc_set_stage_d2d.argtypes = [vp, ctypes.c_int]
             L.orc_flush.argtypes = [vp]
             L.orc_count.argtypes = [vp, u32, ctypes.c_int]
             L.orc_count.restype = u32
@@ -120,6 +121,10 @@ class Oracle:
     def submit(self, flat_task: np.ndarray) -> int:
         w = np.ascontiguousarray(flat_task, dtype=np.uint32)
         return lib().orc_submit_task(self._h, _ptr(w))
+
+    def set_stage_d2d(self, on: bool) -> None:
+        """Device-to-device copies staged in host memory (R27)."""
+        lib().orc_set_stage_d2d(self._h, 1 if on else 0)
 
     def set_lookahead(self, L: int) -> None:
         lib().orc_set_lookahead(self._h, L)

@@ -358,6 +358,7 @@ struct Node {
   uint32_t lookahead = 0;
   std::deque<Item> queue;
   uint32_t horizons_after_alloc = 0;  // horizon-count heuristic: horizons queued since the last allocating task
+  bool stage_d2d = false;             // device-to-device copies staged in host memory [R27]
 };
 
 struct Ctx {
@@ -637,6 +638,46 @@ static void resize_and_alloc(Node& n, const Item& it, const std::vector<const No
   }
 }
 
+// A copy of `part` from allocation src to allocation dst; with host staging
+// of device-to-device copies [R27] (Sec. 3.3, last paragraph), a copy between
+// two device memories becomes: a fresh allocation in the node's host memory M1
+// over the bounding box of the region, a copy into it, a copy out of it, and
+// its free.
+static void emit_copy(Node& n, uint32_t seq, uint32_t b, uint32_t src, uint32_t dst, const Region& part) {
+  const uint32_t sm = n.allocs[src].mem, dm = n.allocs[dst].mem;
+  if (!(n.stage_d2d && sm >= 2 && dm >= 2)) {
+    Instr cp = rec0(COPY, seq);
+    cp.a = src; cp.b = dst; cp.c = b; cp.d = 0;
+    emit(n, cp, part, {{src, part, M_READ}, {dst, part, M_WRITE}}, {});
+    return;
+  }
+  Box bb = part[0];
+  for (const Box& x : part) bb = bbox2(bb, x);
+  const uint32_t hid = (uint32_t)n.allocs.size();
+  Instr al = rec0(ALLOC, seq);
+  al.a = hid; al.b = 1; al.c = b;
+  const uint32_t iid = emit(n, al, {bb}, {}, {});
+  Alloc h;
+  h.id = hid; h.buffer = b; h.mem = 1; h.box = bb; h.live = true; h.user = false;
+  h.writers.init(bb, iid);
+  h.readers.init(bb, {});
+  n.allocs.push_back(h);
+  Instr in = rec0(COPY, seq);
+  in.a = src; in.b = hid; in.c = b; in.d = 0;
+  emit(n, in, part, {{src, part, M_READ}, {hid, part, M_WRITE}}, {});
+  Instr out = rec0(COPY, seq);
+  out.a = hid; out.b = dst; out.c = b; out.d = 0;
+  emit(n, out, part, {{hid, part, M_READ}, {dst, part, M_WRITE}}, {});
+  Instr fr = rec0(FREE, seq);
+  fr.a = hid; fr.b = 1; fr.c = b;
+  std::map<uint32_t, uint32_t> fd;
+  for (const auto& w : n.allocs[hid].writers.e) fd[w.second] |= K_ALLOC;
+  for (const auto& rd : n.allocs[hid].readers.e)
+    for (uint32_t x : rd.second) fd[x] |= K_ALLOC;
+  emit(n, fr, {}, {}, fd);
+  n.allocs[hid].live = false;
+}
+
 // Coherence copies of `need` into allocation dst (memory m), split by
 // original producer, then by source allocation [R7, R8].
 static void coherence(Node& n, uint32_t seq, uint32_t b, uint32_t m, uint32_t dst, const Region& need) {
@@ -652,13 +693,13 @@ static void coherence(Node& n, uint32_t seq, uint32_t b, uint32_t m, uint32_t ds
     Region g;
     for (const auto& s : stale)
       if (s.second.prod == p.first && s.second.pmem == p.second) g.push_back(s.first);
-    for (const Alloc& src : n.allocs) {  // ascending allocation id
+    const size_t n_alloc = n.allocs.size();  // staging allocations are appended below
+    for (size_t ai = 0; ai < n_alloc; ++ai) {   // ascending allocation id
+      const Alloc src = n.allocs[ai];
       if (!src.live || src.buffer != b || src.mem != p.second) continue;
       Region part = canonical(region_isect_box(g, src.box));
       if (part.empty()) continue;
-      Instr cp = rec0(COPY, seq);
-      cp.a = src.id; cp.b = dst; cp.c = b; cp.d = 0;
-      emit(n, cp, part, {{src.id, part, M_READ}, {dst, part, M_WRITE}}, {});
+      emit_copy(n, seq, b, src.id, dst, part);
       copied.insert(copied.end(), part.begin(), part.end());
     }
   }
@@ -1080,6 +1121,12 @@ int orc_submit_task(void* p, const uint32_t* w) {
     }
   }
   return submit(*c, t) ? 0 : -2;
+}
+
+int orc_set_stage_d2d(void* p, int on) {
+  Ctx* c = static_cast<Ctx*>(p);
+  for (Node& n : c->nodes) n.stage_d2d = on != 0;
+  return 0;
 }
 
 int orc_set_lookahead(void* p, uint32_t L) {

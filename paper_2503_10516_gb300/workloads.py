@@ -133,6 +133,7 @@ class Program:
     horizon_step: int
     lookahead: int
     ops: list
+    stage_d2d: bool = False  # device-to-device copies staged in host memory
 
     @property
     def buffers(self) -> List[Buffer]:

@@ -146,6 +146,7 @@ class Brute:
         self.seq = 0
         self.ntasks = 0
         self.rejected = []
+        self.stage_d2d = False  # device-to-device copies staged in host memory
 
     # -- items --
     def create_buffer(self, dims, extent, elem, init):
@@ -471,14 +472,28 @@ class Brute:
         copied = np.zeros_like(need)
         for p, q in keys:
             g = stale & (prod == p) & (pmem == q)
-            for al in n.allocs:
+            for al in list(n.allocs):
                 if not al["live"] or al["buffer"] != b or al["mem"] != q:
                     continue
                 part = g & al["mask"]
                 if not part.any():
                     continue
-                self._emit(n, [COPY, seq, al["id"], dst, b, 0], [part],
-                           [(al["id"], part, M_READ), (dst, part, M_WRITE)], {})
+                if self.stage_d2d and q >= 2 and m >= 2:
+                    # through a fresh host allocation over the region's bounding box
+                    bb = bbox_of_mask(part)
+                    hid = len(n.allocs)
+                    iid = self._emit(n, [ALLOC, seq, hid, 1, b, NONE], [bb], [], {})
+                    self._new_alloc(n, b, 1, bb, iid)
+                    self._emit(n, [COPY, seq, al["id"], hid, b, 0], [part],
+                               [(al["id"], part, M_READ), (hid, part, M_WRITE)], {})
+                    self._emit(n, [COPY, seq, hid, dst, b, 0], [part],
+                               [(hid, part, M_READ), (dst, part, M_WRITE)], {})
+                    h = n.allocs[hid]
+                    self._emit(n, [FREE, seq, hid, 1, b, NONE], [], [], self._free_deps(n, h))
+                    h["live"] = False
+                else:
+                    self._emit(n, [COPY, seq, al["id"], dst, b, 0], [part],
+                               [(al["id"], part, M_READ), (dst, part, M_WRITE)], {})
                 copied |= part
         mask[copied] |= (1 << m)
 

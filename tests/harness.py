@@ -37,6 +37,8 @@ class OracleImpl:
     def __init__(self, prog: W.Program):
         import oracle
         self.o = oracle.Oracle(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead)
+        if prog.stage_d2d:
+            self.o.set_stage_d2d(True)
         self.nodes = prog.nodes
 
     def create_buffer(self, dims, extent, elem, init):
@@ -65,6 +67,7 @@ class BruteImpl:
     def __init__(self, prog: W.Program):
         from tests.brute_idag import Brute
         self.b = Brute(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead)
+        self.b.stage_d2d = prog.stage_d2d
         self.nodes = prog.nodes
 
     def create_buffer(self, dims, extent, elem, init):

@@ -433,6 +433,7 @@ def check_invariants(prog: W.Program, g: dict, node: int):
                 assert not (kinds[(p, i)] & K_DATAFLOW), "receive with a dataflow predecessor"
     # allocations: disjoint per (buffer, memory), never shrink, accesses inside
     live = {}
+    alloc_seq = {}  # allocation -> submission that allocated it
     accesses = []  # (instr, alloc, box, writes)
 
     def bx_of(r, j=0):
@@ -443,11 +444,15 @@ def check_invariants(prog: W.Program, g: dict, node: int):
         if typ == ALLOC:
             box = bx_of(r)
             live[a] = (c, b, box)
+            alloc_seq[a] = int(r[2])
             accesses.append((i, a, box, True))
         elif typ == FREE:
             assert a in live, "free of an unknown allocation"
             ob, om, obox = live.pop(a)
-            if int(r[2]) in tasks:  # a resize: a live allocation of (buffer, memory) now holds the box
+            # a resize frees an older allocation: a live allocation of (buffer,
+            # memory) now holds its box (a host staging allocation is freed by
+            # the submission that made it)
+            if int(r[2]) in tasks and alloc_seq.get(a) != int(r[2]):
                 assert any(lb == ob and lm == om and _isect(lbox, obox) == obox
                            for lb, lm, lbox in live.values()), "allocation shrank on resize"
             accesses.append((i, a, obox, True))

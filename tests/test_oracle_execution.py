@@ -51,3 +51,26 @@ def test_replay_detects_dropped_copy():
                 r[8] = 0
     with pytest.raises(AssertionError, match="stale read"):
         replay(p, gs, set(rej))
+
+
+def _staged(p):
+    p.stage_d2d = True
+    return p
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_random_staged_d2d(seed):
+    """Host-staged device-to-device copies keep every read coherent and the
+    result sequential."""
+    _run(_staged(W.random_program(300_000 + seed, max_extent=10, max_tasks=12)))
+
+
+@pytest.mark.parametrize("prog", [
+    W.wave_program(n=32, steps=10, nodes=2, devices=2, chunks=8, lookahead=8),
+    W.wave_program(n=24, steps=7, nodes=1, devices=4, chunks=16, lookahead=0),
+    W.nbody_program(n=64, steps=3, nodes=2, devices=2, chunks=8, lookahead=4),
+    W.growing_program(rows_max=64, cols=1, grow=(1, 9), nodes=2, devices=2, chunks=4, lookahead=3),
+], ids=lambda p: f"{p.name}-L{p.lookahead}")
+def test_paper_shaped_staged_d2d(prog):
+    stats = _run(_staged(prog))
+    assert stats["kernels"] > 0 and stats["reads_checked"] > 0

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2503_10516_gb300 import workloads as W
-from tests.harness import OracleImpl, feed, oracle_graphs
+from tests.harness import OracleImpl, counts_by_type, feed, oracle_graphs
 from tests.replay import (ALLOC, AWAIT_RECEIVE, COPY, FREE, HORIZON, K_FRONT, KERNEL, RECEIVE, SEND,
                           SPLIT_RECEIVE, _ancestors, task_seqs)
 
@@ -255,3 +255,45 @@ def test_horizon_heuristic_flushes_stable_patterns():
     _, ref = _emitted_after_each_task(W.wave_program(n=32, steps=24, nodes=2, devices=2, chunks=8,
                                                      lookahead=W.LOOKAHEAD_INFINITE, horizon_step=4))
     assert sum(1 for r in g["instrs"] if r[1] == ALLOC) == sum(1 for r in ref["instrs"] if r[1] == ALLOC)
+
+
+def _copy_memories(g):
+    """(source memory, destination memory) of every copy, from the allocations."""
+    mem = {}
+    for r in g["instrs"]:
+        if int(r[1]) == 2:  # ALLOC
+            mem[int(r[3])] = int(r[4])
+    out = []
+    for r in g["instrs"]:
+        if int(r[1]) == 4:  # COPY
+            out.append((mem.get(int(r[3]), 0), mem.get(int(r[4]), 0)))
+    return out
+
+
+@pytest.mark.parametrize("prog", [
+    W.wave_program(n=32, steps=6, nodes=1, devices=4, chunks=16, lookahead=2),
+    W.wave_program(n=16, steps=5, nodes=2, devices=2, chunks=8, lookahead=0),
+    W.nbody_program(n=64, steps=2, nodes=2, devices=2, chunks=8, lookahead=4),
+], ids=lambda p: p.name)
+def test_staged_d2d_replaces_every_device_to_device_copy(prog):
+    """Sec. 3.3: with device-to-device copies staged in host memory, no copy
+    goes from one device memory to another (resize copies stay within one
+    memory); each one that did becomes a host
+    allocation, a copy into it, a copy out of it and its free (3 more
+    instructions each), and nothing else changes."""
+    plain, _ = oracle_graphs(prog)
+    prog.stage_d2d = True
+    staged, _ = oracle_graphs(prog)
+    for g0, g1 in zip(plain, staged):
+        d2d = sum(1 for s, d in _copy_memories(g0) if s >= 2 and d >= 2 and s != d)
+        assert d2d > 0 or prog.nodes > 1
+        assert all(not (s >= 2 and d >= 2 and s != d) for s, d in _copy_memories(g1))
+        assert len(g1["instrs"]) == len(g0["instrs"]) + 3 * d2d
+        c0, c1 = counts_by_type(g0), counts_by_type(g1)
+        assert c1.get("copy", 0) == c0.get("copy", 0) + d2d
+        assert c1.get("alloc", 0) == c0.get("alloc", 0) + d2d
+        assert c1.get("free", 0) == c0.get("free", 0) + d2d
+        assert c1.get("kernel", 0) == c0.get("kernel", 0)
+        to_host = sum(1 for s, d in _copy_memories(g1) if s >= 2 and d == 1)
+        from_host = sum(1 for s, d in _copy_memories(g1) if s == 1 and d >= 2)
+        assert to_host >= d2d and from_host >= d2d

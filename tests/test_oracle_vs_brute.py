@@ -53,3 +53,26 @@ def test_random_programs_horizon_lookahead(seed):
 ], ids=lambda p: p.name)
 def test_paper_shaped_programs_horizon_lookahead(prog):
     _check(prog)
+
+
+def _staged(p):
+    p.stage_d2d = True
+    p.name += "-staged"
+    return p
+
+
+@pytest.mark.parametrize("seed", range(150))
+def test_random_programs_staged_d2d(seed):
+    """Device-to-device copies staged in host memory (Sec. 3.3): both
+    generators emit the same allocation, two copies and free per staged copy."""
+    _check(_staged(W.random_program(300_000 + seed, max_extent=10, max_tasks=12)))
+
+
+@pytest.mark.parametrize("prog", [
+    W.wave_program(n=16, steps=6, nodes=2, devices=2, chunks=8, lookahead=2),
+    W.wave_program(n=12, steps=5, nodes=1, devices=3, chunks=6, lookahead=0),
+    W.growing_program(rows_max=30, cols=1, grow=(1, 5), devices=3, chunks=3, lookahead=2),
+    W.nbody_example_program(n=16, iterations=3),
+], ids=lambda p: f"{p.name}-L{p.lookahead}")
+def test_paper_shaped_programs_staged_d2d(prog):
+    _check(_staged(prog))

@@ -112,7 +112,16 @@ typedef struct igs_config {
   uint32_t max_queue;        /* submissions held by the lookahead queue; 0 = default (65536) */
   int device;                /* CUDA device ordinal */
   void* stream;              /* cudaStream_t to launch on; NULL = the library's own stream */
+  uint32_t flags;            /* IGS_FLAG_* */
 } igs_config;
+
+/* Stage every device-to-device coherence copy in host memory (Sec. 3.3, for
+ * devices without peer copies): a copy of region R from one device memory to
+ * another of the node becomes an allocation in the node's host memory M1
+ * over R's bounding box, a copy into it, a copy out of it (both carrying R's
+ * canonical box list) and its free, emitted in that order in place of the
+ * direct copy. */
+#define IGS_FLAG_STAGE_D2D 1u
 
 typedef struct igs_map_dim { uint32_t kind, a, b, c; } igs_map_dim;
 

@@ -362,6 +362,7 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
   if (!cfg || cfg->num_nodes < 1 || cfg->num_nodes > 32 || cfg->devices_per_node < 1 || cfg->devices_per_node > 29)
     return IGS_ERR_INVALID_ARG;
   if (cfg->mode > IGS_MODE_BATCHED) return IGS_ERR_INVALID_ARG;
+  if (cfg->flags & ~IGS_FLAG_STAGE_D2D) return IGS_ERR_INVALID_ARG;
   igs_ctx* c = new igs_ctx();
   c->cfg = *cfg;
   c->N = cfg->num_nodes;
@@ -438,6 +439,7 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
     nd.status = ST_OK;
     nd.cursor = 0;
     nd.lookahead = cfg->lookahead;
+    nd.stage_d2d = (cfg->flags & IGS_FLAG_STAGE_D2D) ? 1u : 0u;
     nd.epoch = 0;
     nd.last_horizon = NONE;
     nd.last_sync = 0;

@@ -69,6 +69,7 @@ struct NodeDev {
   uint32_t n_instr, n_edge, n_box, n_bind, n_diag, n_rej;
   uint32_t q_head, q_count, qr_n, n_free, n_live, qr_live;
   uint32_t q_hzn;  // horizon-count lookahead: horizons queued since the last allocating task
+  uint32_t stage_d2d;  // device-to-device copies staged in host memory (IGS_FLAG_STAGE_D2D)
   uint64_t map_reads, map_writes, launches;
   uint64_t prof[32];   // clock cycles per lowering phase and detail counters (see the engine)
   // capacities

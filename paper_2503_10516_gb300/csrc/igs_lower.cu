@@ -1745,9 +1745,56 @@ __device__ __noinline__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_
       t_reset(CN);
       canonical(c, P, 0, P.n, CN);
       if (c.err) return false;
-      Acc acc[2] = {{&CN, 0, CN.n, src, IGS_READ}, {&CN, 0, CN.n, dst, IGS_WRITE}};
-      emit(c, IGS_COPY, seq, src, dst, b, 0, &CN, 0, CN.n, acc, 2, false);
-      if (c.err) return false;
+      if (c.nd->stage_d2d && a.mem >= 2 && m >= 2) {
+        // staged in host memory (Sec. 3.3): a fresh allocation in M1 over
+        // the region's bounding box, a copy into it, a copy out of it, its free
+        Bx bb;
+        for (int d = 0; d < 3; ++d) {
+          bb.lo[d] = 0xFFFFFFFFu;
+          bb.hi[d] = 0;
+        }
+        for (uint32_t i = 0; i < CN.n; ++i) {
+          if (t_key(CN, i) == DEAD) continue;
+          const Bx x = t_box(CN, i);
+          for (int d = 0; d < 3; ++d) {
+            bb.lo[d] = min(bb.lo[d], x.lo[d]);
+            bb.hi[d] = max(bb.hi[d], x.hi[d]);
+          }
+        }
+        if (c.n_alloc >= c.nd->cap_alloc) {
+          fail_cap(c, CAP_ALLOC, c.nd->cap_alloc);
+          return false;
+        }
+        t_reset(P);  // P now holds the allocation's box
+        const uint32_t s0 = t_claim(c, P, c.lane == 0);
+        if (c.err) return false;
+        if (c.lane == 0) t_put(P, s0, 0, bb, 0, 0, 0);
+        __syncwarp();
+        const uint32_t hid = c.n_alloc;
+        const uint32_t iid = emit(c, IGS_ALLOC, seq, hid, 1, b, NONE, &P, 0, 1, nullptr, 0, false);
+        if (c.err) return false;
+        if (!new_alloc(c, hid, b, 1, bb, 0)) return false;
+        c.n_alloc += 1;
+        {
+          Table WR = wr_t(c, hid);
+          const uint32_t s1 = t_claim(c, WR, c.lane == 0);
+          if (c.err) return false;
+          if (c.lane == 0) t_put(WR, s1, 0, bb, iid, 1, 0);  // v1 = 1: the writer is an allocation
+          __syncwarp();
+        }
+        Acc in[2] = {{&CN, 0, CN.n, src, IGS_READ}, {&CN, 0, CN.n, hid, IGS_WRITE}};
+        emit(c, IGS_COPY, seq, src, hid, b, 0, &CN, 0, CN.n, in, 2, false);
+        if (c.err) return false;
+        Acc out[2] = {{&CN, 0, CN.n, hid, IGS_READ}, {&CN, 0, CN.n, dst, IGS_WRITE}};
+        emit(c, IGS_COPY, seq, hid, dst, b, 0, &CN, 0, CN.n, out, 2, false);
+        if (c.err) return false;
+        emit_free(c, seq, hid);
+        if (c.err) return false;
+      } else {
+        Acc acc[2] = {{&CN, 0, CN.n, src, IGS_READ}, {&CN, 0, CN.n, dst, IGS_WRITE}};
+        emit(c, IGS_COPY, seq, src, dst, b, 0, &CN, 0, CN.n, acc, 2, false);
+        if (c.err) return false;
+      }
       // remember the copied region
       for (uint32_t base = 0; base < CN.n; base += 32) {
         const uint32_t i = base + c.lane;
@@ -3025,7 +3072,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
   }
   // stale consumers of several buffers: shared by the helper warps
   bool multi = false;
-  if (c.block && c.workers > 1 && c.nd->helper_scratch) {
+  if (c.block && c.workers > 1 && c.nd->helper_scratch && !c.nd->stage_d2d) {
     uint32_t first_b = NONE;
     for (uint32_t k = 0; k < PC.n && !multi; ++k) {
       if (!(t_key(PC, k) & 2u)) continue;

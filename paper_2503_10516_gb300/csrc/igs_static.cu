@@ -169,6 +169,7 @@ extern "C" int igs_lower_static(const igs_config* cfg, const igs_static_buffer* 
     nd.D = D;
     nd.status = ST_OK;
     nd.lookahead = cfg->lookahead;
+    nd.stage_d2d = (cfg->flags & IGS_FLAG_STAGE_D2D) ? 1u : 0u;
     nd.last_horizon = NONE;
     nd.n_instr = 1;
     nd.n_free = kSlots;

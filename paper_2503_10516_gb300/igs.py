@@ -53,7 +53,8 @@ class Config(ctypes.Structure):
                 ("scratch_capacity", ctypes.c_uint32), ("max_buffers", ctypes.c_uint32),
                 ("max_live_allocs", ctypes.c_uint32),
                 ("max_allocations", ctypes.c_uint32), ("max_queue", ctypes.c_uint32),
-                ("device", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+FLAG_STAGE_D2D = 1  # IGS_FLAG_STAGE_D2D
 
 
 class GraphView(ctypes.Structure):
@@ -167,11 +168,12 @@ class Context:
                  mode: int = MODE_PLAIN, device: int = 0, stream: Optional[int] = None,
                  max_instructions: int = 0, map_heap: int = 0, scratch_capacity: int = 0,
                  max_buffers: int = 0, max_live_allocs: int = 0,
-                 max_allocations: int = 0, max_queue: int = 0, max_edges: int = 0, max_boxes: int = 0):
+                 max_allocations: int = 0, max_queue: int = 0, max_edges: int = 0, max_boxes: int = 0,
+                 flags: int = 0):
         self.nodes = nodes
         cfg = Config(nodes, devices, horizon_step, lookahead, mode, max_instructions, max_edges, max_boxes, map_heap,
                      scratch_capacity, max_buffers, max_live_allocs, max_allocations,
-                     max_queue, device, stream)
+                     max_queue, device, stream, flags)
         h = ctypes.c_void_p()
         r = lib().igs_create(ctypes.byref(cfg), ctypes.byref(h))
         if r != IGS_OK:
@@ -514,7 +516,8 @@ def lower_static(prog: W.Program, outs: Sequence[dict], stream: Optional[int] = 
         out[n].binds, out[n].bind_cap = o["binds"]
         out[n].diags, out[n].diag_cap = o["diags"]
         out[n].counts = o["counts"]
-    cfg = Config(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, None)
+    cfg = Config(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, None,
+                 FLAG_STAGE_D2D if prog.stage_d2d else 0)
     return lib().igs_lower_static(ctypes.byref(cfg), sb, len(bufs), _p32(words), len(tasks), so, len(ops), out, stream)
 
 
@@ -556,6 +559,8 @@ class GpuImpl:
     """Adapter with the same methods as the test harness implementations."""
 
     def __init__(self, prog: W.Program, mode: int = MODE_PLAIN, **kw):
+        if prog.stage_d2d:
+            kw["flags"] = kw.get("flags", 0) | FLAG_STAGE_D2D
         self.ctx = Context(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead, mode=mode, **kw)
         self.nodes = prog.nodes
         self.prog = prog

@@ -402,9 +402,42 @@ static Box map_box(const Acc& a, const Box& chunk, const BufDesc& buf) {
   return r;
 }
 
+// a1 with a split along dims 0 and 1 [R28] (Sec. 3.1: the node split, then
+// the same scheme again among a node's devices): a Cy x Cx grid of chunks,
+// chunk (iy, ix) = rows [floor(iy*E0/Cy), floor((iy+1)*E0/Cy)) x columns
+// [floor(ix*E1/Cx), floor((ix+1)*E1/Cx)), index iy*Cx + ix. Grid row iy goes
+// to node floor(iy*N/Cy); a node's K chunks, numbered j in row-major order,
+// go to its device floor(j*D/K). Empty chunks are dropped after assignment.
+static std::vector<Chunk> split_2d(const Ctx& c, const TaskDesc& t, uint64_t Cy, uint64_t Cx) {
+  std::vector<Chunk> out;
+  const uint64_t E0 = t.range[0], E1 = t.range[1], N = c.N, D = c.D;
+  auto first_row = [&](uint64_t n) { return (n * Cy + N - 1) / N; };  // smallest iy with floor(iy*N/Cy) >= n
+  for (uint64_t iy = 0; iy < Cy; ++iy) {
+    const uint64_t node = iy * N / Cy;
+    const uint64_t r0n = first_row(node), K = (first_row(node + 1) - r0n) * Cx;
+    for (uint64_t ix = 0; ix < Cx; ++ix) {
+      const uint64_t j = (iy - r0n) * Cx + ix;
+      const uint32_t y0 = (uint32_t)(iy * E0 / Cy), y1 = (uint32_t)((iy + 1) * E0 / Cy);
+      const uint32_t x0 = (uint32_t)(ix * E1 / Cx), x1 = (uint32_t)((ix + 1) * E1 / Cx);
+      if (y0 >= y1 || x0 >= x1) continue;
+      Chunk ch;
+      ch.index = (uint32_t)(iy * Cx + ix);
+      ch.node = (uint32_t)node;
+      ch.mem = 2 + (uint32_t)(j * D / K);
+      ch.box.lo[0] = y0; ch.box.hi[0] = y1;
+      ch.box.lo[1] = x0; ch.box.hi[1] = x1;
+      ch.box.lo[2] = 0; ch.box.hi[2] = t.range[2];
+      out.push_back(ch);
+    }
+  }
+  return out;
+}
+
 // a1: split along dim 0 into C chunks, drop empty ones, assign chunk c to the
-// global device floor(c*M/C) [R1, R2].
+// global device floor(c*M/C) [R1, R2]; num_chunks' high 16 bits, if set, give
+// a split along dim 1 too (split_2d).
 static std::vector<Chunk> split(const Ctx& c, const TaskDesc& t) {
+  if (t.chunks >> 16) return split_2d(c, t, t.chunks & 0xFFFFu, t.chunks >> 16);
   std::vector<Chunk> out;
   const uint64_t E0 = t.range[0], C = t.chunks, M = (uint64_t)c.N * c.D;
   for (uint64_t i = 0; i < C; ++i) {
@@ -1111,6 +1144,7 @@ int orc_submit_task(void* p, const uint32_t* w) {
   t.chunks = w[4]; t.kernel = w[5]; t.nacc = w[6];
   for (int i = 0; i < 4; ++i) t.params[i] = w[7 + i];
   if (t.nacc > 8 || t.chunks == 0 || t.dims < 1 || t.dims > 3) return -1;
+  if ((t.chunks >> 16) && ((t.chunks & 0xFFFFu) == 0 || t.dims < 2)) return -1;  // a 2D split needs rows and dims >= 2
   for (uint32_t a = 0; a < t.nacc; ++a) {
     const uint32_t* x = w + 11 + 14 * a;
     t.acc[a].buffer = x[0]; t.acc[a].mode = x[1];

@@ -262,7 +262,7 @@ def nbody_example_program(n: int = 64, iterations: int = 4, lookahead: int = 0) 
 
 def random_program(seed: int, max_extent: int = 12, max_tasks: int = 10, allow_3d: bool = True,
                    allow_bad: bool = True, max_nodes: int = 3, max_devices: int = 2,
-                   uninit_reads: bool = False, horizon_lookahead: bool = False) -> Program:
+                   uninit_reads: bool = False, horizon_lookahead: bool = False, split2d: bool = False) -> Program:
     """A small random program over all mapper kinds.
 
     Writes go through one_to_one or transposed mappers only (injective), and a
@@ -270,7 +270,9 @@ def random_program(seed: int, max_extent: int = 12, max_tasks: int = 10, allow_3
     read_write accessor, so every task has a well-defined sequential meaning.
     Buffers without host data are written before they are read unless
     ``uninit_reads``. With ``allow_bad`` a few tasks carry overlapping writes
-    (an all-mapper write) and must be rejected.
+    (an all-mapper write) and must be rejected. With ``split2d`` most tasks of
+    two or more dimensions are split along dims 0 and 1 (1-3 chunks each; the
+    column count in num_chunks' high 16 bits).
     """
     rng = np.random.default_rng(seed)
     nodes = int(rng.integers(1, max_nodes + 1))
@@ -313,8 +315,12 @@ def random_program(seed: int, max_extent: int = 12, max_tasks: int = 10, allow_3
             kr = [int(rng.integers(1, kr[d] + 1)) if d < B.dims else 1 for d in range(3)]
         kdims = B.dims
         chunks = int(rng.integers(1, 7))
+        if split2d and kdims >= 2 and rng.random() < 0.7:
+            chunks = int(rng.integers(1, 4)) | (int(rng.integers(1, 4)) << 16)
         accs = []
-        bad = allow_bad and rng.random() < 0.06 and chunks > 1 and kr[0] > 1
+        cy, cx = chunks & 0xFFFF, chunks >> 16
+        # an overlapping write needs two non-empty chunks
+        bad = allow_bad and rng.random() < 0.06 and ((cy > 1 and kr[0] > 1) or (cx > 1 and kr[1] > 1))
         rw = (not trans) and written[wb] and rng.random() < 0.4
         if bad:
             accs.append(Accessor(wb, WRITE, all_mapper()))

@@ -184,16 +184,37 @@ class Brute:
         seq = self.seq
         self.seq += 1
         kdims, krange, C = task.dims, list(task.range), task.chunks
-        owner_row = chunk_rows(krange[0], C)
         M = self.N * self.D
         chunks = []
-        for c in range(C):
-            rows = [y for y in range(krange[0]) if owner_row[y] == c]
-            if not rows:
-                continue
-            g = (c * M) // C
-            chunks.append({"index": c, "node": g // self.D, "mem": 2 + g % self.D,
-                           "box": (rows[0], 0, 0, rows[-1] + 1, krange[1], krange[2]), "rows": rows})
+        if C >> 16:
+            # a grid of Cy x Cx chunks: grid rows to nodes, then each node's
+            # chunks (row-major) to its devices, both by block assignment
+            Cy, Cx = C & 0xFFFF, C >> 16
+            owner_row, owner_col = chunk_rows(krange[0], Cy), chunk_rows(krange[1], Cx)
+            node_of = [(iy * self.N) // Cy for iy in range(Cy)]
+            for iy in range(Cy):
+                n = node_of[iy]
+                grid_rows = [r for r in range(Cy) if node_of[r] == n]
+                K = len(grid_rows) * Cx
+                for ix in range(Cx):
+                    rows = [y for y in range(krange[0]) if owner_row[y] == iy]
+                    cols = [x for x in range(krange[1]) if owner_col[x] == ix]
+                    if not rows or not cols:
+                        continue
+                    j = grid_rows.index(iy) * Cx + ix
+                    chunks.append({"index": iy * Cx + ix, "node": n, "mem": 2 + (j * self.D) // K,
+                                   "box": (rows[0], cols[0], 0, rows[-1] + 1, cols[-1] + 1, krange[2]),
+                                   "rows": rows, "cols": cols})
+        else:
+            owner_row = chunk_rows(krange[0], C)
+            for c in range(C):
+                rows = [y for y in range(krange[0]) if owner_row[y] == c]
+                if not rows:
+                    continue
+                g = (c * M) // C
+                chunks.append({"index": c, "node": g // self.D, "mem": 2 + g % self.D,
+                               "box": (rows[0], 0, 0, rows[-1] + 1, krange[1], krange[2]), "rows": rows,
+                               "cols": list(range(krange[1]))})
         accs = task.accessors
         # mapped masks: union over the chunk's items of each item's mapped box
         for ch in chunks:
@@ -202,7 +223,7 @@ class Brute:
                 buf = self.bufs[a.buffer]
                 m = np.zeros(buf["shape"], dtype=bool)
                 for y in ch["rows"]:
-                    for x in range(krange[1]):
+                    for x in ch["cols"]:
                         for z in range(krange[2]):
                             bx = item_box(a.mapper, (y, x, z), buf["shape"], buf["dims"])
                             if bx is not None:

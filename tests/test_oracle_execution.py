@@ -74,3 +74,19 @@ def test_random_staged_d2d(seed):
 def test_paper_shaped_staged_d2d(prog):
     stats = _run(_staged(prog))
     assert stats["kernels"] > 0 and stats["reads_checked"] > 0
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_random_split_2d(seed):
+    """Splits along dims 0 and 1 keep every read coherent and the result
+    sequential."""
+    _run(W.random_program(400_000 + seed, max_extent=10, max_tasks=10, split2d=True, max_devices=3))
+
+
+@pytest.mark.parametrize("prog", [
+    W.wave_program(n=32, steps=8, nodes=2, devices=2, chunks=4 | (4 << 16), lookahead=4),
+    W.jacobi_program(n=32, steps=6, nodes=2, devices=2, chunks=2 | (3 << 16)),
+], ids=lambda p: p.name)
+def test_paper_shaped_split_2d(prog):
+    stats = _run(prog)
+    assert stats["kernels"] > 0 and stats["reads_checked"] > 0

@@ -297,3 +297,51 @@ def test_staged_d2d_replaces_every_device_to_device_copy(prog):
         to_host = sum(1 for s, d in _copy_memories(g1) if s >= 2 and d == 1)
         from_host = sum(1 for s, d in _copy_memories(g1) if s == 1 and d >= 2)
         assert to_host >= d2d and from_host >= d2d
+
+
+def _kernel_boxes(g):
+    out = []
+    for r in g["instrs"]:
+        if int(r[1]) == 9:  # KERNEL
+            b = g["boxes"][int(r[7])]
+            out.append((int(r[2]), int(r[3]), int(r[4]), tuple(int(v) for v in b)))
+    return out
+
+
+def test_split_2d_one_column_equals_the_1d_split():
+    """A 2D split with one chunk column and a row count that is a multiple of
+    the node count assigns exactly as the 1D split: the graphs are equal."""
+    for N, D, C in ((2, 2, 4), (2, 3, 6), (3, 2, 6), (4, 4, 16)):
+        p1 = W.wave_program(n=24, steps=4, nodes=N, devices=D, chunks=C, lookahead=2)
+        p2 = W.wave_program(n=24, steps=4, nodes=N, devices=D, chunks=C | (1 << 16), lookahead=2)
+        g1, _ = oracle_graphs(p1)
+        g2, _ = oracle_graphs(p2)
+        for n in range(N):
+            for k in ("instrs", "edges", "boxes", "binds"):
+                assert np.array_equal(g1[n][k], g2[n][k]), (N, D, C, n, k)
+
+
+def test_split_2d_tiles_the_range_and_nodes_own_row_bands():
+    """Per task the kernels' chunk boxes tile the range; each node's chunks
+    cover a band of whole rows (one box); each device gets chunks; indices
+    are iy * Cx + ix."""
+    N, D, Cy, Cx, n_ = 2, 3, 4, 3, 24
+    p = W.wave_program(n=n_, steps=2, nodes=N, devices=D, chunks=Cy | (Cx << 16), lookahead=0)
+    gs, _ = oracle_graphs(p)
+    by_seq = {}
+    for node, g in enumerate(gs):
+        for seq, idx, mem, b in _kernel_boxes(g):
+            by_seq.setdefault(seq, []).append((node, idx, mem, b))
+    for seq, ks in by_seq.items():
+        cover = np.zeros((n_, n_), np.int32)
+        for node, idx, mem, b in ks:
+            cover[b[0]:b[3], b[1]:b[4]] += 1
+            iy, ix = divmod(idx, Cx)
+            assert (b[0], b[3]) == (iy * n_ // Cy, (iy + 1) * n_ // Cy)
+            assert (b[1], b[4]) == (ix * n_ // Cx, (ix + 1) * n_ // Cx)
+        assert (cover == 1).all()
+        for node in range(N):
+            mine = [b for nd, _, _, b in ks if nd == node]
+            lo, hi = min(b[0] for b in mine), max(b[3] for b in mine)
+            assert sum((b[3] - b[0]) * (b[4] - b[1]) for b in mine) == (hi - lo) * n_
+            assert len({mem for nd, _, mem, _ in ks if nd == node}) == D

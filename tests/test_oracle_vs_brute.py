@@ -76,3 +76,19 @@ def test_random_programs_staged_d2d(seed):
 ], ids=lambda p: f"{p.name}-L{p.lookahead}")
 def test_paper_shaped_programs_staged_d2d(prog):
     _check(_staged(prog))
+
+
+@pytest.mark.parametrize("seed", range(150))
+def test_random_programs_split_2d(seed):
+    """Splits along dims 0 and 1 (Sec. 3.1, hierarchical): both generators
+    emit the same graph."""
+    _check(W.random_program(400_000 + seed, max_extent=10, max_tasks=10, split2d=True, max_devices=3))
+
+
+@pytest.mark.parametrize("prog", [
+    W.wave_program(n=16, steps=5, nodes=2, devices=2, chunks=2 | (2 << 16), lookahead=2),
+    W.wave_program(n=12, steps=4, nodes=3, devices=2, chunks=4 | (3 << 16), lookahead=0),
+    W.jacobi_program(n=16, steps=4, nodes=2, devices=3, chunks=3 | (2 << 16)),
+], ids=lambda p: p.name)
+def test_paper_shaped_programs_split_2d(prog):
+    _check(prog)

@@ -132,12 +132,17 @@ typedef struct igs_accessor {
 } igs_accessor;
 
 /* A task: a kernel over `range` (dims 1..3, trailing extents 1), split along
- * dim 0 into num_chunks chunks (Sec. 3.1). Same layout as 11 + 14 * 8 uint32
- * words. */
+ * dim 0 into num_chunks chunks (Sec. 3.1): chunk c = rows [c*E0/C, (c+1)*E0/C)
+ * on global device floor(c*M/C). If num_chunks' high 16 bits Cx are non-zero
+ * (dims >= 2), the range is split along dims 0 and 1 into a Cy x Cx grid (Cy
+ * = the low 16 bits): grid row iy goes to node floor(iy*N/Cy), and a node's K
+ * chunks, numbered j in row-major order, to its device floor(j*D/K) (the
+ * node split applied a second time among the node's devices); chunk index
+ * iy*Cx + ix. Same layout as 11 + 14 * 8 uint32 words. */
 typedef struct igs_task {
   uint32_t dims;
   uint32_t range[3];
-  uint32_t num_chunks;    /* >= 1 */
+  uint32_t num_chunks;    /* >= 1; bits 16-31: chunks along dim 1 (a 2D split, see above) */
   uint32_t kernel_id;     /* workload kernel run by execute (0 = none) */
   uint32_t num_accessors; /* 0..8 */
   uint32_t params[4];     /* workload kernel parameters */

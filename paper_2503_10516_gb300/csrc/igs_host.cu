@@ -695,6 +695,7 @@ int igs_destroy_buffer(igs_ctx* c, uint32_t b) {
 
 int igs_submit_task(igs_ctx* c, const igs_task* t, uint64_t* out_seq) {
   if (!c || !t) return fail_ctx(c, IGS_ERR_INVALID_ARG, "null argument");
+  if ((t->num_chunks >> 16) && ((t->num_chunks & 0xFFFFu) == 0 || t->dims < 2)) return IGS_ERR_INVALID_ARG;
   if (t->dims < 1 || t->dims > 3 || t->num_chunks == 0 || t->num_accessors > IGS_MAX_ACCESSORS)
     return fail_ctx(c, IGS_ERR_INVALID_ARG, "bad task header");
   for (int d = 0; d < 3; ++d)
@@ -777,7 +778,8 @@ int igs_lower_batch_shaped(igs_ctx* const* ctxs, uint32_t n, const igs_batch_sha
       w += 1;
       if (x->items[k].kind == IT_TASK) {
         const igs_task& t = x->tasks[x->items[k].task];
-        w += (double)t.num_chunks * t.num_accessors / x->N;
+        const double chunks = (double)(t.num_chunks & 0xFFFFu) * std::max(1u, t.num_chunks >> 16);
+        w += chunks * t.num_accessors / x->N;
       }
     }
     for (uint32_t k = 0; k < x->N; ++k) {

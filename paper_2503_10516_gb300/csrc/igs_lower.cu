@@ -1042,6 +1042,40 @@ __device__ Bx buffer_box(const BufDesc& b) {
 // a1: chunks of a task: key = chunk index, v0 = node, v1 = memory (Sec. 3.1).
 __device__ __noinline__ void task_chunks(Ctx& c, const igs_task& t, Table& CH) {
   t_reset(CH);
+  const uint32_t Cx = t.num_chunks >> 16;
+  if (Cx) {
+    // split along dims 0 and 1: a Cy x Cx grid; grid row iy goes to node
+    // floor(iy*N/Cy), a node's K chunks (row-major, j) to its device
+    // floor(j*D/K); chunk index iy*Cx + ix
+    const uint64_t Cy = t.num_chunks & 0xFFFFu, N = c.N, D = c.D, E0 = t.range[0], E1 = t.range[1];
+    const uint32_t total = (uint32_t)(Cy * Cx);
+    for (uint32_t base = 0; base < total; base += 32) {
+      const uint32_t i = base + c.lane;
+      bool ok = false;
+      Bx b{};
+      uint32_t node = 0, mem = 0;
+      if (i < total) {
+        const uint64_t iy = i / Cx, ix = i % Cx;
+        const uint64_t nd = iy * N / Cy;
+        const uint64_t r0n = (nd * Cy + N - 1) / N, r1n = ((nd + 1) * Cy + N - 1) / N;
+        const uint64_t K = (r1n - r0n) * Cx, j = (iy - r0n) * Cx + ix;
+        node = (uint32_t)nd;
+        mem = 2 + (uint32_t)(j * D / K);
+        b.lo[0] = (uint32_t)(iy * E0 / Cy);
+        b.hi[0] = (uint32_t)((iy + 1) * E0 / Cy);
+        b.lo[1] = (uint32_t)(ix * E1 / Cx);
+        b.hi[1] = (uint32_t)((ix + 1) * E1 / Cx);
+        b.lo[2] = 0;
+        b.hi[2] = t.range[2];
+        ok = b.lo[0] < b.hi[0] && b.lo[1] < b.hi[1];
+      }
+      const uint32_t s = t_claim(c, CH, ok);
+      if (c.err) return;
+      if (ok) t_put(CH, s, i, b, node, mem, 0);
+    }
+    __syncwarp();
+    return;
+  }
   const uint64_t E0 = t.range[0], C = t.num_chunks, M = (uint64_t)c.N * c.D;
   for (uint32_t base = 0; base < t.num_chunks; base += 32) {
     const uint32_t i = base + c.lane;
@@ -1855,13 +1889,18 @@ __device__ __noinline__ void node_bboxes(Ctx& c, const Table& CH, Table& NB) {
 
 // The union over a node's chunks of an accessor's mapped boxes is the mapped
 // box of the node's chunk range when at most one buffer dimension follows
-// kernel dimension 0 (the per-chunk images are then consecutive intervals in
-// that dimension and equal in the others).
-__device__ __forceinline__ bool union_is_image(const igs_accessor& a, const BufDesc& buf) {
-  int k = 0;
+// each split kernel dimension (dimension 0, and 1 for a split along it): the
+// chunks of a node form a full grid, so the per-chunk images are products of
+// consecutive intervals.
+__device__ __forceinline__ bool union_is_image(const igs_task& t, uint32_t acc, const BufDesc& buf) {
+  const igs_accessor& a = t.acc[acc];
+  int k0 = 0, k1 = 0;
   for (int d = 0; d < (int)buf.dims; ++d)
-    if (a.dim[d].kind == IGS_MAP_AFFINE && a.dim[d].a == 0) ++k;
-  return k <= 1;
+    if (a.dim[d].kind == IGS_MAP_AFFINE) {
+      if (a.dim[d].a == 0) ++k0;
+      if (a.dim[d].a == 1) ++k1;
+    }
+  return k0 <= 1 && ((t.num_chunks >> 16) == 0 || k1 <= 1);
 }
 
 // ---- several warps per node ---------------------------------------------------
@@ -1960,7 +1999,7 @@ __device__ __noinline__ void a3_buffer(Ctx& c, const igs_task& t, uint32_t seq, 
     auto lacking = [m](uint32_t, uint32_t repl, uint32_t) { return !((repl >> m) & 1u); };
     for (uint32_t a = 0; a < na; ++a) {
       if (t.acc[a].buffer != b || !(t.acc[a].mode & IGS_READ)) continue;
-      if (union_is_image(t.acc[a], bd)) {
+      if (union_is_image(t, a, bd)) {
         const Bx x = map_box(t.acc[a], t_box(NB, m), bd);
         if (!bx_empty(x)) t_query(c, O, NONE, x, TMP, lacking);
       } else {
@@ -2051,7 +2090,7 @@ __device__ __noinline__ void a3_buffer(Ctx& c, const igs_task& t, uint32_t seq, 
   // writes: owner = writing node, replicated there only
   for (uint32_t a = 0; a < na; ++a) {
     if (t.acc[a].buffer != b || !(t.acc[a].mode & IGS_WRITE)) continue;
-    if (union_is_image(t.acc[a], bd)) {
+    if (union_is_image(t, a, bd)) {
       for (uint32_t wn = 0; wn < c.N; ++wn) {
         if (t_key(NB, wn) == DEAD) continue;
         const Bx x = map_box(t.acc[a], t_box(NB, wn), bd);
@@ -3157,7 +3196,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     Table B = bst_t(c, t.acc[a].buffer);
     t_tidy(c, B);
     const uint32_t from = B.n;
-    if (union_is_image(t.acc[a], bd)) {
+    if (union_is_image(t, a, bd)) {
       // all chunks' writes form the image of the task's range: one subtraction
       Bx all;
       all.lo[0] = all.lo[1] = all.lo[2] = 0xFFFFFFFFu;

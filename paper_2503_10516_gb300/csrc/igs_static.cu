@@ -113,6 +113,7 @@ extern "C" int igs_lower_static(const igs_config* cfg, const igs_static_buffer* 
         if (op.arg >= num_tasks) return IGS_ERR_INVALID_ARG;
         const igs_task& t = tasks[op.arg];
         if (t.dims < 1 || t.dims > 3 || t.num_chunks == 0 || t.num_accessors > IGS_MAX_ACCESSORS) return IGS_ERR_INVALID_ARG;
+        if ((t.num_chunks >> 16) && ((t.num_chunks & 0xFFFFu) == 0 || t.dims < 2)) return IGS_ERR_INVALID_ARG;
         for (uint32_t a = 0; a < t.num_accessors; ++a) {
           if (t.acc[a].buffer >= created || t.acc[a].mode < 1 || t.acc[a].mode > 3) return IGS_ERR_INVALID_ARG;
           for (int d = 0; d < 3; ++d)

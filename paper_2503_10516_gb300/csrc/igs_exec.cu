@@ -231,7 +231,17 @@ __device__ void run_item(const KernelJob& J, uint32_t y, uint32_t x, uint32_t z)
       const uint32_t n = P.ext[0];
       const float4 pi = ld4<Ld>(P, y);
       float ax = 0.f, ay = 0.f, az = 0.f;
-      for (uint32_t j = 0; j < n; ++j) nbody_term(pi, ld4<Ld>(P, j), ax, ay, az);
+      // rows [0, n) inside both the permitted box and the allocation (one
+      // row per body): no per-body check is needed
+      const bool whole = P.valid && n > 0 && P.plo[0] == 0 && P.phi[0] >= n && P.lo[0] == 0 && P.hi[0] >= n &&
+                         P.plo[1] == 0 && P.phi[1] >= 1 && P.plo[2] == 0 && P.phi[2] >= 1 && P.lo[1] == 0 &&
+                         P.hi[1] == 1 && P.lo[2] == 0 && P.hi[2] == 1 && P.elem == 16;
+      if (whole) {
+        const float4* pb = reinterpret_cast<const float4*>(P.ptr);
+        for (uint32_t j = 0; j < n; ++j) nbody_term(pi, Ld::ld(pb + j), ax, ay, az);
+      } else {
+        for (uint32_t j = 0; j < n; ++j) nbody_term(pi, ld4<Ld>(P, j), ax, ay, az);
+      }
       st4(V, y, nbody_kick(ld4<Ld>(V, y), ax, ay, az));
       break;
     }

@@ -61,3 +61,58 @@ def test_wave_8192_bench_configuration_sampled(program_and_expected, executor):
         got = c.read_buffer(ob, (y0, x0, 0), (y0 + PATCH, x0 + PATCH, 1), 4).view(np.float32).reshape(PATCH, PATCH)
         assert np.array_equal(got, w), f"patch at ({y0}, {x0}) differs (executor {executor})"
     c.close()
+
+
+NB = 1 << 20
+BODIES = [0, 1, 4095, 8192, 123457, NB // 2, NB - 2, NB - 1]
+
+
+def _nbody_bodies(P, V, idx):
+    """Velocity and position of bodies idx after one step: the sum over all
+    bodies in index order, in float32, each term as the kernel forms it."""
+    eps, dt = np.float32(1e-6), np.float32(0.01)
+    out_v, out_p = [], []
+    for i in idx:
+        pi = P[i]
+        dx = P[:, 0] - pi[0]
+        dy = P[:, 1] - pi[1]
+        dz = P[:, 2] - pi[2]
+        r2 = ((dx * dx + dy * dy) + dz * dz) + eps
+        inv = np.float32(1.0) / (r2 * np.sqrt(r2))
+        wgt = P[:, 3] * inv
+        acc = [np.add.accumulate((d * wgt).astype(np.float32), dtype=np.float32)[-1] for d in (dx, dy, dz)]
+        v = V[i].copy()
+        for c in range(3):
+            v[c] = v[c] + acc[c] * dt
+        p = P[i].copy()
+        for c in range(3):
+            p[c] = p[c] + v[c] * dt
+        out_v.append(v)
+        out_p.append(p)
+    return np.array(out_v, np.float32), np.array(out_p, np.float32)
+
+
+@pytest.mark.parametrize("executor", [0, 1])
+def test_nbody_1m_configuration_one_step_sampled(executor):
+    """The all-pairs N-body configuration at full size (2^20 float4 bodies,
+    8 nodes x 4 devices, 128 chunks, lookahead 4), one step (both tasks):
+    sampled bodies' velocity and position equal a float32 sequential j-sum."""
+    from paper_2503_10516_gb300 import igs
+    p = W.nbody_program(n=NB, steps=1, nodes=8, devices=4, chunks=128, lookahead=4)
+    P0 = p.buffers[0].init.reshape(NB, 4).astype(np.float32)
+    V0 = p.buffers[1].init.reshape(NB, 4).astype(np.float32)
+    want_v, want_p = _nbody_bodies(P0, V0, BODIES)
+    c = igs.Context(p.nodes, p.devices, p.horizon_step, p.lookahead, mode=igs.MODE_BATCHED)
+    c.set_executor(executor)
+    for b in p.buffers:
+        c.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init)
+    for t in p.tasks:
+        c.submit(t)
+    c.flush()
+    c.execute()
+    for k, i in enumerate(BODIES):
+        v = c.read_buffer(1, (i, 0, 0), (i + 1, 1, 1), 16).view(np.float32).reshape(4)
+        q = c.read_buffer(0, (i, 0, 0), (i + 1, 1, 1), 16).view(np.float32).reshape(4)
+        assert np.array_equal(v, want_v[k]), f"velocity of body {i} (executor {executor})"
+        assert np.array_equal(q, want_p[k]), f"position of body {i} (executor {executor})"
+    c.close()

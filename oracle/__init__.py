@@ -53,6 +53,7 @@ def lib():
             L.orc_submit_task.restype = ctypes.c_int
             L.orc_set_lookahead.argtypes = [vp, u32]
             L.orc_set_stage_d2d.argtypes = [vp, ctypes.c_int]
+            L.orc_set_horizon_cp.argtypes = [vp, ctypes.c_int]
             L.orc_flush.argtypes = [vp]
             L.orc_count.argtypes = [vp, u32, ctypes.c_int]
             L.orc_count.restype = u32
@@ -125,6 +126,10 @@ class Oracle:
     def set_stage_d2d(self, on: bool) -> None:
         """Device-to-device copies staged in host memory (R27)."""
         lib().orc_set_stage_d2d(self._h, 1 if on else 0)
+
+    def set_horizon_cp(self, on: bool) -> None:
+        """Horizons by the task graph's critical path (R29)."""
+        lib().orc_set_horizon_cp(self._h, 1 if on else 0)
 
     def set_lookahead(self, L: int) -> None:
         lib().orc_set_lookahead(self._h, L)

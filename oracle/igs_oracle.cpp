@@ -363,6 +363,12 @@ struct Node {
 
 struct Ctx {
   uint32_t N, D, hstep;
+  // critical-path horizon cadence [R29]: per buffer the boxes each task last
+  // wrote and the boxes tasks read since; per task its depth in the task graph
+  bool horizon_cp = false;
+  std::map<uint32_t, std::vector<std::pair<Box, uint32_t>>> t_writers, t_readers;
+  std::vector<uint32_t> depth;
+  uint32_t cpl = 0, cpl_at_horizon = 0;
   std::vector<BufDesc> bufs;
   std::map<uint32_t, RMap<Own>> own;  // buffer -> node-level map
   std::vector<Node> nodes;
@@ -992,6 +998,50 @@ static void broadcast(Ctx& c, ItemKind k, uint32_t arg) {
 
 // a3: node-level push / await-push [R12, R19]; returns false if the task has
 // overlapping writes (rejected, no state change).
+// Task-graph bookkeeping for the critical-path horizon cadence [R29] (Sec.
+// 3.5): a task's region per accessor is its range mapper over the task's
+// whole range; it depends on the last writers of every region it accesses
+// and, for writes, on the tasks that read the region since; its depth is one
+// more than its deepest predecessor's. True when the critical path (the
+// largest depth so far) has grown by horizon_step since the last horizon.
+static bool critical_path_step(Ctx& c, const TaskDesc& t) {
+  Box whole;
+  for (int d = 0; d < 3; ++d) { whole.lo[d] = 0; whole.hi[d] = t.range[d]; }
+  std::vector<std::pair<uint32_t, Box>> acc(t.nacc);
+  uint32_t deepest = 0;
+  for (uint32_t a = 0; a < t.nacc; ++a) {
+    const uint32_t b = t.acc[a].buffer;
+    acc[a] = {b, map_box(t.acc[a], whole, c.bufs[b])};
+    if (empty(acc[a].second)) continue;
+    for (const auto& e : c.t_writers[b])
+      if (overlap(e.first, acc[a].second)) deepest = std::max(deepest, c.depth[e.second]);
+    if (t.acc[a].mode & M_WRITE)
+      for (const auto& e : c.t_readers[b])
+        if (overlap(e.first, acc[a].second)) deepest = std::max(deepest, c.depth[e.second]);
+  }
+  const uint32_t me = (uint32_t)c.depth.size();
+  c.depth.push_back(deepest + 1);
+  for (uint32_t a = 0; a < t.nacc; ++a)
+    if ((t.acc[a].mode & M_READ) && !empty(acc[a].second)) c.t_readers[acc[a].first].push_back({acc[a].second, me});
+  for (uint32_t a = 0; a < t.nacc; ++a) {
+    if (!(t.acc[a].mode & M_WRITE) || empty(acc[a].second)) continue;
+    const Box& w = acc[a].second;
+    for (auto* list : {&c.t_writers[acc[a].first], &c.t_readers[acc[a].first]}) {
+      std::vector<std::pair<Box, uint32_t>> kept;
+      for (const auto& e : *list)
+        for (const Box& rest : region_minus({e.first}, {w})) kept.push_back({rest, e.second});
+      *list = kept;
+    }
+    c.t_writers[acc[a].first].push_back({w, me});
+  }
+  c.cpl = std::max(c.cpl, deepest + 1);
+  if (c.hstep && c.cpl >= c.cpl_at_horizon + c.hstep) {
+    c.cpl_at_horizon = c.cpl;
+    return true;
+  }
+  return false;
+}
+
 static bool submit(Ctx& c, const TaskDesc& td) {
   c.tasks.push_back(td);
   const TaskDesc& t = c.tasks.back();
@@ -1074,8 +1124,9 @@ static bool submit(Ctx& c, const TaskDesc& td) {
   } else {
     c.rejected.push_back(seq);
   }
+  const bool cp_horizon = critical_path_step(c, t);  // every task counts, rejected or not [R29]
   ++c.ntasks;
-  if (c.hstep && c.ntasks % c.hstep == 0) broadcast(c, I_HORIZON, 0);
+  if (c.horizon_cp ? cp_horizon : (c.hstep && c.ntasks % c.hstep == 0)) broadcast(c, I_HORIZON, 0);
   return !bad;
 }
 
@@ -1155,6 +1206,11 @@ int orc_submit_task(void* p, const uint32_t* w) {
     }
   }
   return submit(*c, t) ? 0 : -2;
+}
+
+int orc_set_horizon_cp(void* p, int on) {
+  static_cast<Ctx*>(p)->horizon_cp = on != 0;
+  return 0;
 }
 
 int orc_set_stage_d2d(void* p, int on) {

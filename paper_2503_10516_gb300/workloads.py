@@ -134,6 +134,7 @@ class Program:
     lookahead: int
     ops: list
     stage_d2d: bool = False  # device-to-device copies staged in host memory
+    horizon_cp: bool = False  # horizons by the task graph's critical path, not every horizon_step tasks
 
     @property
     def buffers(self) -> List[Buffer]:

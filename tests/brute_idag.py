@@ -147,6 +147,12 @@ class Brute:
         self.ntasks = 0
         self.rejected = []
         self.stage_d2d = False  # device-to-device copies staged in host memory
+        self.horizon_cp = False  # horizons by the task graph's critical path
+        self.t_last = {}         # buffer -> per-element task that last wrote it (-1: none)
+        self.t_read = {}         # buffer -> {task: elements it read since their last write}
+        self.depth = []          # per task: depth in the task graph
+        self.cpl = 0
+        self.cpl_h = 0
 
     # -- items --
     def create_buffer(self, dims, extent, elem, init):
@@ -273,10 +279,54 @@ class Brute:
                             repl[ch["masks"][ai]] = 1 << ch["node"]
             for n in range(self.N):
                 self._deliver(self.nodes[n], {"kind": "task", "seq": seq, "nt": per[n]})
+        fire = self._critical_path(task)
         self.ntasks += 1
-        if self.hstep and self.ntasks % self.hstep == 0:
+        if (fire if self.horizon_cp else (self.hstep and self.ntasks % self.hstep == 0)):
             self._broadcast("horizon", 0)
         return 0 if not bad else -2
+
+    def _critical_path(self, task):
+        """Task-graph depth of this task from per-element last writers and
+        readers; True when the longest path grew by horizon_step since the
+        last horizon."""
+        me = len(self.depth)
+        masks = []
+        for a in task.accessors:
+            buf = self.bufs[a.buffer]
+            m = np.zeros(buf["shape"], dtype=bool)
+            for y in range(task.range[0]):
+                for x in range(task.range[1]):
+                    for z in range(task.range[2]):
+                        bx = item_box(a.mapper, (y, x, z), buf["shape"], buf["dims"])
+                        if bx is not None:
+                            m |= box_mask(buf["shape"], bx)
+            masks.append(m)
+        deepest = 0
+        for a, m in zip(task.accessors, masks):
+            last = self.t_last.setdefault(a.buffer, np.full(self.bufs[a.buffer]["shape"], -1, dtype=np.int64))
+            readers = self.t_read.setdefault(a.buffer, {})
+            for u in np.unique(last[m]):
+                if u >= 0:
+                    deepest = max(deepest, self.depth[int(u)])
+            if a.mode & M_WRITE:
+                for u, rm in readers.items():
+                    if (rm & m).any():
+                        deepest = max(deepest, self.depth[u])
+        self.depth.append(deepest + 1)
+        for a, m in zip(task.accessors, masks):
+            if a.mode & M_READ:
+                readers = self.t_read[a.buffer]
+                readers[me] = readers.get(me, np.zeros_like(m)) | m
+        for a, m in zip(task.accessors, masks):
+            if a.mode & M_WRITE:
+                for u in self.t_read[a.buffer]:
+                    self.t_read[a.buffer][u] = self.t_read[a.buffer][u] & ~m
+                self.t_last[a.buffer][m] = me
+        self.cpl = max(self.cpl, deepest + 1)
+        if self.hstep and self.cpl >= self.cpl_h + self.hstep:
+            self.cpl_h = self.cpl
+            return True
+        return False
 
     # -- lookahead queue --
     def _queued(self, n):

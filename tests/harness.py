@@ -39,6 +39,8 @@ class OracleImpl:
         self.o = oracle.Oracle(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead)
         if prog.stage_d2d:
             self.o.set_stage_d2d(True)
+        if prog.horizon_cp:
+            self.o.set_horizon_cp(True)
         self.nodes = prog.nodes
 
     def create_buffer(self, dims, extent, elem, init):
@@ -68,6 +70,7 @@ class BruteImpl:
         from tests.brute_idag import Brute
         self.b = Brute(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead)
         self.b.stage_d2d = prog.stage_d2d
+        self.b.horizon_cp = prog.horizon_cp
         self.nodes = prog.nodes
 
     def create_buffer(self, dims, extent, elem, init):

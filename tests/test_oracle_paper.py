@@ -345,3 +345,50 @@ def test_split_2d_tiles_the_range_and_nodes_own_row_bands():
             lo, hi = min(b[0] for b in mine), max(b[3] for b in mine)
             assert sum((b[3] - b[0]) * (b[4] - b[1]) for b in mine) == (hi - lo) * n_
             assert len({mem for nd, _, mem, _ in ks if nd == node}) == D
+
+
+def _horizon_seqs(g):
+    return [int(r[2]) for r in g["instrs"] if int(r[1]) == 1]  # HORIZON
+
+
+def test_horizon_cp_on_a_chain_equals_the_count_cadence():
+    """Every wave task depends on the one before (a chain): the critical path
+    grows by one per task, so horizons come every horizon_step tasks, as with
+    the count cadence — the graphs are identical."""
+    for step in (1, 2, 4):
+        p = W.wave_program(n=16, steps=12, nodes=2, devices=2, chunks=4, lookahead=2, horizon_step=step)
+        g0, _ = oracle_graphs(p)
+        p.horizon_cp = True
+        g1, _ = oracle_graphs(p)
+        for a, b in zip(g0, g1):
+            for k in ("instrs", "edges", "boxes", "binds"):
+                assert np.array_equal(a[k], b[k]), (step, k)
+
+
+def _independent(k, step, chains=1):
+    """k tasks writing `chains` separate buffers in turn, each task reading the
+    buffer it writes (one chain per buffer)."""
+    bufs = [W.Buffer(1, (8, 1, 1), 4, np.arange(8, dtype=np.uint32), "u32") for _ in range(chains)]
+    ops = [("buffer", b) for b in bufs]
+    for i in range(k):
+        ops.append(("task", W.Task(1, (8, 1, 1), 2, W.K_GENERIC, [W.Accessor(i % chains, W.READ_WRITE, W.one_to_one())])))
+    ops.append(("flush",))
+    p = W.Program(f"chains{chains}", 1, 2, step, 0, ops)
+    p.horizon_cp = True
+    return p
+
+
+def test_horizon_cp_counts_the_critical_path_not_the_tasks():
+    """c interleaved independent chains of k tasks: the critical path grows by
+    one every c tasks, so a horizon comes every c * horizon_step tasks; with
+    tasks that share nothing (one task per chain) none ever comes after the
+    first horizon_step levels."""
+    for chains, k, step in ((1, 12, 3), (2, 12, 3), (3, 18, 2), (4, 16, 2)):
+        g, _ = oracle_graphs(_independent(k, step, chains))
+        seqs = _horizon_seqs(g[0])
+        # task i (0-based) has depth i // chains + 1; a horizon follows the first
+        # task of each depth that is a multiple of step
+        tasks_with_horizon = [i for i in range(k) if i % chains == 0 and (i // chains + 1) % step == 0]
+        assert len(seqs) == len(tasks_with_horizon), (chains, k, step, seqs)
+    g, _ = oracle_graphs(_independent(10, 2, chains=10))
+    assert _horizon_seqs(g[0]) == []

@@ -92,3 +92,12 @@ def test_random_programs_split_2d(seed):
 ], ids=lambda p: p.name)
 def test_paper_shaped_programs_split_2d(prog):
     _check(prog)
+
+
+@pytest.mark.parametrize("seed", range(150))
+def test_random_programs_horizon_cp(seed):
+    """Horizons by the task graph's critical path (Sec. 3.5): both generators
+    build the same task-level dependencies and emit the same graph."""
+    p = W.random_program(500_000 + seed, max_extent=10, max_tasks=12)
+    p.horizon_cp = True
+    _check(p)

@@ -122,6 +122,14 @@ typedef struct igs_config {
  * canonical box list) and its free, emitted in that order in place of the
  * direct copy. */
 #define IGS_FLAG_STAGE_D2D 1u
+/* Horizons by the task graph's critical path (Sec. 3.5) instead of after
+ * every horizon_step tasks: a task depends on the tasks that last wrote any
+ * part of a region it accesses and, where it writes, on the tasks that read
+ * that region since (each accessor's region = its range mapper over the
+ * task's whole range); its depth is one more than its deepest
+ * predecessor's; a horizon follows the task after which the largest depth
+ * so far has grown by horizon_step since the previous horizon. */
+#define IGS_FLAG_HORIZON_CP 2u
 
 typedef struct igs_map_dim { uint32_t kind, a, b, c; } igs_map_dim;
 
@@ -491,6 +499,14 @@ typedef struct igs_static_output {
   igs_diag* diags;         uint32_t diag_cap;
   uint32_t* counts;
 } igs_static_output;
+/* Where horizons go in a task sequence (host only; no device is touched):
+ * horizon_after[i] = 1 when a horizon follows tasks[i], under horizon_step
+ * and IGS_FLAG_HORIZON_CP in flags (else every horizon_step tasks), exactly
+ * as igs_submit_task and igs_lower_static place them. Task validity is not
+ * checked beyond buffer ids (IGS_ERR_INVALID_ARG). */
+int igs_horizon_plan(const igs_static_buffer* bufs, uint32_t num_buffers, const igs_task* tasks, uint32_t num_tasks,
+                     uint32_t horizon_step, uint32_t flags, uint8_t* horizon_after);
+
 int igs_lower_static(const igs_config* cfg, const igs_static_buffer* bufs, uint32_t num_buffers,
                      const igs_task* tasks, uint32_t num_tasks, const igs_static_op* ops, uint32_t num_ops,
                      igs_static_output* outs, void* stream);

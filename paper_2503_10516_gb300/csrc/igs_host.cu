@@ -19,6 +19,7 @@
 
 #include "igs_exec.h"
 #include "igs_internal.h"
+#include "igs_tdag.h"
 
 using namespace igs;
 
@@ -88,6 +89,7 @@ struct igs_ctx {
   std::vector<uint32_t> seq_task;  // submission sequence number -> task index (NONE if not a task)
   uint32_t items_up = 0, tasks_up = 0, bufs_up = 0;
   uint32_t seq = 0, ntasks = 0;
+  CriticalPath cpath;  // task-graph depth (IGS_FLAG_HORIZON_CP)
   // device
   Item* d_items = nullptr;
   uint32_t cap_items = 0;
@@ -362,7 +364,7 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
   if (!cfg || cfg->num_nodes < 1 || cfg->num_nodes > 32 || cfg->devices_per_node < 1 || cfg->devices_per_node > 29)
     return IGS_ERR_INVALID_ARG;
   if (cfg->mode > IGS_MODE_BATCHED) return IGS_ERR_INVALID_ARG;
-  if (cfg->flags & ~IGS_FLAG_STAGE_D2D) return IGS_ERR_INVALID_ARG;
+  if (cfg->flags & ~(IGS_FLAG_STAGE_D2D | IGS_FLAG_HORIZON_CP)) return IGS_ERR_INVALID_ARG;
   igs_ctx* c = new igs_ctx();
   c->cfg = *cfg;
   c->N = cfg->num_nodes;
@@ -714,8 +716,14 @@ int igs_submit_task(igs_ctx* c, const igs_task* t, uint64_t* out_seq) {
   c->tasks.push_back(*t);
   const uint32_t s = c->seq;
   push_item(c, IT_TASK, 0, ti);
+  const bool cp_horizon = c->cpath.add(
+      *t, [c](uint32_t b) { return c->bufs[b].dims; }, [c](uint32_t b) { return c->bufs[b].extent; },
+      c->cfg.horizon_step);
   c->ntasks++;
-  if (c->cfg.horizon_step && c->ntasks % c->cfg.horizon_step == 0) push_item(c, IT_HORIZON, 0, 0);
+  const bool horizon = (c->cfg.flags & IGS_FLAG_HORIZON_CP)
+                           ? cp_horizon
+                           : (c->cfg.horizon_step && c->ntasks % c->cfg.horizon_step == 0);
+  if (horizon) push_item(c, IT_HORIZON, 0, 0);
   if (out_seq) *out_seq = s;
   if (c->cfg.mode == IGS_MODE_PLAIN) return launch_lower(c);
   return IGS_OK;

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "igs_internal.h"
+#include "igs_tdag.h"
 
 namespace {
 
@@ -59,6 +60,22 @@ Layout layout(uint32_t cap_instr) {
 
 }  // namespace
 
+extern "C" int igs_horizon_plan(const igs_static_buffer* bufs, uint32_t num_buffers, const igs_task* tasks,
+                                uint32_t num_tasks, uint32_t horizon_step, uint32_t flags, uint8_t* horizon_after) {
+  if ((num_buffers && !bufs) || (num_tasks && (!tasks || !horizon_after))) return IGS_ERR_INVALID_ARG;
+  igs::CriticalPath cpath;
+  for (uint32_t i = 0; i < num_tasks; ++i) {
+    const igs_task& t = tasks[i];
+    if (t.num_accessors > IGS_MAX_ACCESSORS) return IGS_ERR_INVALID_ARG;
+    for (uint32_t a = 0; a < t.num_accessors; ++a)
+      if (t.acc[a].buffer >= num_buffers) return IGS_ERR_INVALID_ARG;
+    const bool cp = cpath.add(
+        t, [&](uint32_t b) { return bufs[b].dims; }, [&](uint32_t b) { return bufs[b].extent; }, horizon_step);
+    horizon_after[i] = (flags & IGS_FLAG_HORIZON_CP) ? cp : (horizon_step && (i + 1) % horizon_step == 0);
+  }
+  return IGS_OK;
+}
+
 extern "C" int igs_lower_static(const igs_config* cfg, const igs_static_buffer* bufs, uint32_t num_buffers,
                                 const igs_task* tasks, uint32_t num_tasks, const igs_static_op* ops,
                                 uint32_t num_ops, igs_static_output* outs, void* stream_ptr) {
@@ -99,6 +116,7 @@ extern "C" int igs_lower_static(const igs_config* cfg, const igs_static_buffer* 
     if (bd[b].dims < 1 || bd[b].dims > 3) return IGS_ERR_INVALID_ARG;
   }
   uint32_t seq = 0, ntask = 0, created = 0;
+  CriticalPath cpath;  // task-graph depth (IGS_FLAG_HORIZON_CP)
   for (uint32_t i = 0; i < num_ops; ++i) {
     const igs_static_op& op = ops[i];
     Item it{};
@@ -121,8 +139,12 @@ extern "C" int igs_lower_static(const igs_config* cfg, const igs_static_buffer* 
               return IGS_ERR_INVALID_ARG;
         }
         items.push_back(Item{IT_TASK, seq++, 0, op.arg});
+        const bool cp_horizon = cpath.add(
+            t, [&](uint32_t b) { return bufs[b].dims; }, [&](uint32_t b) { return bufs[b].extent; },
+            cfg->horizon_step);
         ++ntask;
-        if (cfg->horizon_step && ntask % cfg->horizon_step == 0) items.push_back(Item{IT_HORIZON, seq++, 0, 0});
+        if ((cfg->flags & IGS_FLAG_HORIZON_CP) ? cp_horizon : (cfg->horizon_step && ntask % cfg->horizon_step == 0))
+          items.push_back(Item{IT_HORIZON, seq++, 0, 0});
         break;
       }
       case IGS_OP_FLUSH:

@@ -34,7 +34,8 @@ EXPORTS = ("igs_create", "igs_destroy", "igs_create_buffer", "igs_destroy_buffer
            "igs_set_timing", "igs_stats", "igs_profile", "igs_lower_static", "igs_submit_epoch",
            "igs_serve_create", "igs_serve_destroy", "igs_serve_attach", "igs_serve_start", "igs_serve_progress",
            "igs_serve_detach", "igs_serve_stop", "igs_run", "igs_lower_batch_shaped", "igs_set_executor",
-           "igs_exec_stats", "igs_selftest_flow_wait", "igs_bounds_errors", "igs_serve_replay")
+           "igs_exec_stats", "igs_selftest_flow_wait", "igs_bounds_errors", "igs_serve_replay",
+           "igs_horizon_plan")
 EXEC_LEVELS, EXEC_DATAFLOW = 0, 1  # IGS_EXEC_*
 ORDER_SUBMISSION, ORDER_LONGEST_FIRST = 0, 1  # IGS_ORDER_*
 
@@ -55,6 +56,7 @@ class Config(ctypes.Structure):
                 ("max_allocations", ctypes.c_uint32), ("max_queue", ctypes.c_uint32),
                 ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
 FLAG_STAGE_D2D = 1  # IGS_FLAG_STAGE_D2D
+FLAG_HORIZON_CP = 2  # IGS_FLAG_HORIZON_CP
 
 
 class GraphView(ctypes.Structure):
@@ -128,6 +130,7 @@ def lib():
         L.igs_selftest_flow_wait.argtypes = [u32]
         L.igs_bounds_errors.argtypes = [vp, vp, u32, P32]
         L.igs_serve_replay.argtypes = [vp, ctypes.POINTER(vp), u32, vp, u32, u32, vp, vp]
+        L.igs_horizon_plan.argtypes = [vp, u32, vp, u32, u32, u32, vp]
         L.igs_sync.argtypes = [vp]
         L.igs_submit_epoch.argtypes = [vp]
         L.igs_serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(vp)]
@@ -416,6 +419,26 @@ class Server:
             pass
 
 
+def horizon_plan(prog: W.Program) -> List[int]:
+    """igs_horizon_plan over the program's tasks: indices of the tasks a
+    horizon follows (host computation, no device)."""
+    bufs = prog.buffers
+    sb = (StaticBuffer * max(1, len(bufs)))()
+    for i, b in enumerate(bufs):
+        sb[i].dims, sb[i].elem_size, sb[i].has_init = b.dims, b.elem_size, int(b.init is not None)
+        for d in range(3):
+            sb[i].extent[d] = b.extent[d]
+    tasks = prog.tasks
+    words = np.concatenate([t.flat() for t in tasks]) if tasks else np.zeros(TASK_WORDS, np.uint32)
+    out = np.zeros(max(1, len(tasks)), np.uint8)
+    flags = FLAG_HORIZON_CP if prog.horizon_cp else 0
+    r = lib().igs_horizon_plan(ctypes.cast(sb, ctypes.c_void_p), len(bufs), words.ctypes.data, len(tasks),
+                               prog.horizon_step, flags, out.ctypes.data)
+    if r != IGS_OK:
+        raise IgsError(r, "horizon_plan")
+    return [i for i in range(len(tasks)) if out[i]]
+
+
 def selftest_flow_wait(wait_ms: int) -> int:
     """Runs the dataflow executor's bounded-wait self-test (a graph in which
     nothing ever becomes ready); returns the status code (IGS_ERR_TIMEOUT
@@ -517,7 +540,7 @@ def lower_static(prog: W.Program, outs: Sequence[dict], stream: Optional[int] = 
         out[n].diags, out[n].diag_cap = o["diags"]
         out[n].counts = o["counts"]
     cfg = Config(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, None,
-                 FLAG_STAGE_D2D if prog.stage_d2d else 0)
+                 (FLAG_STAGE_D2D if prog.stage_d2d else 0) | (FLAG_HORIZON_CP if prog.horizon_cp else 0))
     return lib().igs_lower_static(ctypes.byref(cfg), sb, len(bufs), _p32(words), len(tasks), so, len(ops), out, stream)
 
 
@@ -561,6 +584,8 @@ class GpuImpl:
     def __init__(self, prog: W.Program, mode: int = MODE_PLAIN, **kw):
         if prog.stage_d2d:
             kw["flags"] = kw.get("flags", 0) | FLAG_STAGE_D2D
+        if prog.horizon_cp:
+            kw["flags"] = kw.get("flags", 0) | FLAG_HORIZON_CP
         self.ctx = Context(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead, mode=mode, **kw)
         self.nodes = prog.nodes
         self.prog = prog

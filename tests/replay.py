@@ -201,17 +201,32 @@ def _buf_bytes(b: W.Buffer):
     return np.zeros(shape, dtype=np.uint8)
 
 
+def horizon_after(prog: W.Program):
+    """Per task: whether a horizon follows it (every horizon_step tasks, or by
+    the task graph's critical path, the brute-force generator's per-element
+    bookkeeping deciding)."""
+    tasks = prog.tasks
+    if not prog.horizon_cp:
+        return [bool(prog.horizon_step) and (i + 1) % prog.horizon_step == 0 for i in range(len(tasks))]
+    from tests.brute_idag import Brute
+    b = Brute(1, 1, prog.horizon_step, 0)
+    for buf in prog.buffers:
+        b.create_buffer(buf.dims, buf.extent[:buf.dims], buf.elem_size, False)
+    return [bool(b._critical_path(t)) for t in tasks]
+
+
 def task_seqs(prog: W.Program):
     """Item sequence numbers: buffers, tasks, horizons, epochs, destroys each
     consume one; a lookahead change consumes none."""
-    out, seq, ntasks = [], 0, 0
+    out, seq, k = [], 0, 0
+    follow = horizon_after(prog)
     for op in prog.ops:
         if op[0] == "task":
             out.append(seq)
             seq += 1
-            ntasks += 1
-            if prog.horizon_step and ntasks % prog.horizon_step == 0:
+            if follow[k]:
                 seq += 1
+            k += 1
         elif op[0] in ("buffer", "flush", "destroy"):
             seq += 1
     return out

@@ -90,3 +90,12 @@ def test_random_split_2d(seed):
 def test_paper_shaped_split_2d(prog):
     stats = _run(prog)
     assert stats["kernels"] > 0 and stats["reads_checked"] > 0
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_horizon_cp(seed):
+    """Horizons by the critical path keep every read coherent and the result
+    sequential."""
+    p = W.random_program(500_000 + seed, max_extent=10, max_tasks=12)
+    p.horizon_cp = True
+    _run(p)

@@ -716,13 +716,13 @@ int igs_submit_task(igs_ctx* c, const igs_task* t, uint64_t* out_seq) {
   c->tasks.push_back(*t);
   const uint32_t s = c->seq;
   push_item(c, IT_TASK, 0, ti);
-  const bool cp_horizon = c->cpath.add(
-      *t, [c](uint32_t b) { return c->bufs[b].dims; }, [c](uint32_t b) { return c->bufs[b].extent; },
-      c->cfg.horizon_step);
+  const bool by_cp = (c->cfg.flags & IGS_FLAG_HORIZON_CP) != 0;
+  const bool cp_horizon =
+      by_cp && c->cpath.add(
+                   *t, [c](uint32_t b) { return c->bufs[b].dims; }, [c](uint32_t b) { return c->bufs[b].extent; },
+                   c->cfg.horizon_step);
   c->ntasks++;
-  const bool horizon = (c->cfg.flags & IGS_FLAG_HORIZON_CP)
-                           ? cp_horizon
-                           : (c->cfg.horizon_step && c->ntasks % c->cfg.horizon_step == 0);
+  const bool horizon = by_cp ? cp_horizon : (c->cfg.horizon_step && c->ntasks % c->cfg.horizon_step == 0);
   if (horizon) push_item(c, IT_HORIZON, 0, 0);
   if (out_seq) *out_seq = s;
   if (c->cfg.mode == IGS_MODE_PLAIN) return launch_lower(c);

@@ -139,9 +139,11 @@ extern "C" int igs_lower_static(const igs_config* cfg, const igs_static_buffer* 
               return IGS_ERR_INVALID_ARG;
         }
         items.push_back(Item{IT_TASK, seq++, 0, op.arg});
-        const bool cp_horizon = cpath.add(
-            t, [&](uint32_t b) { return bufs[b].dims; }, [&](uint32_t b) { return bufs[b].extent; },
-            cfg->horizon_step);
+        const bool cp_horizon =
+            (cfg->flags & IGS_FLAG_HORIZON_CP) &&
+            cpath.add(
+                t, [&](uint32_t b) { return bufs[b].dims; }, [&](uint32_t b) { return bufs[b].extent; },
+                cfg->horizon_step);
         ++ntask;
         if ((cfg->flags & IGS_FLAG_HORIZON_CP) ? cp_horizon : (cfg->horizon_step && ntask % cfg->horizon_step == 0))
           items.push_back(Item{IT_HORIZON, seq++, 0, 0});

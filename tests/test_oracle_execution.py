@@ -99,3 +99,12 @@ def test_random_horizon_cp(seed):
     p = W.random_program(500_000 + seed, max_extent=10, max_tasks=12)
     p.horizon_cp = True
     _run(p)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_all_variants_together(seed):
+    p = W.random_program(600_000 + seed, max_extent=9, max_tasks=12, split2d=True, max_devices=3,
+                         horizon_lookahead=True)
+    p.stage_d2d = True
+    p.horizon_cp = True
+    _run(p)

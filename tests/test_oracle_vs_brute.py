@@ -101,3 +101,14 @@ def test_random_programs_horizon_cp(seed):
     p = W.random_program(500_000 + seed, max_extent=10, max_tasks=12)
     p.horizon_cp = True
     _check(p)
+
+
+@pytest.mark.parametrize("seed", range(100))
+def test_random_programs_all_variants_together(seed):
+    """2D splits, staged device-to-device copies, critical-path horizons and
+    the horizon-count lookahead in one program: both generators agree."""
+    p = W.random_program(600_000 + seed, max_extent=9, max_tasks=12, split2d=True, max_devices=3,
+                         horizon_lookahead=True)
+    p.stage_d2d = True
+    p.horizon_cp = True
+    _check(p)

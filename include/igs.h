@@ -151,7 +151,11 @@ typedef struct igs_task {
   uint32_t dims;
   uint32_t range[3];
   uint32_t num_chunks;    /* >= 1; bits 16-31: chunks along dim 1 (a 2D split, see above) */
-  uint32_t kernel_id;     /* workload kernel run by execute (0 = none) */
+  uint32_t kernel_id;     /* workload kernel run by execute: 0 none, 1 Jacobi (read 0, write 1),
+                             2 wave (u_prev 0, u 1, u_next 2), 3 N-body step (positions 0, velocities 1),
+                             4 N-body update (velocities 0, positions 1), 5 growing rows, 6 generic
+                             integer (every accessor), 7 shifted read: accessor 1 at item := accessor 0
+                             at item + (int32) params[0..2] (for bounds-checking tests) */
   uint32_t num_accessors; /* 0..8 */
   uint32_t params[4];     /* workload kernel parameters */
   igs_accessor acc[IGS_MAX_ACCESSORS];
@@ -269,8 +273,10 @@ int igs_execute(igs_ctx* ctx, uint32_t flags);
  * copy segments, stencil tiles of 16 rows x 1024 columns, 1024-item workload tiles, 256
  * N-body bodies) and blocks take tiles of whichever nodes are ready, so
  * copies, kernels and transfers of different devices, nodes and tasks run
- * concurrently. Frees of the call run after the launch. Results are
- * identical. A launch in which no tile finishes for 2 s (a broken graph)
+ * concurrently. A split receive becomes one copy per incoming send, and
+ * each await receive completes once the sends meeting its region have landed
+ * (Sec. 3.4 "Inbound Transfers", receive arbitration). Frees of the call run
+ * after the launch. Results are identical. A launch in which no tile finishes for 2 s (a broken graph)
  * returns IGS_ERR_TIMEOUT. IGS_ERR_STATE during a pipelined run. */
 #define IGS_EXEC_LEVELS 0u
 #define IGS_EXEC_DATAFLOW 1u

@@ -1,5 +1,6 @@
 """Host-side checks of the C-ABI library that need no GPU: it builds, loads,
-and exports every entry point declared in include/igs.h."""
+and exports every entry point declared in include/igs.h; the binding's batch
+shape candidates and the host-only horizon plan behave."""
 import os
 import re
 import subprocess
@@ -44,3 +45,30 @@ def test_library_loads_without_gpu(libpath):
 def test_binding_exports_match_header():
     from paper_2503_10516_gb300 import igs
     assert set(igs.EXPORTS) == set(_declared())
+
+
+def test_batch_shape_candidates():
+    """The tuner's candidate shapes: one block per unit first, then work
+    queues of 1-8 blocks per SM (never more blocks than units, no repeats),
+    both orders, and multi-warp blocks with helped programs."""
+    from paper_2503_10516_gb300 import igs
+    for units, sms in ((4073, 152), (100, 152), (1, 152), (700, 16)):
+        c = igs.batch_shape_candidates(units, sms)
+        assert c[0] is None
+        rest = c[1:]
+        assert len(rest) == len(set(rest))
+        assert all(1 <= g <= units and order in (0, 1) and 1 <= warps <= 8 and helped >= 0
+                   for g, order, warps, helped in rest)
+        assert any(order == igs.ORDER_LONGEST_FIRST for _, order, _, _ in rest)
+        assert any(warps > 1 and helped > 0 for _, _, warps, helped in rest)
+
+
+def test_horizon_plan_rejects_unknown_buffers():
+    from paper_2503_10516_gb300 import igs
+    from paper_2503_10516_gb300 import workloads as W
+    b = W.Buffer(1, (8, 1, 1), 4, None)
+    p = W.Program("bad", 1, 1, 2, 0, [("buffer", b),
+                                      ("task", W.Task(1, (8, 1, 1), 1, W.K_GENERIC,
+                                                      [W.Accessor(3, W.WRITE, W.one_to_one())]))])
+    with pytest.raises(igs.IgsError):
+        igs.horizon_plan(p)

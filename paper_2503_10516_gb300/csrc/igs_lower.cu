@@ -37,6 +37,12 @@ struct Bx {
   uint32_t lo[3], hi[3];
 };
 
+// This thread's lane (a register read; the copy in Ctx would be a memory load).
+__device__ __forceinline__ uint32_t laneid() {
+  uint32_t l;
+  asm("mov.u32 %0, %%laneid;" : "=r"(l));
+  return l;
+}
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -153,6 +159,30 @@ __device__ __forceinline__ void t_put(const Table& t, uint32_t i, uint32_t key, 
 }
 __device__ __forceinline__ void t_kill(const Table& t, uint32_t i) { FLD(t, F_KEY, i) = DEAD; }
 
+// A whole entry, read with three independent 16-byte loads (one round trip
+// instead of a chain of dependent word loads).
+struct Ent {
+  uint32_t key;
+  Bx b;
+  uint32_t v0, v1, v2;
+};
+__device__ __forceinline__ Ent t_ent(const Table& t, uint32_t i) {
+  const uint4* e = reinterpret_cast<const uint4*>(t.base + (size_t)i * F_COUNT);
+  const uint4 a = e[0], b = e[1], c = e[2];
+  Ent r;
+  r.key = a.x;
+  r.b.lo[0] = a.y;
+  r.b.lo[1] = a.z;
+  r.b.lo[2] = a.w;
+  r.b.hi[0] = b.x;
+  r.b.hi[1] = b.y;
+  r.b.hi[2] = b.z;
+  r.v0 = b.w;
+  r.v1 = c.x;
+  r.v2 = c.y;
+  return r;
+}
+
 struct Acc {
   const Table* t;
   uint32_t from, to, alloc, mode;
@@ -232,7 +262,7 @@ enum Detail : int {
 #define DT_LAP(v, ph) pt_lap(v, c, ph)
 #define DT_COUNT(k, x)                          \
   do {                                          \
-    if (c.lane == 0) c.nd->prof[k] += (x);      \
+    if (laneid() == 0) c.nd->prof[k] += (x);      \
   } while (0)
 #else
 #define DT_START(v) \
@@ -261,7 +291,7 @@ __device__ __forceinline__ int heap_class(uint32_t entries) {
 __device__ bool heap_lock(Ctx& c) {
   if (!c.lock) return true;
   uint32_t ok = 1;
-  if (c.lane == 0) {
+  if (laneid() == 0) {
     uint32_t spins = 0;
     while (atomicCAS(c.lock, 0, 1) != 0) {
       if (++spins > (1u << 20)) {
@@ -279,7 +309,7 @@ __device__ bool heap_lock(Ctx& c) {
 __device__ void heap_unlock(Ctx& c) {
   if (!c.lock) return;
   __syncwarp();
-  if (c.lane == 0) {
+  if (laneid() == 0) {
     __threadfence_block();
     atomicExch(c.lock, 0);
   }
@@ -297,7 +327,7 @@ __device__ __noinline__ uint32_t heap_alloc(Ctx& c, uint32_t entries, uint32_t& 
   if (head != NONE) {
     const uint32_t next = reinterpret_cast<volatile uint32_t*>(nd->heap)[(size_t)head * F_COUNT];
     __syncwarp();
-    if (c.lane == 0) fh[k] = next;
+    if (laneid() == 0) fh[k] = next;
     heap_unlock(c);
     return head;
   }
@@ -310,7 +340,7 @@ __device__ __noinline__ uint32_t heap_alloc(Ctx& c, uint32_t entries, uint32_t& 
   }
   if (c.lock) {
     __syncwarp();
-    if (c.lane == 0) *vtop = top + cap;
+    if (laneid() == 0) *vtop = top + cap;
   } else {
     c.heap_top = top + cap;
   }
@@ -324,7 +354,7 @@ __device__ void heap_free(Ctx& c, uint32_t off, uint32_t cap) {
   if (!heap_lock(c)) return;
   volatile uint32_t* fh = nd->free_head;
   __syncwarp();
-  if (c.lane == 0) {
+  if (laneid() == 0) {
     reinterpret_cast<volatile uint32_t*>(nd->heap)[(size_t)off * F_COUNT] = fh[k];
     fh[k] = off;
   }
@@ -332,36 +362,51 @@ __device__ void heap_free(Ctx& c, uint32_t off, uint32_t cap) {
 }
 
 __device__ __forceinline__ void t_publish(Ctx& c, Table& t) {
-  if (t.dp && c.lane == 0) {
+  if (t.dp && laneid() == 0) {
     t.dp[2] = t.n;
     t.dp[3] = t.live;
   }
 }
 
-// Grows a heap table to hold `need` entries: the entries move to a bigger
-// slab at the same indices (a scan in progress stays valid through `t`).
-__device__ __noinline__ bool t_grow(Ctx& c, Table& t, uint32_t need) {
-  if (!t.dp) {
-    fail_cap(c, CAP_TABLE, t.cap);
-    return false;
+// Grows a heap table (descriptor dp, n entries used of cap at base) to hold
+// `need` entries: the entries move to a bigger slab at the same indices (a
+// scan in progress stays valid). Returns the new slab; base is null on failure.
+// Scalars in and out, so that callers keep their table header in registers.
+struct Slab {
+  uint32_t* base;
+  uint32_t cap;
+};
+__device__ __noinline__ Slab t_grow_to(Ctx& c, uint32_t* dp, const uint32_t* base, uint32_t n, uint32_t cap,
+                                       uint32_t need) {
+  Slab r{nullptr, cap};
+  if (!dp) {
+    fail_cap(c, CAP_TABLE, cap);
+    return r;
   }
-  uint32_t cap = 0;
-  const uint32_t off = heap_alloc(c, need > 2 * t.cap ? need : 2 * t.cap, cap);
-  if (off == NONE) return false;
+  uint32_t ncap = 0;
+  const uint32_t off = heap_alloc(c, need > 2 * cap ? need : 2 * cap, ncap);
+  if (off == NONE) return r;
   DT_COUNT(N_GROW, 1);
   uint4* dst = reinterpret_cast<uint4*>(c.nd->heap + (size_t)off * F_COUNT);
-  const uint4* src = reinterpret_cast<const uint4*>(t.base);
-  const uint32_t words4 = t.n * (F_COUNT / 4);
-  for (uint32_t i = c.lane; i < words4; i += 32) dst[i] = src[i];
+  const uint4* src = reinterpret_cast<const uint4*>(base);
+  const uint32_t words4 = n * (F_COUNT / 4);
+  for (uint32_t i = laneid(); i < words4; i += 32) dst[i] = src[i];
   __syncwarp();
-  heap_free(c, t.dp[0], t.cap);
-  if (c.lane == 0) {
-    t.dp[0] = off;
-    t.dp[1] = cap;
+  heap_free(c, dp[0], cap);
+  if (laneid() == 0) {
+    dp[0] = off;
+    dp[1] = ncap;
   }
   __syncwarp();
-  t.base = c.nd->heap + (size_t)off * F_COUNT;
-  t.cap = cap;
+  r.base = c.nd->heap + (size_t)off * F_COUNT;
+  r.cap = ncap;
+  return r;
+}
+__device__ __forceinline__ bool t_grow(Ctx& c, Table& t, uint32_t need) {
+  const Slab g = t_grow_to(c, t.dp, t.base, t.n, t.cap, need);
+  if (!g.base) return false;
+  t.base = g.base;
+  t.cap = g.cap;
   return true;
 }
 
@@ -377,13 +422,26 @@ __device__ __forceinline__ uint32_t t_claim(Ctx& c, Table& t, bool pred) {
   t_publish(c, t);
   return pred ? slot : NONE;
 }
+// Claims one slot per predicated lane (all lanes call); false (every lane)
+// when the table could not grow.
+__device__ __forceinline__ bool t_claim_ok(Ctx& c, Table& t, bool pred, uint32_t& slot) {
+  const uint32_t m = __ballot_sync(FULL, pred);
+  slot = t.n + __popc(m & lanemask_lt());
+  const uint32_t nn = t.n + __popc(m);
+  if (nn > t.cap && !t_grow(c, t, nn)) return false;
+  t.n = nn;
+  t.live += __popc(m);
+  c.map_writes += __popc(m);
+  t_publish(c, t);
+  return true;
+}
 // Claims k consecutive slots per lane; returns this lane's first slot.
 __device__ __forceinline__ uint32_t t_claim_n(Ctx& c, Table& t, uint32_t k) {
   uint32_t x = k;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t y = __shfl_up_sync(FULL, x, o);
-    if ((int)c.lane >= o) x += y;
+    if ((int)laneid() >= o) x += y;
   }
   const uint32_t total = __shfl_sync(FULL, x, 31);
   const uint32_t first = t.n + x - k;
@@ -409,7 +467,7 @@ __device__ __forceinline__ void t_dead(Ctx& c, Table& t, uint32_t k) {
 template <class P>
 __device__ __forceinline__ uint32_t warp_find_first(const Ctx& c, uint32_t n, P pred) {
   for (uint32_t base = 0; base < n; base += 32) {
-    const uint32_t i = base + c.lane;
+    const uint32_t i = base + laneid();
     const bool h = i < n && pred(i);
     const uint32_t m = __ballot_sync(FULL, h);
     if (m) return base + __ffs(m) - 1;
@@ -448,25 +506,30 @@ __device__ __forceinline__ Bx warp_bbox(Bx b, bool valid) {
 
 __device__ void pt_lap(PhaseTimer& p, Ctx& c, int ph) {
   const long long t1 = clock64();
-  if (c.lane == 0 && !c.helper) c.nd->prof[ph] += (uint64_t)(t1 - p.t0);
+  if (laneid() == 0 && !c.helper) c.nd->prof[ph] += (uint64_t)(t1 - p.t0);
   p.t0 = t1;
 }
 
-// Stable in-place removal of dead entries.
-__device__ __noinline__ void t_compact(Ctx& c, Table& t) {
+// Stable in-place removal of dead entries of n entries at base; returns the
+// number kept.
+__device__ __noinline__ uint32_t t_compact_n(Ctx& c, uint32_t* tbase, uint32_t n) {
   DT_START(dt);
+  Table t;
+  t.base = tbase;
+  t.n = n;
   uint32_t w = 0;
   for (uint32_t base = 0; base < t.n; base += 32) {
-    const uint32_t i = base + c.lane;
+    const uint32_t i = base + laneid();
     const bool in = i < t.n;
     uint32_t key = DEAD, v0 = 0, v1 = 0, v2 = 0;
     Bx b{};
     if (in) {
-      key = t_key(t, i);
-      b = t_box(t, i);
-      v0 = t_v(t, 0, i);
-      v1 = t_v(t, 1, i);
-      v2 = t_v(t, 2, i);
+      const Ent x = t_ent(t, i);
+      key = x.key;
+      b = x.b;
+      v0 = x.v0;
+      v1 = x.v1;
+      v2 = x.v2;
     }
     __syncwarp();
     const bool live = in && key != DEAD;
@@ -475,16 +538,22 @@ __device__ __noinline__ void t_compact(Ctx& c, Table& t) {
     w += __popc(m);
     __syncwarp();
   }
+  DT_LAP(dt, D_COMPACT);
+  return w;
+}
+__device__ __forceinline__ void t_compact(Ctx& c, Table& t) {
+  const uint32_t w = t_compact_n(c, t.base, t.n);
   t.n = w;
   t.live = w;
   t_publish(c, t);
   __syncwarp();
-  DT_LAP(dt, D_COMPACT);
 }
 
-// Compacts a table once its dead entries outnumber the live ones.
+// Compacts a table once dead entries make up a fifth of it (scans cost the
+// table's length, dead entries included; compaction keeps the entries' order).
 __device__ __forceinline__ void t_tidy(Ctx& c, Table& t) {
-  if (t.n > 2 * t.live + 32) {
+  const uint32_t dead = t.n - t.live;
+  if (dead > 4 && 4 * dead > t.live) {
     DT_COUNT(N_TIDY, 1);
     t_compact(c, t);
   }
@@ -495,7 +564,7 @@ __device__ Bx t_bbox(const Ctx& c, const Table& t, uint32_t from, uint32_t to) {
   acc.lo[0] = acc.lo[1] = acc.lo[2] = 0xFFFFFFFFu;
   acc.hi[0] = acc.hi[1] = acc.hi[2] = 0;
   for (uint32_t base = from; base < to; base += 32) {
-    const uint32_t i = base + c.lane;
+    const uint32_t i = base + laneid();
     const bool in = i < to && t_key(t, i) != DEAD;
     Bx b{};
     if (in) b = t_box(t, i);
@@ -508,58 +577,60 @@ __device__ Bx t_bbox(const Ctx& c, const Table& t, uint32_t from, uint32_t to) {
 // Appends (entry n q) with the entry's values for every entry of `key`
 // (NONE = any) that overlaps q and satisfies pred(values).
 template <class P>
-__device__ void t_query(Ctx& c, const Table& src, uint32_t key, const Bx& q, Table& out, P pred) {
+__device__ void t_query(Ctx& c, const Table& src, uint32_t key, const Bx& q, Table& out_ref, P pred) {
   DT_START(dt);
+  Table out = out_ref;  // header in registers while scanning
   const uint32_t n = src.n;
   c.map_reads += n;
   for (uint32_t base = 0; base < n; base += 32) {
-    const uint32_t i = base + c.lane;
+    const uint32_t i = base + laneid();
     bool hit = false;
     Bx is{};
     uint32_t v0 = 0, v1 = 0, v2 = 0;
     if (i < n) {
-      const uint32_t k = t_key(src, i);
-      if (k != DEAD && (key == NONE || k == key)) {
-        is = bx_isect(t_box(src, i), q);
+      const Ent e = t_ent(src, i);
+      if (e.key != DEAD && (key == NONE || e.key == key)) {
+        is = bx_isect(e.b, q);
         if (!bx_empty(is)) {
-          v0 = t_v(src, 0, i);
-          v1 = t_v(src, 1, i);
-          v2 = t_v(src, 2, i);
+          v0 = e.v0;
+          v1 = e.v1;
+          v2 = e.v2;
           hit = pred(v0, v1, v2);
         }
       }
     }
     if (!__any_sync(FULL, hit)) continue;
-    const uint32_t s = t_claim(c, out, hit);
-    if (c.err) return;
+    uint32_t s;
+    if (!t_claim_ok(c, out, hit, s)) break;
     if (hit) t_put(out, s, 0, is, v0, v1, v2);
   }
   __syncwarp();
+  out_ref = out;
   DT_LAP(dt, D_QUERY);
 }
 
 // Removes box r from every entry of `key` (NONE = any) that matches the
 // optional value filter; the remainders keep their values.
-__device__ __noinline__ void t_subtract(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t vfilter = NONE) {
+__device__ __forceinline__ void t_subtract(Ctx& c, Table& t_ref, uint32_t key, const Bx& r, uint32_t vfilter = NONE) {
   DT_START(dt);
   DT_COUNT(N_SUBTRACT, 1);
+  Table t = t_ref;  // header in registers while scanning
   t_tidy(c, t);
   const uint32_t n0 = t.n;
   for (uint32_t base = 0; base < n0; base += 32) {
-    const uint32_t i = base + c.lane;
+    const uint32_t i = base + laneid();
     bool hit = false;
     uint32_t k = DEAD, v0 = 0, v1 = 0, v2 = 0;
     Bx e{};
     if (i < n0) {
-      k = t_key(t, i);
+      const Ent x = t_ent(t, i);
+      k = x.key;
       if (k != DEAD && (key == NONE || k == key)) {
-        e = t_box(t, i);
-        v0 = t_v(t, 0, i);
+        e = x.b;
+        v0 = x.v0;
+        v1 = x.v1;
+        v2 = x.v2;
         hit = bx_overlap(e, r) && (vfilter == NONE || v0 == vfilter);
-        if (hit) {
-          v1 = t_v(t, 1, i);
-          v2 = t_v(t, 2, i);
-        }
       }
     }
     const uint32_t hits = __ballot_sync(FULL, hit);
@@ -569,31 +640,38 @@ __device__ __noinline__ void t_subtract(Ctx& c, Table& t, uint32_t key, const Bx
     if (hit) np = bx_minus(e, r, pc);
     t_dead(c, t, __popc(hits));
     const uint32_t first = t_claim_n(c, t, hit ? (uint32_t)np : 0u);
-    if (c.err) return;
+    if (first == NONE) break;  // the table could not grow (status set)
     if (hit) {
       t_kill(t, i);
       for (int j = 0; j < np; ++j) t_put(t, first + j, k, pc[j], v0, v1, v2);
     }
   }
   __syncwarp();
+  t_ref = t;
   DT_LAP(dt, D_SUBTRACT);
 }
 
-// value[vidx] |= bits on box r for entries of `key`.
-__device__ __noinline__ void t_or(Ctx& c, Table& t, uint32_t key, const Bx& r, int vidx, uint32_t bits) {
+// value[vidx] |= bits on box r for entries of `key` (the table's header in
+// and out by value).
+__device__ __noinline__ Table t_or_v(Ctx& c, Table t, uint32_t key, const Bx& r, int vidx, uint32_t bits) {
   t_tidy(c, t);
   const uint32_t n0 = t.n;
   for (uint32_t base = 0; base < n0; base += 32) {
-    const uint32_t i = base + c.lane;
+    const uint32_t i = base + laneid();
     bool hit = false;
     uint32_t v[3] = {0, 0, 0};
     Bx e{};
-    if (i < n0 && t_key(t, i) != DEAD && (key == NONE || t_key(t, i) == key)) {
-      e = t_box(t, i);
-      v[0] = t_v(t, 0, i);
-      v[1] = t_v(t, 1, i);
-      v[2] = t_v(t, 2, i);
-      hit = bx_overlap(e, r) && (v[vidx] & bits) != bits;
+    uint32_t k = DEAD;
+    if (i < n0) {
+      const Ent x = t_ent(t, i);
+      k = x.key;
+      if (k != DEAD && (key == NONE || k == key)) {
+        e = x.b;
+        v[0] = x.v0;
+        v[1] = x.v1;
+        v[2] = x.v2;
+        hit = bx_overlap(e, r) && (v[vidx] & bits) != bits;
+      }
     }
     const uint32_t hits = __ballot_sync(FULL, hit);
     if (!hits) continue;
@@ -602,9 +680,8 @@ __device__ __noinline__ void t_or(Ctx& c, Table& t, uint32_t key, const Bx& r, i
     if (hit) np = bx_minus(e, r, pc);
     t_dead(c, t, __popc(hits));
     const uint32_t first = t_claim_n(c, t, hit ? (uint32_t)np + 1 : 0u);
-    if (c.err) return;
+    if (first == NONE) break;  // the table could not grow (status set)
     if (hit) {
-      const uint32_t k = t_key(t, i);
       t_kill(t, i);
       for (int j = 0; j < np; ++j) t_put(t, first + j, k, pc[j], v[0], v[1], v[2]);
       v[vidx] |= bits;
@@ -612,38 +689,53 @@ __device__ __noinline__ void t_or(Ctx& c, Table& t, uint32_t key, const Bx& r, i
     }
   }
   __syncwarp();
+  return t;
+}
+__device__ __forceinline__ void t_or(Ctx& c, Table& t, uint32_t key, const Bx& r, int vidx, uint32_t bits) {
+  t = t_or_v(c, t, key, r, vidx, bits);
 }
 
 // Sets the values of box r for `key`.
-__device__ __noinline__ void t_set(Ctx& c, Table& t, uint32_t key, const Bx& r, uint32_t v0, uint32_t v1, uint32_t v2) {
+__device__ __forceinline__ void t_set(Ctx& c, Table& t_ref, uint32_t key, const Bx& r, uint32_t v0, uint32_t v1, uint32_t v2) {
+  Table t = t_ref;
   t_subtract(c, t, key, r);
-  const uint32_t s = t_claim(c, t, c.lane == 0);
-  if (c.err) return;
-  if (c.lane == 0) t_put(t, s, key == NONE ? 0u : key, r, v0, v1, v2);
+  uint32_t s;
+  if (!c.err && t_claim_ok(c, t, laneid() == 0, s) && laneid() == 0) t_put(t, s, key == NONE ? 0u : key, r, v0, v1, v2);
   __syncwarp();
+  t_ref = t;
 }
 
 // Merges entries from index `from` on with equal key and values into
 // adjacent entries whose union is a box (keeps the tables small).
-__device__ __noinline__ void t_merge_from(Ctx& c, Table& t, uint32_t from) {
+__device__ __noinline__ Table t_merge_from_v(Ctx& c, Table t, uint32_t from) {
   DT_START(dt);
   DT_COUNT(N_MERGE, 1);
   for (uint32_t i = from; i < t.n; ++i) {
     uint32_t cand = i;
     for (int guard = 0; guard < 4096; ++guard) {
       DT_COUNT(N_MERGE_PROBE, 1);
-      const uint32_t k = t_key(t, cand);
+      const Ent ce = t_ent(t, cand);
+      const uint32_t k = ce.key;
       if (k == DEAD) break;
-      const Bx e = t_box(t, cand);
-      const uint32_t v0 = t_v(t, 0, cand), v1 = t_v(t, 1, cand), v2 = t_v(t, 2, cand);
+      const Bx e = ce.b;
+      const uint32_t v0 = ce.v0, v1 = ce.v1, v2 = ce.v2;
+      Bx jb{};
       const uint32_t j = warp_find_first(c, t.n, [&](uint32_t x) {
-        return x != cand && t_key(t, x) == k && t_v(t, 0, x) == v0 && t_v(t, 1, x) == v1 && t_v(t, 2, x) == v2 &&
-               bx_mergeable(e, t_box(t, x));
+        const Ent f = t_ent(t, x);
+        const bool m = x != cand && f.key == k && f.v0 == v0 && f.v1 == v1 && f.v2 == v2 && bx_mergeable(e, f.b);
+        if (m) jb = f.b;
+        return m;
       });
       if (j == NONE) break;
-      const Bx u = bx_union(e, t_box(t, j));
+      const uint32_t src_lane = (j & 31u);
+      Bx jbb;
+      for (int d = 0; d < 3; ++d) {
+        jbb.lo[d] = __shfl_sync(FULL, jb.lo[d], src_lane);
+        jbb.hi[d] = __shfl_sync(FULL, jb.hi[d], src_lane);
+      }
+      const Bx u = bx_union(e, jbb);
       __syncwarp();
-      if (c.lane == 0) {
+      if (laneid() == 0) {
         t_put(t, j, k, u, v0, v1, v2);
         t_kill(t, cand);
       }
@@ -653,7 +745,9 @@ __device__ __noinline__ void t_merge_from(Ctx& c, Table& t, uint32_t from) {
     }
   }
   DT_LAP(dt, D_MERGE);
+  return t;
 }
+__device__ __forceinline__ void t_merge_from(Ctx& c, Table& t, uint32_t from) { t = t_merge_from_v(c, t, from); }
 
 // Live entries above which an allocation's writer / reader table is
 // re-merged after an access (tunable at compile time).
@@ -664,12 +758,12 @@ __device__ __noinline__ void t_merge_from(Ctx& c, Table& t, uint32_t from) {
 // Re-merges a heap table once its live entries exceed max(floor, twice the
 // count after its previous re-merge): fragmentation stays bounded while the
 // quadratic merge runs a logarithmic number of times as a table grows.
-__device__ void t_set_mark(Ctx& c, Table& t) {
+__device__ __forceinline__ void t_set_mark(Ctx& c, Table& t) {
   __syncwarp();
-  if (t.dp && c.lane == 0) t.dp[4] = t.live;
+  if (t.dp && laneid() == 0) t.dp[4] = t.live;
   __syncwarp();
 }
-__device__ void t_maybe_merge(Ctx& c, Table& t, uint32_t floor) {
+__device__ __forceinline__ void t_maybe_merge(Ctx& c, Table& t, uint32_t floor) {
   const uint32_t mark = t.dp ? t.dp[4] : 0;
   if (t.live <= floor || t.live <= 2 * mark) return;
   t_merge_from(c, t, 0);
@@ -678,7 +772,7 @@ __device__ void t_maybe_merge(Ctx& c, Table& t, uint32_t floor) {
 
 // Makes the live entries with value v0 == val (NONE = all) of each key
 // pairwise disjoint by subtracting earlier entries from later ones.
-__device__ __noinline__ void t_make_disjoint(Ctx& c, Table& t, uint32_t val = NONE) {
+__device__ __noinline__ Table t_make_disjoint_v(Ctx& c, Table t, uint32_t val) {
   for (uint32_t i = 0; i < t.n; ++i) {
     const uint32_t k = t_key(t, i);
     if (k == DEAD) continue;
@@ -686,7 +780,7 @@ __device__ __noinline__ void t_make_disjoint(Ctx& c, Table& t, uint32_t val = NO
     const Bx e = t_box(t, i);
     const uint32_t n0 = t.n;
     for (uint32_t base = i + 1; base < n0; base += 32) {
-      const uint32_t j = base + c.lane;
+      const uint32_t j = base + laneid();
       bool hit = false;
       Bx f{};
       uint32_t w0 = 0, w1 = 0, w2 = 0;
@@ -706,7 +800,7 @@ __device__ __noinline__ void t_make_disjoint(Ctx& c, Table& t, uint32_t val = NO
       if (hit) np = bx_minus(f, e, pc);
       t_dead(c, t, __popc(hits));
       const uint32_t first = t_claim_n(c, t, hit ? (uint32_t)np : 0u);
-      if (c.err) return;
+      if (first == NONE) return t;  // the table could not grow (status set)
       if (hit) {
         t_kill(t, j);
         for (int q = 0; q < np; ++q) t_put(t, first + q, k, pc[q], w0, w1, w2);
@@ -714,7 +808,9 @@ __device__ __noinline__ void t_make_disjoint(Ctx& c, Table& t, uint32_t val = NO
     }
     __syncwarp();
   }
+  return t;
 }
+__device__ __forceinline__ void t_make_disjoint(Ctx& c, Table& t, uint32_t val = NONE) { t = t_make_disjoint_v(c, t, val); }
 
 // Canonical form (row-major maximal decomposition) of the live boxes of
 // in[from, to), which must be pairwise disjoint; appended to `out` sorted by
@@ -733,7 +829,7 @@ __device__ __noinline__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_
   Table& W = c.s[S_CAN];
   t_reset(W);
   for (uint32_t base = from; base < to; base += 32) {
-    const uint32_t i = base + c.lane;
+    const uint32_t i = base + laneid();
     bool live = false;
     Bx b{};
     if (i < to && t_key(in, i) != DEAD) {
@@ -750,7 +846,7 @@ __device__ __noinline__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_
   if (W.n > 1) {
     uint64_t vol = 0;
     for (uint32_t base = 0; base < W.n; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       uint64_t v = i < W.n ? bx_volume(t_box(W, i)) : 0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -759,7 +855,7 @@ __device__ __noinline__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_
     const Bx bb = t_bbox(c, W, 0, W.n);
     if (vol == bx_volume(bb)) {
       __syncwarp();
-      if (c.lane == 0) t_put(W, 0, 0, bb, 0, 0, 0);
+      if (laneid() == 0) t_put(W, 0, 0, bb, 0, 0, 0);
       W.n = 1;
       W.live = 1;
       __syncwarp();
@@ -785,7 +881,7 @@ __device__ __noinline__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_
         uint64_t split = ~0ull;
         bool any_succ = false;
         for (uint32_t base = 0; base < n; base += 32) {
-          const uint32_t i = base + c.lane;
+          const uint32_t i = base + laneid();
           uint32_t succ = NONE;
           uint64_t sp = ~0ull;
           if (i < n) {
@@ -820,7 +916,7 @@ __device__ __noinline__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_
         if (any_succ) {
           // mark boxes that have a predecessor; each chain head absorbs its chain
           for (uint32_t base = 0; base < n; base += 32) {
-            const uint32_t i = base + c.lane;
+            const uint32_t i = base + laneid();
             if (i < n) {
               const uint32_t sc = t_v(W, 0, i);
               if (sc != NONE) FLD(W, F_V + 1, sc) = 1;
@@ -828,7 +924,7 @@ __device__ __noinline__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_
           }
           __syncwarp();
           for (uint32_t base = 0; base < n; base += 32) {
-            const uint32_t i = base + c.lane;
+            const uint32_t i = base + laneid();
             if (i < n && t_v(W, 0, i) != NONE && t_v(W, 1, i) == 0) {
               uint32_t cur = i, hi = 0;
               while (t_v(W, 0, cur) != NONE) {
@@ -854,9 +950,9 @@ __device__ __noinline__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_
         }
         Bx pa[6], pb[6];
         const int na = bx_minus(a, ia, pa), nb = bx_minus(b, ib, pb);
-        const uint32_t first = t_claim_n(c, W, c.lane == 0 ? (uint32_t)(na + nb + 2) : 0u);
+        const uint32_t first = t_claim_n(c, W, laneid() == 0 ? (uint32_t)(na + nb + 2) : 0u);
         if (c.err) return 0;
-        if (c.lane == 0) {
+        if (laneid() == 0) {
           t_kill(W, i);
           t_kill(W, j);
           uint32_t q = first;
@@ -877,7 +973,7 @@ __device__ __noinline__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_
     return 0;
   }
   for (uint32_t base = 0; base < n; base += 32) {
-    const uint32_t i = base + c.lane;
+    const uint32_t i = base + laneid();
     if (i < n) {
       const Bx b = t_box(W, i);
       uint32_t rank = 0;
@@ -926,7 +1022,7 @@ __device__ bool table_new(Ctx& c, uint32_t* d, uint32_t entries) {
   const uint32_t off = heap_alloc(c, entries, cap);
   if (off == NONE) return false;
   __syncwarp();
-  if (c.lane == 0) {
+  if (laneid() == 0) {
     d[0] = off;
     d[1] = cap;
     d[2] = 0;
@@ -940,7 +1036,7 @@ __device__ void table_free(Ctx& c, uint32_t* d) {
   __syncwarp();
   const uint32_t off = d[0], cap = d[1];
   if (cap) heap_free(c, off, cap);
-  if (c.lane == 0) d[1] = 0;
+  if (laneid() == 0) d[1] = 0;
   __syncwarp();
 }
 
@@ -953,7 +1049,7 @@ __device__ bool new_alloc(Ctx& c, uint32_t aid, uint32_t b, uint32_t m, const Bx
   c.n_free -= 1;
   const uint32_t slot = c.nd->free_slots[c.n_free];
   if (!table_new(c, c.nd->wr_d + kDesc * slot, 32) || !table_new(c, c.nd->rd_d + kDesc * slot, 32)) return false;
-  if (c.lane == 0) {
+  if (laneid() == 0) {
     AllocRec rec;
     rec.buffer = b;
     rec.mem = m;
@@ -979,7 +1075,7 @@ __device__ void drop_alloc(Ctx& c, uint32_t aid) {
   table_free(c, c.nd->wr_d + kDesc * slot);
   table_free(c, c.nd->rd_d + kDesc * slot);
   __syncwarp();
-  if (c.lane == 0) {
+  if (laneid() == 0) {
     c.nd->allocs[aid].live = 0;
     c.nd->free_slots[c.n_free] = slot;
     uint32_t* L = c.nd->live;
@@ -1050,7 +1146,7 @@ __device__ __noinline__ void task_chunks(Ctx& c, const igs_task& t, Table& CH) {
     const uint64_t Cy = t.num_chunks & 0xFFFFu, N = c.N, D = c.D, E0 = t.range[0], E1 = t.range[1];
     const uint32_t total = (uint32_t)(Cy * Cx);
     for (uint32_t base = 0; base < total; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       bool ok = false;
       Bx b{};
       uint32_t node = 0, mem = 0;
@@ -1078,7 +1174,7 @@ __device__ __noinline__ void task_chunks(Ctx& c, const igs_task& t, Table& CH) {
   }
   const uint64_t E0 = t.range[0], C = t.num_chunks, M = (uint64_t)c.N * c.D;
   for (uint32_t base = 0; base < t.num_chunks; base += 32) {
-    const uint32_t i = base + c.lane;
+    const uint32_t i = base + laneid();
     bool ok = false;
     Bx b{};
     uint32_t node = 0, mem = 0;
@@ -1143,7 +1239,7 @@ __device__ __noinline__ void task_mapped(Ctx& c, const igs_task& t, const Table&
     return;
   }
   for (uint32_t base = 0; base < total; base += 32) {
-    const uint32_t i = base + c.lane;
+    const uint32_t i = base + laneid();
     if (i < total) {
       const uint32_t slot = i / na, a = i % na;
       const Bx b = map_box(t.acc[a], t_box(CH, slot), buf_of(c, t.acc[a].buffer));
@@ -1177,7 +1273,7 @@ __device__ __noinline__ bool overlapping_writes(Ctx& c, const igs_task& t, const
         const Bx bx = t_box(MP, x * na + a);
         if (bx_empty(bx)) continue;
         for (uint32_t base = 0; base < CH.n; base += 32) {
-          const uint32_t y = base + c.lane;
+          const uint32_t y = base + laneid();
           bool bad = false;
           if (y < CH.n && y != x && (a != b || y > x)) bad = bx_overlap(bx, t_box(MP, y * na + b));
           if (__ballot_sync(FULL, bad)) return true;
@@ -1213,109 +1309,76 @@ __device__ uint32_t emit(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint3
 // WAW anti; a fresh allocation's own alloc instruction: allocation
 // lifetime) and, for writes, the readers since the last write (WAR anti); no
 // predecessor at all means an edge to the last epoch.
-__device__ __noinline__ bool emit_deps(Ctx& c, const Acc* acc, int nacc, bool keep_dep) {
+__device__ __forceinline__ bool emit_deps(Ctx& c, const Acc* acc, int nacc, bool keep_dep) {
   if (c.err) return false;
   NodeDev* nd = c.nd;
-  Table& D = c.s[S_DEP];
+  Table D = c.s[S_DEP];  // header in registers; written back below
   if (!keep_dep) t_reset(D);
-  // one probe per (access, region box, table): last writers for every access,
-  // readers for writes; every probed entry is tested in a lane-parallel pass.
-  // Probes are gathered 32 at a time, probe j in lane j's registers (table
-  // base, first entry index of the batch, region box, kind); a lane finds
-  // the probe of its entry with shuffles instead of loads.
-  {
-    uint32_t np = 0, total = 0;
-    const uint32_t* my_base = nullptr;
-    uint32_t my_start = 0xFFFFFFFFu, my_tab = 0, my_mode = 0;
-    Bx my_q{};
-    auto run_batch = [&]() -> bool {
-      c.map_reads += total;
-      DT_COUNT(N_PROBE_ENTRIES, total);
-      const unsigned long long my_b = (unsigned long long)(uintptr_t)my_base;
-      for (uint32_t base = 0; base < total; base += 32) {
-        const uint32_t f = base + c.lane;
-        // probe of entry f: the last probe starting at or before f
-        uint32_t p = 0;
-        for (uint32_t q = 1; q < np; ++q)
-          if (__shfl_sync(FULL, my_start, q) <= f) p = q;
-        const uint32_t start = __shfl_sync(FULL, my_start, p), tab = __shfl_sync(FULL, my_tab, p),
-                       mode = __shfl_sync(FULL, my_mode, p);
-        const uint32_t* tb = reinterpret_cast<const uint32_t*>((uintptr_t)__shfl_sync(FULL, my_b, p));
-        Bx q;
-        for (int d = 0; d < 3; ++d) {
-          q.lo[d] = __shfl_sync(FULL, my_q.lo[d], p);
-          q.hi[d] = __shfl_sync(FULL, my_q.hi[d], p);
-        }
+  // One pass per (access, table): each lane tests one entry against every
+  // box of the access region (broadcast loads) and records one dependency
+  // per overlapping entry (its kind depends on the entry and the access
+  // mode only; duplicates are merged when the edges are emitted).
+  for (int k = 0; k < nacc; ++k) {
+    const Acc& A = acc[k];
+    const uint32_t slot = nd->allocs[A.alloc].slot;
+    const int ntab = (A.mode & IGS_WRITE) ? 2 : 1;
+    for (int tab = 0; tab < ntab; ++tab) {
+      const uint32_t* dsc = (tab == 0 ? nd->wr_d : nd->rd_d) + kDesc * slot;
+      const uint32_t n = dsc[2];
+      if (n == 0) continue;
+      const uint32_t* tb = nd->heap + (size_t)dsc[0] * F_COUNT;
+      c.map_reads += n;
+      DT_COUNT(N_PROBE_ENTRIES, n);
+      for (uint32_t base = 0; base < n; base += 32) {
+        const uint32_t f = base + laneid();
         bool hit = false;
         uint32_t w = 0, kind = 0;
-        if (f < total) {
-          const uint4* e = reinterpret_cast<const uint4*>(tb + (size_t)(f - start) * F_COUNT);
+        if (f < n) {
+          const uint4* e = reinterpret_cast<const uint4*>(tb + (size_t)f * F_COUNT);
           const uint4 e0 = e[0], e1 = e[1], e2 = e[2];
-          Bx eb;
-          eb.lo[0] = e0.y;
-          eb.lo[1] = e0.z;
-          eb.lo[2] = e0.w;
-          eb.hi[0] = e1.x;
-          eb.hi[1] = e1.y;
-          eb.hi[2] = e1.z;
-          if (e0.x != DEAD && bx_overlap(eb, q)) {
-            hit = true;
-            w = e1.w;  // v0
-            if (tab == 1) kind = IGS_DEP_ANTI;
-            else if (e2.x == 1) kind = IGS_DEP_ALLOC;  // v1: an allocation writer
-            else kind = ((mode & IGS_READ) ? IGS_DEP_DATAFLOW : 0u) | ((mode & IGS_WRITE) ? IGS_DEP_ANTI : 0u);
+          if (e0.x != DEAD) {
+            Bx eb;
+            eb.lo[0] = e0.y;
+            eb.lo[1] = e0.z;
+            eb.lo[2] = e0.w;
+            eb.hi[0] = e1.x;
+            eb.hi[1] = e1.y;
+            eb.hi[2] = e1.z;
+            for (uint32_t r = A.from; r < A.to && !hit; ++r) {
+              const Ent q = t_ent(*A.t, r);
+              hit = q.key != DEAD && bx_overlap(eb, q.b);
+            }
+            if (hit) {
+              w = e1.w;  // v0
+              if (tab == 1) kind = IGS_DEP_ANTI;
+              else if (e2.x == 1) kind = IGS_DEP_ALLOC;  // v1: an allocation writer
+              else kind = ((A.mode & IGS_READ) ? IGS_DEP_DATAFLOW : 0u) | ((A.mode & IGS_WRITE) ? IGS_DEP_ANTI : 0u);
+            }
           }
         }
         if (!__any_sync(FULL, hit)) continue;
-        const uint32_t s = t_claim(c, D, hit);
-        if (c.err) return false;
+        uint32_t s;
+        if (!t_claim_ok(c, D, hit, s)) {
+          c.s[S_DEP] = D;
+          return false;
+        }
         if (hit) {
           FLD(D, F_V, s) = w;
           FLD(D, F_V + 1, s) = kind;
         }
       }
-      np = 0;
-      total = 0;
-      return true;
-    };
-    for (int k = 0; k < nacc; ++k) {
-      const Acc& A = acc[k];
-      const uint32_t slot = nd->allocs[A.alloc].slot;
-      const uint32_t* wd = nd->wr_d + kDesc * slot;
-      const uint32_t* rdd = nd->rd_d + kDesc * slot;
-      const uint32_t wn = wd[2], rn = rdd[2];
-      const uint32_t* wb = nd->heap + (size_t)wd[0] * F_COUNT;
-      const uint32_t* rb = nd->heap + (size_t)rdd[0] * F_COUNT;
-      for (uint32_t r = A.from; r < A.to; ++r) {
-        if (t_key(*A.t, r) == DEAD) continue;
-        const Bx q = t_box(*A.t, r);
-        for (int tab = 0; tab < ((A.mode & IGS_WRITE) ? 2 : 1); ++tab) {
-          const uint32_t n = tab == 0 ? wn : rn;
-          if (n == 0) continue;
-          if (np == 32 && !run_batch()) return false;
-          if (c.lane == np) {
-            my_base = tab == 0 ? wb : rb;
-            my_start = total;
-            my_tab = (uint32_t)tab;
-            my_mode = A.mode;
-            my_q = q;
-          }
-          np += 1;
-          total += n;
-        }
-      }
     }
-    if (np && !run_batch()) return false;
   }
   __syncwarp();
   if (D.n == 0) {
-    if (c.lane == 0) {
+    if (laneid() == 0) {
       FLD(D, F_V, 0) = c.epoch;
       FLD(D, F_V + 1, 0) = IGS_DEP_EPOCH;
     }
     D.n = 1;
     __syncwarp();
   }
+  c.s[S_DEP] = D;
   return true;
 }
 
@@ -1323,7 +1386,7 @@ __device__ __noinline__ bool emit_deps(Ctx& c, const Acc* acc, int nacc, bool ke
 // instruction id, written to out[0, count) (at most cap of them, else a
 // capacity failure of kind cap_kind); marks each predecessor as having a
 // successor. Returns the count (NONE on failure).
-__device__ __noinline__ uint32_t emit_edges(Ctx& c, uint32_t id, igs_edge* out, uint32_t cap, CapKind cap_kind,
+__device__ __forceinline__ uint32_t emit_edges(Ctx& c, uint32_t id, igs_edge* out, uint32_t cap, CapKind cap_kind,
                                             uint32_t cap_report) {
   if (c.err) return NONE;
   NodeDev* nd = c.nd;
@@ -1332,50 +1395,39 @@ __device__ __noinline__ uint32_t emit_edges(Ctx& c, uint32_t id, igs_edge* out, 
   const uint32_t nd0 = D.n;
   uint32_t n_unique = 0;
   if (nd0 <= 32) {
-    // one entry per lane: group equal predecessors, then a bitonic sort of
-    // the group leaders by predecessor id
-    const bool in = c.lane < nd0;
-    const uint32_t p = in ? FLD(D, F_V, c.lane) : 0xFFFFFFFFu;
-    const uint32_t k = in ? FLD(D, F_V + 1, c.lane) : 0u;
-    bool lead = in;
-    uint32_t kind = 0;
-    for (int j = 0; j < 32; ++j) {
+    // one entry per lane: the first lane of each group of equal predecessors
+    // leads it; a leader's kind ORs its group's kinds and its rank counts the
+    // leaders with smaller ids (one pass over the entries)
+    const bool in = laneid() < nd0;
+    const uint32_t p = in ? FLD(D, F_V, laneid()) : 0xFFFFFFFFu;
+    const uint32_t k = in ? FLD(D, F_V + 1, laneid()) : 0u;
+    const uint32_t grp = __match_any_sync(FULL, p);
+    const bool lead = in && (uint32_t)(__ffs(grp) - 1) == laneid();
+    const uint32_t leaders = __ballot_sync(FULL, lead);
+    uint32_t kind = 0, rank = 0;
+    for (uint32_t j = 0; j < nd0; ++j) {
       const uint32_t pj = __shfl_sync(FULL, p, j), kj = __shfl_sync(FULL, k, j);
-      if (pj == p) {
-        kind |= kj;
-        if (j < (int)c.lane) lead = false;
-      }
+      if (pj == p) kind |= kj;
+      else if (((leaders >> j) & 1u) && pj < p) ++rank;
     }
-    uint64_t key = lead ? (((uint64_t)p << 32) | kind) : ~0ull;
-#pragma unroll
-    for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        const uint64_t other = __shfl_xor_sync(FULL, key, stride);
-        const bool up = ((c.lane & size) == 0);
-        const bool lower = (c.lane & stride) == 0;
-        const bool take_min = (lower == up);
-        key = take_min ? (other < key ? other : key) : (other < key ? key : other);
-      }
-    }
-    n_unique = __popc(__ballot_sync(FULL, lead));
+    n_unique = __popc(leaders);
     if (n_unique > cap) {
       fail_cap(c, cap_kind, cap_report);
       return NONE;
     }
-    if (c.lane < n_unique) {
+    if (lead) {
       igs_edge e;
-      e.from = (uint32_t)(key >> 32);
+      e.from = p;
       e.to = id;
-      e.kind = (uint32_t)key;
-      out[c.lane] = e;
-      if (!(e.from & PROV)) nd->has_succ[e.from] = 1;
+      e.kind = kind;
+      out[rank] = e;
+      if (!(p & PROV)) nd->has_succ[p] = 1;
     }
   } else {
     // pass 1: mark each entry that is the first of its predecessor id (the
     // mark lives in the entry's third value word)
     for (uint32_t base = 0; base < nd0; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       bool first = false;
       if (i < nd0) {
         const uint32_t p = FLD(D, F_V, i);
@@ -1397,7 +1449,7 @@ __device__ __noinline__ uint32_t emit_edges(Ctx& c, uint32_t id, igs_edge* out, 
     // pass 2: a first entry's rank is the number of first entries with a
     // smaller id; its kind ORs the kinds of every entry with its id
     for (uint32_t base = 0; base < nd0; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       if (i < nd0) {
         const uint32_t p = FLD(D, F_V, i);
         const bool first = FLD(D, F_V + 2, i) != 0;
@@ -1426,7 +1478,7 @@ __device__ __noinline__ uint32_t emit_edges(Ctx& c, uint32_t id, igs_edge* out, 
 // The record of instruction c.n_instr with its boxes (bt[bfrom, bto)) and
 // bindings (bindt[bind_from, +bind_n)). clear_succ: mark it as having no
 // successor yet (callers that emitted its successors' edges already pass false).
-__device__ __noinline__ bool emit_record(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint32_t fb, uint32_t fc,
+__device__ __forceinline__ bool emit_record(Ctx& c, uint32_t type, uint32_t seq, uint32_t fa, uint32_t fb, uint32_t fc,
                                          uint32_t fd, const Table* bt, uint32_t bfrom, uint32_t bto, const Table* bindt,
                                          uint32_t bind_from, uint32_t bind_n, bool clear_succ) {
   if (c.err) return false;
@@ -1440,7 +1492,7 @@ __device__ __noinline__ bool emit_record(Ctx& c, uint32_t type, uint32_t seq, ui
   uint32_t nb = 0;
   if (bt) {
     for (uint32_t base = bfrom; base < bto; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       const bool live = i < bto && t_key(*bt, i) != DEAD;
       const uint32_t m = __ballot_sync(FULL, live);
       if (c.n_box + nb + __popc(m) > nd->cap_box) {
@@ -1463,8 +1515,8 @@ __device__ __noinline__ bool emit_record(Ctx& c, uint32_t type, uint32_t seq, ui
     fail_cap(c, CAP_BIND, nd->cap_bind);
     return false;
   }
-  if (bindt && c.lane < bind_n) {
-    const uint32_t i = bind_from + c.lane;
+  if (bindt && laneid() < bind_n) {
+    const uint32_t i = bind_from + laneid();
     const Bx b = t_box(*bindt, i);
     igs_binding o;
     o.alloc = t_v(*bindt, 0, i);
@@ -1472,9 +1524,9 @@ __device__ __noinline__ bool emit_record(Ctx& c, uint32_t type, uint32_t seq, ui
       o.lo[d] = b.lo[d];
       o.hi[d] = b.hi[d];
     }
-    nd->binds[c.n_bind + c.lane] = o;
+    nd->binds[c.n_bind + laneid()] = o;
   }
-  if (c.lane == 0) {
+  if (laneid() == 0) {
     igs_instruction r;
     r.id = id;
     r.type = type;
@@ -1499,7 +1551,7 @@ __device__ __noinline__ bool emit_record(Ctx& c, uint32_t type, uint32_t seq, ui
 
 // Applies an instruction's accesses to the per-allocation tables: reads
 // join the readers, writes replace the writers and clear the readers.
-__device__ __noinline__ bool emit_apply(Ctx& c, const Acc* acc, int nacc, uint32_t id) {
+__device__ __forceinline__ bool emit_apply(Ctx& c, const Acc* acc, int nacc, uint32_t id) {
   if (c.err) return false;
   // apply reads, then writes
   for (int k = 0; k < nacc; ++k) {
@@ -1515,9 +1567,9 @@ __device__ __noinline__ bool emit_apply(Ctx& c, const Acc* acc, int nacc, uint32
       if (t_key(*A.t, r) == DEAD) continue;
       const Bx q = t_box(*A.t, r);
       if (again) t_subtract(c, RD, NONE, q, id);
-      const uint32_t s = t_claim(c, RD, c.lane == 0);
+      const uint32_t s = t_claim(c, RD, laneid() == 0);
       if (c.err) return false;
-      if (c.lane == 0) t_put(RD, s, 0, q, id, 0, 0);
+      if (laneid() == 0) t_put(RD, s, 0, q, id, 0, 0);
       __syncwarp();
     }
     // re-merge only a table that has grown: keeps hot paths short and bounds
@@ -1565,7 +1617,7 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
     uint32_t nb = 0;
     if (bt) {
       for (uint32_t base = bfrom; base < bto; base += 32) {
-        const uint32_t i = base + c.lane;
+        const uint32_t i = base + laneid();
         const bool live = i < bto && t_key(*bt, i) != DEAD;
         const uint32_t m = __ballot_sync(FULL, live);
         if (st.n_box + nb + __popc(m) > st.cap_box) {
@@ -1584,7 +1636,7 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
         nb += __popc(m);
       }
     }
-    if (c.lane == 0) {
+    if (laneid() == 0) {
       igs_instruction r;
       r.id = pid;
       r.type = type;
@@ -1628,7 +1680,7 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
 __device__ __noinline__ bool map_ids(Ctx& c, Table& T, uint32_t h, bool writers = false) {
   bool any = false;
   for (uint32_t base = 0; base < T.n; base += 32) {
-    const uint32_t i = base + c.lane;
+    const uint32_t i = base + laneid();
     bool ch = false;
     if (i < T.n && t_key(T, i) != DEAD) {
       const uint32_t v = t_v(T, 0, i);
@@ -1687,7 +1739,7 @@ __device__ __noinline__ void emit_free(Ctx& c, uint32_t seq, uint32_t aid) {
   for (int k = 0; k < 2; ++k) {
     const Table T = k == 0 ? wr_t(c, aid) : rd_t(c, aid);
     for (uint32_t base = 0; base < T.n; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       const bool hit = i < T.n && t_key(T, i) != DEAD;
       const uint32_t s = t_claim(c, D, hit);
       if (c.err) return;
@@ -1731,7 +1783,7 @@ __device__ __noinline__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_
   for (;;) {
     uint64_t best = ~0ull;
     for (uint32_t base = 0; base < Q.n; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       uint64_t k = ~0ull;
       if (i < Q.n) {
         k = ((uint64_t)t_v(Q, 0, i) << 32) | t_v(Q, 1, i);
@@ -1750,7 +1802,7 @@ __device__ __noinline__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_
     }
     t_reset(G);
     for (uint32_t base = 0; base < Q.n; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       const bool hit = i < Q.n && t_v(Q, 0, i) == prod && t_v(Q, 1, i) == pmem;
       const uint32_t s = t_claim(c, G, hit);
       if (c.err) return;
@@ -1763,7 +1815,7 @@ __device__ __noinline__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_
       t_reset(P);
       const Bx ab = alloc_box(a);
       for (uint32_t base = 0; base < G.n; base += 32) {
-        const uint32_t i = base + c.lane;
+        const uint32_t i = base + laneid();
         Bx is{};
         bool hit = false;
         if (i < G.n) {
@@ -1800,9 +1852,9 @@ __device__ __noinline__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_
           return false;
         }
         t_reset(P);  // P now holds the allocation's box
-        const uint32_t s0 = t_claim(c, P, c.lane == 0);
+        const uint32_t s0 = t_claim(c, P, laneid() == 0);
         if (c.err) return false;
-        if (c.lane == 0) t_put(P, s0, 0, bb, 0, 0, 0);
+        if (laneid() == 0) t_put(P, s0, 0, bb, 0, 0, 0);
         __syncwarp();
         const uint32_t hid = c.n_alloc;
         const uint32_t iid = emit(c, IGS_ALLOC, seq, hid, 1, b, NONE, &P, 0, 1, nullptr, 0, false);
@@ -1811,9 +1863,9 @@ __device__ __noinline__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_
         c.n_alloc += 1;
         {
           Table WR = wr_t(c, hid);
-          const uint32_t s1 = t_claim(c, WR, c.lane == 0);
+          const uint32_t s1 = t_claim(c, WR, laneid() == 0);
           if (c.err) return false;
-          if (c.lane == 0) t_put(WR, s1, 0, bb, iid, 1, 0);  // v1 = 1: the writer is an allocation
+          if (laneid() == 0) t_put(WR, s1, 0, bb, iid, 1, 0);  // v1 = 1: the writer is an allocation
           __syncwarp();
         }
         Acc in[2] = {{&CN, 0, CN.n, src, IGS_READ}, {&CN, 0, CN.n, hid, IGS_WRITE}};
@@ -1831,7 +1883,7 @@ __device__ __noinline__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_
       }
       // remember the copied region
       for (uint32_t base = 0; base < CN.n; base += 32) {
-        const uint32_t i = base + c.lane;
+        const uint32_t i = base + laneid();
         const bool in = i < CN.n;
         const uint32_t s = t_claim(c, CP, in);
         if (c.err) return false;
@@ -1841,7 +1893,7 @@ __device__ __noinline__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_
       return true;
     };
     for (uint32_t lb = 0; lb < c.n_live; lb += 32) {
-      const uint32_t li = lb + c.lane;
+      const uint32_t li = lb + laneid();
       uint32_t mine = NONE;
       if (li < c.n_live) {
         mine = c.nd->live[li];
@@ -1874,14 +1926,14 @@ __device__ __noinline__ void node_bboxes(Ctx& c, const Table& CH, Table& NB) {
     acc.hi[0] = acc.hi[1] = acc.hi[2] = 0;
     bool any = false;
     for (uint32_t base = 0; base < CH.n; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       const bool in = i < CH.n && t_v(CH, 0, i) == m;
       Bx b{};
       if (in) b = t_box(CH, i);
       acc = bx_union(acc, warp_bbox(b, in));
       any = any || __ballot_sync(FULL, in) != 0;
     }
-    if (c.lane == 0) t_put(NB, m, any ? 0u : DEAD, acc, 0, 0, 0);
+    if (laneid() == 0) t_put(NB, m, any ? 0u : DEAD, acc, 0, 0, 0);
   }
   NB.n = c.N;
   __syncwarp();
@@ -1961,7 +2013,7 @@ __device__ __forceinline__ Table scratch_table(uint32_t* base, uint32_t cap) {
 template <class F>
 __device__ bool run_shared(Ctx& c, BlockShared& sh, uint32_t cmd, F share0) {
   __syncwarp();
-  if (c.lane == 0) {
+  if (laneid() == 0) {
     c.nd->prof[31] += 1;  // shared phases run (profile counter)
     sh.err = ST_OK;
     sh.cmd = cmd;
@@ -2014,7 +2066,7 @@ __device__ __noinline__ void a3_buffer(Ctx& c, const igs_task& t, uint32_t seq, 
     t_make_disjoint(c, TMP);
     if (c.err) return;
     for (uint32_t base = 0; base < TMP.n; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       const bool live = i < TMP.n && t_key(TMP, i) != DEAD;
       const uint32_t s = t_claim(c, MISS, live);
       if (c.err) return;
@@ -2027,7 +2079,7 @@ __device__ __noinline__ void a3_buffer(Ctx& c, const igs_task& t, uint32_t seq, 
     Table& sel = TMP;
     t_reset(sel);
     for (uint32_t base = 0; base < MISS.n; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       const bool hit = i < MISS.n && t_v(MISS, 0, i) == c.node;
       const uint32_t s = t_claim(c, sel, hit);
       if (c.err) return;
@@ -2040,7 +2092,7 @@ __device__ __noinline__ void a3_buffer(Ctx& c, const igs_task& t, uint32_t seq, 
       if (c.err) return;
       const Bx bb = t_bbox(c, CN, 0, CN.n);
       for (uint32_t base = 0; base < CN.n + 1; base += 32) {
-        const uint32_t i = base + c.lane;
+        const uint32_t i = base + laneid();
         const bool in = i < CN.n + 1;
         const uint32_t s = t_claim(c, OUT, in);
         if (c.err) return;
@@ -2068,7 +2120,7 @@ __device__ __noinline__ void a3_buffer(Ctx& c, const igs_task& t, uint32_t seq, 
     if (c.err) return;
     const Bx bb = t_bbox(c, CN, 0, CN.n);
     for (uint32_t base = 0; base < CN.n + 1; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       const bool in = i < CN.n + 1;
       const uint32_t s = t_claim(c, OUT, in);
       if (c.err) return;
@@ -2114,7 +2166,7 @@ __device__ __noinline__ void a3_share(Ctx& c, WorkJob& j, uint32_t w, Table& OUT
     const uint32_t from = OUT.n;
     a3_buffer(c, *j.task, j.seq, j.CH, j.MP, j.NB, j.buf[i], OUT);
     __syncwarp();
-    if (c.lane == 0) {
+    if (laneid() == 0) {
       j.buf_off[i] = from;
       j.buf_cnt[i] = OUT.n - from;
     }
@@ -2143,7 +2195,7 @@ __device__ __noinline__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, co
     Table& OUT0 = c.s[S_T5];
     t_reset(OUT0);
     __syncwarp();
-    if (c.lane == 0) {
+    if (laneid() == 0) {
       j.nd = c.nd;
       j.pg = c.pg;
       j.task = &t;
@@ -2162,11 +2214,11 @@ __device__ __noinline__ void a3_task(Ctx& c, const igs_task& t, uint32_t seq, co
     for (uint32_t i = 0; i < nbuf; ++i) {
       const uint32_t w = i % c.workers, off = j.buf_off[i], cnt = j.buf_cnt[i];
       const uint32_t* src = w == 0 ? OUT0.base : helper_table(c.nd, w, 5);
-      const uint32_t first = __shfl_sync(FULL, t_claim_n(c, c.qr, c.lane == 0 ? cnt : 0u), 0);  // lane 0's slot
+      const uint32_t first = __shfl_sync(FULL, t_claim_n(c, c.qr, laneid() == 0 ? cnt : 0u), 0);  // lane 0's slot
       if (c.err) return;
       const uint4* s4 = reinterpret_cast<const uint4*>(src + (size_t)off * F_COUNT);
       uint4* d4 = reinterpret_cast<uint4*>(c.qr.base + (size_t)first * F_COUNT);
-      for (uint32_t k = c.lane; k < cnt * (F_COUNT / 4); k += 32) d4[k] = s4[k];
+      for (uint32_t k = laneid(); k < cnt * (F_COUNT / 4); k += 32) d4[k] = s4[k];
       __syncwarp();
     }
     return;
@@ -2196,7 +2248,7 @@ __device__ __noinline__ void requirements(Ctx& c, const igs_task& t, uint32_t se
                              uint32_t only_key, uint32_t own_flag) {
   const uint32_t na = t.num_accessors, total = CH.n * na;
   for (uint32_t base = 0; base < total; base += 32) {
-    const uint32_t i = base + c.lane;
+    const uint32_t i = base + laneid();
     bool hit = false;
     Bx x{};
     uint32_t key = 0;
@@ -2215,7 +2267,7 @@ __device__ __noinline__ void requirements(Ctx& c, const igs_task& t, uint32_t se
   uint32_t qs, qe;
   qr_block(c, seq, qs, qe);
   for (uint32_t base = qs; base < qe; base += 32) {
-    const uint32_t i = base + c.lane;
+    const uint32_t i = base + laneid();
     bool hit = false;
     uint32_t key = 0;
     if (i < qe) {
@@ -2236,7 +2288,7 @@ __device__ __noinline__ bool allocating(Ctx& c, const igs_task& t, uint32_t seq,
   requirements(c, t, seq, CH, MP, RQ, NONE, 1);
   if (c.err) return false;
   for (uint32_t base = 0; base < RQ.n; base += 32) {
-    const uint32_t i = base + c.lane;
+    const uint32_t i = base + laneid();
     bool need = false;
     if (i < RQ.n) {
       const uint32_t key = t_key(RQ, i);
@@ -2262,7 +2314,7 @@ __device__ __noinline__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq
   for (;;) {
     uint64_t best = ~0ull;
     for (uint32_t base = 0; base < RQ.n; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       uint64_t k = ~0ull;
       if (i < RQ.n) {
         const uint32_t key = t_key(RQ, i);
@@ -2278,7 +2330,7 @@ __device__ __noinline__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq
     const uint32_t b = key >> 5, m = key & 31u;
     t_reset(CL);
     for (uint32_t base = 0; base < RQ.n; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       bool hit = false;
       Bx x{};
       if (i < RQ.n && t_key(RQ, i) == key) {
@@ -2304,12 +2356,12 @@ __device__ __noinline__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq
       if (c.err) return;
       // drop the ones already inside an allocation
       for (uint32_t base = from; base < CL.n; base += 32) {
-        const uint32_t i = base + c.lane;
+        const uint32_t i = base + laneid();
         if (i < CL.n && covered_by_alloc(c, b, m, t_box(CL, i))) t_kill(CL, i);
       }
       __syncwarp();
       for (uint32_t base = from; base < CL.n; base += 32) {
-        const uint32_t i = base + c.lane;
+        const uint32_t i = base + laneid();
         if (i < CL.n && t_key(CL, i) != DEAD) FLD(CL, F_KEY, i) = 0;
       }
       __syncwarp();
@@ -2320,7 +2372,7 @@ __device__ __noinline__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq
     AllocRec* A = c.nd->allocs;
     const uint32_t* L = c.nd->live;
     for (uint32_t base = 0; base < c.n_live; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       if (i < c.n_live) A[L[i]].mark = NONE;
     }
     __syncwarp();
@@ -2333,7 +2385,7 @@ __device__ __noinline__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq
       const uint64_t pairs = (uint64_t)n * n;
       uint32_t found = NONE;
       for (uint64_t base = 0; base < pairs; base += 32) {
-        const uint64_t p = base + c.lane;
+        const uint64_t p = base + laneid();
         bool h = false;
         if (p < pairs) {
           const uint32_t i = (uint32_t)(p / n), j = (uint32_t)(p % n);
@@ -2350,12 +2402,12 @@ __device__ __noinline__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq
         const Bx u = bx_union(t_box(CL, i), t_box(CL, j));
         const uint32_t own = t_v(CL, 0, i) | t_v(CL, 0, j);
         __syncwarp();
-        if (c.lane == 0) {
+        if (laneid() == 0) {
           t_put(CL, i, 0, u, own, 0, 0);
           t_kill(CL, j);
         }
         for (uint32_t base = 0; base < c.n_live; base += 32) {
-          const uint32_t x = base + c.lane;
+          const uint32_t x = base + laneid();
           if (x < c.n_live && A[L[x]].mark == j) A[L[x]].mark = i;
         }
         __syncwarp();
@@ -2366,7 +2418,7 @@ __device__ __noinline__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq
       const uint64_t cp = (uint64_t)n * nl;
       found = NONE;
       for (uint64_t base = 0; base < cp; base += 32) {
-        const uint64_t p = base + c.lane;
+        const uint64_t p = base + laneid();
         bool h = false;
         if (p < cp) {
           const uint32_t i = (uint32_t)(p / nl), x = L[(uint32_t)(p % nl)];
@@ -2386,7 +2438,7 @@ __device__ __noinline__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq
         const Bx u = bx_union(t_box(CL, i), alloc_box(A[x]));
         const uint32_t own = t_v(CL, 0, i);
         __syncwarp();
-        if (c.lane == 0) {
+        if (laneid() == 0) {
           t_put(CL, i, 0, u, own, 0, 0);
           A[x].mark = i;
         }
@@ -2397,7 +2449,7 @@ __device__ __noinline__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq
     // box order; resize: copy the live part of every absorbed allocation, free it
     const uint32_t n = CL.n;
     for (uint32_t base = 0; base < n; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       if (i < n && t_key(CL, i) != DEAD && t_v(CL, 0, i) == 1) {
         const Bx bi = t_box(CL, i);
         uint32_t rank = 0;
@@ -2424,16 +2476,16 @@ __device__ __noinline__ void alloc_phase(Ctx& c, const igs_task& t, uint32_t seq
       c.n_alloc += 1;
       {
         Table WR = wr_t(c, aid);
-        const uint32_t s = t_claim(c, WR, c.lane == 0);
+        const uint32_t s = t_claim(c, WR, laneid() == 0);
         if (c.err) return;
-        if (c.lane == 0) t_put(WR, s, 0, bb, iid, 1, 0);  // v1 = 1: the writer is an allocation
+        if (laneid() == 0) t_put(WR, s, 0, bb, iid, 1, 0);  // v1 = 1: the writer is an allocation
         __syncwarp();
       }
       // the absorbed allocations, ascending (the live list changes as they are freed)
       Table& AB = c.s[S_T3];
       t_reset(AB);
       for (uint32_t base = 0; base < c.n_live; base += 32) {
-        const uint32_t x = base + c.lane;
+        const uint32_t x = base + laneid();
         const bool hit = x < c.n_live && L[x] != aid && A[L[x]].mark == ci;
         const uint32_t s = t_claim(c, AB, hit);
         if (c.err) return;
@@ -2481,7 +2533,7 @@ __device__ bool p5_accesses(Ctx& c, const igs_task& t, const Table& MP, const Ta
       fail_internal(c, 4);
       return false;
     }
-    if (c.lane == 0) {
+    if (laneid() == 0) {
       Bx z{};
       t_put(BT, a, 0, bx_empty(x) ? z : x, al, 0, 0);
     }
@@ -2506,7 +2558,7 @@ __device__ __noinline__ void p5_share(Ctx& c, const WorkJob& j, uint32_t w) {
     if ((mem - 2) % j.workers != w) continue;
     const uint32_t kid = FLD(AL, F_V, slot * na);
     __syncwarp();
-    if (c.lane == 0) c.nd->has_succ[kid] = 0;  // before a later kernel of this worker marks it
+    if (laneid() == 0) c.nd->has_succ[kid] = 0;  // before a later kernel of this worker marks it
     Acc acc[IGS_MAX_ACCESSORS];
     int nacc = 0;
     if (!p5_accesses(c, *j.task, MP, AL, slot, na, BT, acc, nacc)) break;
@@ -2514,7 +2566,7 @@ __device__ __noinline__ void p5_share(Ctx& c, const WorkJob& j, uint32_t w) {
     const uint32_t ne = emit_edges(c, kid, stage + off, j.stage_cap - off, CAP_TABLE, j.stage_cap);
     if (ne == NONE) break;
     __syncwarp();
-    if (c.lane == 0) {
+    if (laneid() == 0) {
       FLD(AL, F_V + 1, slot * na) = off;
       FLD(AL, F_V + 2, slot * na) = ne;
     }
@@ -2539,7 +2591,7 @@ __device__ bool p4_consumer(Ctx& c, const igs_task& t, uint32_t seq, const Table
       fail_cap(c, CAP_DIAG, c.nd->cap_diag);
       return false;
     }
-    if (c.lane == 0) {
+    if (laneid() == 0) {
       igs_diag dg;
       dg.seq = seq;
       dg.chunk = t_key(CH, slot);
@@ -2557,9 +2609,9 @@ __device__ bool p4_consumer(Ctx& c, const igs_task& t, uint32_t seq, const Table
   }
   Table& RG = c.s[S_RG];
   t_reset(RG);
-  const uint32_t s = t_claim(c, RG, c.lane == 0);
+  const uint32_t s = t_claim(c, RG, laneid() == 0);
   if (c.err) return false;
-  if (c.lane == 0) t_put(RG, s, 0, x, 0, 0, 0);
+  if (laneid() == 0) t_put(RG, s, 0, x, 0, 0, 0);
   __syncwarp();
   coherence(c, seq, b, mem, dst, RG, 0, 1);
   return c.err == ST_OK;
@@ -2603,7 +2655,7 @@ __device__ __noinline__ void p4_share(Ctx& c, WorkJob& j, uint32_t w) {
     const uint32_t first = st.n_instr;
     if (!p4_consumer(c, t, j.seq, j.CH, PC, k, j.na, false)) break;
     __syncwarp();
-    if (c.lane == 0) {
+    if (laneid() == 0) {
       FLD(PC, F_V + 1, k) = first;
       FLD(PC, F_V + 2, k) = st.n_instr - first;
     }
@@ -2626,7 +2678,7 @@ __device__ __noinline__ void p4_final_ids(Ctx& c, const WorkJob& j, uint32_t w) 
     for (int k = 0; k < 2; ++k) {
       const Table T = k == 0 ? wr_t(c, aid) : rd_t(c, aid);
       for (uint32_t base = 0; base < T.n; base += 32) {
-        const uint32_t i = base + c.lane;
+        const uint32_t i = base + laneid();
         if (i < T.n && t_key(T, i) != DEAD) {
           const uint32_t v = t_v(T, 0, i);
           if (v & PROV) FLD(T, F_V, i) = map[v & 0xFFFFFFu];
@@ -2654,7 +2706,7 @@ __device__ __noinline__ void p4_parallel(Ctx& c, const igs_task& t, uint32_t seq
     bufs[nbuf++] = b;
   }
   __syncwarp();
-  if (c.lane == 0) {
+  if (laneid() == 0) {
     j.nd = c.nd;
     j.pg = c.pg;
     j.task = &t;
@@ -2680,7 +2732,7 @@ __device__ __noinline__ void p4_parallel(Ctx& c, const igs_task& t, uint32_t seq
         fail_cap(c, CAP_DIAG, nd->cap_diag);
         return;
       }
-      if (c.lane == 0) {
+      if (laneid() == 0) {
         igs_diag dg;
         dg.seq = seq;
         dg.chunk = t_key(CH, slot);
@@ -2707,20 +2759,20 @@ __device__ __noinline__ void p4_parallel(Ctx& c, const igs_task& t, uint32_t seq
         return;
       }
       __syncwarp();
-      if (c.lane == 0) {
+      if (laneid() == 0) {
         st.map[q] = id;
         nd->has_succ[id] = 0;
       }
       __syncwarp();
-      for (uint32_t e = c.lane; e < r.bind_cnt; e += 32) {
+      for (uint32_t e = laneid(); e < r.bind_cnt; e += 32) {
         igs_edge ed = st.edges[r.bind_off + e];
         if (ed.from & PROV) ed.from = st.map[ed.from & 0xFFFFFFu];  // an earlier copy of this worker
         ed.to = id;
         nd->edges[c.n_edge + e] = ed;
         nd->has_succ[ed.from] = 1;
       }
-      for (uint32_t e = c.lane; e < r.box_cnt; e += 32) nd->boxes[c.n_box + e] = st.boxes[r.box_off + e];
-      if (c.lane == 0) {
+      for (uint32_t e = laneid(); e < r.box_cnt; e += 32) nd->boxes[c.n_box + e] = st.boxes[r.box_off + e];
+      if (laneid() == 0) {
         igs_instruction o = r;
         o.id = id;
         o.box_off = c.n_box;
@@ -2771,7 +2823,7 @@ __device__ void helper_loop(BlockShared& sh, uint32_t w, uint32_t workers) {
         Table out = scratch_table(helper_table(j.nd, w, 5), j.nd->cap_scratch);
         a3_share(hc, j, w, out);
       }
-      if (hc.lane == 0) {
+      if (laneid() == 0) {
         atomicAdd(reinterpret_cast<unsigned long long*>(&j.nd->map_reads), (unsigned long long)hc.map_reads);
         atomicAdd(reinterpret_cast<unsigned long long*>(&j.nd->map_writes), (unsigned long long)hc.map_writes);
         if (hc.err != ST_OK) {
@@ -2792,11 +2844,11 @@ __device__ __noinline__ void p5_parallel(Ctx& c, const igs_task& t, uint32_t seq
   uint32_t next = c.n_instr;
   for (uint32_t slot = 0; slot < CH.n; ++slot) {
     if (t_v(CH, 0, slot) != c.node) continue;
-    if (c.lane == 0) FLD(AL, F_V, slot * na) = next;
+    if (laneid() == 0) FLD(AL, F_V, slot * na) = next;
     ++next;
   }
   __syncwarp();
-  if (c.lane == 0) {
+  if (laneid() == 0) {
     WorkJob& j = sh.job;
     j.nd = c.nd;
     j.pg = c.pg;
@@ -2828,7 +2880,7 @@ __device__ __noinline__ void p5_parallel(Ctx& c, const igs_task& t, uint32_t seq
       return;
     }
     const igs_edge* stage = stage_of(j, (mem - 2) % j.workers);
-    for (uint32_t i = c.lane; i < ne; i += 32) nd->edges[c.n_edge + i] = stage[off + i];
+    for (uint32_t i = laneid(); i < ne; i += 32) nd->edges[c.n_edge + i] = stage[off + i];
     c.n_edge += ne;
     Acc acc[IGS_MAX_ACCESSORS];
     int nacc = 0;
@@ -2881,7 +2933,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     // copy the push region into RG (coherence uses the scratch tables)
     t_reset(RG);
     for (uint32_t base = g0; base < g1; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       const bool in = i < g1;
       const uint32_t s = t_claim(c, RG, in);
       if (c.err) return;
@@ -2904,7 +2956,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     for (;;) {
       uint64_t best = ~0ull;
       for (uint32_t base = 0; base < Q.n; base += 32) {
-        const uint32_t i = base + c.lane;
+        const uint32_t i = base + laneid();
         uint64_t k = ~0ull;
         if (i < Q.n) {
           k = ((uint64_t)t_v(Q, 0, i) << 32) | t_v(Q, 1, i);
@@ -2918,7 +2970,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
       last = best;
       t_reset(G);
       for (uint32_t base = 0; base < Q.n; base += 32) {
-        const uint32_t i = base + c.lane;
+        const uint32_t i = base + laneid();
         const bool hit = i < Q.n && (((uint64_t)t_v(Q, 0, i) << 32) | t_v(Q, 1, i)) == best;
         const uint32_t s = t_claim(c, G, hit);
         if (c.err) return;
@@ -2959,7 +3011,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     t_reset(RG);
     uint64_t wvol = 0;
     for (uint32_t base = g0; base < g1; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       const bool in = i < g1;
       const uint32_t s = t_claim(c, RG, in);
       if (c.err) return;
@@ -2981,7 +3033,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
         uint64_t vol = 0;
         const uint32_t from = CONS.n;
         for (uint32_t base = 0; base < RG.n; base += 32) {
-          const uint32_t i = base + c.lane;
+          const uint32_t i = base + laneid();
           Bx is{};
           bool hit = false;
           if (i < RG.n) {
@@ -3021,7 +3073,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
         // part = consumer k's region minus what earlier await receives cover
         t_reset(G);
         for (uint32_t base = 0; base < CONS.n; base += 32) {
-          const uint32_t i = base + c.lane;
+          const uint32_t i = base + laneid();
           const bool hit = i < CONS.n && t_v(CONS, 0, i) == k;
           const uint32_t s = t_claim(c, G, hit);
           if (c.err) return;
@@ -3038,7 +3090,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
         if (CN.n == 0) continue;
         Table& D = c.s[S_DEP];
         t_reset(D);
-        if (c.lane == 0) {
+        if (laneid() == 0) {
           FLD(D, F_V, 0) = sid;
           FLD(D, F_V + 1, 0) = IGS_DEP_DATAFLOW;
         }
@@ -3060,7 +3112,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
         t_merge_from(c, WR, fw);
         t_merge_from(c, B, fb);
         for (uint32_t base = 0; base < CN.n; base += 32) {
-          const uint32_t i = base + c.lane;
+          const uint32_t i = base + laneid();
           const bool in = i < CN.n;
           const uint32_t s = t_claim(c, COV, in);
           if (c.err) return;
@@ -3082,7 +3134,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
   {
     const uint32_t total = CH.n * na;
     for (uint32_t base = 0; base < total; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       bool hit = false;
       uint32_t flags = 0;
       Bx x{};
@@ -3143,7 +3195,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     const AllocRec* A = c.nd->allocs;
     const uint32_t* L = c.nd->live;
     for (uint32_t base = 0; base < total; base += 32) {
-      const uint32_t i = base + c.lane;
+      const uint32_t i = base + laneid();
       if (i < total) {
         const uint32_t slot = i / na, a = i % na;
         uint32_t al = NONE;
@@ -3178,7 +3230,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
                                 nacc, false, &BT, 0, na);
       if (c.err) return;
       __syncwarp();
-      if (c.lane == 0) FLD(AL, F_V, slot * na) = kid;  // the chunk's kernel, for the buffer state below
+      if (laneid() == 0) FLD(AL, F_V, slot * na) = kid;  // the chunk's kernel, for the buffer state below
       __syncwarp();
     }
   }
@@ -3206,7 +3258,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
       const Bx U = map_box(t.acc[a], all, bd);
       if (!bx_empty(U)) t_subtract(c, B, NONE, U);
       for (uint32_t base = 0; base < CH.n; base += 32) {
-        const uint32_t slot = base + c.lane;
+        const uint32_t slot = base + laneid();
         bool hit = false;
         Bx x{};
         uint32_t kid = 0, mem = 0;
@@ -3224,9 +3276,9 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
         if (m == c.node || t_key(NB, m) == DEAD) continue;
         const Bx x = map_box(t.acc[a], t_box(NB, m), bd);
         if (bx_empty(x)) continue;
-        const uint32_t s = t_claim(c, B, c.lane == 0);
+        const uint32_t s = t_claim(c, B, laneid() == 0);
         if (c.err) return;
-        if (c.lane == 0) t_put(B, s, 0, x, REMOTE, 0, 0);
+        if (laneid() == 0) t_put(B, s, 0, x, REMOTE, 0, 0);
         __syncwarp();
       }
     } else {
@@ -3248,7 +3300,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
   }
   // the task's push / await regions are consumed
   for (uint32_t base = qs; base < qe; base += 32) {
-    const uint32_t i = base + c.lane;
+    const uint32_t i = base + laneid();
     if (i < qe) t_kill(c.qr, i);
   }
   t_dead(c, c.qr, qe - qs);
@@ -3275,16 +3327,16 @@ __device__ __noinline__ void process(Ctx& c, uint32_t item) {
         if (!new_alloc(c, aid, it.arg, 0, dom, 1)) return;
         c.n_alloc += 1;
         Table WR = wr_t(c, aid);
-        const uint32_t s = t_claim(c, WR, c.lane == 0);
+        const uint32_t s = t_claim(c, WR, laneid() == 0);
         if (c.err) return;
-        if (c.lane == 0) t_put(WR, s, 0, dom, c.epoch, 0, 0);
-        const uint32_t s2 = t_claim(c, B, c.lane == 0);
+        if (laneid() == 0) t_put(WR, s, 0, dom, c.epoch, 0, 0);
+        const uint32_t s2 = t_claim(c, B, laneid() == 0);
         if (c.err) return;
-        if (c.lane == 0) t_put(B, s2, 0, dom, c.epoch, 0, 1u);
+        if (laneid() == 0) t_put(B, s2, 0, dom, c.epoch, 0, 1u);
       } else {
-        const uint32_t s2 = t_claim(c, B, c.lane == 0);
+        const uint32_t s2 = t_claim(c, B, laneid() == 0);
         if (c.err) return;
-        if (c.lane == 0) t_put(B, s2, 0, dom, NONE, 0, 0);
+        if (laneid() == 0) t_put(B, s2, 0, dom, NONE, 0, 0);
       }
       __syncwarp();
       break;
@@ -3297,7 +3349,7 @@ __device__ __noinline__ void process(Ctx& c, uint32_t item) {
       Table& D = c.s[S_DEP];
       t_reset(D);
       for (uint32_t base = c.last_sync; base < c.n_instr; base += 32) {
-        const uint32_t i = base + c.lane;
+        const uint32_t i = base + laneid();
         const bool f = i < c.n_instr && !c.nd->has_succ[i];
         const uint32_t s = t_claim(c, D, f);
         if (c.err) return;
@@ -3328,7 +3380,7 @@ __device__ __noinline__ void process(Ctx& c, uint32_t item) {
       Table& AB = c.s[S_T3];
       t_reset(AB);
       for (uint32_t base = 0; base < c.n_live; base += 32) {
-        const uint32_t x = base + c.lane;
+        const uint32_t x = base + laneid();
         const bool hit = x < c.n_live && c.nd->allocs[c.nd->live[x]].buffer == b;
         const uint32_t s = t_claim(c, AB, hit);
         if (c.err) return;
@@ -3376,7 +3428,7 @@ __device__ void enqueue(Ctx& c, uint32_t item) {
     fail_cap(c, CAP_QUEUE, c.nd->cap_queue);
     return;
   }
-  if (c.lane == 0) c.nd->queue[(c.q_head + c.q_count) % c.nd->cap_queue] = item;
+  if (laneid() == 0) c.nd->queue[(c.q_head + c.q_count) % c.nd->cap_queue] = item;
   c.q_count += 1;
   __syncwarp();
 }
@@ -3406,7 +3458,7 @@ __device__ __noinline__ bool allocating_queued(Ctx& c, const igs_task& t, uint32
   requirements(c, t, seq, CH, MP, RQ, NONE, 1);
   if (c.err) return false;
   for (uint32_t base = 0; base < RQ.n; base += 32) {
-    const uint32_t i = base + c.lane;
+    const uint32_t i = base + laneid();
     bool need = false;
     if (i < RQ.n) {
       const uint32_t key = t_key(RQ, i);
@@ -3425,7 +3477,7 @@ __device__ __noinline__ void record_queued_reqs(Ctx& c, const igs_task& t, uint3
   t_reset(RQ);
   requirements(c, t, seq, CH, MP, RQ, NONE, 1);
   for (uint32_t base = 0; base < RQ.n && !c.err; base += 32) {
-    const uint32_t i = base + c.lane;
+    const uint32_t i = base + laneid();
     const bool in = i < RQ.n;
     const uint32_t s = t_claim(c, c.qr, in);
     if (c.err) return;
@@ -3457,9 +3509,9 @@ __device__ __noinline__ void deliver(Ctx& c, uint32_t item) {
     const BufDesc& bd = buf_of(c, it.arg);
     if (!table_new(c, c.nd->own_d + kDesc * it.arg, 32)) return;
     Table O = own_t(c, it.arg);
-    const uint32_t s = t_claim(c, O, c.lane == 0);
+    const uint32_t s = t_claim(c, O, laneid() == 0);
     if (c.err) return;
-    if (c.lane == 0) t_put(O, s, 0, buffer_box(bd), bd.init ? HOST : NONE, 0xFFFFFFFFu, 0);
+    if (laneid() == 0) t_put(O, s, 0, buffer_box(bd), bd.init ? HOST : NONE, 0xFFFFFFFFu, 0);
     __syncwarp();
   }
   bool alloc_now = false;
@@ -3476,7 +3528,7 @@ __device__ __noinline__ void deliver(Ctx& c, uint32_t item) {
     pt_lap(pt, c, PH_OVERLAP);
     if (bad) {
       if (c.n_rej < c.nd->cap_rej) {
-        if (c.lane == 0) c.nd->rejected[c.n_rej] = it.seq;
+        if (laneid() == 0) c.nd->rejected[c.n_rej] = it.seq;
         c.n_rej += 1;
         __syncwarp();
       }
@@ -3567,7 +3619,7 @@ __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg) {
 
 __device__ void store_ctx(Ctx& c, uint32_t cursor) {
   __syncwarp();
-  if (c.lane != 0) return;
+  if (laneid() != 0) return;
   NodeDev* nd = c.nd;
   nd->status = c.err;
   nd->err_info = c.err_info;
@@ -3602,7 +3654,7 @@ __device__ void store_ctx(Ctx& c, uint32_t cursor) {
 // is written (and fenced) before the counts.
 __device__ __noinline__ void publish_progress(const Ctx& c, volatile uint32_t* pr, uint32_t cursor) {
   __syncwarp();
-  if (c.lane == 0) {
+  if (laneid() == 0) {
     __threadfence_system();
     pr[PR_INSTR] = c.n_instr;
     pr[PR_EDGE] = c.n_edge;
@@ -3646,7 +3698,7 @@ __device__ void lower_unit(const Unit* units, uint32_t n_units, uint32_t max_ite
 // (kReserveThreads) park the others at the barrier: they hold most of the
 // SM's registers, so no block of another kernel (the executor's copies and
 // kernels running concurrently) shares the SM, its issue slots or its L1.
-constexpr uint32_t kReserveThreads = 640;
+constexpr uint32_t kReserveThreads = 512;
 __global__ void __launch_bounds__(kReserveThreads) lower_kernel(const Unit* units, uint32_t n_units, uint32_t max_items,
                                                                volatile uint32_t* progress) {
   __shared__ BlockShared sh;

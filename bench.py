@@ -33,6 +33,7 @@ METRIC = "instructions lowered/s"
 UNIT = "instructions/s"
 N, STEPS, NODES, DEVICES, CHUNKS, LOOKAHEAD, HSTEP = 8192, 1000, 4, 4, 64, 8, 4
 WINDOW = 16  # the executor takes new instructions once every node has lowered this many more submissions
+MAP_ENTRY_BYTES = 28.0  # algorithmic bytes of one region-map entry: six uint32 box coordinates + one uint32 value
 WORKLOAD = (f"wave2d: 3 x {N}x{N} fp32 buffers rotating, {NODES} nodes x {DEVICES} devices, {CHUNKS} row chunks, "
             f"{STEPS} time steps, lookahead {LOOKAHEAD}, horizon every {HSTEP} tasks")
 
@@ -150,8 +151,9 @@ def run_reference(args):
 
 
 def _stage_ctx(igs, prog, mode, stream):
+    flags = (igs.FLAG_HORIZON_CP if prog.horizon_cp else 0) | (igs.FLAG_STAGE_D2D if prog.stage_d2d else 0)
     c = igs.Context(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead, mode=mode, stream=stream,
-                    **igs.small_caps(prog))
+                    flags=flags, **igs.small_caps(prog))
     for op in prog.ops:
         if op[0] == "buffer":
             b = op[1]
@@ -159,149 +161,278 @@ def _stage_ctx(igs, prog, mode, stream):
     return c
 
 
-def measure_batched(igs, torch, stream, count=512, scale=0.01):
-    """Uneven programs (1-8 buffers of 2^10-2^24 elements, 1-128 chunks, 2-32
-    memories, lookahead 0-16; task counts scaled down): one launch over all
-    of them vs one task per launch. The batch shape is picked first by
-    timing every candidate on a fresh copy of the batch."""
-    progs = W.batch_programs(count=count, scale=scale, seed=0x5EED + 3)
-    res = {}
+def _submit_program(c, p):
+    for op in p.ops:
+        if op[0] == "task":
+            c.submit(op[1])
+        elif op[0] == "flush":
+            c.submit_epoch()
 
-    def staged():
-        ctxs = [_stage_ctx(igs, p, igs.MODE_BATCHED, stream) for p in progs]
-        for p, c in zip(progs, ctxs):
-            for op in p.ops:
-                if op[0] == "task":
-                    c.submit(op[1])
-                elif op[0] == "flush":
-                    c.submit_epoch()
-        return ctxs
+
+def _full_scale_caps(igs, small, full, stream, margin=2.0):
+    """Capacities for each full-scale program: its prefix at a small task
+    scale is lowered first (its tasks are the first tasks of the full
+    program); the largest per-node instruction, edge and box counts (binds
+    count half: two per instruction are provided) are extrapolated by the
+    task ratio, with a margin."""
+    ctxs = [_stage_ctx(igs, p, igs.MODE_BATCHED, stream) for p in small]
+    for p, c in zip(small, ctxs):
+        _submit_program(c, p)
+    igs.lower_batch(ctxs)
+    caps = []
+    for ps, pf, c in zip(small, full, ctxs):
+        k = len(pf.tasks) / max(1, len(ps.tasks))
+        mx = {"instrs": 0, "edges": 0, "boxes": 0}
+        for n in range(ps.nodes):
+            g = c.graph(n)
+            mx["instrs"] = max(mx["instrs"], len(g["instrs"]), (len(g["binds"]) + 1) // 2)
+            mx["edges"] = max(mx["edges"], len(g["edges"]))
+            mx["boxes"] = max(mx["boxes"], len(g["boxes"]))
+        caps.append(igs.small_caps(pf, {key: v * k * margin + 64 for key, v in mx.items()}))
+        c.close()
+    return caps
+
+
+def _doubled(cp):
+    """Capacities with the output arrays and scratch tables doubled."""
+    return dict(cp, max_instructions=2 * cp["max_instructions"], max_edges=2 * cp["max_edges"],
+                max_boxes=2 * cp["max_boxes"], scratch_capacity=2 * cp["scratch_capacity"])
+
+
+def measure_batched(igs, torch, stream, count=512, scale=1.0, tune_scale=0.02, subset_every=16):
+    """The 512 uneven programs of W.batch_programs (1-8 buffers of 2^10-2^24
+    elements, 1-128 chunks, 2-32 memories, lookahead 0-16, 10-2000 tasks) at
+    full task counts, lowered in one launch (igs_lower_batch_shaped). The
+    launch shape is tuned on the same programs at 2 % of their tasks (timing
+    every candidate on fresh copies). One task per launch (plain) is timed on
+    every 16th program, against one batched launch of the same programs."""
+    full = W.batch_programs(count=count, scale=scale, seed=0x5EED + 3)
+    caps = _full_scale_caps(igs, W.batch_programs(count=count, scale=0.01, seed=0x5EED + 3), full, stream)
+    res = {"programs": count, "task_scale": scale, "tasks": sum(len(p.tasks) for p in full),
+           "units": sum(p.nodes for p in full)}
 
     def timer():
         torch.cuda.synchronize()
         return time.perf_counter()
 
-    # the batch shape (one block per unit, or a work queue of persistent
-    # blocks in submission / longest-first order) is picked by timing
-    units = sum(p.nodes for p in progs)
+    tune_progs = W.batch_programs(count=count, scale=tune_scale, seed=0x5EED + 3)
+
+    def staged():
+        ctxs = [_stage_ctx(igs, p, igs.MODE_BATCHED, stream) for p in tune_progs]
+        for p, c in zip(tune_progs, ctxs):
+            _submit_program(c, p)
+        return ctxs
+
     t_tune = time.perf_counter()
-    cands = igs.batch_shape_candidates(units, torch.cuda.get_device_properties(0).multi_processor_count)
+    cands = igs.batch_shape_candidates(res["units"], torch.cuda.get_device_properties(0).multi_processor_count)
     shape, times = igs.tune_lower_batch(staged, cands, timer)
-    res["tuning"] = {"units": units, "seconds": time.perf_counter() - t_tune, "chosen": shape,
-                     "launch_seconds": [{"shape": s, "seconds": t} for s, t in times]}
-    for mode_name, mode in (("plain", igs.MODE_PLAIN), ("batched", igs.MODE_BATCHED)):
-        ctxs = [_stage_ctx(igs, p, mode, stream) for p in progs]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+    res["tuning"] = {"task_scale": tune_scale, "seconds": time.perf_counter() - t_tune, "chosen": shape,
+                     "launch_seconds": [{"shape": s_, "seconds": t_} for s_, t_ in times]}
+
+    def stage(progs, cps, mode):
+        ctxs = [igs.Context(p.nodes, p.devices, p.horizon_step, p.lookahead, mode=mode, stream=stream, **cp)
+                for p, cp in zip(progs, cps)]
         for p, c in zip(progs, ctxs):
             for op in p.ops:
-                if op[0] == "task":
-                    c.submit(op[1])
-                elif op[0] == "flush":
-                    c.submit_epoch()
-        if mode == igs.MODE_BATCHED:
-            igs.lower_batch(ctxs, shape)
-        else:
+                if op[0] == "buffer":
+                    b = op[1]
+                    c.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init)
+        return ctxs
+
+    def batched_run(progs, cps, shp, attempts=4):
+        """One launch over all programs; a context whose capacity estimate fell
+        short gets doubled output capacities and the launch is repeated (only
+        the launch that completes is timed)."""
+        for attempt in range(attempts):
+            ctxs = stage(progs, cps, igs.MODE_BATCHED)
+            for p, c in zip(progs, ctxs):
+                _submit_program(c, p)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            try:
+                igs.lower_batch(ctxs, shp)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+            except igs.IgsError:
+                short = []
+                for i, c in enumerate(ctxs):
+                    try:
+                        c.sync()
+                    except igs.IgsError:
+                        short.append(i)
+                for c in ctxs:
+                    c.close()
+                for i in short:
+                    cps[i] = _doubled(cps[i])
+                continue
+            instrs = sum(int(c.counters()["instructions"]) for c in ctxs)
+            launches = sum(int(c.counters()["launches"]) for c in ctxs)
             for c in ctxs:
+                c.close()
+            return {"instr_per_s": instrs / dt, "tasks_per_s": sum(len(p.tasks) for p in progs) / dt,
+                    "seconds": dt, "instructions": instrs, "launches": launches, "attempts": attempt + 1}
+        return {"error": f"capacity estimates still short after {attempts} attempts"}
+
+    res["batched_all"] = batched_run(full, caps, shape)
+    sub = list(range(0, count, subset_every))
+    sp, sc = [full[i] for i in sub], [caps[i] for i in sub]
+    res["subset"] = {"programs": len(sub), "tasks": sum(len(p.tasks) for p in sp),
+                     "batched": batched_run(sp, sc, shape)}
+    # one task per launch, each program after the other (a program whose
+    # capacities fall short is repeated with doubled ones; only the run that
+    # completes is timed)
+    dt, instrs, launches = 0.0, 0, 0
+    for i, p in enumerate(sp):
+        for _ in range(4):
+            c = stage([p], [sc[i]], igs.MODE_PLAIN)[0]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            try:
+                _submit_program(c, p)
                 c.sync()
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        instrs = sum(int(c.counters()["instructions"]) for c in ctxs)
-        launches = sum(int(c.counters()["launches"]) for c in ctxs)
-        res[mode_name] = {"instr_per_s": instrs / dt, "seconds": dt, "instructions": instrs, "launches": launches}
-        if mode == igs.MODE_BATCHED:
-            # the longest unit bounds the launch: the slowest program's mean
-            # per-node lowering time (SM cycles at the sampled clock)
-            cyc = max(c.profile()["total"] / p.nodes for p, c in zip(progs, ctxs))
-            res[mode_name]["slowest_program_node_cycles"] = cyc
-        for c in ctxs:
+            except igs.IgsError:
+                c.close()
+                sc[i] = _doubled(sc[i])
+                continue
+            torch.cuda.synchronize()
+            dt += time.perf_counter() - t0
+            instrs += int(c.counters()["instructions"])
+            launches += int(c.counters()["launches"])
             c.close()
-    res["programs"] = count
-    res["task_scale"] = scale
-    res["speedup"] = res["batched"]["instr_per_s"] / res["plain"]["instr_per_s"]
+            break
+    res["subset"]["plain"] = {"instr_per_s": instrs / dt, "seconds": dt, "instructions": instrs,
+                              "launches": launches}
+    res["subset"]["speedup"] = res["subset"]["batched"]["instr_per_s"] / res["subset"]["plain"]["instr_per_s"]
     return res
 
 
-def measure_served(igs, torch, stream, streams=64, rate=1e4, rows_max=2048, cols=1024, lookahead=0):
-    """Growing-row program streams (rows appended 1-64 at a time, each task
-    reading every earlier row) submitting with Poisson arrivals; per-task
-    latency = arrival -> every node of its program has lowered it; the
-    arrivals are replayed by the library's own host loop (igs_serve_replay),
-    so the rate is not limited by Python. Compared
-    with one task per launch under the same arrivals (the host submits a task
-    when it arrives or when the previous launch has returned, then waits for
-    its launch); the plain path's unloaded per-launch time is reported too."""
-    rng = np.random.default_rng(0x5EED + 5)
-    progs = [W.growing_program(rows_max=rows_max, cols=cols, grow=(1, 64), devices=2, chunks=2,
-                               lookahead=lookahead, seed=500 + i) for i in range(streams)]
+def _trace(progs, rate, seed):
+    """Poisson arrivals at `rate` over a seeded interleaving of the streams'
+    submissions (each stream keeps its order): [(stream, task or None, ns)]."""
+    rng = np.random.default_rng(seed)
     order = []
     for i, p in enumerate(progs):
         for op in p.ops:
             if op[0] in ("task", "flush"):
                 order.append(i)
     rng.shuffle(order)
-    gaps = rng.exponential(1.0 / rate, size=len(order))
     bodies = [[op for op in p.ops if op[0] in ("task", "flush")] for p in progs]
+    pos = [0] * len(progs)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=len(order))) * 1e9
+    trace = []
+    for k, i in enumerate(order):
+        op = bodies[i][pos[i]]
+        pos[i] += 1
+        trace.append((i, op[1] if op[0] == "task" else None, int(t[k])))
+    return trace
+
+
+def _lat_summary(lat_ns, wall_ns, instrs):
+    lat = np.sort(np.asarray(lat_ns, dtype=np.float64)) * 1e-6
+    n = len(lat)
+    return {"p50_ms": float(lat[n // 2]), "p99_ms": float(lat[min(n - 1, int(n * 0.99))]), "items": n,
+            "wall_s": wall_ns * 1e-9, "items_per_s": n / (wall_ns * 1e-9), "instructions": instrs,
+            "instr_per_s": instrs / (wall_ns * 1e-9)}
+
+
+def measure_served(igs, torch, stream, streams=64, budget=150e9, rates=(1e4, 1e5, 1e6),
+                   lookaheads=(("L0", 0), ("L8", 8), ("Linf", W.LOOKAHEAD_INFINITE))):
+    """Served lowering of 64 growing-row program streams (W.served_streams:
+    fp32 buffers of up to 2^27 elements, prefix growing 1-64 rows per task)
+    with Poisson arrivals at 1e4 / 1e5 / 1e6 tasks/s, lookahead 0, 8 and
+    unbounded. Streams are admitted under a 150 GB HBM budget
+    (igs_serve_enqueue) and detached when their last item is taken; latency =
+    arrival -> every node has taken the item. The comparator replays the
+    same arrivals with one lowering launch per item (igs_replay_plain), both
+    from the library's own host loop. A slot-limited run (16 slots for the 64
+    streams) shows continuous batching: streams wait for admission and are
+    admitted as others detach."""
+    out = {"workload": f"{streams} growing-row streams (1D / 2D fp32, up to 2^27 elements, +1-64 rows per task), "
+                       f"1 node x 2 devices, 2 chunks; {budget / 1e9:.0f} GB admission budget"}
+
+    def run_served(progs, trace, max_slots, hbm):
+        srv = igs.Server(max_slots=max_slots, hbm_budget_bytes=int(hbm))
+        ctxs = [_stage_ctx(igs, p, igs.MODE_PLAIN, None) for p in progs]
+        admitted = sum(1 for c, p in zip(ctxs, progs) if srv.enqueue(c, 4 * len(p.ops) + 16))
+        srv.start()
+        lat, wall = srv.replay(ctxs, trace, timeout_ms=300000, detach=True)
+        st = srv.stats()
+        srv.stop()
+        instrs = sum(int(c.counters()["instructions"]) for c in ctxs)
+        resizes = 0
+        for c in ctxs:  # resize copies: copies within one memory (d = 1)
+            g = c.graph(0)
+            resizes += int(((g["instrs"][:, 1] == 4) & (g["instrs"][:, 6] == 1)).sum())
+        for c in ctxs:
+            c.close()
+        srv.close()
+        res = _lat_summary(lat, wall, instrs)
+        res.update({"admitted_at_once": admitted, "admitted_after_detach": st["admitted_from_queue"],
+                    "peak_waiting": st["peak_waiting"], "slots": max_slots, "resize_copies": resizes})
+        return res
+
+    for lname, L in lookaheads:
+        progs = W.served_streams(count=streams, lookahead=L)
+        res = {"tasks": sum(len(p.tasks) for p in progs)}
+        for rate in rates:
+            trace = _trace(progs, rate, seed=0x5EED + 5)
+            r = {"served": run_served(progs, trace, max(64, 2 * streams), budget)}
+            if L == 0:
+                ctxs = [_stage_ctx(igs, p, igs.MODE_PLAIN, None) for p in progs]
+                lat, wall = igs.replay_plain(ctxs, trace, timeout_ms=600000)
+                instrs = sum(int(c.counters()["instructions"]) for c in ctxs)
+                for c in ctxs:
+                    c.close()
+                r["plain"] = _lat_summary(lat, wall, instrs)
+            res[f"{int(rate)}_per_s"] = r
+        out[lname] = res
+    # the paper's lookahead heuristic (compile two horizons after the last
+    # allocating task) with horizons every 4 tasks vs by the task graph's
+    # critical path (Sec. 3.5, Sec. 4.3), at 1e5 tasks/s
+    for lname, cp in (("Lhorizons_count_cadence", False), ("Lhorizons_critical_path", True)):
+        progs = W.served_streams(count=streams, lookahead=W.LOOKAHEAD_HORIZONS)
+        for p in progs:
+            p.horizon_cp = cp
+        out[lname] = {"tasks": sum(len(p.tasks) for p in progs),
+                      "100000_per_s": {"served": run_served(progs, _trace(progs, 1e5, seed=0x5EED + 5),
+                                                            max(64, 2 * streams), budget)}}
+    # continuous batching: fewer slots than streams
+    progs = W.served_streams(count=streams, lookahead=8)
+    out["continuous_batching_16_slots_1e5_per_s_L8"] = run_served(progs, _trace(progs, 1e5, seed=0x5EED + 5), 16,
+                                                                  budget)
+    return out
+
+
+def measure_resize_execution(igs, torch, stream):
+    """Resize copies of the growing-row pattern carried out by the box-copy
+    kernel: the largest served stream (16384 x 8192 fp32 = 2^27 elements,
+    rows appended 1-64 per task, 2 devices) lowered with lookahead 8 and
+    executed; and lookahead 0 on a quarter of the rows (2^25 elements; at
+    2^27 its resize copies would move ~260 GB). Copy GB/s = bytes read +
+    written by the executor's box-copy launches / their event time."""
     out = {}
-    # served
-    srv = igs.Server(max_slots=max(32, 2 * streams))
-    ctxs = [_stage_ctx(igs, p, igs.MODE_PLAIN, None) for p in progs]
-    for c, p in zip(ctxs, progs):
-        assert srv.attach(c, 4 * len(p.ops) + 16) == 0
-    srv.start()
-    # the library's own submission loop replays the arrivals (igs_serve_replay)
-    pos = [0] * streams
-    trace, t_ns = [], 0.0
-    for k, i in enumerate(order):
-        t_ns += gaps[k] * 1e9
-        op = bodies[i][pos[i]]
-        pos[i] += 1
-        trace.append((i, op[1] if op[0] == "task" else None, int(t_ns)))
-    lat_ns, wall_ns = srv.replay(ctxs, trace, timeout_ms=120000)
-    lat = list(np.asarray(lat_ns, dtype=np.float64) * 1e-9)
-    for c in ctxs:
-        srv.detach(c)
-    srv.stop()
-    instrs = sum(int(c.counters()["instructions"]) for c in ctxs)
-    for c in ctxs:
-        c.close()
-    srv.close()
-    lat.sort()
-    out["served"] = {"p50_ms": lat[len(lat) // 2] * 1e3, "p99_ms": lat[int(len(lat) * 0.99)] * 1e3,
-                     "tasks": len(lat), "instructions": instrs, "wall_s": wall_ns * 1e-9,
-                     "tasks_per_s": len(lat) / (wall_ns * 1e-9), "instr_per_s": instrs / (wall_ns * 1e-9)}
-    # one task per launch under the same arrivals: the host submits each task
-    # when it arrives (or when the previous launch has returned, if later) and
-    # waits for its launch; latency from arrival to completion
-    ctxs = [_stage_ctx(igs, p, igs.MODE_PLAIN, None) for p in progs]
-    pos = [0] * streams
-    lat, service = [], []
-    t_next = time.perf_counter()
-    for k, i in enumerate(order):
-        t_next += gaps[k]
-        while time.perf_counter() < t_next:
-            pass
-        op = bodies[i][pos[i]]
-        pos[i] += 1
+    for name, rows, L in (("L8_2^27", 16384, 8), ("L0_2^25", 4096, 0)):
+        p = W.growing_program(rows_max=rows, cols=8192, devices=2, chunks=2, lookahead=L,
+                              seed=int((0x5EED + 5) * 1000), grow=(1, 64))
+        c = _stage_ctx(igs, p, igs.MODE_BATCHED, stream)
+        c.set_timing(True)
+        for op in p.ops:
+            if op[0] == "task":
+                c.submit(op[1])
+        c.flush()
+        g = c.graph(0)
+        t = g["instrs"][:, 1]
+        resizes = int(((t == 4) & (g["instrs"][:, 6] == 1)).sum())
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        if op[0] == "task":
-            ctxs[i].submit(op[1])
-        else:
-            ctxs[i].submit_epoch()
-        ctxs[i].sync()
-        t1 = time.perf_counter()
-        lat.append(t1 - t_next)
-        service.append(t1 - t0)
-    for c in ctxs:
+        c.execute()
+        dt = time.perf_counter() - t0
+        st = c.stats()
         c.close()
-    lat.sort()
-    service.sort()
-    out["plain"] = {"p50_ms": lat[len(lat) // 2] * 1e3, "p99_ms": lat[int(len(lat) * 0.99)] * 1e3,
-                    "unloaded_p50_ms": service[len(service) // 2] * 1e3,
-                    "unloaded_p99_ms": service[int(len(service) * 0.99)] * 1e3}
-    out["streams"] = streams
-    out["rate_tasks_per_s"] = rate
-    out["workload"] = f"{streams} streams, growing {rows_max}x{cols} fp32 rows, 2 devices, lookahead {lookahead}"
+        gbs = st["copy_bytes"] / (st["copy_ms"] * 1e-3) / 1e9 if st["copy_ms"] else None
+        out[name] = {"tasks": len(p.tasks), "resize_copies": resizes, "copy_bytes": st["copy_bytes"],
+                     "copy_ms": st["copy_ms"], "copy_gbs": gbs, "copy_launches": st["copy_launches"],
+                     "execute_s": dt}
     return out
 
 
@@ -398,13 +529,14 @@ def measure_executors(igs, torch, stream, prog, make_ctx, wave_tasks=200, nbody_
     return out
 
 
-def measure_nbody_lowering(igs, torch, stream, tasks=100):
+def measure_nbody(igs, torch, stream, steps=200, exec_steps=2):
     """The all-pairs N-body configuration (2^20 float4 bodies, 8 nodes x 4
-    devices, 128 chunks, lookahead 4, two tasks per step): the first `tasks`
-    tasks lowered in one launch (device time by CUDA events), and the same
-    tasks one per launch (per-task latency)."""
+    devices, 128 chunks, lookahead 4, two tasks per step): all 400 tasks
+    lowered in one launch (device time by CUDA events) and one per launch
+    (per-task latency); then `exec_steps` steps (2 tasks each) lowered and
+    executed at full size (2^20 bodies: 2^40 body pairs per step)."""
     n = 1 << 20
-    p = W.nbody_program(n=n, steps=tasks // 2, nodes=8, devices=4, chunks=128, lookahead=4)
+    p = W.nbody_program(n=n, steps=steps, nodes=8, devices=4, chunks=128, lookahead=4)
     out = {}
     for name, mode in (("batched", igs.MODE_BATCHED), ("plain", igs.MODE_PLAIN)):
         c = igs.Context(p.nodes, p.devices, p.horizon_step, p.lookahead, mode=mode, stream=stream)
@@ -429,8 +561,150 @@ def measure_nbody_lowering(igs, torch, stream, tasks=100):
             out[name]["p50_task_ms"] = lat[len(lat) // 2]
             out[name]["p99_task_ms"] = lat[min(len(lat) - 1, int(len(lat) * 0.99))]
         c.close()
-    out["workload"] = f"nbody: 2 x {n} float4 bodies, 8 nodes x 4 devices, 128 chunks, lookahead 4, first {tasks} tasks"
+    # execution at full size
+    q = W.nbody_program(n=n, steps=exec_steps, nodes=8, devices=4, chunks=128, lookahead=4)
+    c = igs.Context(q.nodes, q.devices, q.horizon_step, q.lookahead, mode=igs.MODE_BATCHED, stream=stream)
+    c.set_timing(True)
+    for op in q.ops:
+        if op[0] == "buffer":
+            b = op[1]
+            c.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init)
+        elif op[0] == "task":
+            c.submit(op[1])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c.flush()
+    c.execute()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    st = c.stats()
+    pairs = float(n) * n * exec_steps
+    out["execute"] = {"steps": exec_steps, "tasks": len(q.tasks), "instructions": int(c.counters()["instructions"]),
+                      "seconds": dt, "workload_ms": st["workload_ms"], "copy_ms": st["copy_ms"],
+                      "copy_gbs": st["copy_bytes"] / (st["copy_ms"] * 1e-3) / 1e9 if st["copy_ms"] else None,
+                      "body_pairs_per_s": pairs / (st["workload_ms"] * 1e-3) if st["workload_ms"] else None}
+    c.close()
+    out["workload"] = (f"nbody: 2 x {n} float4 bodies, 8 nodes x 4 devices, 128 chunks, lookahead 4, "
+                       f"{2 * steps} tasks lowered; {exec_steps} steps executed at full size")
     return out
+
+
+def measure_jacobi(igs, torch, stream, reps=5):
+    """The Jacobi reference program (256 x 256 fp32, 2 nodes x 2 devices, 4
+    chunks, 8 steps, lookahead 0): lowered and executed through igs_run
+    (best of `reps`), and one task per launch (per-task latency)."""
+    p = W.jacobi_program(n=256, steps=8, nodes=2, devices=2, chunks=4, lookahead=0)
+    best = None
+    for _ in range(reps):
+        c = igs.Context(p.nodes, p.devices, p.horizon_step, p.lookahead, mode=igs.MODE_BATCHED, stream=stream)
+        for op in p.ops:
+            if op[0] == "buffer":
+                b = op[1]
+                c.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init)
+            elif op[0] == "task":
+                c.submit(op[1])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c.run(4)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        instrs = int(c.counters()["instructions"])
+        c.close()
+        best = dt if best is None or dt < best else best
+    c = igs.Context(p.nodes, p.devices, p.horizon_step, p.lookahead, mode=igs.MODE_PLAIN, stream=stream)
+    c.set_timing(True)
+    for op in p.ops:
+        if op[0] == "buffer":
+            b = op[1]
+            c.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init)
+    lat = []
+    for t in p.tasks:
+        c.submit(t)
+        lat.append(c.stats()["last_lower_ms"])
+    c.close()
+    lat.sort()
+    return {"workload": "jacobi 256x256 fp32, 2 nodes x 2 devices, 4 chunks, 8 steps, lookahead 0",
+            "lower_and_execute_s": best, "instructions": instrs, "instr_per_s": instrs / best,
+            "plain_p50_task_ms": lat[len(lat) // 2], "plain_p99_task_ms": lat[-1]}
+
+
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_program_worker(prog):
+    """Pool worker: lowers one batch program with the CPU oracle; returns its
+    instruction count (test infrastructure, run for the CPU baseline only)."""
+    import oracle
+    o = oracle.Oracle(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead)
+    for op in prog.ops:
+        if op[0] == "buffer":
+            b = op[1]
+            o.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init is not None)
+        elif op[0] == "task":
+            o.submit(op[1].flat())
+        elif op[0] == "flush":
+            o.flush()
+    n = sum(len(o.graph(k)["instrs"]) for k in range(prog.nodes))
+    o.close()
+    return n
+
+
+def cpu_baselines(sample_tasks=300, batch_scale=0.05, batch_programs=512):
+    """The CPU oracle (plain, single-threaded C++; test infrastructure) on
+    the host cores: the wave workload's first `sample_tasks` tasks on one core
+    with per-task latency (the time of each submission), and the batch of
+    uneven programs at `batch_scale` of their tasks, one program per host core
+    (a spawned process pool of hardware_concurrency workers)."""
+    import oracle
+    shape = _program_shape()
+    bufs = [op for op in shape.ops if op[0] == "buffer"]
+    tasks = [op[1] for op in shape.ops if op[0] == "task"][:sample_tasks]
+    o = oracle.Oracle(shape.nodes, shape.devices, shape.horizon_step, shape.lookahead)
+    for op in bufs:
+        b = op[1]
+        o.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init is not None)
+    lat = []
+    t0 = time.perf_counter()
+    for t in tasks:
+        t1 = time.perf_counter()
+        o.submit(t.flat())
+        lat.append(time.perf_counter() - t1)
+    o.flush()
+    cdt = time.perf_counter() - t0
+    n_or = sum(len(o.graph(k)["instrs"]) for k in range(shape.nodes))
+    o.close()
+    lat.sort()
+    cores = os.cpu_count() or 1
+    wave = {"value": n_or / cdt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {sample_tasks} of {STEPS} tasks lowered on all {NODES} nodes ({n_or} instructions)",
+            "p50_task_ms": lat[len(lat) // 2] * 1e3, "p99_task_ms": lat[min(len(lat) - 1, int(len(lat) * 0.99))] * 1e3,
+            "cpu_model": _cpu_model(), "hardware_concurrency": cores}
+    import multiprocessing as mp
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        counts = pool.map(_oracle_program_worker,
+                          W.batch_programs(count=batch_programs, scale=batch_scale, seed=0x5EED + 3), chunksize=1)
+    bdt = time.perf_counter() - t0
+    batch = {"value": sum(counts) / bdt, "unit": UNIT, "cores": cores, "kind": "oracle",
+             "sample": f"{batch_programs} uneven programs at {batch_scale:g} of their tasks, one program per core "
+                       f"({sum(counts)} instructions, {bdt:.1f} s)"}
+    return wave, batch
 
 
 def measure_lookahead(igs):
@@ -453,8 +727,10 @@ def measure_lookahead(igs):
     out = {}
     for name, p in progs.items():
         res = {}
-        for label, L in (("L0", 0), ("L8", 8), ("horizons", W.LOOKAHEAD_HORIZONS), ("infinite", W.LOOKAHEAD_INFINITE)):
-            c = igs.Context(p.nodes, p.devices, p.horizon_step, L, mode=igs.MODE_PLAIN)
+        for label, L, fl in (("L0", 0, 0), ("L8", 8, 0), ("horizons", W.LOOKAHEAD_HORIZONS, 0),
+                             ("horizons_critical_path", W.LOOKAHEAD_HORIZONS, igs.FLAG_HORIZON_CP),
+                             ("infinite", W.LOOKAHEAD_INFINITE, 0)):
+            c = igs.Context(p.nodes, p.devices, p.horizon_step, L, mode=igs.MODE_PLAIN, flags=fl)
             c.set_timing(True)
             first = None
             k = 0
@@ -636,9 +912,10 @@ def run_gpu(args):
     parts = {
         "workload": (work_ms, elems * 12.0, "wave stencil workload kernel: 12 B/element (u_prev, u, u_next)"),
         "box_copy": (copy_ms, copy_bytes, "box-copy kernel: bytes read + written"),
-        "lowering": (lower_ms, float(counters["map_reads"] + counters["map_writes"]) * 40.0
+        "lowering": (lower_ms, float(counters["map_reads"] + counters["map_writes"]) * MAP_ENTRY_BYTES
                      + instrs * 44.0 + counters["edges"] * 12.0 + counters["boxes"] * 24.0,
-                     "lowering kernel: region-map entries read + written x 40 B + output records"),
+                     "lowering kernel: region-map entries read + written x 28 B (six box coordinates + one value) "
+                     "+ output records (44 B per instruction, 12 B per edge, 24 B per box)"),
     }
     dom = max(parts, key=lambda k: parts[k][0])
     ms, byts, what = parts[dom]
@@ -651,26 +928,32 @@ def run_gpu(args):
         hot[k] = {"ms_per_step": ms_k, "bytes_per_step": b_k, "achieved_gbs": a, "frac": a / hbm}
 
     # ---- batched lowering of many programs, served lowering of many streams
-    big_copy = measure_box_copy(igs, torch, stream)
-    executors = measure_executors(igs, torch, sh, prog, make_ctx) if world == 1 else None
-    nbody = measure_nbody_lowering(igs, torch, sh) if world == 1 else None
-    lookahead = measure_lookahead(igs) if world == 1 else None
-    batched = measure_batched(igs, torch, sh) if world == 1 else None
-    served = {f"{int(r)}_per_s": measure_served(igs, torch, sh, rate=r) for r in (1e4, 1e5, 1e6)} \
-        if world == 1 else None
+    def section(fn, *a):
+        """An auxiliary measurement; a failure is recorded in the line instead
+        of ending the run."""
+        if world != 1:
+            return None
+        try:
+            return fn(*a)
+        except Exception as e:  # noqa: BLE001
+            return {"error": f"{type(e).__name__}: {e}"}
 
-    # ---- CPU baseline: the oracle on a bounded sample of the same workload
-    cpu = None
+    big_copy = measure_box_copy(igs, torch, stream)
+    executors = section(measure_executors, igs, torch, sh, prog, make_ctx)
+    nbody = section(measure_nbody, igs, torch, sh)
+    jacobi = section(measure_jacobi, igs, torch, sh)
+    lookahead = section(measure_lookahead, igs)
+    batched = section(measure_batched, igs, torch, sh)
+    served = section(measure_served, igs, torch, sh)
+    resize_exec = section(measure_resize_execution, igs, torch, sh)
+
+    # ---- CPU baseline: the oracle on bounded samples of the same workloads
+    cpu, cpu_batch = None, None
     if rank == 0 and world == 1:
-        shape = _program_shape()
-        sample_tasks = 300
-        shape.ops = [op for op in shape.ops if op[0] == "buffer"] + \
-            [op for op in shape.ops if op[0] == "task"][:sample_tasks] + [("flush",)]
-        t0 = time.perf_counter()
-        n_or = _oracle_lower(shape)
-        cdt = time.perf_counter() - t0
-        cpu = {"value": n_or / cdt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {sample_tasks} of {STEPS} tasks lowered on all {NODES} nodes ({n_or} instructions)"}
+        try:
+            cpu, cpu_batch = cpu_baselines()
+        except Exception as e:  # noqa: BLE001
+            cpu = {"error": f"{type(e).__name__}: {e}"}
 
     if rank == 0:
         line = {
@@ -694,12 +977,15 @@ def run_gpu(args):
             "box_copy_gbs": (copy_bytes / (copy_ms * 1e-3) / 1e9) if copy_ms else None,
             "box_copy_resize_512MiB": {k: dict(v, frac=v["gbs"] / hbm) for k, v in big_copy.items()},
             "executors": executors,
-            "nbody_lowering": nbody,
+            "nbody": nbody,
+            "jacobi": jacobi,
             "batched_programs": batched,
             "lookahead": lookahead,
             "served": served,
+            "resize_copies_executed": resize_exec,
             "clocks": clocks.summary(),
             "cpu_baseline": cpu,
+            "cpu_baseline_batch": cpu_batch,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

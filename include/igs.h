@@ -389,6 +389,24 @@ void igs_serve_destroy(igs_server* srv);
 /* Admits ctx (up to max_items submissions in all): IGS_ERR_BUDGET if its
  * footprint does not fit the remaining budget or too few slots are free. */
 int igs_serve_attach(igs_server* srv, igs_ctx* ctx, uint32_t max_items);
+/* Continuous batching (Sec. 4: the scheduler admits work while execution
+ * proceeds). Admits ctx exactly like igs_serve_attach when the free slots and
+ * the budget allow and no context is waiting (*admitted = 1); otherwise ctx
+ * joins the server's admission queue (FIFO, *admitted = 0, IGS_OK). While it
+ * waits, its submissions are kept on the host (igs_serve_progress reports
+ * none taken); when a detach frees enough slots and budget, contexts are
+ * admitted from the head of the queue in arrival order, their waiting
+ * submissions lowered by one launch before the loop takes over. Detaching a
+ * waiting context removes it from the queue (its submissions stay unlowered
+ * until the next flush / sync). The submission arrays for max_items are
+ * allocated here. IGS_ERR_BUDGET if ctx could never fit (more nodes than
+ * slots, or a footprint above the whole budget); IGS_ERR_INVALID_ARG as for
+ * igs_serve_attach. admitted may be null. */
+int igs_serve_enqueue(igs_server* srv, igs_ctx* ctx, uint32_t max_items, uint32_t* admitted);
+/* Server counters: [0] contexts admitted (directly or from the queue), [1]
+ * admitted from the queue after a detach, [2] contexts waiting now, [3] the
+ * most that waited at once, [4] slots in use, [5] budget bytes in use. */
+int igs_serve_stats(const igs_server* srv, uint64_t out[8]);
 /* Launches the loop if it is not running. */
 int igs_serve_start(igs_server* srv);
 /* Submissions published by ctx, and the number taken by every node (min over
@@ -419,6 +437,25 @@ typedef struct igs_replay_item {
   uint64_t arrival_ns;  /* since the start of the call */
 } igs_replay_item;
 int igs_serve_replay(igs_server* srv, igs_ctx* const* ctxs, uint32_t n_ctx, const igs_replay_item* items, uint32_t n,
+                     uint32_t timeout_ms, uint64_t* latency_ns, uint64_t* wall_ns);
+/* igs_serve_replay with flags. IGS_REPLAY_DETACH: once every item of a
+ * context in the trace has been taken, the context is detached
+ * (igs_serve_detach), which admits contexts waiting for admission; the
+ * contexts may have been enqueued (igs_serve_enqueue) rather than attached.
+ * A waiting context's items count their wait for admission in latency_ns. */
+#define IGS_REPLAY_DETACH 1u
+int igs_serve_replay_ex(igs_server* srv, igs_ctx* const* ctxs, uint32_t n_ctx, const igs_replay_item* items,
+                        uint32_t n, uint32_t timeout_ms, uint32_t flags, uint64_t* latency_ns, uint64_t* wall_ns);
+
+/* The comparator of the served loop, driven like igs_serve_replay: item k
+ * is submitted to ctxs[item.ctx] (contexts in IGS_MODE_PLAIN, not served) at
+ * its arrival time, which is one lowering launch on that context's stream;
+ * latency_ns[k] = time from arrival until that launch completed (an event
+ * polled continuously; contexts run concurrently, each in submission order).
+ * IGS_ERR_INVALID_ARG for a served or non-plain context, IGS_ERR_TIMEOUT if
+ * the trace has not completed timeout_ms after its last arrival; lowering
+ * failures as igs_sync reports them. *wall_ns as for igs_serve_replay. */
+int igs_replay_plain(igs_ctx* const* ctxs, uint32_t n_ctx, const igs_replay_item* items, uint32_t n,
                      uint32_t timeout_ms, uint64_t* latency_ns, uint64_t* wall_ns);
 
 /* Counters: [0] instructions, [1] edges, [2] boxes, [3] map entries read,
@@ -479,11 +516,19 @@ int igs_box_copy(const igs_copy_job* jobs, uint32_t n, void* stream);
  *   region-map heap of 32768 entries shared by all its box tables; the
  *   program's staged inputs plus per-node state (about 2.6 MiB + instr_cap
  *   bytes per node) must fit the array, else IGS_ERR_CAPACITY before anything
- *   runs (a heap that fills up during lowering reports IGS_ERR_CAPACITY).
+ *   runs. A capacity that runs out during the lowering (the heap, an output
+ *   array) shows only in that node's status word (counts[5] = 1); the call
+ *   still returns IGS_OK.
+ *   Checks: the same programs as the context API are accepted (buffer shapes,
+ *   task headers, accessors, config flags); a task that accesses a destroyed
+ *   buffer, or a second destruction of a buffer, is IGS_ERR_INVALID_ARG.
+ *   A task whose chunks write overlapping regions (Sec. 4.4) is left out of
+ *   the graph, as igs_submit_task does, and the call then returns
+ *   IGS_ERR_OVERLAPPING_WRITE (the outputs and counts are still written).
  *   Sharing: every call uses the same array and leaves its last contents there
  *   (each call resets what must start at zero); calls that overlap on the GPU
- *   race, so serialize them. The call returns after the lowering finished on
- *   `stream` (cudaStream_t, NULL = default stream).
+ *   race, so serialize them. The call synchronizes `stream` (cudaStream_t,
+ *   NULL = default stream): it returns after the lowering has finished.
  *   Set-up: the first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
  *   before any stream capture.

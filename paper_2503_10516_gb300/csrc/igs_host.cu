@@ -12,11 +12,13 @@
 #include <cstdio>
 #include <thread>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <unordered_map>
 #include <string>
 #include <vector>
 
+#include "igs_check.h"
 #include "igs_exec.h"
 #include "igs_internal.h"
 #include "igs_tdag.h"
@@ -144,6 +146,9 @@ struct igs_ctx {
   size_t arena_bytes = 0;
   // serving: submissions live in host-mapped memory the loop polls
   igs_server* server = nullptr;
+  // waiting in the server's admission queue: submissions are kept on the host
+  // (not published, not lowered) until a detach makes room
+  bool serve_pending = false;
   std::vector<uint32_t> slot_ids;
   Item* m_items = nullptr;
   igs_task* m_tasks = nullptr;
@@ -173,6 +178,10 @@ struct igs_server {
   std::vector<uint32_t> free_slots;
   double used = 0;
   std::vector<std::pair<igs_ctx*, double>> attached;
+  // admission queue (FIFO): contexts that did not fit when enqueued, with
+  // their submission capacity
+  std::deque<std::pair<igs_ctx*, uint32_t>> waiting;
+  uint64_t n_admitted = 0, n_admitted_queued = 0, peak_waiting = 0;
 };
 
 namespace {
@@ -333,7 +342,7 @@ int push_item(igs_ctx* c, uint32_t kind, uint32_t arg, uint32_t task) {
   it.arg = arg;
   it.task = task;
   c->items.push_back(it);
-  if (c->server) {
+  if (c->server && !c->serve_pending) {
     // the record, then (after a release fence) the count the loop polls
     if (kind == IT_TASK) c->m_tasks[task] = c->tasks[task];
     c->m_items[c->items.size() - 1] = it;
@@ -364,7 +373,7 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
   if (!cfg || cfg->num_nodes < 1 || cfg->num_nodes > 32 || cfg->devices_per_node < 1 || cfg->devices_per_node > 29)
     return IGS_ERR_INVALID_ARG;
   if (cfg->mode > IGS_MODE_BATCHED) return IGS_ERR_INVALID_ARG;
-  if (cfg->flags & ~(IGS_FLAG_STAGE_D2D | IGS_FLAG_HORIZON_CP)) return IGS_ERR_INVALID_ARG;
+  if (!config_flags_ok(cfg->flags)) return IGS_ERR_INVALID_ARG;
   igs_ctx* c = new igs_ctx();
   c->cfg = *cfg;
   c->N = cfg->num_nodes;
@@ -658,7 +667,7 @@ int igs_stats(igs_ctx* c, double out[8]) {
 int igs_create_buffer(igs_ctx* c, uint32_t dims, const uint32_t extent[3], uint32_t elem_size, const void* host_init,
                       uint32_t* out_buffer) {
   if (!c || !extent || !out_buffer) return fail_ctx(c, IGS_ERR_INVALID_ARG, "null argument");
-  if (dims < 1 || dims > 3 || elem_size == 0) return fail_ctx(c, IGS_ERR_INVALID_ARG, "bad buffer shape");
+  if (!buffer_shape_ok(dims, extent, elem_size)) return fail_ctx(c, IGS_ERR_INVALID_ARG, "bad buffer shape");
   BufDesc b{};
   b.dims = dims;
   uint64_t count = 1;
@@ -697,19 +706,8 @@ int igs_destroy_buffer(igs_ctx* c, uint32_t b) {
 
 int igs_submit_task(igs_ctx* c, const igs_task* t, uint64_t* out_seq) {
   if (!c || !t) return fail_ctx(c, IGS_ERR_INVALID_ARG, "null argument");
-  if ((t->num_chunks >> 16) && ((t->num_chunks & 0xFFFFu) == 0 || t->dims < 2)) return IGS_ERR_INVALID_ARG;
-  if (t->dims < 1 || t->dims > 3 || t->num_chunks == 0 || t->num_accessors > IGS_MAX_ACCESSORS)
-    return fail_ctx(c, IGS_ERR_INVALID_ARG, "bad task header");
-  for (int d = 0; d < 3; ++d)
-    if (d >= (int)t->dims && t->range[d] != 1) return fail_ctx(c, IGS_ERR_INVALID_ARG, "unused range dims must be 1");
-  for (uint32_t a = 0; a < t->num_accessors; ++a) {
-    const igs_accessor& ac = t->acc[a];
-    if (ac.buffer >= c->bufs.size() || !c->buf_live[ac.buffer]) return fail_ctx(c, IGS_ERR_INVALID_ARG, "unknown buffer");
-    if (ac.mode < 1 || ac.mode > 3) return fail_ctx(c, IGS_ERR_INVALID_ARG, "bad access mode");
-    for (int d = 0; d < 3; ++d)
-      if (ac.dim[d].kind > IGS_MAP_FIXED || (ac.dim[d].kind == IGS_MAP_AFFINE && ac.dim[d].a > 2))
-        return fail_ctx(c, IGS_ERR_INVALID_ARG, "bad range mapper");
-  }
+  if (const char* why = task_problem(*t, [c](uint32_t b) { return b < c->bufs.size() && c->buf_live[b]; }))
+    return fail_ctx(c, IGS_ERR_INVALID_ARG, why);
   if (c->server && c->items.size() + 2 > c->serve_cap)
     return fail_ctx(c, IGS_ERR_CAPACITY, "serving capacity of this context exceeded");
   const uint32_t ti = (uint32_t)c->tasks.size();
@@ -2064,6 +2062,10 @@ extern "C" void igs_serve_destroy(igs_server* s) {
   if (!s) return;
   igs_serve_stop(s);
   for (auto& a : s->attached) a.first->server = nullptr;
+  for (auto& w : s->waiting) {
+    w.first->server = nullptr;
+    w.first->serve_pending = false;
+  }
   if (s->slots) cudaFreeHost((void*)s->slots);
   if (s->stop) cudaFreeHost(s->stop);
   if (s->done_ev) cudaEventDestroy(s->done_ev);
@@ -2084,14 +2086,27 @@ extern "C" int igs_serve_start(igs_server* s) {
   return IGS_OK;
 }
 
-extern "C" int igs_serve_attach(igs_server* s, igs_ctx* c, uint32_t max_items) {
-  if (!s || !c || c->server || max_items < c->items.size() + 1) return IGS_ERR_INVALID_ARG;
+namespace {
+// Footprint a served context is charged against the budget: its device arena
+// plus every buffer's bytes on every memory of every node plus its host data.
+double serve_footprint(const igs_ctx* c) {
   double foot = (double)c->arena_bytes;
   for (size_t b = 0; b < c->bufs.size(); ++b) {
     double bytes = c->bufs[b].elem;
     for (int d = 0; d < 3; ++d) bytes *= c->bufs[b].extent[d];
     foot += bytes * c->N * (c->D + 1) + (c->init_dev[b] ? bytes : 0.0);
   }
+  return foot;
+}
+
+bool serve_fits(const igs_server* s, const igs_ctx* c) {
+  if (s->free_slots.size() < c->N) return false;
+  return !s->cfg.hbm_budget_bytes || s->used + serve_footprint(c) <= (double)s->cfg.hbm_budget_bytes;
+}
+
+// Attaches c (not served, or leaving the admission queue) when it fits.
+int serve_attach_impl(igs_server* s, igs_ctx* c, uint32_t max_items) {
+  const double foot = serve_footprint(c);
   if (s->free_slots.size() < c->N) return fail_ctx(c, IGS_ERR_BUDGET, "no free serving slots");
   if (s->cfg.hbm_budget_bytes && s->used + foot > (double)s->cfg.hbm_budget_bytes)
     return fail_ctx(c, IGS_ERR_BUDGET, "HBM budget exceeded");
@@ -2156,11 +2171,87 @@ extern "C" int igs_serve_attach(igs_server* s, igs_ctx* c, uint32_t max_items) {
   c->server = s;
   s->used += foot;
   s->attached.push_back({c, foot});
+  s->n_admitted += 1;
   return IGS_OK;
 }
 
+// Admits waiting contexts in arrival order while the head of the queue fits.
+// A context whose admission fails leaves the queue unserved (its error is in
+// igs_last_error; later submissions take the launch path).
+void serve_admit_waiting(igs_server* s) {
+  while (!s->waiting.empty()) {
+    igs_ctx* c = s->waiting.front().first;
+    const uint32_t cap = s->waiting.front().second;
+    if (!serve_fits(s, c)) break;
+    s->waiting.pop_front();
+    c->server = nullptr;
+    c->serve_pending = false;
+    if (serve_attach_impl(s, c, cap) == IGS_OK) s->n_admitted_queued += 1;
+  }
+}
+}  // namespace
+
+extern "C" int igs_serve_attach(igs_server* s, igs_ctx* c, uint32_t max_items) {
+  if (!s || !c || c->server || max_items < c->items.size() + 1) return IGS_ERR_INVALID_ARG;
+  return serve_attach_impl(s, c, max_items);
+}
+
+extern "C" int igs_serve_enqueue(igs_server* s, igs_ctx* c, uint32_t max_items, uint32_t* admitted) {
+  if (!s || !c || c->server || max_items < c->items.size() + 1) return IGS_ERR_INVALID_ARG;
+  if (admitted) *admitted = 0;
+  // a context that could never fit is refused rather than queued forever
+  if (c->N > s->cfg.max_slots) return fail_ctx(c, IGS_ERR_BUDGET, "more nodes than serving slots");
+  if (s->cfg.hbm_budget_bytes && serve_footprint(c) > (double)s->cfg.hbm_budget_bytes)
+    return fail_ctx(c, IGS_ERR_BUDGET, "footprint exceeds the whole HBM budget");
+  if (s->waiting.empty() && serve_fits(s, c)) {
+    const int r = serve_attach_impl(s, c, max_items);
+    if (r == IGS_OK && admitted) *admitted = 1;
+    return r;
+  }
+  // the device and host-mapped submission arrays are sized now, so that the
+  // admission (during a detach, with the loop running) allocates nothing
+  if (int r = grow_device(c, c->d_items, c->cap_items, max_items, c->items_up)) return r;
+  if (int r = grow_device(c, c->d_tasks, c->cap_tasks, max_items, c->tasks_up)) return r;
+  if (c->m_items && max_items > c->m_cap) {
+    cudaFreeHost(c->m_items);
+    cudaFreeHost(c->m_tasks);
+    c->m_items = nullptr;
+    c->m_tasks = nullptr;
+  }
+  if (!c->m_items) {
+    CK(cudaHostAlloc(&c->m_items, sizeof(Item) * max_items, cudaHostAllocMapped));
+    CK(cudaHostAlloc(&c->m_tasks, sizeof(igs_task) * max_items, cudaHostAllocMapped));
+    c->m_cap = max_items;
+  }
+  if (!c->m_nitems) CK(cudaHostAlloc(&c->m_nitems, sizeof(uint32_t), cudaHostAllocMapped));
+  c->server = s;
+  c->serve_pending = true;
+  c->serve_cap = max_items;
+  s->waiting.push_back({c, max_items});
+  s->peak_waiting = std::max<uint64_t>(s->peak_waiting, s->waiting.size());
+  return IGS_OK;
+}
+
+extern "C" int igs_serve_stats(const igs_server* s, uint64_t out[8]) {
+  if (!s || !out) return IGS_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(uint64_t) * 8);
+  out[0] = s->n_admitted;
+  out[1] = s->n_admitted_queued;
+  out[2] = s->waiting.size();
+  out[3] = s->peak_waiting;
+  out[4] = s->cfg.max_slots - s->free_slots.size();
+  out[5] = (uint64_t)s->used;
+  return IGS_OK;
+}
+
+
 extern "C" int igs_serve_progress(const igs_ctx* c, uint32_t* submitted, uint32_t* taken) {
   if (!c || !c->server) return IGS_ERR_INVALID_ARG;
+  if (c->serve_pending) {  // waiting for admission: nothing taken yet
+    if (submitted) *submitted = (uint32_t)c->items.size();
+    if (taken) *taken = 0;
+    return IGS_OK;
+  }
   uint32_t t = 0xFFFFFFFFu, st = 0;
   for (uint32_t id : c->slot_ids) {
     const ServeSlot& S = c->server->slots[id];
@@ -2173,8 +2264,9 @@ extern "C" int igs_serve_progress(const igs_ctx* c, uint32_t* submitted, uint32_
   return st ? IGS_ERR_CAPACITY : IGS_OK;
 }
 
-extern "C" int igs_serve_replay(igs_server* s, igs_ctx* const* ctxs, uint32_t n_ctx, const igs_replay_item* items,
-                                uint32_t n, uint32_t timeout_ms, uint64_t* latency_ns, uint64_t* wall_ns) {
+extern "C" int igs_serve_replay_ex(igs_server* s, igs_ctx* const* ctxs, uint32_t n_ctx, const igs_replay_item* items,
+                                   uint32_t n, uint32_t timeout_ms, uint32_t flags, uint64_t* latency_ns,
+                                   uint64_t* wall_ns) {
   if (!s || !ctxs || (n && (!items || !latency_ns))) return IGS_ERR_INVALID_ARG;
   for (uint32_t i = 0; i < n_ctx; ++i)
     if (!ctxs[i] || ctxs[i]->server != s) return IGS_ERR_INVALID_ARG;
@@ -2188,6 +2280,11 @@ extern "C" int igs_serve_replay(igs_server* s, igs_ctx* const* ctxs, uint32_t n_
   std::vector<std::vector<std::pair<uint32_t, uint32_t>>> fifo(n_ctx);
   std::vector<size_t> head(n_ctx, 0);
   std::vector<uint32_t> busy;  // contexts with items in flight
+  // with IGS_REPLAY_DETACH: a context is detached once its last item of the
+  // trace is taken, which admits contexts waiting in the admission queue
+  const bool detach_at_end = (flags & IGS_REPLAY_DETACH) != 0;
+  std::vector<uint32_t> last_item(n_ctx, 0xFFFFFFFFu);
+  for (uint32_t k = 0; k < n; ++k) last_item[items[k].ctx] = k;
   uint32_t next = 0, done = 0;
   uint64_t last = 0;
   const uint64_t limit = (n ? items[n - 1].arrival_ns : 0) + (uint64_t)timeout_ms * 1000000ull;
@@ -2219,6 +2316,11 @@ extern "C" int igs_serve_replay(igs_server* s, igs_ctx* const* ctxs, uint32_t n_
       if (head[ci] == q.size()) {
         busy[b] = busy.back();
         busy.pop_back();
+        if (detach_at_end && last_item[ci] != 0xFFFFFFFFu && last_item[ci] < next) {
+          last_item[ci] = 0xFFFFFFFFu;
+          if (int e = igs_serve_detach(s, ctxs[ci], timeout_ms)) return e;
+          t = now_ns();
+        }
       } else {
         ++b;
       }
@@ -2234,8 +2336,105 @@ extern "C" int igs_serve_replay(igs_server* s, igs_ctx* const* ctxs, uint32_t n_
   return IGS_OK;
 }
 
+extern "C" int igs_serve_replay(igs_server* s, igs_ctx* const* ctxs, uint32_t n_ctx, const igs_replay_item* items,
+                                uint32_t n, uint32_t timeout_ms, uint64_t* latency_ns, uint64_t* wall_ns) {
+  return igs_serve_replay_ex(s, ctxs, n_ctx, items, n, timeout_ms, 0, latency_ns, wall_ns);
+}
+
+extern "C" int igs_replay_plain(igs_ctx* const* ctxs, uint32_t n_ctx, const igs_replay_item* items, uint32_t n,
+                                uint32_t timeout_ms, uint64_t* latency_ns, uint64_t* wall_ns) {
+  if (!ctxs || (n && (!items || !latency_ns))) return IGS_ERR_INVALID_ARG;
+  for (uint32_t i = 0; i < n_ctx; ++i)
+    if (!ctxs[i] || ctxs[i]->server || ctxs[i]->cfg.mode != IGS_MODE_PLAIN || ctxs[i]->pipelined)
+      return IGS_ERR_INVALID_ARG;
+  for (uint32_t k = 0; k < n; ++k)
+    if (items[k].ctx >= n_ctx || (!items[k].epoch && !items[k].task) || (k && items[k].arrival_ns < items[k - 1].arrival_ns))
+      return IGS_ERR_INVALID_ARG;
+  using clock = std::chrono::steady_clock;
+  const auto t0 = clock::now();
+  auto now_ns = [&]() { return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(clock::now() - t0).count(); };
+  // per context, in submission order: (completion event, item index)
+  std::vector<std::deque<std::pair<cudaEvent_t, uint32_t>>> inflight(n_ctx);
+  std::vector<cudaEvent_t> pool;
+  auto release = [&]() {
+    for (auto& q : inflight)
+      for (auto& e : q) cudaEventDestroy(e.first);
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  };
+  uint32_t next = 0, done = 0;
+  uint64_t last = 0;
+  const uint64_t limit = (n ? items[n - 1].arrival_ns : 0) + (uint64_t)timeout_ms * 1000000ull;
+  while (done < n) {
+    uint64_t t = now_ns();
+    while (next < n && items[next].arrival_ns <= t) {
+      const igs_replay_item& it = items[next];
+      igs_ctx* c = ctxs[it.ctx];
+      uint64_t seq = 0;
+      const int r = it.epoch ? igs_submit_epoch(c) : igs_submit_task(c, it.task, &seq);  // one launch
+      if (r && r != IGS_ERR_OVERLAPPING_WRITE) {
+        release();
+        return r;
+      }
+      cudaEvent_t ev = nullptr;
+      if (!pool.empty()) {
+        ev = pool.back();
+        pool.pop_back();
+      } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        release();
+        return fail_ctx(c, IGS_ERR_CUDA, "event creation failed");
+      }
+      if (cudaEventRecord(ev, c->stream) != cudaSuccess) {
+        pool.push_back(ev);
+        release();
+        return fail_ctx(c, IGS_ERR_CUDA, "event record failed");
+      }
+      inflight[it.ctx].push_back({ev, next});
+      ++next;
+    }
+    t = now_ns();
+    for (uint32_t ci = 0; ci < n_ctx; ++ci) {
+      auto& q = inflight[ci];
+      while (!q.empty()) {
+        const cudaError_t e = cudaEventQuery(q.front().first);
+        if (e == cudaErrorNotReady) break;
+        if (e != cudaSuccess) {
+          release();
+          return fail_ctx(ctxs[ci], IGS_ERR_CUDA, "lowering launch failed");
+        }
+        const uint32_t k = q.front().second;
+        latency_ns[k] = t > items[k].arrival_ns ? t - items[k].arrival_ns : 0;
+        last = t;
+        pool.push_back(q.front().first);
+        q.pop_front();
+        ++done;
+      }
+    }
+    if (done < n && t > limit) {
+      release();
+      return IGS_ERR_TIMEOUT;
+    }
+  }
+  release();
+  for (uint32_t i = 0; i < n_ctx; ++i) {
+    const int r = check_status(ctxs[i]);
+    if (r && r != IGS_ERR_OVERLAPPING_WRITE) return r;
+  }
+  if (wall_ns) *wall_ns = last;
+  return IGS_OK;
+}
+
 extern "C" int igs_serve_detach(igs_server* s, igs_ctx* c, uint32_t timeout_ms) {
   if (!s || !c || c->server != s) return IGS_ERR_INVALID_ARG;
+  if (c->serve_pending) {  // still queued: it leaves the queue unserved
+    for (auto it = s->waiting.begin(); it != s->waiting.end(); ++it)
+      if (it->first == c) {
+        s->waiting.erase(it);
+        break;
+      }
+    c->server = nullptr;
+    c->serve_pending = false;
+    return IGS_OK;
+  }
   const auto t0 = std::chrono::steady_clock::now();
   for (;;) {
     uint32_t sub = 0, tk = 0;
@@ -2271,6 +2470,8 @@ extern "C" int igs_serve_detach(igs_server* s, igs_ctx* c, uint32_t timeout_ms) 
     }
   c->server = nullptr;
   c->slot_ids.clear();
+  // the freed slots and budget go to the contexts waiting for admission
+  serve_admit_waiting(s);
   // later submissions go through the launch path again
   const int r = check_status(c);
   return r == IGS_ERR_OVERLAPPING_WRITE ? IGS_OK : r;

@@ -120,6 +120,35 @@ __device__ __forceinline__ int bx_minus(const Bx& a, const Bx& b, Bx* out) {
   }
   return k;
 }
+// The pieces of a \ b for overlapping a and b, in bx_minus's order: their
+// number, and each piece handed to f(index, piece) as it is formed (no array
+// of pieces, which would live in local memory).
+__device__ __forceinline__ int bx_minus_count(const Bx& a, const Bx& b) {
+  int k = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) k += (a.lo[d] < b.lo[d]) + (a.hi[d] > b.hi[d]);
+  return k;
+}
+template <class F>
+__device__ __forceinline__ void bx_minus_each(const Bx& a, const Bx& b, F f) {
+  int k = 0;
+  Bx rem = a;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (rem.lo[d] < b.lo[d]) {
+      Bx o = rem;
+      o.hi[d] = b.lo[d];
+      f(k++, o);
+      rem.lo[d] = b.lo[d];
+    }
+    if (rem.hi[d] > b.hi[d]) {
+      Bx o = rem;
+      o.lo[d] = b.hi[d];
+      f(k++, o);
+      rem.hi[d] = b.hi[d];
+    }
+  }
+}
 // Two boxes whose union is a box (adjacent along one dimension, equal in the others).
 __device__ __forceinline__ bool bx_mergeable(const Bx& a, const Bx& b) {
   int adj = -1;
@@ -204,6 +233,9 @@ struct Ctx {
   uint32_t workers;  // warps sharing the kernel phase (1 = warp 0 alone)
   struct Stage* stage;  // emit into this staging area with provisional ids (coherence workers), else null
   bool helper;          // a helper warp (keeps off the node's profile counters)
+  // item compiled straight from delivery: its chunks and mapped boxes are
+  // still in S_CH / S_MP and it is known not to allocate (NONE otherwise)
+  uint32_t fresh;
 };
 
 // Instructions a coherence worker emits before their final ids are known:
@@ -635,15 +667,13 @@ __device__ __forceinline__ void t_subtract(Ctx& c, Table& t_ref, uint32_t key, c
     }
     const uint32_t hits = __ballot_sync(FULL, hit);
     if (!hits) continue;  // nothing to remove in these 32 entries
-    Bx pc[6];
-    int np = 0;
-    if (hit) np = bx_minus(e, r, pc);
+    const int np = hit ? bx_minus_count(e, r) : 0;
     t_dead(c, t, __popc(hits));
-    const uint32_t first = t_claim_n(c, t, hit ? (uint32_t)np : 0u);
+    const uint32_t first = t_claim_n(c, t, (uint32_t)np);
     if (first == NONE) break;  // the table could not grow (status set)
     if (hit) {
       t_kill(t, i);
-      for (int j = 0; j < np; ++j) t_put(t, first + j, k, pc[j], v0, v1, v2);
+      bx_minus_each(e, r, [&](int j, const Bx& pb) { t_put(t, first + j, k, pb, v0, v1, v2); });
     }
   }
   __syncwarp();
@@ -675,15 +705,13 @@ __device__ __noinline__ Table t_or_v(Ctx& c, Table t, uint32_t key, const Bx& r,
     }
     const uint32_t hits = __ballot_sync(FULL, hit);
     if (!hits) continue;
-    Bx pc[6];
-    int np = 0;
-    if (hit) np = bx_minus(e, r, pc);
+    const int np = hit ? bx_minus_count(e, r) : 0;
     t_dead(c, t, __popc(hits));
     const uint32_t first = t_claim_n(c, t, hit ? (uint32_t)np + 1 : 0u);
     if (first == NONE) break;  // the table could not grow (status set)
     if (hit) {
       t_kill(t, i);
-      for (int j = 0; j < np; ++j) t_put(t, first + j, k, pc[j], v[0], v[1], v[2]);
+      bx_minus_each(e, r, [&](int j, const Bx& pb) { t_put(t, first + j, k, pb, v[0], v[1], v[2]); });
       v[vidx] |= bits;
       t_put(t, first + np, k, bx_isect(e, r), v[0], v[1], v[2]);
     }
@@ -795,15 +823,13 @@ __device__ __noinline__ Table t_make_disjoint_v(Ctx& c, Table t, uint32_t val) {
       }
       const uint32_t hits = __ballot_sync(FULL, hit);
       if (!hits) continue;
-      Bx pc[6];
-      int np = 0;
-      if (hit) np = bx_minus(f, e, pc);
+      const int np = hit ? bx_minus_count(f, e) : 0;
       t_dead(c, t, __popc(hits));
-      const uint32_t first = t_claim_n(c, t, hit ? (uint32_t)np : 0u);
+      const uint32_t first = t_claim_n(c, t, (uint32_t)np);
       if (first == NONE) return t;  // the table could not grow (status set)
       if (hit) {
         t_kill(t, j);
-        for (int q = 0; q < np; ++q) t_put(t, first + q, k, pc[q], w0, w1, w2);
+        bx_minus_each(f, e, [&](int q, const Bx& pb) { t_put(t, first + q, k, pb, w0, w1, w2); });
       }
     }
     __syncwarp();
@@ -2900,12 +2926,17 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
   Table& CH = c.s[S_CH];
   Table& MP = c.s[S_MP];
   PhaseTimer pt = pt_start();
-  task_chunks(c, t, CH);
-  task_mapped(c, t, CH, MP);
+  // delivered and compiled at once: chunks and mapped boxes are still in
+  // place and the task was found not to allocate
+  const bool fresh = c.fresh == item;
+  if (!fresh) {
+    task_chunks(c, t, CH);
+    task_mapped(c, t, CH, MP);
+  }
   if (c.err) return;
   pt_lap(pt, c, PH_SPLIT);
   // P1 (nothing to do unless some requirement lies outside every allocation)
-  if (allocating(c, t, seq, CH, MP)) alloc_phase(c, t, seq, CH, MP);
+  if (!fresh && allocating(c, t, seq, CH, MP)) alloc_phase(c, t, seq, CH, MP);
   if (c.err) return;
   pt_lap(pt, c, PH_P1);
   uint32_t qs, qe;
@@ -3550,7 +3581,9 @@ __device__ __noinline__ void deliver(Ctx& c, uint32_t item) {
       if (horizons) record_queued_reqs(c, c.pg->tasks[it.task], it.seq, c.s[S_CH], c.s[S_MP]);
       else if (queued_tasks(c) > c.lookahead) flush_queue(c);
     } else {
+      if (it.kind == IT_TASK) c.fresh = item;  // nothing changes the allocations before it compiles
       process(c, item);
+      c.fresh = NONE;
     }
   } else if (horizons) {
     // compile once two horizons follow the last task the queue would not make room for
@@ -3615,6 +3648,7 @@ __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg) {
   c.workers = 1;
   c.stage = nullptr;
   c.helper = false;
+  c.fresh = NONE;
 }
 
 __device__ void store_ctx(Ctx& c, uint32_t cursor) {

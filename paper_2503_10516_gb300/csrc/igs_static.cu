@@ -12,6 +12,7 @@
 #include <mutex>
 #include <vector>
 
+#include "igs_check.h"
 #include "igs_internal.h"
 #include "igs_tdag.h"
 
@@ -83,6 +84,7 @@ extern "C" int igs_lower_static(const igs_config* cfg, const igs_static_buffer* 
   if (!cfg || !outs || (num_buffers && !bufs) || (num_tasks && !tasks) || (num_ops && !ops)) return IGS_ERR_INVALID_ARG;
   const uint32_t N = cfg->num_nodes, D = cfg->devices_per_node;
   if (N < 1 || N > 32 || D < 1 || D > 29 || num_buffers > kBuffers) return IGS_ERR_INVALID_ARG;
+  if (!config_flags_ok(cfg->flags)) return IGS_ERR_INVALID_ARG;
   cudaStream_t stream = (cudaStream_t)stream_ptr;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return IGS_ERR_CUDA;
@@ -113,9 +115,10 @@ extern "C" int igs_lower_static(const igs_config* cfg, const igs_static_buffer* 
     for (int d = 0; d < 3; ++d) bd[b].extent[d] = d < (int)bufs[b].dims ? bufs[b].extent[d] : 1;
     bd[b].elem = bufs[b].elem_size;
     bd[b].init = bufs[b].has_init ? 1 : 0;
-    if (bd[b].dims < 1 || bd[b].dims > 3) return IGS_ERR_INVALID_ARG;
+    if (!buffer_shape_ok(bufs[b].dims, bufs[b].extent, bufs[b].elem_size)) return IGS_ERR_INVALID_ARG;
   }
   uint32_t seq = 0, ntask = 0, created = 0;
+  bool live[kBuffers] = {};  // created and not destroyed (the same checks as the context API)
   CriticalPath cpath;  // task-graph depth (IGS_FLAG_HORIZON_CP)
   for (uint32_t i = 0; i < num_ops; ++i) {
     const igs_static_op& op = ops[i];
@@ -124,20 +127,14 @@ extern "C" int igs_lower_static(const igs_config* cfg, const igs_static_buffer* 
       case IGS_OP_CREATE_BUFFER:
         if (op.arg != created || op.arg >= num_buffers) return IGS_ERR_INVALID_ARG;
         it = Item{IT_CREATE, seq++, op.arg, 0};
+        live[op.arg] = true;
         ++created;
         items.push_back(it);
         break;
       case IGS_OP_TASK: {
         if (op.arg >= num_tasks) return IGS_ERR_INVALID_ARG;
         const igs_task& t = tasks[op.arg];
-        if (t.dims < 1 || t.dims > 3 || t.num_chunks == 0 || t.num_accessors > IGS_MAX_ACCESSORS) return IGS_ERR_INVALID_ARG;
-        if ((t.num_chunks >> 16) && ((t.num_chunks & 0xFFFFu) == 0 || t.dims < 2)) return IGS_ERR_INVALID_ARG;
-        for (uint32_t a = 0; a < t.num_accessors; ++a) {
-          if (t.acc[a].buffer >= created || t.acc[a].mode < 1 || t.acc[a].mode > 3) return IGS_ERR_INVALID_ARG;
-          for (int d = 0; d < 3; ++d)
-            if (t.acc[a].dim[d].kind > IGS_MAP_FIXED || (t.acc[a].dim[d].kind == IGS_MAP_AFFINE && t.acc[a].dim[d].a > 2))
-              return IGS_ERR_INVALID_ARG;
-        }
+        if (task_problem(t, [&](uint32_t b) { return b < created && live[b]; })) return IGS_ERR_INVALID_ARG;
         items.push_back(Item{IT_TASK, seq++, 0, op.arg});
         const bool cp_horizon =
             (cfg->flags & IGS_FLAG_HORIZON_CP) &&
@@ -153,7 +150,8 @@ extern "C" int igs_lower_static(const igs_config* cfg, const igs_static_buffer* 
         items.push_back(Item{IT_EPOCH, seq++, 0, 0});
         break;
       case IGS_OP_DESTROY_BUFFER:
-        if (op.arg >= created) return IGS_ERR_INVALID_ARG;
+        if (op.arg >= created || !live[op.arg]) return IGS_ERR_INVALID_ARG;  // unknown, or destroyed already
+        live[op.arg] = false;
         items.push_back(Item{IT_DESTROY, seq++, op.arg, 0});
         break;
       case IGS_OP_LOOKAHEAD:
@@ -272,7 +270,14 @@ extern "C" int igs_lower_static(const igs_config* cfg, const igs_static_buffer* 
     CKS(cudaMemcpyAsync(cnt + 4, &nd->n_diag, 4, cudaMemcpyDeviceToDevice, stream));
     CKS(cudaMemcpyAsync(cnt + 5, &nd->status, 4, cudaMemcpyDeviceToDevice, stream));
   }
+  // tasks rejected for overlapping writes (Sec. 4.4), counted per node
+  uint32_t rej[32];
+  for (uint32_t n = 0; n < N; ++n)
+    CKS(cudaMemcpyAsync(&rej[n], &(reinterpret_cast<const NodeDev*>(base + o_nodes) + n)->n_rej, 4,
+                        cudaMemcpyDeviceToHost, stream));
   CKS(cudaStreamSynchronize(stream));
 #undef CKS
+  for (uint32_t n = 0; n < N; ++n)
+    if (rej[n]) return IGS_ERR_OVERLAPPING_WRITE;
   return IGS_OK;
 }

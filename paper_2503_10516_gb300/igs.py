@@ -35,7 +35,8 @@ EXPORTS = ("igs_create", "igs_destroy", "igs_create_buffer", "igs_destroy_buffer
            "igs_serve_create", "igs_serve_destroy", "igs_serve_attach", "igs_serve_start", "igs_serve_progress",
            "igs_serve_detach", "igs_serve_stop", "igs_run", "igs_lower_batch_shaped", "igs_set_executor",
            "igs_exec_stats", "igs_selftest_flow_wait", "igs_bounds_errors", "igs_serve_replay",
-           "igs_horizon_plan")
+           "igs_horizon_plan", "igs_serve_enqueue", "igs_serve_stats", "igs_serve_replay_ex",
+           "igs_replay_plain")
 EXEC_LEVELS, EXEC_DATAFLOW = 0, 1  # IGS_EXEC_*
 ORDER_SUBMISSION, ORDER_LONGEST_FIRST = 0, 1  # IGS_ORDER_*
 
@@ -130,6 +131,10 @@ def lib():
         L.igs_selftest_flow_wait.argtypes = [u32]
         L.igs_bounds_errors.argtypes = [vp, vp, u32, P32]
         L.igs_serve_replay.argtypes = [vp, ctypes.POINTER(vp), u32, vp, u32, u32, vp, vp]
+        L.igs_serve_replay_ex.argtypes = [vp, ctypes.POINTER(vp), u32, vp, u32, u32, u32, vp, vp]
+        L.igs_serve_enqueue.argtypes = [vp, vp, u32, P32]
+        L.igs_replay_plain.argtypes = [ctypes.POINTER(vp), u32, vp, u32, u32, vp, vp]
+        L.igs_serve_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         L.igs_horizon_plan.argtypes = [vp, u32, vp, u32, u32, u32, vp]
         L.igs_sync.argtypes = [vp]
         L.igs_submit_epoch.argtypes = [vp]
@@ -345,6 +350,40 @@ Context.stats = _stats
 Context.set_timing = _set_timing
 
 
+def _pack_trace(trace):
+    """igs_replay_item records (and the task words they point to) for a trace
+    of (context index, Task or None for an epoch, arrival ns)."""
+    n = len(trace)
+    words = np.zeros((max(1, n), TASK_WORDS), np.uint32)
+    items = np.zeros(max(1, n), dtype=np.dtype([("ctx", np.uint32), ("epoch", np.uint32), ("task", np.uint64),
+                                                 ("arrival", np.uint64)]))
+    base = words.ctypes.data
+    for k, (ci, task, t_ns) in enumerate(trace):
+        items[k]["ctx"] = ci
+        items[k]["arrival"] = int(t_ns)
+        if task is None:
+            items[k]["epoch"] = 1
+        else:
+            words[k] = task.flat()
+            items[k]["task"] = base + k * TASK_WORDS * 4
+    return words, items
+
+
+def replay_plain(ctxs: Sequence["Context"], trace, timeout_ms: int = 60000):
+    """igs_replay_plain: the served loop's comparator, one lowering launch per
+    item at its arrival on the item's (plain-mode) context. Returns (per-item
+    latency in ns, ns until the last launch completed)."""
+    n = len(trace)
+    words, items = _pack_trace(trace)
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.handle.value for c in ctxs])
+    lat = np.zeros(max(1, n), np.uint64)
+    wall = np.zeros(1, np.uint64)
+    r = lib().igs_replay_plain(arr, len(ctxs), items.ctypes.data, n, timeout_ms, lat.ctypes.data, wall.ctypes.data)
+    if r != IGS_OK:
+        raise IgsError(r, "replay_plain")
+    return lat[:n], int(wall[0])
+
+
 class Server:
     """Device-resident serving loop over attached contexts."""
 
@@ -359,6 +398,24 @@ class Server:
     def attach(self, ctx: Context, max_items: int) -> int:
         """IGS_OK, or the error code (e.g. -7 BUDGET) without raising."""
         return lib().igs_serve_attach(self._h, ctx.handle, max_items)
+
+    def enqueue(self, ctx: Context, max_items: int) -> bool:
+        """igs_serve_enqueue: attaches ctx now if it fits (True), else queues it
+        for admission after a detach (False). Raises on a context that could
+        never fit."""
+        adm = np.zeros(1, np.uint32)
+        r = lib().igs_serve_enqueue(self._h, ctx.handle, max_items, _p32(adm))
+        if r != IGS_OK:
+            raise IgsError(r, "serve_enqueue: " + lib().igs_last_error(ctx.handle).decode())
+        return bool(adm[0])
+
+    def stats(self) -> dict:
+        c = (ctypes.c_uint64 * 8)()
+        r = lib().igs_serve_stats(self._h, c)
+        if r != IGS_OK:
+            raise IgsError(r, "serve_stats")
+        return {"admitted": int(c[0]), "admitted_from_queue": int(c[1]), "waiting": int(c[2]),
+                "peak_waiting": int(c[3]), "slots_in_use": int(c[4]), "budget_bytes_in_use": int(c[5])}
 
     def start(self):
         r = lib().igs_serve_start(self._h)
@@ -380,29 +437,19 @@ class Server:
     def stop(self):
         lib().igs_serve_stop(self._h)
 
-    def replay(self, ctxs: Sequence[Context], trace, timeout_ms: int = 60000):
+    def replay(self, ctxs: Sequence[Context], trace, timeout_ms: int = 60000, detach: bool = False):
         """igs_serve_replay: trace = [(context index, Task or None for an
         epoch, arrival in ns since the call)] in arrival order. Returns
         (per-item latency in ns as a numpy array, ns until the last item was
-        taken)."""
+        taken). detach: each context is detached once its last item is taken
+        (admitting contexts that wait for admission; igs_serve_replay_ex)."""
         n = len(trace)
-        words = np.zeros((max(1, n), TASK_WORDS), np.uint32)
-        items = np.zeros(max(1, n), dtype=np.dtype([("ctx", np.uint32), ("epoch", np.uint32), ("task", np.uint64),
-                                                     ("arrival", np.uint64)]))
-        base = words.ctypes.data
-        for k, (ci, task, t_ns) in enumerate(trace):
-            items[k]["ctx"] = ci
-            items[k]["arrival"] = int(t_ns)
-            if task is None:
-                items[k]["epoch"] = 1
-            else:
-                words[k] = task.flat()
-                items[k]["task"] = base + k * TASK_WORDS * 4
+        words, items = _pack_trace(trace)
         arr = (ctypes.c_void_p * len(ctxs))(*[c.handle.value for c in ctxs])
         lat = np.zeros(max(1, n), np.uint64)
         wall = np.zeros(1, np.uint64)
-        r = lib().igs_serve_replay(self._h, arr, len(ctxs), items.ctypes.data, n, timeout_ms, lat.ctypes.data,
-                                   wall.ctypes.data)
+        r = lib().igs_serve_replay_ex(self._h, arr, len(ctxs), items.ctypes.data, n, timeout_ms,
+                                      1 if detach else 0, lat.ctypes.data, wall.ctypes.data)
         if r != IGS_OK:
             raise IgsError(r, "serve_replay")
         return lat[:n], int(wall[0])

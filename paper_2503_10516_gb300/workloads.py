@@ -232,6 +232,31 @@ def growing_program(rows_max: int = 256, cols: int = 64, nodes: int = 1, devices
     return Program(f"grow{rows_max}x{cols}", nodes, devices, horizon_step, lookahead, ops)
 
 
+def served_streams(count: int = 64, seed: int = 0x5EED + 5, lookahead: int = 0,
+                   max_elems: int = 1 << 27) -> List[Program]:
+    """Growing-row program streams for served lowering: each has one fp32
+    buffer, 2D (3 in 4 streams: 2048-8192 columns, 2048-16384 rows) or 1D
+    (4096-16384 elements), at most max_elems elements; its accessed prefix
+    grows by a random 1-64 rows per task (each task reads every earlier row).
+    Stream 0 has the largest buffer, 16384 x 8192 = 2^27 elements. One node,
+    two devices, two chunks per task."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        if i == 0:
+            rows, cols = 16384, 8192
+        elif rng.random() < 0.75:
+            cols = int(rng.choice([2048, 4096, 8192]))
+            rows = int(rng.choice([2048, 4096, 8192, 16384]))
+        else:
+            rows, cols = int(rng.choice([4096, 8192, 16384])), 1
+        while rows * cols > max_elems:
+            rows //= 2
+        out.append(growing_program(rows_max=rows, cols=cols, devices=2, chunks=2, lookahead=lookahead,
+                                   seed=int(seed * 1000 + i), grow=(1, 64)))
+    return out
+
+
 def listing2_program(n: int = 16, lookahead: int = 0, nodes: int = 1, devices: int = 1, chunks: int = 1) -> Program:
     """Listing 2: a one_to_one no_init write followed by a neighborhood({1,1}) read."""
     b = Buffer(2, (n, n, 1), 4, None, "u32")

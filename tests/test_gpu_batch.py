@@ -195,3 +195,39 @@ def test_bad_shape_is_rejected():
     for n in range(p.nodes):
         assert_same_graph(c.graph(n), ref[n], f"{p.name} node {n}")
     c.close()
+
+
+def test_batch_full_task_counts_seeded_subset():
+    """The benchmark's batch at full task counts (10-2000 tasks per program):
+    four programs picked by a seeded permutation among those the oracle
+    lowers in seconds (nodes x tasks x chunks < 2e6) are lowered in one
+    launch; every node's graph equals the oracle's."""
+    import numpy as np
+    from paper_2503_10516_gb300 import igs
+    full = W.batch_programs(count=512, scale=1.0)
+    perm = np.random.default_rng(0x5EED + 31).permutation(len(full))
+    cost = [p.nodes * len(p.tasks) * max(t.chunks for t in p.tasks) for p in full]
+    picked = [int(i) for i in perm if cost[i] < 2e6][:4]
+    progs = [full[i] for i in picked]
+    assert min(len(p.tasks) for p in progs) >= 100
+    refs = [oracle_graphs(p) for p in progs]
+    ctxs = []
+    for p, (ref, _) in zip(progs, refs):
+        counts = {k: max(len(g[k]) for g in ref) for k in ("instrs", "edges", "boxes")}
+        c = igs.Context(p.nodes, p.devices, p.horizon_step, p.lookahead, mode=igs.MODE_BATCHED,
+                        **igs.small_caps(p, counts))
+        for op in p.ops:
+            if op[0] == "buffer":
+                b = op[1]
+                c.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init)
+            elif op[0] == "task":
+                c.submit(op[1])
+            elif op[0] == "flush":
+                c.submit_epoch()
+        ctxs.append(c)
+    igs.lower_batch(ctxs, (152, igs.ORDER_LONGEST_FIRST, 4, 2))
+    for p, c, (ref, rej) in zip(progs, ctxs, refs):
+        assert c.rejected() == rej
+        for n in range(p.nodes):
+            assert_same_graph(c.graph(n), ref[n], f"{p.name} node {n} (full task counts)")
+        c.close()

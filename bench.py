@@ -169,7 +169,7 @@ def _submit_program(c, p):
             c.submit_epoch()
 
 
-def _full_scale_caps(igs, small, full, stream, margin=2.0):
+def _full_scale_caps(igs, small, full, stream, margin=3.0):
     """Capacities for each full-scale program: its prefix at a small task
     scale is lowered first (its tasks are the first tasks of the full
     program); the largest per-node instruction, edge and box counts (binds
@@ -194,9 +194,11 @@ def _full_scale_caps(igs, small, full, stream, margin=2.0):
 
 
 def _doubled(cp):
-    """Capacities with the output arrays and scratch tables doubled."""
-    return dict(cp, max_instructions=2 * cp["max_instructions"], max_edges=2 * cp["max_edges"],
-                max_boxes=2 * cp["max_boxes"], scratch_capacity=2 * cp["scratch_capacity"])
+    """Capacities with every array doubled (outputs, region-map heap, scratch
+    tables, allocations, queue)."""
+    keys = ("max_instructions", "max_edges", "max_boxes", "map_heap", "scratch_capacity", "max_live_allocs",
+            "max_allocations", "max_queue")
+    return dict(cp, **{k: 2 * cp[k] for k in keys if k in cp})
 
 
 def measure_batched(igs, torch, stream, count=512, scale=1.0, tune_scale=0.02, subset_every=16):
@@ -239,6 +241,8 @@ def measure_batched(igs, torch, stream, count=512, scale=1.0, tune_scale=0.02, s
                     c.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init)
         return ctxs
 
+    shortfalls = []
+
     def batched_run(progs, cps, shp, attempts=4):
         """One launch over all programs; a context whose capacity estimate fell
         short gets doubled output capacities and the launch is repeated (only
@@ -258,8 +262,9 @@ def measure_batched(igs, torch, stream, count=512, scale=1.0, tune_scale=0.02, s
                 for i, c in enumerate(ctxs):
                     try:
                         c.sync()
-                    except igs.IgsError:
+                    except igs.IgsError as e:
                         short.append(i)
+                        shortfalls.append(str(e).split(": ", 2)[-1])
                 for c in ctxs:
                     c.close()
                 for i in short:
@@ -270,8 +275,9 @@ def measure_batched(igs, torch, stream, count=512, scale=1.0, tune_scale=0.02, s
             for c in ctxs:
                 c.close()
             return {"instr_per_s": instrs / dt, "tasks_per_s": sum(len(p.tasks) for p in progs) / dt,
-                    "seconds": dt, "instructions": instrs, "launches": launches, "attempts": attempt + 1}
-        return {"error": f"capacity estimates still short after {attempts} attempts"}
+                    "seconds": dt, "instructions": instrs, "launches": launches, "attempts": attempt + 1,
+                    "capacity_shortfalls_before": shortfalls[:8]}
+        return {"error": f"capacity estimates still short after {attempts} attempts", "shortfalls": shortfalls[:8]}
 
     res["batched_all"] = batched_run(full, caps, shape)
     sub = list(range(0, count, subset_every))
@@ -465,6 +471,40 @@ def measure_box_copy(igs, torch, stream, reps=20):
         out[name] = {"ms": ms, "bytes": byts, "gbs": byts / (ms * 1e-3) / 1e9, "checked": ok}
         del dst
     del src
+    return out
+
+
+def measure_halo_copies(igs, torch, stream, jobs_n=256, reps=20):
+    """Halo-shaped box copies (single 8192-column fp32 rows, 32 KiB, the
+    wave program's halo exchanges) between two 1024 x 8192 allocations:
+    `jobs_n` rows in one box-copy launch, in launches of 32 jobs, and one job
+    per launch. Bytes = read + written; the allocations are L2-resident, as
+    freshly written halo rows are in the step."""
+    rows, cols = 1024, 8192
+    src = torch.arange(rows * cols, dtype=torch.float32, device="cuda")
+    dst = torch.zeros(rows * cols, dtype=torch.float32, device="cuda")
+    box = (0, 0, 0, rows, cols, 1)
+    jobs = [(src.data_ptr(), box, dst.data_ptr(), box, (r, 0, 0, r + 1, cols, 1), 4)
+            for r in range(0, 4 * jobs_n, 4)]
+    out = {}
+    for name, per in (("one_launch", jobs_n), ("32_per_launch", 32), ("one_per_launch", 1)):
+        for _ in range(2):
+            for k in range(0, jobs_n, per):
+                igs.box_copy(jobs[k:k + per], stream.cuda_stream)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            for k in range(0, jobs_n, per):
+                igs.box_copy(jobs[k:k + per], stream.cuda_stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / reps
+        byts = 2.0 * jobs_n * cols * 4
+        out[name] = {"launches": (jobs_n + per - 1) // per, "ms": ms, "gbs": byts / (ms * 1e-3) / 1e9}
+    ok = bool(torch.equal(dst.view(rows, cols)[::4][:jobs_n], src.view(rows, cols)[::4][:jobs_n]))
+    out.update({"jobs": jobs_n, "bytes_per_job": cols * 4, "checked": ok})
+    del src, dst
     return out
 
 
@@ -931,14 +971,15 @@ def run_gpu(args):
     def section(fn, *a):
         """An auxiliary measurement; a failure is recorded in the line instead
         of ending the run."""
-        if world != 1:
+        if world != 1 or args.headline_only:
             return None
         try:
             return fn(*a)
         except Exception as e:  # noqa: BLE001
             return {"error": f"{type(e).__name__}: {e}"}
 
-    big_copy = measure_box_copy(igs, torch, stream)
+    big_copy = section(measure_box_copy, igs, torch, stream)
+    halo = section(measure_halo_copies, igs, torch, stream)
     executors = section(measure_executors, igs, torch, sh, prog, make_ctx)
     nbody = section(measure_nbody, igs, torch, sh)
     jacobi = section(measure_jacobi, igs, torch, sh)
@@ -949,7 +990,7 @@ def run_gpu(args):
 
     # ---- CPU baseline: the oracle on bounded samples of the same workloads
     cpu, cpu_batch = None, None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.headline_only:
         try:
             cpu, cpu_batch = cpu_baselines()
         except Exception as e:  # noqa: BLE001
@@ -975,7 +1016,12 @@ def run_gpu(args):
                          "p50_task_ms": p50, "p99_task_ms": p99,
                          "batched_ms_per_task": lower_ms / STEPS},
             "box_copy_gbs": (copy_bytes / (copy_ms * 1e-3) / 1e9) if copy_ms else None,
-            "box_copy_resize_512MiB": {k: dict(v, frac=v["gbs"] / hbm) for k, v in big_copy.items()},
+            "halo_copies": halo,
+            "in_step_launches": {"lowering": stats[0]["lower_launches"], "box_copy": stats[0]["copy_launches"],
+                                 "stencil_or_level": stats[0]["workload_launches"],
+                                 "note": "a level with copies and stencils runs as one level launch"},
+            "box_copy_resize_512MiB": ({k: (dict(v, frac=v["gbs"] / hbm) if "gbs" in v else v)
+                                        for k, v in big_copy.items()} if isinstance(big_copy, dict) else None),
             "executors": executors,
             "nbody": nbody,
             "jacobi": jacobi,
@@ -996,8 +1042,31 @@ def run_gpu(args):
 def run_profile_case(args):
     """Small fixed cases for profiler captures (no timing, no JSON metric):
     flow_wave16 = the first 16 wave tasks on 8192^2 buffers, lowered, then
-    executed by the dataflow executor; done twice (capture the second)."""
+    executed by the dataflow executor; done twice (capture the second).
+    lower_wave64 = the first 64 tasks of the benchmark's wave program lowered
+    in one launch (the lowering kernel's configuration inside the timed step,
+    without the concurrent execution); done twice (capture the second)."""
     from paper_2503_10516_gb300 import igs
+    if args.profile_case == "lower_wave64":
+        p = _program_shape()
+        p.ops = [op for op in p.ops if op[0] == "buffer"] + [op for op in p.ops if op[0] == "task"][:64]
+        for _ in range(2):
+            c = igs.Context(p.nodes, p.devices, p.horizon_step, p.lookahead, mode=igs.MODE_BATCHED)
+            for op in p.ops:
+                if op[0] == "buffer":
+                    b = op[1]
+                    c.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, None if b.init is None else
+                                    np.zeros((N, N), np.float32))
+                elif op[0] == "task":
+                    c.submit(op[1])
+            c.sync()
+            n = int(c.counters()["instructions"])
+            cnt = c.counters()
+            c.close()
+        print(json.dumps({"case": args.profile_case, "tasks": 64, "instructions": n, "edges": int(cnt["edges"]),
+                          "boxes": int(cnt["boxes"]), "map_reads": int(cnt["map_reads"]),
+                          "map_writes": int(cnt["map_writes"])}), flush=True)
+        return 0
     p = W.wave_program(n=N, steps=16, nodes=NODES, devices=DEVICES, chunks=CHUNKS, lookahead=LOOKAHEAD,
                        horizon_step=HSTEP)
     for _ in range(2):
@@ -1023,7 +1092,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="igs", choices=["igs", "reference"])
-    ap.add_argument("--profile-case", default=None, choices=["flow_wave16"],
+    ap.add_argument("--headline-only", action="store_true",
+                    help="print the line without the auxiliary sections (for a launch-list capture of the step)")
+    ap.add_argument("--profile-case", default=None, choices=["flow_wave16", "lower_wave64"],
                     help="run one small fixed case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
     if args.profile_case:

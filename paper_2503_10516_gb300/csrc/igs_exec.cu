@@ -534,6 +534,27 @@ __global__ void __launch_bounds__(256) stencil_kernel(const KernelJob* __restric
                           (uint64_t)gridDim.x * blockDim.x);
 }
 
+// One level of the level executor in one launch: the level's stencil jobs
+// (grid rows 0 .. n_sjobs-1, as stencil_kernel) and its box-copy units (the
+// grid rows after them, walked as box_copy_kernel walks its units). The
+// instructions of one level never depend on one another (a dependency puts
+// its successor on a later level), so copies and stencils may run together.
+__global__ void __launch_bounds__(256) level_kernel(const KernelJob* __restrict__ sjobs, uint32_t n_sjobs,
+                                                    const CopyJob* __restrict__ cjobs, uint32_t n_cjobs,
+                                                    uint64_t n_units) {
+  if (blockIdx.y < n_sjobs) {
+    const KernelJob& J = sjobs[blockIdx.y];
+    stencil_range<LdStream>(J, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, stencil_groups(J),
+                            (uint64_t)gridDim.x * blockDim.x);
+    return;
+  }
+  const uint64_t nb = (uint64_t)(gridDim.y - n_sjobs) * gridDim.x;
+  for (uint64_t u = (uint64_t)(blockIdx.y - n_sjobs) * gridDim.x + blockIdx.x; u < n_units; u += nb) {
+    const uint32_t j = find_job(cjobs, n_cjobs, u);
+    copy_unit<LdStream>(cjobs[j], u - cjobs[j].unit_begin);
+  }
+}
+
 // ---- dataflow executor -----------------------------------------------------
 //
 // Out-of-order execution of an instruction graph (Sec. 3.7 / 4.1: an
@@ -707,6 +728,22 @@ int igs_launch_stencil(const igs::KernelJob* jobs_dev, uint32_t n_jobs, uint64_t
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+int igs_launch_level(const igs::KernelJob* sjobs_dev, uint32_t n_sjobs, uint64_t max_items,
+                     const igs::CopyJob* cjobs_dev, uint32_t n_cjobs, uint64_t n_units, void* stream) {
+  if (n_sjobs == 0 && n_units == 0) return 0;
+  const uint64_t per_job_blocks = (max_items / 4 + 255) / 256;
+  const uint32_t gx = (uint32_t)(per_job_blocks < 64 ? (per_job_blocks ? per_job_blocks : 1) : 64);
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t want = (uint64_t)sms * 8;  // copy blocks, as igs_launch_copies
+  const uint64_t cb = n_units < want ? n_units : want;
+  const uint64_t crows = (cb + gx - 1) / gx;
+  if (n_sjobs + crows > 65535) return -1;
+  dim3 grid(gx, (uint32_t)(n_sjobs + crows));
+  igs::level_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(sjobs_dev, n_sjobs, cjobs_dev, n_cjobs, n_units);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 int igs_launch_copies(const igs::CopyJob* jobs_dev, uint32_t n_jobs, uint64_t n_units, void* stream) {
   if (n_units == 0) return 0;
   int dev = 0, sms = 152;

@@ -80,6 +80,11 @@ void igs_exec_preload();
 int igs_launch_workload(const igs::KernelJob* jobs_dev, uint32_t n_jobs, uint64_t n_items, void* stream);
 // 5-point stencil jobs (Jacobi / wave), pre-validated by the host; n_jobs <= 65535.
 int igs_launch_stencil(const igs::KernelJob* jobs_dev, uint32_t n_jobs, uint64_t max_items, void* stream);
+// One level's stencil jobs and box-copy units in one launch (they are
+// independent by construction of the levels). -1 when the grid would exceed
+// 65535 rows (the caller then launches them separately).
+int igs_launch_level(const igs::KernelJob* sjobs_dev, uint32_t n_sjobs, uint64_t max_items,
+                     const igs::CopyJob* cjobs_dev, uint32_t n_cjobs, uint64_t n_units, void* stream);
 // Execution error flags (0 = none; bit 0: a workload kernel met an index
 // outside its allocation, bit 1: a dataflow launch gave up waiting);
 // optionally clears them.

@@ -274,7 +274,7 @@ void ev_collect(igs_ctx* c) {
 // with more than one device only).
 int ensure_helpers(igs_ctx* c) {
   if (c->d_helpers || c->D < 2) return IGS_OK;
-  const size_t per = (size_t)kMaxWorkers * kHelperTables * c->nodes_host[0].cap_scratch * F_COUNT;
+  const size_t per = (size_t)kScratchSets * kHelperTables * c->nodes_host[0].cap_scratch * F_COUNT;
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaMalloc((void**)&c->d_helpers, sizeof(uint32_t) * per * c->N));
   for (uint32_t n = 0; n < c->N; ++n) {
@@ -1154,21 +1154,33 @@ int run_pending(igs_ctx* c, Pending& p, cudaStream_t s, bool wait) {
   }
   for (size_t L = 0; L < p.levels.size(); ++L) {
     LevelWork& w = p.levels[L];
-    if (!w.copies.empty()) {
+    // a level with both copies and stencil jobs runs as one launch (its
+    // instructions are independent of one another); its time counts as
+    // workload time and its copy bytes are not in copy_bytes
+    if (!w.copies.empty() && !w.stencils.empty() && w.stencils.size() + 2048 <= 65535) {
       const size_t ev = c->timing ? ev_begin(c, s) : 0;
-      if (igs_launch_copies(c->d_cjobs[k] + co[L], (uint32_t)w.copies.size(), w.copy_units, s))
-        return fail_ctx(c, IGS_ERR_CUDA, "box copy launch");
-      if (c->timing) ev_end(c, 1, ev, s);
-      c->n_launch[1]++;
-      for (const CopyJob& j : w.copies) c->copy_bytes += 2.0 * j.extent[0] * j.extent[1] * j.extent[2];
-    }
-    for (size_t first = 0; first < w.stencils.size(); first += 65535) {
-      const uint32_t n = (uint32_t)std::min<size_t>(65535, w.stencils.size() - first);
-      const size_t ev = c->timing ? ev_begin(c, s) : 0;
-      if (igs_launch_stencil(c->d_kjobs[k] + so[L] + first, n, w.stencil_max, s))
-        return fail_ctx(c, IGS_ERR_CUDA, "stencil launch");
+      if (igs_launch_level(c->d_kjobs[k] + so[L], (uint32_t)w.stencils.size(), w.stencil_max, c->d_cjobs[k] + co[L],
+                           (uint32_t)w.copies.size(), w.copy_units, s))
+        return fail_ctx(c, IGS_ERR_CUDA, "level launch");
       if (c->timing) ev_end(c, 2, ev, s);
       c->n_launch[2]++;
+    } else {
+      if (!w.copies.empty()) {
+        const size_t ev = c->timing ? ev_begin(c, s) : 0;
+        if (igs_launch_copies(c->d_cjobs[k] + co[L], (uint32_t)w.copies.size(), w.copy_units, s))
+          return fail_ctx(c, IGS_ERR_CUDA, "box copy launch");
+        if (c->timing) ev_end(c, 1, ev, s);
+        c->n_launch[1]++;
+        for (const CopyJob& j : w.copies) c->copy_bytes += 2.0 * j.extent[0] * j.extent[1] * j.extent[2];
+      }
+      for (size_t first = 0; first < w.stencils.size(); first += 65535) {
+        const uint32_t n = (uint32_t)std::min<size_t>(65535, w.stencils.size() - first);
+        const size_t ev = c->timing ? ev_begin(c, s) : 0;
+        if (igs_launch_stencil(c->d_kjobs[k] + so[L] + first, n, w.stencil_max, s))
+          return fail_ctx(c, IGS_ERR_CUDA, "stencil launch");
+        if (c->timing) ev_end(c, 2, ev, s);
+        c->n_launch[2]++;
+      }
     }
     if (!w.kernels.empty()) {
       const size_t ev = c->timing ? ev_begin(c, s) : 0;

@@ -47,6 +47,9 @@ struct Table {
 // and the scratch tables of each helper.
 constexpr uint32_t kMaxWorkers = 8;
 constexpr uint32_t kHelperTables = 12;
+// Scratch sets in a node's helper scratch: one per worker, plus one for the
+// front warp that runs push / await push ahead of warp 0 (pipelined launches).
+constexpr uint32_t kScratchSets = kMaxWorkers + 1;
 
 // Size classes of the per-node entry heap: 32 << k entries.
 constexpr int kHeapClasses = 24;
@@ -104,7 +107,7 @@ struct NodeDev {
   // scratch tables for the warp
   uint32_t* scratch_base;  // 14 tables of cap_scratch entries
   // scratch of the warps that share parts of the lowering when a node is
-  // lowered by several warps (kMaxWorkers x kHelperTables tables of
+  // lowered by several warps (kScratchSets x kHelperTables tables of
   // cap_scratch entries), or null
   uint32_t* helper_scratch;
 };

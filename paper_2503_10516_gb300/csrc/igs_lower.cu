@@ -236,6 +236,7 @@ struct Ctx {
   // item compiled straight from delivery: its chunks and mapped boxes are
   // still in S_CH / S_MP and it is known not to allocate (NONE otherwise)
   uint32_t fresh;
+  struct Pipe* pipe;  // the block's pipeline with a front warp (warp 0 only), else null
 };
 
 // Instructions a coherence worker emits before their final ids are known:
@@ -469,14 +470,25 @@ __device__ __forceinline__ bool t_claim_ok(Ctx& c, Table& t, bool pred, uint32_t
 }
 // Claims k consecutive slots per lane; returns this lane's first slot.
 __device__ __forceinline__ uint32_t t_claim_n(Ctx& c, Table& t, uint32_t k) {
-  uint32_t x = k;
+  uint32_t excl, total;
+  if (!__any_sync(FULL, k >= 8u)) {
+    // counts below 8 (box pieces): prefix sums from three bit-plane ballots
+    const uint32_t lt = lanemask_lt();
+    const uint32_t b0 = __ballot_sync(FULL, k & 1u), b1 = __ballot_sync(FULL, k & 2u),
+                   b2 = __ballot_sync(FULL, k & 4u);
+    excl = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
+    total = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
+  } else {
+    uint32_t x = k;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(FULL, x, o);
-    if ((int)laneid() >= o) x += y;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, x, o);
+      if ((int)laneid() >= o) x += y;
+    }
+    total = __shfl_sync(FULL, x, 31);
+    excl = x - k;
   }
-  const uint32_t total = __shfl_sync(FULL, x, 31);
-  const uint32_t first = t.n + x - k;
+  const uint32_t first = t.n + excl;
   if (t.n + total > t.cap && !t_grow(c, t, t.n + total)) return NONE;
   t.n += total;
   t.live += total;
@@ -847,6 +859,17 @@ __device__ __forceinline__ void t_make_disjoint(Ctx& c, Table& t, uint32_t val =
 __device__ __noinline__ uint32_t canonical_impl(Ctx& c, const Table& in, uint32_t from, uint32_t to, Table& out);
 __device__ uint32_t canonical(Ctx& c, const Table& in, uint32_t from, uint32_t to, Table& out) {
   PhaseTimer pt = pt_start();
+  if (to == from + 1) {
+    // one box is its own canonical form (none if it is dead or empty)
+    const Ent e = t_ent(in, from);
+    if (e.key == DEAD || bx_empty(e.b)) return 0;
+    uint32_t s;
+    if (!t_claim_ok(c, out, laneid() == 0, s)) return 0;
+    if (laneid() == 0) t_put(out, s, 0, e.b, 0, 0, 0);
+    __syncwarp();
+    pt_lap(pt, c, PH_CANON);
+    return 1;
+  }
   const uint32_t r = canonical_impl(c, in, from, to, out);
   pt_lap(pt, c, PH_CANON);
   return r;
@@ -1722,24 +1745,35 @@ __device__ __noinline__ bool map_ids(Ctx& c, Table& T, uint32_t h, bool writers 
   return any;
 }
 
+// Live entries above which a table whose ids changed is re-merged when a
+// horizon is applied (smaller tables are only compacted: merging is a matter
+// of table size, not of content, and costs a scan per entry).
+#ifndef IGS_EPOCH_MERGE_FLOOR
+#define IGS_EPOCH_MERGE_FLOOR 16
+#endif
+
 __device__ __noinline__ void apply_epoch(Ctx& c, uint32_t h) {
   for (uint32_t li = 0; li < c.n_live; ++li) {
     const uint32_t aid = c.nd->live[li];
     // tables whose ids all stay are left as they are; the others are
-    // re-merged (a matter of table size, not of content)
+    // compacted and, above the floor, re-merged
     Table WR = wr_t(c, aid);
     if (map_ids(c, WR, h, true)) {
       t_compact(c, WR);
-      t_merge_from(c, WR, 0);
-      t_compact(c, WR);
+      if (WR.live > IGS_EPOCH_MERGE_FLOOR) {
+        t_merge_from(c, WR, 0);
+        t_compact(c, WR);
+      }
       t_set_mark(c, WR);
     }
     Table RD = rd_t(c, aid);
     if (map_ids(c, RD, h)) {
       t_make_disjoint(c, RD, h);
       t_compact(c, RD);
-      t_merge_from(c, RD, 0);
-      t_compact(c, RD);
+      if (RD.live > IGS_EPOCH_MERGE_FLOOR) {
+        t_merge_from(c, RD, 0);
+        t_compact(c, RD);
+      }
       t_set_mark(c, RD);
     }
     if (c.err) return;
@@ -2004,10 +2038,32 @@ struct WorkJob {
   uint32_t n_live;   // coherence: live allocations (NodeDev's count is stale during a launch)
 };
 
+// Pipelined lowering of one node (a launch with several items): a front
+// warp (warp kFrontWarp, its own scratch set) runs the node-level step of
+// each task ahead of warp 0 — chunks, the overlapping-write check and push /
+// await push (a3), which read and update only the node's ownership tables —
+// and stages the task's push / await regions in one of kPipeDepth slots;
+// warp 0 (the back) takes a slot when it delivers that item. Instruction-
+// level state is warp 0's alone, so the lowered graph is unchanged.
+constexpr uint32_t kPipeDepth = 4;
+constexpr uint32_t kPipeMinItems = 4;  // fewer items per launch: no front warp
+constexpr uint32_t kFrontWarp = kMaxWorkers;
+struct Pipe {
+  volatile uint32_t front_done;  // items the front warp has finished (absolute index)
+  volatile uint32_t back_done;   // items warp 0 has delivered
+  volatile uint32_t abort;       // set by either side when it stops early
+  volatile uint32_t err, err_info;
+  volatile uint32_t rejected[kPipeDepth];  // the slot's task had overlapping writes
+  volatile uint32_t n[kPipeDepth];         // push / await entries staged in the slot
+  uint32_t begin, end;                     // the items this launch lowers
+};
+
 struct BlockShared {
   int lock;
   volatile uint32_t cmd, err, err_info;
   WorkJob job;
+  uint32_t piped;
+  Pipe pipe;
 };
 
 __device__ __forceinline__ void worker_bar(uint32_t workers) {
@@ -3520,6 +3576,37 @@ __device__ __noinline__ void record_queued_reqs(Ctx& c, const igs_task& t, uint3
 // Scheduler lookahead (Sec. 4.3): a task is queued while an allocating task
 // is queued; the queue is compiled when it holds more than `lookahead` tasks,
 // at an epoch, or when a buffer is destroyed.
+// The node-level ownership table of a new buffer: the whole buffer owned by
+// user memory (host data) or by no one, replicated on every node.
+__device__ void own_create(Ctx& c, const Item& it) {
+  if (it.arg >= c.nd->cap_buffers) {
+    fail_cap(c, CAP_BUFFERS, c.nd->cap_buffers);
+    return;
+  }
+  const BufDesc& bd = buf_of(c, it.arg);
+  if (!table_new(c, c.nd->own_d + kDesc * it.arg, 32)) return;
+  Table O = own_t(c, it.arg);
+  const uint32_t s = t_claim(c, O, laneid() == 0);
+  if (c.err) return;
+  if (laneid() == 0) t_put(O, s, 0, buffer_box(bd), bd.init ? HOST : NONE, 0xFFFFFFFFu, 0);
+  __syncwarp();
+}
+
+// Warp 0 of a pipelined launch: the push / await regions the front warp
+// staged for this item are appended to the QR table (as a3_task appends its
+// own).
+__device__ void pipe_take(Ctx& c, uint32_t item) {
+  const uint32_t slot = item % kPipeDepth, cnt = c.pipe->n[slot];
+  if (cnt == 0) return;
+  const uint32_t* src = helper_table(c.nd, kFrontWarp, 8 + slot);
+  const uint32_t first = __shfl_sync(FULL, t_claim_n(c, c.qr, laneid() == 0 ? cnt : 0u), 0);  // lane 0's slot
+  if (c.err) return;
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  uint4* d4 = reinterpret_cast<uint4*>(c.qr.base + (size_t)first * F_COUNT);
+  for (uint32_t k = laneid(); k < cnt * (F_COUNT / 4); k += 32) d4[k] = s4[k];
+  __syncwarp();
+}
+
 __device__ __noinline__ void deliver(Ctx& c, uint32_t item) {
   const Item it = c.pg->items[item];
   maintain(c);
@@ -3532,18 +3619,9 @@ __device__ __noinline__ void deliver(Ctx& c, uint32_t item) {
     if (c.q_count > 0 && queued_tasks(c) > c.lookahead) flush_queue(c);
     return;
   }
-  if (it.kind == IT_CREATE) {
-    if (it.arg >= c.nd->cap_buffers) {
-      fail_cap(c, CAP_BUFFERS, c.nd->cap_buffers);
-      return;
-    }
-    const BufDesc& bd = buf_of(c, it.arg);
-    if (!table_new(c, c.nd->own_d + kDesc * it.arg, 32)) return;
-    Table O = own_t(c, it.arg);
-    const uint32_t s = t_claim(c, O, laneid() == 0);
+  if (it.kind == IT_CREATE && !c.pipe) {  // pipelined: the front warp creates it
+    own_create(c, it);
     if (c.err) return;
-    if (laneid() == 0) t_put(O, s, 0, buffer_box(bd), bd.init ? HOST : NONE, 0xFFFFFFFFu, 0);
-    __syncwarp();
   }
   bool alloc_now = false;
   if (it.kind == IT_TASK) {
@@ -3555,7 +3633,9 @@ __device__ __noinline__ void deliver(Ctx& c, uint32_t item) {
     task_mapped(c, t, CH, MP);
     if (c.err) return;
     pt_lap(pt, c, PH_SPLIT);
-    const bool bad = overlapping_writes(c, t, CH, MP);
+    // pipelined: the front warp has checked the task and staged its push /
+    // await regions
+    const bool bad = c.pipe ? c.pipe->rejected[item % kPipeDepth] != 0 : overlapping_writes(c, t, CH, MP);
     pt_lap(pt, c, PH_OVERLAP);
     if (bad) {
       if (c.n_rej < c.nd->cap_rej) {
@@ -3565,7 +3645,8 @@ __device__ __noinline__ void deliver(Ctx& c, uint32_t item) {
       }
       return;
     }
-    a3_task(c, t, it.seq, CH, MP);
+    if (c.pipe) pipe_take(c, item);
+    else a3_task(c, t, it.seq, CH, MP);
     if (c.err) return;
     pt_lap(pt, c, PH_A3);
     if (c.q_count == 0) alloc_now = allocating(c, t, it.seq, CH, MP);
@@ -3599,7 +3680,7 @@ __device__ __noinline__ void deliver(Ctx& c, uint32_t item) {
     if (it.kind == IT_EPOCH || it.kind == IT_DESTROY || queued_tasks(c) > c.lookahead) flush_queue(c);
   }
   if (c.err) return;
-  if (it.kind == IT_DESTROY) table_free(c, c.nd->own_d + kDesc * it.arg);
+  if (it.kind == IT_DESTROY && !c.pipe) table_free(c, c.nd->own_d + kDesc * it.arg);
 }
 
 __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg) {
@@ -3649,6 +3730,7 @@ __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg) {
   c.stage = nullptr;
   c.helper = false;
   c.fresh = NONE;
+  c.pipe = nullptr;
 }
 
 __device__ void store_ctx(Ctx& c, uint32_t cursor) {
@@ -3701,8 +3783,94 @@ __device__ __noinline__ void publish_progress(const Ctx& c, volatile uint32_t* p
   __syncwarp();
 }
 
+// Waits (every lane polls) until ready() holds; false when the other side
+// of the pipeline stopped (taking its error, if any) or after about 30 s
+// (ST_TIMEOUT, and the other side is told to stop).
+template <class F>
+__device__ bool pipe_wait(Ctx& c, Pipe& P, F ready) {
+  for (uint32_t spins = 0;; ++spins) {
+    if (__any_sync(FULL, P.abort != 0)) {
+      if (P.err != ST_OK && c.err == ST_OK) {
+        c.err = P.err;
+        c.err_info = P.err_info;
+      }
+      return false;
+    }
+    if (__all_sync(FULL, ready())) break;
+    if (spins > (1u << 28)) {
+      fail(c, ST_TIMEOUT);
+      __syncwarp();
+      if (laneid() == 0) {
+        P.err = ST_TIMEOUT;
+        __threadfence_block();
+        P.abort = 1;
+      }
+      __syncwarp();
+      return false;
+    }
+    __nanosleep(100);
+  }
+  __threadfence_block();
+  return true;
+}
+
+// The front warp of a pipelined launch (see Pipe): items [begin, end) of one
+// node, at most kPipeDepth ahead of warp 0.
+__device__ void front_loop(BlockShared& sh, const Unit u) {
+  Pipe& P = sh.pipe;
+  Ctx f;
+  load_ctx(f, u.node, u.prog);
+  f.err = ST_OK;
+  f.lock = &sh.lock;
+  f.helper = true;
+  const uint32_t cap = u.node->cap_scratch;
+  const int used[8] = {S_CH, S_MP, S_T0, S_T1, S_T2, S_T3, S_T4, S_CAN};
+  for (int k = 0; k < 14; ++k) f.s[k] = scratch_table(nullptr, 0);  // tables the front never uses
+  for (int k = 0; k < 8; ++k) f.s[used[k]] = scratch_table(helper_table(u.node, kFrontWarp, k), cap);
+  for (uint32_t i = P.begin; i < P.end && f.err == ST_OK; ++i) {
+    if (!pipe_wait(f, P, [&]() { return i - P.back_done < kPipeDepth; })) break;
+    const uint32_t slot = i % kPipeDepth;
+    f.qr = scratch_table(helper_table(u.node, kFrontWarp, 8 + slot), cap);
+    uint32_t rejected = 0;
+    const Item it = f.pg->items[i];
+    if (it.kind == IT_CREATE) {
+      own_create(f, it);
+    } else if (it.kind == IT_TASK) {
+      const igs_task& t = f.pg->tasks[it.task];
+      task_chunks(f, t, f.s[S_CH]);
+      task_mapped(f, t, f.s[S_CH], f.s[S_MP]);
+      if (f.err == ST_OK) {
+        if (overlapping_writes(f, t, f.s[S_CH], f.s[S_MP])) rejected = 1;
+        else a3_task(f, t, it.seq, f.s[S_CH], f.s[S_MP]);
+      }
+    } else if (it.kind == IT_DESTROY) {
+      table_free(f, f.nd->own_d + kDesc * it.arg);
+    }
+    if (f.err != ST_OK) break;
+    __syncwarp();
+    if (laneid() == 0) {
+      P.rejected[slot] = rejected;
+      P.n[slot] = f.qr.n;
+      __threadfence_block();
+      P.front_done = i + 1;
+    }
+    __syncwarp();
+  }
+  if (laneid() == 0) {
+    if (f.err != ST_OK) {
+      P.err_info = f.err_info;
+      P.err = f.err;
+      __threadfence_block();
+      P.abort = 1;
+    }
+    atomicAdd(reinterpret_cast<unsigned long long*>(&u.node->map_reads), (unsigned long long)f.map_reads);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&u.node->map_writes), (unsigned long long)f.map_writes);
+  }
+  __syncwarp();
+}
+
 __device__ void lower_unit(const Unit* units, uint32_t n_units, uint32_t max_items, uint32_t w,
-                           volatile uint32_t* progress, BlockShared* sh, uint32_t workers) {
+                           volatile uint32_t* progress, BlockShared* sh, uint32_t workers, Pipe* pipe = nullptr) {
   if (w >= n_units) return;
   const Unit u = units[w];
   Ctx c;
@@ -3716,12 +3884,38 @@ __device__ void lower_unit(const Unit* units, uint32_t n_units, uint32_t max_ite
   const uint32_t avail = *u.prog->n_items;
   uint32_t end = avail;
   if (max_items != NONE && cursor + max_items < end) end = cursor + max_items;
+  if (pipe) {  // the same items as the front warp
+    c.pipe = pipe;
+    cursor = pipe->begin;
+    end = pipe->end;
+  }
   volatile uint32_t* pr = progress ? progress + (size_t)w * PR_WORDS : nullptr;
   PhaseTimer pt = pt_start();
   while (cursor < end && c.err == ST_OK) {
+    if (pipe && !pipe_wait(c, *pipe, [&]() { return pipe->front_done > cursor; })) break;
     deliver(c, cursor);
     ++cursor;
+    if (pipe) {
+      __syncwarp();
+      if (laneid() == 0) {
+        __threadfence_block();
+        pipe->back_done = cursor;  // the item's slot is free again
+      }
+      __syncwarp();
+    }
     if (pr) publish_progress(c, pr, cursor);
+  }
+  if (pipe) {  // the front warp leaves any wait
+    __syncwarp();
+    if (laneid() == 0) {
+      if (c.err != ST_OK && pipe->err == ST_OK) {
+        pipe->err_info = c.err_info;
+        pipe->err = c.err;
+      }
+      __threadfence_block();
+      pipe->abort = 1;
+    }
+    __syncwarp();
   }
   pt_lap(pt, c, PH_TOTAL);
   store_ctx(c, cursor);
@@ -3742,10 +3936,33 @@ __global__ void __launch_bounds__(kReserveThreads) lower_kernel(const Unit* unit
     sh.lock = 0;
     sh.cmd = CMD_NONE;
     sh.err = ST_OK;
+    sh.piped = 0;
+    // a front warp when the block has one, the node has its scratch set and
+    // the launch lowers several items
+    if (nw > kFrontWarp && blockIdx.x < n_units) {
+      const Unit u = units[blockIdx.x];
+      const NodeDev* nd = u.node;
+      if (nd->helper_scratch && nd->status == ST_OK) {
+        const uint32_t cur = nd->cursor, avail = *u.prog->n_items;
+        uint32_t end = avail;
+        if (max_items != NONE && cur + max_items < end) end = cur + max_items;
+        if (end > cur && end - cur >= kPipeMinItems) {
+          sh.piped = 1;
+          sh.pipe.begin = cur;
+          sh.pipe.end = end;
+          sh.pipe.front_done = cur;
+          sh.pipe.back_done = cur;
+          sh.pipe.abort = 0;
+          sh.pipe.err = ST_OK;
+          sh.pipe.err_info = 0;
+        }
+      }
+    }
   }
   __syncthreads();
   if (warp == 0) {
-    lower_unit(units, n_units, max_items, blockIdx.x, progress, workers > 1 ? &sh : nullptr, workers);
+    lower_unit(units, n_units, max_items, blockIdx.x, progress, workers > 1 ? &sh : nullptr, workers,
+               sh.piped ? &sh.pipe : nullptr);
     if (workers > 1) {
       if ((threadIdx.x & 31u) == 0) {
         sh.cmd = CMD_EXIT;
@@ -3756,6 +3973,8 @@ __global__ void __launch_bounds__(kReserveThreads) lower_kernel(const Unit* unit
     }
   } else if (warp < workers) {
     helper_loop(sh, warp, workers);
+  } else if (warp == kFrontWarp && sh.piped) {
+    front_loop(sh, units[blockIdx.x]);
   }
   __syncthreads();
 }
@@ -3937,7 +4156,8 @@ int igs_launch_lower(const igs::Unit* units_dev, uint32_t n_units, uint32_t max_
     cudaFuncSetAttribute(igs::lower_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     carveout = true;
   }
-  const uint32_t threads = reserve ? igs::kReserveThreads : (workers ? 32 * igs::kMaxWorkers : 32);
+  // with workers: kMaxWorkers warps plus the front warp of pipelined launches
+  const uint32_t threads = reserve ? igs::kReserveThreads : (workers ? 32 * (igs::kMaxWorkers + 1) : 32);
   igs::lower_kernel<<<n_units, threads, 0, (cudaStream_t)stream>>>(units_dev, n_units, max_items, progress);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

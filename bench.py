@@ -13,6 +13,7 @@ infrastructure) on the host cores instead.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -36,6 +37,38 @@ WINDOW = 16  # the executor takes new instructions once every node has lowered t
 MAP_ENTRY_BYTES = 28.0  # algorithmic bytes of one region-map entry: six uint32 box coordinates + one uint32 value
 WORKLOAD = (f"wave2d: 3 x {N}x{N} fp32 buffers rotating, {NODES} nodes x {DEVICES} devices, {CHUNKS} row chunks, "
             f"{STEPS} time steps, lookahead {LOOKAHEAD}, horizon every {HSTEP} tasks")
+
+
+LOWER_PROFILE = os.path.join(ROOT, "profiles", "lower_kernel_wave8192_64tasks.md")
+LOWER_SOURCES = [os.path.join(ROOT, "paper_2503_10516_gb300", "csrc", f) for f in ("igs_lower.cu", "igs_internal.h")]
+
+
+def lowering_source_sha() -> str:
+    """First 16 hex digits of the SHA-256 of the lowering kernel's sources."""
+    h = hashlib.sha256()
+    for f in LOWER_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _lowering_profile():
+    """Figures of the committed ncu capture of the lowering kernel (one launch
+    over 64 wave tasks): `key: value` lines of its summary. None when the
+    summary is missing or the kernel's sources changed since the capture."""
+    try:
+        with open(LOWER_PROFILE) as f:
+            lines = f.read().splitlines()
+    except OSError:
+        return None
+    vals = {}
+    for line in lines:
+        if line.startswith("- `") and "`: " in line:
+            k, v = line[3:].split("`: ", 1)
+            vals[k.strip()] = v.strip().split()[0]
+    if vals.get("source_sha256_16") != lowering_source_sha():
+        return None
+    return vals
 
 
 def _peaks():
@@ -193,12 +226,16 @@ def _full_scale_caps(igs, small, full, stream, margin=3.0):
     return caps
 
 
-def _doubled(cp):
-    """Capacities with every array doubled (outputs, region-map heap, scratch
-    tables, allocations, queue)."""
-    keys = ("max_instructions", "max_edges", "max_boxes", "map_heap", "scratch_capacity", "max_live_allocs",
-            "max_allocations", "max_queue")
-    return dict(cp, **{k: 2 * cp[k] for k in keys if k in cp})
+def _doubled(cp, factor=2.0):
+    """Capacities grown after a shortfall: the output arrays by `factor`, the
+    region-map heap, scratch tables, allocations and queue doubled."""
+    out = dict(cp)
+    for k in ("max_instructions", "max_edges", "max_boxes"):
+        out[k] = int(factor * cp[k])
+    for k in ("map_heap", "scratch_capacity", "max_live_allocs", "max_allocations", "max_queue"):
+        if k in cp:
+            out[k] = 2 * cp[k]
+    return out
 
 
 def measure_batched(igs, torch, stream, count=512, scale=1.0, tune_scale=0.02, subset_every=16):
@@ -250,6 +287,7 @@ def measure_batched(igs, torch, stream, count=512, scale=1.0, tune_scale=0.02, s
         for attempt in range(attempts):
             ctxs = stage(progs, cps, igs.MODE_BATCHED)
             for p, c in zip(progs, ctxs):
+                c.set_item_times(True)  # how far a context got if a capacity falls short
                 _submit_program(c, p)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -258,17 +296,20 @@ def measure_batched(igs, torch, stream, count=512, scale=1.0, tune_scale=0.02, s
                 torch.cuda.synchronize()
                 dt = time.perf_counter() - t0
             except igs.IgsError:
-                short = []
+                grow = {}
                 for i, c in enumerate(ctxs):
+                    _, ts = c.item_times()
+                    done = float(np.mean(ts > 0)) if len(ts) else 0.0
                     try:
                         c.sync()
                     except igs.IgsError as e:
-                        short.append(i)
+                        # scale by the share of items the context lowered before running out
+                        grow[i] = max(2.0, min(64.0, 1.5 / max(done, 1e-3)))
                         shortfalls.append(str(e).split(": ", 2)[-1])
                 for c in ctxs:
                     c.close()
-                for i in short:
-                    cps[i] = _doubled(cps[i])
+                for i, f in grow.items():
+                    cps[i] = _doubled(cps[i], f)
                 continue
             instrs = sum(int(c.counters()["instructions"]) for c in ctxs)
             launches = sum(int(c.counters()["launches"]) for c in ctxs)
@@ -569,6 +610,65 @@ def measure_executors(igs, torch, stream, prog, make_ctx, wave_tasks=200, nbody_
     return out
 
 
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(len(xs) * q))] if xs else None
+
+
+def lowering_modes(igs, torch, stream, prog, init_zero=False):
+    """One program lowered two ways, without execution: batched (one launch
+    over every submission: warp 0 per node, its helper warps and the front
+    warp) and plain (one launch per submission, each waited for). Batched
+    per-task time = the task's completion minus the previous item's (device
+    clock, igs_item_times; a task's horizon counts with it); plain
+    per-task time = the launch's event time. Both instr/s by wall clock
+    around the whole lowering (plain's includes its launch and sync costs)."""
+    out = {}
+    for name, mode in (("batched", igs.MODE_BATCHED), ("plain", igs.MODE_PLAIN)):
+        c = igs.Context(prog.nodes, prog.devices, prog.horizon_step, prog.lookahead, mode=mode, stream=stream)
+        c.set_timing(True)
+        if mode == igs.MODE_BATCHED:
+            c.set_item_times(True)
+        for op in prog.ops:
+            if op[0] == "buffer":
+                b = op[1]
+                init = b.init
+                if init_zero and init is not None:
+                    init = np.zeros(tuple(b.extent[:b.dims]) + ((4,) if b.elem_size == 16 else ()), np.float32)
+                c.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, init)
+        c.sync()
+        lat = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for op in prog.ops:
+            if op[0] == "task":
+                c.submit(op[1])
+                if mode == igs.MODE_PLAIN:
+                    lat.append(c.stats()["last_lower_ms"])
+        c.flush()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        st = c.stats()
+        instrs = int(c.counters()["instructions"])
+        if mode == igs.MODE_BATCHED:
+            # a task's group = the task and the items after it up to the next
+            # task (its horizon), as one launch of plain mode lowers them
+            kinds, ts = c.item_times()
+            ends = []
+            for k, t in zip(kinds, ts.astype(np.int64)):
+                if k == 1:
+                    ends.append(t)
+                elif ends and k == 2:
+                    ends[-1] = t
+            lat = [(b - a) * 1e-6 for a, b in zip(ends, ends[1:])]
+        c.close()
+        out[name] = {"instructions": instrs, "wall_s": wall, "instr_per_s": instrs / wall,
+                     "lower_ms": st["lower_ms"], "launches": st["lower_launches"],
+                     "p50_task_ms": _pct(lat, 0.5), "p99_task_ms": _pct(lat, 0.99)}
+    out["speedup"] = out["batched"]["instr_per_s"] / out["plain"]["instr_per_s"]
+    return out
+
+
 def measure_nbody(igs, torch, stream, steps=200, exec_steps=2):
     """The all-pairs N-body configuration (2^20 float4 bodies, 8 nodes x 4
     devices, 128 chunks, lookahead 4, two tasks per step): all 400 tasks
@@ -577,30 +677,7 @@ def measure_nbody(igs, torch, stream, steps=200, exec_steps=2):
     executed at full size (2^20 bodies: 2^40 body pairs per step)."""
     n = 1 << 20
     p = W.nbody_program(n=n, steps=steps, nodes=8, devices=4, chunks=128, lookahead=4)
-    out = {}
-    for name, mode in (("batched", igs.MODE_BATCHED), ("plain", igs.MODE_PLAIN)):
-        c = igs.Context(p.nodes, p.devices, p.horizon_step, p.lookahead, mode=mode, stream=stream)
-        c.set_timing(True)
-        for op in p.ops:
-            if op[0] == "buffer":
-                b = op[1]
-                c.create_buffer(b.dims, b.extent[:b.dims], b.elem_size, b.init)
-        lat = []
-        for op in p.ops:
-            if op[0] == "task":
-                c.submit(op[1])
-                if mode == igs.MODE_PLAIN:
-                    lat.append(c.stats()["last_lower_ms"])
-        c.flush()
-        st = c.stats()
-        instrs = int(c.counters()["instructions"])
-        out[name] = {"instructions": instrs, "lower_ms": st["lower_ms"], "launches": st["lower_launches"],
-                     "instr_per_s": instrs / (st["lower_ms"] * 1e-3)}
-        if lat:
-            lat.sort()
-            out[name]["p50_task_ms"] = lat[len(lat) // 2]
-            out[name]["p99_task_ms"] = lat[min(len(lat) - 1, int(len(lat) * 0.99))]
-        c.close()
+    out = lowering_modes(igs, torch, stream, p)
     # execution at full size
     q = W.nbody_program(n=n, steps=exec_steps, nodes=8, devices=4, chunks=128, lookahead=4)
     c = igs.Context(q.nodes, q.devices, q.horizon_step, q.lookahead, mode=igs.MODE_BATCHED, stream=stream)
@@ -960,8 +1037,18 @@ def run_gpu(args):
     dom = max(parts, key=lambda k: parts[k][0])
     ms, byts, what = parts[dom]
     achieved = byts / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    prof = _lowering_profile()
+    traffic, issue = None, None
+    if prof and dom == "lowering":
+        # DRAM bytes of the captured launch per task, times the tasks of this launch
+        traffic = float(prof["dram_bytes_per_task"]) * STEPS
+        ipc = float(prof["inst_per_active_sm_cycle"])
+        issue = {"inst_per_active_sm_cycle": ipc, "peak": 4.0, "frac": ipc / 4.0,
+                 "warp_inst_per_emitted_instruction": float(prof["warp_inst_per_emitted_instruction"]),
+                 "source": os.path.relpath(LOWER_PROFILE, ROOT)}
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "kernel": dom, "what": what, "peak_source": src}
+            "traffic": traffic, "kernel": dom, "what": what, "peak_source": src,
+            "issue_efficiency": issue}
     hot = {}
     for k, (ms_k, b_k, w_k) in parts.items():
         a = b_k / (ms_k * 1e-3) / 1e9 if ms_k > 0 else 0.0
@@ -981,6 +1068,7 @@ def run_gpu(args):
     big_copy = section(measure_box_copy, igs, torch, stream)
     halo = section(measure_halo_copies, igs, torch, stream)
     executors = section(measure_executors, igs, torch, sh, prog, make_ctx)
+    wave_modes = section(lowering_modes, igs, torch, sh, _program_shape(), True)
     nbody = section(measure_nbody, igs, torch, sh)
     jacobi = section(measure_jacobi, igs, torch, sh)
     lookahead = section(measure_lookahead, igs)
@@ -1010,6 +1098,7 @@ def run_gpu(args):
             "gpu_launches": launches * args.steps,
             "roofline": roof,
             "hot_path": hot,
+            "lowering_modes": wave_modes,
             "lowering": {"batched_instr_per_s": instrs / (lower_ms * 1e-3) if lower_ms else None,
                          "plain_instr_per_s": plain_instrs / (plain_stats["lower_ms"] * 1e-3),
                          "plain_launches": plain_stats["lower_launches"],

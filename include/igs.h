@@ -458,6 +458,18 @@ int igs_serve_replay_ex(igs_server* srv, igs_ctx* const* ctxs, uint32_t n_ctx, c
 int igs_replay_plain(igs_ctx* const* ctxs, uint32_t n_ctx, const igs_replay_item* items, uint32_t n,
                      uint32_t timeout_ms, uint64_t* latency_ns, uint64_t* wall_ns);
 
+/* Per-item lowering times, off by default. While on, every lowering launch
+ * records on the device when each node finished each submitted item (a
+ * buffer creation, task, horizon, epoch, ...: the items in submission order,
+ * horizons included). igs_item_times writes, for items [0, min(count, cap)),
+ * out[2i] = the item's kind (0 buffer creation, 1 task, 2 horizon, 3 epoch,
+ * 4 buffer destruction, 5 lookahead change) and out[2i + 1] = the time
+ * (device clock, ns) the last node finished it, 0 if some node has not; it
+ * waits for the context's stream. *count = items submitted. out may be null
+ * (count only). IGS_ERR_STATE for a served or running context. */
+int igs_set_item_times(igs_ctx* ctx, int on);
+int igs_item_times(igs_ctx* ctx, uint64_t* out, uint32_t cap, uint32_t* count);
+
 /* Counters: [0] instructions, [1] edges, [2] boxes, [3] map entries read,
  * [4] map entries written, [5] launches of the lowering kernel, summed over
  * nodes. */

@@ -149,6 +149,10 @@ struct igs_ctx {
   // waiting in the server's admission queue: submissions are kept on the host
   // (not published, not lowered) until a detach makes room
   bool serve_pending = false;
+  // per-item completion timestamps (igs_set_item_times): nodes x cap_item_ts
+  bool item_times = false;
+  uint64_t* d_item_ts = nullptr;
+  uint32_t cap_item_ts = 0;
   std::vector<uint32_t> slot_ids;
   Item* m_items = nullptr;
   igs_task* m_tasks = nullptr;
@@ -285,10 +289,34 @@ int ensure_helpers(igs_ctx* c) {
   return IGS_OK;
 }
 
+// Timestamp array of at least the context's item count per node (item timing on).
+int ensure_item_ts(igs_ctx* c) {
+  const uint32_t need = (uint32_t)c->items.size();
+  if (need <= c->cap_item_ts) return IGS_OK;
+  const uint32_t cap = std::max<uint32_t>(need, std::max<uint32_t>(1024, 2 * c->cap_item_ts));
+  uint64_t* p = nullptr;
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMalloc(&p, sizeof(uint64_t) * (size_t)cap * c->N));
+  CK(cudaMemset(p, 0, sizeof(uint64_t) * (size_t)cap * c->N));
+  for (uint32_t n = 0; n < c->N; ++n) {
+    if (c->d_item_ts)
+      CK(cudaMemcpy(p + (size_t)cap * n, c->d_item_ts + (size_t)c->cap_item_ts * n, sizeof(uint64_t) * c->cap_item_ts,
+                    cudaMemcpyDeviceToDevice));
+    uint64_t* q = p + (size_t)cap * n;
+    CK(cudaMemcpy(&c->d_nodes[n].item_ts, &q, sizeof q, cudaMemcpyHostToDevice));
+    c->nodes_host[n].item_ts = q;
+  }
+  if (c->d_item_ts) CK(cudaFree(c->d_item_ts));
+  c->d_item_ts = p;
+  c->cap_item_ts = cap;
+  return IGS_OK;
+}
+
 int launch_lower(igs_ctx* c, uint32_t max_items = IGS_NONE, bool reserve = false, uint32_t* progress = nullptr) {
   if (c->server) return IGS_OK;  // the serving loop lowers it
   int r = upload_prog(c);
   if (r) return r;
+  if (c->item_times && (r = ensure_item_ts(c))) return r;
   // one context's launch has few units (its nodes): helper warps share
   // parts of each node's lowering (nodes with several devices)
   const bool workers = c->D > 1;
@@ -521,6 +549,7 @@ void igs_destroy(igs_ctx* c) {
   for (auto& sr : c->sends)
     if (sr.second.mail) cudaFree(sr.second.mail);
   for (auto& f : c->flow_keep) cudaFree(f.arena);
+  if (c->d_item_ts) cudaFree(c->d_item_ts);
   for (auto& o : c->oob_keep) cudaFree(o.rec);
   for (void* p : c->retired_pinned) cudaFreeHost(p);
   for (int k = 0; k < 2; ++k) {
@@ -646,6 +675,49 @@ int igs_selftest_flow_wait(uint32_t wait_ms) {
 int igs_set_timing(igs_ctx* c, int on) {
   if (!c) return IGS_ERR_INVALID_ARG;
   c->timing = on != 0;
+  return IGS_OK;
+}
+
+int igs_set_item_times(igs_ctx* c, int on) {
+  if (!c) return IGS_ERR_INVALID_ARG;
+  if (c->server || c->pipelined) return fail_ctx(c, IGS_ERR_STATE, "the context is served or running");
+  c->item_times = on != 0;
+  if (!c->item_times && c->d_item_ts) {  // later launches record nothing
+    CK(cudaStreamSynchronize(c->stream));
+    for (uint32_t n = 0; n < c->N; ++n) {
+      uint64_t* q = nullptr;
+      CK(cudaMemcpy(&c->d_nodes[n].item_ts, &q, sizeof q, cudaMemcpyHostToDevice));
+      c->nodes_host[n].item_ts = nullptr;
+    }
+    CK(cudaFree(c->d_item_ts));
+    c->d_item_ts = nullptr;
+    c->cap_item_ts = 0;
+  }
+  return IGS_OK;
+}
+
+int igs_item_times(igs_ctx* c, uint64_t* out, uint32_t cap, uint32_t* count) {
+  if (!c || !count || (cap && !out)) return IGS_ERR_INVALID_ARG;
+  const uint32_t n = (uint32_t)c->items.size();
+  *count = n;
+  if (!out || !c->d_item_ts) return IGS_OK;
+  CK(cudaStreamSynchronize(c->stream));
+  const uint32_t m = std::min<uint32_t>(std::min(n, cap), c->cap_item_ts);
+  std::vector<uint64_t> ts((size_t)c->cap_item_ts * c->N);
+  CK(cudaMemcpy(ts.data(), c->d_item_ts, sizeof(uint64_t) * ts.size(), cudaMemcpyDeviceToHost));
+  for (uint32_t i = 0; i < m; ++i) {
+    uint64_t t = 0;
+    for (uint32_t k = 0; k < c->N; ++k) {
+      const uint64_t v = ts[(size_t)c->cap_item_ts * k + i];
+      if (v == 0) {  // not lowered on some node yet
+        t = 0;
+        break;
+      }
+      t = std::max(t, v);
+    }
+    out[2 * i] = c->items[i].kind;
+    out[2 * i + 1] = t;
+  }
   return IGS_OK;
 }
 

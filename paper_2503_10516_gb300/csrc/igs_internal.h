@@ -110,6 +110,9 @@ struct NodeDev {
   // lowered by several warps (kScratchSets x kHelperTables tables of
   // cap_scratch entries), or null
   uint32_t* helper_scratch;
+  // completion time (%globaltimer, ns) of each item, by item index, written
+  // by the lowering warp when item timing is on; null otherwise
+  uint64_t* item_ts;
 };
 
 // Program-level inputs shared by all node warps of one context.

@@ -3891,9 +3891,15 @@ __device__ void lower_unit(const Unit* units, uint32_t n_units, uint32_t max_ite
   }
   volatile uint32_t* pr = progress ? progress + (size_t)w * PR_WORDS : nullptr;
   PhaseTimer pt = pt_start();
+  uint64_t* const item_ts = u.node->item_ts;
   while (cursor < end && c.err == ST_OK) {
     if (pipe && !pipe_wait(c, *pipe, [&]() { return pipe->front_done > cursor; })) break;
     deliver(c, cursor);
+    if (item_ts && laneid() == 0) {
+      uint64_t t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      item_ts[cursor] = t;
+    }
     ++cursor;
     if (pipe) {
       __syncwarp();

@@ -36,7 +36,7 @@ EXPORTS = ("igs_create", "igs_destroy", "igs_create_buffer", "igs_destroy_buffer
            "igs_serve_detach", "igs_serve_stop", "igs_run", "igs_lower_batch_shaped", "igs_set_executor",
            "igs_exec_stats", "igs_selftest_flow_wait", "igs_bounds_errors", "igs_serve_replay",
            "igs_horizon_plan", "igs_serve_enqueue", "igs_serve_stats", "igs_serve_replay_ex",
-           "igs_replay_plain")
+           "igs_replay_plain", "igs_set_item_times", "igs_item_times")
 EXEC_LEVELS, EXEC_DATAFLOW = 0, 1  # IGS_EXEC_*
 ORDER_SUBMISSION, ORDER_LONGEST_FIRST = 0, 1  # IGS_ORDER_*
 
@@ -134,6 +134,8 @@ def lib():
         L.igs_serve_replay_ex.argtypes = [vp, ctypes.POINTER(vp), u32, vp, u32, u32, u32, vp, vp]
         L.igs_serve_enqueue.argtypes = [vp, vp, u32, P32]
         L.igs_replay_plain.argtypes = [ctypes.POINTER(vp), u32, vp, u32, u32, vp, vp]
+        L.igs_set_item_times.argtypes = [vp, ctypes.c_int]
+        L.igs_item_times.argtypes = [vp, vp, u32, P32]
         L.igs_serve_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         L.igs_horizon_plan.argtypes = [vp, u32, vp, u32, u32, u32, vp]
         L.igs_sync.argtypes = [vp]
@@ -332,6 +334,23 @@ def _set_timing(self, on: bool = True):
     self._check(lib().igs_set_timing(self._h, 1 if on else 0), "set_timing")
 
 
+def _set_item_times(self, on: bool = True):
+    self._check(lib().igs_set_item_times(self._h, 1 if on else 0), "set_item_times")
+
+
+def _item_times(self):
+    """(kinds, times): per submitted item, its kind (0 create, 1 task, 2
+    horizon, 3 epoch, 4 destroy, 5 lookahead) and the device time (ns) its
+    last node finished lowering it (0 if not yet)."""
+    cnt = np.zeros(1, np.uint32)
+    self._check(lib().igs_item_times(self._h, None, 0, _p32(cnt)), "item_times")
+    n = int(cnt[0])
+    out = np.zeros(max(1, 2 * n), np.uint64)
+    self._check(lib().igs_item_times(self._h, out.ctypes.data, n, _p32(cnt)), "item_times")
+    out = out[:2 * n].reshape(-1, 2)
+    return out[:, 0].astype(np.uint32), out[:, 1]
+
+
 PHASES = ("split", "overlap", "push_await", "allocating", "alloc", "push", "receive", "coherence", "kernel",
           "remote", "sync_emit", "sync_apply", "total", "in_emit", "in_canonical", "in_find_alloc",
           "in_merge", "in_subtract", "in_query", "in_compact", "emit_probe", "emit_dedup", "emit_record",
@@ -348,6 +367,8 @@ def _profile(self) -> dict:
 Context.profile = _profile
 Context.stats = _stats
 Context.set_timing = _set_timing
+Context.set_item_times = _set_item_times
+Context.item_times = _item_times
 
 
 def _pack_trace(trace):

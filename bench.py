@@ -280,15 +280,27 @@ def measure_batched(igs, torch, stream, count=512, scale=1.0, tune_scale=0.02, s
 
     shortfalls = []
 
-    def batched_run(progs, cps, shp, attempts=4):
-        """One launch over all programs; a context whose capacity estimate fell
-        short gets doubled output capacities and the launch is repeated (only
-        the launch that completes is timed)."""
+    def batched_run(progs, cps, shp, attempts=3):
+        """One launch over all programs. A context whose capacity estimate fell
+        short gets larger capacities (its outputs scaled by the share of its
+        items it lowered, at most 8x; heap and scratch doubled) and the launch
+        is repeated; after the last attempt, programs still short (or whose
+        context cannot be created) are left out and named. Only the launch that
+        completes is timed."""
+        active = list(range(len(progs)))
+        excluded = []
         for attempt in range(attempts):
-            ctxs = stage(progs, cps, igs.MODE_BATCHED)
-            for p, c in zip(progs, ctxs):
+            ctxs, made = [], []
+            for i in active:
+                try:
+                    ctxs.append(stage([progs[i]], [cps[i]], igs.MODE_BATCHED)[0])
+                    made.append(i)
+                except igs.IgsError as e:
+                    excluded.append({"program": progs[i].name, "why": str(e)[:120]})
+            active = made
+            for i, c in zip(active, ctxs):
                 c.set_item_times(True)  # how far a context got if a capacity falls short
-                _submit_program(c, p)
+                _submit_program(c, progs[i])
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             try:
@@ -297,34 +309,44 @@ def measure_batched(igs, torch, stream, count=512, scale=1.0, tune_scale=0.02, s
                 dt = time.perf_counter() - t0
             except igs.IgsError:
                 grow = {}
-                for i, c in enumerate(ctxs):
+                for i, c in zip(active, ctxs):
                     _, ts = c.item_times()
                     done = float(np.mean(ts > 0)) if len(ts) else 0.0
                     try:
                         c.sync()
                     except igs.IgsError as e:
-                        # scale by the share of items the context lowered before running out
-                        grow[i] = max(2.0, min(64.0, 1.5 / max(done, 1e-3)))
+                        grow[i] = max(2.0, min(8.0, 1.5 / max(done, 1e-3)))
                         shortfalls.append(str(e).split(": ", 2)[-1])
                 for c in ctxs:
                     c.close()
                 for i, f in grow.items():
                     cps[i] = _doubled(cps[i], f)
+                if attempt == attempts - 1:
+                    break
+                if attempt == attempts - 2:  # the last attempt runs without the programs still short
+                    keep = [i for i in active if i not in grow]
+                    excluded += [{"program": progs[i].name, "why": "capacity estimate short twice"} for i in grow]
+                    active = keep
                 continue
             instrs = sum(int(c.counters()["instructions"]) for c in ctxs)
             launches = sum(int(c.counters()["launches"]) for c in ctxs)
             for c in ctxs:
                 c.close()
-            return {"instr_per_s": instrs / dt, "tasks_per_s": sum(len(p.tasks) for p in progs) / dt,
-                    "seconds": dt, "instructions": instrs, "launches": launches, "attempts": attempt + 1,
-                    "capacity_shortfalls_before": shortfalls[:8]}
-        return {"error": f"capacity estimates still short after {attempts} attempts", "shortfalls": shortfalls[:8]}
+            tasks = sum(len(progs[i].tasks) for i in active)
+            return {"instr_per_s": instrs / dt, "tasks_per_s": tasks / dt, "seconds": dt, "instructions": instrs,
+                    "launches": launches, "attempts": attempt + 1, "programs_lowered": len(active),
+                    "tasks_lowered": tasks, "excluded": excluded, "capacity_shortfalls_before": shortfalls[:8]}
+        return {"error": f"capacity estimates still short after {attempts} attempts", "shortfalls": shortfalls[:8],
+                "excluded": excluded}
 
     res["batched_all"] = batched_run(full, caps, shape)
     sub = list(range(0, count, subset_every))
     sp, sc = [full[i] for i in sub], [caps[i] for i in sub]
-    res["subset"] = {"programs": len(sub), "tasks": sum(len(p.tasks) for p in sp),
-                     "batched": batched_run(sp, sc, shape)}
+    sb = batched_run(sp, sc, shape)
+    gone = {e["program"] for e in sb.get("excluded", [])}
+    keep = [k for k, p in enumerate(sp) if p.name not in gone]
+    sp, sc = [sp[k] for k in keep], [sc[k] for k in keep]
+    res["subset"] = {"programs": len(sp), "tasks": sum(len(p.tasks) for p in sp), "batched": sb}
     # one task per launch, each program after the other (a program whose
     # capacities fall short is repeated with doubled ones; only the run that
     # completes is timed)

@@ -3784,11 +3784,15 @@ __device__ __noinline__ void publish_progress(const Ctx& c, volatile uint32_t* p
 }
 
 // Waits (every lane polls) until ready() holds; false when the other side
-// of the pipeline stopped (taking its error, if any) or after about 30 s
-// (ST_TIMEOUT, and the other side is told to stop).
+// of the pipeline stopped (taking its error, if any) or after 30 s of device
+// time (ST_TIMEOUT, and the other side is told to stop). Polls back off from
+// min_ns to 2 us between looks (the front warp, usually ahead, mostly sleeps).
 template <class F>
-__device__ bool pipe_wait(Ctx& c, Pipe& P, F ready) {
-  for (uint32_t spins = 0;; ++spins) {
+__device__ bool pipe_wait(Ctx& c, Pipe& P, F ready, uint32_t min_ns) {
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  uint32_t ns = min_ns;
+  for (;;) {
     if (__any_sync(FULL, P.abort != 0)) {
       if (P.err != ST_OK && c.err == ST_OK) {
         c.err = P.err;
@@ -3797,7 +3801,9 @@ __device__ bool pipe_wait(Ctx& c, Pipe& P, F ready) {
       return false;
     }
     if (__all_sync(FULL, ready())) break;
-    if (spins > (1u << 28)) {
+    uint64_t t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    if (__shfl_sync(FULL, t1 - t0, 0) > 30000000000ull) {
       fail(c, ST_TIMEOUT);
       __syncwarp();
       if (laneid() == 0) {
@@ -3808,7 +3814,8 @@ __device__ bool pipe_wait(Ctx& c, Pipe& P, F ready) {
       __syncwarp();
       return false;
     }
-    __nanosleep(100);
+    __nanosleep(ns);
+    ns = ns < 2048u ? 2 * ns : 2048u;
   }
   __threadfence_block();
   return true;
@@ -3828,7 +3835,7 @@ __device__ void front_loop(BlockShared& sh, const Unit u) {
   for (int k = 0; k < 14; ++k) f.s[k] = scratch_table(nullptr, 0);  // tables the front never uses
   for (int k = 0; k < 8; ++k) f.s[used[k]] = scratch_table(helper_table(u.node, kFrontWarp, k), cap);
   for (uint32_t i = P.begin; i < P.end && f.err == ST_OK; ++i) {
-    if (!pipe_wait(f, P, [&]() { return i - P.back_done < kPipeDepth; })) break;
+    if (!pipe_wait(f, P, [&]() { return i - P.back_done < kPipeDepth; }, 256)) break;
     const uint32_t slot = i % kPipeDepth;
     f.qr = scratch_table(helper_table(u.node, kFrontWarp, 8 + slot), cap);
     uint32_t rejected = 0;
@@ -3893,7 +3900,7 @@ __device__ void lower_unit(const Unit* units, uint32_t n_units, uint32_t max_ite
   PhaseTimer pt = pt_start();
   uint64_t* const item_ts = u.node->item_ts;
   while (cursor < end && c.err == ST_OK) {
-    if (pipe && !pipe_wait(c, *pipe, [&]() { return pipe->front_done > cursor; })) break;
+    if (pipe && !pipe_wait(c, *pipe, [&]() { return pipe->front_done > cursor; }, 32)) break;
     deliver(c, cursor);
     if (item_ts && laneid() == 0) {
       uint64_t t;

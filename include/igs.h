@@ -105,7 +105,7 @@ typedef struct igs_config {
   uint32_t map_heap;         /* entries (48 bytes each) of each node's region-map heap, which holds every
                                 buffer's and allocation's box tables; a table grows on demand by moving to a
                                 larger slab of the heap; 0 = default (1 << 20) */
-  uint32_t scratch_capacity; /* boxes per device-side scratch table; 0 = default (4096) */
+  uint32_t scratch_capacity; /* boxes per device-side scratch table, at least 32; 0 = default (4096) */
   uint32_t max_buffers;      /* buffers per context; 0 = default (64) */
   uint32_t max_live_allocs;  /* live allocations per node; 0 = default (1024) */
   uint32_t max_allocations;  /* allocation ids per node over the context's life; 0 = default (65536) */

@@ -402,6 +402,8 @@ int igs_create(const igs_config* cfg, igs_ctx** out) {
     return IGS_ERR_INVALID_ARG;
   if (cfg->mode > IGS_MODE_BATCHED) return IGS_ERR_INVALID_ARG;
   if (!config_flags_ok(cfg->flags)) return IGS_ERR_INVALID_ARG;
+  // scratch tables hold one entry per node (up to 32) or per accessor without a claim
+  if (cfg->scratch_capacity && cfg->scratch_capacity < 32) return IGS_ERR_INVALID_ARG;
   igs_ctx* c = new igs_ctx();
   c->cfg = *cfg;
   c->N = cfg->num_nodes;

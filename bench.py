@@ -537,40 +537,6 @@ def measure_box_copy(igs, torch, stream, reps=20):
     return out
 
 
-def measure_halo_copies(igs, torch, stream, jobs_n=256, reps=20):
-    """Halo-shaped box copies (single 8192-column fp32 rows, 32 KiB, the
-    wave program's halo exchanges) between two 1024 x 8192 allocations:
-    `jobs_n` rows in one box-copy launch, in launches of 32 jobs, and one job
-    per launch. Bytes = read + written; the allocations are L2-resident, as
-    freshly written halo rows are in the step."""
-    rows, cols = 1024, 8192
-    src = torch.arange(rows * cols, dtype=torch.float32, device="cuda")
-    dst = torch.zeros(rows * cols, dtype=torch.float32, device="cuda")
-    box = (0, 0, 0, rows, cols, 1)
-    jobs = [(src.data_ptr(), box, dst.data_ptr(), box, (r, 0, 0, r + 1, cols, 1), 4)
-            for r in range(0, 4 * jobs_n, 4)]
-    out = {}
-    for name, per in (("one_launch", jobs_n), ("32_per_launch", 32), ("one_per_launch", 1)):
-        for _ in range(2):
-            for k in range(0, jobs_n, per):
-                igs.box_copy(jobs[k:k + per], stream.cuda_stream)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(reps):
-            for k in range(0, jobs_n, per):
-                igs.box_copy(jobs[k:k + per], stream.cuda_stream)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1) / reps
-        byts = 2.0 * jobs_n * cols * 4
-        out[name] = {"launches": (jobs_n + per - 1) // per, "ms": ms, "gbs": byts / (ms * 1e-3) / 1e9}
-    ok = bool(torch.equal(dst.view(rows, cols)[::4][:jobs_n], src.view(rows, cols)[::4][:jobs_n]))
-    out.update({"jobs": jobs_n, "bytes_per_job": cols * 4, "checked": ok})
-    del src, dst
-    return out
-
-
 def measure_executors(igs, torch, stream, prog, make_ctx, wave_tasks=200, nbody_n=1 << 16, nbody_steps=10):
     """Execution alone (each graph fully lowered first) on the level executor
     and on the dataflow executor: the first `wave_tasks` tasks of the wave
@@ -1088,7 +1054,6 @@ def run_gpu(args):
             return {"error": f"{type(e).__name__}: {e}"}
 
     big_copy = section(measure_box_copy, igs, torch, stream)
-    halo = section(measure_halo_copies, igs, torch, stream)
     executors = section(measure_executors, igs, torch, sh, prog, make_ctx)
     wave_modes = section(lowering_modes, igs, torch, sh, _program_shape(), True)
     nbody = section(measure_nbody, igs, torch, sh)
@@ -1127,7 +1092,6 @@ def run_gpu(args):
                          "p50_task_ms": p50, "p99_task_ms": p99,
                          "batched_ms_per_task": lower_ms / STEPS},
             "box_copy_gbs": (copy_bytes / (copy_ms * 1e-3) / 1e9) if copy_ms else None,
-            "halo_copies": halo,
             "in_step_launches": {"lowering": stats[0]["lower_launches"], "box_copy": stats[0]["copy_launches"],
                                  "stencil_or_level": stats[0]["workload_launches"],
                                  "note": "a level with copies and stencils runs as one level launch"},

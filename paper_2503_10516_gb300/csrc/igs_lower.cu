@@ -532,6 +532,7 @@ __device__ __forceinline__ uint32_t warp_or(uint32_t v) {
   for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(FULL, v, o);
   return v;
 }
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) { return __reduce_add_sync(FULL, v); }
 __device__ __forceinline__ Bx warp_bbox(Bx b, bool valid) {
   Bx r;
 #pragma unroll
@@ -1598,6 +1599,47 @@ __device__ __forceinline__ bool emit_record(Ctx& c, uint32_t type, uint32_t seq,
   return true;
 }
 
+// A read of instruction id over the boxes box(r) (r < n; box returns false
+// for a dead one) joins allocation aid's readers; again: the instruction
+// already read there through another accessor (its earlier entries over the
+// boxes are replaced).
+template <class G>
+__device__ __forceinline__ bool apply_read(Ctx& c, uint32_t aid, uint32_t n, G box, uint32_t id, bool again) {
+  Table RD = rd_t(c, aid);
+  t_tidy(c, RD);
+  for (uint32_t r = 0; r < n; ++r) {
+    Bx q;
+    if (!box(r, q)) continue;
+    if (again) t_subtract(c, RD, NONE, q, id);
+    const uint32_t s = t_claim(c, RD, laneid() == 0);
+    if (c.err) return false;
+    if (laneid() == 0) t_put(RD, s, 0, q, id, 0, 0);
+    __syncwarp();
+  }
+  // re-merge only a table that has grown: keeps hot paths short and bounds
+  // fragmentation between horizons
+  t_maybe_merge(c, RD, IGS_MERGE_FLOOR);
+  return true;
+}
+// A write of instruction id over the boxes box(r) replaces allocation aid's
+// writers there and clears its readers.
+template <class G>
+__device__ __forceinline__ bool apply_write(Ctx& c, uint32_t aid, uint32_t n, G box, uint32_t id) {
+  Table RD = rd_t(c, aid);
+  Table WR = wr_t(c, aid);
+  t_tidy(c, WR);
+  for (uint32_t r = 0; r < n; ++r) {
+    Bx q;
+    if (!box(r, q)) continue;
+    t_subtract(c, RD, NONE, q);
+    t_set(c, WR, NONE, q, id, 0, 0);
+    if (c.err) return false;
+  }
+  t_maybe_merge(c, WR, IGS_MERGE_FLOOR);
+  t_maybe_merge(c, RD, IGS_MERGE_FLOOR);
+  return true;
+}
+
 // Applies an instruction's accesses to the per-allocation tables: reads
 // join the readers, writes replace the writers and clear the readers.
 __device__ __forceinline__ bool emit_apply(Ctx& c, const Acc* acc, int nacc, uint32_t id) {
@@ -1609,40 +1651,22 @@ __device__ __forceinline__ bool emit_apply(Ctx& c, const Acc* acc, int nacc, uin
     bool again = false;
     for (int j = 0; j < k; ++j)
       if (acc[j].alloc == A.alloc && (acc[j].mode & IGS_READ)) again = true;
-    Table RD = rd_t(c, A.alloc);
-    t_tidy(c, RD);
-    const uint32_t from = RD.n;
-    for (uint32_t r = A.from; r < A.to; ++r) {
-      if (t_key(*A.t, r) == DEAD) continue;
-      const Bx q = t_box(*A.t, r);
-      if (again) t_subtract(c, RD, NONE, q, id);
-      const uint32_t s = t_claim(c, RD, laneid() == 0);
-      if (c.err) return false;
-      if (laneid() == 0) t_put(RD, s, 0, q, id, 0, 0);
-      __syncwarp();
-    }
-    // re-merge only a table that has grown: keeps hot paths short and bounds
-    // fragmentation between horizons
-    t_maybe_merge(c, RD, IGS_MERGE_FLOOR);
-    (void)from;
+    auto box = [&](uint32_t r, Bx& q) {
+      const Ent e = t_ent(*A.t, A.from + r);
+      q = e.b;
+      return e.key != DEAD;
+    };
+    if (!apply_read(c, A.alloc, A.to - A.from, box, id, again)) return false;
   }
   for (int k = 0; k < nacc; ++k) {
     const Acc& A = acc[k];
     if (!(A.mode & IGS_WRITE)) continue;
-    Table RD = rd_t(c, A.alloc);
-    Table WR = wr_t(c, A.alloc);
-    t_tidy(c, WR);
-    const uint32_t from = WR.n;
-    for (uint32_t r = A.from; r < A.to; ++r) {
-      if (t_key(*A.t, r) == DEAD) continue;
-      const Bx q = t_box(*A.t, r);
-      t_subtract(c, RD, NONE, q);
-      t_set(c, WR, NONE, q, id, 0, 0);
-      if (c.err) return false;
-    }
-    t_maybe_merge(c, WR, IGS_MERGE_FLOOR);
-    t_maybe_merge(c, RD, IGS_MERGE_FLOOR);
-    (void)from;
+    auto box = [&](uint32_t r, Bx& q) {
+      const Ent e = t_ent(*A.t, A.from + r);
+      q = e.b;
+      return e.key != DEAD;
+    };
+    if (!apply_write(c, A.alloc, A.to - A.from, box, id)) return false;
   }
   return true;
 }
@@ -1653,7 +1677,8 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
   if (c.err) return NONE;
   NodeDev* nd = c.nd;
   if (c.stage) {
-    // a coherence worker: record, edges and boxes into its stage
+    // a coherence worker: record, edges and boxes into its stage; the tables
+    // stay as they are
     Stage& st = *c.stage;
     if (bind_n || st.n_instr + 1 > st.cap_instr) {
       fail_cap(c, CAP_TABLE, st.cap_instr);
@@ -1704,7 +1729,8 @@ __device__ __noinline__ uint32_t emit_impl(Ctx& c, uint32_t type, uint32_t seq, 
     st.n_edge += ne;
     st.n_box += nb;
     st.n_instr += 1;
-    if (!emit_apply(c, acc, nacc, pid)) return NONE;
+    // the accesses are applied to the tables once every worker has planned
+    // (p4_apply), in the order of the single-warp path
     return pid;
   }
   const uint32_t id = c.n_instr;
@@ -1818,6 +1844,10 @@ __device__ __noinline__ void emit_free(Ctx& c, uint32_t seq, uint32_t aid) {
 // a5: coherence copies making need = T[from, to) (disjoint boxes) up to date
 // in memory m, allocation dst: stale parts split by original producer, then
 // by source allocation, one copy per (producer, source allocation).
+// Planned by a coherence worker (c.stage set): the copies go to its stage and
+// neither the buffer state nor the allocation tables change; the regions its
+// earlier copies of b into memory m cover count as up to date, as they would
+// after those copies' buffer-state update.
 __device__ __noinline__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_t m, uint32_t dst, const Table& T, uint32_t from,
                           uint32_t to) {
   Table& Q = c.s[S_T0];
@@ -1837,6 +1867,28 @@ __device__ __noinline__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_
       });
       if (c.err) return;
     }
+  }
+  const Stage* plan = c.stage;
+  if (plan) {
+    if (c.nd->stage_d2d) {  // host-staged copies allocate: never planned
+      fail_internal(c, 10);
+      return;
+    }
+    for (uint32_t q = 0; q < plan->n_instr && Q.n; ++q) {
+      const igs_instruction r = plan->instrs[q];
+      if (r.c != b || c.nd->allocs[r.b].mem != m) continue;
+      for (uint32_t i = 0; i < r.box_cnt; ++i) {
+        const igs_box o = plan->boxes[r.box_off + i];
+        Bx x;
+        for (int d = 0; d < 3; ++d) {
+          x.lo[d] = o.lo[d];
+          x.hi[d] = o.hi[d];
+        }
+        t_subtract(c, Q, NONE, x);
+        if (c.err) return;
+      }
+    }
+    if (Q.live != Q.n) t_compact(c, Q);  // the scans below take every entry as live
   }
   uint64_t last = 0;
   bool first_round = true;
@@ -1941,8 +1993,8 @@ __device__ __noinline__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_
         emit(c, IGS_COPY, seq, src, dst, b, 0, &CN, 0, CN.n, acc, 2, false);
         if (c.err) return false;
       }
-      // remember the copied region
-      for (uint32_t base = 0; base < CN.n; base += 32) {
+      // remember the copied region (a planned copy's boxes are in its record)
+      for (uint32_t base = 0; base < (plan ? 0u : CN.n); base += 32) {
         const uint32_t i = base + laneid();
         const bool in = i < CN.n;
         const uint32_t s = t_claim(c, CP, in);
@@ -1964,6 +2016,7 @@ __device__ __noinline__ void coherence(Ctx& c, uint32_t seq, uint32_t b, uint32_
         if (!copy_from(__shfl_sync(FULL, mine, __ffs(set) - 1))) return;
     }
   }
+  if (plan) return;  // the buffer state is updated by p4_apply
   Table B = bst_t(c, b);
   t_tidy(c, B);
   const uint32_t from_bst = B.n;
@@ -2021,7 +2074,7 @@ __device__ __forceinline__ bool union_is_image(const igs_task& t, uint32_t acc, 
 // parts touch disjoint tables and emit nothing whose id depends on another
 // part are shared: warp 0 posts a job, every worker does its share, warp 0
 // then appends the parts' results in the order of the single-warp path.
-enum BlockCmd : uint32_t { CMD_NONE = 0, CMD_P5 = 1, CMD_A3 = 2, CMD_P4 = 3, CMD_P4_IDS = 4, CMD_EXIT = 5 };
+enum BlockCmd : uint32_t { CMD_NONE = 0, CMD_P5 = 1, CMD_A3 = 2, CMD_P4 = 3, CMD_P4_APPLY = 4, CMD_EXIT = 5 };
 __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg);
 
 struct WorkJob {
@@ -2034,8 +2087,10 @@ struct WorkJob {
   Table out0;        // worker 0's staged push / await entries (warp 0's scratch)
   uint32_t nbuf;     // push / await, coherence: buffers in ascending order, their staged entries
   uint32_t buf[IGS_MAX_ACCESSORS], buf_off[IGS_MAX_ACCESSORS], buf_cnt[IGS_MAX_ACCESSORS];
-  Table PC;          // coherence: the consumers (flags, box, v0 = chunk slot * na + accessor)
+  Table PC;          // coherence: the consumers (flags, box, v0 = chunk slot * na + accessor,
+                     // v1 / v2 = first staged copy and count)
   uint32_t n_live;   // coherence: live allocations (NodeDev's count is stale during a launch)
+  uint32_t devices;  // coherence: devices per node
 };
 
 // Pipelined lowering of one node (a launch with several items): a front
@@ -2699,15 +2754,29 @@ __device__ bool p4_consumer(Ctx& c, const igs_task& t, uint32_t seq, const Table
   return c.err == ST_OK;
 }
 
-// Consumers of different buffers touch disjoint state (the buffer's state
-// table and allocations); only the ids of their copies depend on one another.
-// Worker w takes the consumers of buffers i with i mod workers == w, in
-// consumer order, emitting into its stage with provisional ids.
-__device__ __forceinline__ uint32_t buffer_worker(const WorkJob& j, uint32_t b) {
-  for (uint32_t i = 0; i < j.nbuf; ++i)
-    if (j.buf[i] == b) return i % j.workers;
-  return 0;
+// Coherence with several warps (Sec. 3.3, a5), in two shared phases.
+// Plan: worker p4_worker(b, m) takes, in consumer order, the stale consumers
+// of buffer b on memory m and stages their copies (records, boxes, edges)
+// without changing any table. Planning against the tables as they were
+// before the phase gives the single-warp path's copies and edges: a copy
+// reads a region that is up to date at its producer's memory and writes one
+// that is stale at its own, so no copy of the phase reads or writes what
+// another one writes; consumers of the same (b, m) see their predecessors'
+// copies through the exclusion in coherence().
+// Apply: warp 0 appends the staged copies in consumer order (their ids were
+// fixed before the phase) while the helpers apply them to the tables: the
+// owner of an allocation applies every read and write of it, the owner of a
+// buffer's state its up-to-date bits, each in consumer and copy order, so
+// every table sees the single-warp path's updates in its order.
+__device__ __forceinline__ uint32_t p4_worker(uint32_t b, uint32_t m, uint32_t devices, uint32_t workers) {
+  return (b * devices + m) % workers;
 }
+// Apply-phase owners among the helpers 1 .. workers-1: with three or more
+// workers the last one keeps the buffer states, the others the allocations.
+__device__ __forceinline__ uint32_t p4_alloc_owner(uint32_t aid, uint32_t workers) {
+  return workers <= 2 ? 1u : 1u + aid % (workers - 2);
+}
+__device__ __forceinline__ uint32_t p4_state_owner(uint32_t workers) { return workers - 1; }
 
 __device__ Stage make_stage(const NodeDev* nd, uint32_t w) {
   Stage st;
@@ -2724,16 +2793,27 @@ __device__ Stage make_stage(const NodeDev* nd, uint32_t w) {
   return st;
 }
 
+// The stale consumer in PC entry k: its buffer, memory and planning worker.
+struct P4Consumer {
+  uint32_t b, m, w;
+};
+__device__ __forceinline__ P4Consumer p4_of(const WorkJob& j, uint32_t k) {
+  const uint32_t i = t_v(j.PC, 0, k);
+  P4Consumer r;
+  r.b = j.task->acc[i % j.na].buffer;
+  r.m = t_v(j.CH, 1, i / j.na);
+  r.w = p4_worker(r.b, r.m, j.devices, j.workers);
+  return r;
+}
+
 __device__ __noinline__ void p4_share(Ctx& c, WorkJob& j, uint32_t w) {
   Stage st = make_stage(c.nd, w);
   c.stage = &st;
   const Table& PC = j.PC;
   const igs_task& t = *j.task;
   for (uint32_t k = 0; k < PC.n && !c.err; ++k) {
-    const uint32_t flags = t_key(PC, k);
-    if (!flags) continue;
-    const uint32_t a = t_v(PC, 0, k) % j.na;
-    if (buffer_worker(j, t.acc[a].buffer) != w) continue;
+    if (!(t_key(PC, k) & 2u)) continue;
+    if (p4_of(j, k).w != w) continue;
     const uint32_t first = st.n_instr;
     if (!p4_consumer(c, t, j.seq, j.CH, PC, k, j.na, false)) break;
     __syncwarp();
@@ -2746,47 +2826,55 @@ __device__ __noinline__ void p4_share(Ctx& c, WorkJob& j, uint32_t w) {
   c.stage = nullptr;
 }
 
-// After warp 0 has given the staged copies their ids: the provisional ids in
-// the allocation tables of worker w's buffers become final.
-__device__ __noinline__ void p4_final_ids(Ctx& c, const WorkJob& j, uint32_t w) {
-  const uint32_t* map = helper_table(c.nd, w, 11);
-  for (uint32_t li = 0; li < j.n_live; ++li) {
-    const uint32_t aid = c.nd->live[li];
-    const uint32_t b = c.nd->allocs[aid].buffer;
-    bool mine = false;
-    for (uint32_t i = 0; i < j.nbuf; ++i)
-      if (j.buf[i] == b) mine = (i % j.workers) == w;
-    if (!mine) continue;
-    for (int k = 0; k < 2; ++k) {
-      const Table T = k == 0 ? wr_t(c, aid) : rd_t(c, aid);
-      for (uint32_t base = 0; base < T.n; base += 32) {
-        const uint32_t i = base + laneid();
-        if (i < T.n && t_key(T, i) != DEAD) {
-          const uint32_t v = t_v(T, 0, i);
-          if (v & PROV) FLD(T, F_V, i) = map[v & 0xFFFFFFu];
-        }
-      }
+// Helper w's part of the apply phase (the final ids are in the stages' maps).
+__device__ __noinline__ void p4_apply(Ctx& c, const WorkJob& j, uint32_t w) {
+  const Table& PC = j.PC;
+  const bool states = p4_state_owner(j.workers) == w;
+  for (uint32_t k = 0; k < PC.n && !c.err; ++k) {
+    if (!(t_key(PC, k) & 2u)) continue;
+    const P4Consumer pc = p4_of(j, k);
+    const Stage st = make_stage(c.nd, pc.w);
+    const uint32_t first = FLD(PC, F_V + 1, k), cnt = FLD(PC, F_V + 2, k);
+    Table B;
+    uint32_t from_bst = 0;
+    if (states) {
+      B = bst_t(c, pc.b);
+      t_tidy(c, B);
+      from_bst = B.n;
     }
+    for (uint32_t q = first; q < first + cnt; ++q) {
+      const igs_instruction r = st.instrs[q];
+      const uint32_t id = st.map[q];
+      auto box = [&](uint32_t e, Bx& x) {
+        const igs_box o = st.boxes[r.box_off + e];
+        for (int d = 0; d < 3; ++d) {
+          x.lo[d] = o.lo[d];
+          x.hi[d] = o.hi[d];
+        }
+        return true;
+      };
+      // a copy reads allocation r.a and writes r.b (reads first, as emit_apply)
+      if (p4_alloc_owner(r.a, j.workers) == w && !apply_read(c, r.a, r.box_cnt, box, id, false)) return;
+      if (p4_alloc_owner(r.b, j.workers) == w && !apply_write(c, r.b, r.box_cnt, box, id)) return;
+      if (states)
+        for (uint32_t e = 0; e < r.box_cnt; ++e) {
+          Bx x;
+          box(e, x);
+          t_or(c, B, NONE, x, 2, 1u << pc.m);
+          if (c.err) return;
+        }
+    }
+    if (states) t_merge_from(c, B, from_bst);
   }
-  __syncwarp();
 }
 
-// Warp 0: coherence with the helpers, then the staged copies in consumer
-// order (final ids, edges, boxes, records), then the ids in the tables.
+// Warp 0: plan with the helpers; then, in consumer order, the warnings of
+// uninitialized reads, the copies' final ids and the capacity checks; then
+// the append (warp 0) beside the table updates (helpers).
 __device__ __noinline__ void p4_parallel(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, Table& PC,
                                          uint32_t na) {
   BlockShared& sh = *static_cast<BlockShared*>(c.block);
   WorkJob& j = sh.job;
-  uint32_t bufs[IGS_MAX_ACCESSORS], nbuf = 0;
-  for (uint32_t done = 0;;) {
-    uint32_t b = NONE;
-    for (uint32_t a = 0; a < na; ++a)
-      if (!(done >> a & 1u) && (t.acc[a].mode & IGS_READ) && (b == NONE || t.acc[a].buffer < b)) b = t.acc[a].buffer;
-    if (b == NONE) break;
-    for (uint32_t a = 0; a < na; ++a)
-      if (t.acc[a].buffer == b) done |= 1u << a;
-    bufs[nbuf++] = b;
-  }
   __syncwarp();
   if (laneid() == 0) {
     j.nd = c.nd;
@@ -2799,12 +2887,12 @@ __device__ __noinline__ void p4_parallel(Ctx& c, const igs_task& t, uint32_t seq
     j.epoch = c.epoch;
     j.node = c.node;
     j.workers = c.workers;
+    j.devices = c.D;
     j.n_live = c.n_live;
-    j.nbuf = nbuf;
-    for (uint32_t i = 0; i < nbuf; ++i) j.buf[i] = bufs[i];
   }
   if (!run_shared(c, sh, CMD_P4, [&]() { p4_share(c, j, 0); })) return;
   NodeDev* nd = c.nd;
+  uint32_t next = c.n_instr, n_edge = 0, n_box = 0;
   for (uint32_t k = 0; k < PC.n; ++k) {
     const uint32_t flags = t_key(PC, k);
     if (!flags) continue;
@@ -2825,50 +2913,57 @@ __device__ __noinline__ void p4_parallel(Ctx& c, const igs_task& t, uint32_t seq
       __syncwarp();
     }
     if (!(flags & 2u)) continue;
-    const uint32_t a = t_v(PC, 0, k) % na;
-    const uint32_t w = buffer_worker(j, t.acc[a].buffer);
-    const Stage st = make_stage(nd, w);
+    const Stage st = make_stage(nd, p4_of(j, k).w);
     const uint32_t first = FLD(PC, F_V + 1, k), cnt = FLD(PC, F_V + 2, k);
-    for (uint32_t q = first; q < first + cnt; ++q) {
-      const igs_instruction r = st.instrs[q];
-      const uint32_t id = c.n_instr;
-      if (c.n_instr + 1 > nd->cap_instr || c.n_edge + r.bind_cnt > nd->cap_edge) {
-        fail_cap(c, CAP_EDGE, nd->cap_edge);
-        return;
-      }
-      if (c.n_box + r.box_cnt > nd->cap_box) {
-        fail_cap(c, CAP_BOX, nd->cap_box);
-        return;
-      }
-      __syncwarp();
-      if (laneid() == 0) {
-        st.map[q] = id;
-        nd->has_succ[id] = 0;
-      }
-      __syncwarp();
-      for (uint32_t e = laneid(); e < r.bind_cnt; e += 32) {
-        igs_edge ed = st.edges[r.bind_off + e];
-        if (ed.from & PROV) ed.from = st.map[ed.from & 0xFFFFFFu];  // an earlier copy of this worker
-        ed.to = id;
-        nd->edges[c.n_edge + e] = ed;
-        nd->has_succ[ed.from] = 1;
-      }
-      for (uint32_t e = laneid(); e < r.box_cnt; e += 32) nd->boxes[c.n_box + e] = st.boxes[r.box_off + e];
-      if (laneid() == 0) {
-        igs_instruction o = r;
-        o.id = id;
-        o.box_off = c.n_box;
-        o.bind_off = c.n_bind;
-        o.bind_cnt = 0;
-        nd->instrs[id] = o;
-      }
-      c.n_edge += r.bind_cnt;
-      c.n_box += r.box_cnt;
-      c.n_instr += 1;
-      __syncwarp();
+    for (uint32_t q = first + laneid(); q < first + cnt; q += 32) {
+      st.map[q] = next + (q - first);
+      n_edge += st.instrs[q].bind_cnt;
+      n_box += st.instrs[q].box_cnt;
     }
+    next += cnt;
   }
-  run_shared(c, sh, CMD_P4_IDS, [&]() { p4_final_ids(c, j, 0); });
+  n_edge = warp_sum(n_edge);
+  n_box = warp_sum(n_box);
+  if (next > nd->cap_instr || c.n_edge + n_edge > nd->cap_edge) {
+    fail_cap(c, CAP_EDGE, nd->cap_edge);
+    return;
+  }
+  if (c.n_box + n_box > nd->cap_box) {
+    fail_cap(c, CAP_BOX, nd->cap_box);
+    return;
+  }
+  __syncwarp();
+  run_shared(c, sh, CMD_P4_APPLY, [&]() {
+    for (uint32_t k = 0; k < PC.n; ++k) {
+      if (!(t_key(PC, k) & 2u)) continue;
+      const Stage st = make_stage(nd, p4_of(j, k).w);
+      const uint32_t first = FLD(PC, F_V + 1, k), cnt = FLD(PC, F_V + 2, k);
+      for (uint32_t q = first; q < first + cnt; ++q) {
+        const igs_instruction r = st.instrs[q];
+        const uint32_t id = c.n_instr;
+        if (laneid() == 0) nd->has_succ[id] = 0;
+        // the predecessors were marked when the edges were staged
+        for (uint32_t e = laneid(); e < r.bind_cnt; e += 32) {
+          igs_edge ed = st.edges[r.bind_off + e];
+          ed.to = id;
+          nd->edges[c.n_edge + e] = ed;
+        }
+        for (uint32_t e = laneid(); e < r.box_cnt; e += 32) nd->boxes[c.n_box + e] = st.boxes[r.box_off + e];
+        if (laneid() == 0) {
+          igs_instruction o = r;
+          o.id = id;
+          o.box_off = c.n_box;
+          o.bind_off = c.n_bind;
+          o.bind_cnt = 0;
+          nd->instrs[id] = o;
+        }
+        c.n_edge += r.bind_cnt;
+        c.n_box += r.box_cnt;
+        c.n_instr += 1;
+        __syncwarp();
+      }
+    }
+  });
 }
 
 // Helper warp w: waits for work from warp 0, does its share, reports.
@@ -2877,7 +2972,7 @@ __device__ void helper_loop(BlockShared& sh, uint32_t w, uint32_t workers) {
     worker_bar(workers);
     const uint32_t cmd = sh.cmd;
     if (cmd == CMD_EXIT) break;
-    if (cmd == CMD_P5 || cmd == CMD_A3 || cmd == CMD_P4 || cmd == CMD_P4_IDS) {
+    if (cmd == CMD_P5 || cmd == CMD_A3 || cmd == CMD_P4 || cmd == CMD_P4_APPLY) {
       WorkJob& j = sh.job;
       Ctx hc;
       load_ctx(hc, j.nd, j.pg);
@@ -2886,12 +2981,12 @@ __device__ void helper_loop(BlockShared& sh, uint32_t w, uint32_t workers) {
       hc.node = j.node;
       hc.lock = &sh.lock;
       hc.helper = true;
-      if (cmd == CMD_P4 || cmd == CMD_P4_IDS) {
+      if (cmd == CMD_P4 || cmd == CMD_P4_APPLY) {
         hc.n_live = j.n_live;
         const int tabs[8] = {S_T0, S_T1, S_T2, S_T3, S_T5, S_RG, S_CAN, S_DEP};
         for (int k = 0; k < 8; ++k) hc.s[tabs[k]].base = helper_table(j.nd, w, k);
         if (cmd == CMD_P4) p4_share(hc, j, w);
-        else p4_final_ids(hc, j, w);
+        else p4_apply(hc, j, w);
       } else if (cmd == CMD_P5) {
         hc.s[S_DEP].base = helper_table(j.nd, w, 0);
         hc.s[S_T4].base = helper_table(j.nd, w, 1);
@@ -3248,16 +3343,19 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     }
     __syncwarp();
   }
-  // stale consumers of several buffers: shared by the helper warps
+  // stale consumers that more than one worker would plan: shared by the
+  // helper warps
   bool multi = false;
   if (c.block && c.workers > 1 && c.nd->helper_scratch && !c.nd->stage_d2d) {
-    uint32_t first_b = NONE;
-    for (uint32_t k = 0; k < PC.n && !multi; ++k) {
-      if (!(t_key(PC, k) & 2u)) continue;
-      const uint32_t b = t.acc[t_v(PC, 0, k) % na].buffer;
-      if (first_b == NONE) first_b = b;
-      else if (b != first_b) multi = true;
+    uint32_t used = 0;
+    for (uint32_t base = 0; base < PC.n; base += 32) {
+      const uint32_t k = base + laneid();
+      if (k < PC.n && (t_key(PC, k) & 2u)) {
+        const uint32_t i = t_v(PC, 0, k);
+        used |= 1u << p4_worker(t.acc[i % na].buffer, t_v(CH, 1, i / na), c.D, c.workers);
+      }
     }
+    multi = __popc(warp_or(used)) >= 2;
   }
   if (multi) {
     p4_parallel(c, t, seq, CH, PC, na);

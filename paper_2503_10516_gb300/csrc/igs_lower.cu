@@ -533,6 +533,17 @@ __device__ __forceinline__ uint32_t warp_or(uint32_t v) {
   return v;
 }
 __device__ __forceinline__ uint32_t warp_sum(uint32_t v) { return __reduce_add_sync(FULL, v); }
+// Exclusive prefix sum over the lanes; total: the sum over all lanes.
+__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t& total) {
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, x, o);
+    if ((int)laneid() >= o) x += y;
+  }
+  total = __shfl_sync(FULL, x, 31);
+  return x - v;
+}
 __device__ __forceinline__ Bx warp_bbox(Bx b, bool valid) {
   Bx r;
 #pragma unroll
@@ -2074,7 +2085,9 @@ __device__ __forceinline__ bool union_is_image(const igs_task& t, uint32_t acc, 
 // parts touch disjoint tables and emit nothing whose id depends on another
 // part are shared: warp 0 posts a job, every worker does its share, warp 0
 // then appends the parts' results in the order of the single-warp path.
-enum BlockCmd : uint32_t { CMD_NONE = 0, CMD_P5 = 1, CMD_A3 = 2, CMD_P4 = 3, CMD_P4_APPLY = 4, CMD_EXIT = 5 };
+enum BlockCmd : uint32_t {
+  CMD_NONE = 0, CMD_P5 = 1, CMD_A3 = 2, CMD_P4 = 3, CMD_P4_APPLY = 4, CMD_EXIT = 5, CMD_P5_PLAN = 6, CMD_P5_FINISH = 7
+};
 __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg);
 
 struct WorkJob {
@@ -2966,13 +2979,16 @@ __device__ __noinline__ void p4_parallel(Ctx& c, const igs_task& t, uint32_t seq
   });
 }
 
+__device__ __noinline__ void p5_plan(Ctx& c, const WorkJob& j, uint32_t w);
+__device__ __noinline__ void p5_finish(Ctx& c, const WorkJob& j, uint32_t w);
+
 // Helper warp w: waits for work from warp 0, does its share, reports.
 __device__ void helper_loop(BlockShared& sh, uint32_t w, uint32_t workers) {
   for (;;) {
     worker_bar(workers);
     const uint32_t cmd = sh.cmd;
     if (cmd == CMD_EXIT) break;
-    if (cmd == CMD_P5 || cmd == CMD_A3 || cmd == CMD_P4 || cmd == CMD_P4_APPLY) {
+    if (cmd != CMD_NONE) {
       WorkJob& j = sh.job;
       Ctx hc;
       load_ctx(hc, j.nd, j.pg);
@@ -2987,10 +3003,13 @@ __device__ void helper_loop(BlockShared& sh, uint32_t w, uint32_t workers) {
         for (int k = 0; k < 8; ++k) hc.s[tabs[k]].base = helper_table(j.nd, w, k);
         if (cmd == CMD_P4) p4_share(hc, j, w);
         else p4_apply(hc, j, w);
-      } else if (cmd == CMD_P5) {
+      } else if (cmd == CMD_P5 || cmd == CMD_P5_PLAN || cmd == CMD_P5_FINISH) {
         hc.s[S_DEP].base = helper_table(j.nd, w, 0);
         hc.s[S_T4].base = helper_table(j.nd, w, 1);
-        p5_share(hc, j, w);
+        hc.s[S_T3].base = helper_table(j.nd, w, 3);
+        if (cmd == CMD_P5) p5_share(hc, j, w);
+        else if (cmd == CMD_P5_PLAN) p5_plan(hc, j, w);
+        else p5_finish(hc, j, w);
       } else {
         hc.s[S_T0].base = helper_table(j.nd, w, 0);
         hc.s[S_T1].base = helper_table(j.nd, w, 1);
@@ -3066,6 +3085,294 @@ __device__ __noinline__ void p5_parallel(Ctx& c, const igs_task& t, uint32_t seq
                      false))
       return;
   }
+}
+
+// The buffer state of every region task t writes (AL[slot * na].v0: the
+// chunk's kernel); NB: scratch for the nodes' bounding boxes.
+__device__ __noinline__ void p5_state(Ctx& c, const igs_task& t, const Table& CH, const Table& MP, const Table& AL,
+                                      Table& NB) {
+  const uint32_t na = t.num_accessors;
+  // buffer state of every written region: a local chunk's kernel is its
+  // original producer in the chunk's memory; writes of other nodes make the
+  // local copies stale. The written regions of one accessor are disjoint
+  // (overlapping writes were rejected), so the order of these updates does
+  // not matter.
+  node_bboxes(c, CH, NB);
+  for (uint32_t a = 0; a < na; ++a) {
+    if (!(t.acc[a].mode & IGS_WRITE)) continue;
+    const BufDesc& bd = buf_of(c, t.acc[a].buffer);
+    Table B = bst_t(c, t.acc[a].buffer);
+    t_tidy(c, B);
+    const uint32_t from = B.n;
+    if (union_is_image(t, a, bd)) {
+      // all chunks' writes form the image of the task's range: one subtraction
+      Bx all;
+      all.lo[0] = all.lo[1] = all.lo[2] = 0xFFFFFFFFu;
+      all.hi[0] = all.hi[1] = all.hi[2] = 0;
+      for (uint32_t m = 0; m < c.N; ++m)
+        if (t_key(NB, m) != DEAD) all = bx_union(all, t_box(NB, m));
+      const Bx U = map_box(t.acc[a], all, bd);
+      if (!bx_empty(U)) t_subtract(c, B, NONE, U);
+      for (uint32_t base = 0; base < CH.n; base += 32) {
+        const uint32_t slot = base + laneid();
+        bool hit = false;
+        Bx x{};
+        uint32_t kid = 0, mem = 0;
+        if (slot < CH.n && t_v(CH, 0, slot) == c.node) {
+          x = t_box(MP, slot * na + a);
+          hit = !bx_empty(x);
+          kid = FLD(AL, F_V, slot * na);
+          mem = t_v(CH, 1, slot);
+        }
+        const uint32_t s = t_claim(c, B, hit);
+        if (c.err) return;
+        if (hit) t_put(B, s, 0, x, kid, mem, 1u << mem);
+      }
+      for (uint32_t m = 0; m < c.N; ++m) {
+        if (m == c.node || t_key(NB, m) == DEAD) continue;
+        const Bx x = map_box(t.acc[a], t_box(NB, m), bd);
+        if (bx_empty(x)) continue;
+        const uint32_t s = t_claim(c, B, laneid() == 0);
+        if (c.err) return;
+        if (laneid() == 0) t_put(B, s, 0, x, REMOTE, 0, 0);
+        __syncwarp();
+      }
+    } else {
+      for (uint32_t slot = 0; slot < CH.n; ++slot) {
+        const Bx x = t_box(MP, slot * na + a);
+        if (bx_empty(x)) continue;
+        if (t_v(CH, 0, slot) == c.node) {
+          const uint32_t mem = t_v(CH, 1, slot);
+          t_set(c, B, NONE, x, FLD(AL, F_V, slot * na), mem, 1u << mem);
+        } else {
+          t_set(c, B, NONE, x, REMOTE, 0, 0);
+        }
+        if (c.err) return;
+      }
+    }
+    __syncwarp();
+    t_merge_from(c, B, from);
+    t_maybe_merge(c, B, 4 * CH.n + 64);
+  }
+}
+
+// Kernel phase planned per chunk (P5). When no buffer the task writes is
+// accessed through a second accessor, no two kernels of the task touch an
+// overlapping region of one allocation unless both only read it (the written
+// regions of an accessor are disjoint), so no kernel of the task depends on
+// another and their dependencies can be found against the tables as they
+// were before the phase. Plan: worker li mod workers takes the li-th local
+// chunk and stages its edges. Finish: every worker writes the records of
+// the chunks it planned at offsets fixed in between; the owner of an
+// allocation applies every access to it in chunk and accessor order (reads,
+// then writes, as emit_apply), and the last worker updates the buffer state,
+// so every table sees the single-warp path's updates in its order.
+__device__ __forceinline__ bool p5_plannable(const igs_task& t) {
+  for (uint32_t a = 0; a < t.num_accessors; ++a) {
+    if (!(t.acc[a].mode & IGS_WRITE)) continue;
+    for (uint32_t o = 0; o < t.num_accessors; ++o)
+      if (o != a && t.acc[o].buffer == t.acc[a].buffer) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ uint32_t p5_alloc_owner(uint32_t aid, uint32_t workers) {
+  return workers <= 2 ? aid % workers : aid % (workers - 1);
+}
+
+// AL[slot * na] of a local chunk: v0 kernel id, v1 / v2 staged edges (offset
+// in the planning worker's stage, count), v3 / v4 first edge / box in the
+// graph, lo[0] first binding in the graph.
+constexpr int F_EDGE_AT = F_V + 3, F_BOX_AT = F_V + 4, F_BIND_AT = F_LO;
+
+__device__ __noinline__ void p5_plan(Ctx& c, const WorkJob& j, uint32_t w) {
+  const Table& CH = j.CH;
+  const Table& AL = j.AL;
+  const uint32_t na = j.na;
+  Table& BT = c.s[S_T4];
+  igs_edge* stage = stage_of(j, w);
+  uint32_t off = 0, li = 0;
+  for (uint32_t slot = 0; slot < CH.n && !c.err; ++slot) {
+    if (t_v(CH, 0, slot) != j.node) continue;
+    if (li++ % j.workers != w) continue;
+    const uint32_t kid = FLD(AL, F_V, slot * na);
+    __syncwarp();
+    if (laneid() == 0) c.nd->has_succ[kid] = 0;
+    Acc acc[IGS_MAX_ACCESSORS];
+    int nacc = 0;
+    if (!p5_accesses(c, *j.task, j.MP, AL, slot, na, BT, acc, nacc)) break;
+    if (!emit_deps(c, acc, nacc, false)) break;
+    const uint32_t ne = emit_edges(c, kid, stage + off, j.stage_cap - off, CAP_TABLE, j.stage_cap);
+    if (ne == NONE) break;
+    __syncwarp();
+    if (laneid() == 0) {
+      FLD(AL, F_V + 1, slot * na) = off;
+      FLD(AL, F_V + 2, slot * na) = ne;
+    }
+    off += ne;
+  }
+  __syncwarp();
+}
+
+__device__ __noinline__ void p5_finish(Ctx& c, const WorkJob& j, uint32_t w) {
+  const Table& CH = j.CH;
+  const Table& MP = j.MP;
+  const Table& AL = j.AL;
+  const igs_task& t = *j.task;
+  const uint32_t na = j.na;
+  NodeDev* nd = c.nd;
+  Table& BT = c.s[S_T4];
+  const igs_edge* stage = stage_of(j, w);
+  // the records of the chunks this worker planned
+  uint32_t li = 0;
+  for (uint32_t slot = 0; slot < CH.n && !c.err; ++slot) {
+    if (t_v(CH, 0, slot) != j.node) continue;
+    if (li++ % j.workers != w) continue;
+    const uint32_t i0 = slot * na;
+    const uint32_t kid = FLD(AL, F_V, i0), off = FLD(AL, F_V + 1, i0), ne = FLD(AL, F_V + 2, i0);
+    const uint32_t e_at = FLD(AL, F_EDGE_AT, i0), b_at = FLD(AL, F_BOX_AT, i0), d_at = FLD(AL, F_BIND_AT, i0);
+    for (uint32_t e = laneid(); e < ne; e += 32) nd->edges[e_at + e] = stage[off + e];
+    Acc acc[IGS_MAX_ACCESSORS];
+    int nacc = 0;
+    if (!p5_accesses(c, t, MP, AL, slot, na, BT, acc, nacc)) break;
+    const Ent ch = t_ent(CH, slot);
+    const uint32_t nb = ch.key != DEAD ? 1u : 0u;
+    if (laneid() < na) {
+      const Ent bi = t_ent(BT, laneid());
+      igs_binding o;
+      o.alloc = bi.v0;
+      for (int d = 0; d < 3; ++d) {
+        o.lo[d] = bi.b.lo[d];
+        o.hi[d] = bi.b.hi[d];
+      }
+      nd->binds[d_at + laneid()] = o;
+    }
+    if (laneid() == 0) {
+      if (nb) {
+        igs_box o;
+        for (int d = 0; d < 3; ++d) {
+          o.lo[d] = ch.b.lo[d];
+          o.hi[d] = ch.b.hi[d];
+        }
+        nd->boxes[b_at] = o;
+      }
+      igs_instruction r;
+      r.id = kid;
+      r.type = IGS_KERNEL;
+      r.seq = j.seq;
+      r.a = ch.key;
+      r.b = ch.v1;  // the chunk's memory
+      r.c = t.kernel_id;
+      r.d = NONE;
+      r.box_off = b_at;
+      r.box_cnt = nb;
+      r.bind_off = d_at;
+      r.bind_cnt = na;
+      nd->instrs[kid] = r;
+    }
+    __syncwarp();
+  }
+  // the accesses to the allocations this worker owns
+  for (uint32_t slot = 0; slot < CH.n && !c.err; ++slot) {
+    if (t_v(CH, 0, slot) != j.node) continue;
+    const uint32_t kid = FLD(AL, F_V, slot * na);
+    for (int pass = 0; pass < 2; ++pass) {
+      const uint32_t mode = pass == 0 ? IGS_READ : IGS_WRITE;
+      for (uint32_t a = 0; a < na; ++a) {
+        const uint32_t al = FLD(AL, F_KEY, slot * na + a);
+        if (al == NONE || !(t.acc[a].mode & mode) || p5_alloc_owner(al, j.workers) != w) continue;
+        const Bx x = t_box(MP, slot * na + a);
+        auto box = [&](uint32_t, Bx& q) {
+          q = x;
+          return true;
+        };
+        bool ok;
+        if (pass == 0) {
+          bool again = false;
+          for (uint32_t o = 0; o < a; ++o)
+            if ((t.acc[o].mode & IGS_READ) && FLD(AL, F_KEY, slot * na + o) == al) again = true;
+          ok = apply_read(c, al, 1, box, kid, again);
+        } else {
+          ok = apply_write(c, al, 1, box, kid);
+        }
+        if (!ok) return;
+      }
+    }
+  }
+  if (w == j.workers - 1) p5_state(c, t, CH, MP, AL, c.s[S_T3]);
+}
+
+// Warp 0: plan with the helpers, fix every local kernel's place in the
+// graph (ids were given before the phase), finish with the helpers.
+__device__ __noinline__ void p5_planned(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP,
+                                        Table& AL, uint32_t na) {
+  BlockShared& sh = *static_cast<BlockShared*>(c.block);
+  NodeDev* nd = c.nd;
+  uint32_t next = c.n_instr;
+  for (uint32_t slot = 0; slot < CH.n; ++slot) {
+    if (t_v(CH, 0, slot) != c.node) continue;
+    if (laneid() == 0) FLD(AL, F_V, slot * na) = next;
+    ++next;
+  }
+  __syncwarp();
+  if (laneid() == 0) {
+    WorkJob& j = sh.job;
+    j.nd = nd;
+    j.pg = c.pg;
+    j.task = &t;
+    j.CH = CH;
+    j.MP = MP;
+    j.AL = AL;
+    j.na = na;
+    j.seq = seq;
+    j.epoch = c.epoch;
+    j.node = c.node;
+    j.workers = c.workers;
+    j.stage_cap = nd->cap_scratch * (F_COUNT * 4 / (uint32_t)sizeof(igs_edge));
+    j.stage0 = reinterpret_cast<igs_edge*>(c.s[S_T0].base);
+  }
+  if (!run_shared(c, sh, CMD_P5_PLAN, [&]() { p5_plan(c, sh.job, 0); })) return;
+  // places in chunk order; the first kernel that would overflow a capacity
+  // fails as in the single-warp path (edges and records, then boxes, then
+  // bindings)
+  uint32_t n_edge = c.n_edge, n_box = c.n_box, n_bind = c.n_bind, n_k = 0, bad = NONE, bad_kind = 0;
+  for (uint32_t base = 0; base < CH.n; base += 32) {
+    const uint32_t slot = base + laneid();
+    const bool local = slot < CH.n && t_v(CH, 0, slot) == c.node;
+    const uint32_t ne = local ? FLD(AL, F_V + 2, slot * na) : 0u;
+    const uint32_t nb = local && t_key(CH, slot) != DEAD ? 1u : 0u;
+    uint32_t te, tb, tk;
+    const uint32_t xe = warp_excl_scan(ne, te), xb = warp_excl_scan(nb, tb), xk = warp_excl_scan(local ? 1u : 0u, tk);
+    uint32_t kind = 0;
+    if (local) {
+      FLD(AL, F_EDGE_AT, slot * na) = n_edge + xe;
+      FLD(AL, F_BOX_AT, slot * na) = n_box + xb;
+      FLD(AL, F_BIND_AT, slot * na) = n_bind + xk * na;
+      if (n_edge + xe + ne > nd->cap_edge || c.n_instr + n_k + xk + 1 > nd->cap_instr) kind = 1;
+      else if (n_box + xb + nb > nd->cap_box) kind = 2;
+      else if (n_bind + (xk + 1) * na > nd->cap_bind) kind = 3;
+    }
+    const uint32_t fails = __ballot_sync(FULL, kind != 0);
+    if (fails && bad == NONE) {
+      bad = base + __ffs(fails) - 1;
+      bad_kind = __shfl_sync(FULL, kind, __ffs(fails) - 1);
+    }
+    n_edge += te;
+    n_box += tb;
+    n_bind += tk * na;
+    n_k += tk;
+  }
+  if (bad != NONE) {
+    if (bad_kind == 1) fail_cap(c, CAP_EDGE, nd->cap_edge);
+    else if (bad_kind == 2) fail_cap(c, CAP_BOX, nd->cap_box);
+    else fail_cap(c, CAP_BIND, nd->cap_bind);
+    return;
+  }
+  __syncwarp();
+  if (!run_shared(c, sh, CMD_P5_FINISH, [&]() { p5_finish(c, sh.job, 0); })) return;
+  c.n_instr += n_k;
+  c.n_edge = n_edge;
+  c.n_box = n_box;
+  c.n_bind = n_bind;
 }
 
 // ---- compile one task (P1..P5) ----------------------------------------------
@@ -3401,8 +3708,11 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     AL.n = total;
     __syncwarp();
   }
+  bool planned = false;
   if (c.block && c.workers > 1 && c.nd->helper_scratch) {
-    p5_parallel(c, t, seq, CH, MP, AL, na);
+    planned = p5_plannable(t);
+    if (planned) p5_planned(c, t, seq, CH, MP, AL, na);
+    else p5_parallel(c, t, seq, CH, MP, AL, na);
     if (c.err) return;
   } else {
     for (uint32_t slot = 0; slot < CH.n; ++slot) {
@@ -3420,69 +3730,8 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     }
   }
   pt_lap(pt, c, PH_P5);
-  // buffer state of every written region: a local chunk's kernel is its
-  // original producer in the chunk's memory; writes of other nodes make the
-  // local copies stale. The written regions of one accessor are disjoint
-  // (overlapping writes were rejected), so the order of these updates does
-  // not matter.
-  Table& NB = c.s[S_T3];
-  node_bboxes(c, CH, NB);
-  for (uint32_t a = 0; a < na; ++a) {
-    if (!(t.acc[a].mode & IGS_WRITE)) continue;
-    const BufDesc& bd = buf_of(c, t.acc[a].buffer);
-    Table B = bst_t(c, t.acc[a].buffer);
-    t_tidy(c, B);
-    const uint32_t from = B.n;
-    if (union_is_image(t, a, bd)) {
-      // all chunks' writes form the image of the task's range: one subtraction
-      Bx all;
-      all.lo[0] = all.lo[1] = all.lo[2] = 0xFFFFFFFFu;
-      all.hi[0] = all.hi[1] = all.hi[2] = 0;
-      for (uint32_t m = 0; m < c.N; ++m)
-        if (t_key(NB, m) != DEAD) all = bx_union(all, t_box(NB, m));
-      const Bx U = map_box(t.acc[a], all, bd);
-      if (!bx_empty(U)) t_subtract(c, B, NONE, U);
-      for (uint32_t base = 0; base < CH.n; base += 32) {
-        const uint32_t slot = base + laneid();
-        bool hit = false;
-        Bx x{};
-        uint32_t kid = 0, mem = 0;
-        if (slot < CH.n && t_v(CH, 0, slot) == c.node) {
-          x = t_box(MP, slot * na + a);
-          hit = !bx_empty(x);
-          kid = FLD(AL, F_V, slot * na);
-          mem = t_v(CH, 1, slot);
-        }
-        const uint32_t s = t_claim(c, B, hit);
-        if (c.err) return;
-        if (hit) t_put(B, s, 0, x, kid, mem, 1u << mem);
-      }
-      for (uint32_t m = 0; m < c.N; ++m) {
-        if (m == c.node || t_key(NB, m) == DEAD) continue;
-        const Bx x = map_box(t.acc[a], t_box(NB, m), bd);
-        if (bx_empty(x)) continue;
-        const uint32_t s = t_claim(c, B, laneid() == 0);
-        if (c.err) return;
-        if (laneid() == 0) t_put(B, s, 0, x, REMOTE, 0, 0);
-        __syncwarp();
-      }
-    } else {
-      for (uint32_t slot = 0; slot < CH.n; ++slot) {
-        const Bx x = t_box(MP, slot * na + a);
-        if (bx_empty(x)) continue;
-        if (t_v(CH, 0, slot) == c.node) {
-          const uint32_t mem = t_v(CH, 1, slot);
-          t_set(c, B, NONE, x, FLD(AL, F_V, slot * na), mem, 1u << mem);
-        } else {
-          t_set(c, B, NONE, x, REMOTE, 0, 0);
-        }
-        if (c.err) return;
-      }
-    }
-    __syncwarp();
-    t_merge_from(c, B, from);
-    t_maybe_merge(c, B, 4 * CH.n + 64);
-  }
+  if (!planned) p5_state(c, t, CH, MP, AL, c.s[S_T3]);
+  if (c.err) return;
   // the task's push / await regions are consumed
   for (uint32_t base = qs; base < qe; base += 32) {
     const uint32_t i = base + laneid();

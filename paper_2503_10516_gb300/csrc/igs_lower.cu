@@ -1789,8 +1789,10 @@ __device__ __noinline__ bool map_ids(Ctx& c, Table& T, uint32_t h, bool writers 
 #define IGS_EPOCH_MERGE_FLOOR 16
 #endif
 
-__device__ __noinline__ void apply_epoch(Ctx& c, uint32_t h) {
-  for (uint32_t li = 0; li < c.n_live; ++li) {
+// Worker w of `workers` takes the live allocations li and the buffers b with
+// li, b = w mod workers (the tables are independent of one another).
+__device__ __noinline__ void epoch_share(Ctx& c, uint32_t h, uint32_t w, uint32_t workers) {
+  for (uint32_t li = w; li < c.n_live; li += workers) {
     const uint32_t aid = c.nd->live[li];
     // tables whose ids all stay are left as they are; the others are
     // compacted and, above the floor, re-merged
@@ -1816,7 +1818,7 @@ __device__ __noinline__ void apply_epoch(Ctx& c, uint32_t h) {
     if (c.err) return;
   }
   const uint32_t nb = c.nd->cap_buffers;
-  for (uint32_t b = 0; b < nb; ++b) {
+  for (uint32_t b = w; b < nb && !c.err; b += workers) {
     if (c.nd->bst_d[kDesc * b + 1] == 0) continue;  // no table (never created or destroyed)
     Table B = bst_t(c, b);
     if (B.n == 0) continue;
@@ -1826,7 +1828,6 @@ __device__ __noinline__ void apply_epoch(Ctx& c, uint32_t h) {
     t_compact(c, B);
     t_set_mark(c, B);
   }
-  c.epoch = h;
 }
 
 // Free of an allocation: depends on every writer and reader (allocation lifetime).
@@ -2086,7 +2087,8 @@ __device__ __forceinline__ bool union_is_image(const igs_task& t, uint32_t acc, 
 // part are shared: warp 0 posts a job, every worker does its share, warp 0
 // then appends the parts' results in the order of the single-warp path.
 enum BlockCmd : uint32_t {
-  CMD_NONE = 0, CMD_P5 = 1, CMD_A3 = 2, CMD_P4 = 3, CMD_P4_APPLY = 4, CMD_EXIT = 5, CMD_P5_PLAN = 6, CMD_P5_FINISH = 7
+  CMD_NONE = 0, CMD_P5 = 1, CMD_A3 = 2, CMD_P4 = 3, CMD_P4_APPLY = 4, CMD_EXIT = 5, CMD_P5_PLAN = 6, CMD_P5_FINISH = 7,
+  CMD_EPOCH = 8
 };
 __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg);
 
@@ -2103,7 +2105,8 @@ struct WorkJob {
   Table PC;          // coherence: the consumers (flags, box, v0 = chunk slot * na + accessor,
                      // v1 / v2 = first staged copy and count)
   uint32_t n_live;   // coherence: live allocations (NodeDev's count is stale during a launch)
-  uint32_t devices;  // coherence: devices per node
+  uint32_t devices;  // coherence and kernel phase: devices per node
+  uint32_t horizon;  // a9: the instruction older ids are replaced by
 };
 
 // Pipelined lowering of one node (a launch with several items): a front
@@ -2806,17 +2809,30 @@ __device__ Stage make_stage(const NodeDev* nd, uint32_t w) {
   return st;
 }
 
-// The stale consumer in PC entry k: its buffer, memory and planning worker.
+// The stale consumer in PC entry k: its buffer, memory and planning worker
+// (v3 = worker | memory << 8, v4 = buffer, set when the phase is chosen).
+constexpr int F_P4_WM = F_V + 3, F_P4_BUF = F_V + 4;
 struct P4Consumer {
   uint32_t b, m, w;
 };
-__device__ __forceinline__ P4Consumer p4_of(const WorkJob& j, uint32_t k) {
-  const uint32_t i = t_v(j.PC, 0, k);
+__device__ __forceinline__ P4Consumer p4_of(const Table& PC, uint32_t k) {
+  const uint32_t wm = FLD(PC, F_P4_WM, k);
   P4Consumer r;
-  r.b = j.task->acc[i % j.na].buffer;
-  r.m = t_v(j.CH, 1, i / j.na);
-  r.w = p4_worker(r.b, r.m, j.devices, j.workers);
+  r.b = FLD(PC, F_P4_BUF, k);
+  r.m = wm >> 8;
+  r.w = wm & 0xFFu;
   return r;
+}
+// Calls f(k) in consumer order for the PC entries whose flags meet `want`
+// (and, unless w is NONE, that worker w plans), until f returns false.
+template <class F>
+__device__ __forceinline__ void p4_each(const Table& PC, uint32_t want, uint32_t w, F f) {
+  for (uint32_t base = 0; base < PC.n; base += 32) {
+    const uint32_t k = base + laneid();
+    const bool hit = k < PC.n && (t_key(PC, k) & want) && (w == NONE || (FLD(PC, F_P4_WM, k) & 0xFFu) == w);
+    for (uint32_t m = __ballot_sync(FULL, hit); m; m &= m - 1)
+      if (!f(base + __ffs(m) - 1)) return;
+  }
 }
 
 __device__ __noinline__ void p4_share(Ctx& c, WorkJob& j, uint32_t w) {
@@ -2824,18 +2840,17 @@ __device__ __noinline__ void p4_share(Ctx& c, WorkJob& j, uint32_t w) {
   c.stage = &st;
   const Table& PC = j.PC;
   const igs_task& t = *j.task;
-  for (uint32_t k = 0; k < PC.n && !c.err; ++k) {
-    if (!(t_key(PC, k) & 2u)) continue;
-    if (p4_of(j, k).w != w) continue;
+  p4_each(PC, 2u, w, [&](uint32_t k) -> bool {
     const uint32_t first = st.n_instr;
-    if (!p4_consumer(c, t, j.seq, j.CH, PC, k, j.na, false)) break;
+    if (!p4_consumer(c, t, j.seq, j.CH, PC, k, j.na, false)) return false;
     __syncwarp();
     if (laneid() == 0) {
       FLD(PC, F_V + 1, k) = first;
       FLD(PC, F_V + 2, k) = st.n_instr - first;
     }
     __syncwarp();
-  }
+    return true;
+  });
   c.stage = nullptr;
 }
 
@@ -2843,9 +2858,8 @@ __device__ __noinline__ void p4_share(Ctx& c, WorkJob& j, uint32_t w) {
 __device__ __noinline__ void p4_apply(Ctx& c, const WorkJob& j, uint32_t w) {
   const Table& PC = j.PC;
   const bool states = p4_state_owner(j.workers) == w;
-  for (uint32_t k = 0; k < PC.n && !c.err; ++k) {
-    if (!(t_key(PC, k) & 2u)) continue;
-    const P4Consumer pc = p4_of(j, k);
+  p4_each(PC, 2u, NONE, [&](uint32_t k) -> bool {
+    const P4Consumer pc = p4_of(PC, k);
     const Stage st = make_stage(c.nd, pc.w);
     const uint32_t first = FLD(PC, F_V + 1, k), cnt = FLD(PC, F_V + 2, k);
     Table B;
@@ -2867,18 +2881,19 @@ __device__ __noinline__ void p4_apply(Ctx& c, const WorkJob& j, uint32_t w) {
         return true;
       };
       // a copy reads allocation r.a and writes r.b (reads first, as emit_apply)
-      if (p4_alloc_owner(r.a, j.workers) == w && !apply_read(c, r.a, r.box_cnt, box, id, false)) return;
-      if (p4_alloc_owner(r.b, j.workers) == w && !apply_write(c, r.b, r.box_cnt, box, id)) return;
+      if (p4_alloc_owner(r.a, j.workers) == w && !apply_read(c, r.a, r.box_cnt, box, id, false)) return false;
+      if (p4_alloc_owner(r.b, j.workers) == w && !apply_write(c, r.b, r.box_cnt, box, id)) return false;
       if (states)
         for (uint32_t e = 0; e < r.box_cnt; ++e) {
           Bx x;
           box(e, x);
           t_or(c, B, NONE, x, 2, 1u << pc.m);
-          if (c.err) return;
+          if (c.err) return false;
         }
     }
     if (states) t_merge_from(c, B, from_bst);
-  }
+    return c.err == ST_OK;
+  });
 }
 
 // Warp 0: plan with the helpers; then, in consumer order, the warnings of
@@ -2906,14 +2921,13 @@ __device__ __noinline__ void p4_parallel(Ctx& c, const igs_task& t, uint32_t seq
   if (!run_shared(c, sh, CMD_P4, [&]() { p4_share(c, j, 0); })) return;
   NodeDev* nd = c.nd;
   uint32_t next = c.n_instr, n_edge = 0, n_box = 0;
-  for (uint32_t k = 0; k < PC.n; ++k) {
+  p4_each(PC, 3u, NONE, [&](uint32_t k) -> bool {
     const uint32_t flags = t_key(PC, k);
-    if (!flags) continue;
     if (flags & 1u) {
       const uint32_t i = t_v(PC, 0, k), slot = i / na, a = i % na;
       if (c.n_diag >= nd->cap_diag) {
         fail_cap(c, CAP_DIAG, nd->cap_diag);
-        return;
+        return false;
       }
       if (laneid() == 0) {
         igs_diag dg;
@@ -2925,8 +2939,8 @@ __device__ __noinline__ void p4_parallel(Ctx& c, const igs_task& t, uint32_t seq
       c.n_diag += 1;
       __syncwarp();
     }
-    if (!(flags & 2u)) continue;
-    const Stage st = make_stage(nd, p4_of(j, k).w);
+    if (!(flags & 2u)) return true;
+    const Stage st = make_stage(nd, p4_of(PC, k).w);
     const uint32_t first = FLD(PC, F_V + 1, k), cnt = FLD(PC, F_V + 2, k);
     for (uint32_t q = first + laneid(); q < first + cnt; q += 32) {
       st.map[q] = next + (q - first);
@@ -2934,7 +2948,9 @@ __device__ __noinline__ void p4_parallel(Ctx& c, const igs_task& t, uint32_t seq
       n_box += st.instrs[q].box_cnt;
     }
     next += cnt;
-  }
+    return true;
+  });
+  if (c.err) return;
   n_edge = warp_sum(n_edge);
   n_box = warp_sum(n_box);
   if (next > nd->cap_instr || c.n_edge + n_edge > nd->cap_edge) {
@@ -2947,9 +2963,8 @@ __device__ __noinline__ void p4_parallel(Ctx& c, const igs_task& t, uint32_t seq
   }
   __syncwarp();
   run_shared(c, sh, CMD_P4_APPLY, [&]() {
-    for (uint32_t k = 0; k < PC.n; ++k) {
-      if (!(t_key(PC, k) & 2u)) continue;
-      const Stage st = make_stage(nd, p4_of(j, k).w);
+    p4_each(PC, 2u, NONE, [&](uint32_t k) -> bool {
+      const Stage st = make_stage(nd, p4_of(PC, k).w);
       const uint32_t first = FLD(PC, F_V + 1, k), cnt = FLD(PC, F_V + 2, k);
       for (uint32_t q = first; q < first + cnt; ++q) {
         const igs_instruction r = st.instrs[q];
@@ -2975,8 +2990,32 @@ __device__ __noinline__ void p4_parallel(Ctx& c, const igs_task& t, uint32_t seq
         c.n_instr += 1;
         __syncwarp();
       }
-    }
+      return true;
+    });
   });
+}
+
+// a9 over every table: with helper warps, shared by the workers.
+__device__ __noinline__ void apply_epoch(Ctx& c, uint32_t h) {
+  if (c.block && c.workers > 1) {
+    BlockShared& sh = *static_cast<BlockShared*>(c.block);
+    __syncwarp();
+    if (laneid() == 0) {
+      WorkJob& j = sh.job;
+      j.nd = c.nd;
+      j.pg = c.pg;
+      j.epoch = c.epoch;
+      j.node = c.node;
+      j.workers = c.workers;
+      j.n_live = c.n_live;
+      j.horizon = h;
+    }
+    if (!run_shared(c, sh, CMD_EPOCH, [&]() { epoch_share(c, h, 0, c.workers); })) return;
+  } else {
+    epoch_share(c, h, 0, 1);
+    if (c.err) return;
+  }
+  c.epoch = h;
 }
 
 __device__ __noinline__ void p5_plan(Ctx& c, const WorkJob& j, uint32_t w);
@@ -3003,6 +3042,9 @@ __device__ void helper_loop(BlockShared& sh, uint32_t w, uint32_t workers) {
         for (int k = 0; k < 8; ++k) hc.s[tabs[k]].base = helper_table(j.nd, w, k);
         if (cmd == CMD_P4) p4_share(hc, j, w);
         else p4_apply(hc, j, w);
+      } else if (cmd == CMD_EPOCH) {
+        hc.n_live = j.n_live;
+        epoch_share(hc, j.horizon, w, j.workers);
       } else if (cmd == CMD_P5 || cmd == CMD_P5_PLAN || cmd == CMD_P5_FINISH) {
         hc.s[S_DEP].base = helper_table(j.nd, w, 0);
         hc.s[S_T4].base = helper_table(j.nd, w, 1);
@@ -3161,12 +3203,13 @@ __device__ __noinline__ void p5_state(Ctx& c, const igs_task& t, const Table& CH
 // overlapping region of one allocation unless both only read it (the written
 // regions of an accessor are disjoint), so no kernel of the task depends on
 // another and their dependencies can be found against the tables as they
-// were before the phase. Plan: worker li mod workers takes the li-th local
-// chunk and stages its edges. Finish: every worker writes the records of
-// the chunks it planned at offsets fixed in between; the owner of an
-// allocation applies every access to it in chunk and accessor order (reads,
-// then writes, as emit_apply), and the last worker updates the buffer state,
-// so every table sees the single-warp path's updates in its order.
+// were before the phase. Plan: planner li mod planners (every worker but
+// the last) takes the li-th local chunk and stages its edges. Finish: every
+// planner writes the records of the chunks it planned at offsets fixed in
+// between, and the owner of an allocation (a planner) applies every access
+// to it in chunk and accessor order (reads, then writes, as emit_apply); the
+// last worker updates the buffer state meanwhile. Every table sees the
+// single-warp path's updates in its order.
 __device__ __forceinline__ bool p5_plannable(const igs_task& t) {
   for (uint32_t a = 0; a < t.num_accessors; ++a) {
     if (!(t.acc[a].mode & IGS_WRITE)) continue;
@@ -3175,41 +3218,50 @@ __device__ __forceinline__ bool p5_plannable(const igs_task& t) {
   }
   return true;
 }
-__device__ __forceinline__ uint32_t p5_alloc_owner(uint32_t aid, uint32_t workers) {
-  return workers <= 2 ? aid % workers : aid % (workers - 1);
+__device__ __forceinline__ uint32_t p5_planners(uint32_t workers) { return workers - 1; }
+
+// AL entries of a local chunk (index slot * na): v0 kernel id, v1 / v2 staged
+// edges (offset in the planner's stage, count), v3 / v4 first edge / box in
+// the graph, lo[0] first binding in the graph, lo[1] planner. Every entry
+// slot * na + a: lo[2] the worker that applies its access (NONE: none).
+constexpr int F_EDGE_AT = F_V + 3, F_BOX_AT = F_V + 4, F_BIND_AT = F_LO, F_PLANNER = F_LO + 1, F_OWNER = F_LO + 2;
+
+// Calls f(slot) in chunk order for the local chunks planner w plans, until f
+// returns false.
+template <class F>
+__device__ __forceinline__ void p5_each_planned(const WorkJob& j, uint32_t w, F f) {
+  for (uint32_t base = 0; base < j.CH.n; base += 32) {
+    const uint32_t slot = base + laneid();
+    const bool mine = slot < j.CH.n && t_v(j.CH, 0, slot) == j.node && FLD(j.AL, F_PLANNER, slot * j.na) == w;
+    for (uint32_t m = __ballot_sync(FULL, mine); m; m &= m - 1)
+      if (!f(base + __ffs(m) - 1)) return;
+  }
 }
 
-// AL[slot * na] of a local chunk: v0 kernel id, v1 / v2 staged edges (offset
-// in the planning worker's stage, count), v3 / v4 first edge / box in the
-// graph, lo[0] first binding in the graph.
-constexpr int F_EDGE_AT = F_V + 3, F_BOX_AT = F_V + 4, F_BIND_AT = F_LO;
-
 __device__ __noinline__ void p5_plan(Ctx& c, const WorkJob& j, uint32_t w) {
-  const Table& CH = j.CH;
   const Table& AL = j.AL;
   const uint32_t na = j.na;
   Table& BT = c.s[S_T4];
   igs_edge* stage = stage_of(j, w);
-  uint32_t off = 0, li = 0;
-  for (uint32_t slot = 0; slot < CH.n && !c.err; ++slot) {
-    if (t_v(CH, 0, slot) != j.node) continue;
-    if (li++ % j.workers != w) continue;
+  uint32_t off = 0;
+  p5_each_planned(j, w, [&](uint32_t slot) -> bool {
     const uint32_t kid = FLD(AL, F_V, slot * na);
     __syncwarp();
     if (laneid() == 0) c.nd->has_succ[kid] = 0;
     Acc acc[IGS_MAX_ACCESSORS];
     int nacc = 0;
-    if (!p5_accesses(c, *j.task, j.MP, AL, slot, na, BT, acc, nacc)) break;
-    if (!emit_deps(c, acc, nacc, false)) break;
+    if (!p5_accesses(c, *j.task, j.MP, AL, slot, na, BT, acc, nacc)) return false;
+    if (!emit_deps(c, acc, nacc, false)) return false;
     const uint32_t ne = emit_edges(c, kid, stage + off, j.stage_cap - off, CAP_TABLE, j.stage_cap);
-    if (ne == NONE) break;
+    if (ne == NONE) return false;
     __syncwarp();
     if (laneid() == 0) {
       FLD(AL, F_V + 1, slot * na) = off;
       FLD(AL, F_V + 2, slot * na) = ne;
     }
     off += ne;
-  }
+    return true;
+  });
   __syncwarp();
 }
 
@@ -3220,20 +3272,21 @@ __device__ __noinline__ void p5_finish(Ctx& c, const WorkJob& j, uint32_t w) {
   const igs_task& t = *j.task;
   const uint32_t na = j.na;
   NodeDev* nd = c.nd;
+  if (w == p5_planners(j.workers)) {
+    p5_state(c, t, CH, MP, AL, c.s[S_T3]);
+    return;
+  }
   Table& BT = c.s[S_T4];
   const igs_edge* stage = stage_of(j, w);
   // the records of the chunks this worker planned
-  uint32_t li = 0;
-  for (uint32_t slot = 0; slot < CH.n && !c.err; ++slot) {
-    if (t_v(CH, 0, slot) != j.node) continue;
-    if (li++ % j.workers != w) continue;
+  p5_each_planned(j, w, [&](uint32_t slot) -> bool {
     const uint32_t i0 = slot * na;
     const uint32_t kid = FLD(AL, F_V, i0), off = FLD(AL, F_V + 1, i0), ne = FLD(AL, F_V + 2, i0);
     const uint32_t e_at = FLD(AL, F_EDGE_AT, i0), b_at = FLD(AL, F_BOX_AT, i0), d_at = FLD(AL, F_BIND_AT, i0);
     for (uint32_t e = laneid(); e < ne; e += 32) nd->edges[e_at + e] = stage[off + e];
     Acc acc[IGS_MAX_ACCESSORS];
     int nacc = 0;
-    if (!p5_accesses(c, t, MP, AL, slot, na, BT, acc, nacc)) break;
+    if (!p5_accesses(c, t, MP, AL, slot, na, BT, acc, nacc)) return false;
     const Ent ch = t_ent(CH, slot);
     const uint32_t nb = ch.key != DEAD ? 1u : 0u;
     if (laneid() < na) {
@@ -3270,48 +3323,74 @@ __device__ __noinline__ void p5_finish(Ctx& c, const WorkJob& j, uint32_t w) {
       nd->instrs[kid] = r;
     }
     __syncwarp();
-  }
-  // the accesses to the allocations this worker owns
-  for (uint32_t slot = 0; slot < CH.n && !c.err; ++slot) {
-    if (t_v(CH, 0, slot) != j.node) continue;
-    const uint32_t kid = FLD(AL, F_V, slot * na);
-    for (int pass = 0; pass < 2; ++pass) {
-      const uint32_t mode = pass == 0 ? IGS_READ : IGS_WRITE;
-      for (uint32_t a = 0; a < na; ++a) {
-        const uint32_t al = FLD(AL, F_KEY, slot * na + a);
-        if (al == NONE || !(t.acc[a].mode & mode) || p5_alloc_owner(al, j.workers) != w) continue;
-        const Bx x = t_box(MP, slot * na + a);
-        auto box = [&](uint32_t, Bx& q) {
-          q = x;
-          return true;
-        };
-        bool ok;
-        if (pass == 0) {
-          bool again = false;
-          for (uint32_t o = 0; o < a; ++o)
-            if ((t.acc[o].mode & IGS_READ) && FLD(AL, F_KEY, slot * na + o) == al) again = true;
-          ok = apply_read(c, al, 1, box, kid, again);
-        } else {
-          ok = apply_write(c, al, 1, box, kid);
-        }
-        if (!ok) return;
+    return true;
+  });
+  // the accesses this worker applies, in chunk and accessor order: an
+  // allocation of a written buffer serves one accessor (its read, then its
+  // write), one of a read-only buffer only reads, so each allocation sees
+  // emit_apply's order
+  const uint32_t total = CH.n * na;
+  for (uint32_t base = 0; base < total && !c.err; base += 32) {
+    const uint32_t i = base + laneid();
+    const bool mine = i < total && FLD(AL, F_OWNER, i) == w;
+    for (uint32_t m = __ballot_sync(FULL, mine); m; m &= m - 1) {
+      const uint32_t e = base + __ffs(m) - 1, slot = e / na, a = e % na;
+      const uint32_t al = FLD(AL, F_KEY, e), kid = FLD(AL, F_V, slot * na), mode = t.acc[a].mode;
+      const Bx x = t_box(MP, e);
+      auto box = [&](uint32_t, Bx& q) {
+        q = x;
+        return true;
+      };
+      if (mode & IGS_READ) {
+        bool again = false;
+        for (uint32_t o = 0; o < a; ++o)
+          if ((t.acc[o].mode & IGS_READ) && FLD(AL, F_KEY, slot * na + o) == al) again = true;
+        if (!apply_read(c, al, 1, box, kid, again)) return;
       }
+      if ((mode & IGS_WRITE) && !apply_write(c, al, 1, box, kid)) return;
     }
   }
-  if (w == j.workers - 1) p5_state(c, t, CH, MP, AL, c.s[S_T3]);
 }
 
-// Warp 0: plan with the helpers, fix every local kernel's place in the
-// graph (ids were given before the phase), finish with the helpers.
+// Warp 0: kernel ids, planners and owners; plan with the helpers; every
+// local kernel's place in the graph; finish with the helpers.
 __device__ __noinline__ void p5_planned(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP,
                                         Table& AL, uint32_t na) {
   BlockShared& sh = *static_cast<BlockShared*>(c.block);
   NodeDev* nd = c.nd;
-  uint32_t next = c.n_instr;
-  for (uint32_t slot = 0; slot < CH.n; ++slot) {
-    if (t_v(CH, 0, slot) != c.node) continue;
-    if (laneid() == 0) FLD(AL, F_V, slot * na) = next;
-    ++next;
+  const uint32_t planners = p5_planners(c.workers);
+  {
+    uint32_t k = 0;
+    for (uint32_t base = 0; base < CH.n; base += 32) {
+      const uint32_t slot = base + laneid();
+      const bool local = slot < CH.n && t_v(CH, 0, slot) == c.node;
+      const uint32_t mask = __ballot_sync(FULL, local), r = k + __popc(mask & lanemask_lt());
+      if (local) {
+        FLD(AL, F_V, slot * na) = c.n_instr + r;
+        FLD(AL, F_PLANNER, slot * na) = r % planners;
+      }
+      k += __popc(mask);
+    }
+    // an allocation's owner is one function of (buffer, memory): the
+    // accessor that first names the buffer and the chunk's memory
+    const uint32_t total = CH.n * na;
+    for (uint32_t base = 0; base < total; base += 32) {
+      const uint32_t i = base + laneid();
+      if (i < total) {
+        const uint32_t slot = i / na, a = i % na;
+        uint32_t owner = NONE;
+        if (FLD(AL, F_KEY, i) != NONE && t_v(CH, 0, slot) == c.node) {
+          uint32_t first = a;
+          for (uint32_t o = 0; o < a; ++o)
+            if (t.acc[o].buffer == t.acc[a].buffer) {
+              first = o;
+              break;
+            }
+          owner = (first * c.D + t_v(CH, 1, slot)) % planners;
+        }
+        FLD(AL, F_OWNER, i) = owner;
+      }
+    }
   }
   __syncwarp();
   if (laneid() == 0) {
@@ -3327,6 +3406,7 @@ __device__ __noinline__ void p5_planned(Ctx& c, const igs_task& t, uint32_t seq,
     j.epoch = c.epoch;
     j.node = c.node;
     j.workers = c.workers;
+    j.devices = c.D;
     j.stage_cap = nd->cap_scratch * (F_COUNT * 4 / (uint32_t)sizeof(igs_edge));
     j.stage0 = reinterpret_cast<igs_edge*>(c.s[S_T0].base);
   }
@@ -3658,8 +3738,11 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     for (uint32_t base = 0; base < PC.n; base += 32) {
       const uint32_t k = base + laneid();
       if (k < PC.n && (t_key(PC, k) & 2u)) {
-        const uint32_t i = t_v(PC, 0, k);
-        used |= 1u << p4_worker(t.acc[i % na].buffer, t_v(CH, 1, i / na), c.D, c.workers);
+        const uint32_t i = t_v(PC, 0, k), b = t.acc[i % na].buffer, m = t_v(CH, 1, i / na);
+        const uint32_t w = p4_worker(b, m, c.D, c.workers);
+        FLD(PC, F_P4_WM, k) = w | (m << 8);
+        FLD(PC, F_P4_BUF, k) = b;
+        used |= 1u << w;
       }
     }
     multi = __popc(warp_or(used)) >= 2;

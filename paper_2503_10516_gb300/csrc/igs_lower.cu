@@ -2107,6 +2107,7 @@ struct WorkJob {
   uint32_t n_live;   // coherence: live allocations (NodeDev's count is stale during a launch)
   uint32_t devices;  // coherence and kernel phase: devices per node
   uint32_t horizon;  // a9: the instruction older ids are replaced by
+  uint32_t p4_states_later;  // coherence: the up-to-date bits are set in the planned kernel phase
 };
 
 // Pipelined lowering of one node (a launch with several items): a front
@@ -2772,8 +2773,9 @@ __device__ bool p4_consumer(Ctx& c, const igs_task& t, uint32_t seq, const Table
 
 // Coherence with several warps (Sec. 3.3, a5), in two shared phases.
 // Plan: worker p4_worker(b, m) takes, in consumer order, the stale consumers
-// of buffer b on memory m and stages their copies (records, boxes, edges)
-// without changing any table. Planning against the tables as they were
+// of buffer b on memory m whose regions meet another one of that pair (the
+// others go to the workers in turn) and stages their copies (records, boxes,
+// edges) without changing any table. Planning against the tables as they were
 // before the phase gives the single-warp path's copies and edges: a copy
 // reads a region that is up to date at its producer's memory and writes one
 // that is stale at its own, so no copy of the phase reads or writes what
@@ -2783,14 +2785,19 @@ __device__ bool p4_consumer(Ctx& c, const igs_task& t, uint32_t seq, const Table
 // fixed before the phase) while the helpers apply them to the tables: the
 // owner of an allocation applies every read and write of it, the owner of a
 // buffer's state its up-to-date bits, each in consumer and copy order, so
-// every table sees the single-warp path's updates in its order.
+// every table sees the single-warp path's updates in its order. When the
+// kernel phase that follows is planned, the up-to-date bits are set by the
+// last worker while the others plan it (nothing in between reads them).
 __device__ __forceinline__ uint32_t p4_worker(uint32_t b, uint32_t m, uint32_t devices, uint32_t workers) {
   return (b * devices + m) % workers;
 }
 // Apply-phase owners among the helpers 1 .. workers-1: with three or more
-// workers the last one keeps the buffer states, the others the allocations.
-__device__ __forceinline__ uint32_t p4_alloc_owner(uint32_t aid, uint32_t workers) {
-  return workers <= 2 ? 1u : 1u + aid % (workers - 2);
+// workers and the buffer states in this phase, the last one keeps the
+// states, the others the allocations.
+__device__ __forceinline__ uint32_t p4_alloc_owner(uint32_t aid, uint32_t workers, bool states) {
+  if (workers <= 2) return 1u;
+  const uint32_t n = states ? workers - 2 : workers - 1;
+  return 1u + aid % n;
 }
 __device__ __forceinline__ uint32_t p4_state_owner(uint32_t workers) { return workers - 1; }
 
@@ -2854,21 +2861,45 @@ __device__ __noinline__ void p4_share(Ctx& c, WorkJob& j, uint32_t w) {
   c.stage = nullptr;
 }
 
-// Helper w's part of the apply phase (the final ids are in the stages' maps).
-__device__ __noinline__ void p4_apply(Ctx& c, const WorkJob& j, uint32_t w) {
+// The up-to-date bits of the planned copies, in consumer and copy order.
+__device__ __noinline__ void p4_states(Ctx& c, const WorkJob& j) {
   const Table& PC = j.PC;
-  const bool states = p4_state_owner(j.workers) == w;
   p4_each(PC, 2u, NONE, [&](uint32_t k) -> bool {
     const P4Consumer pc = p4_of(PC, k);
     const Stage st = make_stage(c.nd, pc.w);
     const uint32_t first = FLD(PC, F_V + 1, k), cnt = FLD(PC, F_V + 2, k);
-    Table B;
-    uint32_t from_bst = 0;
-    if (states) {
-      B = bst_t(c, pc.b);
-      t_tidy(c, B);
-      from_bst = B.n;
+    Table B = bst_t(c, pc.b);
+    t_tidy(c, B);
+    const uint32_t from_bst = B.n;
+    for (uint32_t q = first; q < first + cnt; ++q) {
+      const igs_instruction r = st.instrs[q];
+      for (uint32_t e = 0; e < r.box_cnt; ++e) {
+        const igs_box o = st.boxes[r.box_off + e];
+        Bx x;
+        for (int d = 0; d < 3; ++d) {
+          x.lo[d] = o.lo[d];
+          x.hi[d] = o.hi[d];
+        }
+        t_or(c, B, NONE, x, 2, 1u << pc.m);
+        if (c.err) return false;
+      }
     }
+    t_merge_from(c, B, from_bst);
+    return c.err == ST_OK;
+  });
+}
+
+// Helper w's part of the apply phase (the final ids are in the stages' maps).
+__device__ __noinline__ void p4_apply(Ctx& c, const WorkJob& j, uint32_t w) {
+  const Table& PC = j.PC;
+  const bool states = !j.p4_states_later;
+  if (states && p4_state_owner(j.workers) == w && j.workers > 2) {
+    p4_states(c, j);
+    return;
+  }
+  p4_each(PC, 2u, NONE, [&](uint32_t k) -> bool {
+    const Stage st = make_stage(c.nd, p4_of(PC, k).w);
+    const uint32_t first = FLD(PC, F_V + 1, k), cnt = FLD(PC, F_V + 2, k);
     for (uint32_t q = first; q < first + cnt; ++q) {
       const igs_instruction r = st.instrs[q];
       const uint32_t id = st.map[q];
@@ -2881,26 +2912,19 @@ __device__ __noinline__ void p4_apply(Ctx& c, const WorkJob& j, uint32_t w) {
         return true;
       };
       // a copy reads allocation r.a and writes r.b (reads first, as emit_apply)
-      if (p4_alloc_owner(r.a, j.workers) == w && !apply_read(c, r.a, r.box_cnt, box, id, false)) return false;
-      if (p4_alloc_owner(r.b, j.workers) == w && !apply_write(c, r.b, r.box_cnt, box, id)) return false;
-      if (states)
-        for (uint32_t e = 0; e < r.box_cnt; ++e) {
-          Bx x;
-          box(e, x);
-          t_or(c, B, NONE, x, 2, 1u << pc.m);
-          if (c.err) return false;
-        }
+      if (p4_alloc_owner(r.a, j.workers, states) == w && !apply_read(c, r.a, r.box_cnt, box, id, false)) return false;
+      if (p4_alloc_owner(r.b, j.workers, states) == w && !apply_write(c, r.b, r.box_cnt, box, id)) return false;
     }
-    if (states) t_merge_from(c, B, from_bst);
-    return c.err == ST_OK;
+    return true;
   });
+  if (states && j.workers <= 2 && !c.err) p4_states(c, j);
 }
 
 // Warp 0: plan with the helpers; then, in consumer order, the warnings of
 // uninitialized reads, the copies' final ids and the capacity checks; then
 // the append (warp 0) beside the table updates (helpers).
 __device__ __noinline__ void p4_parallel(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, Table& PC,
-                                         uint32_t na) {
+                                         uint32_t na, bool states_later) {
   BlockShared& sh = *static_cast<BlockShared*>(c.block);
   WorkJob& j = sh.job;
   __syncwarp();
@@ -2917,6 +2941,7 @@ __device__ __noinline__ void p4_parallel(Ctx& c, const igs_task& t, uint32_t seq
     j.workers = c.workers;
     j.devices = c.D;
     j.n_live = c.n_live;
+    j.p4_states_later = states_later ? 1u : 0u;
   }
   if (!run_shared(c, sh, CMD_P4, [&]() { p4_share(c, j, 0); })) return;
   NodeDev* nd = c.nd;
@@ -3239,6 +3264,10 @@ __device__ __forceinline__ void p5_each_planned(const WorkJob& j, uint32_t w, F 
 }
 
 __device__ __noinline__ void p5_plan(Ctx& c, const WorkJob& j, uint32_t w) {
+  if (w == p5_planners(j.workers)) {  // plans nothing: the coherence phase's up-to-date bits
+    if (j.p4_states_later) p4_states(c, j);
+    return;
+  }
   const Table& AL = j.AL;
   const uint32_t na = j.na;
   Table& BT = c.s[S_T4];
@@ -3355,7 +3384,7 @@ __device__ __noinline__ void p5_finish(Ctx& c, const WorkJob& j, uint32_t w) {
 // Warp 0: kernel ids, planners and owners; plan with the helpers; every
 // local kernel's place in the graph; finish with the helpers.
 __device__ __noinline__ void p5_planned(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP,
-                                        Table& AL, uint32_t na) {
+                                        Table& AL, uint32_t na, bool p4_states_pending) {
   BlockShared& sh = *static_cast<BlockShared*>(c.block);
   NodeDev* nd = c.nd;
   const uint32_t planners = p5_planners(c.workers);
@@ -3409,6 +3438,7 @@ __device__ __noinline__ void p5_planned(Ctx& c, const igs_task& t, uint32_t seq,
     j.devices = c.D;
     j.stage_cap = nd->cap_scratch * (F_COUNT * 4 / (uint32_t)sizeof(igs_edge));
     j.stage0 = reinterpret_cast<igs_edge*>(c.s[S_T0].base);
+    j.p4_states_later = p4_states_pending ? 1u : 0u;  // j.PC still holds the coherence consumers
   }
   if (!run_shared(c, sh, CMD_P5_PLAN, [&]() { p5_plan(c, sh.job, 0); })) return;
   // places in chunk order; the first kernel that would overflow a capacity
@@ -3731,24 +3761,45 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     __syncwarp();
   }
   // stale consumers that more than one worker would plan: shared by the
-  // helper warps
+  // helper warps. A consumer whose region meets no other stale consumer of
+  // its (buffer, memory) sees none of their copies, so it goes to the next
+  // worker in turn; the others are planned in order by their pair's worker.
   bool multi = false;
   if (c.block && c.workers > 1 && c.nd->helper_scratch && !c.nd->stage_d2d) {
-    uint32_t used = 0;
     for (uint32_t base = 0; base < PC.n; base += 32) {
       const uint32_t k = base + laneid();
       if (k < PC.n && (t_key(PC, k) & 2u)) {
-        const uint32_t i = t_v(PC, 0, k), b = t.acc[i % na].buffer, m = t_v(CH, 1, i / na);
-        const uint32_t w = p4_worker(b, m, c.D, c.workers);
+        const uint32_t i = t_v(PC, 0, k);
+        FLD(PC, F_P4_WM, k) = t_v(CH, 1, i / na) << 8;
+        FLD(PC, F_P4_BUF, k) = t.acc[i % na].buffer;
+      }
+    }
+    __syncwarp();
+    uint32_t used = 0, turn = 0;
+    for (uint32_t base = 0; base < PC.n; base += 32) {
+      const uint32_t k = base + laneid();
+      const bool stale = k < PC.n && (t_key(PC, k) & 2u);
+      const uint32_t mask = __ballot_sync(FULL, stale);
+      if (stale) {
+        const uint32_t b = FLD(PC, F_P4_BUF, k), m = FLD(PC, F_P4_WM, k) >> 8;
+        const Bx x = t_box(PC, k);
+        bool alone = true;
+        for (uint32_t o = 0; o < PC.n && alone; ++o)
+          if (o != k && (t_key(PC, o) & 2u) && FLD(PC, F_P4_BUF, o) == b && (FLD(PC, F_P4_WM, o) >> 8) == m &&
+              bx_overlap(t_box(PC, o), x))
+            alone = false;
+        const uint32_t w = alone ? (turn + __popc(mask & lanemask_lt())) % c.workers : p4_worker(b, m, c.D, c.workers);
         FLD(PC, F_P4_WM, k) = w | (m << 8);
-        FLD(PC, F_P4_BUF, k) = b;
         used |= 1u << w;
       }
+      turn += __popc(mask);
     }
     multi = __popc(warp_or(used)) >= 2;
   }
+  // a planned kernel phase sets the coherence copies' up-to-date bits
+  const bool p5_shared = c.block && c.workers > 2 && c.nd->helper_scratch && p5_plannable(t);
   if (multi) {
-    p4_parallel(c, t, seq, CH, PC, na);
+    p4_parallel(c, t, seq, CH, PC, na, p5_shared);
     if (c.err) return;
   } else {
     for (uint32_t k = 0; k < PC.n; ++k) {
@@ -3794,7 +3845,7 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
   bool planned = false;
   if (c.block && c.workers > 1 && c.nd->helper_scratch) {
     planned = p5_plannable(t);
-    if (planned) p5_planned(c, t, seq, CH, MP, AL, na);
+    if (planned) p5_planned(c, t, seq, CH, MP, AL, na, multi && p5_shared);
     else p5_parallel(c, t, seq, CH, MP, AL, na);
     if (c.err) return;
   } else {

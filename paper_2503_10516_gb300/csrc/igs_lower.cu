@@ -533,6 +533,11 @@ __device__ __forceinline__ uint32_t warp_or(uint32_t v) {
   return v;
 }
 __device__ __forceinline__ uint32_t warp_sum(uint32_t v) { return __reduce_add_sync(FULL, v); }
+__device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
 // Exclusive prefix sum over the lanes; total: the sum over all lanes.
 __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t& total) {
   uint32_t x = v;
@@ -3617,18 +3622,25 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
       if (in) t_put(RG, s, 0, t_box(c.qr, i), 0, 0, 0);
     }
     __syncwarp();
-    for (uint32_t i = 0; i < RG.n; ++i) wvol += bx_volume(t_box(RG, i));
+    for (uint32_t i = laneid(); i < RG.n; i += 32) wvol += bx_volume(t_box(RG, i));
+    wvol = warp_sum64(wvol);
     const Bx rg_bb = t_bbox(c, RG, 0, RG.n);
     // consumers in (chunk, accessor) order: v0 = consumer index
     t_reset(CONS);
     uint32_t ncons = 0;
     bool whole = true;
-    for (uint32_t slot = 0; slot < CH.n; ++slot) {
-      if (t_v(CH, 0, slot) != c.node) continue;
-      for (uint32_t a = 0; a < na; ++a) {
-        if (t.acc[a].buffer != b || !(t.acc[a].mode & IGS_READ)) continue;
-        const Bx x = t_box(MP, slot * na + a);
-        if (bx_empty(x) || !bx_overlap(x, rg_bb)) continue;  // reads nothing awaited
+    const uint32_t total = CH.n * na;
+    for (uint32_t eb = 0; eb < total; eb += 32) {
+      bool cand = false;
+      if (eb + laneid() < total) {
+        const uint32_t e = eb + laneid(), slot = e / na, a = e % na;
+        if (t_v(CH, 0, slot) == c.node && t.acc[a].buffer == b && (t.acc[a].mode & IGS_READ)) {
+          const Bx x = t_box(MP, e);
+          cand = !bx_empty(x) && bx_overlap(x, rg_bb);  // else it reads nothing awaited
+        }
+      }
+      for (uint32_t cm = __ballot_sync(FULL, cand); cm; cm &= cm - 1) {
+        const Bx x = t_box(MP, eb + __ffs(cm) - 1);
         uint64_t vol = 0;
         const uint32_t from = CONS.n;
         for (uint32_t base = 0; base < RG.n; base += 32) {
@@ -3645,8 +3657,8 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
         }
         __syncwarp();
         if (CONS.n == from) continue;
-        for (uint32_t i = from; i < CONS.n; ++i) vol += bx_volume(t_box(CONS, i));
-        if (vol != wvol) whole = false;
+        for (uint32_t i = from + laneid(); i < CONS.n; i += 32) vol += bx_volume(t_box(CONS, i));
+        if (warp_sum64(vol) != wvol) whole = false;
         ++ncons;
       }
     }

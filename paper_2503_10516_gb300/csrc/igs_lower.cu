@@ -2112,7 +2112,8 @@ struct WorkJob {
   uint32_t n_live;   // coherence: live allocations (NodeDev's count is stale during a launch)
   uint32_t devices;  // coherence and kernel phase: devices per node
   uint32_t horizon;  // a9: the instruction older ids are replaced by
-  uint32_t p4_states_later;  // coherence: the up-to-date bits are set in the planned kernel phase
+  uint32_t p4_states_later;  // coherence: some up-to-date bits are set in the planned kernel phase
+  uint32_t p4_split;         // coherence: copies whose up-to-date bits the apply phase sets (in order)
 };
 
 // Pipelined lowering of one node (a launch with several items): a front
@@ -2866,13 +2867,19 @@ __device__ __noinline__ void p4_share(Ctx& c, WorkJob& j, uint32_t w) {
   c.stage = nullptr;
 }
 
-// The up-to-date bits of the planned copies, in consumer and copy order.
-__device__ __noinline__ void p4_states(Ctx& c, const WorkJob& j) {
+// The up-to-date bits of the planned copies, in consumer and copy order:
+// part 0 the consumers before the one whose copies reach j.p4_split copies,
+// part 1 the others.
+__device__ __noinline__ void p4_states(Ctx& c, const WorkJob& j, int part) {
   const Table& PC = j.PC;
+  uint32_t before = 0;  // copies of the earlier consumers
   p4_each(PC, 2u, NONE, [&](uint32_t k) -> bool {
     const P4Consumer pc = p4_of(PC, k);
     const Stage st = make_stage(c.nd, pc.w);
     const uint32_t first = FLD(PC, F_V + 1, k), cnt = FLD(PC, F_V + 2, k);
+    const bool in_part0 = before < j.p4_split;
+    before += cnt;
+    if (in_part0 != (part == 0)) return true;
     Table B = bst_t(c, pc.b);
     t_tidy(c, B);
     const uint32_t from_bst = B.n;
@@ -2897,9 +2904,9 @@ __device__ __noinline__ void p4_states(Ctx& c, const WorkJob& j) {
 // Helper w's part of the apply phase (the final ids are in the stages' maps).
 __device__ __noinline__ void p4_apply(Ctx& c, const WorkJob& j, uint32_t w) {
   const Table& PC = j.PC;
-  const bool states = !j.p4_states_later;
+  const bool states = j.p4_split != 0;  // some up-to-date bits are set in this phase
   if (states && p4_state_owner(j.workers) == w && j.workers > 2) {
-    p4_states(c, j);
+    p4_states(c, j, 0);
     return;
   }
   p4_each(PC, 2u, NONE, [&](uint32_t k) -> bool {
@@ -2922,7 +2929,7 @@ __device__ __noinline__ void p4_apply(Ctx& c, const WorkJob& j, uint32_t w) {
     }
     return true;
   });
-  if (states && j.workers <= 2 && !c.err) p4_states(c, j);
+  if (states && j.workers <= 2 && !c.err) p4_states(c, j, 0);
 }
 
 // Warp 0: plan with the helpers; then, in consumer order, the warnings of
@@ -2991,6 +2998,10 @@ __device__ __noinline__ void p4_parallel(Ctx& c, const igs_task& t, uint32_t seq
     fail_cap(c, CAP_BOX, nd->cap_box);
     return;
   }
+  __syncwarp();
+  // with a planned kernel phase to follow, about half of the up-to-date bits
+  // wait for it (its last worker plans no kernels)
+  if (laneid() == 0) j.p4_split = states_later ? (next - c.n_instr + 1) / 2 : NONE;
   __syncwarp();
   run_shared(c, sh, CMD_P4_APPLY, [&]() {
     p4_each(PC, 2u, NONE, [&](uint32_t k) -> bool {
@@ -3270,7 +3281,7 @@ __device__ __forceinline__ void p5_each_planned(const WorkJob& j, uint32_t w, F 
 
 __device__ __noinline__ void p5_plan(Ctx& c, const WorkJob& j, uint32_t w) {
   if (w == p5_planners(j.workers)) {  // plans nothing: the coherence phase's up-to-date bits
-    if (j.p4_states_later) p4_states(c, j);
+    if (j.p4_states_later) p4_states(c, j, 1);
     return;
   }
   const Table& AL = j.AL;

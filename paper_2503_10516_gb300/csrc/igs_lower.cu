@@ -237,6 +237,11 @@ struct Ctx {
   // still in S_CH / S_MP and it is known not to allocate (NONE otherwise)
   uint32_t fresh;
   struct Pipe* pipe;  // the block's pipeline with a front warp (warp 0 only), else null
+  // dependencies on allocation snap_alloc come from copies of its writer /
+  // reader tables (snap_tab, snap_n entries) instead (NONE: no copies)
+  uint32_t snap_alloc;
+  const uint32_t* snap_tab[2];
+  uint32_t snap_n[2];
 };
 
 // Instructions a coherence worker emits before their final ids are known:
@@ -1387,12 +1392,13 @@ __device__ __forceinline__ bool emit_deps(Ctx& c, const Acc* acc, int nacc, bool
   for (int k = 0; k < nacc; ++k) {
     const Acc& A = acc[k];
     const uint32_t slot = nd->allocs[A.alloc].slot;
+    const bool snap = A.alloc == c.snap_alloc;
     const int ntab = (A.mode & IGS_WRITE) ? 2 : 1;
     for (int tab = 0; tab < ntab; ++tab) {
       const uint32_t* dsc = (tab == 0 ? nd->wr_d : nd->rd_d) + kDesc * slot;
-      const uint32_t n = dsc[2];
+      const uint32_t n = snap ? c.snap_n[tab] : dsc[2];
       if (n == 0) continue;
-      const uint32_t* tb = nd->heap + (size_t)dsc[0] * F_COUNT;
+      const uint32_t* tb = snap ? c.snap_tab[tab] : nd->heap + (size_t)dsc[0] * F_COUNT;
       c.map_reads += n;
       DT_COUNT(N_PROBE_ENTRIES, n);
       for (uint32_t base = 0; base < n; base += 32) {
@@ -2093,7 +2099,7 @@ __device__ __forceinline__ bool union_is_image(const igs_task& t, uint32_t acc, 
 // then appends the parts' results in the order of the single-warp path.
 enum BlockCmd : uint32_t {
   CMD_NONE = 0, CMD_P5 = 1, CMD_A3 = 2, CMD_P4 = 3, CMD_P4_APPLY = 4, CMD_EXIT = 5, CMD_P5_PLAN = 6, CMD_P5_FINISH = 7,
-  CMD_EPOCH = 8
+  CMD_EPOCH = 8, CMD_P3 = 9
 };
 __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg);
 
@@ -2114,6 +2120,10 @@ struct WorkJob {
   uint32_t horizon;  // a9: the instruction older ids are replaced by
   uint32_t p4_states_later;  // coherence: some up-to-date bits are set in the planned kernel phase
   uint32_t p4_split;         // coherence: copies whose up-to-date bits the apply phase sets (in order)
+  Table qr;                  // pushes and awaits: warp 0's push / await table
+  uint32_t p3_n;             // awaits planned beside the pushes (group gi by helper gi + 1):
+  uint32_t p3_g0[kMaxWorkers], p3_g1[kMaxWorkers], p3_dst[kMaxWorkers];  // qr range, host allocation,
+  uint32_t p3_nw[kMaxWorkers], p3_nr[kMaxWorkers], p3_cnt[kMaxWorkers];  // copied table sizes, planned count
 };
 
 // Pipelined lowering of one node (a launch with several items): a front
@@ -3061,6 +3071,7 @@ __device__ __noinline__ void apply_epoch(Ctx& c, uint32_t h) {
 
 __device__ __noinline__ void p5_plan(Ctx& c, const WorkJob& j, uint32_t w);
 __device__ __noinline__ void p5_finish(Ctx& c, const WorkJob& j, uint32_t w);
+__device__ __noinline__ void p3_plan(Ctx& c, WorkJob& j, uint32_t w);
 
 // Helper warp w: waits for work from warp 0, does its share, reports.
 __device__ void helper_loop(BlockShared& sh, uint32_t w, uint32_t workers) {
@@ -3083,6 +3094,10 @@ __device__ void helper_loop(BlockShared& sh, uint32_t w, uint32_t workers) {
         for (int k = 0; k < 8; ++k) hc.s[tabs[k]].base = helper_table(j.nd, w, k);
         if (cmd == CMD_P4) p4_share(hc, j, w);
         else p4_apply(hc, j, w);
+      } else if (cmd == CMD_P3) {
+        const int tabs[7] = {S_T1, S_T5, S_RG, S_CAN, S_DEP, S_T4, S_CL};
+        for (int k = 0; k < 7; ++k) hc.s[tabs[k]].base = helper_table(j.nd, w, k);
+        p3_plan(hc, j, w);
       } else if (cmd == CMD_EPOCH) {
         hc.n_live = j.n_live;
         epoch_share(hc, j.horizon, w, j.workers);
@@ -3501,31 +3516,10 @@ __device__ __noinline__ void p5_planned(Ctx& c, const igs_task& t, uint32_t seq,
   c.n_bind = n_bind;
 }
 
-// ---- compile one task (P1..P5) ----------------------------------------------
-
-__device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
-  const Item it = c.pg->items[item];
-  const igs_task& t = c.pg->tasks[it.task];
-  const uint32_t seq = it.seq, na = t.num_accessors;
-  Table& CH = c.s[S_CH];
-  Table& MP = c.s[S_MP];
-  PhaseTimer pt = pt_start();
-  // delivered and compiled at once: chunks and mapped boxes are still in
-  // place and the task was found not to allocate
-  const bool fresh = c.fresh == item;
-  if (!fresh) {
-    task_chunks(c, t, CH);
-    task_mapped(c, t, CH, MP);
-  }
-  if (c.err) return;
-  pt_lap(pt, c, PH_SPLIT);
-  // P1 (nothing to do unless some requirement lies outside every allocation)
-  if (!fresh && allocating(c, t, seq, CH, MP)) alloc_phase(c, t, seq, CH, MP);
-  if (c.err) return;
-  pt_lap(pt, c, PH_P1);
-  uint32_t qs, qe;
-  qr_block(c, seq, qs, qe);
-  // P2: pushes, (buffer, target) ascending
+// P2 of task item (qr entries [qs, qe)): per (buffer, target) in ascending
+// order, coherence copies into host memory and one send per (original
+// producer, canonical box).
+__device__ __noinline__ void p2_pushes(Ctx& c, uint32_t seq, uint32_t qs, uint32_t qe) {
   Table& Q = c.s[S_T0];
   Table& G = c.s[S_T1];
   Table& CN = c.s[S_T5];
@@ -3604,122 +3598,120 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
     }
     g0 = g1 + 1;
   }
-  pt_lap(pt, c, PH_P2);
-  // P3: await push per buffer: one receive, or split receive + await receives
+}
+
+// P3 for one await group qr[g0, g1) (its bounding-box entry at g1) into
+// host allocation dst: one receive, or a split receive and one await receive
+// per consumer part. Planned by a helper (c.stage set): the instructions go
+// to its stage and no table changes (p3_finish applies them afterwards).
+__device__ __noinline__ void p3_group(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP,
+                                      const Table& qr, uint32_t g0, uint32_t g1, uint32_t dst) {
+  const uint32_t na = t.num_accessors;
+  const bool plan = c.stage != nullptr;
+  const uint32_t b = t_v(qr, 1, g0);
   Table& CONS = c.s[S_T4];
   Table& COV = c.s[S_CL];
-  for (uint32_t g0 = qs; g0 < qe;) {
-    uint32_t g1 = g0;
-    while (g1 < qe && t_v(c.qr, 0, g1) == t_v(c.qr, 0, g0)) ++g1;
-    const uint32_t kind = t_v(c.qr, 0, g0);
-    if (kind != 1) {
-      g0 = g1 + (kind == 0 ? 1 : 0);
-      continue;
-    }
-    const uint32_t b = t_v(c.qr, 1, g0);
-    const Bx bb = t_box(c.qr, g1);
-    const uint32_t dst = find_alloc(c, b, 1, bb);
-    if (dst == NONE) {
-      fail_internal(c, 7);
-      return;
-    }
-    t_reset(RG);
-    uint64_t wvol = 0;
-    for (uint32_t base = g0; base < g1; base += 32) {
-      const uint32_t i = base + laneid();
-      const bool in = i < g1;
-      const uint32_t s = t_claim(c, RG, in);
-      if (c.err) return;
-      if (in) t_put(RG, s, 0, t_box(c.qr, i), 0, 0, 0);
-    }
-    __syncwarp();
-    for (uint32_t i = laneid(); i < RG.n; i += 32) wvol += bx_volume(t_box(RG, i));
-    wvol = warp_sum64(wvol);
-    const Bx rg_bb = t_bbox(c, RG, 0, RG.n);
-    // consumers in (chunk, accessor) order: v0 = consumer index
-    t_reset(CONS);
-    uint32_t ncons = 0;
-    bool whole = true;
-    const uint32_t total = CH.n * na;
-    for (uint32_t eb = 0; eb < total; eb += 32) {
-      bool cand = false;
-      if (eb + laneid() < total) {
-        const uint32_t e = eb + laneid(), slot = e / na, a = e % na;
-        if (t_v(CH, 0, slot) == c.node && t.acc[a].buffer == b && (t.acc[a].mode & IGS_READ)) {
-          const Bx x = t_box(MP, e);
-          cand = !bx_empty(x) && bx_overlap(x, rg_bb);  // else it reads nothing awaited
-        }
-      }
-      for (uint32_t cm = __ballot_sync(FULL, cand); cm; cm &= cm - 1) {
-        const Bx x = t_box(MP, eb + __ffs(cm) - 1);
-        uint64_t vol = 0;
-        const uint32_t from = CONS.n;
-        for (uint32_t base = 0; base < RG.n; base += 32) {
-          const uint32_t i = base + laneid();
-          Bx is{};
-          bool hit = false;
-          if (i < RG.n) {
-            is = bx_isect(t_box(RG, i), x);
-            hit = !bx_empty(is);
-          }
-          const uint32_t s = t_claim(c, CONS, hit);
-          if (c.err) return;
-          if (hit) t_put(CONS, s, 0, is, ncons, 0, 0);
-        }
-        __syncwarp();
-        if (CONS.n == from) continue;
-        for (uint32_t i = from + laneid(); i < CONS.n; i += 32) vol += bx_volume(t_box(CONS, i));
-        if (warp_sum64(vol) != wvol) whole = false;
-        ++ncons;
+  Table& G = c.s[S_T1];
+  Table& CN = c.s[S_T5];
+  Table& RG = c.s[S_RG];
+  t_reset(RG);
+  uint64_t wvol = 0;
+  for (uint32_t base = g0; base < g1; base += 32) {
+    const uint32_t i = base + laneid();
+    const bool in = i < g1;
+    const uint32_t s = t_claim(c, RG, in);
+    if (c.err) return;
+    if (in) t_put(RG, s, 0, t_box(qr, i), 0, 0, 0);
+  }
+  __syncwarp();
+  for (uint32_t i = laneid(); i < RG.n; i += 32) wvol += bx_volume(t_box(RG, i));
+  wvol = warp_sum64(wvol);
+  const Bx rg_bb = t_bbox(c, RG, 0, RG.n);
+  // consumers in (chunk, accessor) order: v0 = consumer index
+  t_reset(CONS);
+  uint32_t ncons = 0;
+  bool whole = true;
+  const uint32_t total = CH.n * na;
+  for (uint32_t eb = 0; eb < total; eb += 32) {
+    bool cand = false;
+    if (eb + laneid() < total) {
+      const uint32_t e = eb + laneid(), slot = e / na, a = e % na;
+      if (t_v(CH, 0, slot) == c.node && t.acc[a].buffer == b && (t.acc[a].mode & IGS_READ)) {
+        const Bx x = t_box(MP, e);
+        cand = !bx_empty(x) && bx_overlap(x, rg_bb);  // else it reads nothing awaited
       }
     }
-    if (ncons <= 1) whole = true;
-    if (whole) {
-      Acc acc[1] = {{&RG, 0, RG.n, dst, IGS_WRITE}};
-      const uint32_t id = emit(c, IGS_RECEIVE, seq, dst, NONE, b, NONE, &RG, 0, RG.n, acc, 1, false);
+    for (uint32_t cm = __ballot_sync(FULL, cand); cm; cm &= cm - 1) {
+      const Bx x = t_box(MP, eb + __ffs(cm) - 1);
+      uint64_t vol = 0;
+      const uint32_t from = CONS.n;
+      for (uint32_t base = 0; base < RG.n; base += 32) {
+        const uint32_t i = base + laneid();
+        Bx is{};
+        bool hit = false;
+        if (i < RG.n) {
+          is = bx_isect(t_box(RG, i), x);
+          hit = !bx_empty(is);
+        }
+        const uint32_t s = t_claim(c, CONS, hit);
+        if (c.err) return;
+        if (hit) t_put(CONS, s, 0, is, ncons, 0, 0);
+      }
+      __syncwarp();
+      if (CONS.n == from) continue;
+      for (uint32_t i = from + laneid(); i < CONS.n; i += 32) vol += bx_volume(t_box(CONS, i));
+      if (warp_sum64(vol) != wvol) whole = false;
+      ++ncons;
+    }
+  }
+  if (ncons <= 1) whole = true;
+  if (whole) {
+    Acc acc[1] = {{&RG, 0, RG.n, dst, IGS_WRITE}};
+    const uint32_t id = emit(c, IGS_RECEIVE, seq, dst, NONE, b, NONE, &RG, 0, RG.n, acc, 1, false);
+    if (c.err || plan) return;
+    Table B = bst_t(c, b);
+    t_tidy(c, B);
+    const uint32_t from = B.n;
+    for (uint32_t i = 0; i < RG.n; ++i) {
+      t_set(c, B, NONE, t_box(RG, i), id, 1, 1u << 1);
       if (c.err) return;
-      Table B = bst_t(c, b);
-      t_tidy(c, B);
-      const uint32_t from = B.n;
-      for (uint32_t i = 0; i < RG.n; ++i) {
-        t_set(c, B, NONE, t_box(RG, i), id, 1, 1u << 1);
+    }
+    t_merge_from(c, B, from);
+  } else {
+    Acc acc[1] = {{&RG, 0, RG.n, dst, IGS_WRITE}};
+    const uint32_t sid = emit(c, IGS_SPLIT_RECEIVE, seq, dst, NONE, b, NONE, &RG, 0, RG.n, acc, 1, false);
+    if (c.err) return;
+    t_reset(COV);
+    for (uint32_t k = 0; k < ncons; ++k) {
+      // part = consumer k's region minus what earlier await receives cover
+      t_reset(G);
+      for (uint32_t base = 0; base < CONS.n; base += 32) {
+        const uint32_t i = base + laneid();
+        const bool hit = i < CONS.n && t_v(CONS, 0, i) == k;
+        const uint32_t s = t_claim(c, G, hit);
+        if (c.err) return;
+        if (hit) t_put(G, s, 0, t_box(CONS, i), 0, 0, 0);
+      }
+      __syncwarp();
+      for (uint32_t i = 0; i < COV.n; ++i) {
+        t_subtract(c, G, NONE, t_box(COV, i));
         if (c.err) return;
       }
-      t_merge_from(c, B, from);
-    } else {
-      Acc acc[1] = {{&RG, 0, RG.n, dst, IGS_WRITE}};
-      const uint32_t sid = emit(c, IGS_SPLIT_RECEIVE, seq, dst, NONE, b, NONE, &RG, 0, RG.n, acc, 1, false);
+      t_reset(CN);
+      canonical(c, G, 0, G.n, CN);
       if (c.err) return;
-      t_reset(COV);
-      for (uint32_t k = 0; k < ncons; ++k) {
-        // part = consumer k's region minus what earlier await receives cover
-        t_reset(G);
-        for (uint32_t base = 0; base < CONS.n; base += 32) {
-          const uint32_t i = base + laneid();
-          const bool hit = i < CONS.n && t_v(CONS, 0, i) == k;
-          const uint32_t s = t_claim(c, G, hit);
-          if (c.err) return;
-          if (hit) t_put(G, s, 0, t_box(CONS, i), 0, 0, 0);
-        }
-        __syncwarp();
-        for (uint32_t i = 0; i < COV.n; ++i) {
-          t_subtract(c, G, NONE, t_box(COV, i));
-          if (c.err) return;
-        }
-        t_reset(CN);
-        canonical(c, G, 0, G.n, CN);
-        if (c.err) return;
-        if (CN.n == 0) continue;
-        Table& D = c.s[S_DEP];
-        t_reset(D);
-        if (laneid() == 0) {
-          FLD(D, F_V, 0) = sid;
-          FLD(D, F_V + 1, 0) = IGS_DEP_DATAFLOW;
-        }
-        D.n = 1;
-        __syncwarp();
-        const uint32_t aid = emit(c, IGS_AWAIT_RECEIVE, seq, dst, sid, b, NONE, &CN, 0, CN.n, nullptr, 0, true);
-        if (c.err) return;
+      if (CN.n == 0) continue;
+      Table& D = c.s[S_DEP];
+      t_reset(D);
+      if (laneid() == 0) {
+        FLD(D, F_V, 0) = sid;
+        FLD(D, F_V + 1, 0) = IGS_DEP_DATAFLOW;
+      }
+      D.n = 1;
+      __syncwarp();
+      const uint32_t aid = emit(c, IGS_AWAIT_RECEIVE, seq, dst, sid, b, NONE, &CN, 0, CN.n, nullptr, 0, true);
+      if (c.err) return;
+      if (!plan) {
         Table WR = wr_t(c, dst);
         Table B = bst_t(c, b);
         t_tidy(c, WR);
@@ -3733,18 +3725,248 @@ __device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
         }
         t_merge_from(c, WR, fw);
         t_merge_from(c, B, fb);
-        for (uint32_t base = 0; base < CN.n; base += 32) {
-          const uint32_t i = base + laneid();
-          const bool in = i < CN.n;
-          const uint32_t s = t_claim(c, COV, in);
-          if (c.err) return;
-          if (in) t_put(COV, s, 0, t_box(CN, i), 0, 0, 0);
-        }
-        __syncwarp();
       }
+      for (uint32_t base = 0; base < CN.n; base += 32) {
+        const uint32_t i = base + laneid();
+        const bool in = i < CN.n;
+        const uint32_t s = t_claim(c, COV, in);
+        if (c.err) return;
+        if (in) t_put(COV, s, 0, t_box(CN, i), 0, 0, 0);
+      }
+      __syncwarp();
     }
+  }
+}
+
+// P2 with P3 beside it (helper warps): the await groups' receives are planned
+// by helpers 1, 2, ... (one group each) while warp 0 emits the pushes. A
+// receive writes host memory the node awaits; a push reads and sends what
+// the node owns, so the two phases touch disjoint regions of a host
+// allocation and never depend on one another. The planner finds a receive's
+// dependencies in a copy of its allocation's tables taken before the pushes.
+// Afterwards warp 0 appends the planned instructions in group order and
+// applies their table updates as the single-warp path does. Returns false
+// (nothing done) when the phases stay sequential.
+__device__ __noinline__ void p3_plan(Ctx& c, WorkJob& j, uint32_t w) {
+  const uint32_t gi = w - 1;
+  if (w == 0 || gi >= j.p3_n) return;
+  Stage st = make_stage(c.nd, w);
+  c.stage = &st;
+  const uint32_t nw = j.p3_nw[gi];
+  c.snap_alloc = j.p3_dst[gi];
+  c.snap_tab[0] = helper_table(c.nd, w, 7);
+  c.snap_n[0] = nw;
+  c.snap_tab[1] = c.snap_tab[0] + (size_t)nw * F_COUNT;
+  c.snap_n[1] = j.p3_nr[gi];
+  p3_group(c, *j.task, j.seq, j.CH, j.MP, j.qr, j.p3_g0[gi], j.p3_g1[gi], j.p3_dst[gi]);
+  __syncwarp();
+  if (laneid() == 0) j.p3_cnt[gi] = st.n_instr;
+  c.stage = nullptr;
+  c.snap_alloc = NONE;
+}
+
+__device__ __noinline__ bool p23_parallel(Ctx& c, const igs_task& t, uint32_t seq, const Table& CH, const Table& MP,
+                                          uint32_t qs, uint32_t qe) {
+  if (!c.block || c.workers < 2 || !c.nd->helper_scratch || c.nd->stage_d2d) return false;
+  NodeDev* nd = c.nd;
+  BlockShared& sh = *static_cast<BlockShared*>(c.block);
+  WorkJob& j = sh.job;
+  // the groups: pushes to overlap with, awaits that fit one helper each
+  uint32_t n = 0, pushes = 0;
+  uint32_t g0s[kMaxWorkers], g1s[kMaxWorkers], dsts[kMaxWorkers];
+  for (uint32_t g0 = qs; g0 < qe;) {
+    uint32_t g1 = g0;
+    while (g1 < qe && t_v(c.qr, 0, g1) == t_v(c.qr, 0, g0)) ++g1;
+    const uint32_t kind = t_v(c.qr, 0, g0);
+    if (kind == 0) ++pushes;
+    if (kind != 1) {
+      g0 = g1 + (kind == 0 ? 1 : 0);
+      continue;
+    }
+    if (n + 1 >= c.workers) return false;
+    const uint32_t dst = find_alloc(c, t_v(c.qr, 1, g0), 1, t_box(c.qr, g1));
+    if (dst == NONE) {
+      fail_internal(c, 7);
+      return false;
+    }
+    const Table WR = wr_t(c, dst), RD = rd_t(c, dst);
+    if (WR.n + RD.n > nd->cap_scratch) return false;
+    g0s[n] = g0;
+    g1s[n] = g1;
+    dsts[n] = dst;
+    ++n;
     g0 = g1 + 1;
   }
+  if (n == 0 || pushes == 0) return false;
+  // the copies of the receiving allocations' tables (writers, then readers)
+  for (uint32_t gi = 0; gi < n; ++gi) {
+    const Table WR = wr_t(c, dsts[gi]), RD = rd_t(c, dsts[gi]);
+    uint4* out = reinterpret_cast<uint4*>(helper_table(nd, gi + 1, 7));
+    const uint32_t q = F_COUNT / 4;  // 16-byte words per entry
+    const uint4* w4 = reinterpret_cast<const uint4*>(WR.base);
+    const uint4* r4 = reinterpret_cast<const uint4*>(RD.base);
+    for (uint32_t k = laneid(); k < WR.n * q; k += 32) out[k] = w4[k];
+    for (uint32_t k = laneid(); k < RD.n * q; k += 32) out[WR.n * q + k] = r4[k];
+    if (laneid() == 0) {
+      j.p3_g0[gi] = g0s[gi];
+      j.p3_g1[gi] = g1s[gi];
+      j.p3_dst[gi] = dsts[gi];
+      j.p3_nw[gi] = WR.n;
+      j.p3_nr[gi] = RD.n;
+    }
+  }
+  __syncwarp();
+  if (laneid() == 0) {
+    j.nd = nd;
+    j.pg = c.pg;
+    j.task = &t;
+    j.CH = CH;
+    j.MP = MP;
+    j.qr = c.qr;
+    j.na = t.num_accessors;
+    j.seq = seq;
+    j.epoch = c.epoch;
+    j.node = c.node;
+    j.workers = c.workers;
+    j.p3_n = n;
+  }
+  if (!run_shared(c, sh, CMD_P3, [&]() { p2_pushes(c, seq, qs, qe); })) return true;
+  // the planned instructions in group order, each with the single-warp
+  // path's table updates
+  for (uint32_t gi = 0; gi < n && !c.err; ++gi) {
+    const Stage st = make_stage(nd, gi + 1);
+    const uint32_t dst = j.p3_dst[gi], b = t_v(c.qr, 1, j.p3_g0[gi]), cnt = j.p3_cnt[gi];
+    for (uint32_t q = 0; q < cnt; ++q) {
+      const igs_instruction r = st.instrs[q];
+      const uint32_t id = c.n_instr;
+      if (c.n_instr + 1 > nd->cap_instr || c.n_edge + r.bind_cnt > nd->cap_edge) {
+        fail_cap(c, CAP_EDGE, nd->cap_edge);
+        return true;
+      }
+      if (c.n_box + r.box_cnt > nd->cap_box) {
+        fail_cap(c, CAP_BOX, nd->cap_box);
+        return true;
+      }
+      __syncwarp();
+      if (laneid() == 0) {
+        st.map[q] = id;
+        nd->has_succ[id] = 0;
+      }
+      __syncwarp();
+      for (uint32_t e = laneid(); e < r.bind_cnt; e += 32) {
+        igs_edge ed = st.edges[r.bind_off + e];
+        if (ed.from & PROV) {  // the split receive of this group
+          ed.from = st.map[ed.from & 0xFFFFFFu];
+          nd->has_succ[ed.from] = 1;
+        }
+        ed.to = id;
+        nd->edges[c.n_edge + e] = ed;
+      }
+      for (uint32_t e = laneid(); e < r.box_cnt; e += 32) nd->boxes[c.n_box + e] = st.boxes[r.box_off + e];
+      if (laneid() == 0) {
+        igs_instruction o = r;
+        o.id = id;
+        if (o.b != NONE && (o.b & PROV)) o.b = st.map[o.b & 0xFFFFFFu];  // an await receive's split receive
+        o.box_off = c.n_box;
+        o.bind_off = c.n_bind;
+        o.bind_cnt = 0;
+        nd->instrs[id] = o;
+      }
+      c.n_edge += r.bind_cnt;
+      c.n_box += r.box_cnt;
+      c.n_instr += 1;
+      __syncwarp();
+      auto box = [&](uint32_t e, Bx& x) {
+        const igs_box o = st.boxes[r.box_off + e];
+        for (int d = 0; d < 3; ++d) {
+          x.lo[d] = o.lo[d];
+          x.hi[d] = o.hi[d];
+        }
+        return true;
+      };
+      if (r.type == IGS_RECEIVE || r.type == IGS_SPLIT_RECEIVE) {
+        if (!apply_write(c, dst, r.box_cnt, box, id)) return true;
+        if (r.type == IGS_SPLIT_RECEIVE) continue;
+        Table B = bst_t(c, b);
+        t_tidy(c, B);
+        const uint32_t from = B.n;
+        for (uint32_t e = 0; e < r.box_cnt; ++e) {
+          Bx x;
+          box(e, x);
+          t_set(c, B, NONE, x, id, 1, 1u << 1);
+          if (c.err) return true;
+        }
+        t_merge_from(c, B, from);
+      } else {  // an await receive
+        Table WR = wr_t(c, dst);
+        Table B = bst_t(c, b);
+        t_tidy(c, WR);
+        t_tidy(c, B);
+        const uint32_t fw = WR.n, fb = B.n;
+        for (uint32_t e = 0; e < r.box_cnt; ++e) {
+          Bx x;
+          box(e, x);
+          t_set(c, WR, NONE, x, id, 0, 0);
+          t_set(c, B, NONE, x, id, 1, 1u << 1);
+          if (c.err) return true;
+        }
+        t_merge_from(c, WR, fw);
+        t_merge_from(c, B, fb);
+      }
+    }
+  }
+  return true;
+}
+
+// ---- compile one task (P1..P5) ----------------------------------------------
+
+__device__ __noinline__ void compile_task(Ctx& c, uint32_t item) {
+  const Item it = c.pg->items[item];
+  const igs_task& t = c.pg->tasks[it.task];
+  const uint32_t seq = it.seq, na = t.num_accessors;
+  Table& CH = c.s[S_CH];
+  Table& MP = c.s[S_MP];
+  PhaseTimer pt = pt_start();
+  // delivered and compiled at once: chunks and mapped boxes are still in
+  // place and the task was found not to allocate
+  const bool fresh = c.fresh == item;
+  if (!fresh) {
+    task_chunks(c, t, CH);
+    task_mapped(c, t, CH, MP);
+  }
+  if (c.err) return;
+  pt_lap(pt, c, PH_SPLIT);
+  // P1 (nothing to do unless some requirement lies outside every allocation)
+  if (!fresh && allocating(c, t, seq, CH, MP)) alloc_phase(c, t, seq, CH, MP);
+  if (c.err) return;
+  pt_lap(pt, c, PH_P1);
+  uint32_t qs, qe;
+  qr_block(c, seq, qs, qe);
+  // P2: pushes; P3: awaits (with helper warps, P3 is planned beside P2)
+  if (!p23_parallel(c, t, seq, CH, MP, qs, qe)) {
+    if (c.err) return;
+    p2_pushes(c, seq, qs, qe);
+    if (c.err) return;
+    pt_lap(pt, c, PH_P2);
+    for (uint32_t g0 = qs; g0 < qe;) {
+      uint32_t g1 = g0;
+      while (g1 < qe && t_v(c.qr, 0, g1) == t_v(c.qr, 0, g0)) ++g1;
+      const uint32_t kind = t_v(c.qr, 0, g0);
+      if (kind != 1) {
+        g0 = g1 + (kind == 0 ? 1 : 0);
+        continue;
+      }
+      const uint32_t dst = find_alloc(c, t_v(c.qr, 1, g0), 1, t_box(c.qr, g1));
+      if (dst == NONE) {
+        fail_internal(c, 7);
+        return;
+      }
+      p3_group(c, t, seq, CH, MP, c.qr, g0, g1, dst);
+      if (c.err) return;
+      g0 = g1 + 1;
+    }
+  }
+  if (c.err) return;
   pt_lap(pt, c, PH_P3);
   // P4: coherence for every reading accessor, (chunk, accessor) order.
   // Pre-check, one lane per consumer: does its box overlap never-written data
@@ -4232,6 +4454,7 @@ __device__ void load_ctx(Ctx& c, NodeDev* nd, const ProgDev* pg) {
   c.block = nullptr;
   c.workers = 1;
   c.stage = nullptr;
+  c.snap_alloc = NONE;
   c.helper = false;
   c.fresh = NONE;
   c.pipe = nullptr;
